@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test ties one oracle routine to a closed form, an invariant of the
+diffusion-map construction (Algorithm 1, Eq. W, Eq. 2.18, Algorithm 2), brute
+force on tiny inputs, or a library special case, so that a dropped term, a
+wrong sign or index or a transposed operand in oracle.c fails at least one.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _scurve(n, seed=0):
+    return synth.as_f32(synth.s_curve(n, seed))
+
+
+# ---------------------------------------------------------------- generator
+
+def test_splitmix64_published_outputs():
+    want = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if l.startswith("0x")]
+    assert O.splitmix64_sequence(0, 3) == want
+
+
+def test_counter_stream_is_the_sequential_generator():
+    # or_rng(key, c) must be the (c+1)-th output of the sequential generator started at key
+    key = O.stream_key(7, 1, 42)
+    assert [O.rng(key, c) for c in range(5)] == O.splitmix64_sequence(key, 5)
+
+
+# ---------------------------------------------------------------- kernel, bandwidth, degrees
+
+def test_sqdist_bruteforce():
+    X = _scurve(20, 3)
+    Xd = X.astype(np.float64)
+    for i, j in [(0, 1), (5, 19), (7, 7)]:
+        assert O.sqdist(X, i, j) == pytest.approx(float(np.sum((Xd[i] - Xd[j]) ** 2)), rel=1e-15, abs=0)
+
+
+def test_median_all_pairs_matches_numpy():
+    X = _scurve(301, 5)  # 45150 pairs (odd count -> the middle value)
+    Xd = X.astype(np.float64)
+    iu = np.triu_indices(301, 1)
+    d2 = np.sum((Xd[iu[0]] - Xd[iu[1]]) ** 2, axis=1)
+    assert O.median_sqdist(X) == pytest.approx(float(np.median(d2)), rel=1e-15)
+    X2 = _scurve(300, 6)  # even count -> mean of the two middle values
+    Xd = X2.astype(np.float64)
+    iu = np.triu_indices(300, 1)
+    d2 = np.sum((Xd[iu[0]] - Xd[iu[1]]) ** 2, axis=1)
+    assert O.median_sqdist(X2) == pytest.approx(float(np.median(d2)), rel=1e-15)
+
+
+def test_median_sampled_pairs():
+    n = 1500  # 1,124,250 pairs > 2^20 -> 2^20 seeded pairs
+    X = _scurve(n, 2)
+    Xd = X.astype(np.float64)
+    key = O.stream_key(11, 3, 0)
+    m = 1 << 20
+    u = np.array(O.splitmix64_sequence(key, 2 * m), dtype=np.uint64)
+    i = ((u[0::2] >> np.uint64(32)) * np.uint64(n)) >> np.uint64(32)
+    j = ((u[1::2] >> np.uint64(32)) * np.uint64(n - 1)) >> np.uint64(32)
+    j = j + (j >= i)
+    i, j = i.astype(np.int64), j.astype(np.int64)
+    assert np.all(i != j)
+    d2 = np.sum((Xd[i] - Xd[j]) ** 2, axis=1)
+    assert O.median_sqdist(X, seed=11) == pytest.approx(float(np.median(d2)), rel=1e-15)
+
+
+def test_degrees_bruteforce_tiny():
+    X = _scurve(9, 4)
+    eps, alpha = 0.7, 1.0
+    pts = [[float(v) for v in row] for row in X]
+    n = len(pts)
+
+    def w(i, j):
+        return math.exp(-sum((a - b) ** 2 for a, b in zip(pts[i], pts[j])) / eps)
+
+    q = [sum(w(i, j) for j in range(n)) for i in range(n)]
+    walpha = [[w(i, j) / (q[i] ** alpha * q[j] ** alpha) for j in range(n)] for i in range(n)]
+    dg = [sum(r) for r in walpha]
+    s = [q[i] ** -alpha / math.sqrt(dg[i]) for i in range(n)]
+    oq, odg, os_ = O.degrees(X, eps, alpha)
+    np.testing.assert_allclose(oq, q, rtol=1e-14)
+    np.testing.assert_allclose(odg, dg, rtol=1e-14)
+    np.testing.assert_allclose(os_, s, rtol=1e-14)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.0])
+def test_markov_rows_sum_to_one(alpha):
+    X = _scurve(200, 1)
+    eps = O.median_sqdist(X)
+    W = O.kernel_W(X, eps)
+    q, dg, s = O.degrees(X, eps, alpha)
+    Wa = W / np.outer(q ** alpha, q ** alpha)
+    P = Wa / dg[:, None]  # Algorithm 1 step 3 with the row-sum denominator
+    np.testing.assert_allclose(P.sum(axis=1), 1.0, rtol=0, atol=1e-13)
+    # S = diag(s) W diag(s) is the symmetric conjugate Dg^1/2 P Dg^-1/2
+    S = s[:, None] * W * s[None, :]
+    np.testing.assert_allclose(S, np.sqrt(dg)[:, None] * P / np.sqrt(dg)[None, :], rtol=1e-12, atol=0)
+
+
+def test_alpha_zero_special_case():
+    X = _scurve(150, 2)
+    eps = O.median_sqdist(X)
+    q, dg, s = O.degrees(X, eps, 0.0)
+    np.testing.assert_allclose(dg, q, rtol=1e-14)  # W^0 = W
+    np.testing.assert_allclose(s, q ** -0.5, rtol=1e-14)
+
+
+def test_top_eigenpair_is_one_and_sqrt_degree():
+    X = _scurve(300, 8)
+    eps = O.median_sqdist(X)
+    q, dg, s = O.degrees(X, eps, 1.0)
+    phi = np.sqrt(dg)
+    y = O.S_matvec(X, eps, s, phi)
+    np.testing.assert_allclose(y, phi, rtol=1e-13)
+    W = O.kernel_W(X, eps)
+    ev, V = O.jacobi(s[:, None] * W * s[None, :])
+    assert ev[0] == pytest.approx(1.0, abs=1e-13)
+    v = V[:, 0] * np.sign(V[0, 0])
+    np.testing.assert_allclose(v, phi / np.linalg.norm(phi) * np.sign(phi[0]), atol=1e-12)
+    assert ev[1] < 1.0 - 1e-6
+
+
+@pytest.mark.parametrize("n,eps", [(64, 0.5), (101, 2.0), (48, 0.05)])
+def test_circle_closed_form_spectrum(n, eps):
+    """Equally spaced points on a circle: W is circulant (w_k = exp(-(2R sin(pi k/n))^2/eps)),
+    q is constant, S = W / sum_k w_k and its eigenvalues are the DFT of w over sum w.
+    Float32 storage of the coordinates perturbs distances by ~1e-7, hence the tolerance."""
+    X = synth.as_f32(synth.circle(n, 1.0))
+    wk = np.array([math.exp(-(2.0 * math.sin(math.pi * k / n)) ** 2 / eps) for k in range(n)])
+    lam = np.array([sum(wk[k] * math.cos(2 * math.pi * k * m / n) for k in range(n)) for m in range(n)]) / wk.sum()
+    q, dg, s = O.degrees(X, eps, 1.0)
+    np.testing.assert_allclose(q, wk.sum(), rtol=1e-6)
+    W = O.kernel_W(X, eps)
+    ev, _ = O.jacobi(s[:, None] * W * s[None, :])
+    np.testing.assert_allclose(ev, np.sort(lam)[::-1], rtol=0, atol=2e-6)
+
+
+# ---------------------------------------------------------------- dense eigensolvers
+
+def test_jacobi_matches_library_eigh():
+    g = np.random.default_rng(3)
+    B = g.normal(size=(40, 40))
+    A = B + B.T
+    ev, V = O.jacobi(A)
+    ref = np.linalg.eigh(A)[0][::-1]
+    np.testing.assert_allclose(ev, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(V.T @ V, np.eye(40), atol=1e-12)
+    np.testing.assert_allclose(A @ V, V * ev[None, :], atol=1e-11)
+
+
+def test_jacobi_tridiagonal_closed_form():
+    n = 37
+    A = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    ev, _ = O.jacobi(A)
+    want = np.sort(2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))[::-1]
+    np.testing.assert_allclose(ev, want, atol=1e-13)
+
+
+def test_lanczos_on_diagonal_matrix():
+    n = 200
+    d = np.linspace(0.0, 1.0, n) ** 3
+    ev, V, it, st = O.lanczos_dense(np.diag(d), k=6, conv_tol=1e-12)
+    assert st == 0
+    np.testing.assert_allclose(ev, np.sort(d)[::-1][:6], atol=1e-13)
+    for i in range(6):
+        j = n - 1 - i
+        assert abs(abs(V[j, i]) - 1.0) < 1e-9
+
+
+def test_lanczos_matches_jacobi_on_S():
+    X = _scurve(400, 9)
+    eps = O.median_sqdist(X)
+    q, dg, s = O.degrees(X, eps, 1.0)
+    W = O.kernel_W(X, eps)
+    S = s[:, None] * W * s[None, :]
+    evj, Vj = O.jacobi(S)
+    k = 10
+    ev, V, it, st = O.lanczos_S(X, eps, s, k, conv_tol=1e-12)
+    assert st == 0 and it < 200
+    np.testing.assert_allclose(ev, evj[:k], rtol=1e-11)
+    for i in range(k):
+        c = abs(float(V[:, i] @ Vj[:, i]))
+        assert math.acos(min(1.0, c)) < 1e-6
+    # sign convention: largest-magnitude entry positive
+    for i in range(k):
+        assert V[np.argmax(np.abs(V[:, i])), i] > 0
+
+
+# ---------------------------------------------------------------- tree
+
+def test_tree_depth_and_ranges():
+    assert O.tree_depth(100_000, 512) == 8
+    assert O.tree_depth(2048, 128) == 4
+    assert O.tree_depth(60_000, 256) == 8
+    assert O.tree_depth(512, 512) == 0
+    assert O.tree_depth(513, 512) == 1
+    n, L = 100_000, 8
+    sizes = [O.node_range(n, (1 << L) - 1 + k)[1] for k in range(1 << L)]
+    assert sum(sizes) == n and set(sizes) == {390, 391}
+    st = 0
+    for k in range(1 << L):
+        s0, sz = O.node_range(n, (1 << L) - 1 + k)
+        assert s0 == st
+        st += sz
+
+
+def test_tree_split_rule_bruteforce():
+    n, leaf = 700, 60
+    X = _scurve(n, 12)
+    Xd = X.astype(np.float64)
+    eps = O.median_sqdist(X)
+    perm, L = O.tree(X, eps, leaf)
+    assert sorted(perm.tolist()) == list(range(n))
+    assert L == O.tree_depth(n, leaf)
+
+    def W(i, idx):
+        return np.exp(-np.sum((Xd[idx] - Xd[i]) ** 2, axis=1) / eps)
+
+    for node in range((1 << L) - 1):
+        st, sz = O.node_range(n, node)
+        idx = np.sort(perm[st:st + sz])
+        lst, lsz = O.node_range(n, 2 * node + 1)
+        left = perm[lst:lst + lsz]
+        right = perm[lst + lsz:st + sz]
+        assert lsz == (sz + 1) // 2
+        i0 = idx[0]
+        w0 = W(i0, idx)
+        p = idx[np.lexsort((idx, w0))[0]]
+        wp = W(p, idx)
+        q = idx[np.lexsort((idx, wp))[0]]
+        key = {int(i): float(v) for i, v in zip(idx, W(q, idx) - wp)}
+        kl = max((key[int(i)], int(i)) for i in left)
+        kr = min((key[int(i)], int(i)) for i in right)
+        assert kl < kr
+    # leaves keep their points in increasing original index
+    for k in range(1 << L):
+        st, sz = O.node_range(n, (1 << L) - 1 + k)
+        assert np.all(np.diff(perm[st:st + sz]) > 0)
+
+
+# ---------------------------------------------------------------- skeletonization and HSS matvec
+
+def _setup(n, seed, leaf):
+    X = _scurve(n, seed)
+    eps = O.median_sqdist(X)
+    q, dg, s = O.degrees(X, eps, 1.0)
+    return X, eps, s
+
+
+def test_hmatvec_exact_at_zero_tolerance_full_rank():
+    X, eps, s = _setup(256, 3, 32)
+    H = O.compress(X, eps, s, 32, 0.0, 256)
+    x = synth.random_rhs(256, 3, 5)
+    y = O.S_matvec(X, eps, s, x)
+    yh = O.hmatvec(X, eps, s, H, x)
+    np.testing.assert_allclose(yh, y, rtol=0, atol=1e-13 * np.abs(y).max())
+
+
+def test_interpolative_decomposition_exact_low_rank_block():
+    """With every off-node row sampled and tol 0, each node's ID reproduces its sampled
+    block exactly: K(R, C) = K(R, J) P with P(:, J) = I."""
+    n = 256
+    X, eps, s = _setup(n, 4, 32)
+    perm, L = O.tree(X, eps, 32)
+    H = O.skeletonize(X, eps, s, perm, L, 0.0, 40, seed=0)  # rank cap 40 < leaf: P nontrivial
+    W = O.kernel_W(X, eps)
+    K = s[:, None] * W * s[None, :]
+    Kp = K[np.ix_(perm, perm)]
+    for node in [(1 << L) - 1, (1 << L), 3, 1]:
+        st, sz = O.node_range(n, node)
+        r = H.ranks[node]
+        lvl = int(math.log2(node + 1))
+        if lvl == L:
+            C = np.arange(st, st + sz)
+        else:
+            l, rr = 2 * node + 1, 2 * node + 2
+            C = np.concatenate([H.skel[l * H.max_rank:l * H.max_rank + H.ranks[l]],
+                                H.skel[rr * H.max_rank:rr * H.max_rank + H.ranks[rr]]])
+        Pn = H.P[node * H.max_rank * H.cmax:(node + 1) * H.max_rank * H.cmax].reshape(H.max_rank, H.cmax)[:r, :len(C)]
+        J = H.skel[node * H.max_rank:node * H.max_rank + r]
+        off = np.concatenate([np.arange(0, st), np.arange(st + sz, n)])
+        A = Kp[np.ix_(off, C)]
+        # skeleton columns are identity columns of P
+        cols = [int(np.where(C == j)[0][0]) for j in J]
+        np.testing.assert_allclose(Pn[:, cols], np.eye(r), atol=0)
+        err = np.linalg.norm(A - Kp[np.ix_(off, J)] @ Pn) / np.linalg.norm(A)
+        # rank-capped ID: error at most the discarded singular part, and exact when rank == |C|
+        if r == len(C):
+            assert err < 1e-13
+        else:
+            sv = np.linalg.svd(A, compute_uv=False)
+            assert err <= 50 * sv[r] / sv[0] + 1e-14
+
+
+def test_hmatvec_error_decreases_with_tolerance():
+    n = 1024
+    X, eps, s = _setup(n, 6, 64)
+    x = synth.random_rhs(n, 1, 2)[:, 0]
+    y = O.S_matvec(X, eps, s, x)
+    errs = []
+    for tol in [1e-2, 1e-4, 1e-6, 1e-8]:
+        H = O.compress(X, eps, s, 64, tol, 64)
+        errs.append(np.linalg.norm(O.hmatvec(X, eps, s, H, x) - y) / np.linalg.norm(y))
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[1] < 1e-2 and errs[3] < 1e-5
+
+
+def test_hmatvec_is_symmetric():
+    """Far field is P_l^T K(S_l,S_r) P_r + its transpose: x^T K~ y = y^T K~ x."""
+    n = 900
+    X, eps, s = _setup(n, 7, 50)
+    H = O.compress(X, eps, s, 50, 1e-3, 20)
+    xy = synth.random_rhs(n, 2, 9)
+    a = float(xy[:, 0] @ O.hmatvec(X, eps, s, H, xy[:, 1]))
+    b = float(xy[:, 1] @ O.hmatvec(X, eps, s, H, xy[:, 0]))
+    assert abs(a - b) <= 1e-13 * abs(a)
+
+
+def test_rank_caps():
+    n = 1000
+    X, eps, s = _setup(n, 2, 100)
+    H = O.compress(X, eps, s, 100, 1e-12, 17)
+    assert H.ranks[0] == 0
+    assert H.ranks[1:].max() <= 17
+    assert np.all(H.ranks[1:] >= 1)
+
+
+def test_lanczos_on_hmatrix_approaches_exact():
+    n = 1024
+    X, eps, s = _setup(n, 1, 64)
+    ev, _, _, st = O.lanczos_S(X, eps, s, 8, conv_tol=1e-11)
+    assert st == 0
+    errs = []
+    for tol in [1e-3, 1e-6]:
+        H = O.compress(X, eps, s, 64, tol, 64)
+        evh, _, _, sth = O.lanczos_hmat(X, eps, s, H, 8, conv_tol=1e-11)
+        assert sth == 0
+        errs.append(np.max(np.abs(evh - ev) / ev))
+    assert errs[1] < errs[0] and errs[1] < 1e-5
+
+
+def test_golden_scurve_2048_regression():
+    """Oracle output at the 2048-point s-curve workload, stored by tests/golden/make_golden.py."""
+    import json
+    g = json.load(open(os.path.join(GOLDEN, "scurve_n2048.json")))
+    X = _scurve(2048, 0)
+    eps = O.median_sqdist(X)
+    assert eps == pytest.approx(g["eps"], rel=1e-15)
+    q, dg, s = O.degrees(X, eps, 1.0)
+    ev, _, _, st = O.lanczos_S(X, eps, s, 10, conv_tol=1e-10)
+    assert st == 0
+    np.testing.assert_allclose(ev, g["evals_top10"], rtol=1e-10)
