@@ -214,13 +214,15 @@ static int or_cmp_keyed(const void *a, const void *b) {
 }
 
 /* Farthest point from `from` in the Gram distance of W, d^2(i,j) = W_ii + W_jj - 2 W_ij
- * = 2 - 2 W_ij: the minimiser of W_from,i, ties to the lowest original index. */
-static int32_t or_farthest(const float *X, int32_t d, double eps, const int32_t *idx, int64_t n, int32_t from) {
+ * = 2 - 2 exp(-r_ij^2 / eps). That distance is strictly increasing in r_ij^2 (Eq. W),
+ * so the farthest point is the one with the largest squared distance; comparing r^2
+ * keeps the integer decision free of exp rounding. Ties go to the lowest original index. */
+static int32_t or_farthest(const float *X, int32_t d, const int32_t *idx, int64_t n, int32_t from) {
     int32_t best = idx[0];
-    double bw = or_w(X, d, eps, from, idx[0]);
+    double br = or_sqdist(X, d, from, idx[0]);
     for (int64_t t = 1; t < n; ++t) {
-        double w = or_w(X, d, eps, from, idx[t]);
-        if (w < bw || (w == bw && idx[t] < best)) { bw = w; best = idx[t]; }
+        double r = or_sqdist(X, d, from, idx[t]);
+        if (r > br || (r == br && idx[t] < best)) { br = r; best = idx[t]; }
     }
     return best;
 }
@@ -231,8 +233,8 @@ static int32_t or_farthest(const float *X, int32_t d, double eps, const int32_t 
  * go left; each child keeps increasing original-index order. */
 static void or_split(const float *X, int32_t d, double eps, int32_t *idx, int64_t n) {
     int32_t i0 = idx[0];
-    int32_t p = or_farthest(X, d, eps, idx, n, i0);
-    int32_t q = or_farthest(X, d, eps, idx, n, p);
+    int32_t p = or_farthest(X, d, idx, n, i0);
+    int32_t q = or_farthest(X, d, idx, n, p);
     or_keyed *kv = (or_keyed *)malloc(sizeof(or_keyed) * (size_t)n);
     for (int64_t t = 0; t < n; ++t) {
         kv[t].key = or_w(X, d, eps, idx[t], q) - or_w(X, d, eps, idx[t], p);

@@ -232,10 +232,13 @@ def test_tree_split_rule_bruteforce():
         right = perm[lst + lsz:st + sz]
         assert lsz == (sz + 1) // 2
         i0 = idx[0]
-        w0 = W(i0, idx)
-        p = idx[np.lexsort((idx, w0))[0]]
+        # farthest in the Gram distance 2 - 2 W: largest squared distance, lowest index on ties
+        r0 = np.sum((Xd[idx] - Xd[i0]) ** 2, axis=1)
+        p = idx[np.lexsort((idx, -r0))[0]]
+        assert W(i0, idx)[np.searchsorted(idx, p)] == W(i0, idx).min()
+        rp = np.sum((Xd[idx] - Xd[p]) ** 2, axis=1)
+        q = idx[np.lexsort((idx, -rp))[0]]
         wp = W(p, idx)
-        q = idx[np.lexsort((idx, wp))[0]]
         key = {int(i): float(v) for i, v in zip(idx, W(q, idx) - wp)}
         kl = max((key[int(i)], int(i)) for i in left)
         kr = min((key[int(i)], int(i)) for i in right)
