@@ -1,0 +1,182 @@
+/*
+ * dmaps.h -- C ABI of the GB300 (sm_103a) diffusion-map eigensolver.
+ *
+ * The library computes the top-k eigenpairs of the diffusion-map matrix of
+ * Gaddameedi, Reiz, Neckel, Bungartz, "Efficient and Scalable Kernel Matrix
+ * Approximations using Hierarchical Decomposition" (arXiv 2311.06115):
+ *
+ *   W_ij  = exp(-||x_i - x_j||^2 / eps)                 (Eq. W, eps = sigma^2)
+ *   q     = W 1,  W^a_ij = W_ij / (q_i^a q_j^a)          (Algorithm 1, steps 1-2)
+ *   P     = Dg^-1 W^a,  dg = W^a 1                       (Algorithm 1, step 3)
+ *   S     = Dg^-1/2 W^a Dg^-1/2 = diag(s) W diag(s),  s = q^-a dg^-1/2
+ *
+ * S is the symmetric conjugate of P (same eigenvalues; right eigenvectors of P
+ * are psi = Dg^-1/2 phi for eigenvectors phi of S). S is approximated by an
+ * H-matrix K~ = D + UV (Eq. 2.18) built once (dm_compress) and applied in every
+ * iteration of a Lanczos eigensolver (Algorithm 2 in its symmetric form,
+ * Section 2.3.1), which is what scipy's eigsh does with the paper's
+ * LinearOperator (Section 3.3).
+ *
+ * Conventions for every call:
+ *   - Return value: DM_OK (0) or a negative DM_E* status; dm_status_str() names it
+ *     and dm_last_error() gives the message of the calling thread's last failure.
+ *   - Buffers may be host or device memory; the library detects which with
+ *     cudaPointerGetAttributes and copies host buffers through the handle's
+ *     stream. The caller owns every buffer it passes; the library keeps no
+ *     pointer to it after the call returns.
+ *   - Vectors are float32 in the ORIGINAL point order; blocks of vectors are
+ *     N x nrhs column-major (column c starts at element c*N).
+ *   - Calls on one handle are not thread-safe; distinct handles are independent.
+ *     All device work of a handle runs on its stream; every call that returns
+ *     results to the caller synchronises that stream before returning.
+ */
+#ifndef DMAPS_H
+#define DMAPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DM_OK 0
+#define DM_EINVAL (-1)   /* bad argument (sizes, eps, k, tolerances, NULL pointers) */
+#define DM_ENOMEM (-2)   /* device allocation failed */
+#define DM_ESTATE (-3)   /* call out of order (e.g. dm_eigs before dm_compress) */
+#define DM_ENOCONV (-4)  /* Lanczos reached m_max before the top k converged; results still written */
+#define DM_ETIMEOUT (-5) /* a bounded device-side wait gave up */
+#define DM_ECUDA (-6)    /* a CUDA runtime call failed */
+#define DM_EBUSY (-7)    /* serving queue full or ticket still running */
+
+typedef struct dm_ctx *dm_handle;
+typedef uint64_t dm_ticket;
+
+/* Device allocator hooks (e.g. a framework's caching allocator). alloc returns a
+ * device pointer aligned to at least 256 bytes, or NULL on failure. */
+typedef void *(*dm_alloc_fn)(size_t bytes, void *user);
+typedef void (*dm_free_fn)(void *ptr, size_t bytes, void *user);
+
+#define DM_NEAR_AUTO 0   /* pick the faster near-field variant */
+#define DM_NEAR_CACHED 1 /* store the leaf blocks K(I_a, I_a) in HBM and stream them */
+#define DM_NEAR_ONTHEFLY 2 /* recompute leaf-block entries from the points in every matvec */
+
+typedef struct dm_config {
+    uint64_t seed;        /* random choices: ID row samples, Lanczos start vector, bandwidth pairs */
+    int32_t near_mode;    /* DM_NEAR_* */
+    int32_t m_max;        /* Lanczos basis cap (default 300) */
+    double conv_tol;      /* Ritz residual bound beta_j |y_j| <= conv_tol * theta_1 (default 1e-7) */
+    int32_t check_every;  /* Lanczos steps between convergence checks (default 10) */
+    int32_t device;       /* CUDA device ordinal (default: the current device) */
+    void *stream;         /* cudaStream_t to run on; NULL = a stream the handle creates */
+    dm_alloc_fn alloc;    /* NULL = cudaMalloc */
+    dm_free_fn free;      /* NULL = cudaFree */
+    void *alloc_user;
+    int32_t profile;      /* 1 = time every H-matvec of dm_eigs with CUDA events on the handle's stream */
+} dm_config;
+
+/* Fill *cfg with the defaults listed above. */
+void dm_config_default(dm_config *cfg);
+
+/* Create a handle for N points in R^d (points: N x d row-major float32, host or
+ * device). eps > 0 is the kernel scale sigma^2 of Eq. W; eps <= 0 selects the
+ * median squared pairwise distance (all pairs when N(N-1)/2 <= 2^20, else 2^20
+ * pairs drawn with cfg->seed). alpha is the density exponent of Algorithm 1,
+ * step 2 (the paper uses alpha = 1). Computes the degree vectors q, dg and the
+ * scaling s exactly (O(N^2) kernel evaluations, FP32 exp, FP64 sums).
+ * cfg may be NULL (defaults). Errors: DM_EINVAL if N < 2, d < 1, alpha < 0 or
+ * a pointer is NULL; DM_ENOMEM; DM_ECUDA. */
+int dm_create(const float *points, int64_t N, int32_t d, double eps, double alpha,
+              const dm_config *cfg, dm_handle *out);
+
+/* Build the H-matrix approximation of S (Eq. 2.18, accuracy target Eq. 1.1):
+ * a balanced binary partition tree of depth L = min{L : ceil(N/2^L) <= leaf_size}
+ * in the Gram distance of W, then per node (bottom-up) an interpolative
+ * decomposition of a sampled off-node block whose rank stops at the first
+ * pivot with residual norm <= tol * (first pivot norm), capped at max_rank;
+ * finally the near (leaf) and far (sibling skeleton) blocks are packed.
+ * Errors: DM_EINVAL if tol < 0, leaf_size < 1, max_rank < 1 or the tree would
+ * exceed 2^20 leaves; DM_ENOMEM; DM_ECUDA. Replaces any earlier structure. */
+int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank);
+
+/* y = K~ x for nrhs right-hand sides (N x nrhs column-major, original order),
+ * the LinearOperator matvec/matmat of Section 3.3. Before dm_compress it
+ * applies the exact S with entries generated on the fly (O(N^2) per column).
+ * x and y must not overlap. Errors: DM_EINVAL (nrhs < 1, NULL); DM_ECUDA. */
+int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs);
+
+/* Top-k eigenpairs of K~ by Lanczos with full reorthogonalisation (eigsh's
+ * role in Section 3.3; Algorithm 2 in symmetric form). evals: k doubles,
+ * descending (the first is 1 up to the approximation error). evecs: N x k
+ * column-major float32 (may be NULL), orthonormal, in original point order,
+ * each column signed so its largest-magnitude entry is positive.
+ * Errors: DM_ESTATE before dm_compress; DM_EINVAL if k < 1 or k >= N or
+ * k > m_max; DM_ENOCONV if m_max steps did not converge (best Ritz pairs are
+ * still written); DM_ECUDA. */
+int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
+
+/* Diffusion coordinates of the last dm_eigs: psi_i = theta_i^t Dg^-1/2 phi_i
+ * (Algorithm 1, steps 4-5: the eigenvalues of P^t are theta^t and its right
+ * eigenvectors Dg^-1/2 phi). psi: N x k column-major float32 (k <= the k of
+ * the last dm_eigs). Errors: DM_ESTATE if dm_eigs has not run; DM_EINVAL. */
+int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi);
+
+/* Release every device buffer of the handle. */
+int dm_destroy(dm_handle h);
+
+const char *dm_status_str(int status);
+const char *dm_last_error(void);
+
+/* ---- introspection (tests, checkpointing) ---- */
+typedef struct dm_stats {
+    int64_t N;
+    int32_t d, L;
+    double eps, alpha, tol;
+    int32_t leaf_max, max_rank, rank_min, rank_max;
+    double rank_mean;
+    int64_t near_bytes;      /* stored leaf blocks (cached mode) */
+    int64_t basis_bytes;     /* P matrices actually used (sum of s_a * |C_a| * 4) */
+    int64_t far_bytes;       /* sibling skeleton blocks (sum of s_l * s_r * 4) */
+    int64_t matvec_bytes;    /* algorithmic bytes of one nrhs=1 H-matvec in the active near mode */
+    int32_t near_mode;       /* mode in use after AUTO resolution */
+    int32_t lanczos_iters;   /* steps of the last dm_eigs */
+    int32_t converged;       /* 1 if the last dm_eigs converged */
+    float ms_create, ms_tree, ms_skeleton, ms_pack, ms_eigs; /* device time of each phase */
+    int32_t matvec_calls;    /* H-matvecs timed in the last dm_eigs (profile = 1) */
+    float ms_matvec;         /* their summed device time */
+} dm_stats;
+
+int dm_get_stats(dm_handle h, dm_stats *st);
+
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+int64_t dm_kernel_launches(void);
+
+/* eps in use, and the degree vectors of Algorithm 1 (N doubles each, original
+ * order; any pointer may be NULL). */
+int dm_get_eps(dm_handle h, double *eps);
+int dm_get_degrees(dm_handle h, double *q, double *dg, double *s);
+
+/* The compressed structure, in the layout dm_load_hmatrix accepts:
+ * perm[N] (perm[pos] = original index); ranks[2^(L+1)-1] (root 0);
+ * skel[node*max_rank + t] = position of skeleton t of node (-1 past the rank);
+ * P[(node*max_rank + t)*cmax + j] = interpolation matrix entry (row t, candidate
+ * j; candidates of a leaf are its positions in order, of an internal node the
+ * left then right child skeletons), cmax = max(ceil(N/2^L), 2*max_rank).
+ * Query sizes first with dm_get_tree(h, &L, NULL) and dm_get_stats. */
+int dm_get_tree(dm_handle h, int32_t *L, int32_t *perm);
+int dm_get_hmatrix(dm_handle h, int32_t *ranks, int32_t *skel, float *P);
+
+/* Adopt an externally built structure (same layout as dm_get_hmatrix; host
+ * buffers) instead of running dm_compress: checkpoint/resume of a compressed
+ * operator, and replay of a reference structure. The near and far blocks are
+ * packed from the handle's own points and scaling. Errors: DM_EINVAL on an
+ * inconsistent structure (bad permutation, ranks above max_rank, skeleton
+ * positions outside their node); DM_ENOMEM; DM_ECUDA. */
+int dm_load_hmatrix(dm_handle h, int32_t L, int32_t max_rank, const int32_t *perm,
+                    const int32_t *ranks, const int32_t *skel, const float *P);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMAPS_H */

@@ -1,0 +1,773 @@
+// dm_capi.cu -- the C ABI of include/dmaps.h: handle lifetime, memory, host
+// orchestration of the device phases, host/device buffer marshalling.
+//
+// Phases (all device work on the handle's stream):
+//   dm_create   : bandwidth (optional), pre-scaled points, degrees q, dg, scaling s
+//                 (Algorithm 1, steps 1-3)
+//   dm_compress : partition tree -> skeletons (interpolative decompositions) ->
+//                 packed near and far blocks (Eq. 2.18)
+//   dm_matvec   : y = K~ x (the LinearOperator of Section 3.3)
+//   dm_eigs     : Lanczos with full reorthogonalisation (Algorithm 2, symmetric form)
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dm_internal.cuh"
+
+cudaError_t dm_launch_dense_matvec_ws(const float *Xs, const float *sf, int64_t N, int d, const float *x, float *y,
+                                      float *tmpw, double *acc, cudaStream_t st);
+
+static std::atomic<long long> g_launches{0};
+void dm_count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define DM_CUDA(expr)                                                                                  \
+    do {                                                                                               \
+        cudaError_t _e = (expr);                                                                       \
+        if (_e != cudaSuccess)                                                                         \
+            return fail(DM_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+    } while (0)
+
+#define DM_CHECK(expr)          \
+    do {                        \
+        int _s = (expr);        \
+        if (_s != DM_OK) return _s; \
+    } while (0)
+
+enum Group { G_BASE = 0, G_STRUCT = 1, G_WORK = 2, G_LANCZOS = 3, G_IO = 4 };
+
+struct Alloc {
+    void *p;
+    size_t bytes;
+    int group;
+};
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct dm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    dm_config cfg;
+    int64_t N = 0;
+    int d = 0;
+    double eps = 0, alpha = 1;
+    std::vector<Alloc> allocs;
+    // base
+    float *X = nullptr, *Xs = nullptr, *sf = nullptr, *qaf = nullptr, *tmpw = nullptr;
+    double *q = nullptr, *dg = nullptr, *s = nullptr, *qa = nullptr, *acc = nullptr;
+    // structure
+    bool compressed = false;
+    double tol = 0;
+    int L = 0, leaf_max = 0, ldk = 0, max_rank = 0, cmax = 0, ldp = 0, near_mode = DM_NEAR_CACHED;
+    int32_t *perm = nullptr, *ranks = nullptr, *skel = nullptr;
+    float *P = nullptr, *B = nullptr, *Knear = nullptr, *Xp = nullptr, *sp = nullptr;
+    float *what = nullptr, *uhat = nullptr, *ynear = nullptr;
+    unsigned *cnt = nullptr;
+    // lanczos
+    DmLanczos lz{};
+    bool lz_ready = false;
+    int last_k = 0;
+    float *evecs = nullptr;  // N x kmax, original order, last dm_eigs
+    // io staging
+    float *io_x = nullptr, *io_y = nullptr;
+    int64_t io_elems = 0;
+    dm_stats stats{};
+
+    ~dm_ctx() {
+        for (auto &a : allocs) release(a);
+        allocs.clear();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+    void release(const Alloc &a) {
+        if (!a.p) return;
+        if (cfg.free) cfg.free(a.p, a.bytes, cfg.alloc_user);
+        else cudaFree(a.p);
+    }
+    template <class T>
+    int alloc(T **out, size_t count, int group) {
+        size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+        bytes = (bytes + 255) & ~size_t(255);
+        void *p = nullptr;
+        if (cfg.alloc) {
+            p = cfg.alloc(bytes, cfg.alloc_user);
+            if (!p) return fail(DM_ENOMEM, "device allocation of %zu bytes failed (caller allocator)", bytes);
+        } else {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            }
+        }
+        allocs.push_back({p, bytes, group});
+        *out = reinterpret_cast<T *>(p);
+        return DM_OK;
+    }
+    void free_group(int group) {
+        std::vector<Alloc> keep;
+        for (auto &a : allocs) {
+            if (a.group == group) release(a);
+            else keep.push_back(a);
+        }
+        allocs.swap(keep);
+    }
+    DmHmat hmat() const {
+        DmHmat H;
+        H.N = N;
+        H.d = d;
+        H.L = L;
+        H.leaf_max = leaf_max;
+        H.ldk = ldk;
+        H.max_rank = max_rank;
+        H.cmax = cmax;
+        H.ldp = ldp;
+        H.perm = perm;
+        H.ranks = ranks;
+        H.skel = skel;
+        H.P = P;
+        H.B = B;
+        H.Knear = Knear;
+        H.Xs = Xp;
+        H.sp = sp;
+        H.what = what;
+        H.uhat = uhat;
+        H.ynear = ynear;
+        H.cnt = cnt;
+        return H;
+    }
+};
+
+namespace {
+
+struct PhaseTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t st;
+    explicit PhaseTimer(cudaStream_t s) : st(s) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+    }
+    float stop() {
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+    ~PhaseTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+int set_device(dm_ctx *h) {
+    int cur = -1;
+    DM_CUDA(cudaGetDevice(&cur));
+    if (cur != h->device) DM_CUDA(cudaSetDevice(h->device));
+    return DM_OK;
+}
+
+// ensure io staging buffers of `elems` floats each
+int ensure_io(dm_ctx *h, int64_t elems) {
+    if (h->io_elems >= elems) return DM_OK;
+    h->free_group(G_IO);
+    h->io_x = h->io_y = nullptr;
+    DM_CHECK(h->alloc(&h->io_x, (size_t)elems, G_IO));
+    DM_CHECK(h->alloc(&h->io_y, (size_t)elems, G_IO));
+    h->io_elems = elems;
+    return DM_OK;
+}
+
+int copy_out(dm_ctx *h, void *dst, const void *src, size_t bytes) {
+    DM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+    return DM_OK;
+}
+
+// pack blocks, permuted points and matvec workspaces for the current tree/skeletons
+int finish_structure(dm_ctx *h) {
+    const int nnodes = (1 << (h->L + 1)) - 1;
+    const int nleaves = 1 << h->L;
+    const bool cached = h->near_mode == DM_NEAR_CACHED;
+    if (cached) DM_CHECK(h->alloc(&h->Knear, (size_t)nleaves * h->leaf_max * h->ldk, G_STRUCT));
+    DM_CHECK(h->alloc(&h->B, (size_t)(nleaves > 1 ? nleaves - 1 : 1) * h->max_rank * h->max_rank, G_STRUCT));
+    DM_CHECK(h->alloc(&h->what, (size_t)nnodes * h->max_rank, G_STRUCT));
+    DM_CHECK(h->alloc(&h->uhat, (size_t)nnodes * h->max_rank, G_STRUCT));
+    DM_CHECK(h->alloc(&h->ynear, (size_t)h->N, G_STRUCT));
+    DM_CHECK(h->alloc(&h->cnt, (size_t)nnodes, G_STRUCT));
+    DM_CUDA(cudaMemsetAsync(h->cnt, 0, sizeof(unsigned) * nnodes, h->stream));
+    DM_CUDA(cudaMemsetAsync(h->what, 0, sizeof(float) * (size_t)nnodes * h->max_rank, h->stream));
+    DM_CUDA(cudaMemsetAsync(h->uhat, 0, sizeof(float) * (size_t)nnodes * h->max_rank, h->stream));
+    DmHmat H = h->hmat();
+    DM_CUDA(dm_pack(H, h->Knear, h->B, cached, h->stream));
+    // statistics
+    std::vector<int32_t> rk(nnodes);
+    DM_CUDA(cudaMemcpyAsync(rk.data(), h->ranks, sizeof(int32_t) * nnodes, cudaMemcpyDeviceToHost, h->stream));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    int rmin = 1 << 30, rmax = 0;
+    double rsum = 0;
+    int64_t basis = 0, far = 0, near = 0;
+    for (int node = 1; node < nnodes; ++node) {
+        rmin = rk[node] < rmin ? rk[node] : rmin;
+        rmax = rk[node] > rmax ? rk[node] : rmax;
+        rsum += rk[node];
+        int64_t st, sz;
+        dm_node_range(h->N, node, &st, &sz);
+        const int lvl = dm_level_of(node);
+        const int64_t c = (lvl == h->L) ? sz : (int64_t)rk[2 * node + 1] + rk[2 * node + 2];
+        basis += (int64_t)rk[node] * c * 4;
+    }
+    for (int node = 0; node < nleaves - 1; ++node) far += (int64_t)rk[2 * node + 1] * rk[2 * node + 2] * 4;
+    for (int lf = 0; lf < nleaves; ++lf) {
+        int64_t st, sz;
+        dm_node_range(h->N, nleaves - 1 + lf, &st, &sz);
+        near += sz * sz * 4;
+    }
+    int64_t sksum = 0;
+    for (int node = 1; node < nnodes; ++node) sksum += rk[node];
+    dm_stats &S = h->stats;
+    S.L = h->L;
+    S.tol = h->tol;
+    S.leaf_max = h->leaf_max;
+    S.max_rank = h->max_rank;
+    S.rank_min = nnodes > 1 ? rmin : 0;
+    S.rank_max = rmax;
+    S.rank_mean = nnodes > 1 ? rsum / (nnodes - 1) : 0.0;
+    S.near_bytes = cached ? near : 0;
+    S.basis_bytes = basis;
+    S.far_bytes = far;
+    // algorithmic bytes of one nrhs=1 matvec: stored operands once, x and y once, skeleton
+    // weights written and read once each
+    S.matvec_bytes = (cached ? near : (int64_t)h->N * (h->d + 1) * 4) + basis + far + 2 * h->N * 4 + 2 * sksum * 4 * 2;
+    S.near_mode = h->near_mode;
+    h->compressed = true;
+    return DM_OK;
+}
+
+int alloc_structure(dm_ctx *h, int L, int max_rank) {
+    h->free_group(G_STRUCT);
+    h->free_group(G_LANCZOS);
+    h->lz_ready = false;
+    h->compressed = false;
+    h->Knear = nullptr;
+    h->L = L;
+    h->leaf_max = (int)((h->N + ((int64_t)1 << L) - 1) >> L);
+    h->ldk = (int)round_up(h->leaf_max, 4);
+    h->max_rank = max_rank;
+    h->cmax = h->leaf_max > 2 * max_rank ? h->leaf_max : 2 * max_rank;
+    h->ldp = (int)round_up(h->cmax, 4);
+    const int nnodes = (1 << (L + 1)) - 1;
+    DM_CHECK(h->alloc(&h->ranks, (size_t)nnodes, G_STRUCT));
+    DM_CHECK(h->alloc(&h->skel, (size_t)nnodes * max_rank, G_STRUCT));
+    DM_CHECK(h->alloc(&h->P, (size_t)nnodes * max_rank * h->ldp, G_STRUCT));
+    DM_CHECK(h->alloc(&h->Xp, (size_t)h->N * h->d, G_STRUCT));
+    DM_CHECK(h->alloc(&h->sp, (size_t)h->N, G_STRUCT));
+    DM_CUDA(cudaMemsetAsync(h->P, 0, sizeof(float) * (size_t)nnodes * max_rank * h->ldp, h->stream));
+    return DM_OK;
+}
+
+int resolve_near_mode(dm_ctx *h) {
+    int mode = h->cfg.near_mode;
+    const size_t otf_smem = sizeof(float) * ((size_t)round_up(h->leaf_max, 4) + (size_t)h->leaf_max * h->d);
+    if (mode == DM_NEAR_ONTHEFLY && otf_smem > 200 * 1024) mode = DM_NEAR_CACHED;
+    if (mode == DM_NEAR_AUTO) mode = DM_NEAR_CACHED;
+    h->near_mode = mode;
+    return DM_OK;
+}
+
+int ensure_lanczos(dm_ctx *h) {
+    if (h->lz_ready) return DM_OK;
+    const int kmax = dm_lanczos_kmax();
+    DmLanczos &L = h->lz;
+    L.N = h->N;
+    L.ldv = round_up(h->N, 64);
+    L.m_max = h->cfg.m_max;
+    DM_CHECK(h->alloc(&L.V, (size_t)(L.m_max + 1) * L.ldv, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.z, (size_t)L.ldv, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.alpha, (size_t)L.m_max + 1, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.beta, (size_t)L.m_max + 1, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.h, (size_t)2 * (L.m_max + 1), G_LANCZOS));
+    DM_CHECK(h->alloc(&L.nrm2, 1, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.theta, (size_t)kmax, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.resid, (size_t)kmax, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.Y, (size_t)kmax * L.m_max, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.Yf, (size_t)kmax * L.m_max, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.twork, (size_t)kmax * 6 * L.m_max, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.colsum, (size_t)kmax, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.phi, (size_t)kmax * h->N, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.best, (size_t)kmax, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.neg, (size_t)kmax, G_LANCZOS));
+    DM_CHECK(h->alloc(&h->evecs, (size_t)kmax * h->N, G_LANCZOS));
+    // zero the whole basis once: padding rows beyond N must read as zero
+    DM_CUDA(cudaMemsetAsync(L.V, 0, sizeof(float) * (size_t)(L.m_max + 1) * L.ldv, h->stream));
+    DM_CUDA(cudaMemsetAsync(L.z, 0, sizeof(float) * (size_t)L.ldv, h->stream));
+    h->lz_ready = true;
+    return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dm_config_default(dm_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->seed = 0;
+    cfg->near_mode = DM_NEAR_AUTO;
+    cfg->m_max = 300;
+    cfg->conv_tol = 1e-7;
+    cfg->check_every = 10;
+    cfg->device = -1;
+    cfg->stream = nullptr;
+}
+
+const char *dm_status_str(int status) {
+    switch (status) {
+        case DM_OK: return "DM_OK";
+        case DM_EINVAL: return "DM_EINVAL";
+        case DM_ENOMEM: return "DM_ENOMEM";
+        case DM_ESTATE: return "DM_ESTATE";
+        case DM_ENOCONV: return "DM_ENOCONV";
+        case DM_ETIMEOUT: return "DM_ETIMEOUT";
+        case DM_ECUDA: return "DM_ECUDA";
+        case DM_EBUSY: return "DM_EBUSY";
+        default: return "DM_UNKNOWN";
+    }
+}
+
+const char *dm_last_error(void) { return g_err.c_str(); }
+
+int64_t dm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int dm_create(const float *points, int64_t N, int32_t d, double eps, double alpha, const dm_config *cfg,
+              dm_handle *out) {
+    if (!out) return fail(DM_EINVAL, "out handle is NULL");
+    *out = nullptr;
+    if (!points) return fail(DM_EINVAL, "points is NULL");
+    if (N < 2) return fail(DM_EINVAL, "N must be >= 2 (got %lld)", (long long)N);
+    if (N > (int64_t)0x7fffffff) return fail(DM_EINVAL, "N must fit in int32");
+    if (d < 1) return fail(DM_EINVAL, "d must be >= 1 (got %d)", d);
+    if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(DM_EINVAL, "alpha must be finite and >= 0");
+    if (!std::isfinite(eps)) return fail(DM_EINVAL, "eps must be finite");
+    dm_ctx *h = new dm_ctx();
+    dm_config_default(&h->cfg);
+    if (cfg) h->cfg = *cfg;
+    if (h->cfg.m_max < 2) h->cfg.m_max = 2;
+    if (h->cfg.check_every < 1) h->cfg.check_every = 1;
+    if (!(h->cfg.conv_tol > 0)) h->cfg.conv_tol = 1e-7;
+    int rc;
+    {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) {
+            delete h;
+            return fail(DM_ECUDA, "no CUDA device available");
+        }
+        h->device = h->cfg.device >= 0 ? h->cfg.device : cur;
+        if (cudaSetDevice(h->device) != cudaSuccess) {
+            delete h;
+            return fail(DM_ECUDA, "cudaSetDevice(%d) failed", h->device);
+        }
+    }
+    if (h->cfg.stream) h->stream = reinterpret_cast<cudaStream_t>(h->cfg.stream);
+    else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(DM_ECUDA, "cudaStreamCreate failed");
+        }
+        h->own_stream = true;
+    }
+    h->N = N;
+    h->d = d;
+    h->alpha = alpha;
+    h->stats.N = N;
+    h->stats.d = d;
+    h->stats.alpha = alpha;
+    rc = [&]() -> int {
+        PhaseTimer t(h->stream);
+        DM_CHECK(h->alloc(&h->X, (size_t)N * d, G_BASE));
+        DM_CUDA(cudaMemcpyAsync(h->X, points, sizeof(float) * (size_t)N * d, cudaMemcpyDefault, h->stream));
+        if (eps <= 0.0) {
+            const int64_t npairs = N * (N - 1) / 2;
+            const int64_t m = npairs <= ((int64_t)1 << 20) ? npairs : ((int64_t)1 << 20);
+            double *pairs = nullptr, *res = nullptr;
+            DM_CHECK(h->alloc(&pairs, (size_t)m, G_WORK));
+            DM_CHECK(h->alloc(&res, 1, G_WORK));
+            DM_CUDA(dm_launch_pair_sqdist(h->X, N, d, h->cfg.seed, pairs, m, h->stream));
+            DM_CUDA(dm_launch_select_median(pairs, m, res, h->stream));
+            DM_CUDA(cudaMemcpyAsync(&eps, res, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            h->free_group(G_WORK);
+            if (!(eps > 0.0)) return fail(DM_EINVAL, "median squared distance is %g (duplicate points?)", eps);
+        }
+        h->eps = eps;
+        h->stats.eps = eps;
+        DM_CHECK(h->alloc(&h->Xs, (size_t)N * d, G_BASE));
+        DM_CHECK(h->alloc(&h->q, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&h->dg, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&h->s, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&h->qa, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&h->acc, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&h->sf, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&h->qaf, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&h->tmpw, (size_t)N, G_BASE));
+        DM_CUDA(dm_launch_scale_points(h->X, N, d, eps, h->Xs, h->stream));
+        DM_CUDA(dm_launch_degree_pass(h->Xs, N, d, nullptr, h->q, h->stream));
+        DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
+        DM_CUDA(dm_launch_degree_pass(h->Xs, N, d, h->qaf, h->dg, h->stream));
+        DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
+        h->stats.ms_create = t.stop();
+        DM_CUDA(cudaGetLastError());
+        return DM_OK;
+    }();
+    if (rc != DM_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return DM_OK;
+}
+
+int dm_destroy(dm_handle h) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    set_device(h);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+    return DM_OK;
+}
+
+int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(DM_EINVAL, "tol must be finite and >= 0");
+    if (leaf_size < 1) return fail(DM_EINVAL, "leaf_size must be >= 1");
+    if (max_rank < 1) return fail(DM_EINVAL, "max_rank must be >= 1");
+    DM_CHECK(set_device(h));
+    const int L = dm_depth_for(h->N, leaf_size);
+    if (L > 20) return fail(DM_EINVAL, "tree of depth %d (leaf_size %d) exceeds 2^20 leaves", L, leaf_size);
+    if (((int64_t)1 << L) > h->N) return fail(DM_EINVAL, "leaf_size %d too small for N=%lld", leaf_size, (long long)h->N);
+    if (max_rank > 1024) return fail(DM_EINVAL, "max_rank must be <= 1024");
+    DM_CHECK(alloc_structure(h, L, max_rank));
+    h->tol = tol;
+    resolve_near_mode(h);
+    const int nleaves = 1 << L;
+    // ---- tree
+    float ms_tree = 0, ms_skel = 0, ms_pack = 0;
+    {
+        PhaseTimer t(h->stream);
+        int32_t *pa = nullptr, *pb = nullptr;
+        DM_CHECK(h->alloc(&pa, (size_t)h->N, G_STRUCT));
+        DM_CHECK(h->alloc(&pb, (size_t)h->N, G_STRUCT));
+        // identity permutation: every node starts in increasing original index
+        std::vector<int32_t> ident((size_t)h->N);
+        for (int64_t i = 0; i < h->N; ++i) ident[(size_t)i] = (int32_t)i;
+        DM_CUDA(cudaMemcpyAsync(pa, ident.data(), sizeof(int32_t) * (size_t)h->N, cudaMemcpyHostToDevice, h->stream));
+        DmTreeWork w{};
+        const size_t nitems = dm_tree_items_bound(h->N, L) + 1;
+        w.max_items = (int)nitems;
+        DM_CHECK(h->alloc(&w.wbuf, (size_t)h->N, G_WORK));
+        DM_CHECK(h->alloc(&w.keys, (size_t)h->N, G_WORK));
+        unsigned char *items = nullptr, *c1 = nullptr, *c2 = nullptr;
+        DM_CHECK(h->alloc(&items, nitems * dm_tree_item_bytes(), G_WORK));
+        DM_CHECK(h->alloc(&c1, nitems * dm_tree_cand_bytes(), G_WORK));
+        DM_CHECK(h->alloc(&c2, nitems * dm_tree_cand_bytes(), G_WORK));
+        w.items = items;
+        w.cand1 = c1;
+        w.cand2 = c2;
+        int32_t *perm = nullptr;
+        DM_CUDA(dm_tree_build(h->X, h->N, h->d, h->eps, L, pa, pb, &perm, &w, h->stream));
+        h->perm = perm;
+        ms_tree = t.stop();
+        h->free_group(G_WORK);
+    }
+    // ---- skeletons
+    {
+        PhaseTimer t(h->stream);
+        DM_CUDA(dm_permute_points(h->Xs, h->sf, h->perm, h->N, h->d, h->Xp, h->sp, h->stream));
+        DmSkelWork w{};
+        w.rmax = 2 * max_rank + 10;
+        const size_t smem = dm_skel_smem_bytes(h->cmax, w.rmax, max_rank);
+        if (smem > 220 * 1024) return fail(DM_EINVAL, "leaf size / rank too large for the skeletonization kernel");
+        DM_CHECK(h->alloc(&w.A, (size_t)nleaves * w.rmax * h->cmax, G_WORK));
+        DM_CHECK(h->alloc(&w.R, (size_t)nleaves * max_rank * h->cmax, G_WORK));
+        DM_CUDA(dm_skeletonize(h->Xp, h->sp, h->N, h->d, L, h->perm, tol, max_rank, h->cmax, h->ldp, h->cfg.seed,
+                               h->ranks, h->skel, h->P, &w, h->stream));
+        ms_skel = t.stop();
+        h->free_group(G_WORK);
+    }
+    {
+        PhaseTimer t(h->stream);
+        DM_CHECK(finish_structure(h));
+        ms_pack = t.stop();
+    }
+    h->stats.ms_tree = ms_tree;
+    h->stats.ms_skeleton = ms_skel;
+    h->stats.ms_pack = ms_pack;
+    DM_CUDA(cudaGetLastError());
+    return DM_OK;
+}
+
+int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    if (!x || !y) return fail(DM_EINVAL, "x or y is NULL");
+    if (nrhs < 1) return fail(DM_EINVAL, "nrhs must be >= 1");
+    DM_CHECK(set_device(h));
+    const int64_t n = h->N * nrhs;
+    const bool xd = is_device_ptr(x), yd = is_device_ptr(y);
+    const float *dx = x;
+    float *dy = y;
+    if (!xd || !yd) DM_CHECK(ensure_io(h, n));
+    if (!xd) {
+        DM_CUDA(cudaMemcpyAsync(h->io_x, x, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+        dx = h->io_x;
+    }
+    if (!yd) dy = h->io_y;
+    for (int c = 0; c < nrhs; ++c) {
+        const float *xc = dx + (size_t)c * h->N;
+        float *yc = dy + (size_t)c * h->N;
+        if (h->compressed) DM_CUDA(dm_hmatvec(h->hmat(), h->near_mode, xc, yc, false, h->stream));
+        else DM_CUDA(dm_launch_dense_matvec_ws(h->Xs, h->sf, h->N, h->d, xc, yc, h->tmpw, h->acc, h->stream));
+    }
+    if (!yd) DM_CUDA(cudaMemcpyAsync(y, dy, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    return DM_OK;
+}
+
+int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    if (!h->compressed) return fail(DM_ESTATE, "dm_eigs before dm_compress");
+    if (!evals) return fail(DM_EINVAL, "evals is NULL");
+    if (k < 1 || k >= h->N) return fail(DM_EINVAL, "k must be in [1, N)");
+    if (k > dm_lanczos_kmax()) return fail(DM_EINVAL, "k must be <= %d", dm_lanczos_kmax());
+    if (k > h->cfg.m_max) return fail(DM_EINVAL, "k must be <= m_max");
+    DM_CHECK(set_device(h));
+    DM_CHECK(ensure_lanczos(h));
+    PhaseTimer t(h->stream);
+    DmLanczos &Lz = h->lz;
+    const DmHmat H = h->hmat();
+    int m_cap = h->cfg.m_max;
+    if (m_cap > h->N) m_cap = (int)h->N;
+    DM_CUDA(dm_lanczos_start(Lz, h->perm, h->cfg.seed, h->stream));
+    std::vector<double> th(k), rs(k);
+    double bj = 0.0;
+    int m = 0;
+    bool converged = false, ritz_current = false;
+    std::vector<cudaEvent_t> ev_mv;
+    const bool prof = h->cfg.profile != 0;
+    for (int j = 0; j < m_cap; ++j) {
+        if (prof) {
+            cudaEvent_t e0, e1;
+            DM_CUDA(cudaEventCreate(&e0));
+            DM_CUDA(cudaEventCreate(&e1));
+            ev_mv.push_back(e0);
+            ev_mv.push_back(e1);
+            DM_CUDA(cudaEventRecord(e0, h->stream));
+        }
+        DM_CUDA(dm_hmatvec(H, h->near_mode, Lz.V + (size_t)j * Lz.ldv, Lz.z, true, h->stream));
+        if (prof) DM_CUDA(cudaEventRecord(ev_mv.back(), h->stream));
+        DM_CUDA(dm_lanczos_orth(Lz, j, h->stream));
+        m = j + 1;
+        ritz_current = false;
+        const bool last = (m == m_cap);
+        if (m >= k && (m % h->cfg.check_every == 0 || last)) {
+            DM_CUDA(dm_lanczos_ritz(Lz, m, k, h->cfg.conv_tol, h->stream));
+            DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaMemcpyAsync(rs.data(), Lz.resid, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaMemcpyAsync(&bj, Lz.beta + j, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            ritz_current = true;
+            const double scale = std::fabs(th[0]) > 0 ? std::fabs(th[0]) : 1.0;
+            bool ok = true;
+            for (int i = 0; i < k; ++i)
+                if (!(rs[i] <= h->cfg.conv_tol * scale)) ok = false;
+            if (ok || bj <= 1e-12 * scale) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    if (!ritz_current) {
+        DM_CUDA(dm_lanczos_ritz(Lz, m, k, h->cfg.conv_tol, h->stream));
+        DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+    }
+    DM_CUDA(dm_lanczos_vectors(Lz, m, k, h->perm, h->evecs, h->stream));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    if (is_device_ptr(evals)) DM_CUDA(cudaMemcpyAsync(evals, th.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+    else
+        for (int i = 0; i < k; ++i) evals[i] = th[i];
+    if (evecs) DM_CHECK(copy_out(h, evecs, h->evecs, sizeof(float) * (size_t)k * h->N));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    h->stats.matvec_calls = 0;
+    h->stats.ms_matvec = 0.f;
+    for (size_t e = 0; e + 1 < ev_mv.size(); e += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev_mv[e], ev_mv[e + 1]) == cudaSuccess) {
+            h->stats.ms_matvec += ms;
+            h->stats.matvec_calls += 1;
+        }
+        cudaEventDestroy(ev_mv[e]);
+        cudaEventDestroy(ev_mv[e + 1]);
+    }
+    h->last_k = k;
+    h->stats.lanczos_iters = m;
+    h->stats.converged = converged ? 1 : 0;
+    h->stats.ms_eigs = t.stop();
+    return converged ? DM_OK : fail(DM_ENOCONV, "Lanczos did not converge in %d steps", m);
+}
+
+int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    if (h->last_k == 0) return fail(DM_ESTATE, "dm_coords before dm_eigs");
+    if (k < 1 || k > h->last_k) return fail(DM_EINVAL, "k must be in [1, %d]", h->last_k);
+    if (t < 0) return fail(DM_EINVAL, "t must be >= 0");
+    if (!psi) return fail(DM_EINVAL, "psi is NULL");
+    DM_CHECK(set_device(h));
+    const int64_t n = h->N * k;
+    const bool pd = is_device_ptr(psi);
+    float *dst = psi;
+    if (!pd) {
+        DM_CHECK(ensure_io(h, n));
+        dst = h->io_y;
+    }
+    DM_CUDA(dm_launch_coords(h->evecs, h->lz.theta, h->dg, h->N, k, t, dst, h->stream));
+    if (!pd) DM_CUDA(cudaMemcpyAsync(psi, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    return DM_OK;
+}
+
+int dm_get_stats(dm_handle h, dm_stats *st) {
+    if (!h || !st) return fail(DM_EINVAL, "NULL argument");
+    *st = h->stats;
+    return DM_OK;
+}
+
+int dm_get_eps(dm_handle h, double *eps) {
+    if (!h || !eps) return fail(DM_EINVAL, "NULL argument");
+    *eps = h->eps;
+    return DM_OK;
+}
+
+int dm_get_degrees(dm_handle h, double *q, double *dg, double *s) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    DM_CHECK(set_device(h));
+    const size_t b = sizeof(double) * (size_t)h->N;
+    if (q) DM_CHECK(copy_out(h, q, h->q, b));
+    if (dg) DM_CHECK(copy_out(h, dg, h->dg, b));
+    if (s) DM_CHECK(copy_out(h, s, h->s, b));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    return DM_OK;
+}
+
+int dm_get_tree(dm_handle h, int32_t *L, int32_t *perm) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    if (!h->compressed) return fail(DM_ESTATE, "no compressed structure");
+    DM_CHECK(set_device(h));
+    if (L) *L = h->L;
+    if (perm) {
+        DM_CHECK(copy_out(h, perm, h->perm, sizeof(int32_t) * (size_t)h->N));
+        DM_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return DM_OK;
+}
+
+int dm_get_hmatrix(dm_handle h, int32_t *ranks, int32_t *skel, float *P) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    if (!h->compressed) return fail(DM_ESTATE, "no compressed structure");
+    DM_CHECK(set_device(h));
+    const int nnodes = (1 << (h->L + 1)) - 1;
+    if (ranks) DM_CHECK(copy_out(h, ranks, h->ranks, sizeof(int32_t) * nnodes));
+    if (skel) DM_CHECK(copy_out(h, skel, h->skel, sizeof(int32_t) * (size_t)nnodes * h->max_rank));
+    if (P)
+        DM_CUDA(cudaMemcpy2DAsync(P, sizeof(float) * h->cmax, h->P, sizeof(float) * h->ldp, sizeof(float) * h->cmax,
+                                  (size_t)nnodes * h->max_rank, cudaMemcpyDefault, h->stream));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    return DM_OK;
+}
+
+int dm_load_hmatrix(dm_handle h, int32_t L, int32_t max_rank, const int32_t *perm, const int32_t *ranks,
+                    const int32_t *skel, const float *P) {
+    if (!h) return fail(DM_EINVAL, "handle is NULL");
+    if (!perm || !ranks || !skel || !P) return fail(DM_EINVAL, "NULL structure array");
+    if (L < 0 || L > 20 || ((int64_t)1 << L) > h->N) return fail(DM_EINVAL, "bad depth %d", L);
+    if (max_rank < 1 || max_rank > 1024) return fail(DM_EINVAL, "bad max_rank %d", max_rank);
+    if (is_device_ptr(perm) || is_device_ptr(ranks) || is_device_ptr(skel) || is_device_ptr(P))
+        return fail(DM_EINVAL, "dm_load_hmatrix takes host buffers");
+    DM_CHECK(set_device(h));
+    const int nnodes = (1 << (L + 1)) - 1;
+    const int leaf_max = (int)((h->N + ((int64_t)1 << L) - 1) >> L);
+    const int cmax = leaf_max > 2 * max_rank ? leaf_max : 2 * max_rank;
+    // ---- validate on the host
+    std::vector<char> seen((size_t)h->N, 0);
+    for (int64_t i = 0; i < h->N; ++i) {
+        const int32_t v = perm[i];
+        if (v < 0 || v >= h->N || seen[(size_t)v]) return fail(DM_EINVAL, "perm is not a permutation");
+        seen[(size_t)v] = 1;
+    }
+    if (ranks[0] != 0) return fail(DM_EINVAL, "root rank must be 0");
+    for (int node = nnodes - 1; node >= 1; --node) {
+        int64_t st, sz;
+        dm_node_range(h->N, node, &st, &sz);
+        const int lvl = dm_level_of(node);
+        const int r = ranks[node];
+        const int64_t c = (lvl == L) ? sz : (int64_t)ranks[2 * node + 1] + ranks[2 * node + 2];
+        if (r < 0 || r > max_rank || r > c) return fail(DM_EINVAL, "node %d: rank %d out of range", node, r);
+        for (int t = 0; t < r; ++t) {
+            const int32_t p = skel[(int64_t)node * max_rank + t];
+            bool ok = false;
+            if (lvl == L) ok = p >= st && p < st + sz;
+            else {
+                for (int child = 2 * node + 1; child <= 2 * node + 2 && !ok; ++child)
+                    for (int u = 0; u < ranks[child] && !ok; ++u) ok = skel[(int64_t)child * max_rank + u] == p;
+            }
+            if (!ok) return fail(DM_EINVAL, "node %d: skeleton %d is not a candidate", node, p);
+        }
+        for (int t = 0; t < r; ++t)
+            for (int64_t j = 0; j < c; ++j)
+                if (!std::isfinite(P[((int64_t)node * max_rank + t) * cmax + j]))
+                    return fail(DM_EINVAL, "node %d: non-finite P", node);
+    }
+    DM_CHECK(alloc_structure(h, L, max_rank));
+    h->tol = -1.0;
+    resolve_near_mode(h);
+    int32_t *pa = nullptr;
+    DM_CHECK(h->alloc(&pa, (size_t)h->N, G_STRUCT));
+    h->perm = pa;
+    DM_CUDA(cudaMemcpyAsync(h->perm, perm, sizeof(int32_t) * (size_t)h->N, cudaMemcpyHostToDevice, h->stream));
+    DM_CUDA(cudaMemcpyAsync(h->ranks, ranks, sizeof(int32_t) * nnodes, cudaMemcpyHostToDevice, h->stream));
+    DM_CUDA(cudaMemcpyAsync(h->skel, skel, sizeof(int32_t) * (size_t)nnodes * max_rank, cudaMemcpyHostToDevice,
+                            h->stream));
+    DM_CUDA(cudaMemcpy2DAsync(h->P, sizeof(float) * h->ldp, P, sizeof(float) * cmax, sizeof(float) * cmax,
+                              (size_t)nnodes * max_rank, cudaMemcpyHostToDevice, h->stream));
+    DM_CUDA(dm_permute_points(h->Xs, h->sf, h->perm, h->N, h->d, h->Xp, h->sp, h->stream));
+    DM_CHECK(finish_structure(h));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    return DM_OK;
+}
+
+}  // extern "C"

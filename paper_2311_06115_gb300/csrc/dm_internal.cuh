@@ -1,0 +1,273 @@
+// dm_internal.cuh -- shared definitions of the CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dmaps.h"
+
+#define DM_WARP 32
+
+// process-wide count of kernel launches (dm_kernel_launches)
+void dm_count_launches(long long n);
+#define DM_FULL 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) used as a counter-based
+// generator: output (key, ctr) is the (ctr+1)-th draw of a generator whose
+// state starts at key; streams are keyed by (seed, purpose tag, id).
+// ---------------------------------------------------------------------------
+#define DM_GAMMA 0x9E3779B97F4A7C15ULL
+#define DM_TAG_ROWS 1u
+#define DM_TAG_V0 2u
+#define DM_TAG_PAIRS 3u
+
+__host__ __device__ __forceinline__ uint64_t dm_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t dm_stream_key(uint64_t seed, uint32_t tag, uint64_t id) {
+    return dm_mix64(seed * DM_GAMMA + ((uint64_t)tag << 48) + id);
+}
+__host__ __device__ __forceinline__ uint64_t dm_rng(uint64_t key, uint64_t ctr) {
+    return dm_mix64(key + (ctr + 1) * DM_GAMMA);
+}
+// integer in [0, n) from the top 32 bits (n < 2^32)
+__host__ __device__ __forceinline__ uint64_t dm_below(uint64_t u, uint64_t n) { return ((u >> 32) * n) >> 32; }
+// double in [0, 1) from the top 53 bits
+__host__ __device__ __forceinline__ double dm_unit(uint64_t u) {
+    return (double)(u >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ---------------------------------------------------------------------------
+// Perfect binary partition tree: node (level l, k) has heap id 2^l - 1 + k; a
+// node of n points splits into ceil(n/2) (left) and floor(n/2) (right).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int dm_level_of(int node) {
+    int l = 0;
+    unsigned h = (unsigned)node + 1u;
+    while (h >> (l + 1)) ++l;
+    return l;
+}
+__host__ __device__ __forceinline__ void dm_node_range(int64_t N, int node, int64_t *start, int64_t *size) {
+    int64_t st = 0, sz = N;
+    unsigned h = (unsigned)node + 1u;
+    int lvl = dm_level_of(node);
+    for (int b = lvl - 1; b >= 0; --b) {
+        int64_t left = (sz + 1) / 2;
+        if ((h >> b) & 1u) {
+            st += left;
+            sz -= left;
+        } else {
+            sz = left;
+        }
+    }
+    *start = st;
+    *size = sz;
+}
+static inline int dm_depth_for(int64_t N, int64_t leaf) {
+    int L = 0;
+    while (((N + ((int64_t)1 << L) - 1) >> L) > leaf) ++L;
+    return L;
+}
+
+// FP64 -> uint64 whose unsigned order is the numeric order (no NaNs here).
+__device__ __forceinline__ uint64_t dm_order_key(double v) {
+    uint64_t u = (uint64_t)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dm_warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DM_FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ double dm_warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DM_FULL, v, o);
+    return v;
+}
+
+// exp2 on the MUFU unit (PTX ex2.approx.ftz.f32: documented max error ~2 ulp over its range)
+__device__ __forceinline__ float dm_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Squared distance of two FP32 points in FP64 without contraction, in the order
+// k = 0..d-1 (reproducible bit for bit on any IEEE machine).
+__device__ __forceinline__ double dm_sqdist64(const float *a, const float *b, int d) {
+    double r2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double t = __dsub_rn((double)a[k], (double)b[k]);
+        r2 = __dadd_rn(r2, __dmul_rn(t, t));
+    }
+    return r2;
+}
+
+// ---------------------------------------------------------------------------
+// Device-side structure of a compressed operator (all pointers device memory).
+// ---------------------------------------------------------------------------
+struct DmHmat {
+    int64_t N;
+    int d;
+    int L;              // tree depth; leaves are level L
+    int leaf_max;       // ceil(N / 2^L)
+    int ldk;            // leading dimension of a stored leaf block (leaf_max rounded up to 4)
+    int max_rank;
+    int cmax;           // max candidates of a node = max(leaf_max, 2 max_rank)
+    int ldp;            // row stride of a P slot (cmax rounded up to 4)
+    const int32_t *perm;   // perm[pos] = original index
+    const int32_t *ranks;  // per node
+    const int32_t *skel;   // per node, max_rank positions
+    const float *P;        // per node slot max_rank x ldp, row-major
+    const float *B;        // per internal node slot max_rank x max_rank: K(S_l, S_r), row-major s_l x s_r
+    const float *Knear;    // per leaf slot leaf_max x ldk (cached mode)
+    const float *Xs;       // points in position order, scaled by sqrt(log2(e)/eps), N x d (on-the-fly mode)
+    const float *sp;       // s in position order (FP32)
+    float *what;           // per node max_rank: skeleton weights (N2S)
+    float *uhat;           // per node max_rank: S2S parts
+    float *ynear;          // N, near-field result in position order
+    unsigned *cnt;         // per node arrival counters of the upward pass (zero between calls)
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions in each .cu; all enqueue on `st` and return the
+// launch status).
+// ---------------------------------------------------------------------------
+// k_degrees.cu
+cudaError_t dm_launch_pair_sqdist(const float *X, int64_t N, int d, uint64_t seed, double *out, int64_t m,
+                                  cudaStream_t st);
+cudaError_t dm_launch_select_median(double *vals, int64_t m, double *result, cudaStream_t st);
+cudaError_t dm_launch_scale_points(const float *X, int64_t N, int d, double eps, float *Xs, cudaStream_t st);
+cudaError_t dm_launch_degree_pass(const float *Xs, int64_t N, int d, const float *wcol, double *out,
+                                  cudaStream_t st);
+cudaError_t dm_launch_finish_degrees(int64_t N, double alpha, const double *q, double *qa, float *qaf,
+                                     cudaStream_t st);
+cudaError_t dm_launch_finish_scaling(int64_t N, const double *qa, double *dgsum, double *s, float *sf,
+                                     cudaStream_t st);
+cudaError_t dm_launch_dense_matvec_ws(const float *Xs, const float *sf, int64_t N, int d, const float *x, float *y,
+                                      float *tmpw, double *acc, cudaStream_t st);
+
+// k_tree.cu
+struct DmTreeWork {
+    double *wbuf;     // N doubles
+    uint64_t *keys;   // N keys
+    void *items;      // dm_tree_items_bound(N, L) items of dm_tree_item_bytes() each
+    void *cand1;      // as many candidates of dm_tree_cand_bytes() each
+    void *cand2;
+    int max_items;
+};
+size_t dm_tree_items_bound(int64_t N, int L);
+size_t dm_tree_item_bytes();
+size_t dm_tree_cand_bytes();
+cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, int32_t *perm_a, int32_t *perm_b,
+                          int32_t **perm_out, DmTreeWork *w, cudaStream_t st);
+
+// k_skel.cu
+struct DmSkelWork {
+    float *A;      // per node slot rmax x cmax (column-major)
+    float *R;      // per node slot max_rank x cmax
+    int rmax;
+};
+size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank);
+cudaError_t dm_skeletonize(const float *Xs, const float *sf, int64_t N, int d, int L, const int32_t *perm,
+                           double tol, int max_rank, int cmax, int ldp, uint64_t seed, int32_t *ranks,
+                           int32_t *skel, float *P, DmSkelWork *w, cudaStream_t st);
+cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cudaStream_t st);
+cudaError_t dm_permute_points(const float *Xs, const float *sf, const int32_t *perm, int64_t N, int d,
+                              float *Xp, float *sp, cudaStream_t st);
+
+// k_hmatvec.cu
+// x, y: FP32 vectors; `permuted` = vectors are in position order (Lanczos) instead of original order.
+cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted, cudaStream_t st);
+int dm_near_rows(int near_mode, int leaf_max);
+
+// k_lanczos.cu
+struct DmLanczos {
+    int64_t N;
+    int64_t ldv;      // column stride of V (N rounded up to 64)
+    int m_max;
+    float *V;         // (m_max+1) columns
+    float *z;         // work vector (ldv, zero padded)
+    double *alpha;    // m_max
+    double *beta;     // m_max (beta[j] = |r_j|)
+    double *h;        // 2 x (m_max+1) projection coefficients (two passes)
+    double *nrm2;     // scalar accumulator
+    double *theta;    // kmax Ritz values (descending)
+    double *resid;    // kmax residual bounds
+    double *Y;        // kmax columns of length m_max: eigenvectors of T
+    float *Yf;        // m_max x kmax FP32 copy
+    double *twork;    // kmax x (6 m_max) doubles for inverse iteration
+    double *colsum;   // kmax
+    float *phi;       // N x kmax Ritz vectors in position order
+    unsigned long long *best;  // kmax
+    int *neg;         // kmax
+};
+int dm_lanczos_kmax();
+cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st);
+cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st);
+cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st);
+cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig,
+                               cudaStream_t st);
+cudaError_t dm_launch_coords(const float *evecs, const double *theta, const double *dg, int64_t N, int k, int t,
+                             float *psi, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// CTA-wide exact selection: the k-th smallest (0-based) of n uint64 keys given
+// by key(i), by most-significant-digit radix passes (8 bits per pass) with
+// warp-aggregated shared-memory histograms. Every thread of the CTA must call
+// it; all threads receive the key. `hist` is 256 unsigned of shared memory.
+// On return *below holds the number of keys strictly smaller than the result.
+// ---------------------------------------------------------------------------
+template <class KeyFn>
+__device__ uint64_t dm_cta_select(KeyFn key, int64_t n, int64_t k, unsigned *hist, int64_t *below) {
+    __shared__ uint64_t s_prefix;
+    __shared__ int64_t s_k, s_below;
+    uint64_t prefix = 0, mask = 0;
+    if (threadIdx.x == 0) { s_below = 0; }
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+        for (int64_t base = 0; base < n; base += blockDim.x) {
+            int64_t i = base + threadIdx.x;
+            bool act = false;
+            unsigned bin = 0;
+            if (i < n) {
+                uint64_t u = key(i);
+                if ((u & mask) == prefix) { act = true; bin = (unsigned)((u >> shift) & 255u); }
+            }
+            unsigned am = __ballot_sync(DM_FULL, act);
+            if (act) {
+                unsigned peers = __match_any_sync(am, bin);
+                int leader = __ffs(peers) - 1;
+                if (lane == leader) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t kk = (shift == 56) ? k : s_k;
+            int64_t acc = 0;
+            int b = 0;
+            for (; b < 256; ++b) {
+                if (acc + (int64_t)hist[b] > kk) break;
+                acc += hist[b];
+            }
+            s_k = kk - acc;
+            s_below += acc;
+            s_prefix = prefix | ((uint64_t)b << shift);
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        mask |= (uint64_t)255 << shift;
+        __syncthreads();
+    }
+    *below = s_below;
+    return prefix;
+}

@@ -1,0 +1,468 @@
+// k_lanczos.cu -- Lanczos with full reorthogonalisation on the device.
+//
+// Algorithm 2 of the paper (k-step Arnoldi factorisation) in its symmetric form,
+// the Lanczos method of Section 2.3.1 that eigsh/ARPACK runs: x_1 = v/|v|; per
+// step z = A x_j, h = X^T z, r = z - X h (Gram-Schmidt, done twice here), the
+// projected matrix is tridiagonal T = tridiag(beta, alpha, beta) with
+// alpha_j = h_j and beta_j = |r|. Ritz values of T (its eigenvalues) approximate
+// those of A; a Ritz pair has residual |A phi - theta phi| = beta_m |y_m|.
+//
+// GB300 design: the basis X is FP32 (HBM-bound passes), every dot product is a
+// warp-level FP32 partial folded into FP64 atomics (FP64 is a narrow pipe on
+// this part, so it is spent only on the coefficients), and the small tridiagonal
+// eigenproblem is solved in FP64 with division-free Sturm sequences
+// (multisection: 32 shifts per warp per round) and inverse iteration.
+#include "dm_internal.cuh"
+
+namespace {
+
+constexpr int kProjRows = 2048;  // rows per projection block
+constexpr int kKMax = 32;        // max eigenpairs returned per solve
+
+__global__ void start_vector_kernel(const int32_t *__restrict__ perm, int64_t N, uint64_t key, float *__restrict__ z,
+                                    double *__restrict__ nrm2) {
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float v = 0.f;
+    if (pos < N) {
+        v = (float)(2.0 * dm_unit(dm_rng(key, (uint64_t)perm[pos])) - 1.0);
+        z[pos] = v;
+    }
+    float ss = dm_warp_sum(v * v);
+    if ((threadIdx.x & 31) == 0) atomicAdd(nrm2, (double)ss);
+}
+
+// V[:, col] = z / sqrt(nrm2)
+__global__ void normalize_kernel(const float *__restrict__ z, int64_t N, const double *__restrict__ nrm2,
+                                 float *__restrict__ vout) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) vout[i] = (float)((double)z[i] / sqrt(*nrm2));
+}
+
+// h[c] += sum_rows V[c][row] z[row] for c <= j; grid (row blocks, column groups of 8)
+__global__ void __launch_bounds__(256) proj_kernel(const float *__restrict__ V, int64_t ldv, int ncols,
+                                                   const float *__restrict__ z, int64_t N, double *__restrict__ h) {
+    __shared__ float4 sz4[kProjRows / 4];
+    const int64_t r0 = (int64_t)blockIdx.x * kProjRows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nq = (int)(((N - r0) < kProjRows ? (N - r0) : kProjRows) + 3) / 4;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) sz4[q] = *reinterpret_cast<const float4 *>(z + r0 + 4 * q);
+    __syncthreads();
+    const int c = blockIdx.y * 8 + warp;
+    if (c >= ncols) return;
+    const float4 *col = reinterpret_cast<const float4 *>(V + (size_t)c * ldv + r0);
+    float acc = 0.f;
+#pragma unroll 4
+    for (int q = lane; q < nq; q += 32) {
+        const float4 a = __ldcs(col + q);
+        const float4 b = sz4[q];
+        acc = fmaf(a.x, b.x, acc);
+        acc = fmaf(a.y, b.y, acc);
+        acc = fmaf(a.z, b.z, acc);
+        acc = fmaf(a.w, b.w, acc);
+    }
+    acc = dm_warp_sum(acc);
+    if (lane == 0) atomicAdd(h + c, (double)acc);
+}
+
+// z -= V[:, 0:ncols] h; optionally accumulate |z|^2 (FP64) after the update
+__global__ void __launch_bounds__(256) update_kernel(const float *__restrict__ V, int64_t ldv, int ncols,
+                                                     float *__restrict__ z, int64_t N, const double *__restrict__ h,
+                                                     double *__restrict__ nrm2) {
+    extern __shared__ float sh[];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) sh[c] = (float)h[c];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float v = 0.f;
+    if (i < N) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int c = 0;
+        for (; c + 4 <= ncols; c += 4) {
+            a0 = fmaf(__ldcs(V + (size_t)c * ldv + i), sh[c], a0);
+            a1 = fmaf(__ldcs(V + (size_t)(c + 1) * ldv + i), sh[c + 1], a1);
+            a2 = fmaf(__ldcs(V + (size_t)(c + 2) * ldv + i), sh[c + 2], a2);
+            a3 = fmaf(__ldcs(V + (size_t)(c + 3) * ldv + i), sh[c + 3], a3);
+        }
+        for (; c < ncols; ++c) a0 = fmaf(__ldcs(V + (size_t)c * ldv + i), sh[c], a0);
+        v = z[i] - ((a0 + a1) + (a2 + a3));
+        z[i] = v;
+    }
+    if (nrm2) {
+        float ss = dm_warp_sum(v * v);
+        if ((threadIdx.x & 31) == 0) atomicAdd(nrm2, (double)ss);
+    }
+}
+
+// alpha_j = h0_j + h1_j ; beta_j = sqrt(nrm2)
+__global__ void coeff_kernel(int j, const double *__restrict__ h0, const double *__restrict__ h1,
+                             const double *__restrict__ nrm2, double *__restrict__ alpha, double *__restrict__ beta) {
+    alpha[j] = h0[j] + h1[j];
+    beta[j] = sqrt(*nrm2);
+}
+
+// ---- Sturm count of T_m - x I by the division-free characteristic-polynomial
+// recurrence p_i = (alpha_i - x) p_{i-1} - beta_{i-1}^2 p_{i-2} with exact power-of-two
+// rescaling; returns the number of eigenvalues of T_m below x.
+__device__ int sturm_count(const double *__restrict__ al, const double *__restrict__ b2, int m, double x) {
+    double pm = 1.0, p = al[0] - x;
+    int cnt = (p < 0.0) ? 1 : 0;
+    bool prev_neg = p < 0.0;
+    if (p == 0.0) { p = -1e-300; cnt = 1; prev_neg = true; }
+    for (int i = 1; i < m; ++i) {
+        double pn = fma(-b2[i - 1], pm, (al[i] - x) * p);
+        if (pn == 0.0) pn = prev_neg ? 1e-300 : -1e-300;  // a zero takes the sign that counts a change
+        const bool neg = pn < 0.0;
+        cnt += (neg != prev_neg) ? 1 : 0;
+        prev_neg = neg;
+        // keep magnitudes in range: scale both terms by the same power of two, chosen
+        // from the larger one so that neither overflows
+        const int e = (int)((__double_as_longlong(fabs(pn) > fabs(p) ? pn : p) >> 52) & 0x7ff);
+        if (e > 1023 + 500 || e < 1023 - 500) {
+            const int sh = 1023 - e;
+            pn = scalbn(pn, sh);
+            p = scalbn(p, sh);
+        }
+        pm = p;
+        p = pn;
+    }
+    return cnt;
+}
+
+// One warp per wanted eigenvalue (descending index i): multisection to full FP64
+// precision, then the residual bound beta_{m-1} |y_m| from |y_m|^2 = |p_{m-1}(theta) / p_m'(theta)|.
+__global__ void __launch_bounds__(32) ritz_kernel(const double *__restrict__ alpha, const double *__restrict__ beta,
+                                                  int m, double *__restrict__ theta, double *__restrict__ resid,
+                                                  double *__restrict__ work) {
+    extern __shared__ double sd[];
+    double *al = sd, *b2 = sd + m;
+    const int lane = threadIdx.x;
+    for (int i = lane; i < m; i += 32) {
+        al[i] = alpha[i];
+        b2[i] = (i < m - 1) ? beta[i] * beta[i] : 0.0;
+    }
+    __syncwarp();
+    // Gershgorin interval
+    double lo = 1e300, hi = -1e300;
+    for (int i = lane; i < m; i += 32) {
+        const double r = (i > 0 ? sqrt(b2[i - 1]) : 0.0) + (i < m - 1 ? sqrt(b2[i]) : 0.0);
+        lo = fmin(lo, al[i] - r);
+        hi = fmax(hi, al[i] + r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(DM_FULL, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(DM_FULL, hi, o));
+    }
+    const double span = fmax(hi - lo, 1e-300);
+    lo -= 1e-3 * span;
+    hi += 1e-3 * span;
+    const int target = m - 1 - (int)blockIdx.x;  // ascending index of the wanted eigenvalue
+    for (int round = 0; round < 16; ++round) {
+        if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const int c = sturm_count(al, b2, m, x);
+        const unsigned above = __ballot_sync(DM_FULL, c > target);  // lanes whose shift is above the eigenvalue
+        const double xlo = __shfl_sync(DM_FULL, x, above ? max(__ffs(above) - 2, 0) : 31);
+        const double xhi = __shfl_sync(DM_FULL, x, above ? __ffs(above) - 1 : 31);
+        if (above == 0u) lo = xhi;                      // all shifts below: eigenvalue in (x_31, hi]
+        else {
+            if (__ffs(above) - 1 > 0) lo = xlo;
+            hi = xhi;
+        }
+    }
+    const double th = 0.5 * (lo + hi);
+    if (lane == 0) {
+        // p and p' of det(T_i - x I) with shared rescaling
+        double pm = 1.0, p = al[0] - th, dpm = 0.0, dp = -1.0;
+        for (int i = 1; i < m; ++i) {
+            const double t = al[i] - th;
+            const double pn = fma(-b2[i - 1], pm, t * p);
+            const double dpn = fma(-b2[i - 1], dpm, fma(t, dp, -p));
+            pm = p;
+            dpm = dp;
+            p = pn;
+            dp = dpn;
+            const int e = (int)((__double_as_longlong(fabs(dp) > fabs(p) ? dp : p) >> 52) & 0x7ff);
+            if (e > 1023 + 500 || e < 1023 - 500) {
+                const int sh = 1023 - e;
+                p = scalbn(p, sh);
+                pm = scalbn(pm, sh);
+                dp = scalbn(dp, sh);
+                dpm = scalbn(dpm, sh);
+            }
+        }
+        // after the loop: p = p_m, pm = p_{m-1}, dp = p_m'
+        const double y2 = (dp != 0.0) ? fabs(pm / dp) : 1.0;
+        theta[blockIdx.x] = th;
+        resid[blockIdx.x] = beta[m - 1] * sqrt(fmin(y2, 1.0));
+    }
+}
+
+// Eigenvector of T_m for theta (one warp per vector, serial in lane 0): inverse
+// iteration with an LU factorisation with partial pivoting of T - theta I (three
+// solves), normalised; written as column i of Y (ld = ldy).
+__global__ void __launch_bounds__(32) tvec_kernel(const double *__restrict__ alpha, const double *__restrict__ beta,
+                                                  int m, const double *__restrict__ theta, double *__restrict__ Y,
+                                                  int ldy, double *__restrict__ work, uint64_t key) {
+    if (threadIdx.x != 0) return;
+    const int iv = blockIdx.x;
+    double *dl = work + (size_t)iv * 6 * m;  // sub (L multipliers)
+    double *dd = dl + m, *du = dd + m, *du2 = du + m, *y = du2 + m;
+    int *ip = reinterpret_cast<int *>(y + m);
+    const double th = theta[iv];
+    double tnorm = 0.0;
+    for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(alpha[i]) + (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < m - 1 ? fabs(beta[i]) : 0.0));
+    const double pivmin = 1e-300 + 2.2e-16 * tnorm;
+    // factor T - th I = P L U (LAPACK dgttrf-style elimination)
+    for (int i = 0; i < m; ++i) {
+        dd[i] = alpha[i] - th;
+        if (i < m - 1) { dl[i] = beta[i]; du[i] = beta[i]; }
+        du2[i] = 0.0;
+    }
+    for (int i = 0; i < m - 1; ++i) {
+        if (fabs(dd[i]) >= fabs(dl[i])) {
+            ip[i] = 0;
+            if (fabs(dd[i]) < pivmin) dd[i] = (dd[i] < 0 ? -pivmin : pivmin);
+            const double f = dl[i] / dd[i];
+            dl[i] = f;
+            dd[i + 1] -= f * du[i];
+        } else {
+            ip[i] = 1;
+            const double f = dd[i] / dl[i];
+            dd[i] = dl[i];
+            dl[i] = f;
+            const double t = du[i];
+            du[i] = dd[i + 1];
+            dd[i + 1] = t - f * dd[i + 1];
+            if (i < m - 2) {
+                du2[i] = du[i + 1];
+                du[i + 1] = -f * du[i + 1];
+            }
+        }
+    }
+    if (fabs(dd[m - 1]) < pivmin) dd[m - 1] = (dd[m - 1] < 0 ? -pivmin : pivmin);
+    for (int i = 0; i < m; ++i) y[i] = 2.0 * dm_unit(dm_rng(key, (uint64_t)(iv * 1024 + i))) - 1.0;
+    for (int it = 0; it < 3; ++it) {
+        // solve L: apply row interchanges and multipliers
+        for (int i = 0; i < m - 1; ++i) {
+            if (ip[i] == 0) y[i + 1] -= dl[i] * y[i];
+            else {
+                const double t = y[i];
+                y[i] = y[i + 1];
+                y[i + 1] = t - dl[i] * y[i];
+            }
+        }
+        // solve U (upper, bandwidth 2)
+        y[m - 1] /= dd[m - 1];
+        if (m > 1) y[m - 2] = (y[m - 2] - du[m - 2] * y[m - 1]) / dd[m - 2];
+        for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
+        double nn = 0.0;
+        for (int i = 0; i < m; ++i) nn += y[i] * y[i];
+        const double inv = 1.0 / sqrt(nn);
+        for (int i = 0; i < m; ++i) y[i] *= inv;
+    }
+    for (int i = 0; i < m; ++i) Y[(size_t)iv * ldy + i] = y[i];
+}
+
+// Gram-Schmidt of Y's columns within clusters of (numerically) equal Ritz values,
+// then an FP32 copy for the Ritz-vector product.
+__global__ void tvec_orth_kernel(int m, int k, const double *__restrict__ theta, double *__restrict__ Y, int ldy,
+                                 float *__restrict__ Yf) {
+    __shared__ double red[32];
+    double tmax = 0.0;
+    for (int i = 0; i < k; ++i) tmax = fmax(tmax, fabs(theta[i]));
+    for (int i = 1; i < k; ++i) {
+        for (int j = 0; j < i; ++j) {
+            if (fabs(theta[i] - theta[j]) > 1e-10 * tmax) continue;
+            double part = 0.0;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) part += Y[(size_t)i * ldy + t] * Y[(size_t)j * ldy + t];
+            part = dm_warp_sum_d(part);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+            __syncthreads();
+            double dot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) dot += red[w];
+            __syncthreads();
+            for (int t = threadIdx.x; t < m; t += blockDim.x) Y[(size_t)i * ldy + t] -= dot * Y[(size_t)j * ldy + t];
+            __syncthreads();
+            part = 0.0;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) part += Y[(size_t)i * ldy + t] * Y[(size_t)i * ldy + t];
+            part = dm_warp_sum_d(part);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+            __syncthreads();
+            double nn = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nn += red[w];
+            __syncthreads();
+            const double inv = 1.0 / sqrt(nn);
+            for (int t = threadIdx.x; t < m; t += blockDim.x) Y[(size_t)i * ldy + t] *= inv;
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
+        const int i = e / m, t = e % m;
+        Yf[(size_t)t * k + i] = (float)Y[(size_t)i * ldy + t];
+    }
+}
+
+// Phi~[pos, i] = sum_t V[t][pos] Y[t][i] (position order), plus per-column |.|^2 (FP64)
+__global__ void __launch_bounds__(256) ritzvec_kernel(const float *__restrict__ V, int64_t ldv, int m, int k,
+                                                      const float *__restrict__ Yf, int64_t N,
+                                                      float *__restrict__ Phi, double *__restrict__ colsum) {
+    extern __shared__ float sY[];  // m x k
+    for (int e = threadIdx.x; e < m * k; e += blockDim.x) sY[e] = Yf[e];
+    __syncthreads();
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float acc[kKMax];
+#pragma unroll
+    for (int i = 0; i < kKMax; ++i) acc[i] = 0.f;
+    if (pos < N) {
+        for (int t = 0; t < m; ++t) {
+            const float v = V[(size_t)t * ldv + pos];
+#pragma unroll
+            for (int i = 0; i < kKMax; ++i)
+                if (i < k) acc[i] = fmaf(v, sY[t * k + i], acc[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kKMax; ++i) {
+        if (i < k) {
+            if (pos < N) Phi[(size_t)i * N + pos] = acc[i];
+            const float ss = dm_warp_sum(acc[i] * acc[i]);
+            if ((threadIdx.x & 31) == 0) atomicAdd(colsum + i, (double)ss);
+        }
+    }
+}
+
+// normalise each column and find its largest-magnitude entry (ties: lowest original index)
+__global__ void __launch_bounds__(256) colmax_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm,
+                                                     int64_t N, int k, const double *__restrict__ colsum,
+                                                     unsigned long long *__restrict__ best) {
+    const int i = blockIdx.y;
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long key = 0ull;
+    if (pos < N) {
+        const float a = fabsf(Phi[(size_t)i * N + pos]);
+        key = ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)perm[pos]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(DM_FULL, key, o);
+        key = other > key ? other : key;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best + i, key);
+}
+
+// sign of each column's largest-magnitude entry: the thread holding that original index reports it
+__global__ void sign_pick_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm, int64_t N,
+                                 const unsigned long long *__restrict__ best, int *__restrict__ neg) {
+    const int i = blockIdx.y;
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= N) return;
+    const int arg = (int)(0xffffffffu - (unsigned)(best[i] & 0xffffffffull));
+    if (perm[pos] == arg) neg[i] = Phi[(size_t)i * N + pos] < 0.f ? 1 : 0;
+}
+
+// unit norm, largest-magnitude entry positive, scattered to the original order
+__global__ void finalize_vec_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm, int64_t N,
+                                    const double *__restrict__ colsum, const int *__restrict__ neg,
+                                    float *__restrict__ out) {
+    const int i = blockIdx.y;
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= N) return;
+    const double sc = (neg[i] ? -1.0 : 1.0) / sqrt(colsum[i]);
+    out[(size_t)i * N + perm[pos]] = (float)((double)Phi[(size_t)i * N + pos] * sc);
+}
+
+__global__ void coords_kernel(const float *__restrict__ evecs, const double *__restrict__ theta,
+                              const double *__restrict__ dg, int64_t N, int t, float *__restrict__ psi) {
+    const int i = blockIdx.y;
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const double lt = pow(theta[i], (double)t);
+    psi[(size_t)i * N + r] = (float)(lt * (double)evecs[(size_t)i * N + r] / sqrt(dg[r]));
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int dm_lanczos_kmax() { return kKMax; }
+
+cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(Lz.nrm2, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    start_vector_kernel<<<nblk(Lz.N, 256), 256, 0, st>>>(perm, Lz.N, dm_stream_key(seed, DM_TAG_V0, 0), Lz.z, Lz.nrm2);
+    dm_count_launches(1);
+    normalize_kernel<<<nblk(Lz.N, 256), 256, 0, st>>>(Lz.z, Lz.N, Lz.nrm2, Lz.V);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+// After Lz.z = A v_j: two Gram-Schmidt passes against V[:, 0..j], alpha_j, beta_j and V[:, j+1].
+cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st) {
+    const int ncols = j + 1;
+    double *h0 = Lz.h, *h1 = Lz.h + (Lz.m_max + 1);
+    cudaError_t e = cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (Lz.m_max + 1), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(Lz.nrm2, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const dim3 pgrid(nblk(Lz.N, kProjRows), nblk(ncols, 8));
+    const size_t ush = sizeof(float) * (size_t)ncols;
+    proj_kernel<<<pgrid, 256, 0, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h0);
+    dm_count_launches(1);
+    update_kernel<<<nblk(Lz.N, 256), 256, ush, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h0, nullptr);
+    dm_count_launches(1);
+    proj_kernel<<<pgrid, 256, 0, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h1);
+    dm_count_launches(1);
+    update_kernel<<<nblk(Lz.N, 256), 256, ush, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h1, Lz.nrm2);
+    dm_count_launches(1);
+    coeff_kernel<<<1, 1, 0, st>>>(j, h0, h1, Lz.nrm2, Lz.alpha, Lz.beta);
+    dm_count_launches(1);
+    if (j + 1 <= Lz.m_max) {
+        normalize_kernel<<<nblk(Lz.N, 256), 256, 0, st>>>(Lz.z, Lz.N, Lz.nrm2, Lz.V + (size_t)(j + 1) * Lz.ldv);
+        dm_count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st) {
+    (void)conv_tol;
+    ritz_kernel<<<k, 32, sizeof(double) * 2 * (size_t)m, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.resid, nullptr);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig,
+                               cudaStream_t st) {
+    float *phi_work = Lz.phi;
+    unsigned long long *best = Lz.best;
+    tvec_kernel<<<k, 32, 0, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.Y, Lz.m_max, Lz.twork,
+                                  dm_stream_key(0x5eedULL, DM_TAG_V0, 1));
+    dm_count_launches(1);
+    tvec_orth_kernel<<<1, 256, 0, st>>>(m, k, Lz.theta, Lz.Y, Lz.m_max, Lz.Yf);
+    dm_count_launches(1);
+    cudaError_t e = cudaMemsetAsync(Lz.colsum, 0, sizeof(double) * k, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(best, 0, sizeof(unsigned long long) * k, st);
+    if (e != cudaSuccess) return e;
+    const size_t ysh = sizeof(float) * (size_t)m * k;
+    if (ysh > 48 * 1024) {
+        e = cudaFuncSetAttribute(ritzvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysh);
+        if (e != cudaSuccess) return e;
+    }
+    ritzvec_kernel<<<nblk(Lz.N, 256), 256, ysh, st>>>(Lz.V, Lz.ldv, m, k, Lz.Yf, Lz.N, phi_work, Lz.colsum);
+    dm_count_launches(1);
+    const dim3 g2(nblk(Lz.N, 256), (unsigned)k);
+    colmax_kernel<<<g2, 256, 0, st>>>(phi_work, perm, Lz.N, k, Lz.colsum, best);
+    dm_count_launches(1);
+    sign_pick_kernel<<<g2, 256, 0, st>>>(phi_work, perm, Lz.N, best, Lz.neg);
+    dm_count_launches(1);
+    finalize_vec_kernel<<<g2, 256, 0, st>>>(phi_work, perm, Lz.N, Lz.colsum, Lz.neg, evecs_orig);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t dm_launch_coords(const float *evecs, const double *theta, const double *dg, int64_t N, int k, int t,
+                             float *psi, cudaStream_t st) {
+    coords_kernel<<<dim3(nblk(N, 256), (unsigned)k), 256, 0, st>>>(evecs, theta, dg, N, t, psi);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}

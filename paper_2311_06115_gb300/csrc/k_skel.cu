@@ -1,0 +1,333 @@
+// k_skel.cu -- skeletonization (sampled interpolative decomposition) and block packing.
+//
+// The far field of the H-matrix K~ = D + UV (Eq. 2.18) is built from nested
+// skeleton bases: for every non-root node a (bottom-up), with candidate columns
+// C_a (a leaf's own points, an internal node's children skeletons) and sampled
+// off-node rows R_a, an interpolative decomposition K(R_a, C_a) ~= K(R_a, J_a) P_a
+// picks the skeleton J_a subset of C_a with P_a(:, J_a) = I. The rank stops at the first
+// pivot whose residual column norm is <= tol * (first pivot norm) -- the block-relative
+// reading of the tolerance of Eq. 1.1 -- or at max_rank.
+//
+// GPU design: one CTA per node of a level; the sampled block (at most
+// (2 max_rank + 10) x cmax FP32) lives in a per-CTA slot of global memory that
+// stays in L2 while the CTA works on it. Column-pivoted modified Gram-Schmidt
+// with explicit residual updates (each step recomputes every remaining column
+// norm from its updated residual, so no norm downdating loses the small
+// residuals that decide the rank) and one re-orthogonalisation of the pivot
+// column; a warp owns a column at a time. P_a = [I, R11^-1 R12] by back
+// substitution, one thread per candidate column.
+#include "dm_internal.cuh"
+
+namespace {
+
+constexpr int kSkelThreads = 256;
+constexpr int kSkelWarps = kSkelThreads / 32;
+
+__device__ __forceinline__ float kentry(const float *__restrict__ Xp, const float *__restrict__ sp, int d,
+                                        int64_t a, int64_t b) {
+    const float *xa = Xp + a * d, *xb = Xp + b * d;
+    float r2 = 0.f;
+    for (int k = 0; k < d; ++k) {
+        float t = xa[k] - xb[k];
+        r2 = fmaf(t, t, r2);
+    }
+    return sp[a] * sp[b] * dm_ex2(-r2);
+}
+
+struct SkelArgs {
+    const float *Xp;  // points in position order, pre-scaled
+    const float *sp;  // s in position order
+    int64_t N;
+    int d, L, level;
+    float tol;
+    int max_rank, cmax, ldp, rmax;
+    uint64_t seed;
+    int32_t *ranks;
+    int32_t *skel;
+    float *P;
+    float *A;   // per-CTA slot rmax x cmax, column-major (ld rmax)
+    float *R;   // per-CTA slot max_rank x cmax, row-major (ld cmax)
+};
+
+__global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    int *C = reinterpret_cast<int *>(smem_raw);          // cmax candidate positions
+    int *Rw = C + a.cmax;                                // rmax row positions
+    int *selpos = Rw + a.rmax;                           // cmax: -1 or pivot step
+    int *piv = selpos + a.cmax;                          // max_rank
+    float *norms = reinterpret_cast<float *>(piv + a.max_rank);  // cmax
+    float *qv = norms + a.cmax;                          // rmax: current pivot column
+    float *coef = qv + a.rmax;                           // max_rank: re-orthogonalisation coefficients
+    __shared__ float red_v[kSkelWarps];
+    __shared__ int red_i[kSkelWarps];
+    __shared__ int s_p;
+    __shared__ float s_np, s_nrm0, s_qn;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int node = (1 << a.level) - 1 + (int)blockIdx.x;
+    int64_t st, sz;
+    dm_node_range(a.N, node, &st, &sz);
+    float *A = a.A + (size_t)blockIdx.x * a.rmax * a.cmax;
+    float *R = a.R + (size_t)blockIdx.x * a.max_rank * a.cmax;
+
+    // ---- candidates
+    int c;
+    if (a.level == a.L) {
+        c = (int)sz;
+        for (int j = threadIdx.x; j < c; j += blockDim.x) C[j] = (int)(st + j);
+    } else {
+        const int l = 2 * node + 1, r = 2 * node + 2;
+        const int sl = a.ranks[l], sr = a.ranks[r];
+        c = sl + sr;
+        for (int j = threadIdx.x; j < c; j += blockDim.x)
+            C[j] = j < sl ? a.skel[(int64_t)l * a.max_rank + j] : a.skel[(int64_t)r * a.max_rank + (j - sl)];
+    }
+    // ---- rows: every off-node position if few enough, else seeded draws with replacement
+    const int64_t off = a.N - sz;
+    const int rtarget = 2 * a.max_rank + 10;
+    const int r = (int)(off <= rtarget ? off : rtarget);
+    const uint64_t key = dm_stream_key(a.seed, DM_TAG_ROWS, (uint64_t)node);
+    for (int t = threadIdx.x; t < r; t += blockDim.x) {
+        int64_t u = (off <= rtarget) ? (int64_t)t : (int64_t)dm_below(dm_rng(key, (uint64_t)t), (uint64_t)off);
+        Rw[t] = (int)(u < st ? u : u + sz);
+    }
+    for (int j = threadIdx.x; j < c; j += blockDim.x) selpos[j] = -1;
+    __syncthreads();
+
+    // ---- sampled block A = K(R, C) and its column norms
+    for (int j = warp; j < c; j += kSkelWarps) {
+        const int64_t cj = C[j];
+        float ss = 0.f;
+        for (int i = lane; i < r; i += 32) {
+            float v = kentry(a.Xp, a.sp, a.d, Rw[i], cj);
+            A[(size_t)j * a.rmax + i] = v;
+            ss = fmaf(v, v, ss);
+        }
+        ss = dm_warp_sum(ss);
+        if (lane == 0) norms[j] = sqrtf(ss);
+    }
+    __syncthreads();
+
+    int kmax = a.max_rank;
+    if (kmax > c) kmax = c;
+    if (kmax > r) kmax = r;
+    int rank = 0;
+    for (int k = 0; k < kmax; ++k) {
+        // ---- pivot: largest residual norm among unselected columns, lowest index on ties
+        float bv = -1.f;
+        int bi = 0x7fffffff;
+        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+            if (selpos[j] < 0) {
+                float v = norms[j];
+                if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float ov = __shfl_xor_sync(DM_FULL, bv, o);
+            int oi = __shfl_xor_sync(DM_FULL, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float v = red_v[0];
+            int i = red_i[0];
+            for (int w = 1; w < kSkelWarps; ++w)
+                if (red_v[w] > v || (red_v[w] == v && red_i[w] < i)) { v = red_v[w]; i = red_i[w]; }
+            s_p = i;
+            s_np = v;
+            if (k == 0) s_nrm0 = v;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (!(s_np > a.tol * s_nrm0) || s_np <= 0.f) break;
+        float *ap = A + (size_t)p * a.rmax;
+        // ---- re-orthogonalise the pivot column against the earlier pivots (one pass)
+        if (k > 0) {
+            for (int t = warp; t < k; t += kSkelWarps) {
+                const float *qt = A + (size_t)piv[t] * a.rmax;
+                float dsum = 0.f;
+                for (int i = lane; i < r; i += 32) dsum = fmaf(qt[i], ap[i], dsum);
+                dsum = dm_warp_sum(dsum);
+                if (lane == 0) coef[t] = dsum;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < r; i += blockDim.x) {
+                float v = ap[i];
+                for (int t = 0; t < k; ++t) v = fmaf(-coef[t], A[(size_t)piv[t] * a.rmax + i], v);
+                ap[i] = v;
+            }
+            for (int t = threadIdx.x; t < k; t += blockDim.x) R[(size_t)t * a.cmax + p] += coef[t];
+            __syncthreads();
+        }
+        // ---- normalise the pivot column into q_k
+        if (warp == 0) {
+            float ss = 0.f;
+            for (int i = lane; i < r; i += 32) ss = fmaf(ap[i], ap[i], ss);
+            ss = dm_warp_sum(ss);
+            if (lane == 0) {
+                s_qn = sqrtf(ss);
+                R[(size_t)k * a.cmax + p] = s_qn;
+                selpos[p] = k;
+                piv[k] = p;
+            }
+        }
+        __syncthreads();
+        const float inv = 1.f / s_qn;
+        for (int i = threadIdx.x; i < r; i += blockDim.x) {
+            float v = ap[i] * inv;
+            ap[i] = v;
+            qv[i] = v;
+        }
+        __syncthreads();
+        // ---- update the remaining columns: R(k, j) = q^T a_j; a_j -= R(k, j) q; fresh norms
+        for (int j = warp; j < c; j += kSkelWarps) {
+            if (selpos[j] >= 0) continue;
+            float *aj = A + (size_t)j * a.rmax;
+            float dsum = 0.f;
+            for (int i = lane; i < r; i += 32) dsum = fmaf(qv[i], aj[i], dsum);
+            dsum = dm_warp_sum(dsum);
+            float ss = 0.f;
+            for (int i = lane; i < r; i += 32) {
+                float v = fmaf(-dsum, qv[i], aj[i]);
+                aj[i] = v;
+                ss = fmaf(v, v, ss);
+            }
+            ss = dm_warp_sum(ss);
+            if (lane == 0) {
+                R[(size_t)k * a.cmax + j] = dsum;
+                norms[j] = sqrtf(ss);
+            }
+        }
+        rank = k + 1;
+        __syncthreads();
+    }
+    __syncthreads();
+
+    // ---- P = [I, R11^-1 R12] in candidate order; rows t < rank of the node's slot
+    float *Pn = a.P + (size_t)node * a.max_rank * a.ldp;
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        const int sp_ = selpos[j];
+        if (sp_ >= 0) {
+            for (int t = 0; t < rank; ++t) Pn[(size_t)t * a.ldp + j] = (t == sp_) ? 1.f : 0.f;
+        } else {
+            for (int t = rank - 1; t >= 0; --t) {
+                float v = R[(size_t)t * a.cmax + j];
+                for (int u = t + 1; u < rank; ++u) v = fmaf(-R[(size_t)t * a.cmax + piv[u]], Pn[(size_t)u * a.ldp + j], v);
+                Pn[(size_t)t * a.ldp + j] = v / R[(size_t)t * a.cmax + piv[t]];
+            }
+        }
+    }
+    // zero the row padding so vectorised readers may overrun c up to ldp
+    for (int t = 0; t < rank; ++t)
+        for (int j = c + threadIdx.x; j < a.ldp; j += blockDim.x) Pn[(size_t)t * a.ldp + j] = 0.f;
+    for (int t = threadIdx.x; t < a.max_rank; t += blockDim.x)
+        a.skel[(int64_t)node * a.max_rank + t] = t < rank ? C[piv[t]] : -1;
+    if (threadIdx.x == 0) a.ranks[node] = rank;
+}
+
+// ---- near blocks K(I_a, I_a), row-major with leading dimension ldk, zero padded
+__global__ void pack_near_kernel(const float *__restrict__ Xp, const float *__restrict__ sp, int64_t N, int d, int L,
+                                 int leaf_max, int ldk, float *__restrict__ Knear) {
+    const int leaf = blockIdx.x;
+    int64_t st, sz;
+    dm_node_range(N, (1 << L) - 1 + leaf, &st, &sz);
+    float *blk = Knear + (size_t)leaf * leaf_max * ldk;
+    const int rows_per = (leaf_max + gridDim.y - 1) / gridDim.y;
+    const int r0 = blockIdx.y * rows_per;
+    const int r1 = min(leaf_max, r0 + rows_per);
+    for (int i = r0; i < r1; ++i) {
+        for (int j = threadIdx.x; j < ldk; j += blockDim.x) {
+            float v = 0.f;
+            if (i < sz && j < sz) v = kentry(Xp, sp, d, st + i, st + j);
+            blk[(size_t)i * ldk + j] = v;
+        }
+    }
+}
+
+// ---- far blocks B_p = K(S_l, S_r) for the children of every internal node, row-major s_l x s_r
+__global__ void pack_far_kernel(const float *__restrict__ Xp, const float *__restrict__ sp, int d,
+                                const int32_t *__restrict__ ranks, const int32_t *__restrict__ skel, int max_rank,
+                                float *__restrict__ B) {
+    const int node = blockIdx.x;
+    const int l = 2 * node + 1, r = 2 * node + 2;
+    const int sl = ranks[l], sr = ranks[r];
+    float *Bn = B + (size_t)node * max_rank * max_rank;
+    for (int e = threadIdx.x; e < sl * sr; e += blockDim.x) {
+        const int ia = e / sr, ib = e % sr;
+        Bn[e] = kentry(Xp, sp, d, skel[(int64_t)l * max_rank + ia], skel[(int64_t)r * max_rank + ib]);
+    }
+}
+
+__global__ void permute_points_kernel(const float *__restrict__ Xs, const float *__restrict__ sf,
+                                      const int32_t *__restrict__ perm, int64_t N, int d, float *__restrict__ Xp,
+                                      float *__restrict__ sp) {
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= N) return;
+    const int64_t i = perm[pos];
+    for (int k = 0; k < d; ++k) Xp[pos * d + k] = Xs[i * d + k];
+    sp[pos] = sf[i];
+}
+
+}  // namespace
+
+size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
+    return sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank) + sizeof(float) * (size_t)(cmax + rmax + max_rank);
+}
+
+cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, int L, const int32_t *perm,
+                           double tol, int max_rank, int cmax, int ldp, uint64_t seed, int32_t *ranks,
+                           int32_t *skel, float *P, DmSkelWork *w, cudaStream_t st) {
+    (void)perm;
+    SkelArgs a;
+    a.Xp = Xp;
+    a.sp = sp;
+    a.N = N;
+    a.d = d;
+    a.L = L;
+    a.tol = (float)tol;
+    a.max_rank = max_rank;
+    a.cmax = cmax;
+    a.ldp = ldp;
+    a.rmax = w->rmax;
+    a.seed = seed;
+    a.ranks = ranks;
+    a.skel = skel;
+    a.P = P;
+    a.A = w->A;
+    a.R = w->R;
+    const size_t smem = dm_skel_smem_bytes(cmax, w->rmax, max_rank);
+    cudaError_t e = cudaFuncSetAttribute(skel_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(ranks, 0, sizeof(int32_t), st);  // the root has no skeleton
+    if (e != cudaSuccess) return e;
+    for (int lvl = L; lvl >= 1; --lvl) {
+        a.level = lvl;
+        skel_level_kernel<<<1 << lvl, kSkelThreads, smem, st>>>(a);
+        dm_count_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cudaStream_t st) {
+    if (pack_near) {
+        dim3 grid(1u << H.L, (unsigned)((H.leaf_max + 31) / 32));
+        pack_near_kernel<<<grid, 128, 0, st>>>(H.Xs, H.sp, H.N, H.d, H.L, H.leaf_max, H.ldk, Knear);
+        dm_count_launches(1);
+    }
+    if (H.L > 0) {
+        pack_far_kernel<<<(1 << H.L) - 1, 256, 0, st>>>(H.Xs, H.sp, H.d, H.ranks, H.skel, H.max_rank, B);
+        dm_count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t dm_permute_points(const float *Xs, const float *sf, const int32_t *perm, int64_t N, int d, float *Xp,
+                              float *sp, cudaStream_t st) {
+    permute_points_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Xs, sf, perm, N, d, Xp, sp);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}

@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every declared call."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(dm_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2311_06115_gb300 import build
+
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (dm_[a-z0-9_]+)", out))
+    declared = _declared()
+    assert declared, "no declarations found"
+    assert declared <= exported, f"declared but not exported: {sorted(declared - exported)}"
+
+
+def test_binding_covers_the_abi():
+    import paper_2311_06115_gb300 as dm
+
+    for name in _declared():
+        assert hasattr(dm, name), f"binding lacks {name}"
+
+
+def test_library_loads_and_reports_status_strings():
+    import paper_2311_06115_gb300 as dm
+
+    dm.load()
+    assert dm.dm_status_str(dm.DM_ENOCONV) == "DM_ENOCONV"
+    cfg = dm.dm_config_default()
+    assert cfg.m_max == 300 and cfg.check_every >= 1
+
+
+def test_no_gpu_fails_loudly():
+    import numpy as np
+    import torch
+
+    import paper_2311_06115_gb300 as dm
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_create(np.zeros((8, 3), np.float32))
+    assert e.value.status == dm.DM_ECUDA
+
+
+def test_sm103a_target_only():
+    from paper_2311_06115_gb300 import build
+
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

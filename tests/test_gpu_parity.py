@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 device arithmetic against FP64): unit roundoff u = 6e-8; an
+entry exp2(-r^2) from pre-scaled FP32 coordinates carries ~3u relative error
+plus the MUFU ex2 error (~2 ulp); sums of up to a few hundred such terms in FP32
+tiles grow that to ~1e-6 relative at most, so degree vectors are held to 2e-6
+and matvec outputs to 1e-5 of max|x| per element (>= 100 u of headroom).
+Integer work (bandwidth median, tree permutation) is bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2311_06115_gb300 as m
+
+    m.load()
+    return m
+
+
+def _scurve(n, seed=0):
+    return synth.as_f32(synth.s_curve(n, seed))
+
+
+def _rel_inf(a, b, scale):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))) / scale)
+
+
+# ------------------------------------------------------------------ bandwidth and degrees
+
+@pytest.mark.parametrize("n", [1000, 1449, 3000])
+def test_bandwidth_median_bit_exact(dm, n):
+    X = _scurve(n, 5)
+    h = dm.dm_create(X, eps=-1.0)
+    assert dm.dm_get_eps(h) == O.median_sqdist(X, seed=0)
+
+
+@pytest.mark.parametrize("n,alpha", [(2048, 1.0), (1537, 1.0), (999, 0.5), (600, 0.0)])
+def test_degrees_match_oracle(dm, n, alpha):
+    X = _scurve(n, 1)
+    eps = O.median_sqdist(X)
+    h = dm.dm_create(X, eps=eps, alpha=alpha)
+    q, dg, s = dm.dm_get_degrees(h)
+    oq, odg, os_ = O.degrees(X, eps, alpha)
+    np.testing.assert_allclose(q, oq, rtol=2e-6)
+    np.testing.assert_allclose(dg, odg, rtol=2e-6)
+    np.testing.assert_allclose(s, os_, rtol=2e-6)
+
+
+def test_degrees_on_generic_dimension(dm):
+    X = synth.as_f32(synth.gaussian_mixture(700, d=64, seed=2))
+    eps = O.median_sqdist(X)
+    h = dm.dm_create(X, eps=eps)
+    q, dg, s = dm.dm_get_degrees(h)
+    oq, odg, os_ = O.degrees(X, eps, 1.0)
+    np.testing.assert_allclose(q, oq, rtol=5e-6)
+    np.testing.assert_allclose(s, os_, rtol=5e-6)
+
+
+def test_exact_matvec_before_compress(dm):
+    n = 1200
+    X = _scurve(n, 2)
+    eps = O.median_sqdist(X)
+    h = dm.dm_create(X, eps=eps)
+    _, _, s = O.degrees(X, eps, 1.0)
+    x = synth.random_rhs(n, 2, seed=3).astype(np.float32)
+    y = dm.dm_matvec(h, np.asfortranarray(x))
+    yr = O.S_matvec(X, eps, s, x.astype(np.float64))
+    assert _rel_inf(y, yr, np.abs(x).max()) < 1e-5
+
+
+# ------------------------------------------------------------------ tree
+
+@pytest.mark.parametrize("n,leaf", [(2048, 128), (1500, 100), (777, 50), (4097, 256)])
+def test_tree_bit_exact(dm, n, leaf):
+    X = _scurve(n, 7)
+    eps = O.median_sqdist(X)
+    h = dm.dm_create(X, eps=eps)
+    dm.dm_compress(h, 1e-5, leaf, 32)
+    perm, L = dm.dm_get_tree(h)
+    operm, oL = O.tree(X, eps, leaf)
+    assert L == oL
+    assert np.array_equal(perm, operm)
+
+
+# ------------------------------------------------------------------ H-matvec on a replayed oracle structure
+
+@pytest.mark.parametrize("mode", ["cached", "onthefly"])
+@pytest.mark.parametrize("n,leaf,rank,tol", [(2048, 128, 64, 1e-5), (1500, 100, 40, 1e-3), (700, 64, 64, 0.0)])
+def test_hmatvec_replay_matches_oracle(dm, mode, n, leaf, rank, tol):
+    X = _scurve(n, 11)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, leaf, tol, rank)
+    cfg = dm.dm_config_default(near_mode=dm.DM_NEAR_CACHED if mode == "cached" else dm.DM_NEAR_ONTHEFLY)
+    h = dm.dm_create(X, eps=eps, cfg=cfg)
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    x = synth.random_rhs(n, 3, seed=5).astype(np.float32)
+    y = dm.dm_matvec(h, np.asfortranarray(x))
+    yr = O.hmatvec(X, eps, s, H, x.astype(np.float64))
+    assert _rel_inf(y, yr, np.abs(x).max()) < 1e-5
+    # a second call reuses the arrival counters: results must not change
+    y2 = dm.dm_matvec(h, np.asfortranarray(x))
+    assert np.array_equal(y, y2)
+
+
+# ------------------------------------------------------------------ GPU compression
+
+def test_gpu_compression_exact_at_full_rank(dm):
+    n = 256
+    X = _scurve(n, 3)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    h = dm.dm_create(X, eps=eps)
+    dm.dm_compress(h, 0.0, 32, 256)
+    x = synth.random_rhs(n, 1, seed=8)[:, 0].astype(np.float32)
+    y = dm.dm_matvec(h, x)
+    yr = O.S_matvec(X, eps, s, x.astype(np.float64))
+    assert _rel_inf(y, yr, np.abs(x).max()) < 2e-5
+
+
+@pytest.mark.parametrize("n,leaf,rank,tol", [(2048, 128, 64, 1e-5), (3001, 200, 48, 1e-4)])
+def test_gpu_compression_accuracy_and_structure(dm, n, leaf, rank, tol):
+    X = _scurve(n, 4)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    h = dm.dm_create(X, eps=eps)
+    dm.dm_compress(h, tol, leaf, rank)
+    perm, L = dm.dm_get_tree(h)
+    ranks, skel, P = dm.dm_get_hmatrix(h)
+    st = dm.dm_get_stats(h)
+    cmax = max(st["leaf_max"], 2 * rank)
+    P = P.reshape(-1, rank, cmax)
+    # structure: ranks within caps; skeletons are candidates; P(:, J) = I
+    assert ranks[0] == 0 and ranks[1:].max() <= rank and ranks[1:].min() >= 1
+    for node in range(1, len(ranks)):
+        r = ranks[node]
+        J = skel[node * rank:node * rank + r]
+        st0, sz = O.node_range(n, node)
+        lvl = int(math.log2(node + 1))
+        if lvl == L:
+            C = np.arange(st0, st0 + sz)
+        else:
+            l, rr = 2 * node + 1, 2 * node + 2
+            C = np.concatenate([skel[l * rank:l * rank + ranks[l]], skel[rr * rank:rr * rank + ranks[rr]]])
+        assert set(J.tolist()) <= set(C.tolist())
+        cols = [int(np.where(C == j)[0][0]) for j in J]
+        np.testing.assert_array_equal(P[node][:r, cols], np.eye(r, dtype=np.float32))
+    # accuracy against the exact operator, next to the oracle's own compression
+    x = synth.random_rhs(n, 1, seed=9)[:, 0]
+    yr = O.S_matvec(X, eps, s, x)
+    y = dm.dm_matvec(h, x.astype(np.float32))
+    err_gpu = np.linalg.norm(y - yr) / np.linalg.norm(yr)
+    Ho = O.compress(X, eps, s, leaf, tol, rank)
+    err_or = np.linalg.norm(O.hmatvec(X, eps, s, Ho, x) - yr) / np.linalg.norm(yr)
+    assert err_gpu < 10 * err_or + 1e-6, (err_gpu, err_or)
+
+
+# ------------------------------------------------------------------ Lanczos
+
+def test_eigs_replayed_structure_match_oracle_lanczos(dm):
+    n = 2048
+    X = _scurve(n, 0)
+    eps = O.median_sqdist(X)
+    _, dg, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, 128, 1e-5, 64)
+    evo, Vo, _, sto = O.lanczos_hmat(X, eps, s, H, 10, conv_tol=1e-10)
+    assert sto == 0
+    h = dm.dm_create(X, eps=eps)
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    ev, V, conv = dm.dm_eigs(h, 10)
+    assert conv
+    np.testing.assert_allclose(ev, evo, rtol=2e-5, atol=2e-7)
+    for i in range(10):
+        c = abs(float(np.dot(V[:, i].astype(np.float64), Vo[:, i])))
+        assert math.acos(min(1.0, c)) < 2e-3
+
+
+def test_eigs_c1_workload_against_dense_oracle(dm):
+    """2048-point s-curve, leaf 128, rank 64, tol 1e-5, top 10 (the small parity workload)."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "scurve_n2048.json")))
+    X = _scurve(2048, 0)
+    h = dm.dm_create(X, eps=-1.0)
+    assert dm.dm_get_eps(h) == g["eps"]
+    dm.dm_compress(h, 1e-5, 128, 64)
+    ev, V, conv = dm.dm_eigs(h, 10)
+    assert conv
+    ref = np.array(g["evals_top10"])
+    rel = np.abs(ev - ref) / ref
+    assert rel.max() < 1e-4, rel
+    assert abs(ev[0] - 1.0) < 1e-5
+    # orthonormal, signed eigenvectors
+    G = V.astype(np.float64).T @ V.astype(np.float64)
+    np.testing.assert_allclose(G, np.eye(10), atol=2e-5)
+    for i in range(10):
+        assert V[np.argmax(np.abs(V[:, i])), i] > 0
+    # subspace angle against the exact eigenvectors
+    q, dg, s = O.degrees(X, g["eps"], 1.0)
+    _, Vo, _, _ = O.lanczos_S(X, g["eps"], s, 10, conv_tol=1e-10)
+    sv = np.linalg.svd(Vo.T @ V.astype(np.float64), compute_uv=False)
+    assert math.acos(min(1.0, sv.min())) < 1e-3
+    # diffusion coordinates psi = theta^t Dg^-1/2 phi
+    psi = dm.dm_coords(h, 4, 2)
+    want = (ev[:4] ** 2)[None, :] * V[:, :4].astype(np.float64) / np.sqrt(dg)[:, None]
+    np.testing.assert_allclose(psi, want, rtol=2e-5, atol=1e-9)
+
+
+def test_eigs_state_errors(dm):
+    X = _scurve(300, 1)
+    h = dm.dm_create(X, eps=-1.0)
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_eigs(h, 3)
+    assert e.value.status == dm.DM_ESTATE
+    dm.dm_compress(h, 1e-5, 64, 16)
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_eigs(h, 0)
+    assert e.value.status == dm.DM_EINVAL
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_compress(h, -1.0, 64, 16)
+    assert e.value.status == dm.DM_EINVAL
