@@ -200,9 +200,12 @@ __global__ void __launch_bounds__(32) ritz_kernel(const double *__restrict__ alp
 // Eigenvector of T_m for theta (one warp per vector, serial in lane 0): inverse
 // iteration with an LU factorisation with partial pivoting of T - theta I (three
 // solves), normalised; written as column i of Y (ld = ldy).
-__global__ void __launch_bounds__(32) tvec_kernel(const double *__restrict__ alpha, const double *__restrict__ beta,
-                                                  int m, const double *__restrict__ theta, double *__restrict__ Y,
-                                                  int ldy, double *__restrict__ work, uint64_t key) {
+// The workspace is read and written through several pointers carved out of one
+// buffer, so no parameter here is declared __restrict__: with it the optimised
+// build reorders those accesses and returns wrong vectors.
+__global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const double *beta,
+                                                  int m, const double *theta, double *Y,
+                                                  int ldy, double *work, uint64_t key) {
     if (threadIdx.x != 0) return;
     const int iv = blockIdx.x;
     double *dl = work + (size_t)iv * 6 * m;  // sub (L multipliers)
@@ -265,8 +268,8 @@ __global__ void __launch_bounds__(32) tvec_kernel(const double *__restrict__ alp
 
 // Gram-Schmidt of Y's columns within clusters of (numerically) equal Ritz values,
 // then an FP32 copy for the Ritz-vector product.
-__global__ void tvec_orth_kernel(int m, int k, const double *__restrict__ theta, double *__restrict__ Y, int ldy,
-                                 float *__restrict__ Yf) {
+__global__ void tvec_orth_kernel(int m, int k, const double *theta, double *Y, int ldy,
+                                 float *Yf) {
     __shared__ double red[32];
     double tmax = 0.0;
     for (int i = 0; i < k; ++i) tmax = fmax(tmax, fabs(theta[i]));
