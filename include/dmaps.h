@@ -152,6 +152,31 @@ int dm_get_stats(dm_handle h, dm_stats *st);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t dm_kernel_launches(void);
 
+/* ---- allocation-free entry point (no counterpart in the paper) ----
+ * For callers that cannot let a library allocate device memory: code running
+ * inside a framework that owns all device memory and forbids side allocations,
+ * services with a memory budget fixed up front, and hot paths that must not take
+ * cudaMalloc's implicit device-wide synchronisation.
+ *
+ * Computes the same degree vectors as dm_create (q = W 1, dg = W^a 1,
+ * s = q^-a dg^-1/2, each N doubles in the original point order) for N points
+ * (N x d row-major float32) with an explicit eps > 0, enqueued on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream) and not synchronised: the
+ * outputs are ready when the stream reaches this work. All four pointers must
+ * be device memory the caller owns. It calls no cudaMalloc, cudaFree or other
+ * allocating routine: its intermediate arrays live in one fixed 16 MiB
+ * module-scope device array that every GPU loading this library holds until
+ * the process exits, which limits N * (4 d + 16) bytes (rounded up to 256-byte
+ * pieces) to 16 MiB — about 670,000 points at d = 3.
+ * The first call on a device looks up that array's device address with that
+ * device current; make this first call before any stream capture.
+ * Every call shares the one array, so calls whose work overlaps on the GPU
+ * (different streams, threads or devices' streams racing on one device) race;
+ * serialise them. Errors: DM_EINVAL on a NULL or host pointer, N < 2, d < 1,
+ * eps <= 0, alpha < 0, or a size above the limit; DM_ECUDA if a launch fails. */
+int dm_degrees_noalloc(const float *points, int64_t N, int32_t d, double eps, double alpha,
+                       double *q, double *dg, double *s, void *stream);
+
 /* eps in use, and the degree vectors of Algorithm 1 (N doubles each, original
  * order; any pointer may be NULL). */
 int dm_get_eps(dm_handle h, double *eps);

@@ -24,7 +24,7 @@ __all__ = [
     "DM_NEAR_AUTO", "DM_NEAR_CACHED", "DM_NEAR_ONTHEFLY", "dm_config", "dm_stats", "lib_path", "load",
     "dm_config_default", "dm_create", "dm_compress", "dm_matvec", "dm_eigs", "dm_coords", "dm_destroy",
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
-    "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches",
+    "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc",
 ]
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         "dm_get_hmatrix": (i32, [vp, vp, vp, vp]),
         "dm_load_hmatrix": (i32, [vp, i32, i32, vp, vp, vp, vp]),
         "dm_kernel_launches": (i64, []),
+        "dm_degrees_noalloc": (i32, [vp, i64, i32, f64, f64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -293,6 +294,20 @@ def dm_destroy(h: Handle) -> None:
     if h.ptr:
         _check(load().dm_destroy(h))
         h.ptr = None
+
+
+def dm_degrees_noalloc(points, eps: float, alpha: float, q, dg, s, stream=None) -> None:
+    """dm_degrees_noalloc: CUDA float32 points (N, d) and CUDA float64 outputs q, dg, s (N,).
+
+    Enqueues on `stream` (a torch.cuda.Stream or raw handle; default: torch's current stream)
+    and does not synchronise."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    N, d = int(points.shape[0]), int(points.shape[1])
+    _check(load().dm_degrees_noalloc(_ptr(points), N, d, float(eps), float(alpha), _ptr(q), _ptr(dg), _ptr(s),
+                                     handle))
 
 
 def dm_kernel_launches() -> int:

@@ -38,6 +38,13 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+}  // namespace
+
+// message + status for entry points defined in other translation units
+int dm_fail_msg(int code, const char *msg) { return fail(code, "%s", msg); }
+
+namespace {
+
 #define DM_CUDA(expr)                                                                                  \
     do {                                                                                               \
         cudaError_t _e = (expr);                                                                       \

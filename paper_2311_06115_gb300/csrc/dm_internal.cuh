@@ -10,6 +10,8 @@
 
 // process-wide count of kernel launches (dm_kernel_launches)
 void dm_count_launches(long long n);
+// record `msg` as the calling thread's last error (dm_last_error) and return `code`
+int dm_fail_msg(int code, const char *msg);
 #define DM_FULL 0xffffffffu
 
 // ---------------------------------------------------------------------------
