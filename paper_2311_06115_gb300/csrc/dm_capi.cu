@@ -95,11 +95,12 @@ struct dm_ctx {
     // structure
     bool compressed = false;
     double tol = 0;
-    int L = 0, leaf_max = 0, ldk = 0, max_rank = 0, cmax = 0, ldp = 0, near_mode = DM_NEAR_CACHED;
+    int L = 0, leaf_max = 0, ldk = 0, max_rank = 0, rank_hi = 0, cmax = 0, ldp = 0, near_mode = DM_NEAR_CACHED;
     int32_t *perm = nullptr, *ranks = nullptr, *skel = nullptr;
     float *P = nullptr, *B = nullptr, *Knear = nullptr, *Xp = nullptr, *sp = nullptr;
-    float *what = nullptr, *uhat = nullptr, *ynear = nullptr;
+    float *what = nullptr, *uhat = nullptr, *ynear = nullptr, *PT = nullptr;
     unsigned *cnt = nullptr;
+    int ldt = 4;
     // lanczos
     DmLanczos lz{};
     bool lz_ready = false;
@@ -155,12 +156,15 @@ struct dm_ctx {
         H.leaf_max = leaf_max;
         H.ldk = ldk;
         H.max_rank = max_rank;
+        H.rank_hi = rank_hi > 0 ? rank_hi : max_rank;
         H.cmax = cmax;
         H.ldp = ldp;
         H.perm = perm;
         H.ranks = ranks;
         H.skel = skel;
         H.P = P;
+        H.PT = PT;
+        H.ldt = ldt;
         H.B = B;
         H.Knear = Knear;
         H.Xs = Xp;
@@ -233,12 +237,18 @@ int finish_structure(dm_ctx *h) {
     DM_CUDA(cudaMemsetAsync(h->cnt, 0, sizeof(unsigned) * nnodes, h->stream));
     DM_CUDA(cudaMemsetAsync(h->what, 0, sizeof(float) * (size_t)nnodes * h->max_rank, h->stream));
     DM_CUDA(cudaMemsetAsync(h->uhat, 0, sizeof(float) * (size_t)nnodes * h->max_rank, h->stream));
-    DmHmat H = h->hmat();
-    DM_CUDA(dm_pack(H, h->Knear, h->B, cached, h->stream));
     // statistics
     std::vector<int32_t> rk(nnodes);
     DM_CUDA(cudaMemcpyAsync(rk.data(), h->ranks, sizeof(int32_t) * nnodes, cudaMemcpyDeviceToHost, h->stream));
     DM_CUDA(cudaStreamSynchronize(h->stream));
+    int rank_hi = 1;
+    for (int node = 1; node < nnodes; ++node) rank_hi = rk[node] > rank_hi ? rk[node] : rank_hi;
+    h->rank_hi = rank_hi;
+    h->ldt = (int)round_up(rank_hi, 4);
+    DM_CHECK(h->alloc(&h->PT, (size_t)nleaves * h->leaf_max * h->ldt, G_STRUCT));
+    DmHmat H = h->hmat();
+    DM_CUDA(dm_pack(H, h->Knear, h->B, cached, h->stream));
+    DM_CUDA(dm_transpose_leaf_bases(H, h->PT, h->stream));
     int rmin = 1 << 30, rmax = 0;
     double rsum = 0;
     int64_t basis = 0, far = 0, near = 0;
@@ -332,6 +342,9 @@ int ensure_lanczos(dm_ctx *h) {
     DM_CHECK(h->alloc(&L.phi, (size_t)kmax * h->N, G_LANCZOS));
     DM_CHECK(h->alloc(&L.best, (size_t)kmax, G_LANCZOS));
     DM_CHECK(h->alloc(&L.neg, (size_t)kmax, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.bar, 1, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.err, 1, G_LANCZOS));
+    DM_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), h->stream));
     DM_CHECK(h->alloc(&h->evecs, (size_t)kmax * h->N, G_LANCZOS));
     // zero the whole basis once: padding rows beyond N must read as zero
     DM_CUDA(cudaMemsetAsync(L.V, 0, sizeof(float) * (size_t)(L.m_max + 1) * L.ldv, h->stream));
@@ -425,10 +438,12 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
             const int64_t npairs = N * (N - 1) / 2;
             const int64_t m = npairs <= ((int64_t)1 << 20) ? npairs : ((int64_t)1 << 20);
             double *pairs = nullptr, *res = nullptr;
+            unsigned char *sel = nullptr;
             DM_CHECK(h->alloc(&pairs, (size_t)m, G_WORK));
             DM_CHECK(h->alloc(&res, 1, G_WORK));
+            DM_CHECK(h->alloc(&sel, 2 * dm_select_state_bytes(), G_WORK));
             DM_CUDA(dm_launch_pair_sqdist(h->X, N, d, h->cfg.seed, pairs, m, h->stream));
-            DM_CUDA(dm_launch_select_median(pairs, m, res, h->stream));
+            DM_CUDA(dm_launch_select_median(pairs, m, sel, res, h->stream));
             DM_CUDA(cudaMemcpyAsync(&eps, res, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             DM_CUDA(cudaStreamSynchronize(h->stream));
             h->free_group(G_WORK);
@@ -445,12 +460,18 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
         DM_CHECK(h->alloc(&h->sf, (size_t)N, G_BASE));
         DM_CHECK(h->alloc(&h->qaf, (size_t)N, G_BASE));
         DM_CHECK(h->alloc(&h->tmpw, (size_t)N, G_BASE));
-        DM_CUDA(dm_launch_scale_points(h->X, N, d, eps, h->Xs, h->stream));
-        DM_CUDA(dm_launch_degree_pass(h->Xs, N, d, nullptr, h->q, h->stream));
+        float *nrm = nullptr, *nmax = nullptr;
+        double *cwork = nullptr;
+        DM_CHECK(h->alloc(&nrm, (size_t)N, G_WORK));
+        DM_CHECK(h->alloc(&nmax, 1, G_WORK));
+        DM_CHECK(h->alloc(&cwork, 8, G_WORK));
+        DM_CUDA(dm_launch_center_scale(h->X, N, d, eps, h->Xs, nrm, nmax, cwork, h->stream));
+        DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, nullptr, h->q, h->stream));
         DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
-        DM_CUDA(dm_launch_degree_pass(h->Xs, N, d, h->qaf, h->dg, h->stream));
+        DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, h->qaf, h->dg, h->stream));
         DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
         h->stats.ms_create = t.stop();
+        h->free_group(G_WORK);
         DM_CUDA(cudaGetLastError());
         return DM_OK;
     }();
@@ -479,7 +500,9 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
     const int L = dm_depth_for(h->N, leaf_size);
     if (L > 20) return fail(DM_EINVAL, "tree of depth %d (leaf_size %d) exceeds 2^20 leaves", L, leaf_size);
     if (((int64_t)1 << L) > h->N) return fail(DM_EINVAL, "leaf_size %d too small for N=%lld", leaf_size, (long long)h->N);
-    if (max_rank > 1024) return fail(DM_EINVAL, "max_rank must be <= 1024");
+    if (max_rank > 256) return fail(DM_EINVAL, "max_rank must be <= 256");
+    if (((h->N + ((int64_t)1 << L) - 1) >> L) > dm_skel_max_candidates())
+        return fail(DM_EINVAL, "leaves of more than %d points are not supported", dm_skel_max_candidates());
     DM_CHECK(alloc_structure(h, L, max_rank));
     h->tol = tol;
     resolve_near_mode(h);
@@ -519,10 +542,14 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         DM_CUDA(dm_permute_points(h->Xs, h->sf, h->perm, h->N, h->d, h->Xp, h->sp, h->stream));
         DmSkelWork w{};
         w.rmax = 2 * max_rank + 10;
+        w.lda = (int)round_up(h->cmax, 32);
         const size_t smem = dm_skel_smem_bytes(h->cmax, w.rmax, max_rank);
-        if (smem > 220 * 1024) return fail(DM_EINVAL, "leaf size / rank too large for the skeletonization kernel");
-        DM_CHECK(h->alloc(&w.A, (size_t)nleaves * w.rmax * h->cmax, G_WORK));
+        if (smem > 220 * 1024 || h->cmax > dm_skel_max_candidates())
+            return fail(DM_EINVAL, "leaf size (%d) / rank (%d) too large for the skeletonization kernel",
+                        h->leaf_max, max_rank);
+        DM_CHECK(h->alloc(&w.A, (size_t)nleaves * w.rmax * w.lda, G_WORK));
         DM_CHECK(h->alloc(&w.R, (size_t)nleaves * max_rank * h->cmax, G_WORK));
+        DM_CHECK(h->alloc(&w.Q, (size_t)nleaves * max_rank * w.rmax, G_WORK));
         DM_CUDA(dm_skeletonize(h->Xp, h->sp, h->N, h->d, L, h->perm, tol, max_rank, h->cmax, h->ldp, h->cfg.seed,
                                h->ranks, h->skel, h->P, &w, h->stream));
         ms_skel = t.stop();
@@ -602,7 +629,10 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
         m = j + 1;
         ritz_current = false;
         const bool last = (m == m_cap);
-        if (m >= k && (m % h->cfg.check_every == 0 || last)) {
+        // convergence checks from m = 2k on (the wanted pairs rarely converge earlier), then
+        // every check_every steps
+        const int first = 2 * k < m_cap ? 2 * k : m_cap;
+        if (m >= first && ((m - first) % h->cfg.check_every == 0 || last)) {
             DM_CUDA(dm_lanczos_ritz(Lz, m, k, h->cfg.conv_tol, h->stream));
             DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
             DM_CUDA(cudaMemcpyAsync(rs.data(), Lz.resid, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
@@ -625,6 +655,14 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
     }
     DM_CUDA(dm_lanczos_vectors(Lz, m, k, h->perm, h->evecs, h->stream));
     DM_CUDA(cudaStreamSynchronize(h->stream));
+    {
+        int err = 0;
+        DM_CUDA(cudaMemcpy(&err, Lz.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) {
+            DM_CUDA(cudaMemset(Lz.err, 0, sizeof(int)));
+            return fail(DM_ETIMEOUT, "a grid barrier of the Lanczos step gave up waiting");
+        }
+    }
     if (is_device_ptr(evals)) DM_CUDA(cudaMemcpyAsync(evals, th.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
     else
         for (int i = 0; i < k; ++i) evals[i] = th[i];

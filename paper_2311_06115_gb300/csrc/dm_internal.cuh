@@ -94,6 +94,21 @@ __device__ __forceinline__ double dm_warp_sum_d(double v) {
     return v;
 }
 
+// Asynchronous global->shared copies (cp.async): issued back to back with no register
+// round trip, completed by dm_cp_async_wait_all(). A block must wait for its own copies
+// before it exits or reuses the destination.
+__device__ __forceinline__ void dm_cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void dm_cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void dm_cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // exp2 on the MUFU unit (PTX ex2.approx.ftz.f32: documented max error ~2 ulp over its range)
 __device__ __forceinline__ float dm_ex2(float x) {
     float y;
@@ -122,12 +137,15 @@ struct DmHmat {
     int leaf_max;       // ceil(N / 2^L)
     int ldk;            // leading dimension of a stored leaf block (leaf_max rounded up to 4)
     int max_rank;
+    int rank_hi;        // largest rank actually present (<= max_rank)
     int cmax;           // max candidates of a node = max(leaf_max, 2 max_rank)
     int ldp;            // row stride of a P slot (cmax rounded up to 4)
     const int32_t *perm;   // perm[pos] = original index
     const int32_t *ranks;  // per node
     const int32_t *skel;   // per node, max_rank positions
     const float *P;        // per node slot max_rank x ldp, row-major
+    const float *PT;       // per leaf slot leaf_max x ldt: P_leaf transposed (point-major), zero padded
+    int ldt;               // rank_hi rounded up to 4
     const float *B;        // per internal node slot max_rank x max_rank: K(S_l, S_r), row-major s_l x s_r
     const float *Knear;    // per leaf slot leaf_max x ldk (cached mode)
     const float *Xs;       // points in position order, scaled by sqrt(log2(e)/eps), N x d (on-the-fly mode)
@@ -145,10 +163,15 @@ struct DmHmat {
 // k_degrees.cu
 cudaError_t dm_launch_pair_sqdist(const float *X, int64_t N, int d, uint64_t seed, double *out, int64_t m,
                                   cudaStream_t st);
-cudaError_t dm_launch_select_median(double *vals, int64_t m, double *result, cudaStream_t st);
+size_t dm_select_state_bytes();
+cudaError_t dm_launch_select_median(double *vals, int64_t m, void *state, double *result, cudaStream_t st);
 cudaError_t dm_launch_scale_points(const float *X, int64_t N, int d, double eps, float *Xs, cudaStream_t st);
 cudaError_t dm_launch_degree_pass(const float *Xs, int64_t N, int d, const float *wcol, double *out,
                                   cudaStream_t st);
+cudaError_t dm_launch_center_scale(const float *X, int64_t N, int d, double eps, float *Xs, float *nrm, float *nmax,
+                                   double *work, cudaStream_t st);
+cudaError_t dm_launch_degree_pass_centered(const float *Xs, const float *nrm, const float *nmax, int64_t N, int d,
+                                           const float *wcol, double *out, cudaStream_t st);
 cudaError_t dm_launch_finish_degrees(int64_t N, double alpha, const double *q, double *qa, float *qaf,
                                      cudaStream_t st);
 cudaError_t dm_launch_finish_scaling(int64_t N, const double *qa, double *dgsum, double *s, float *sf,
@@ -173,15 +196,19 @@ cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, i
 
 // k_skel.cu
 struct DmSkelWork {
-    float *A;      // per node slot rmax x cmax (column-major)
+    float *A;      // per node slot rmax x lda (row-major)
     float *R;      // per node slot max_rank x cmax
+    float *Q;      // per node slot max_rank x rmax
     int rmax;
+    int lda;       // cmax rounded up to 32
 };
+int dm_skel_max_candidates();
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank);
 cudaError_t dm_skeletonize(const float *Xs, const float *sf, int64_t N, int d, int L, const int32_t *perm,
                            double tol, int max_rank, int cmax, int ldp, uint64_t seed, int32_t *ranks,
                            int32_t *skel, float *P, DmSkelWork *w, cudaStream_t st);
 cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cudaStream_t st);
+cudaError_t dm_transpose_leaf_bases(const DmHmat &H, float *PT, cudaStream_t st);
 cudaError_t dm_permute_points(const float *Xs, const float *sf, const int32_t *perm, int64_t N, int d,
                               float *Xp, float *sp, cudaStream_t st);
 
@@ -210,6 +237,8 @@ struct DmLanczos {
     float *phi;       // N x kmax Ritz vectors in position order
     unsigned long long *best;  // kmax
     int *neg;         // kmax
+    unsigned *bar;    // grid-barrier counter of the fused step
+    int *err;         // set when a bounded device wait gave up
 };
 int dm_lanczos_kmax();
 cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st);

@@ -33,20 +33,96 @@ __global__ void sampled_pairs_kernel(const float *__restrict__ X, int64_t N, int
     out[c] = dm_sqdist64(X + i * d, X + j * d, d);
 }
 
-// median of m non-negative doubles (their bit patterns order like the values);
-// an even count averages the two middle values
-__global__ void __launch_bounds__(1024) median_kernel(const double *__restrict__ v, int64_t m,
-                                                      double *__restrict__ result) {
-    __shared__ unsigned hist[256];
-    auto key = [v](int64_t i) { return (uint64_t)__double_as_longlong(v[i]); };
-    int64_t below;
-    uint64_t hi = dm_cta_select(key, m, m / 2, hist, &below);
-    double r = __longlong_as_double((long long)hi);
-    if (m % 2 == 0) {
-        uint64_t lo = dm_cta_select(key, m, m / 2 - 1, hist, &below);
-        r = __dmul_rn(0.5, __dadd_rn(__longlong_as_double((long long)lo), r));
+// ---- exact order statistics of m non-negative doubles (their bit patterns order
+// like the values) by a multi-block most-significant-digit radix select:
+// 11-bit digits, one histogram pass over all values per digit.
+constexpr int kSelBits = 11;
+constexpr int kSelBins = 1 << kSelBits;
+
+struct SelectState {
+    unsigned long long prefix;  // digits found so far
+    unsigned long long mask;    // bits they cover
+    long long k;                // rank still to find among values matching prefix
+    unsigned hist[kSelBins];
+};
+
+__global__ void __launch_bounds__(512) select_hist_kernel(const double *__restrict__ v, int64_t m, int shift,
+                                                          SelectState *__restrict__ st) {
+    __shared__ unsigned h[kSelBins];
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix, mask = st->mask;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        bool act = false;
+        unsigned bin = 0;
+        if (i < m) {
+            const unsigned long long u = (unsigned long long)__double_as_longlong(v[i]);
+            if ((u & mask) == prefix) {
+                act = true;
+                bin = (unsigned)((u >> shift) & (kSelBins - 1));
+            }
+        }
+        const unsigned am = __ballot_sync(DM_FULL, act);
+        if (act) {
+            const unsigned peers = __match_any_sync(am, bin);
+            if (lane == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
+        }
     }
-    if (threadIdx.x == 0) *result = r;
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
+        if (h[b]) atomicAdd(&st->hist[b], h[b]);
+}
+
+// one block: pick the bin holding rank k, extend the prefix, clear the histogram
+__global__ void __launch_bounds__(1024) select_step_kernel(int shift, int bits, SelectState *__restrict__ st) {
+    __shared__ unsigned part[1024];
+    __shared__ int s_bin;
+    __shared__ long long s_before;
+    const int per = kSelBins / blockDim.x;  // bins per thread (2 with 1024 threads)
+    unsigned loc = 0;
+    for (int q = 0; q < per; ++q) loc += st->hist[threadIdx.x * per + q];
+    part[threadIdx.x] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long acc = 0, k = st->k;
+        int t = 0;
+        for (; t < (int)blockDim.x - 1; ++t) {
+            if (acc + part[t] > k) break;
+            acc += part[t];
+        }
+        int b = t * per;
+        for (; b < kSelBins - 1; ++b) {
+            if (acc + st->hist[b] > k) break;
+            acc += st->hist[b];
+        }
+        s_bin = b;
+        s_before = acc;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) st->hist[b] = 0;
+    if (threadIdx.x == 0) {
+        const unsigned long long digit_mask = ((1ull << bits) - 1ull) << shift;
+        st->prefix |= ((unsigned long long)s_bin << shift) & digit_mask;
+        st->mask |= digit_mask;
+        st->k -= s_before;
+    }
+}
+
+__global__ void select_init_kernel(SelectState *st, long long k) {
+    if (threadIdx.x == 0) {
+        st->prefix = 0ull;
+        st->mask = 0ull;
+        st->k = k;
+    }
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) st->hist[b] = 0;
+}
+
+// result = 0.5 (lo + hi) for an even count, else hi (matching the oracle's arithmetic)
+__global__ void median_finish_kernel(const SelectState *lo, const SelectState *hi, int even, double *result) {
+    const double h = __longlong_as_double((long long)hi->prefix);
+    *result = even ? __dmul_rn(0.5, __dadd_rn(__longlong_as_double((long long)lo->prefix), h)) : h;
 }
 
 __global__ void scale_points_kernel(const float *__restrict__ X, int64_t n, float c, float *__restrict__ Xs) {
@@ -111,6 +187,157 @@ __global__ void __launch_bounds__(kDegThreads) degree_pass_kernel(const float *_
     if (valid) atomicAdd(out + i, acc);
 }
 
+// d = 3 specialisation, two rows per thread in packed FP32x2 arithmetic.
+// With centred, pre-scaled coordinates u and n = |u|^2 the entry is
+//   2^-|u_i - u_j|^2 = 2^-n_i * 2^(2 u_i.u_j - n_j),
+// three FMAs and one MUFU ex2 per entry; the row factor 2^-n_i is applied once per
+// row in FP64. The form is used when every n <= kDotFormMaxNorm (device flag), so
+// the exponent stays below 2^8 in magnitude and its rounding below ~2e-6 relative
+// per entry; otherwise the direct difference form runs. The shared tile holds each
+// column duplicated as pairs so that 128-bit loads feed the packed operands.
+constexpr int kD3Threads = 128;
+constexpr int kD3Rows = 4 * kD3Threads;  // four rows per thread: two packed pairs
+constexpr float kDotFormMaxNorm = 8.f;
+
+struct Rows4 {
+    float2 x0[2], x1[2], x2[2];
+};
+
+__global__ void __launch_bounds__(kD3Threads) degree_pass_d3_kernel(const float *__restrict__ Xs,
+                                                                    const float *__restrict__ nrm,
+                                                                    const float *__restrict__ nmax, int64_t N,
+                                                                    const float *__restrict__ w,
+                                                                    double *__restrict__ out,
+                                                                    int64_t cols_per_split) {
+    __shared__ float4 ta[kDegTile];
+    __shared__ float4 tb[kDegTile];
+    __shared__ float2 tw[kDegTile];
+    const bool dot_form = nrm != nullptr && *nmax <= kDotFormMaxNorm;
+    const float sc = dot_form ? 2.f : 1.f;
+    // rows of this thread: base + threadIdx.x + {0, 1, 2, 3} * kD3Threads; pair p holds rows 2p, 2p+1
+    const int64_t row0 = blockIdx.x * (int64_t)kD3Rows + threadIdx.x;
+    float xr[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t rq = row0 + (int64_t)q * kD3Threads;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) xr[q][k] = rq < N ? sc * Xs[rq * 3 + k] : 0.f;
+    }
+    Rows4 X;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        X.x0[p] = make_float2(xr[2 * p][0], xr[2 * p + 1][0]);
+        X.x1[p] = make_float2(xr[2 * p][1], xr[2 * p + 1][1]);
+        X.x2[p] = make_float2(xr[2 * p][2], xr[2 * p + 1][2]);
+    }
+    const int64_t c0 = blockIdx.y * cols_per_split;
+    const int64_t c1 = (c0 + cols_per_split < N) ? c0 + cols_per_split : N;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t t0 = c0; t0 < c1; t0 += kDegTile) {
+        const int tn = (int)(c1 - t0 < kDegTile ? c1 - t0 : kDegTile);
+        __syncthreads();
+        for (int e = threadIdx.x; e < tn; e += kD3Threads) {
+            const int64_t j = t0 + e;
+            const float x = Xs[j * 3], y = Xs[j * 3 + 1], z = Xs[j * 3 + 2];
+            const float wj = w ? w[j] : 1.f;
+            if (dot_form) {
+                const float nj = -nrm[j];
+                ta[e] = make_float4(x, x, y, y);
+                tb[e] = make_float4(z, z, nj, nj);
+            } else {
+                ta[e] = make_float4(-x, -x, -y, -y);
+                tb[e] = make_float4(-z, -z, 0.f, 0.f);
+            }
+            tw[e] = make_float2(wj, wj);
+        }
+        __syncthreads();
+        float2 part0 = make_float2(0.f, 0.f), part1 = make_float2(0.f, 0.f);
+        if (dot_form) {
+#pragma unroll 2
+            for (int j = 0; j < tn; ++j) {
+                const float4 a = ta[j], b = tb[j];
+                const float2 wj = tw[j];
+                const float2 cx = make_float2(a.x, a.y), cy = make_float2(a.z, a.w), cz = make_float2(b.x, b.y);
+                const float2 cn = make_float2(b.z, b.w);
+                float2 g0 = __ffma2_rn(X.x2[0], cz, cn);
+                float2 g1 = __ffma2_rn(X.x2[1], cz, cn);
+                g0 = __ffma2_rn(X.x1[0], cy, g0);
+                g1 = __ffma2_rn(X.x1[1], cy, g1);
+                g0 = __ffma2_rn(X.x0[0], cx, g0);
+                g1 = __ffma2_rn(X.x0[1], cx, g1);
+                const float2 e0 = make_float2(dm_ex2(g0.x), dm_ex2(g0.y));
+                const float2 e1 = make_float2(dm_ex2(g1.x), dm_ex2(g1.y));
+                part0 = __ffma2_rn(e0, wj, part0);
+                part1 = __ffma2_rn(e1, wj, part1);
+            }
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < tn; ++j) {
+                const float4 a = ta[j], b = tb[j];
+                const float2 wj = tw[j];
+                const float2 cx = make_float2(a.x, a.y), cy = make_float2(a.z, a.w), cz = make_float2(b.x, b.y);
+                float2 d0 = __fadd2_rn(X.x0[0], cx), e0 = __fadd2_rn(X.x0[1], cx);
+                float2 d1 = __fadd2_rn(X.x1[0], cy), e1 = __fadd2_rn(X.x1[1], cy);
+                float2 d2 = __fadd2_rn(X.x2[0], cz), e2 = __fadd2_rn(X.x2[1], cz);
+                float2 r0 = __fmul2_rn(d0, d0), r1 = __fmul2_rn(e0, e0);
+                r0 = __ffma2_rn(d1, d1, r0);
+                r1 = __ffma2_rn(e1, e1, r1);
+                r0 = __ffma2_rn(d2, d2, r0);
+                r1 = __ffma2_rn(e2, e2, r1);
+                const float2 x0 = make_float2(dm_ex2(-r0.x), dm_ex2(-r0.y));
+                const float2 x1 = make_float2(dm_ex2(-r1.x), dm_ex2(-r1.y));
+                part0 = __ffma2_rn(x0, wj, part0);
+                part1 = __ffma2_rn(x1, wj, part1);
+            }
+        }
+        acc[0] += (double)part0.x;
+        acc[1] += (double)part0.y;
+        acc[2] += (double)part1.x;
+        acc[3] += (double)part1.y;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t rq = row0 + (int64_t)q * kD3Threads;
+        if (rq >= N) continue;
+        double v = acc[q];
+        if (dot_form) v *= (double)dm_ex2(-nrm[rq]);
+        atomicAdd(out + rq, v);
+    }
+}
+
+// column sums of X (FP64) for the centring
+__global__ void colsum_kernel(const float *__restrict__ X, int64_t N, int d, double *__restrict__ sums) {
+    double loc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int dd = d < 8 ? d : 8;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < dd; ++k) loc[k] += (double)X[i * d + k];
+    for (int k = 0; k < dd; ++k) {
+        const double v = dm_warp_sum_d(loc[k]);
+        if ((threadIdx.x & 31) == 0) atomicAdd(sums + k, v);
+    }
+}
+
+// u = (x - mean) * c, n = |u|^2 (FP32, k = 0..d-1), running max of n
+__global__ void center_scale_kernel(const float *__restrict__ X, int64_t N, int d, const double *__restrict__ sums,
+                                    float c, float *__restrict__ Xs, float *__restrict__ nrm,
+                                    unsigned *__restrict__ nmax_bits) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float n = 0.f;
+    if (i < N) {
+        for (int k = 0; k < d; ++k) {
+            const double mean = k < 8 ? sums[k] / (double)N : 0.0;
+            const float u = (float)((double)X[i * d + k] - mean) * c;
+            Xs[i * d + k] = u;
+            n = fmaf(u, u, n);
+        }
+        nrm[i] = n;
+    }
+    unsigned m = __float_as_uint(n);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(DM_FULL, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(nmax_bits, m);
+}
+
 __global__ void finish_degrees_kernel(int64_t N, double alpha, const double *__restrict__ q,
                                       double *__restrict__ qa, float *__restrict__ qaf) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -162,8 +389,28 @@ cudaError_t dm_launch_pair_sqdist(const float *X, int64_t N, int d, uint64_t see
     return cudaGetLastError();
 }
 
-cudaError_t dm_launch_select_median(double *vals, int64_t m, double *result, cudaStream_t st) {
-    median_kernel<<<1, 1024, 0, st>>>(vals, m, result);
+size_t dm_select_state_bytes() { return sizeof(SelectState); }
+
+// exact median of vals[0..m): two radix selects (ranks m/2-1 and m/2) into two
+// SelectState records at `state` (2 * dm_select_state_bytes() of device memory)
+cudaError_t dm_launch_select_median(double *vals, int64_t m, void *state, double *result, cudaStream_t st) {
+    SelectState *S = reinterpret_cast<SelectState *>(state);
+    const int even = (m % 2 == 0) ? 1 : 0;
+    const long long ranks[2] = {even ? m / 2 - 1 : m / 2, m / 2};
+    const int blocks = (int)((m + 511) / 512 < 2 * 152 ? (m + 511) / 512 : 2 * 152);
+    for (int r = 0; r < 2; ++r) {
+        select_init_kernel<<<1, 256, 0, st>>>(S + r, ranks[r]);
+        dm_count_launches(1);
+        for (int top = 64; top > 0; top -= kSelBits) {
+            const int bits = top >= kSelBits ? kSelBits : top;
+            const int shift = top - bits;
+            select_hist_kernel<<<blocks, 512, 0, st>>>(vals, m, shift, S + r);
+            dm_count_launches(1);
+            select_step_kernel<<<1, 1024, 0, st>>>(shift, bits, S + r);
+            dm_count_launches(1);
+        }
+    }
+    median_finish_kernel<<<1, 1, 0, st>>>(S, S + 1, even, result);
     dm_count_launches(1);
     return cudaGetLastError();
 }
@@ -177,10 +424,52 @@ cudaError_t dm_launch_scale_points(const float *X, int64_t N, int d, double eps,
     return cudaGetLastError();
 }
 
+// centred, pre-scaled points u = (x - mean) sqrt(log2(e)/eps), their squared norms and max
+// (`work` holds 8 doubles + 1 unsigned of device memory)
+cudaError_t dm_launch_center_scale(const float *X, int64_t N, int d, double eps, float *Xs, float *nrm, float *nmax,
+                                   double *work, cudaStream_t st) {
+    const double log2e = 1.4426950408889634;
+    const float c = (float)sqrt(log2e / eps);
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double) * 8, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(nmax, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    colsum_kernel<<<(unsigned)((N + 255) / 256 < 304 ? (N + 255) / 256 : 304), 256, 0, st>>>(X, N, d, work);
+    dm_count_launches(1);
+    center_scale_kernel<<<blocks_for(N, 256), 256, 0, st>>>(X, N, d, work, c, Xs, nrm,
+                                                            reinterpret_cast<unsigned *>(nmax));
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t dm_launch_degree_pass_centered(const float *Xs, const float *nrm, const float *nmax, int64_t N, int d,
+                                           const float *wcol, double *out, cudaStream_t st);
+
 cudaError_t dm_launch_degree_pass(const float *Xs, int64_t N, int d, const float *wcol, double *out,
                                   cudaStream_t st) {
+    return dm_launch_degree_pass_centered(Xs, nullptr, nullptr, N, d, wcol, out, st);
+}
+
+// out_i = sum_j W_ij w_j. nrm/nmax (may be NULL) enable the centred dot-product form at d = 3:
+// Xs must then be centred and pre-scaled with nrm its squared norms.
+cudaError_t dm_launch_degree_pass_centered(const float *Xs, const float *nrm, const float *nmax, int64_t N, int d,
+                                           const float *wcol, double *out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * N, st);
     if (e != cudaSuccess) return e;
+    if (d == 3) {
+        const int64_t rb = (N + kD3Rows - 1) / kD3Rows;
+        int64_t want = (12 * 152 + rb - 1) / rb;
+        const int64_t maxs = (N + 2 * kDegTile - 1) / (2 * kDegTile);
+        int64_t sp = want < 1 ? 1 : (want > maxs ? maxs : want);
+        if (sp < 1) sp = 1;
+        int64_t per = (N + sp - 1) / sp;
+        per = (per + kDegTile - 1) / kDegTile * kDegTile;
+        sp = (N + per - 1) / per;
+        degree_pass_d3_kernel<<<dim3((unsigned)rb, (unsigned)sp), kD3Threads, 0, st>>>(Xs, nrm, nmax, N, wcol, out,
+                                                                                       per);
+        dm_count_launches(1);
+        return cudaGetLastError();
+    }
     int64_t rowblocks = (N + kDegThreads - 1) / kDegThreads;
     // enough column splits to put ~16 CTAs on each of the 152 SMs, each split >= 2 tiles
     int64_t want = (16 * 152 + rowblocks - 1) / rowblocks;

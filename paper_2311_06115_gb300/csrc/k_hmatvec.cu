@@ -22,8 +22,10 @@
 namespace {
 
 constexpr int kHThreads = 256;
+constexpr int kDownThreads = 128;
+constexpr int kDownSplit = 2;  // blocks per leaf in the downward pass
 constexpr int kHWarps = kHThreads / 32;
-constexpr int kCachedRowsPerItem = 32;   // rows of one leaf block per near item (cached)
+constexpr int kCachedItemsPerLeaf = 4;  // near items (row ranges) per leaf block (cached)
 
 __device__ __forceinline__ float4 ldcs4(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
 
@@ -61,8 +63,67 @@ __device__ __forceinline__ void gemv_rows(const float *__restrict__ P, int ldp, 
     }
 }
 
+// out[t] = P[t, 0:c] . v for t < s, P in global memory (rows zero padded to a multiple of 4):
+// a warp takes two rows at a time and issues all 16-byte loads of both rows (up to 512
+// columns) before any arithmetic, so one memory round trip serves a pair of rows.
+__device__ __forceinline__ void gemv2_rows_global(const float *__restrict__ P, int ldp, int s, int c, const float *v,
+                                                  float *out_global) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c4 = (c + 3) >> 2;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+    for (int t = 2 * warp; t < s; t += 2 * kHWarps) {
+        const bool two = t + 1 < s;
+        const float4 *ra = reinterpret_cast<const float4 *>(P + (size_t)t * ldp);
+        const float4 *rb = reinterpret_cast<const float4 *>(P + (size_t)(two ? t + 1 : t) * ldp);
+        float acc_a = 0.f, acc_b = 0.f;
+        for (int base = 0; base < c4; base += 128) {
+            float4 ka[4], kb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = base + lane + 32 * u;
+                ka[u] = q < c4 ? __ldg(ra + q) : zero;
+                kb[u] = (two && q < c4) ? __ldg(rb + q) : zero;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = base + lane + 32 * u;
+                const float4 xv = q < c4 ? v4[q] : zero;
+                acc_a = fmaf(ka[u].x, xv.x, fmaf(ka[u].y, xv.y, fmaf(ka[u].z, xv.z, fmaf(ka[u].w, xv.w, acc_a))));
+                acc_b = fmaf(kb[u].x, xv.x, fmaf(kb[u].y, xv.y, fmaf(kb[u].z, xv.z, fmaf(kb[u].w, xv.w, acc_b))));
+            }
+        }
+        acc_a = dm_warp_sum(acc_a);
+        acc_b = dm_warp_sum(acc_b);
+        if (lane == 0) {
+            out_global[t] = acc_a;
+            if (two) out_global[t + 1] = acc_b;
+        }
+    }
+}
+
+// out[t] = P[t, 0:c] . v for t < s from a shared-memory copy of P with row stride ld4 (multiple of 4)
+__device__ __forceinline__ void gemv_rows_smem(const float *Ps, int ld4, int s, int c, const float *v, float *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c4 = (c + 3) >> 2;
+    for (int t = warp; t < s; t += kHWarps) {
+        const float4 *row = reinterpret_cast<const float4 *>(Ps + (size_t)t * ld4);
+        float acc = 0.f;
+        for (int q = lane; q < c4; q += 32) {
+            const float4 p = row[q];
+            const float4 xv = *reinterpret_cast<const float4 *>(v + 4 * q);
+            acc = fmaf(p.x, xv.x, acc);
+            acc = fmaf(p.y, xv.y, acc);
+            acc = fmaf(p.z, xv.z, acc);
+            acc = fmaf(p.w, xv.w, acc);
+        }
+        acc = dm_warp_sum(acc);
+        if (lane == 0) out[t] = acc;
+    }
+}
+
 __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const float *__restrict__ x, int permuted,
-                                                            int near_mode, int near_rows) {
+                                                            int near_mode, int near_rows, int climb_smem) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_go;
@@ -77,31 +138,50 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const floa
         int64_t st, sz;
         dm_node_range(H.N, node, &st, &sz);
         const int m = (int)sz, m4 = (m + 3) & ~3;
+        const int RH = H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
         float *sx = sm;                          // m4max
-        float *sw = sm + m4max;                  // 2 * max_rank (+pad): children weights
+        float *sw = sm + m4max;                  // C4: children weights
+        float *Bs = sw + C4;                     // RH x RH4: parent's K(S_l, S_r)
+        float *Ps = Bs + RH * RH4;               // RH x C4: parent's P
         stage_x(H, x, permuted != 0, st, m, m4, sx);
         __syncthreads();
         const int s_leaf = H.ranks[node];
-        gemv_rows(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, s_leaf, m, sx,
-                  H.what + (size_t)node * H.max_rank, nullptr);
+        gemv2_rows_global(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, s_leaf, m, sx,
+                          H.what + (size_t)node * H.max_rank);
         if (H.L == 0) return;
         for (;;) {
+            const int parent = (node - 1) >> 1;
+            const int l = 2 * parent + 1, r = 2 * parent + 2;
+            const int sl = H.ranks[l], sr = H.ranks[r], sp = parent > 0 ? H.ranks[parent] : 0;
+            const int c = sl + sr, c4 = (c + 3) & ~3;
+            if (climb_smem) {
+                // fetch the parent's operands now (asynchronous copies): they travel while the
+                // fence and the arrival atomic complete
+                const float *Bn = H.B + (size_t)parent * H.max_rank * H.max_rank;
+                for (int e = threadIdx.x; e < sl * sr; e += blockDim.x) {
+                    const int ia = e / sr, ib = e % sr;
+                    dm_cp_async4(Bs + ia * RH4 + ib, Bn + e);
+                }
+                const float *Pn = H.P + (size_t)parent * H.max_rank * H.ldp;
+                const int q4 = c4 >> 2;
+                for (int e = threadIdx.x; e < sp * q4; e += blockDim.x) {
+                    const int t = e / q4, q = e % q4;
+                    dm_cp_async16(Ps + t * C4 + 4 * q, Pn + (size_t)t * H.ldp + 4 * q);  // rows zero padded to ldp
+                }
+            }
             // publish this node's weights, then count the arrival at the parent
             __threadfence();
             __syncthreads();
-            const int parent = (node - 1) >> 1;
             if (threadIdx.x == 0) {
                 const unsigned old = atomicAdd(H.cnt + parent, 1u);
                 s_go = (old == 1u);
                 if (old == 1u) H.cnt[parent] = 0u;  // both children arrived: reset for the next call
                 __threadfence();
             }
+            if (climb_smem) dm_cp_async_wait_all();  // own copies land before the block exits or reads them
             __syncthreads();
             if (!s_go) return;
             node = parent;
-            const int l = 2 * node + 1, r = 2 * node + 2;
-            const int sl = H.ranks[l], sr = H.ranks[r];
-            const int c = sl + sr, c4 = (c + 3) & ~3;
             for (int j = threadIdx.x; j < c4; j += blockDim.x) {
                 float v = 0.f;
                 if (j < sl) v = __ldcg(H.what + (size_t)l * H.max_rank + j);
@@ -110,22 +190,39 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const floa
             }
             __syncthreads();
             // S2S: u_l = B w_r (warp per row of B), u_r = B^T w_l (thread per column of B)
-            const float *Bn = H.B + (size_t)node * H.max_rank * H.max_rank;
-            for (int a = warp; a < sl; a += kHWarps) {
-                float acc = 0.f;
-                for (int b = lane; b < sr; b += 32) acc = fmaf(__ldg(Bn + (size_t)a * sr + b), sw[sl + b], acc);
-                acc = dm_warp_sum(acc);
-                if (lane == 0) H.uhat[(size_t)l * H.max_rank + a] = acc;
-            }
-            for (int b = threadIdx.x; b < sr; b += blockDim.x) {
-                float acc = 0.f;
-                for (int a = 0; a < sl; ++a) acc = fmaf(__ldg(Bn + (size_t)a * sr + b), sw[a], acc);
-                H.uhat[(size_t)r * H.max_rank + b] = acc;
+            if (climb_smem) {
+                for (int a2 = warp; a2 < sl; a2 += kHWarps) {
+                    float acc = 0.f;
+                    for (int b2 = lane; b2 < sr; b2 += 32) acc = fmaf(Bs[a2 * RH4 + b2], sw[sl + b2], acc);
+                    acc = dm_warp_sum(acc);
+                    if (lane == 0) H.uhat[(size_t)l * H.max_rank + a2] = acc;
+                }
+                for (int b2 = threadIdx.x; b2 < sr; b2 += blockDim.x) {
+                    float acc = 0.f;
+                    for (int a2 = 0; a2 < sl; ++a2) acc = fmaf(Bs[a2 * RH4 + b2], sw[a2], acc);
+                    H.uhat[(size_t)r * H.max_rank + b2] = acc;
+                }
+            } else {
+                const float *Bn = H.B + (size_t)node * H.max_rank * H.max_rank;
+                for (int a2 = warp; a2 < sl; a2 += kHWarps) {
+                    float acc = 0.f;
+                    for (int b2 = lane; b2 < sr; b2 += 32) acc = fmaf(__ldg(Bn + (size_t)a2 * sr + b2), sw[sl + b2], acc);
+                    acc = dm_warp_sum(acc);
+                    if (lane == 0) H.uhat[(size_t)l * H.max_rank + a2] = acc;
+                }
+                for (int b2 = threadIdx.x; b2 < sr; b2 += blockDim.x) {
+                    float acc = 0.f;
+                    for (int a2 = 0; a2 < sl; ++a2) acc = fmaf(__ldg(Bn + (size_t)a2 * sr + b2), sw[a2], acc);
+                    H.uhat[(size_t)r * H.max_rank + b2] = acc;
+                }
             }
             if (node == 0) return;
             // N2S of the internal node
-            gemv_rows(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, H.ranks[node], c, sw,
-                      H.what + (size_t)node * H.max_rank, nullptr);
+            if (climb_smem) gemv_rows_smem(Ps, C4, sp, c, sw, H.what + (size_t)node * H.max_rank);
+            else
+                gemv_rows(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, sp, c, sw,
+                          H.what + (size_t)node * H.max_rank, nullptr);
+            __syncthreads();  // Bs/Ps are refilled for the next parent
         }
     }
 
@@ -145,24 +242,36 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const floa
         __syncthreads();
         const float *blk = H.Knear + (size_t)leaf * H.leaf_max * H.ldk;
         const int m4q = m4 >> 2;
-        // two rows per warp pass for memory-level parallelism
+        const float4 *sx4 = reinterpret_cast<const float4 *>(sx);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        // two rows per warp pass; each lane issues all of its 16-byte loads of both rows
+        // (up to 4 per row, rows of up to 512 floats) before any arithmetic
         for (int i = r0 + 2 * warp; i < r1; i += 2 * kHWarps) {
             const bool two = (i + 1) < r1;
-            const float *ra = blk + (size_t)i * H.ldk;
-            const float *rb = blk + (size_t)(two ? i + 1 : i) * H.ldk;
+            const float4 *ra = reinterpret_cast<const float4 *>(blk + (size_t)i * H.ldk);
+            const float4 *rb = reinterpret_cast<const float4 *>(blk + (size_t)(two ? i + 1 : i) * H.ldk);
             float acc_a = 0.f, acc_b = 0.f;
-            for (int q = lane; q < m4q; q += 32) {
-                const float4 ka = ldcs4(ra + 4 * q);
-                const float4 kb = ldcs4(rb + 4 * q);
-                const float4 xv = *reinterpret_cast<const float4 *>(sx + 4 * q);
-                acc_a = fmaf(ka.x, xv.x, acc_a);
-                acc_a = fmaf(ka.y, xv.y, acc_a);
-                acc_a = fmaf(ka.z, xv.z, acc_a);
-                acc_a = fmaf(ka.w, xv.w, acc_a);
-                acc_b = fmaf(kb.x, xv.x, acc_b);
-                acc_b = fmaf(kb.y, xv.y, acc_b);
-                acc_b = fmaf(kb.z, xv.z, acc_b);
-                acc_b = fmaf(kb.w, xv.w, acc_b);
+            for (int base = 0; base < m4q; base += 128) {
+                float4 ka[4], kb[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int q = base + lane + 32 * t;
+                    ka[t] = q < m4q ? __ldcs(ra + q) : zero;
+                    kb[t] = (two && q < m4q) ? __ldcs(rb + q) : zero;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int q = base + lane + 32 * t;
+                    const float4 xv = q < m4q ? sx4[q] : zero;
+                    acc_a = fmaf(ka[t].x, xv.x, acc_a);
+                    acc_a = fmaf(ka[t].y, xv.y, acc_a);
+                    acc_a = fmaf(ka[t].z, xv.z, acc_a);
+                    acc_a = fmaf(ka[t].w, xv.w, acc_a);
+                    acc_b = fmaf(kb[t].x, xv.x, acc_b);
+                    acc_b = fmaf(kb[t].y, xv.y, acc_b);
+                    acc_b = fmaf(kb[t].z, xv.z, acc_b);
+                    acc_b = fmaf(kb[t].w, xv.w, acc_b);
+                }
             }
             acc_a = dm_warp_sum(acc_a);
             acc_b = dm_warp_sum(acc_b);
@@ -207,38 +316,89 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const floa
     }
 }
 
-__global__ void __launch_bounds__(kHThreads) down_kernel(DmHmat H, float *__restrict__ y, int permuted) {
+// Downward pass for one leaf. The ancestor chain (S2S parts u of the ancestors at
+// levels 2..L and, per step, the slice of the parent's P that maps to the child) is
+// fetched into shared memory in one batch of independent loads when it fits
+// (`chain_in_smem`), then combined top-down: t = P_parent(:, child)^T t + u_child.
+// The leaf's own S2N reads the point-major copy PT: one contiguous row per point.
+__global__ void __launch_bounds__(kDownThreads) down_kernel(DmHmat H, float *__restrict__ y, int permuted,
+                                                             int chain_in_smem) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
-    float *ta = sm, *tb = sm + H.max_rank;
-    const int leaf = blockIdx.x;
+    // kDownSplit blocks per leaf, each handling a contiguous quarter of its points
+    const int leaf = blockIdx.x / kDownSplit, part = blockIdx.x % kDownSplit;
     const int nleaves = 1 << H.L;
     const int node_leaf = nleaves - 1 + leaf;
     int64_t st, sz;
     dm_node_range(H.N, node_leaf, &st, &sz);
-    const int m = (int)sz;
+    const int per = ((int)sz + kDownSplit - 1) / kDownSplit;
+    const int i_lo = part * per, i_hi = min((int)sz, i_lo + per);
+    if (i_lo >= i_hi) return;
     if (H.L == 0) {
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        for (int i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
             const float v = H.ynear[st + i];
             if (permuted) y[st + i] = v;
             else y[H.perm[st + i]] = v;
         }
         return;
     }
-    // ancestor at level 1 .. L of this leaf: node(l) = ((node_leaf + 1) >> (L - l)) - 1
+    const int R = H.max_rank, RH = H.rank_hi, RH4 = (RH + 3) & ~3;
+    float *ta = sm, *tb = sm + RH4;
+    float *chain = sm + 2 * RH4;  // per level l >= 2: u_l (RH4) then the P slice (RH x RH4)
+    const int stride = RH4 + RH * RH4;
+    if (chain_in_smem) {
+        for (int lvl = 2; lvl <= H.L; ++lvl) {
+            const int parent = ((node_leaf + 1) >> (H.L - lvl + 1)) - 1;
+            const int child = ((node_leaf + 1) >> (H.L - lvl)) - 1;
+            const int off = (child == 2 * parent + 2) ? H.ranks[2 * parent + 1] : 0;
+            const int sp = H.ranks[parent], sc = H.ranks[child];
+            float *u = chain + (size_t)(lvl - 2) * stride;
+            float *Ps = u + RH4;
+            const float *Pn = H.P + (size_t)parent * R * H.ldp + off;
+            const int tot = sp * sc;
+            for (int e = threadIdx.x; e < tot; e += blockDim.x)
+                dm_cp_async4(Ps + (e / sc) * RH4 + (e % sc), Pn + (size_t)(e / sc) * H.ldp + (e % sc));
+            for (int e = threadIdx.x; e < sc; e += blockDim.x) dm_cp_async4(u + e, H.uhat + (size_t)child * R + e);
+        }
+        dm_cp_async_wait_all();
+    }
     int node = ((node_leaf + 1) >> (H.L - 1)) - 1;
     int s = H.ranks[node];
-    for (int j = threadIdx.x; j < s; j += blockDim.x) ta[j] = H.uhat[(size_t)node * H.max_rank + j];
+    for (int j = threadIdx.x; j < RH4; j += blockDim.x) ta[j] = j < s ? H.uhat[(size_t)node * R + j] : 0.f;
     __syncthreads();
     for (int lvl = 2; lvl <= H.L; ++lvl) {
         const int child = ((node_leaf + 1) >> (H.L - lvl)) - 1;
-        const int off = (child == 2 * node + 2) ? H.ranks[2 * node + 1] : 0;
         const int sc = H.ranks[child];
-        const float *Pn = H.P + (size_t)node * H.max_rank * H.ldp;
-        for (int j = threadIdx.x; j < sc; j += blockDim.x) {
-            float acc = H.uhat[(size_t)child * H.max_rank + j];
-            for (int t = 0; t < s; ++t) acc = fmaf(__ldg(Pn + (size_t)t * H.ldp + off + j), ta[t], acc);
-            tb[j] = acc;
+        if (chain_in_smem) {
+            const float *u = chain + (size_t)(lvl - 2) * stride;
+            const float *Ps = u + RH4;
+            for (int j = threadIdx.x; j < RH4; j += blockDim.x) {
+                float acc = 0.f;
+                if (j < sc) {
+                    float a0 = u[j], a1 = 0.f, a2 = 0.f, a3 = 0.f;  // four independent chains
+                    int t = 0;
+                    for (; t + 4 <= s; t += 4) {
+                        a0 = fmaf(Ps[t * RH4 + j], ta[t], a0);
+                        a1 = fmaf(Ps[(t + 1) * RH4 + j], ta[t + 1], a1);
+                        a2 = fmaf(Ps[(t + 2) * RH4 + j], ta[t + 2], a2);
+                        a3 = fmaf(Ps[(t + 3) * RH4 + j], ta[t + 3], a3);
+                    }
+                    for (; t < s; ++t) a0 = fmaf(Ps[t * RH4 + j], ta[t], a0);
+                    acc = (a0 + a1) + (a2 + a3);
+                }
+                tb[j] = acc;
+            }
+        } else {
+            const int off = (child == 2 * node + 2) ? H.ranks[2 * node + 1] : 0;
+            const float *Pn = H.P + (size_t)node * R * H.ldp;
+            for (int j = threadIdx.x; j < RH4; j += blockDim.x) {
+                float acc = 0.f;
+                if (j < sc) {
+                    acc = H.uhat[(size_t)child * R + j];
+                    for (int t = 0; t < s; ++t) acc = fmaf(__ldg(Pn + (size_t)t * H.ldp + off + j), ta[t], acc);
+                }
+                tb[j] = acc;
+            }
         }
         __syncthreads();
         float *tmp = ta;
@@ -247,11 +407,31 @@ __global__ void __launch_bounds__(kHThreads) down_kernel(DmHmat H, float *__rest
         node = child;
         s = sc;
     }
-    // leaf S2N and output
-    const float *Pl = H.P + (size_t)node_leaf * H.max_rank * H.ldp;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        float acc = H.ynear[st + i];
-        for (int t = 0; t < s; ++t) acc = fmaf(__ldg(Pl + (size_t)t * H.ldp + i), ta[t], acc);
+    // leaf S2N: y_i = y_near_i + PT[i, :] . t, PT rows zero padded to ldt (>= rank, multiple of 4)
+    const float4 *PT = reinterpret_cast<const float4 *>(H.PT + (size_t)leaf * H.leaf_max * H.ldt);
+    const int q4 = H.ldt >> 2;
+    const float4 *t4 = reinterpret_cast<const float4 *>(ta);
+    for (int i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
+        const float4 *row = PT + (size_t)i * q4;
+        float a0 = H.ynear[st + i], a1 = 0.f;
+        // batches of 8 independent 16-byte loads (ranks up to 32 in one round trip)
+        for (int q0 = 0; q0 < q4; q0 += 8) {
+            float4 p[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) p[u] = (q0 + u < q4) ? __ldg(row + q0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                if (q0 + u < q4) {
+                    const float4 v0 = t4[q0 + u];
+                    a0 = fmaf(p[u].x, v0.x, fmaf(p[u].y, v0.y, fmaf(p[u].z, v0.z, fmaf(p[u].w, v0.w, a0))));
+                }
+                if (q0 + u + 1 < q4) {
+                    const float4 v1 = t4[q0 + u + 1];
+                    a1 = fmaf(p[u + 1].x, v1.x, fmaf(p[u + 1].y, v1.y, fmaf(p[u + 1].z, v1.z, fmaf(p[u + 1].w, v1.w, a1))));
+                }
+            }
+        }
+        const float acc = a0 + a1;
         if (permuted) y[st + i] = acc;
         else y[H.perm[st + i]] = acc;
     }
@@ -260,7 +440,7 @@ __global__ void __launch_bounds__(kHThreads) down_kernel(DmHmat H, float *__rest
 }  // namespace
 
 int dm_near_rows(int near_mode, int leaf_max) {
-    if (near_mode == DM_NEAR_CACHED) return kCachedRowsPerItem;
+    if (near_mode == DM_NEAR_CACHED) return (leaf_max + kCachedItemsPerLeaf - 1) / kCachedItemsPerLeaf;
     const int chunks = (leaf_max + kHThreads - 1) / kHThreads;
     return (leaf_max + chunks - 1) / chunks;
 }
@@ -270,9 +450,13 @@ cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y,
     const int rows = dm_near_rows(near_mode, H.leaf_max);
     const int per_leaf = (H.leaf_max + rows - 1) / rows;
     const int m4max = (H.leaf_max + 3) & ~3;
-    size_t smem1 = sizeof(float) * (size_t)(m4max + 2 * H.max_rank + 4);
+    const size_t RH = (size_t)H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
+    // up items: staged x, children weights, and (when small enough) the parent's B and P
+    const size_t climb_bytes = sizeof(float) * (RH * RH4 + RH * C4);
+    const int climb_smem = climb_bytes <= 96 * 1024 ? 1 : 0;
+    size_t smem1 = sizeof(float) * ((size_t)m4max + C4 + 2 * (size_t)H.max_rank + 4) + (climb_smem ? climb_bytes : 0);
     if (near_mode != DM_NEAR_CACHED) {
-        size_t s2 = sizeof(float) * (size_t)(m4max + H.leaf_max * H.d);
+        const size_t s2 = sizeof(float) * (size_t)(m4max + H.leaf_max * H.d);
         if (s2 > smem1) smem1 = s2;
     }
     static thread_local size_t configured = 0;
@@ -281,11 +465,22 @@ cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y,
         if (e != cudaSuccess) return e;
         configured = smem1;
     }
-    near_up_kernel<<<nleaves + nleaves * per_leaf, kHThreads, smem1, st>>>(H, x, permuted ? 1 : 0, near_mode, rows);
+    near_up_kernel<<<nleaves + nleaves * per_leaf, kHThreads, smem1, st>>>(H, x, permuted ? 1 : 0, near_mode, rows,
+                                                                            climb_smem);
     dm_count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    down_kernel<<<nleaves, kHThreads, sizeof(float) * 2 * H.max_rank, st>>>(H, y, permuted ? 1 : 0);
+    // the ancestor chain fits in shared memory for the usual ranks; otherwise read it from L2
+    const size_t chain = sizeof(float) * (2 * RH4 + (size_t)(H.L > 1 ? H.L - 1 : 0) * (RH4 + RH * RH4));
+    const int in_smem = chain <= 160 * 1024 ? 1 : 0;
+    const size_t smem2 = in_smem ? chain : sizeof(float) * 2 * RH4;
+    static thread_local size_t configured2 = 0;
+    if (smem2 > 48 * 1024 && smem2 > configured2) {
+        cudaError_t e2 = cudaFuncSetAttribute(down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        if (e2 != cudaSuccess) return e2;
+        configured2 = smem2;
+    }
+    down_kernel<<<nleaves * kDownSplit, kDownThreads, smem2, st>>>(H, y, permuted ? 1 : 0, in_smem);
     dm_count_launches(1);
     return cudaGetLastError();
 }

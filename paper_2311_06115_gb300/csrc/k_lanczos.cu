@@ -16,7 +16,6 @@
 
 namespace {
 
-constexpr int kProjRows = 2048;  // rows per projection block
 constexpr int kKMax = 32;        // max eigenpairs returned per solve
 
 __global__ void start_vector_kernel(const int32_t *__restrict__ perm, int64_t N, uint64_t key, float *__restrict__ z,
@@ -38,66 +37,141 @@ __global__ void normalize_kernel(const float *__restrict__ z, int64_t N, const d
     if (i < N) vout[i] = (float)((double)z[i] / sqrt(*nrm2));
 }
 
-// h[c] += sum_rows V[c][row] z[row] for c <= j; grid (row blocks, column groups of 8)
-__global__ void __launch_bounds__(256) proj_kernel(const float *__restrict__ V, int64_t ldv, int ncols,
-                                                   const float *__restrict__ z, int64_t N, double *__restrict__ h) {
-    __shared__ float4 sz4[kProjRows / 4];
-    const int64_t r0 = (int64_t)blockIdx.x * kProjRows;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nq = (int)(((N - r0) < kProjRows ? (N - r0) : kProjRows) + 3) / 4;
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) sz4[q] = *reinterpret_cast<const float4 *>(z + r0 + 4 * q);
-    __syncthreads();
-    const int c = blockIdx.y * 8 + warp;
-    if (c >= ncols) return;
-    const float4 *col = reinterpret_cast<const float4 *>(V + (size_t)c * ldv + r0);
-    float acc = 0.f;
-#pragma unroll 4
-    for (int q = lane; q < nq; q += 32) {
-        const float4 a = __ldcs(col + q);
-        const float4 b = sz4[q];
-        acc = fmaf(a.x, b.x, acc);
-        acc = fmaf(a.y, b.y, acc);
-        acc = fmaf(a.z, b.z, acc);
-        acc = fmaf(a.w, b.w, acc);
-    }
-    acc = dm_warp_sum(acc);
-    if (lane == 0) atomicAdd(h + c, (double)acc);
+
+
+// ---- one fused Lanczos orthogonalisation step (cooperative launch) --------------
+// Phases (each block owns a contiguous range of rows):
+//   1 h0 = V^T z        2 z -= V h0        3 h1 = V^T z        4 z -= V h1, |z|^2
+//   5 alpha_j = h0_j + h1_j, beta_j = |z|, V[:, j+1] = z / beta_j
+// separated by a grid barrier. The barrier spins with a bounded iteration count;
+// on exhaustion it raises *err and every block returns (the host reports a timeout).
+constexpr int kStepThreads = 256;
+constexpr long long kBarrierSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// z -= V[:, 0:ncols] h; optionally accumulate |z|^2 (FP64) after the update
-__global__ void __launch_bounds__(256) update_kernel(const float *__restrict__ V, int64_t ldv, int ncols,
-                                                     float *__restrict__ z, int64_t N, const double *__restrict__ h,
-                                                     double *__restrict__ nrm2) {
-    extern __shared__ float sh[];
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) sh[c] = (float)h[c];
+// returns false when the barrier timed out (in this or another block)
+__device__ bool grid_barrier(unsigned *ctr, unsigned target, int *err) {
+    __shared__ int s_ok;
     __syncthreads();
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    float v = 0.f;
-    if (i < N) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int c = 0;
-        for (; c + 4 <= ncols; c += 4) {
-            a0 = fmaf(__ldcs(V + (size_t)c * ldv + i), sh[c], a0);
-            a1 = fmaf(__ldcs(V + (size_t)(c + 1) * ldv + i), sh[c + 1], a1);
-            a2 = fmaf(__ldcs(V + (size_t)(c + 2) * ldv + i), sh[c + 2], a2);
-            a3 = fmaf(__ldcs(V + (size_t)(c + 3) * ldv + i), sh[c + 3], a3);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        int ok = 1;
+        long long spins = 0;
+        while (ld_acquire_gpu(ctr) < target) {
+            if (++spins > kBarrierSpinLimit || *((volatile int *)err) != 0) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(64);
         }
-        for (; c < ncols; ++c) a0 = fmaf(__ldcs(V + (size_t)c * ldv + i), sh[c], a0);
-        v = z[i] - ((a0 + a1) + (a2 + a3));
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// partial V^T z over this block's rows: each thread owns up to two rows and loads all
+// columns for them back to back; per-column warp sums meet in shared memory and one
+// FP64 atomic per column and block goes to h. V goes through L2 (read four times a step).
+__device__ void block_project(const float *V, int64_t ldv, int ncols, const float *z, int64_t r0, int64_t r1,
+                              double *h, float *acc_s) {
+    const int lane = threadIdx.x & 31;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) acc_s[c] = 0.f;
+    __syncthreads();
+    for (int c0 = 0; c0 < ncols; c0 += 8) {
+        float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const float zi = z[i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < ncols) p[u] = fmaf(__ldcg(V + (size_t)(c0 + u) * ldv + i), zi, p[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float w = dm_warp_sum(p[u]);
+            if (lane == 0 && c0 + u < ncols) atomicAdd(acc_s + c0 + u, w);
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) atomicAdd(h + c, (double)acc_s[c]);
+}
+
+// z -= V h over this block's rows (thread per row, eight columns in flight);
+// optional |z|^2 into nrm2 (FP64)
+__device__ void block_update(const float *V, int64_t ldv, int ncols, float *z, int64_t r0, int64_t r1,
+                             const double *h, float *sh, double *nrm2) {
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) sh[c] = (float)__ldcg(h + c);
+    __syncthreads();
+    float ss = 0.f;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c0 = 0; c0 < ncols; c0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (c0 + u < ncols) ? __ldcg(V + (size_t)(c0 + u) * ldv + i) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < ncols) a[u] = fmaf(v[u], sh[c0 + u], a[u]);
+        }
+        const float v = z[i] - (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
         z[i] = v;
+        ss = fmaf(v, v, ss);
     }
     if (nrm2) {
-        float ss = dm_warp_sum(v * v);
+        ss = dm_warp_sum(ss);
         if ((threadIdx.x & 31) == 0) atomicAdd(nrm2, (double)ss);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, int64_t ldv, int64_t N, int j,
+                                                                    float *z, double *h0, double *h1, double *nrm2,
+                                                                    double *alpha, double *beta, int m_max,
+                                                                    unsigned *bar, int *err) {
+    extern __shared__ float sh[];  // (m_max + 1) coefficients, then (m_max + 1) partial sums
+    float *acc_s = sh + (m_max + 1);
+    const int ncols = j + 1;
+    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * per, r1 = (r0 + per < N) ? r0 + per : N;
+    const unsigned G = gridDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nrm2 = 0.0;
+    block_project(V, ldv, ncols, z, r0, r1, h0, acc_s);
+    if (!grid_barrier(bar, G, err)) return;
+    block_update(V, ldv, ncols, z, r0, r1, h0, sh, nullptr);
+    if (!grid_barrier(bar, 2 * G, err)) return;
+    block_project(V, ldv, ncols, z, r0, r1, h1, acc_s);
+    if (!grid_barrier(bar, 3 * G, err)) return;
+    block_update(V, ldv, ncols, z, r0, r1, h1, sh, nrm2);
+    if (!grid_barrier(bar, 4 * G, err)) return;
+    const double b = sqrt(__ldcg(nrm2));
+    if (j + 1 <= m_max) {
+        float *vn = V + (size_t)(j + 1) * ldv;
+        const float inv = (float)(1.0 / b);
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) vn[i] = z[i] * inv;
+    }
+    // block 0 records the coefficients, then clears the projection accumulators for the
+    // next step (no other block reads them past barrier 4)
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            alpha[j] = __ldcg(h0 + j) + __ldcg(h1 + j);
+            beta[j] = b;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncols + 1; c += blockDim.x) {
+            h0[c] = 0.0;
+            h1[c] = 0.0;
+        }
     }
 }
 
-// alpha_j = h0_j + h1_j ; beta_j = sqrt(nrm2)
-__global__ void coeff_kernel(int j, const double *__restrict__ h0, const double *__restrict__ h1,
-                             const double *__restrict__ nrm2, double *__restrict__ alpha, double *__restrict__ beta) {
-    alpha[j] = h0[j] + h1[j];
-    beta[j] = sqrt(*nrm2);
-}
 
 // ---- Sturm count of T_m - x I by the division-free characteristic-polynomial
 // recurrence p_i = (alpha_i - x) p_{i-1} - beta_{i-1}^2 p_{i-2} with exact power-of-two
@@ -399,31 +473,34 @@ cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, 
     return cudaGetLastError();
 }
 
-// After Lz.z = A v_j: two Gram-Schmidt passes against V[:, 0..j], alpha_j, beta_j and V[:, j+1].
+// After Lz.z = A v_j: two Gram-Schmidt passes against V[:, 0..j], alpha_j, beta_j and
+// V[:, j+1], as one cooperative launch (grid = co-resident blocks on every SM).
 cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st) {
-    const int ncols = j + 1;
     double *h0 = Lz.h, *h1 = Lz.h + (Lz.m_max + 1);
-    cudaError_t e = cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (Lz.m_max + 1), st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(Lz.nrm2, 0, sizeof(double), st);
-    if (e != cudaSuccess) return e;
-    const dim3 pgrid(nblk(Lz.N, kProjRows), nblk(ncols, 8));
-    const size_t ush = sizeof(float) * (size_t)ncols;
-    proj_kernel<<<pgrid, 256, 0, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h0);
-    dm_count_launches(1);
-    update_kernel<<<nblk(Lz.N, 256), 256, ush, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h0, nullptr);
-    dm_count_launches(1);
-    proj_kernel<<<pgrid, 256, 0, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h1);
-    dm_count_launches(1);
-    update_kernel<<<nblk(Lz.N, 256), 256, ush, st>>>(Lz.V, Lz.ldv, ncols, Lz.z, Lz.N, h1, Lz.nrm2);
-    dm_count_launches(1);
-    coeff_kernel<<<1, 1, 0, st>>>(j, h0, h1, Lz.nrm2, Lz.alpha, Lz.beta);
-    dm_count_launches(1);
-    if (j + 1 <= Lz.m_max) {
-        normalize_kernel<<<nblk(Lz.N, 256), 256, 0, st>>>(Lz.z, Lz.N, Lz.nrm2, Lz.V + (size_t)(j + 1) * Lz.ldv);
-        dm_count_launches(1);
+    if (j == 0) {
+        cudaError_t e0 = cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (Lz.m_max + 1), st);
+        if (e0 != cudaSuccess) return e0;
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(Lz.bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    static thread_local int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_step_kernel, kStepThreads,
+                                                          sizeof(float) * 2 * (Lz.m_max + 1));
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+        grid = sms * (per_sm < 2 ? per_sm : 2);
+    }
+    int jj = j, mm = Lz.m_max;
+    int64_t N = Lz.N, ldv = Lz.ldv;
+    void *args[] = {&Lz.V, &ldv, &N, &jj, &Lz.z, &h0, &h1, &Lz.nrm2, &Lz.alpha, &Lz.beta, &mm, &Lz.bar, &Lz.err};
+    e = cudaLaunchCooperativeKernel((const void *)lanczos_step_kernel, dim3(grid), dim3(kStepThreads), args,
+                                    sizeof(float) * 2 * (Lz.m_max + 1), st);
+    dm_count_launches(1);
+    return e;
 }
 
 cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st) {

@@ -20,7 +20,7 @@
 
 namespace {
 
-constexpr int kSkelThreads = 256;
+constexpr int kSkelThreads = 512;
 constexpr int kSkelWarps = kSkelThreads / 32;
 
 __device__ __forceinline__ float kentry(const float *__restrict__ Xp, const float *__restrict__ sp, int d,
@@ -40,18 +40,42 @@ struct SkelArgs {
     int64_t N;
     int d, L, level;
     float tol;
-    int max_rank, cmax, ldp, rmax;
+    int max_rank, cmax, ldp, rmax, lda;
     uint64_t seed;
     int32_t *ranks;
     int32_t *skel;
     float *P;
-    float *A;   // per-CTA slot rmax x cmax, column-major (ld rmax)
-    float *R;   // per-CTA slot max_rank x cmax, row-major (ld cmax)
+    float *A;   // per-CTA slot rmax x lda, row-major: A[i][j], i a sampled row, j a candidate
+    float *R;   // per-CTA slot max_rank x cmax, row-major
+    float *Q;   // per-CTA slot max_rank x rmax: orthonormal pivot columns, one contiguous vector each
 };
 
+constexpr int kSkelMaxCand = 512;  // candidates per node (leaf points or two children's skeletons)
+
+// Work split of the sampled block: thread t owns the 4 adjacent columns of group
+// t % ncg over the row slice t / ncg (16-byte loads, coalesced along a row).
+struct SkelSplit {
+    int ncg, nsl, rps;
+};
+__device__ __forceinline__ SkelSplit skel_split(int c, int r) {
+    SkelSplit s;
+    s.ncg = c > 0 ? (c + 3) >> 2 : 1;
+    int nsl = kSkelThreads / s.ncg;
+    const int cap = (r + 15) / 16;  // keep at least 16 rows per slice
+    if (nsl > cap) nsl = cap;
+    if (nsl < 1) nsl = 1;
+    s.nsl = nsl;
+    s.rps = (r + nsl - 1) / nsl;
+    return s;
+}
+
 __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    int *C = reinterpret_cast<int *>(smem_raw);          // cmax candidate positions
+    // float4-accessed arrays first so that every one starts on a 16-byte boundary
+    extern __shared__ float4 smem4[];
+    float *red = reinterpret_cast<float *>(smem4);       // kSkelThreads x 4 partials
+    float *dots = red + 4 * kSkelThreads;                // cmax rounded to 4: R(k, :)
+    float *xr = dots + ((a.cmax + 3) & ~3);              // rmax x 4: row coordinates (d <= 3) and s
+    int *C = reinterpret_cast<int *>(xr + 4 * a.rmax);   // cmax candidate positions
     int *Rw = C + a.cmax;                                // rmax row positions
     int *selpos = Rw + a.rmax;                           // cmax: -1 or pivot step
     int *piv = selpos + a.cmax;                          // max_rank
@@ -67,8 +91,9 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
     const int node = (1 << a.level) - 1 + (int)blockIdx.x;
     int64_t st, sz;
     dm_node_range(a.N, node, &st, &sz);
-    float *A = a.A + (size_t)blockIdx.x * a.rmax * a.cmax;
+    float *A = a.A + (size_t)blockIdx.x * a.rmax * a.lda;
     float *R = a.R + (size_t)blockIdx.x * a.max_rank * a.cmax;
+    float *Q = a.Q + (size_t)blockIdx.x * a.max_rank * a.rmax;
 
     // ---- candidates
     int c;
@@ -87,26 +112,70 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
     const int rtarget = 2 * a.max_rank + 10;
     const int r = (int)(off <= rtarget ? off : rtarget);
     const uint64_t key = dm_stream_key(a.seed, DM_TAG_ROWS, (uint64_t)node);
+    const bool small_d = a.d <= 3;
     for (int t = threadIdx.x; t < r; t += blockDim.x) {
         int64_t u = (off <= rtarget) ? (int64_t)t : (int64_t)dm_below(dm_rng(key, (uint64_t)t), (uint64_t)off);
-        Rw[t] = (int)(u < st ? u : u + sz);
+        const int pos = (int)(u < st ? u : u + sz);
+        Rw[t] = pos;
+        if (small_d) {
+            for (int k = 0; k < 3; ++k) xr[t * 4 + k] = k < a.d ? a.Xp[(int64_t)pos * a.d + k] : 0.f;
+            xr[t * 4 + 3] = a.sp[pos];
+        }
     }
     for (int j = threadIdx.x; j < c; j += blockDim.x) selpos[j] = -1;
     __syncthreads();
 
-    // ---- sampled block A = K(R, C) and its column norms
-    for (int j = warp; j < c; j += kSkelWarps) {
-        const int64_t cj = C[j];
-        float ss = 0.f;
-        for (int i = lane; i < r; i += 32) {
-            float v = kentry(a.Xp, a.sp, a.d, Rw[i], cj);
-            A[(size_t)j * a.rmax + i] = v;
-            ss = fmaf(v, v, ss);
+    const SkelSplit sp4 = skel_split(c, r);
+    const int g = threadIdx.x % sp4.ncg, slice = threadIdx.x / sp4.ncg;
+    const bool worker = slice < sp4.nsl;
+    const int j0 = 4 * g;
+    const int i_lo = slice * sp4.rps, i_hi = min(r, i_lo + sp4.rps);
+
+    // ---- sampled block A = K(R, C) (zero in padding columns) and partial column norms
+    {
+        float4 ss = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (worker) {
+            int64_t cj[4];
+            float sj[4], cx[4][3];
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + q;
+                cj[q] = j < c ? C[j] : -1;
+                sj[q] = 0.f;
+                cx[q][0] = cx[q][1] = cx[q][2] = 0.f;
+                if (cj[q] >= 0) {
+                    sj[q] = a.sp[cj[q]];
+                    if (small_d)
+                        for (int k = 0; k < a.d; ++k) cx[q][k] = a.Xp[cj[q] * a.d + k];
+                }
+            }
+            for (int i = i_lo; i < i_hi; ++i) {
+                float v[4];
+                for (int q = 0; q < 4; ++q) {
+                    if (cj[q] < 0) { v[q] = 0.f; continue; }
+                    if (small_d) {
+                        const float t0 = cx[q][0] - xr[i * 4], t1 = cx[q][1] - xr[i * 4 + 1], t2 = cx[q][2] - xr[i * 4 + 2];
+                        v[q] = xr[i * 4 + 3] * sj[q] * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2)));
+                    } else {
+                        v[q] = kentry(a.Xp, a.sp, a.d, Rw[i], cj[q]);
+                    }
+                }
+                *reinterpret_cast<float4 *>(A + (size_t)i * a.lda + j0) = make_float4(v[0], v[1], v[2], v[3]);
+                ss.x = fmaf(v[0], v[0], ss.x);
+                ss.y = fmaf(v[1], v[1], ss.y);
+                ss.z = fmaf(v[2], v[2], ss.z);
+                ss.w = fmaf(v[3], v[3], ss.w);
+            }
         }
-        ss = dm_warp_sum(ss);
-        if (lane == 0) norms[j] = sqrtf(ss);
+        reinterpret_cast<float4 *>(red)[threadIdx.x] = ss;
+        __syncthreads();
+        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+            const int gg = j >> 2, qq = j & 3;
+            float t = 0.f;
+            for (int s2 = 0; s2 < sp4.nsl; ++s2) t += red[(s2 * sp4.ncg + gg) * 4 + qq];
+            norms[j] = sqrtf(t);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     int kmax = a.max_rank;
     if (kmax > c) kmax = c;
@@ -118,14 +187,14 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
         int bi = 0x7fffffff;
         for (int j = threadIdx.x; j < c; j += blockDim.x) {
             if (selpos[j] < 0) {
-                float v = norms[j];
+                const float v = norms[j];
                 if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(DM_FULL, bv, o);
-            int oi = __shfl_xor_sync(DM_FULL, bi, o);
+            const float ov = __shfl_xor_sync(DM_FULL, bv, o);
+            const int oi = __shfl_xor_sync(DM_FULL, bi, o);
             if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
         if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
@@ -142,29 +211,30 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
         __syncthreads();
         const int p = s_p;
         if (!(s_np > a.tol * s_nrm0) || s_np <= 0.f) break;
-        float *ap = A + (size_t)p * a.rmax;
-        // ---- re-orthogonalise the pivot column against the earlier pivots (one pass)
+        // ---- gather the pivot column, re-orthogonalise it once against q_0..q_{k-1}
+        for (int i = threadIdx.x; i < r; i += blockDim.x) qv[i] = A[(size_t)i * a.lda + p];
+        __syncthreads();
         if (k > 0) {
             for (int t = warp; t < k; t += kSkelWarps) {
-                const float *qt = A + (size_t)piv[t] * a.rmax;
+                const float *qt = Q + (size_t)t * a.rmax;
                 float dsum = 0.f;
-                for (int i = lane; i < r; i += 32) dsum = fmaf(qt[i], ap[i], dsum);
+                for (int i = lane; i < r; i += 32) dsum = fmaf(qt[i], qv[i], dsum);
                 dsum = dm_warp_sum(dsum);
                 if (lane == 0) coef[t] = dsum;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < r; i += blockDim.x) {
-                float v = ap[i];
-                for (int t = 0; t < k; ++t) v = fmaf(-coef[t], A[(size_t)piv[t] * a.rmax + i], v);
-                ap[i] = v;
+                float v = qv[i];
+                for (int t = 0; t < k; ++t) v = fmaf(-coef[t], Q[(size_t)t * a.rmax + i], v);
+                qv[i] = v;
             }
             for (int t = threadIdx.x; t < k; t += blockDim.x) R[(size_t)t * a.cmax + p] += coef[t];
             __syncthreads();
         }
-        // ---- normalise the pivot column into q_k
+        // ---- normalise into q_k
         if (warp == 0) {
             float ss = 0.f;
-            for (int i = lane; i < r; i += 32) ss = fmaf(ap[i], ap[i], ss);
+            for (int i = lane; i < r; i += 32) ss = fmaf(qv[i], qv[i], ss);
             ss = dm_warp_sum(ss);
             if (lane == 0) {
                 s_qn = sqrtf(ss);
@@ -176,28 +246,68 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
         __syncthreads();
         const float inv = 1.f / s_qn;
         for (int i = threadIdx.x; i < r; i += blockDim.x) {
-            float v = ap[i] * inv;
-            ap[i] = v;
+            const float v = qv[i] * inv;
             qv[i] = v;
+            Q[(size_t)k * a.rmax + i] = v;
         }
         __syncthreads();
-        // ---- update the remaining columns: R(k, j) = q^T a_j; a_j -= R(k, j) q; fresh norms
-        for (int j = warp; j < c; j += kSkelWarps) {
-            if (selpos[j] >= 0) continue;
-            float *aj = A + (size_t)j * a.rmax;
-            float dsum = 0.f;
-            for (int i = lane; i < r; i += 32) dsum = fmaf(qv[i], aj[i], dsum);
-            dsum = dm_warp_sum(dsum);
-            float ss = 0.f;
-            for (int i = lane; i < r; i += 32) {
-                float v = fmaf(-dsum, qv[i], aj[i]);
-                aj[i] = v;
-                ss = fmaf(v, v, ss);
+        // ---- R(k, :) = q^T A: float4 partial dots per row slice, reduced through shared memory
+        {
+            float4 dp = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (worker) {
+                const float *base = A + j0;
+#pragma unroll 4
+                for (int i = i_lo; i < i_hi; ++i) {
+                    const float4 v = *reinterpret_cast<const float4 *>(base + (size_t)i * a.lda);
+                    const float qi = qv[i];
+                    dp.x = fmaf(qi, v.x, dp.x);
+                    dp.y = fmaf(qi, v.y, dp.y);
+                    dp.z = fmaf(qi, v.z, dp.z);
+                    dp.w = fmaf(qi, v.w, dp.w);
+                }
             }
-            ss = dm_warp_sum(ss);
-            if (lane == 0) {
-                R[(size_t)k * a.cmax + j] = dsum;
-                norms[j] = sqrtf(ss);
+            reinterpret_cast<float4 *>(red)[threadIdx.x] = dp;
+            __syncthreads();
+            for (int j = threadIdx.x; j < ((c + 3) & ~3); j += blockDim.x) {
+                float t = 0.f;
+                if (j < c && selpos[j] < 0) {
+                    const int gg = j >> 2, qq = j & 3;
+                    for (int s2 = 0; s2 < sp4.nsl; ++s2) t += red[(s2 * sp4.ncg + gg) * 4 + qq];
+                    R[(size_t)k * a.cmax + j] = t;
+                }
+                dots[j] = t;  // zero for selected and padding columns: their residuals stay as they are
+            }
+            __syncthreads();
+        }
+        // ---- a_j -= R(k, j) q for the remaining columns, partial norms of the new residuals
+        {
+            float4 ss = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (worker) {
+                const float4 dk = *reinterpret_cast<const float4 *>(dots + j0);
+                float *base = A + j0;
+#pragma unroll 4
+                for (int i = i_lo; i < i_hi; ++i) {
+                    float4 v = *reinterpret_cast<float4 *>(base + (size_t)i * a.lda);
+                    const float qi = qv[i];
+                    v.x = fmaf(-dk.x, qi, v.x);
+                    v.y = fmaf(-dk.y, qi, v.y);
+                    v.z = fmaf(-dk.z, qi, v.z);
+                    v.w = fmaf(-dk.w, qi, v.w);
+                    *reinterpret_cast<float4 *>(base + (size_t)i * a.lda) = v;
+                    ss.x = fmaf(v.x, v.x, ss.x);
+                    ss.y = fmaf(v.y, v.y, ss.y);
+                    ss.z = fmaf(v.z, v.z, ss.z);
+                    ss.w = fmaf(v.w, v.w, ss.w);
+                }
+            }
+            reinterpret_cast<float4 *>(red)[threadIdx.x] = ss;
+            __syncthreads();
+            for (int j = threadIdx.x; j < c; j += blockDim.x) {
+                if (selpos[j] >= 0) continue;
+                const int gg = j >> 2, qq = j & 3;
+                float t = 0.f;
+                for (int s2 = 0; s2 < sp4.nsl; ++s2) t += red[(s2 * sp4.ncg + gg) * 4 + qq];
+                norms[j] = sqrtf(t);
             }
         }
         rank = k + 1;
@@ -260,6 +370,22 @@ __global__ void pack_far_kernel(const float *__restrict__ Xp, const float *__res
     }
 }
 
+// PT[leaf][i][t] = P_leaf[t][i] (t < rank, zero up to ldt), the point-major copy the
+// downward pass reads with contiguous 16-byte loads
+__global__ void transpose_leaf_kernel(DmHmat H, float *__restrict__ PT) {
+    const int leaf = blockIdx.x;
+    const int node = (1 << H.L) - 1 + leaf;
+    int64_t st, sz;
+    dm_node_range(H.N, node, &st, &sz);
+    const int s = H.ranks[node];
+    const float *Pn = H.P + (size_t)node * H.max_rank * H.ldp;
+    float *out = PT + (size_t)leaf * H.leaf_max * H.ldt;
+    for (int e = threadIdx.x; e < (int)sz * H.ldt; e += blockDim.x) {
+        const int i = e / H.ldt, t = e % H.ldt;
+        out[e] = t < s ? Pn[(size_t)t * H.ldp + i] : 0.f;
+    }
+}
+
 __global__ void permute_points_kernel(const float *__restrict__ Xs, const float *__restrict__ sf,
                                       const int32_t *__restrict__ perm, int64_t N, int d, float *__restrict__ Xp,
                                       float *__restrict__ sp) {
@@ -273,8 +399,11 @@ __global__ void permute_points_kernel(const float *__restrict__ Xs, const float 
 }  // namespace
 
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
-    return sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank) + sizeof(float) * (size_t)(cmax + rmax + max_rank);
+    return sizeof(float) * 4 * (size_t)kSkelThreads + sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank) +
+           sizeof(float) * (size_t)(cmax + rmax + max_rank + ((cmax + 3) & ~3) + 4 * rmax);
 }
+
+int dm_skel_max_candidates() { return kSkelMaxCand; }
 
 cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, int L, const int32_t *perm,
                            double tol, int max_rank, int cmax, int ldp, uint64_t seed, int32_t *ranks,
@@ -297,6 +426,9 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     a.P = P;
     a.A = w->A;
     a.R = w->R;
+    a.Q = w->Q;
+    a.lda = w->lda;
+    if (cmax > kSkelMaxCand || (w->lda & 3) != 0) return cudaErrorInvalidValue;
     const size_t smem = dm_skel_smem_bytes(cmax, w->rmax, max_rank);
     cudaError_t e = cudaFuncSetAttribute(skel_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -322,6 +454,12 @@ cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cud
         pack_far_kernel<<<(1 << H.L) - 1, 256, 0, st>>>(H.Xs, H.sp, H.d, H.ranks, H.skel, H.max_rank, B);
         dm_count_launches(1);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t dm_transpose_leaf_bases(const DmHmat &H, float *PT, cudaStream_t st) {
+    transpose_leaf_kernel<<<1u << H.L, 256, 0, st>>>(H, PT);
+    dm_count_launches(1);
     return cudaGetLastError();
 }
 
