@@ -152,6 +152,59 @@ int dm_get_stats(dm_handle h, dm_stats *st);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t dm_kernel_launches(void);
 
+/* ---- serving: continuous admission of independent solves ----
+ * A process-wide server runs `slots` solves at once, each on its own CUDA stream,
+ * so their kernels overlap on the device. Requests wait in a queue and are
+ * admitted first-fit, in arrival order, whenever a slot is free and the request's
+ * device footprint (dm_request_bytes) fits in what is left of the HBM budget (a
+ * request larger than the whole budget runs alone). Each result is computed
+ * exactly as by dm_create + dm_compress + dm_eigs on a fresh handle.
+ * Submit and poll are thread-safe. No counterpart in the paper. */
+typedef struct dm_request {
+    const float *points;   /* N x d row-major float32, host memory; copied by dm_submit */
+    int64_t N;
+    int32_t d;
+    double eps, alpha;     /* as dm_create (eps <= 0: median squared distance) */
+    double tol;            /* as dm_compress */
+    int32_t leaf_size, max_rank;
+    int32_t k;             /* eigenpairs wanted (as dm_eigs) */
+    int32_t want_vectors;  /* 1: return the N x k eigenvectors too */
+    uint64_t seed;
+} dm_request;
+
+typedef struct dm_result {
+    int32_t status;        /* DM_OK, DM_ENOCONV or the failing call's status */
+    int32_t k;
+    int64_t N;
+    const double *evals;   /* k values, descending; library-owned until dm_release */
+    const float *evecs;    /* N x k column-major, or NULL; library-owned until dm_release */
+    double submit_ms, start_ms, done_ms;  /* wall-clock times since dm_serve_start */
+    int32_t lanczos_iters;
+} dm_result;
+
+typedef struct dm_serve_config {
+    int32_t device;             /* CUDA device ordinal (-1: current) */
+    int32_t slots;              /* concurrent solves (default 4) */
+    uint64_t hbm_budget_bytes;  /* admission budget (0: 150 GB) */
+    int32_t queue_capacity;     /* waiting requests before DM_EBUSY (0: 65536) */
+} dm_serve_config;
+
+/* Device bytes one solve of `r` allocates at its peak (the admission estimate). */
+uint64_t dm_request_bytes(const dm_request *r);
+/* Start the server (DM_ESTATE if running; DM_ECUDA without a device). */
+int dm_serve_start(const dm_serve_config *cfg);
+/* Stop accepting work, finish running solves, drop queued ones (their status
+ * becomes DM_ESTATE), join the workers and free every result. */
+int dm_serve_stop(void);
+/* Queue a request; *t identifies it. DM_EINVAL for an invalid request, DM_ESTATE
+ * if the server is not running, DM_EBUSY if the queue is full. */
+int dm_submit(const dm_request *r, dm_ticket *t);
+/* Non-blocking: *done = 1 once the solve finished (r, if not NULL, then holds the
+ * result); 0 while queued or running. DM_EINVAL for an unknown ticket. */
+int dm_poll(dm_ticket t, dm_result *r, int32_t *done);
+/* Free a finished request's result buffers (DM_EBUSY while it is still running). */
+int dm_release(dm_ticket t);
+
 /* ---- allocation-free entry point (no counterpart in the paper) ----
  * For callers that cannot let a library allocate device memory: code running
  * inside a framework that owns all device memory and forbids side allocations,

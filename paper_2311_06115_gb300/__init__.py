@@ -24,7 +24,9 @@ __all__ = [
     "DM_NEAR_AUTO", "DM_NEAR_CACHED", "DM_NEAR_ONTHEFLY", "dm_config", "dm_stats", "lib_path", "load",
     "dm_config_default", "dm_create", "dm_compress", "dm_matvec", "dm_eigs", "dm_coords", "dm_destroy",
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
-    "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc",
+    "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc", "dm_request",
+    "dm_result", "dm_serve_config", "dm_request_bytes", "dm_serve_start", "dm_serve_stop", "dm_submit", "dm_poll",
+    "dm_release",
 ]
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
@@ -52,6 +54,23 @@ class dm_stats(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class dm_request(C.Structure):
+    _fields_ = [("points", C.c_void_p), ("N", C.c_int64), ("d", C.c_int32), ("eps", C.c_double),
+                ("alpha", C.c_double), ("tol", C.c_double), ("leaf_size", C.c_int32), ("max_rank", C.c_int32),
+                ("k", C.c_int32), ("want_vectors", C.c_int32), ("seed", C.c_uint64)]
+
+
+class dm_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("k", C.c_int32), ("N", C.c_int64), ("evals", C.POINTER(C.c_double)),
+                ("evecs", C.POINTER(C.c_float)), ("submit_ms", C.c_double), ("start_ms", C.c_double),
+                ("done_ms", C.c_double), ("lanczos_iters", C.c_int32)]
+
+
+class dm_serve_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
+                ("queue_capacity", C.c_int32)]
 
 
 class DmError(RuntimeError):
@@ -97,6 +116,12 @@ def load(build_if_missing: bool = True):
         "dm_load_hmatrix": (i32, [vp, i32, i32, vp, vp, vp, vp]),
         "dm_kernel_launches": (i64, []),
         "dm_degrees_noalloc": (i32, [vp, i64, i32, f64, f64, vp, vp, vp, vp]),
+        "dm_request_bytes": (C.c_uint64, [C.POINTER(dm_request)]),
+        "dm_serve_start": (i32, [C.POINTER(dm_serve_config)]),
+        "dm_serve_stop": (i32, []),
+        "dm_submit": (i32, [C.POINTER(dm_request), C.POINTER(C.c_uint64)]),
+        "dm_poll": (i32, [C.c_uint64, C.POINTER(dm_result), C.POINTER(i32)]),
+        "dm_release": (i32, [C.c_uint64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -360,3 +385,57 @@ def dm_load_hmatrix(h: Handle, L: int, max_rank: int, perm, ranks, skel, P) -> N
     P = np.ascontiguousarray(P, dtype=np.float32)
     _check(load().dm_load_hmatrix(h, int(L), int(max_rank), perm.ctypes.data, ranks.ctypes.data,
                                   skel.ctypes.data, P.ctypes.data))
+
+
+# ------------------------------------------------------------------ serving
+
+def _request(points, eps=-1.0, alpha=1.0, tol=1e-5, leaf_size=512, max_rank=128, k=10, want_vectors=True, seed=0):
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    r = dm_request(points=pts.ctypes.data, N=pts.shape[0], d=pts.shape[1], eps=float(eps), alpha=float(alpha),
+                   tol=float(tol), leaf_size=int(leaf_size), max_rank=int(max_rank), k=int(k),
+                   want_vectors=1 if want_vectors else 0, seed=int(seed))
+    return r, pts
+
+
+def dm_request_bytes(points, **kw) -> int:
+    """Device bytes one solve of this request allocates at its peak (the admission estimate)."""
+    r, _ = _request(points, **kw)
+    return int(load().dm_request_bytes(C.byref(r)))
+
+
+def dm_serve_start(slots: int = 4, hbm_budget_bytes: int = 0, device: int = -1, queue_capacity: int = 0) -> None:
+    cfg = dm_serve_config(device=device, slots=slots, hbm_budget_bytes=hbm_budget_bytes,
+                          queue_capacity=queue_capacity)
+    _check(load().dm_serve_start(C.byref(cfg)))
+
+
+def dm_serve_stop() -> None:
+    _check(load().dm_serve_stop())
+
+
+def dm_submit(points, **kw) -> int:
+    """Queue a solve of `points` (host array); returns its ticket. Keywords as dm_request."""
+    r, _keep = _request(points, **kw)
+    t = C.c_uint64()
+    _check(load().dm_submit(C.byref(r), C.byref(t)))  # the library copies the points before returning
+    return int(t.value)
+
+
+def dm_poll(ticket: int):
+    """(done, result dict or None): evals (k,), evecs (N, k) or None, status, times in ms."""
+    r = dm_result()
+    done = C.c_int32()
+    _check(load().dm_poll(C.c_uint64(ticket), C.byref(r), C.byref(done)))
+    if not done.value:
+        return False, None
+    out = {"status": int(r.status), "k": int(r.k), "N": int(r.N), "submit_ms": r.submit_ms, "start_ms": r.start_ms,
+           "done_ms": r.done_ms, "lanczos_iters": int(r.lanczos_iters), "evals": None, "evecs": None}
+    if r.evals:
+        out["evals"] = np.ctypeslib.as_array(r.evals, shape=(r.k,)).copy()
+    if r.evecs:
+        out["evecs"] = np.ctypeslib.as_array(r.evecs, shape=(r.k, r.N)).T.copy()
+    return True, out
+
+
+def dm_release(ticket: int) -> None:
+    _check(load().dm_release(C.c_uint64(ticket)))

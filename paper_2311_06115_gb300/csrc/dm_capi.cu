@@ -657,9 +657,11 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
     DM_CUDA(cudaStreamSynchronize(h->stream));
     {
         int err = 0;
-        DM_CUDA(cudaMemcpy(&err, Lz.err, sizeof(int), cudaMemcpyDeviceToHost));
+        DM_CUDA(cudaMemcpyAsync(&err, Lz.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        DM_CUDA(cudaStreamSynchronize(h->stream));
         if (err) {
-            DM_CUDA(cudaMemset(Lz.err, 0, sizeof(int)));
+            DM_CUDA(cudaMemsetAsync(Lz.err, 0, sizeof(int), h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
             return fail(DM_ETIMEOUT, "a grid barrier of the Lanczos step gave up waiting");
         }
     }

@@ -1,0 +1,277 @@
+// dm_serve.cu -- request server: independent diffusion-map solves admitted as
+// slots and device memory free up, each slot on its own CUDA stream so that
+// concurrently running solves overlap on the GPU.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "dm_internal.cuh"
+
+int dm_lanczos_kmax();
+
+namespace {
+
+inline uint64_t r256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+
+enum JobState { kQueued = 0, kRunning = 1, kDone = 2 };
+
+struct Job {
+    dm_ticket id = 0;
+    dm_request req{};
+    std::vector<float> points;
+    uint64_t bytes = 0;
+    JobState state = kQueued;
+    std::vector<double> evals;
+    std::vector<float> evecs;
+    dm_result res{};
+};
+
+struct Server {
+    std::mutex mu;
+    std::condition_variable cv;
+    bool running = false, stopping = false;
+    int device = 0;
+    uint64_t budget = 0, used = 0;
+    int capacity = 65536;
+    int busy = 0;
+    dm_ticket next_id = 1;
+    std::deque<Job *> queue;
+    std::map<dm_ticket, std::unique_ptr<Job>> jobs;
+    std::vector<std::thread> workers;
+    std::chrono::steady_clock::time_point t0;
+
+    double now_ms() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+Server g_srv;
+
+bool valid_request(const dm_request *r) {
+    return r && r->points && r->N >= 2 && r->d >= 1 && r->alpha >= 0.0 && r->tol >= 0.0 && r->leaf_size >= 1 &&
+           r->max_rank >= 1 && r->max_rank <= 256 && r->k >= 1 && r->k < r->N && r->k <= dm_lanczos_kmax() &&
+           r->N <= (int64_t)0x7fffffff;
+}
+
+// pick the first queued job that fits (caller holds the lock); nullptr if none
+Job *admit_locked(Server &S) {
+    for (auto it = S.queue.begin(); it != S.queue.end(); ++it) {
+        Job *j = *it;
+        if (S.used + j->bytes <= S.budget || S.used == 0) {
+            S.queue.erase(it);
+            return j;
+        }
+    }
+    return nullptr;
+}
+
+// stream-ordered allocations on the slot's stream: no device-wide synchronisation
+// between concurrently running solves (plain cudaFree would serialise them)
+void *slot_alloc(size_t bytes, void *user) {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, reinterpret_cast<cudaStream_t>(user)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void slot_free(void *p, size_t, void *user) { cudaFreeAsync(p, reinterpret_cast<cudaStream_t>(user)); }
+
+void run_job(Job *j, cudaStream_t stream) {
+    dm_config cfg;
+    dm_config_default(&cfg);
+    cfg.seed = j->req.seed;
+    cfg.stream = stream;
+    cfg.device = g_srv.device;
+    cfg.alloc = slot_alloc;
+    cfg.free = slot_free;
+    cfg.alloc_user = stream;
+    dm_handle h = nullptr;
+    const int k = j->req.k;
+    int st = dm_create(j->points.data(), j->req.N, j->req.d, j->req.eps, j->req.alpha, &cfg, &h);
+    if (st == DM_OK) st = dm_compress(h, j->req.tol, j->req.leaf_size, j->req.max_rank);
+    if (st == DM_OK) {
+        j->evals.assign((size_t)k, 0.0);
+        if (j->req.want_vectors) j->evecs.assign((size_t)k * (size_t)j->req.N, 0.f);
+        st = dm_eigs(h, k, j->evals.data(), j->req.want_vectors ? j->evecs.data() : nullptr);
+        dm_stats s{};
+        dm_get_stats(h, &s);
+        j->res.lanczos_iters = s.lanczos_iters;
+    }
+    if (h) dm_destroy(h);
+    j->res.status = st;
+}
+
+void worker_main() {
+    cudaSetDevice(g_srv.device);
+    cudaStream_t stream = nullptr;
+    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    for (;;) {
+        Job *j = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(g_srv.mu);
+            g_srv.cv.wait(lk, [&] {
+                if (g_srv.stopping) return true;
+                for (Job *q : g_srv.queue)
+                    if (g_srv.used + q->bytes <= g_srv.budget || g_srv.used == 0) return true;
+                return false;
+            });
+            if (g_srv.stopping) break;
+            j = admit_locked(g_srv);
+            if (!j) continue;
+            g_srv.used += j->bytes;
+            g_srv.busy += 1;
+            j->state = kRunning;
+            j->res.start_ms = g_srv.now_ms();
+        }
+        run_job(j, stream);
+        {
+            std::lock_guard<std::mutex> lk(g_srv.mu);
+            g_srv.used -= j->bytes;
+            g_srv.busy -= 1;
+            j->points.clear();
+            j->points.shrink_to_fit();
+            j->res.done_ms = g_srv.now_ms();
+            j->res.k = j->req.k;
+            j->res.N = j->req.N;
+            j->res.evals = j->evals.empty() ? nullptr : j->evals.data();
+            j->res.evecs = j->evecs.empty() ? nullptr : j->evecs.data();
+            j->state = kDone;
+        }
+        g_srv.cv.notify_all();
+    }
+    if (stream) cudaStreamDestroy(stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t dm_request_bytes(const dm_request *r) {
+    if (!r || r->N < 2 || r->d < 1 || r->leaf_size < 1 || r->max_rank < 1) return 0;
+    const uint64_t N = (uint64_t)r->N, d = (uint64_t)r->d, R = (uint64_t)r->max_rank;
+    const int L = dm_depth_for(r->N, r->leaf_size);
+    const uint64_t nleaves = 1ull << L, nnodes = (2ull << L) - 1;
+    const uint64_t leaf_max = (N + nleaves - 1) / nleaves;
+    const uint64_t ldk = (leaf_max + 3) & ~3ull;
+    const uint64_t cmax = leaf_max > 2 * R ? leaf_max : 2 * R;
+    const uint64_t ldp = (cmax + 3) & ~3ull, lda = (cmax + 31) & ~31ull, rmax = 2 * R + 10;
+    const uint64_t mmax = 300, kmax = (uint64_t)dm_lanczos_kmax(), ldv = (N + 63) & ~63ull;
+    uint64_t b = 0;
+    // points, degrees and scalings
+    b += 2 * r256(4 * N * d) + 5 * r256(8 * N) + 3 * r256(4 * N);
+    // compressed structure
+    b += r256(4 * nnodes) + r256(4 * nnodes * R) + r256(4 * nnodes * R * ldp) + r256(4 * N * d) + r256(4 * N);
+    b += 2 * r256(4 * N) + r256(4 * nleaves * leaf_max * ldk) + r256(4 * (nleaves > 1 ? nleaves - 1 : 1) * R * R);
+    b += 2 * r256(4 * nnodes * R) + r256(4 * N) + r256(4 * nnodes) + r256(4 * nleaves * leaf_max * ((R + 3) & ~3ull));
+    // transient workspaces of the compression (skeletonization is the largest)
+    b += r256(4 * nleaves * rmax * lda) + r256(4 * nleaves * R * cmax) + r256(4 * nleaves * R * rmax);
+    // Lanczos basis, Ritz vectors and small arrays
+    b += r256(4 * (mmax + 1) * ldv) + r256(4 * ldv) + 2 * r256(4 * kmax * N);
+    b += r256(8 * kmax * 6 * mmax) + r256(8 * kmax * mmax) + r256(4 * kmax * mmax) + 16 * 256;
+    return b;
+}
+
+int dm_serve_start(const dm_serve_config *cfg) {
+    std::lock_guard<std::mutex> lk(g_srv.mu);
+    if (g_srv.running) return dm_fail_msg(DM_ESTATE, "server already running");
+    int dev = cfg && cfg->device >= 0 ? cfg->device : -1;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return dm_fail_msg(DM_ECUDA, "no CUDA device available");
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev >= ndev) {
+        cudaGetLastError();
+        return dm_fail_msg(DM_ECUDA, "no CUDA device available");
+    }
+    g_srv.device = dev;
+    {
+        // keep freed blocks in this process's pool between requests
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
+    g_srv.budget = cfg && cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : 150ull * 1000 * 1000 * 1000;
+    g_srv.capacity = cfg && cfg->queue_capacity > 0 ? cfg->queue_capacity : 65536;
+    const int slots = cfg && cfg->slots > 0 ? cfg->slots : 4;
+    g_srv.used = 0;
+    g_srv.busy = 0;
+    g_srv.stopping = false;
+    g_srv.t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < slots; ++i) g_srv.workers.emplace_back(worker_main);
+    g_srv.running = true;
+    return DM_OK;
+}
+
+int dm_serve_stop(void) {
+    std::vector<std::thread> ws;
+    {
+        std::lock_guard<std::mutex> lk(g_srv.mu);
+        if (!g_srv.running) return dm_fail_msg(DM_ESTATE, "server not running");
+        g_srv.stopping = true;
+        for (Job *j : g_srv.queue) {
+            j->res.status = DM_ESTATE;
+            j->state = kDone;
+        }
+        g_srv.queue.clear();
+        ws.swap(g_srv.workers);
+    }
+    g_srv.cv.notify_all();
+    for (auto &t : ws) t.join();
+    std::lock_guard<std::mutex> lk(g_srv.mu);
+    g_srv.jobs.clear();
+    g_srv.running = false;
+    g_srv.stopping = false;
+    return DM_OK;
+}
+
+int dm_submit(const dm_request *r, dm_ticket *t) {
+    if (!t) return dm_fail_msg(DM_EINVAL, "ticket pointer is NULL");
+    if (!valid_request(r)) return dm_fail_msg(DM_EINVAL, "invalid request (sizes, k, ranks, tolerances)");
+    auto j = std::make_unique<Job>();
+    j->req = *r;
+    j->points.assign(r->points, r->points + (size_t)r->N * (size_t)r->d);
+    j->req.points = nullptr;
+    j->bytes = dm_request_bytes(r);
+    std::lock_guard<std::mutex> lk(g_srv.mu);
+    if (!g_srv.running || g_srv.stopping) return dm_fail_msg(DM_ESTATE, "server not running");
+    if ((int)g_srv.queue.size() >= g_srv.capacity) return dm_fail_msg(DM_EBUSY, "request queue full");
+    j->id = g_srv.next_id++;
+    j->res.submit_ms = g_srv.now_ms();
+    *t = j->id;
+    g_srv.queue.push_back(j.get());
+    g_srv.jobs[j->id] = std::move(j);
+    g_srv.cv.notify_all();
+    return DM_OK;
+}
+
+int dm_poll(dm_ticket t, dm_result *r, int32_t *done) {
+    std::lock_guard<std::mutex> lk(g_srv.mu);
+    auto it = g_srv.jobs.find(t);
+    if (it == g_srv.jobs.end()) return dm_fail_msg(DM_EINVAL, "unknown ticket");
+    const bool fin = it->second->state == kDone;
+    if (done) *done = fin ? 1 : 0;
+    if (fin && r) *r = it->second->res;
+    return DM_OK;
+}
+
+int dm_release(dm_ticket t) {
+    std::lock_guard<std::mutex> lk(g_srv.mu);
+    auto it = g_srv.jobs.find(t);
+    if (it == g_srv.jobs.end()) return dm_fail_msg(DM_EINVAL, "unknown ticket");
+    if (it->second->state != kDone) return dm_fail_msg(DM_EBUSY, "request still queued or running");
+    g_srv.jobs.erase(it);
+    return DM_OK;
+}
+
+}  // extern "C"

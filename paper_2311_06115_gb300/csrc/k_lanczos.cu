@@ -12,6 +12,9 @@
 // this part, so it is spent only on the coefficients), and the small tridiagonal
 // eigenproblem is solved in FP64 with division-free Sturm sequences
 // (multisection: 32 shifts per warp per round) and inverse iteration.
+#include <map>
+#include <mutex>
+
 #include "dm_internal.cuh"
 
 namespace {
@@ -473,6 +476,12 @@ cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, 
     return cudaGetLastError();
 }
 
+namespace {
+std::mutex g_coop_mu;
+std::map<std::pair<int, void *>, cudaEvent_t> g_coop_events;  // per (device, stream); kept for the process
+cudaEvent_t g_coop_last = nullptr;
+}  // namespace
+
 // After Lz.z = A v_j: two Gram-Schmidt passes against V[:, 0..j], alpha_j, beta_j and
 // V[:, j+1], as one cooperative launch (grid = co-resident blocks on every SM).
 cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st) {
@@ -497,9 +506,31 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st) {
     int jj = j, mm = Lz.m_max;
     int64_t N = Lz.N, ldv = Lz.ldv;
     void *args[] = {&Lz.V, &ldv, &N, &jj, &Lz.z, &h0, &h1, &Lz.nrm2, &Lz.alpha, &Lz.beta, &mm, &Lz.bar, &Lz.err};
+    // Each step kernel fills every SM; two of them from different streams (concurrent
+    // solves) could each hold part of the device while waiting at a grid barrier for
+    // blocks that cannot become resident. So all step launches of the process form one
+    // chain: a launch waits for the previous one, whichever stream it was on.
+    std::lock_guard<std::mutex> lk(g_coop_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaEvent_t &mine = g_coop_events[std::make_pair(dev, (void *)st)];
+    if (!mine) {
+        e = cudaEventCreateWithFlags(&mine, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            mine = nullptr;
+            return e;
+        }
+    }
+    if (g_coop_last && g_coop_last != mine) {
+        e = cudaStreamWaitEvent(st, g_coop_last, 0);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaLaunchCooperativeKernel((const void *)lanczos_step_kernel, dim3(grid), dim3(kStepThreads), args,
                                     sizeof(float) * 2 * (Lz.m_max + 1), st);
     dm_count_launches(1);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(mine, st);
+    if (e == cudaSuccess) g_coop_last = mine;
     return e;
 }
 

@@ -63,3 +63,37 @@ def test_sm103a_target_only():
     from paper_2311_06115_gb300 import build
 
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_request_footprint_estimate_is_monotone_and_plausible():
+    import numpy as np
+
+    import paper_2311_06115_gb300 as dm
+
+    small = dm.dm_request_bytes(np.zeros((10_000, 3), np.float32), leaf_size=512, max_rank=128, k=20)
+    big = dm.dm_request_bytes(np.zeros((100_000, 3), np.float32), leaf_size=512, max_rank=128, k=20)
+    assert 0 < small < big
+    # the bench workload: leaf blocks (157 MB) + P slots (134 MB) + Krylov basis (120 MB) + workspaces
+    assert 500e6 < big < 1.5e9
+
+
+def test_serving_rejects_bad_requests_and_state():
+    import numpy as np
+    import torch
+
+    import paper_2311_06115_gb300 as dm
+
+    pts = np.zeros((100, 3), np.float32)
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_submit(pts, k=200)  # k >= N
+    assert e.value.status == dm.DM_EINVAL
+    if not torch.cuda.is_available():
+        with pytest.raises(dm.DmError) as e:
+            dm.dm_submit(pts, k=5)  # no server running
+        assert e.value.status == dm.DM_ESTATE
+        with pytest.raises(dm.DmError) as e:
+            dm.dm_serve_start()
+        assert e.value.status == dm.DM_ECUDA
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_poll(123456789)
+    assert e.value.status == dm.DM_EINVAL

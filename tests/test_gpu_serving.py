@@ -1,0 +1,92 @@
+"""Serving: requests admitted as slots and HBM budget free up, overlapping on the device;
+each result must equal the same request solved alone (within the eigensolver tolerance)."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2311_06115_gb300 as m
+
+    m.load()
+    return m
+
+
+REQS = [(1500, 0, 6), (4000, 1, 8), (2500, 2, 5), (6000, 3, 10), (3000, 4, 7), (1200, 5, 4)]
+
+
+def _points(n, seed):
+    return synth.as_f32(synth.s_curve(n, seed) if seed % 2 == 0 else synth.swiss_roll(n, seed))
+
+
+def _wait(dm, tickets, limit_s=120.0):
+    out, t0 = {}, time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                done, res = dm.dm_poll(t)
+                if done:
+                    out[t] = res
+        assert time.time() - t0 < limit_s, "serving did not finish"
+        time.sleep(0.002)
+    return out
+
+
+def _solo(dm, X, k):
+    h = dm.dm_create(X, eps=-1.0)
+    dm.dm_compress(h, 1e-5, 128, 64)
+    ev, V, conv = dm.dm_eigs(h, k)
+    dm.dm_destroy(h)
+    return ev, V
+
+
+def _angle(A, B):
+    sv = np.linalg.svd(A.astype(np.float64).T @ B.astype(np.float64), compute_uv=False)
+    return math.acos(min(1.0, float(sv.min())))
+
+
+def test_mixed_requests_match_solo_runs_and_overlap(dm):
+    dm.dm_serve_start(slots=3)
+    try:
+        tickets = [dm.dm_submit(_points(n, s), tol=1e-5, leaf_size=128, max_rank=64, k=k) for n, s, k in REQS]
+        res = _wait(dm, tickets)
+        for (n, s, k), t in zip(REQS, tickets):
+            r = res[t]
+            assert r["status"] == 0 and r["N"] == n and r["k"] == k
+            ev, V = _solo(dm, _points(n, s), k)
+            np.testing.assert_allclose(r["evals"], ev, rtol=1e-5, atol=1e-9)
+            assert _angle(r["evecs"], V) < 1e-3
+        spans = sorted((res[t]["start_ms"], res[t]["done_ms"]) for t in tickets)
+        assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1)), "no two solves overlapped"
+        for t in tickets:
+            dm.dm_release(t)
+    finally:
+        dm.dm_serve_stop()
+
+
+def test_budget_admits_one_request_at_a_time(dm):
+    X = _points(3000, 0)
+    one = dm.dm_request_bytes(X, leaf_size=128, max_rank=64, k=6)
+    dm.dm_serve_start(slots=4, hbm_budget_bytes=int(1.5 * one))
+    try:
+        tickets = [dm.dm_submit(X, tol=1e-5, leaf_size=128, max_rank=64, k=6, seed=i) for i in range(4)]
+        res = _wait(dm, tickets)
+        spans = sorted((res[t]["start_ms"], res[t]["done_ms"]) for t in tickets)
+        for i in range(len(spans) - 1):
+            assert spans[i + 1][0] >= spans[i][1], "budget allowed two solves at once"
+        assert all(res[t]["status"] == 0 for t in tickets)
+        with pytest.raises(dm.DmError):
+            dm.dm_release(123456789)
+    finally:
+        dm.dm_serve_stop()
