@@ -42,11 +42,16 @@ CPU_SAMPLE_N = 10_000
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=WORKLOAD["N"], help="override N (testing only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=2000,
+                   help="requests in the timed serving run (after warm-up); 0 skips it")
+    p.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
+    p.add_argument("--serve-slots", type=int, default=4)
+    p.add_argument("--serve-dims", default="3,64", help="point dimensions in the request mix")
     return p.parse_args()
 
 
@@ -66,7 +71,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -104,6 +109,77 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ serving: Poisson arrivals of mixed requests
+
+SERVE_MIX = ("N log-uniform in [2000, 100000], d from {dims} (s-curve for d=3, 8-component Gaussian mixture "
+             "for d=64), k uniform in [5, 32], tol from {{1e-4, 1e-5}}, leaf 512, rank 128, eigenvectors returned")
+
+
+def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: int = 100, seed: int = 7) -> dict:
+    """Submit warm + n_req requests at Poisson arrival times through dm_submit and collect them with
+    dm_poll; latency = submit to done on the library's clock. Each request's points are a random
+    window of a seeded 200,000-point cloud of its dimension (generated once, before timing)."""
+    import numpy as np
+
+    import synth
+
+    g = np.random.default_rng(seed)
+    base = {}
+    for d in dims:
+        base[d] = synth.as_f32(synth.s_curve(200_000, seed=11) if d == 3 else
+                               synth.gaussian_mixture(200_000, d=d, seed=11))
+    total = warm + n_req
+    Ns = np.exp(g.uniform(np.log(2000), np.log(100_000), size=total)).astype(np.int64)
+    ds = g.choice(dims, size=total)
+    ks = g.integers(5, 33, size=total)
+    tols = g.choice([1e-4, 1e-5], size=total)
+    offs = [int(g.integers(0, 200_000 - n + 1)) for n in Ns]
+    gaps = g.exponential(1.0 / rate, size=total)
+    dm.dm_serve_start(slots=slots, hbm_budget_bytes=150_000_000_000)
+    pending, done = {}, {}
+
+    def collect():
+        for t in list(pending):
+            fin, r = dm.dm_poll(t)
+            if fin:
+                done[t] = (pending.pop(t), r["status"], r["k"], r["submit_ms"], r["start_ms"], r["done_ms"])
+                dm.dm_release(t)
+
+    try:
+        t0 = time.perf_counter()
+        due = 0.0
+        for i in range(total):
+            due += gaps[i]
+            while time.perf_counter() - t0 < due:
+                collect()
+                time.sleep(0.0002)
+            n, d = int(Ns[i]), int(ds[i])
+            t = dm.dm_submit(base[d][offs[i]:offs[i] + n], eps=-1.0, alpha=1.0, tol=float(tols[i]), leaf_size=512,
+                             max_rank=128, k=int(ks[i]), want_vectors=True, seed=i)
+            pending[t] = i
+        while pending:
+            collect()
+            time.sleep(0.0005)
+    finally:
+        dm.dm_serve_stop()
+    rec = sorted(done.values())[warm:]
+    lat = np.array([r[5] - r[3] for r in rec])
+    ok = [r for r in rec if r[1] == 0]
+    span_s = (max(r[5] for r in rec) - min(r[3] for r in rec)) / 1e3
+    by_d = {}
+    for r in rec:
+        by_d.setdefault(int(ds[r[0]]), []).append(r[5] - r[3])
+    return {"requests": len(rec), "warmup_requests": warm, "rate_per_s": rate, "slots": slots,
+            "mix": SERVE_MIX.format(dims=sorted(set(int(x) for x in dims))),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "eigenpairs_per_s": float(sum(r[2] for r in ok) / span_s),
+            "requests_per_s": len(rec) / span_s, "not_converged": sum(r[1] == -4 for r in rec),
+            "failed": sum(r[1] not in (0, -4) for r in rec),
+            "p50_ms_by_d": {str(d): float(np.percentile(v, 50)) for d, v in sorted(by_d.items())},
+            "p99_ms_by_d": {str(d): float(np.percentile(v, 99)) for d, v in sorted(by_d.items())},
+            "hbm_budget_gb": 150}
 
 
 # ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
@@ -275,7 +351,7 @@ def run_ours(args) -> int:
     mv_bytes = mv[-1][1] if mv else None
     achieved = (mv_bytes / (mv_ms * 1e-3) / 1e9) if mv_ms else None
     traffic = load_traffic()
-    roofline = {"kernel": "H-matvec (near_up_kernel + down_kernel, nrhs=1, cached leaf blocks)", "bound": "hbm",
+    roofline = {"kernel": "H-matvec (leaf_n2s_kernel + tree_kernel + near_cached_kernel chained by programmatic dependent launch; nrhs=1, cached leaf blocks)", "bound": "hbm",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
                 "traffic": traffic.get("hmatvec_bytes_per_launch") if traffic else None,
@@ -296,6 +372,9 @@ def run_ours(args) -> int:
             "lanczos_iters": st["lanczos_iters"], "converged": bool(last["conv"]),
             "ranks": {"min": st["rank_min"], "max": st["rank_max"], "mean": round(st["rank_mean"], 2)},
             "evals_head": [round(float(v), 8) for v in last["ev"][:5]]}
+    if args.serve_requests > 0 and world == 1:
+        line["serving"] = serve_run(dm, args.serve_requests, args.serve_rate, args.serve_slots,
+                                    [int(x) for x in args.serve_dims.split(",")])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
 

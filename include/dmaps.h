@@ -74,6 +74,11 @@ typedef struct dm_config {
     dm_free_fn free;      /* NULL = cudaFree */
     void *alloc_user;
     int32_t profile;      /* 1 = time every H-matvec of dm_eigs with CUDA events on the handle's stream */
+    int32_t shared_device; /* 1 = the device runs other work concurrently (other solves, other
+                              processes): each Lanczos step then runs as five ordinary launches
+                              instead of one cooperative launch whose blocks wait on one another,
+                              so it never depends on SMs that other kernels hold. 0 (default) =
+                              one cooperative launch per step. */
 } dm_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -145,6 +150,9 @@ typedef struct dm_stats {
     float ms_create, ms_tree, ms_skeleton, ms_pack, ms_eigs; /* device time of each phase */
     int32_t matvec_calls;    /* H-matvecs timed in the last dm_eigs (profile = 1) */
     float ms_matvec;         /* their summed device time */
+    int32_t hmatvec_path;    /* 0 = leaf N2S + one-cluster tree pass + near stream (the upper
+                                tree fits the cluster's shared memory), 1 = chained two-launch
+                                form (deep trees at high ranks) */
 } dm_stats;
 
 int dm_get_stats(dm_handle h, dm_stats *st);
@@ -180,6 +188,7 @@ typedef struct dm_result {
     const float *evecs;    /* N x k column-major, or NULL; library-owned until dm_release */
     double submit_ms, start_ms, done_ms;  /* wall-clock times since dm_serve_start */
     int32_t lanczos_iters;
+    const char *error;     /* message of the failing call ("" on success); library-owned */
 } dm_result;
 
 typedef struct dm_serve_config {

@@ -39,7 +39,8 @@ _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class dm_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("near_mode", C.c_int32), ("m_max", C.c_int32), ("conv_tol", C.c_double),
                 ("check_every", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p), ("alloc", _ALLOC_FN),
-                ("free", _FREE_FN), ("alloc_user", C.c_void_p), ("profile", C.c_int32)]
+                ("free", _FREE_FN), ("alloc_user", C.c_void_p), ("profile", C.c_int32),
+                ("shared_device", C.c_int32)]
 
 
 class dm_stats(C.Structure):
@@ -50,7 +51,7 @@ class dm_stats(C.Structure):
                 ("near_mode", C.c_int32), ("lanczos_iters", C.c_int32), ("converged", C.c_int32),
                 ("ms_create", C.c_float), ("ms_tree", C.c_float), ("ms_skeleton", C.c_float),
                 ("ms_pack", C.c_float), ("ms_eigs", C.c_float), ("matvec_calls", C.c_int32),
-                ("ms_matvec", C.c_float)]
+                ("ms_matvec", C.c_float), ("hmatvec_path", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -65,7 +66,7 @@ class dm_request(C.Structure):
 class dm_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("k", C.c_int32), ("N", C.c_int64), ("evals", C.POINTER(C.c_double)),
                 ("evecs", C.POINTER(C.c_float)), ("submit_ms", C.c_double), ("start_ms", C.c_double),
-                ("done_ms", C.c_double), ("lanczos_iters", C.c_int32)]
+                ("done_ms", C.c_double), ("lanczos_iters", C.c_int32), ("error", C.c_char_p)]
 
 
 class dm_serve_config(C.Structure):
@@ -429,7 +430,8 @@ def dm_poll(ticket: int):
     if not done.value:
         return False, None
     out = {"status": int(r.status), "k": int(r.k), "N": int(r.N), "submit_ms": r.submit_ms, "start_ms": r.start_ms,
-           "done_ms": r.done_ms, "lanczos_iters": int(r.lanczos_iters), "evals": None, "evecs": None}
+           "done_ms": r.done_ms, "lanczos_iters": int(r.lanczos_iters), "evals": None, "evecs": None,
+           "error": (r.error or b"").decode(errors="replace")}
     if r.evals:
         out["evals"] = np.ctypeslib.as_array(r.evals, shape=(r.k,)).copy()
     if r.evecs:

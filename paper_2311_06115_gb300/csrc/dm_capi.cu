@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <mutex>
 #include "dm_internal.cuh"
 
 cudaError_t dm_launch_dense_matvec_ws(const float *Xs, const float *sf, int64_t N, int d, const float *x, float *y,
@@ -39,6 +41,21 @@ int fail(int code, const char *fmt, ...) {
 }
 
 }  // namespace
+
+cudaError_t dm_allow_smem(const void *kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> raised;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cap = raised[std::make_pair(dev, kern)];
+    if (bytes <= cap) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+}
 
 // message + status for entry points defined in other translation units
 int dm_fail_msg(int code, const char *msg) { return fail(code, "%s", msg); }
@@ -101,6 +118,12 @@ struct dm_ctx {
     float *what = nullptr, *uhat = nullptr, *ynear = nullptr, *PT = nullptr;
     unsigned *cnt = nullptr;
     int ldt = 4;
+    int4 *tlay = nullptr;
+    int2 *town = nullptr;
+    float *timg = nullptr;
+    int *timg_off = nullptr;
+    int tree_ok = 0, tree_ls = 0, tree_smem = 0;
+    int *herr = nullptr;
     // lanczos
     DmLanczos lz{};
     bool lz_ready = false;
@@ -173,6 +196,14 @@ struct dm_ctx {
         H.uhat = uhat;
         H.ynear = ynear;
         H.cnt = cnt;
+        H.tlay = tlay;
+        H.tree_ok = tree_ok;
+        H.tree_ls = tree_ls;
+        H.tree_smem = tree_smem;
+        H.timg = timg;
+        H.town = town;
+        H.timg_off = timg_off;
+        H.err = herr;
         return H;
     }
 };
@@ -224,6 +255,88 @@ int copy_out(dm_ctx *h, void *dst, const void *src, size_t bytes) {
 }
 
 // pack blocks, permuted points and matvec workspaces for the current tree/skeletons
+// Shared-memory layout of the cluster pass over the upper tree. The tree is cut at level
+// ls = min(3, L - 1) into 2^ls subtrees; CTA c of the cluster owns the subtree under node
+// 2^ls - 1 + c (its internal nodes and its leaves' skeleton vectors). The 2^ls - 1 nodes above
+// ls are spread one per CTA and level: node i of level lv < ls goes to CTA (2i+1) 2^(ls-lv-1).
+// Each CTA's shared memory starts with the node metadata (layout and ranks of every node).
+// The children of an internal node share a slot [w_l | w_r | u_l | u_r] (lay.z below ls, a
+// scratch copy at lay.w above it); nodes at level ls keep their own [w | u] at lay.w, nodes
+// above ls at lay.z; each internal node's P (column-major, column stride rank|1) and B (row
+// stride s_r|1) follow.
+// img_off gets each CTA's offset in the image buffer (floats, multiples of 4). Returns false
+// when a CTA's share does not fit the budget (the chained two-launch path is used then).
+bool tree_layout(const std::vector<int32_t> &rk, int L, int budget_floats, std::vector<int4> &lay,
+                 std::vector<int2> &own, int &ls, int &smem_bytes, std::vector<int> &img_off) {
+    if (L < 1) return false;
+    ls = L - 1 < 3 ? L - 1 : 3;
+    const int nc = 1 << ls, nnodes = (1 << (L + 1)) - 1, ninternal = (1 << L) - 1;
+    lay.assign(nnodes, make_int4(-1, -1, -1, -1));
+    // every CTA first holds the node metadata: the layout (int4 per node), the ranks, and the
+    // offsets of each node's own w and u (int2 per node)
+    const int64_t meta = 4 * (int64_t)nnodes + ((nnodes + 3) & ~3) + 2 * (int64_t)nnodes;
+    if (meta > budget_floats / 2) return false;
+    std::vector<int64_t> used(nc, meta);
+    auto owner = [&](int n) {
+        const int lv = dm_level_of(n);
+        if (lv >= ls) return ((n + 1) >> (lv - ls)) - nc;
+        const int i = n - ((1 << lv) - 1);
+        return (2 * i + 1) * (nc >> (lv + 1));
+    };
+    for (int n = 0; n < ninternal; ++n) {
+        const int c = owner(n), lv = dm_level_of(n);
+        const int64_t pair = 2 * (int64_t)(rk[2 * n + 1] + rk[2 * n + 2]);
+        if (lv >= ls) {
+            lay[n].z = (int)used[c];  // the children's [w_l | w_r | u_l | u_r]
+            used[c] += pair;
+            if (lv == ls && n > 0) {
+                lay[n].w = (int)used[c];  // own [w | u]
+                used[c] += 2 * rk[n];
+            }
+        } else {
+            lay[n].w = (int)used[c];  // scratch copy of the children's pair
+            used[c] += pair;
+            if (n > 0) {
+                lay[n].z = (int)used[c];  // own [w | u]
+                used[c] += 2 * rk[n];
+            }
+        }
+    }
+    for (int n = 0; n < ninternal; ++n) {
+        const int c = owner(n);
+        const int sl = rk[2 * n + 1], sr = rk[2 * n + 2];
+        lay[n].y = (int)used[c];
+        used[c] += (int64_t)sl * (sr | 1);
+        if (n == 0) continue;
+        lay[n].x = (int)used[c];
+        used[c] += (int64_t)(sl + sr) * (rk[n] | 1);
+    }
+    // own [w | u] of every non-root node: levels <= ls have their own slot, deeper nodes sit in
+    // their parent's pair slot [w_l | w_r | u_l | u_r]
+    own.assign(nnodes, make_int2(-1, -1));
+    for (int n = 1; n < nnodes; ++n) {
+        const int lv = dm_level_of(n);
+        if (lv <= ls) {
+            const int w = lv == ls ? lay[n].w : lay[n].z;
+            own[n] = make_int2(w, w + rk[n]);
+        } else {
+            const int p = (n - 1) >> 1, sl = rk[2 * p + 1], sr = rk[2 * p + 2];
+            const bool left = (n & 1) != 0;
+            own[n] = make_int2(lay[p].z + (left ? 0 : sl), lay[p].z + sl + sr + (left ? 0 : sl));
+        }
+    }
+    int64_t mx = 0;
+    img_off.assign(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        used[c] = (used[c] + 3) & ~int64_t(3);
+        if (used[c] > budget_floats) return false;
+        mx = used[c] > mx ? used[c] : mx;
+        img_off[c + 1] = img_off[c] + (int)used[c];
+    }
+    smem_bytes = (int)(mx * 4);
+    return true;
+}
+
 int finish_structure(dm_ctx *h) {
     const int nnodes = (1 << (h->L + 1)) - 1;
     const int nleaves = 1 << h->L;
@@ -246,9 +359,35 @@ int finish_structure(dm_ctx *h) {
     h->rank_hi = rank_hi;
     h->ldt = (int)round_up(rank_hi, 4);
     DM_CHECK(h->alloc(&h->PT, (size_t)nleaves * h->leaf_max * h->ldt, G_STRUCT));
+    DM_CHECK(h->alloc(&h->herr, 1, G_STRUCT));
+    DM_CUDA(cudaMemsetAsync(h->herr, 0, sizeof(int), h->stream));
+    {
+        std::vector<int4> lay;
+        std::vector<int2> own;
+        std::vector<int> img_off;
+        int ls = 0, smem = 0;
+        h->tree_ok = 0;
+        if (tree_layout(rk, h->L, kTreeSmemBudget / 4, lay, own, ls, smem, img_off)) {
+            DM_CHECK(h->alloc(&h->tlay, lay.size(), G_STRUCT));
+            DM_CHECK(h->alloc(&h->town, own.size(), G_STRUCT));
+            DM_CUDA(cudaMemcpyAsync(h->town, own.data(), sizeof(int2) * own.size(), cudaMemcpyHostToDevice,
+                                    h->stream));
+            DM_CHECK(h->alloc(&h->timg_off, img_off.size(), G_STRUCT));
+            DM_CHECK(h->alloc(&h->timg, (size_t)img_off.back(), G_STRUCT));
+            DM_CUDA(cudaMemcpyAsync(h->tlay, lay.data(), sizeof(int4) * lay.size(), cudaMemcpyHostToDevice,
+                                    h->stream));
+            DM_CUDA(cudaMemcpyAsync(h->timg_off, img_off.data(), sizeof(int) * img_off.size(),
+                                    cudaMemcpyHostToDevice, h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));  // lay, own and img_off are host temporaries
+            h->tree_ok = 1;
+            h->tree_ls = ls;
+            h->tree_smem = smem;
+        }
+    }
     DmHmat H = h->hmat();
     DM_CUDA(dm_pack(H, h->Knear, h->B, cached, h->stream));
     DM_CUDA(dm_transpose_leaf_bases(H, h->PT, h->stream));
+    DM_CUDA(dm_tree_image(H, h->stream));
     int rmin = 1 << 30, rmax = 0;
     double rsum = 0;
     int64_t basis = 0, far = 0, near = 0;
@@ -285,6 +424,7 @@ int finish_structure(dm_ctx *h) {
     // weights written and read once each
     S.matvec_bytes = (cached ? near : (int64_t)h->N * (h->d + 1) * 4) + basis + far + 2 * h->N * 4 + 2 * sksum * 4 * 2;
     S.near_mode = h->near_mode;
+    S.hmatvec_path = (h->L == 0 || h->tree_ok) ? 0 : 1;
     h->compressed = true;
     return DM_OK;
 }
@@ -295,6 +435,12 @@ int alloc_structure(dm_ctx *h, int L, int max_rank) {
     h->lz_ready = false;
     h->compressed = false;
     h->Knear = nullptr;
+    h->tlay = nullptr;
+    h->town = nullptr;
+    h->timg = nullptr;
+    h->timg_off = nullptr;
+    h->herr = nullptr;
+    h->tree_ok = 0;
     h->L = L;
     h->leaf_max = (int)((h->N + ((int64_t)1 << L) - 1) >> L);
     h->ldk = (int)round_up(h->leaf_max, 4);
@@ -625,7 +771,7 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
         }
         DM_CUDA(dm_hmatvec(H, h->near_mode, Lz.V + (size_t)j * Lz.ldv, Lz.z, true, h->stream));
         if (prof) DM_CUDA(cudaEventRecord(ev_mv.back(), h->stream));
-        DM_CUDA(dm_lanczos_orth(Lz, j, h->stream));
+        DM_CUDA(dm_lanczos_orth(Lz, j, h->cfg.shared_device != 0, h->stream));
         m = j + 1;
         ritz_current = false;
         const bool last = (m == m_cap);

@@ -130,6 +130,9 @@ __device__ __forceinline__ double dm_sqdist64(const float *a, const float *b, in
 // ---------------------------------------------------------------------------
 // Device-side structure of a compressed operator (all pointers device memory).
 // ---------------------------------------------------------------------------
+// dynamic shared memory per CTA that the cluster pass over the upper tree may use
+constexpr int kTreeSmemBudget = 200 * 1024;
+
 struct DmHmat {
     int64_t N;
     int d;
@@ -154,6 +157,18 @@ struct DmHmat {
     float *uhat;           // per node max_rank: S2S parts
     float *ynear;          // N, near-field result in position order
     unsigned *cnt;         // per node arrival counters of the upward pass (zero between calls)
+    // Upper-tree layout for the cluster pass (tree_ok = 1): the tree is cut at level tree_ls
+    // into 2^tree_ls subtrees, one CTA of a cluster each; CTA 0 also owns the levels above.
+    // tlay[node] = {P offset, B offset, vector offset, mirror offset} in floats within the
+    // owning CTA's shared memory; -1 = not resident (P, B read from global memory) or none.
+    const int4 *tlay;
+    const int2 *town;      // per node: offsets of its own w and u in its owner's shared memory
+    int tree_ok;
+    int tree_ls;
+    int tree_smem;         // bytes of dynamic shared memory per CTA of the cluster pass
+    float *timg;           // per CTA: its shared-memory image (metadata, B and P operands)
+    const int *timg_off;   // 2^tree_ls + 1 offsets (floats, multiples of 4) of the images in timg
+    int *err;              // set when a bounded wait of the H-matvec gives up
 };
 
 // ---------------------------------------------------------------------------
@@ -216,6 +231,16 @@ cudaError_t dm_permute_points(const float *Xs, const float *sf, const int32_t *p
 // x, y: FP32 vectors; `permuted` = vectors are in position order (Lanczos) instead of original order.
 cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted, cudaStream_t st);
 int dm_near_rows(int near_mode, int leaf_max);
+// Raise a kernel's dynamic shared memory cap to at least `bytes` on the current device.
+// Process-wide and monotone (never lowers the cap), so concurrent solves on other host
+// threads cannot shrink it between another thread's check and its launch.
+cudaError_t dm_allow_smem(const void *kern, size_t bytes);
+// the chained two-launch form (k_hmatvec.cu), used when the cluster pass does not fit
+cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted,
+                             cudaStream_t st);
+int dm_near_item_rows(int near_mode, int leaf_max);
+// write each cluster CTA's shared-memory image of the upper tree (after packing)
+cudaError_t dm_tree_image(const DmHmat &H, cudaStream_t st);
 
 // k_lanczos.cu
 struct DmLanczos {
@@ -242,7 +267,7 @@ struct DmLanczos {
 };
 int dm_lanczos_kmax();
 cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st);
-cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st);
+cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st);
 cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st);
 cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig,
                                cudaStream_t st);

@@ -8,6 +8,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -29,6 +30,7 @@ struct Job {
     JobState state = kQueued;
     std::vector<double> evals;
     std::vector<float> evecs;
+    std::string error;
     dm_result res{};
 };
 
@@ -92,6 +94,7 @@ void run_job(Job *j, cudaStream_t stream) {
     cfg.alloc = slot_alloc;
     cfg.free = slot_free;
     cfg.alloc_user = stream;
+    cfg.shared_device = 1;  // other slots run concurrently: no cooperative launches
     dm_handle h = nullptr;
     const int k = j->req.k;
     int st = dm_create(j->points.data(), j->req.N, j->req.d, j->req.eps, j->req.alpha, &cfg, &h);
@@ -104,6 +107,7 @@ void run_job(Job *j, cudaStream_t stream) {
         dm_get_stats(h, &s);
         j->res.lanczos_iters = s.lanczos_iters;
     }
+    if (st != DM_OK && st != DM_ENOCONV) j->error = dm_last_error();
     if (h) dm_destroy(h);
     j->res.status = st;
 }
@@ -142,6 +146,7 @@ void worker_main() {
             j->res.N = j->req.N;
             j->res.evals = j->evals.empty() ? nullptr : j->evals.data();
             j->res.evecs = j->evecs.empty() ? nullptr : j->evecs.data();
+            j->res.error = j->error.c_str();
             j->state = kDone;
         }
         g_srv.cv.notify_all();
@@ -172,6 +177,8 @@ uint64_t dm_request_bytes(const dm_request *r) {
     b += 2 * r256(4 * nnodes * R) + r256(4 * N) + r256(4 * nnodes) + r256(4 * nleaves * leaf_max * ((R + 3) & ~3ull));
     // transient workspaces of the compression (skeletonization is the largest)
     b += r256(4 * nleaves * rmax * lda) + r256(4 * nleaves * R * cmax) + r256(4 * nleaves * R * rmax);
+    // the upper tree's shared-memory images (at most one cluster's shared memory)
+    b += r256((uint64_t)8 * kTreeSmemBudget) + r256(16 * nnodes) + 256;
     // Lanczos basis, Ritz vectors and small arrays
     b += r256(4 * (mmax + 1) * ldv) + r256(4 * ldv) + 2 * r256(4 * kmax * N);
     b += r256(8 * kmax * 6 * mmax) + r256(8 * kmax * mmax) + r256(4 * kmax * mmax) + 16 * 256;
@@ -221,6 +228,8 @@ int dm_serve_stop(void) {
         g_srv.stopping = true;
         for (Job *j : g_srv.queue) {
             j->res.status = DM_ESTATE;
+            j->error = "server stopped before the request ran";
+            j->res.error = j->error.c_str();
             j->state = kDone;
         }
         g_srv.queue.clear();
@@ -248,6 +257,7 @@ int dm_submit(const dm_request *r, dm_ticket *t) {
     if ((int)g_srv.queue.size() >= g_srv.capacity) return dm_fail_msg(DM_EBUSY, "request queue full");
     j->id = g_srv.next_id++;
     j->res.submit_ms = g_srv.now_ms();
+    j->res.error = j->error.c_str();
     *t = j->id;
     g_srv.queue.push_back(j.get());
     g_srv.jobs[j->id] = std::move(j);

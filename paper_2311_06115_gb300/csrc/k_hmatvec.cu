@@ -1,4 +1,6 @@
-// k_hmatvec.cu -- the hierarchical matvec y = K~ x of Eq. 2.18 (K~ = D + UV).
+// k_hmatvec.cu -- the hierarchical matvec y = K~ x of Eq. 2.18 (K~ = D + UV), chained
+// form: used when the upper tree's skeleton vectors do not fit the shared memory of the
+// cluster pass in k_htree.cu (very deep trees at high ranks).
 //
 //   near (D):  y~(I_a) = K(I_a, I_a) x~(I_a)                      every leaf a
 //   N2S  (V):  w_a = P_a x~(I_a) (leaf),  w_a = P_a [w_l; w_r] (internal)
@@ -445,7 +447,7 @@ int dm_near_rows(int near_mode, int leaf_max) {
     return (leaf_max + chunks - 1) / chunks;
 }
 
-cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted, cudaStream_t st) {
+cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted, cudaStream_t st) {
     const int nleaves = 1 << H.L;
     const int rows = dm_near_rows(near_mode, H.leaf_max);
     const int per_leaf = (H.leaf_max + rows - 1) / rows;
@@ -459,11 +461,9 @@ cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y,
         const size_t s2 = sizeof(float) * (size_t)(m4max + H.leaf_max * H.d);
         if (s2 > smem1) smem1 = s2;
     }
-    static thread_local size_t configured = 0;
-    if (smem1 > 48 * 1024 && smem1 > configured) {
-        cudaError_t e = cudaFuncSetAttribute(near_up_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    {
+        cudaError_t e = dm_allow_smem((const void *)near_up_kernel, smem1);
         if (e != cudaSuccess) return e;
-        configured = smem1;
     }
     near_up_kernel<<<nleaves + nleaves * per_leaf, kHThreads, smem1, st>>>(H, x, permuted ? 1 : 0, near_mode, rows,
                                                                             climb_smem);
@@ -474,11 +474,9 @@ cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y,
     const size_t chain = sizeof(float) * (2 * RH4 + (size_t)(H.L > 1 ? H.L - 1 : 0) * (RH4 + RH * RH4));
     const int in_smem = chain <= 160 * 1024 ? 1 : 0;
     const size_t smem2 = in_smem ? chain : sizeof(float) * 2 * RH4;
-    static thread_local size_t configured2 = 0;
-    if (smem2 > 48 * 1024 && smem2 > configured2) {
-        cudaError_t e2 = cudaFuncSetAttribute(down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    {
+        cudaError_t e2 = dm_allow_smem((const void *)down_kernel, smem2);
         if (e2 != cudaSuccess) return e2;
-        configured2 = smem2;
     }
     down_kernel<<<nleaves * kDownSplit, kDownThreads, smem2, st>>>(H, y, permuted ? 1 : 0, in_smem);
     dm_count_launches(1);

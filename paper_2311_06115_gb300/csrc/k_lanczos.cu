@@ -138,22 +138,29 @@ __device__ void block_update(const float *V, int64_t ldv, int ncols, float *z, i
 __global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, int64_t ldv, int64_t N, int j,
                                                                     float *z, double *h0, double *h1, double *nrm2,
                                                                     double *alpha, double *beta, int m_max,
-                                                                    unsigned *bar, int *err) {
+                                                                    unsigned *bar, int *err, int phase) {
+    // phase < 0: the whole step in one cooperative launch, phases separated by grid
+    // barriers; phase 0..4: that phase alone (ordinary launches, the kernel boundary
+    // is the barrier)
     extern __shared__ float sh[];  // (m_max + 1) coefficients, then (m_max + 1) partial sums
     float *acc_s = sh + (m_max + 1);
     const int ncols = j + 1;
     const int64_t per = (N + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * per, r1 = (r0 + per < N) ? r0 + per : N;
     const unsigned G = gridDim.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *nrm2 = 0.0;
-    block_project(V, ldv, ncols, z, r0, r1, h0, acc_s);
-    if (!grid_barrier(bar, G, err)) return;
-    block_update(V, ldv, ncols, z, r0, r1, h0, sh, nullptr);
-    if (!grid_barrier(bar, 2 * G, err)) return;
-    block_project(V, ldv, ncols, z, r0, r1, h1, acc_s);
-    if (!grid_barrier(bar, 3 * G, err)) return;
-    block_update(V, ldv, ncols, z, r0, r1, h1, sh, nrm2);
-    if (!grid_barrier(bar, 4 * G, err)) return;
+    const bool all = phase < 0;
+    if (all || phase == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *nrm2 = 0.0;
+        block_project(V, ldv, ncols, z, r0, r1, h0, acc_s);
+    }
+    if (all && !grid_barrier(bar, G, err)) return;
+    if (all || phase == 1) block_update(V, ldv, ncols, z, r0, r1, h0, sh, nullptr);
+    if (all && !grid_barrier(bar, 2 * G, err)) return;
+    if (all || phase == 2) block_project(V, ldv, ncols, z, r0, r1, h1, acc_s);
+    if (all && !grid_barrier(bar, 3 * G, err)) return;
+    if (all || phase == 3) block_update(V, ldv, ncols, z, r0, r1, h1, sh, nrm2);
+    if (all && !grid_barrier(bar, 4 * G, err)) return;
+    if (!all && phase != 4) return;
     const double b = sqrt(__ldcg(nrm2));
     if (j + 1 <= m_max) {
         float *vn = V + (size_t)(j + 1) * ldv;
@@ -484,7 +491,7 @@ cudaEvent_t g_coop_last = nullptr;
 
 // After Lz.z = A v_j: two Gram-Schmidt passes against V[:, 0..j], alpha_j, beta_j and
 // V[:, j+1], as one cooperative launch (grid = co-resident blocks on every SM).
-cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st) {
+cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) {
     double *h0 = Lz.h, *h1 = Lz.h + (Lz.m_max + 1);
     if (j == 0) {
         cudaError_t e0 = cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (Lz.m_max + 1), st);
@@ -505,7 +512,18 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st) {
     }
     int jj = j, mm = Lz.m_max;
     int64_t N = Lz.N, ldv = Lz.ldv;
-    void *args[] = {&Lz.V, &ldv, &N, &jj, &Lz.z, &h0, &h1, &Lz.nrm2, &Lz.alpha, &Lz.beta, &mm, &Lz.bar, &Lz.err};
+    const size_t shm = sizeof(float) * 2 * (Lz.m_max + 1);
+    if (phased) {
+        for (int ph = 0; ph < 5; ++ph) {
+            lanczos_step_kernel<<<grid, kStepThreads, shm, st>>>(Lz.V, ldv, N, jj, Lz.z, h0, h1, Lz.nrm2, Lz.alpha,
+                                                                 Lz.beta, mm, Lz.bar, Lz.err, ph);
+            dm_count_launches(1);
+        }
+        return cudaGetLastError();
+    }
+    int phase_all = -1;
+    void *args[] = {&Lz.V, &ldv, &N, &jj, &Lz.z, &h0, &h1, &Lz.nrm2, &Lz.alpha, &Lz.beta, &mm, &Lz.bar, &Lz.err,
+                    &phase_all};
     // Each step kernel fills every SM; two of them from different streams (concurrent
     // solves) could each hold part of the device while waiting at a grid barrier for
     // blocks that cannot become resident. So all step launches of the process form one
@@ -525,8 +543,8 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, cudaStream_t st) {
         e = cudaStreamWaitEvent(st, g_coop_last, 0);
         if (e != cudaSuccess) return e;
     }
-    e = cudaLaunchCooperativeKernel((const void *)lanczos_step_kernel, dim3(grid), dim3(kStepThreads), args,
-                                    sizeof(float) * 2 * (Lz.m_max + 1), st);
+    e = cudaLaunchCooperativeKernel((const void *)lanczos_step_kernel, dim3(grid), dim3(kStepThreads), args, shm,
+                                    st);
     dm_count_launches(1);
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(mine, st);
@@ -555,10 +573,8 @@ cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm,
     e = cudaMemsetAsync(best, 0, sizeof(unsigned long long) * k, st);
     if (e != cudaSuccess) return e;
     const size_t ysh = sizeof(float) * (size_t)m * k;
-    if (ysh > 48 * 1024) {
-        e = cudaFuncSetAttribute(ritzvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysh);
-        if (e != cudaSuccess) return e;
-    }
+    e = dm_allow_smem((const void *)ritzvec_kernel, ysh);
+    if (e != cudaSuccess) return e;
     ritzvec_kernel<<<nblk(Lz.N, 256), 256, ysh, st>>>(Lz.V, Lz.ldv, m, k, Lz.Yf, Lz.N, phi_work, Lz.colsum);
     dm_count_launches(1);
     const dim3 g2(nblk(Lz.N, 256), (unsigned)k);

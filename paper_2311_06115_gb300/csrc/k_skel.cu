@@ -430,7 +430,7 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     a.lda = w->lda;
     if (cmax > kSkelMaxCand || (w->lda & 3) != 0) return cudaErrorInvalidValue;
     const size_t smem = dm_skel_smem_bytes(cmax, w->rmax, max_rank);
-    cudaError_t e = cudaFuncSetAttribute(skel_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = dm_allow_smem((const void *)skel_level_kernel, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(ranks, 0, sizeof(int32_t), st);  // the root has no skeleton
     if (e != cudaSuccess) return e;

@@ -111,9 +111,28 @@ def test_hmatvec_replay_matches_oracle(dm, mode, n, leaf, rank, tol):
     y = dm.dm_matvec(h, np.asfortranarray(x))
     yr = O.hmatvec(X, eps, s, H, x.astype(np.float64))
     assert _rel_inf(y, yr, np.abs(x).max()) < 1e-5
-    # a second call reuses the arrival counters: results must not change
+    # a second call reuses the same buffers: results must not change
     y2 = dm.dm_matvec(h, np.asfortranarray(x))
     assert np.array_equal(y, y2)
+
+
+def test_hmatvec_paths_match_oracle(dm):
+    """The one-cluster tree pass (low ranks) and the chained form (a 64-d cloud at rank 128,
+    whose upper tree does not fit the cluster's shared memory) against the oracle."""
+    for X, leaf, rank, tol, path in [(_scurve(3000, 12), 128, 64, 1e-5, 0),
+                                     (synth.as_f32(synth.gaussian_mixture(4000, d=64, seed=3)), 128, 128, 0.0, 1)]:
+        n = X.shape[0]
+        eps = O.median_sqdist(X)
+        _, _, s = O.degrees(X, eps, 1.0)
+        H = O.compress(X, eps, s, leaf, tol, rank)
+        h = dm.dm_create(X, eps=eps)
+        dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+        assert dm.dm_get_stats(h)["hmatvec_path"] == path
+        x = synth.random_rhs(n, 2, seed=6).astype(np.float32)
+        y = dm.dm_matvec(h, np.asfortranarray(x))
+        yr = O.hmatvec(X, eps, s, H, x.astype(np.float64))
+        assert _rel_inf(y, yr, np.abs(x).max()) < 1e-5
+        dm.dm_destroy(h)
 
 
 # ------------------------------------------------------------------ GPU compression
