@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=WORKLOAD["N"], help="override N (testing only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-block", action="store_true", help="skip the block H-matvec and scaling-workload lines")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests in the timed serving run (after warm-up); 0 skips it")
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
@@ -180,6 +181,78 @@ def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: in
             "p50_ms_by_d": {str(d): float(np.percentile(v, 50)) for d, v in sorted(by_d.items())},
             "p99_ms_by_d": {str(d): float(np.percentile(v, 99)) for d, v in sorted(by_d.items())},
             "hbm_budget_gb": 150}
+
+
+# ------------------------------------------------------------------ block H-matvec (nrhs > 1)
+
+def _time_matvec(dm, torch, stream, h, x, reps: int) -> float:
+    """Median device time (ms) of dm_matvec(h, x) on device-resident x, CUDA events on the
+    handle's stream (the near field's side stream joins it before the call returns)."""
+    y = torch.empty_like(x)
+    for _ in range(2):
+        dm.dm_matvec(h, x, y)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dm.dm_matvec(h, x, y)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def block_run(dm, torch, stream, X, W) -> dict:
+    """The block H-matvec at the bench workload against the single-vector path: nrhs = 16
+    (FP32, the block-Lanczos width) and nrhs = 256 (TF32 tensor cores), per right-hand side."""
+    out = {}
+    N = X.shape[0]
+    g = torch.Generator(device="cuda").manual_seed(3)
+    for prec, name in ((dm.DM_PREC_FP32, "fp32"), (dm.DM_PREC_TF32, "tf32")):
+        cfg = dm.dm_config_default(stream=stream.cuda_stream, block_precision=prec, near_mode=dm.DM_NEAR_CACHED)
+        h = dm.dm_create(X, eps=-1.0, alpha=1.0, cfg=cfg)
+        dm.dm_compress(h, W["tol"], W["leaf"], W["rank"])
+        if name == "fp32":
+            x1 = torch.rand(N, device="cuda", generator=g) * 2 - 1
+            out["single_vector_ms"] = _time_matvec(dm, torch, stream, h, x1, 20)
+        for nrhs in ((16, 64) if name == "fp32" else (16, 64, 256)):
+            xb = (torch.rand(nrhs, N, device="cuda", generator=g) * 2 - 1).t()
+            ms = _time_matvec(dm, torch, stream, h, xb, 10)
+            out[f"{name}_nrhs{nrhs}_ms"] = ms
+            out[f"{name}_nrhs{nrhs}_speedup_vs_single_vector"] = out["single_vector_ms"] * nrhs / ms
+        dm.dm_destroy(h)
+    out["note"] = ("dm_matvec on device-resident blocks, CUDA-event median; speedup = nrhs single-vector "
+                   "H-matvecs (the nrhs=1 path) over one block call of the same nrhs")
+    return out
+
+
+def scaling_workload_run(dm, torch, stream) -> dict:
+    """The paper's evaluation workload of Section 4.2 (a 100k x 100k Gaussian kernel of 6-D
+    random points times a 100k x 512 block), here on the diffusion-normalised operator with
+    this library's size limits (leaf <= 512, rank <= 256)."""
+    import synth
+
+    X = synth.as_f32(synth.gaussian_cloud(100_000, d=6, seed=0))
+    res = {"workload": "6-D standard normal cloud N=100000, eps=median sq. distance, alpha=1, leaf 512, "
+                       "max rank 256, tol 1e-3, nrhs=512",
+           "paper_context": "GOFMM on one 48-core Skylake node (leaf 768, rank 768, tol 1e-3, plain Gaussian "
+                            "kernel): compression 13 s (text) / 38.4 s (figure), 100k x 512 evaluation 1.35 s "
+                            "(text) / 4.5 s (figure)"}
+    g = torch.Generator(device="cuda").manual_seed(4)
+    xb = (torch.rand(512, X.shape[0], device="cuda", generator=g) * 2 - 1).t()
+    for prec, name in ((dm.DM_PREC_TF32, "tf32"), (dm.DM_PREC_FP32, "fp32")):
+        cfg = dm.dm_config_default(stream=stream.cuda_stream, block_precision=prec, near_mode=dm.DM_NEAR_CACHED)
+        t0 = time.perf_counter()
+        h = dm.dm_create(X, eps=-1.0, alpha=1.0, cfg=cfg)
+        dm.dm_compress(h, 1e-3, 512, 256)
+        torch.cuda.synchronize()
+        if name == "tf32":
+            res["create_compress_s"] = time.perf_counter() - t0
+            st = dm.dm_get_stats(h)
+            res["ranks"] = {"min": st["rank_min"], "max": st["rank_max"], "mean": round(st["rank_mean"], 2)}
+        res[f"matvec_nrhs512_{name}_s"] = _time_matvec(dm, torch, stream, h, xb, 5) / 1e3
+        dm.dm_destroy(h)
+    return res
 
 
 # ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
@@ -372,6 +445,9 @@ def run_ours(args) -> int:
             "lanczos_iters": st["lanczos_iters"], "converged": bool(last["conv"]),
             "ranks": {"min": st["rank_min"], "max": st["rank_max"], "mean": round(st["rank_mean"], 2)},
             "evals_head": [round(float(v), 8) for v in last["ev"][:5]]}
+    if world == 1 and not args.no_block:
+        line["block_matvec"] = block_run(dm, torch, stream, X, W)
+        line["scaling_workload"] = scaling_workload_run(dm, torch, stream)
     if args.serve_requests > 0 and world == 1:
         line["serving"] = serve_run(dm, args.serve_requests, args.serve_rate, args.serve_slots,
                                     [int(x) for x in args.serve_dims.split(",")])

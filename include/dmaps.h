@@ -79,7 +79,13 @@ typedef struct dm_config {
                               instead of one cooperative launch whose blocks wait on one another,
                               so it never depends on SMs that other kernels hold. 0 (default) =
                               one cooperative launch per step. */
+    int32_t block_precision; /* near field of the block H-matvec (dm_matvec with nrhs >= 2, cached
+                                mode): DM_PREC_FP32 (default, FP32 FMA on the CUDA cores) or
+                                DM_PREC_TF32 (tcgen05 tensor cores, TF32 inputs, FP32 accumulation) */
 } dm_config;
+
+#define DM_PREC_FP32 0
+#define DM_PREC_TF32 1
 
 /* Fill *cfg with the defaults listed above. */
 void dm_config_default(dm_config *cfg);

@@ -21,7 +21,7 @@ from . import build as _build
 
 __all__ = [
     "DmError", "DM_OK", "DM_EINVAL", "DM_ENOMEM", "DM_ESTATE", "DM_ENOCONV", "DM_ETIMEOUT", "DM_ECUDA", "DM_EBUSY",
-    "DM_NEAR_AUTO", "DM_NEAR_CACHED", "DM_NEAR_ONTHEFLY", "dm_config", "dm_stats", "lib_path", "load",
+    "DM_NEAR_AUTO", "DM_NEAR_CACHED", "DM_NEAR_ONTHEFLY", "DM_PREC_FP32", "DM_PREC_TF32", "dm_config", "dm_stats", "lib_path", "load",
     "dm_config_default", "dm_create", "dm_compress", "dm_matvec", "dm_eigs", "dm_coords", "dm_destroy",
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
     "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc", "dm_request",
@@ -31,6 +31,7 @@ __all__ = [
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 DM_NEAR_AUTO, DM_NEAR_CACHED, DM_NEAR_ONTHEFLY = 0, 1, 2
+DM_PREC_FP32, DM_PREC_TF32 = 0, 1
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -40,7 +41,7 @@ class dm_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("near_mode", C.c_int32), ("m_max", C.c_int32), ("conv_tol", C.c_double),
                 ("check_every", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p), ("alloc", _ALLOC_FN),
                 ("free", _FREE_FN), ("alloc_user", C.c_void_p), ("profile", C.c_int32),
-                ("shared_device", C.c_int32)]
+                ("shared_device", C.c_int32), ("block_precision", C.c_int32)]
 
 
 class dm_stats(C.Structure):
@@ -160,8 +161,8 @@ def _ptr(a) -> int:
     """Data pointer of a numpy array or a torch tensor (must be contiguous)."""
     t = _torch()
     if t is not None and isinstance(a, t.Tensor):
-        if not a.is_contiguous():
-            raise ValueError("tensor must be contiguous")
+        if not (a.is_contiguous() or (a.ndim == 2 and a.t().is_contiguous())):
+            raise ValueError("tensor must be contiguous (row-major, or column-major for blocks)")
         return a.data_ptr()
     if isinstance(a, np.ndarray):
         if not a.flags.c_contiguous and not a.flags.f_contiguous:

@@ -75,7 +75,12 @@ namespace {
         if (_s != DM_OK) return _s; \
     } while (0)
 
-enum Group { G_BASE = 0, G_STRUCT = 1, G_WORK = 2, G_LANCZOS = 3, G_IO = 4 };
+enum Group { G_BASE = 0, G_STRUCT = 1, G_WORK = 2, G_LANCZOS = 3, G_IO = 4, G_BLOCK = 5 };
+
+// right-hand sides per block H-matvec call (wider blocks run as several panels): the FP32
+// near field tiles 64 columns, the tensor-core one up to 256 (the largest MMA N)
+constexpr int kBlockPanelFp32 = 64;
+constexpr int kBlockPanelTc = 256;
 
 struct Alloc {
     void *p;
@@ -129,6 +134,10 @@ struct dm_ctx {
     bool lz_ready = false;
     int last_k = 0;
     float *evecs = nullptr;  // N x kmax, original order, last dm_eigs
+    // block H-matvec workspace (nb_max = 0: not allocated) and its near-field stream
+    DmBlockWork blk{};
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // io staging
     float *io_x = nullptr, *io_y = nullptr;
     int64_t io_elems = 0;
@@ -137,6 +146,9 @@ struct dm_ctx {
     ~dm_ctx() {
         for (auto &a : allocs) release(a);
         allocs.clear();
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
     void release(const Alloc &a) {
@@ -431,6 +443,8 @@ int finish_structure(dm_ctx *h) {
 
 int alloc_structure(dm_ctx *h, int L, int max_rank) {
     h->free_group(G_STRUCT);
+    h->free_group(G_BLOCK);
+    h->blk.nb_max = 0;
     h->free_group(G_LANCZOS);
     h->lz_ready = false;
     h->compressed = false;
@@ -463,6 +477,32 @@ int resolve_near_mode(dm_ctx *h) {
     if (mode == DM_NEAR_ONTHEFLY && otf_smem > 200 * 1024) mode = DM_NEAR_CACHED;
     if (mode == DM_NEAR_AUTO) mode = DM_NEAR_CACHED;
     h->near_mode = mode;
+    return DM_OK;
+}
+
+// block H-matvec workspace for up to nb columns (sized for the current structure)
+int ensure_block(dm_ctx *h, int nb) {
+    if (h->blk.nb_max >= nb) return DM_OK;
+    h->free_group(G_BLOCK);
+    h->blk.nb_max = 0;
+    const DmHmat H = h->hmat();
+    const int64_t ldx = dm_block_ldx(H);
+    const size_t nnodes = ((size_t)2 << h->L) - 1;
+    DmBlockWork &W = h->blk;
+    W.ldx = ldx;
+    DM_CHECK(h->alloc(&W.Xb, (size_t)nb * ldx, G_BLOCK));
+    DM_CHECK(h->alloc(&W.Yb, (size_t)nb * ldx, G_BLOCK));
+    DM_CHECK(h->alloc(&W.Wb, nnodes * h->max_rank * nb, G_BLOCK));
+    DM_CHECK(h->alloc(&W.Ub, nnodes * h->max_rank * nb, G_BLOCK));
+    if (!h->side) {
+        DM_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        DM_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        DM_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
+    W.side = h->side;
+    W.fork = h->ev_fork;
+    W.join = h->ev_join;
+    W.nb_max = nb;
     return DM_OK;
 }
 
@@ -728,11 +768,36 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs) {
         dx = h->io_x;
     }
     if (!yd) dy = h->io_y;
-    for (int c = 0; c < nrhs; ++c) {
-        const float *xc = dx + (size_t)c * h->N;
-        float *yc = dy + (size_t)c * h->N;
-        if (h->compressed) DM_CUDA(dm_hmatvec(h->hmat(), h->near_mode, xc, yc, false, h->stream));
-        else DM_CUDA(dm_launch_dense_matvec_ws(h->Xs, h->sf, h->N, h->d, xc, yc, h->tmpw, h->acc, h->stream));
+    if (h->compressed && nrhs >= 2) {
+        // block H-matvec: every stored operand is read once per panel of columns
+        const bool tc = h->cfg.block_precision == DM_PREC_TF32 && h->near_mode == DM_NEAR_CACHED;
+        if (tc && !dm_tc_available()) return fail(DM_ECUDA, "the driver does not provide cuTensorMapEncodeTiled");
+        const int panel = tc ? kBlockPanelTc : kBlockPanelFp32;
+        const int nbp = nrhs < panel ? nrhs : panel;
+        DM_CHECK(ensure_block(h, nbp));
+        const DmHmat H = h->hmat();
+        for (int c0 = 0; c0 < nrhs; c0 += panel) {
+            const int nb = nrhs - c0 < panel ? nrhs - c0 : panel;
+            DM_CUDA(dm_hmatvec_block(H, h->near_mode, tc, h->blk, nb, dx + (size_t)c0 * h->N, h->N, h->perm,
+                                     false, dy + (size_t)c0 * h->N, h->N, true, h->stream));
+        }
+        if (tc) {
+            int err = 0;
+            DM_CUDA(cudaMemcpyAsync(&err, h->herr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            if (err) {
+                DM_CUDA(cudaMemsetAsync(h->herr, 0, sizeof(int), h->stream));
+                DM_CUDA(cudaStreamSynchronize(h->stream));
+                return fail(DM_ETIMEOUT, "a bounded wait of the tensor-core near field gave up");
+            }
+        }
+    } else {
+        for (int c = 0; c < nrhs; ++c) {
+            const float *xc = dx + (size_t)c * h->N;
+            float *yc = dy + (size_t)c * h->N;
+            if (h->compressed) DM_CUDA(dm_hmatvec(h->hmat(), h->near_mode, xc, yc, false, h->stream));
+            else DM_CUDA(dm_launch_dense_matvec_ws(h->Xs, h->sf, h->N, h->d, xc, yc, h->tmpw, h->acc, h->stream));
+        }
     }
     if (!yd) DM_CUDA(cudaMemcpyAsync(y, dy, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
     DM_CUDA(cudaStreamSynchronize(h->stream));

@@ -242,6 +242,30 @@ int dm_near_item_rows(int near_mode, int leaf_max);
 // write each cluster CTA's shared-memory image of the upper tree (after packing)
 cudaError_t dm_tree_image(const DmHmat &H, cudaStream_t st);
 
+// k_hblock.cu -- H-matvec of a block of right-hand sides
+struct DmBlockWork {
+    int nb_max;           // columns per call
+    int64_t ldx;          // column stride of the padded leaf layout (nleaves * ldk)
+    float *Xb, *Yb;       // nb_max columns of ldx floats each
+    float *Wb, *Ub;       // per node max_rank x nb_max (row-major, row stride = the call's nb)
+    cudaStream_t side;    // stream of the near-field GEMM (nullptr: the caller's stream)
+    cudaEvent_t fork, join;
+};
+int64_t dm_block_ldx(const DmHmat &H);
+// Y = K~ X for nb columns. X: original order with column stride ldin when perm_in = H.perm,
+// position order when perm_in = nullptr, or already in the padded leaf layout (x_padded,
+// column stride W.ldx). Y: original order (y_original, column stride ldo) or the padded
+// leaf layout (column stride ldo).
+// near_tc: the cached near field on the tensor cores (TF32), else FP32 on the CUDA cores.
+cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const DmBlockWork &W, int nb,
+                             const float *x, int64_t ldin, const int32_t *perm_in, bool x_padded, float *y,
+                             int64_t ldo, bool y_original, cudaStream_t st);
+// k_tc.cu: Yb = K_a Xb per leaf on tcgen05 (TF32 in, FP32 accumulate); *err set when a
+// bounded wait gave up. dm_tc_available: the driver provides cuTensorMapEncodeTiled.
+bool dm_tc_available();
+cudaError_t dm_launch_near_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, float *Yb, int *err,
+                              cudaStream_t st);
+
 // k_lanczos.cu
 struct DmLanczos {
     int64_t N;

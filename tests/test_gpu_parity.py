@@ -135,6 +135,60 @@ def test_hmatvec_paths_match_oracle(dm):
         dm.dm_destroy(h)
 
 
+@pytest.mark.parametrize("mode", ["cached", "onthefly"])
+@pytest.mark.parametrize("n,leaf,rank,tol,nrhs", [(2048, 128, 64, 1e-5, 16), (1500, 100, 40, 1e-3, 70),
+                                                  (3001, 256, 48, 1e-4, 33), (700, 64, 64, 0.0, 5)])
+def test_block_hmatvec_replay_matches_oracle(dm, mode, n, leaf, rank, tol, nrhs):
+    """The block H-matvec (every operand read once per panel of up to 64 columns; ragged
+    panels, leaves and row chunks) against the oracle's evaluation of the same structure,
+    and against the single-vector path column by column."""
+    X = _scurve(n, 13)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, leaf, tol, rank)
+    cfg = dm.dm_config_default(near_mode=dm.DM_NEAR_CACHED if mode == "cached" else dm.DM_NEAR_ONTHEFLY)
+    h = dm.dm_create(X, eps=eps, cfg=cfg)
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    x = np.asfortranarray(synth.random_rhs(n, nrhs, seed=8).astype(np.float32))
+    y = dm.dm_matvec(h, x)
+    yr = O.hmatvec(X, eps, s, H, x.astype(np.float64))
+    assert _rel_inf(y, yr, np.abs(x).max()) < 1e-5
+    for c in (0, nrhs - 1):
+        y1 = dm.dm_matvec(h, np.ascontiguousarray(x[:, c]))
+        assert _rel_inf(y[:, c], y1, np.abs(x[:, c]).max()) < 1e-5
+    dm.dm_destroy(h)
+
+
+@pytest.mark.parametrize("n,leaf,rank,tol,nrhs", [(3001, 256, 48, 1e-4, 16), (2048, 128, 64, 1e-5, 100),
+                                                  (700, 64, 64, 0.0, 300), (5000, 512, 64, 1e-5, 33)])
+def test_block_hmatvec_tf32_tensor_cores(dm, n, leaf, rank, tol, nrhs):
+    """Near field on tcgen05 (TF32 operands, FP32 accumulation): full and tail row tiles,
+    one and two column panels. Both TF32 factors are truncated to 10 mantissa bits, so
+    each near term carries a relative error below 2 * 2^-10; the bound per row is
+    2.5 * 2^-10 (S |x|)_i (all entries of S are positive, so S|x| dominates the near-field
+    magnitudes) plus the FP32 tolerance of the rest of the path."""
+    X = _scurve(n, 17)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, leaf, tol, rank)
+    cfg = dm.dm_config_default(near_mode=dm.DM_NEAR_CACHED, block_precision=dm.DM_PREC_TF32)
+    h = dm.dm_create(X, eps=eps, cfg=cfg)
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    x = np.asfortranarray(synth.random_rhs(n, nrhs, seed=9).astype(np.float32))
+    y = dm.dm_matvec(h, x)
+    y2 = dm.dm_matvec(h, x)
+    assert np.array_equal(y, y2)
+    xd = x.astype(np.float64)
+    yr = O.hmatvec(X, eps, s, H, xd)
+    for c in range(0, nrhs, max(1, nrhs // 7)):
+        bound = 2.5 * 2.0 ** -10 * O.S_matvec(X, eps, s, np.abs(xd[:, c])) + 1e-5 * np.abs(xd[:, c]).max()
+        assert np.all(np.abs(y[:, c] - yr[:, c]) <= bound), c
+    # and the error is really at TF32 level, not an FP32 path in disguise or garbage
+    err = np.abs(y - yr).max() / np.abs(x).max()
+    assert 1e-7 < err < 2e-3, err
+    dm.dm_destroy(h)
+
+
 # ------------------------------------------------------------------ GPU compression
 
 def test_gpu_compression_exact_at_full_rank(dm):
