@@ -82,6 +82,8 @@ typedef struct dm_config {
     int32_t block_precision; /* near field of the block H-matvec (dm_matvec with nrhs >= 2, cached
                                 mode): DM_PREC_FP32 (default, FP32 FMA on the CUDA cores) or
                                 DM_PREC_TF32 (tcgen05 tensor cores, TF32 inputs, FP32 accumulation) */
+    int32_t block_size;   /* dm_eigs: 0 or 1 = single-vector Lanczos (default); 2..16 = block Lanczos
+                             with this many vectors per step (one block H-matvec per step) */
 } dm_config;
 
 #define DM_PREC_FP32 0

@@ -41,7 +41,8 @@ class dm_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("near_mode", C.c_int32), ("m_max", C.c_int32), ("conv_tol", C.c_double),
                 ("check_every", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p), ("alloc", _ALLOC_FN),
                 ("free", _FREE_FN), ("alloc_user", C.c_void_p), ("profile", C.c_int32),
-                ("shared_device", C.c_int32), ("block_precision", C.c_int32)]
+                ("shared_device", C.c_int32), ("block_precision", C.c_int32),
+                ("block_size", C.c_int32)]
 
 
 class dm_stats(C.Structure):

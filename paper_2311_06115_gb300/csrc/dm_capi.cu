@@ -75,7 +75,7 @@ namespace {
         if (_s != DM_OK) return _s; \
     } while (0)
 
-enum Group { G_BASE = 0, G_STRUCT = 1, G_WORK = 2, G_LANCZOS = 3, G_IO = 4, G_BLOCK = 5 };
+enum Group { G_BASE = 0, G_STRUCT = 1, G_WORK = 2, G_LANCZOS = 3, G_IO = 4, G_BLOCK = 5, G_BLANCZOS = 6 };
 
 // right-hand sides per block H-matvec call (wider blocks run as several panels): the FP32
 // near field tiles 64 columns, the tensor-core one up to 256 (the largest MMA N)
@@ -134,6 +134,8 @@ struct dm_ctx {
     bool lz_ready = false;
     int last_k = 0;
     float *evecs = nullptr;  // N x kmax, original order, last dm_eigs
+    // block Lanczos state (bl.b = 0: not allocated)
+    DmBlockLanczos bl{};
     // block H-matvec workspace (nb_max = 0: not allocated) and its near-field stream
     DmBlockWork blk{};
     cudaStream_t side = nullptr;
@@ -445,6 +447,8 @@ int alloc_structure(dm_ctx *h, int L, int max_rank) {
     h->free_group(G_STRUCT);
     h->free_group(G_BLOCK);
     h->blk.nb_max = 0;
+    h->free_group(G_BLANCZOS);
+    h->bl.b = 0;
     h->free_group(G_LANCZOS);
     h->lz_ready = false;
     h->compressed = false;
@@ -506,6 +510,32 @@ int ensure_block(dm_ctx *h, int nb) {
     return DM_OK;
 }
 
+// block Lanczos buffers for block size b (the basis itself is the Lanczos V)
+int ensure_block_lanczos(dm_ctx *h, int b) {
+    if (h->bl.b == b) return DM_OK;
+    h->free_group(G_BLANCZOS);
+    h->bl.b = 0;
+    DmBlockLanczos &B = h->bl;
+    const int mm = h->lz.m_max;
+    int sms = 0;
+    DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    B.nparts = 2 * sms;
+    if ((int64_t)B.nparts > h->N) B.nparts = (int)h->N;
+    B.ldpart = mm + 1;
+    DM_CHECK(h->alloc(&B.Z, (size_t)b * h->lz.ldv, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.part, (size_t)B.nparts * B.ldpart * b, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.H, (size_t)B.ldpart * b, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.Rinv, (size_t)b * b, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.Bacc, (size_t)b * b, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.T, (size_t)mm * mm, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.W, (size_t)mm * mm, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.hb, (size_t)mm, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.flag, 1, G_BLANCZOS));
+    DM_CUDA(cudaMemsetAsync(B.Z, 0, sizeof(float) * (size_t)b * h->lz.ldv, h->stream));
+    B.b = b;
+    return DM_OK;
+}
+
 int ensure_lanczos(dm_ctx *h) {
     if (h->lz_ready) return DM_OK;
     const int kmax = dm_lanczos_kmax();
@@ -537,6 +567,107 @@ int ensure_lanczos(dm_ctx *h) {
     DM_CUDA(cudaMemsetAsync(L.z, 0, sizeof(float) * (size_t)L.ldv, h->stream));
     h->lz_ready = true;
     return DM_OK;
+}
+
+// dm_eigs with block Lanczos (cfg.block_size = b >= 2): per step one block H-matvec of b
+// columns, block CGS2 and CholQR2; Rayleigh-Ritz on the projected matrix every check.
+int eigs_block(dm_ctx *h, int k, double *evals, float *evecs) {
+    const int b = h->cfg.block_size;
+    if (b > dm_block_lanczos_max_b()) return fail(DM_EINVAL, "block_size must be <= %d", dm_block_lanczos_max_b());
+    DmLanczos &Lz = h->lz;
+    int m_cap = Lz.m_max;
+    if (m_cap > h->N) m_cap = (int)h->N;
+    // blocks 0..jmax of V (and of T's columns, whose last block holds B^T) fit in m_cap columns
+    const int jmax = m_cap / b - 1;
+    if (jmax < 1 || (jmax * b) < k) return fail(DM_EINVAL, "m_max too small for block_size %d and k %d", b, k);
+    DM_CHECK(ensure_block_lanczos(h, b));
+    DM_CHECK(ensure_block(h, b));
+    const bool tc = h->cfg.block_precision == DM_PREC_TF32 && h->near_mode == DM_NEAR_CACHED;
+    if (tc && !dm_tc_available()) return fail(DM_ECUDA, "the driver does not provide cuTensorMapEncodeTiled");
+    PhaseTimer t(h->stream);
+    DmBlockLanczos &B = h->bl;
+    const DmHmat H = h->hmat();
+    DM_CUDA(dm_bl_start(Lz, B, h->perm, h->cfg.seed, h->stream));
+    std::vector<double> th(k), rs(k);
+    int m = 0, flag = 0;
+    bool converged = false, ritz_current = false;
+    const bool prof = h->cfg.profile != 0;
+    std::vector<cudaEvent_t> ev_mv;
+    const int every = h->cfg.check_every / b > 1 ? h->cfg.check_every / b : 1;
+    int since = 0;
+    for (int j = 0; j < jmax; ++j) {
+        if (prof) {
+            cudaEvent_t e0, e1;
+            DM_CUDA(cudaEventCreate(&e0));
+            DM_CUDA(cudaEventCreate(&e1));
+            ev_mv.push_back(e0);
+            ev_mv.push_back(e1);
+            DM_CUDA(cudaEventRecord(e0, h->stream));
+        }
+        DM_CUDA(dm_hmatvec_block(H, h->near_mode, tc, h->blk, b, Lz.V + (size_t)j * b * Lz.ldv, Lz.ldv, nullptr,
+                                 false, B.Z, Lz.ldv, DM_BLK_POSITION, h->stream));
+        if (prof) DM_CUDA(cudaEventRecord(ev_mv.back(), h->stream));
+        DM_CUDA(dm_bl_orth(Lz, B, j, h->stream));
+        m = (j + 1) * b;
+        ritz_current = false;
+        ++since;
+        const bool last = j + 1 == jmax;
+        if (m >= 2 * k && (since >= every || last)) {
+            since = 0;
+            DM_CUDA(dm_bl_ritz(Lz, B, m, k, h->stream));
+            DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaMemcpyAsync(rs.data(), Lz.resid, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaMemcpyAsync(&flag, B.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            ritz_current = true;
+            const double scale = std::fabs(th[0]) > 0 ? std::fabs(th[0]) : 1.0;
+            bool ok = true;
+            for (int i = 0; i < k; ++i)
+                if (!(rs[i] <= h->cfg.conv_tol * scale)) ok = false;
+            if (ok || flag) {
+                converged = ok;
+                break;
+            }
+        }
+    }
+    if (!ritz_current) {
+        DM_CUDA(dm_bl_ritz(Lz, B, m, k, h->stream));
+        DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+    }
+    DM_CUDA(dm_lanczos_phi(Lz, m, k, h->perm, h->evecs, h->stream));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    if (tc) {
+        int err = 0;
+        DM_CUDA(cudaMemcpyAsync(&err, h->herr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        DM_CUDA(cudaStreamSynchronize(h->stream));
+        if (err) {
+            DM_CUDA(cudaMemsetAsync(h->herr, 0, sizeof(int), h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            return fail(DM_ETIMEOUT, "a bounded wait of the tensor-core near field gave up");
+        }
+    }
+    if (is_device_ptr(evals))
+        DM_CUDA(cudaMemcpyAsync(evals, th.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+    else
+        for (int i = 0; i < k; ++i) evals[i] = th[i];
+    if (evecs) DM_CHECK(copy_out(h, evecs, h->evecs, sizeof(float) * (size_t)k * h->N));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    h->stats.matvec_calls = 0;
+    h->stats.ms_matvec = 0.f;
+    for (size_t e = 0; e + 1 < ev_mv.size(); e += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev_mv[e], ev_mv[e + 1]) == cudaSuccess) {
+            h->stats.ms_matvec += ms;
+            h->stats.matvec_calls += 1;
+        }
+        cudaEventDestroy(ev_mv[e]);
+        cudaEventDestroy(ev_mv[e + 1]);
+    }
+    h->last_k = k;
+    h->stats.lanczos_iters = m;
+    h->stats.converged = converged ? 1 : 0;
+    h->stats.ms_eigs = t.stop();
+    return converged ? DM_OK : fail(DM_ENOCONV, "block Lanczos did not converge in %d basis vectors", m);
 }
 
 }  // namespace
@@ -779,7 +910,7 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs) {
         for (int c0 = 0; c0 < nrhs; c0 += panel) {
             const int nb = nrhs - c0 < panel ? nrhs - c0 : panel;
             DM_CUDA(dm_hmatvec_block(H, h->near_mode, tc, h->blk, nb, dx + (size_t)c0 * h->N, h->N, h->perm,
-                                     false, dy + (size_t)c0 * h->N, h->N, true, h->stream));
+                                     false, dy + (size_t)c0 * h->N, h->N, DM_BLK_ORIGINAL, h->stream));
         }
         if (tc) {
             int err = 0;
@@ -813,6 +944,7 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
     if (k > h->cfg.m_max) return fail(DM_EINVAL, "k must be <= m_max");
     DM_CHECK(set_device(h));
     DM_CHECK(ensure_lanczos(h));
+    if (h->cfg.block_size >= 2) return eigs_block(h, k, evals, evecs);
     PhaseTimer t(h->stream);
     DmLanczos &Lz = h->lz;
     const DmHmat H = h->hmat();

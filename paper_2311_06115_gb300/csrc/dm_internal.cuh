@@ -254,12 +254,13 @@ struct DmBlockWork {
 int64_t dm_block_ldx(const DmHmat &H);
 // Y = K~ X for nb columns. X: original order with column stride ldin when perm_in = H.perm,
 // position order when perm_in = nullptr, or already in the padded leaf layout (x_padded,
-// column stride W.ldx). Y: original order (y_original, column stride ldo) or the padded
-// leaf layout (column stride ldo).
+// column stride W.ldx). Y (column stride ldo): DM_BLK_ORIGINAL, DM_BLK_POSITION or
+// DM_BLK_PADDED (the padded leaf layout).
 // near_tc: the cached near field on the tensor cores (TF32), else FP32 on the CUDA cores.
+enum { DM_BLK_PADDED = 0, DM_BLK_ORIGINAL = 1, DM_BLK_POSITION = 2 };
 cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const DmBlockWork &W, int nb,
                              const float *x, int64_t ldin, const int32_t *perm_in, bool x_padded, float *y,
-                             int64_t ldo, bool y_original, cudaStream_t st);
+                             int64_t ldo, int y_layout, cudaStream_t st);
 // k_tc.cu: Yb = K_a Xb per leaf on tcgen05 (TF32 in, FP32 accumulate); *err set when a
 // bounded wait gave up. dm_tc_available: the driver provides cuTensorMapEncodeTiled.
 bool dm_tc_available();
@@ -295,6 +296,29 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st);
 cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st);
 cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig,
                                cudaStream_t st);
+// the two halves of dm_lanczos_vectors: eigenvectors of the tridiagonal (Y, FP32 copy Yf),
+// then the Ritz vectors V Yf, normalised, signed and scattered to the original order
+cudaError_t dm_lanczos_tvecs(DmLanczos &Lz, int m, int k, cudaStream_t st);
+cudaError_t dm_lanczos_phi(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig, cudaStream_t st);
+
+// k_blanczos.cu -- block Lanczos (block size b <= dm_block_lanczos_max_b()); the basis lives
+// in Lz.V (position order), the Ritz data in Lz.alpha/beta/theta/resid/Y/Yf.
+struct DmBlockLanczos {
+    int b;
+    int nparts, ldpart;   // partial-sum blocks of the projections; ldpart >= m_max + 1
+    float *Z;             // b columns of Lz.ldv
+    float *part;          // nparts x ldpart x b
+    double *H;            // ldpart x b projection coefficients (row-major)
+    double *Rinv, *Bacc;  // b x b
+    double *T, *W;        // m_max x m_max (column-major): projected matrix, tridiagonalisation work
+    double *hb;           // m_max Householder coefficients
+    int *flag;            // set when a block lost rank (breakdown)
+};
+int dm_block_lanczos_max_b();
+cudaError_t dm_bl_start(DmLanczos &Lz, DmBlockLanczos &B, const int32_t *perm, uint64_t seed, cudaStream_t st);
+cudaError_t dm_bl_cholqr(DmLanczos &Lz, DmBlockLanczos &B, int j, bool to_T, cudaStream_t st);
+cudaError_t dm_bl_orth(DmLanczos &Lz, DmBlockLanczos &B, int j, cudaStream_t st);
+cudaError_t dm_bl_ritz(DmLanczos &Lz, DmBlockLanczos &B, int m, int k, cudaStream_t st);
 cudaError_t dm_launch_coords(const float *evecs, const double *theta, const double *dg, int64_t N, int k, int t,
                              float *psi, cudaStream_t st);
 

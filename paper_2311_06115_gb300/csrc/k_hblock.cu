@@ -263,13 +263,13 @@ __global__ void __launch_bounds__(kBlkThreads) blk_near_kernel(const __grid_cons
 }
 
 // leaf S2N and output: y[c][out(i)] = Yb[c][a ldk + i] + sum_t PT_a[i][t] U_a[t][c]
-// out(i) = perm[st + i] (original order, column stride ldo), or, with perm == nullptr,
-// the padded position a ldk + i (column stride ldo; may alias Yb)
+// out(i) = perm[st + i] (original order), st + i (position order, posout), or the padded
+// position a ldk + i (may alias Yb); column stride ldo
 __global__ void __launch_bounds__(kBlkThreads) blk_s2n_out_kernel(const __grid_constant__ DmHmat H,
                                                                   const float *Yb, int64_t ldx, int nb,
                                                                   const float *__restrict__ Ub, int far,
-                                                                  const int32_t *__restrict__ perm, float *y,
-                                                                  int64_t ldo) {
+                                                                  const int32_t *__restrict__ perm, int posout,
+                                                                  float *y, int64_t ldo) {
     extern __shared__ float sm[];
     const int a = blockIdx.x, c0 = blockIdx.y * kColTile, ncol = min(kColTile, nb - c0);
     const int node = (1 << H.L) - 1 + a;
@@ -297,6 +297,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_s2n_out_kernel(const __grid_c
             const int c = c0 + lane;
             const float v = Yb[(size_t)c * ldx + (size_t)a * H.ldk + i] + (a0 + a1);
             if (perm) y[(size_t)c * ldo + perm[st + i]] = v;
+            else if (posout) y[(size_t)c * ldo + st + i] = v;
             else y[(size_t)c * ldo + (size_t)a * H.ldk + i] = v;
         }
     }
@@ -322,7 +323,7 @@ int64_t dm_block_ldx(const DmHmat &H) { return (int64_t)(1 << H.L) * H.ldk; }
 
 cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const DmBlockWork &W, int nb,
                              const float *x, int64_t ldin, const int32_t *perm_in, bool x_padded, float *y,
-                             int64_t ldo, bool y_original, cudaStream_t st) {
+                             int64_t ldo, int y_layout, cudaStream_t st) {
     if (nb < 1 || nb > W.nb_max) return cudaErrorInvalidValue;
     const int nleaves = 1 << H.L;
     const int64_t ldx = W.ldx;
@@ -379,7 +380,8 @@ cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const
     const size_t sm_one = sizeof(float) * (size_t)H.max_rank * kColTile;
     if ((e = dm_allow_smem((const void *)blk_s2n_out_kernel, sm_one)) != cudaSuccess) return e;
     blk_s2n_out_kernel<<<dim3(nleaves, cgroups), kBlkThreads, sm_one, st>>>(
-        H, W.Yb, ldx, nb, W.Ub, far ? 1 : 0, y_original ? H.perm : nullptr, y, ldo);
+        H, W.Yb, ldx, nb, W.Ub, far ? 1 : 0, y_layout == DM_BLK_ORIGINAL ? H.perm : nullptr,
+        y_layout == DM_BLK_POSITION ? 1 : 0, y, ldo);
     dm_count_launches(1);
     return cudaGetLastError();
 }

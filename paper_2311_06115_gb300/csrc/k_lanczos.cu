@@ -559,15 +559,25 @@ cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig,
-                               cudaStream_t st) {
-    float *phi_work = Lz.phi;
-    unsigned long long *best = Lz.best;
+cudaError_t dm_lanczos_tvecs(DmLanczos &Lz, int m, int k, cudaStream_t st) {
     tvec_kernel<<<k, 32, 0, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.Y, Lz.m_max, Lz.twork,
                                   dm_stream_key(0x5eedULL, DM_TAG_V0, 1));
     dm_count_launches(1);
     tvec_orth_kernel<<<1, 256, 0, st>>>(m, k, Lz.theta, Lz.Y, Lz.m_max, Lz.Yf);
     dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig,
+                               cudaStream_t st) {
+    cudaError_t e = dm_lanczos_tvecs(Lz, m, k, st);
+    if (e != cudaSuccess) return e;
+    return dm_lanczos_phi(Lz, m, k, perm, evecs_orig, st);
+}
+
+cudaError_t dm_lanczos_phi(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig, cudaStream_t st) {
+    float *phi_work = Lz.phi;
+    unsigned long long *best = Lz.best;
     cudaError_t e = cudaMemsetAsync(Lz.colsum, 0, sizeof(double) * k, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(best, 0, sizeof(unsigned long long) * k, st);

@@ -261,6 +261,39 @@ def test_eigs_replayed_structure_match_oracle_lanczos(dm):
         assert math.acos(min(1.0, c)) < 2e-3
 
 
+@pytest.mark.parametrize("b,k,prec", [(8, 10, 0), (16, 10, 0), (4, 6, 0), (16, 10, 1)])
+def test_block_lanczos_replayed_structure_match_oracle(dm, b, k, prec):
+    """Block Lanczos (b vectors per step, block H-matvec, block CGS2, CholQR2, FP64
+    Rayleigh-Ritz through Householder tridiagonalisation) finds the same eigenpairs of the
+    same operator as the oracle's single-vector Lanczos; with the TF32 near field the
+    operator itself carries TF32 rounding (terms below 2^-9 relative), so eigenvalues are
+    held to 1e-3 there."""
+    n = 2048
+    X = _scurve(n, 0)
+    eps = O.median_sqdist(X)
+    _, dg, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, 128, 1e-5, 64)
+    evo, Vo, _, sto = O.lanczos_hmat(X, eps, s, H, k, conv_tol=1e-10)
+    assert sto == 0
+    cfg = dm.dm_config_default(block_size=b, block_precision=prec, near_mode=dm.DM_NEAR_CACHED)
+    h = dm.dm_create(X, eps=eps, cfg=cfg)
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    ev, V, conv = dm.dm_eigs(h, k)
+    assert conv
+    if prec == 0:
+        np.testing.assert_allclose(ev, evo, rtol=2e-5, atol=2e-7)
+    else:
+        np.testing.assert_allclose(ev, evo, rtol=1e-3, atol=1e-6)
+    G = V.astype(np.float64).T @ V.astype(np.float64)
+    assert np.abs(G - np.eye(k)).max() < 2e-5
+    for i in range(k):
+        c = abs(float(np.dot(V[:, i].astype(np.float64), Vo[:, i])))
+        assert math.acos(min(1.0, c)) < (2e-3 if prec == 0 else 2e-2)
+    st = dm.dm_get_stats(h)
+    assert st["lanczos_iters"] % b == 0
+    dm.dm_destroy(h)
+
+
 def test_eigs_c1_workload_against_dense_oracle(dm):
     """2048-point s-curve, leaf 128, rank 64, tol 1e-5, top 10 (the small parity workload)."""
     import json
