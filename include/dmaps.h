@@ -161,6 +161,9 @@ typedef struct dm_stats {
     int32_t hmatvec_path;    /* 0 = leaf N2S + one-cluster tree pass + near stream (the upper
                                 tree fits the cluster's shared memory), 1 = chained two-launch
                                 form (deep trees at high ranks) */
+    int32_t degree_path;     /* degree passes of dm_create: 0 = CUDA cores (FP32 entries),
+                                1 = tensor cores, TF32 three-term split Gram matrix (d >= 16),
+                                2 = tensor cores, exact BF16 Gram matrix (8-bit quantised data) */
 } dm_stats;
 
 int dm_get_stats(dm_handle h, dm_stats *st);

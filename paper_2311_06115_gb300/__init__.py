@@ -53,7 +53,7 @@ class dm_stats(C.Structure):
                 ("near_mode", C.c_int32), ("lanczos_iters", C.c_int32), ("converged", C.c_int32),
                 ("ms_create", C.c_float), ("ms_tree", C.c_float), ("ms_skeleton", C.c_float),
                 ("ms_pack", C.c_float), ("ms_eigs", C.c_float), ("matvec_calls", C.c_int32),
-                ("ms_matvec", C.c_float), ("hmatvec_path", C.c_int32)]
+                ("ms_matvec", C.c_float), ("hmatvec_path", C.c_int32), ("degree_path", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

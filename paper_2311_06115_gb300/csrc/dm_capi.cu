@@ -783,10 +783,31 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
         DM_CHECK(h->alloc(&nmax, 1, G_WORK));
         DM_CHECK(h->alloc(&cwork, 8, G_WORK));
         DM_CUDA(dm_launch_center_scale(h->X, N, d, eps, h->Xs, nrm, nmax, cwork, h->stream));
-        DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, nullptr, h->q, h->stream));
-        DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
-        DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, h->qaf, h->dg, h->stream));
-        DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
+        if (d >= kDegTcMinD && dm_degtc_available()) {
+            // high dimension: the Gram matrix on the tensor cores, exp and row sums fused
+            unsigned char *work = nullptr;
+            int *derr = nullptr;
+            DM_CHECK(h->alloc(&work, dm_degtc_work_bytes(N, d), G_WORK));
+            DM_CHECK(h->alloc(&derr, 1, G_WORK));
+            DM_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), h->stream));
+            DmDegTc S{};
+            DM_CUDA(dm_degtc_prepare(h->X, N, d, eps, work, &S, h->stream));
+            DM_CUDA(dm_degtc_pass(S, nullptr, h->q, derr, h->stream));
+            DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
+            DM_CUDA(dm_degtc_pass(S, h->qaf, h->dg, derr, h->stream));
+            DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
+            int herr = 0;
+            DM_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            if (herr) return fail(DM_ETIMEOUT, "a bounded wait of the tensor-core degree pass gave up");
+            h->stats.degree_path = S.quant ? 2 : 1;
+        } else {
+            DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, nullptr, h->q, h->stream));
+            DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
+            DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, h->qaf, h->dg, h->stream));
+            DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
+            h->stats.degree_path = 0;
+        }
         h->stats.ms_create = t.stop();
         h->free_group(G_WORK);
         DM_CUDA(cudaGetLastError());

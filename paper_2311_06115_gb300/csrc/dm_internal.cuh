@@ -194,6 +194,24 @@ cudaError_t dm_launch_finish_scaling(int64_t N, const double *qa, double *dgsum,
 cudaError_t dm_launch_dense_matvec_ws(const float *Xs, const float *sf, int64_t N, int d, const float *x, float *y,
                                       float *tmpw, double *acc, cudaStream_t st);
 
+// k_degtc.cu -- degree passes of high-dimensional points on the tensor cores
+struct DmDegTc {
+    int64_t N;
+    int d, dpad, kpad;  // kpad: K of the GEMM (dpad for quantised data, 3 dpad otherwise)
+    bool quant;         // BF16-exact quantised operands (else the TF32 three-term split)
+    float kappa;        // log2(e) sigma^2 / eps
+    void *A, *B;        // N x kpad operands (BF16 or FP32)
+    float *an;          // kappa n_i
+    double *sums;       // column sums
+    unsigned *q_bad;
+};
+constexpr int kDegTcMinD = 16;  // dimensions from which the degree passes use the tensor cores
+size_t dm_degtc_work_bytes(int64_t N, int d);
+bool dm_degtc_available();
+cudaError_t dm_degtc_prepare(const float *X, int64_t N, int d, double eps, void *work, DmDegTc *S,
+                             cudaStream_t st);
+cudaError_t dm_degtc_pass(const DmDegTc &S, const float *w, double *out, int *err, cudaStream_t st);
+
 // k_tree.cu
 struct DmTreeWork {
     double *wbuf;     // N doubles

@@ -19,87 +19,16 @@
 // Every mbarrier wait is bounded (about a second of clock cycles); a wait that gives up
 // raises *err, skips the stores and still frees the tensor memory, and the host reports
 // DM_ETIMEOUT.
-#include <cuda.h>
-
 #include "dm_internal.cuh"
+#include "dm_tc.cuh"
 
 namespace {
+
+using namespace dmtc;
 
 constexpr int kTcThreads = 128;
 constexpr int kTcStages = 4;
 constexpr uint32_t kTcABytes = 128 * 128;  // 128 rows x 32 FP32
-constexpr long long kTcWaitCycles = 1ll << 31;
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
-}
-// wait until the phase with the given parity has completed; false after ~kTcWaitCycles
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-    const long long t0 = clock64();
-    while (true) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(su32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > kTcWaitCycles) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(su32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor for a K-major operand in the 128-byte swizzled layout:
-// rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), tile base 1024-byte
-// aligned; the leading byte offset is not used by this layout.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // leading byte offset (16 B; unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-    d |= (uint64_t)1 << 46;             // descriptor version
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
-    return d;
-}
-// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 template <int NT>
 __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmA8,
@@ -138,12 +67,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -215,53 +139,18 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
-                     : "memory");
+        tmem_dealloc(tmem, kTmemCols);
     }
-}
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-        else
-            cudaGetLastError();
-    }
-    return fn;
-}
-
-// 2-D FP32 tensor map: `rows` rows of `cols` elements, row stride `ld` elements, box
-// box_rows x 32 elements, 128-byte swizzle, zero fill outside
-bool make_map(CUtensorMap *tm, const float *ptr, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dims[2] = {cols, rows};
-    const cuuint64_t strides[1] = {ld * sizeof(float)};
-    const cuuint32_t box[2] = {32, box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int NT>
 cudaError_t launch_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, float *Yb, int *err, cudaStream_t st) {
     CUtensorMap tmA, tmA8, tmB;
     const uint64_t arows = (uint64_t)(1 << H.L) * H.leaf_max;
-    if (!make_map(&tmA, H.Knear, (uint64_t)H.ldk, arows, (uint64_t)H.ldk, 128) ||
-        !make_map(&tmA8, H.Knear, (uint64_t)H.ldk, arows, (uint64_t)H.ldk, 8) ||
-        !make_map(&tmB, Xb, (uint64_t)ldx, (uint64_t)nb, (uint64_t)ldx, NT))
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    if (!tc_make_map(&tmA, f32, 4, H.Knear, (uint64_t)H.ldk, arows, (uint64_t)H.ldk, 32, 128) ||
+        !tc_make_map(&tmA8, f32, 4, H.Knear, (uint64_t)H.ldk, arows, (uint64_t)H.ldk, 32, 8) ||
+        !tc_make_map(&tmB, f32, 4, Xb, (uint64_t)ldx, (uint64_t)nb, (uint64_t)ldx, 32, NT))
         return cudaErrorInvalidValue;
     const int mtiles = (H.leaf_max + 127) / 128;
     const size_t smem = 1024 + (size_t)kTcStages * (kTcABytes + NT * 128) + (2 * kTcStages + 1) * 8 + 16;
@@ -275,7 +164,7 @@ cudaError_t launch_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, flo
 
 }  // namespace
 
-bool dm_tc_available() { return encode_fn() != nullptr; }
+bool dm_tc_available() { return tc_encode_fn() != nullptr; }
 
 cudaError_t dm_launch_near_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, float *Yb, int *err,
                               cudaStream_t st) {

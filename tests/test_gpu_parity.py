@@ -69,6 +69,26 @@ def test_degrees_on_generic_dimension(dm):
     np.testing.assert_allclose(s, os_, rtol=5e-6)
 
 
+@pytest.mark.parametrize("kind,n,d", [("mnist", 3001, 784), ("mnist", 700, 200), ("mixture", 1537, 17),
+                                       ("mixture", 2000, 64), ("mixture", 999, 128)])
+def test_degrees_tensor_core_gram(dm, kind, n, d):
+    """Degree passes of d >= 16 on the tensor cores: 8-bit quantised data (MNIST-shaped) as an
+    exact BF16 Gram matrix, other data as the TF32 three-term split (relative Gram error
+    about 2^-20 of |u_i||u_j|, i.e. ~1e-6 in each exponent at eps = median). Ragged N and d
+    cover partial row/column tiles and zero-padded K."""
+    X = synth.as_f32(synth.mnist_like(n, seed=4, d=d) if kind == "mnist" else synth.gaussian_mixture(n, d=d, seed=4))
+    eps = O.median_sqdist(X)
+    h = dm.dm_create(X, eps=eps)
+    st = dm.dm_get_stats(h)
+    assert st["degree_path"] == (2 if kind == "mnist" else 1)
+    q, dg, s = dm.dm_get_degrees(h)
+    oq, odg, os_ = O.degrees(X, eps, 1.0)
+    np.testing.assert_allclose(q, oq, rtol=5e-6)
+    np.testing.assert_allclose(dg, odg, rtol=5e-6)
+    np.testing.assert_allclose(s, os_, rtol=5e-6)
+    dm.dm_destroy(h)
+
+
 def test_exact_matvec_before_compress(dm):
     n = 1200
     X = _scurve(n, 2)
