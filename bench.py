@@ -118,10 +118,13 @@ SERVE_MIX = ("N log-uniform in [2000, 100000], d from {dims} (s-curve for d=3, 8
              "for d=64), k uniform in [5, 32], tol from {{1e-4, 1e-5}}, leaf 512, rank 128, eigenvectors returned")
 
 
-def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: int = 100, seed: int = 7) -> dict:
+def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: int = 100, seed: int = 7,
+              max_arrival_s: float = 40.0, max_drain_s: float = 30.0) -> dict:
     """Submit warm + n_req requests at Poisson arrival times through dm_submit and collect them with
     dm_poll; latency = submit to done on the library's clock. Each request's points are a random
-    window of a seeded 200,000-point cloud of its dimension (generated once, before timing)."""
+    window of a seeded 200,000-point cloud of its dimension (generated once, before timing).
+    Bounded: arrivals stop after max_arrival_s and the queue is drained for at most
+    max_drain_s (then cancelled); such a run is reported as saturated."""
     import numpy as np
 
     import synth
@@ -148,11 +151,14 @@ def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: in
                 done[t] = (pending.pop(t), r["status"], r["k"], r["submit_ms"], r["start_ms"], r["done_ms"])
                 dm.dm_release(t)
 
+    submitted = 0
     try:
         t0 = time.perf_counter()
         due = 0.0
         for i in range(total):
             due += gaps[i]
+            if due > max_arrival_s:
+                break
             while time.perf_counter() - t0 < due:
                 collect()
                 time.sleep(0.0002)
@@ -160,11 +166,14 @@ def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: in
             t = dm.dm_submit(base[d][offs[i]:offs[i] + n], eps=-1.0, alpha=1.0, tol=float(tols[i]), leaf_size=512,
                              max_rank=128, k=int(ks[i]), want_vectors=True, seed=i)
             pending[t] = i
-        while pending:
+            submitted += 1
+        t1 = time.perf_counter()
+        while pending and time.perf_counter() - t1 < max_drain_s:
             collect()
             time.sleep(0.0005)
     finally:
         dm.dm_serve_stop()
+    cancelled = len(pending)
     rec = sorted(done.values())[warm:]
     lat = np.array([r[5] - r[3] for r in rec])
     ok = [r for r in rec if r[1] == 0]
@@ -172,7 +181,8 @@ def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: in
     by_d = {}
     for r in rec:
         by_d.setdefault(int(ds[r[0]]), []).append(r[5] - r[3])
-    return {"requests": len(rec), "warmup_requests": warm, "rate_per_s": rate, "slots": slots,
+    return {"requests": len(rec), "warmup_requests": warm, "submitted": submitted, "cancelled_at_stop": cancelled,
+            "saturated": bool(cancelled or submitted < total), "rate_per_s": rate, "slots": slots,
             "mix": SERVE_MIX.format(dims=sorted(set(int(x) for x in dims))),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "eigenpairs_per_s": float(sum(r[2] for r in ok) / span_s),
@@ -281,6 +291,33 @@ def scaling_workload_run(dm, torch, stream) -> dict:
         res[f"matvec_nrhs512_{name}_s"] = _time_matvec(dm, torch, stream, h, xb, 5) / 1e3
         dm.dm_destroy(h)
     return res
+
+
+def mnist_workload_run(dm, stream, reps: int = 2) -> dict:
+    """The high-dimensional workload: 60,000 MNIST-shaped vectors in R^784 (8-bit quantised,
+    ~80% zeros; synthetic stand-in for MNIST), eps = median, leaf 256, rank 128, tol 1e-4,
+    top 10; degree passes on the tensor cores (exact BF16 Gram matrix)."""
+    import synth
+
+    X = synth.as_f32(synth.mnist_like(60_000, seed=0))
+    out = {"workload": "MNIST-shaped N=60000 d=784, eps=median, alpha=1, leaf 256, rank 128, tol 1e-4, top-10"}
+    ts = []
+    for _ in range(reps):
+        cfg = dm.dm_config_default(stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        h = dm.dm_create(X, eps=-1.0, alpha=1.0, cfg=cfg)
+        dm.dm_compress(h, 1e-4, 256, 128)
+        ev, _, conv = dm.dm_eigs(h, 10, evecs=True, device_out=True)
+        ts.append(time.perf_counter() - t0)
+        st = dm.dm_get_stats(h)
+        dm.dm_destroy(h)
+    out.update({"wall_s_median": statistics.median(ts), "eigenpairs_per_s": 10 / statistics.median(ts),
+                "phases_ms": {key: round(float(st[key]), 3) for key in
+                              ("ms_create", "ms_tree", "ms_skeleton", "ms_pack", "ms_eigs")},
+                "degree_path": st["degree_path"], "converged": bool(conv), "lanczos_iters": st["lanczos_iters"],
+                "ranks": {"min": st["rank_min"], "max": st["rank_max"], "mean": round(st["rank_mean"], 2)},
+                "evals_head": [round(float(v), 8) for v in ev[:5]]})
+    return out
 
 
 # ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
@@ -474,9 +511,14 @@ def run_ours(args) -> int:
             "ranks": {"min": st["rank_min"], "max": st["rank_max"], "mean": round(st["rank_mean"], 2)},
             "evals_head": [round(float(v), 8) for v in last["ev"][:5]]}
     if world == 1 and not args.no_block:
-        line["block_matvec"] = block_run(dm, torch, stream, X, W)
-        line["block_lanczos"] = block_lanczos_run(dm, stream, X, W)
-        line["scaling_workload"] = scaling_workload_run(dm, torch, stream)
+        for key, fn in (("block_matvec", lambda: block_run(dm, torch, stream, X, W)),
+                        ("block_lanczos", lambda: block_lanczos_run(dm, stream, X, W)),
+                        ("scaling_workload", lambda: scaling_workload_run(dm, torch, stream)),
+                        ("mnist_workload", lambda: mnist_workload_run(dm, stream))):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # a failed side measurement must not hide the headline line
+                line[key] = {"error": f"{type(exc).__name__}: {exc}"}
     if args.serve_requests > 0 and world == 1:
         line["serving"] = serve_run(dm, args.serve_requests, args.serve_rate, args.serve_slots,
                                     [int(x) for x in args.serve_dims.split(",")])
