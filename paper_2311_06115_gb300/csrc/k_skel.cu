@@ -48,6 +48,7 @@ struct SkelArgs {
     float *A;   // per-CTA slot rmax x lda, row-major: A[i][j], i a sampled row, j a candidate
     float *R;   // per-CTA slot max_rank x cmax, row-major
     float *Q;   // per-CTA slot max_rank x rmax: orthonormal pivot columns, one contiguous vector each
+    int prefilled;  // 1: A already holds K(R, C) (written by fill_entries_kernel for d > 3)
 };
 
 constexpr int kSkelMaxCand = 512;  // candidates per node (leaf points or two children's skeletons)
@@ -67,6 +68,130 @@ __device__ __forceinline__ SkelSplit skel_split(int c, int r) {
     s.nsl = nsl;
     s.rps = (r + nsl - 1) / nsl;
     return s;
+}
+
+// ---- kernel entries of a block for d > 3, tiled over the coordinates ------------------
+// E[r][c] = s_row s_col 2^-|xs_row - xs_col|^2 for up to 32 rows (one CTA) and up to 512
+// columns. Both point sets are staged through shared memory 32 coordinates at a time; each
+// thread owns 4 rows x 16 columns (columns g + 32 q) of squared distances in registers.
+// Work item `mode`: 0 = the sampled block K(R, C) of node (2^level - 1 + blockIdx.x), rows
+// drawn exactly as in skel_level_kernel, into its A slot; 1 = the leaf block K(I_a, I_a) of
+// leaf blockIdx.x into its Knear slot (zero padded).
+constexpr int kFillRows = 32;
+constexpr int kFillK = 32;
+
+__global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode, float *__restrict__ Knear,
+                                                           int leaf_max, int ldk) {
+    extern __shared__ float fsm[];
+    float *xr = fsm;                                  // kFillRows x (kFillK + 1)
+    float *xc = xr + kFillRows * (kFillK + 1);         // kSkelMaxCand x (kFillK + 1)
+    int *rowpos = reinterpret_cast<int *>(xc + kSkelMaxCand * (kFillK + 1));  // kFillRows
+    int *colpos = rowpos + kFillRows;                 // kSkelMaxCand
+    __shared__ int s_c, s_r;
+    const int tid = threadIdx.x;
+    const int node = mode == 0 ? (1 << a.level) - 1 + (int)blockIdx.x : (1 << a.L) - 1 + (int)blockIdx.x;
+    int64_t st, sz;
+    dm_node_range(a.N, node, &st, &sz);
+    const int t0 = blockIdx.y * kFillRows;
+    if (tid == 0) {
+        if (mode == 0) {
+            const int64_t off = a.N - sz;
+            const int rtarget = 2 * a.max_rank + 10;
+            s_r = (int)(off <= rtarget ? off : rtarget);
+            s_c = a.level == a.L ? (int)sz : a.ranks[2 * node + 1] + a.ranks[2 * node + 2];
+        } else {
+            s_r = (int)sz;
+            s_c = (int)sz;
+        }
+    }
+    __syncthreads();
+    const int r = s_r, c = s_c;
+    if (t0 >= r && !(mode == 1 && t0 < leaf_max)) return;
+    // row and column positions
+    if (tid < kFillRows) {
+        const int t = t0 + tid;
+        int pos = -1;
+        if (t < r) {
+            if (mode == 0) {
+                const int64_t off = a.N - sz;
+                const int rtarget = 2 * a.max_rank + 10;
+                const uint64_t key = dm_stream_key(a.seed, DM_TAG_ROWS, (uint64_t)node);
+                const int64_t u = (off <= rtarget) ? (int64_t)t : (int64_t)dm_below(dm_rng(key, (uint64_t)t), (uint64_t)off);
+                pos = (int)(u < st ? u : u + sz);
+            } else {
+                pos = (int)(st + t);
+            }
+        }
+        rowpos[tid] = pos;
+    }
+    for (int j = tid; j < c; j += blockDim.x) {
+        int pos;
+        if (mode == 1 || a.level == a.L) pos = (int)(st + j);
+        else {
+            const int l = 2 * node + 1, rr = 2 * node + 2, sl = a.ranks[l];
+            pos = j < sl ? a.skel[(int64_t)l * a.max_rank + j] : a.skel[(int64_t)rr * a.max_rank + (j - sl)];
+        }
+        colpos[j] = pos;
+    }
+    __syncthreads();
+    const int rg = tid & 7, cg = tid >> 3;  // rows 4 rg .. 4 rg + 3; columns cg + 32 q
+    float acc[4][16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[i][q] = 0.f;
+    const int d = a.d;
+    for (int k0 = 0; k0 < d; k0 += kFillK) {
+        __syncthreads();
+        for (int e = tid; e < kFillRows * kFillK; e += blockDim.x) {
+            const int i = e / kFillK, k = e - i * kFillK;
+            const int pos = rowpos[i];
+            xr[i * (kFillK + 1) + k] = (pos >= 0 && k0 + k < d) ? a.Xp[(int64_t)pos * d + k0 + k] : 0.f;
+        }
+        for (int e = tid; e < c * kFillK; e += blockDim.x) {
+            const int j = e / kFillK, k = e - j * kFillK;
+            xc[j * (kFillK + 1) + k] = (k0 + k < d) ? a.Xp[(int64_t)colpos[j] * d + k0 + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kFillK; ++k) {
+            float xv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xv[i] = xr[(4 * rg + i) * (kFillK + 1) + k];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float cv = xc[(cg + 32 * q) * (kFillK + 1) + k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float t = xv[i] - cv;
+                    acc[i][q] = fmaf(t, t, acc[i][q]);
+                }
+            }
+        }
+    }
+    // entries, written with zero padding
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int t = t0 + 4 * rg + i;
+        const int pos = rowpos[4 * rg + i];
+        float *out;
+        int width;
+        if (mode == 0) {
+            if (t >= r) continue;
+            out = a.A + ((size_t)blockIdx.x * a.rmax + t) * a.lda;
+            width = (c + 3) & ~3;
+        } else {
+            if (t >= leaf_max) continue;
+            out = Knear + ((size_t)blockIdx.x * leaf_max + t) * ldk;
+            width = ldk;
+        }
+        const float si = pos >= 0 ? a.sp[pos] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int j = cg + 32 * q;
+            if (j < width) out[j] = (pos >= 0 && j < c) ? si * a.sp[colpos[j]] * dm_ex2(-acc[i][q]) : 0.f;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
@@ -142,7 +267,7 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
                 cj[q] = j < c ? C[j] : -1;
                 sj[q] = 0.f;
                 cx[q][0] = cx[q][1] = cx[q][2] = 0.f;
-                if (cj[q] >= 0) {
+                if (cj[q] >= 0 && !a.prefilled) {
                     sj[q] = a.sp[cj[q]];
                     if (small_d)
                         for (int k = 0; k < a.d; ++k) cx[q][k] = a.Xp[cj[q] * a.d + k];
@@ -152,7 +277,9 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
                 float v[4];
                 for (int q = 0; q < 4; ++q) {
                     if (cj[q] < 0) { v[q] = 0.f; continue; }
-                    if (small_d) {
+                    if (a.prefilled) {
+                        v[q] = A[(size_t)i * a.lda + j0 + q];
+                    } else if (small_d) {
                         const float t0 = cx[q][0] - xr[i * 4], t1 = cx[q][1] - xr[i * 4 + 1], t2 = cx[q][2] - xr[i * 4 + 2];
                         v[q] = xr[i * 4 + 3] * sj[q] * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2)));
                     } else {
@@ -398,6 +525,10 @@ __global__ void permute_points_kernel(const float *__restrict__ Xs, const float 
 
 }  // namespace
 
+size_t dm_fill_smem_bytes() {
+    return sizeof(float) * (size_t)(kFillRows + kSkelMaxCand) * (kFillK + 1) + sizeof(int) * (kFillRows + kSkelMaxCand);
+}
+
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
     return sizeof(float) * 4 * (size_t)kSkelThreads + sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank) +
            sizeof(float) * (size_t)(cmax + rmax + max_rank + ((cmax + 3) & ~3) + 4 * rmax);
@@ -434,8 +565,18 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(ranks, 0, sizeof(int32_t), st);  // the root has no skeleton
     if (e != cudaSuccess) return e;
+    a.prefilled = d > 3 ? 1 : 0;
+    const size_t fsmem = dm_fill_smem_bytes();
+    if (a.prefilled && (e = dm_allow_smem((const void *)fill_entries_kernel, fsmem)) != cudaSuccess) return e;
     for (int lvl = L; lvl >= 1; --lvl) {
         a.level = lvl;
+        if (a.prefilled) {
+            const int rt = 2 * max_rank + 10;
+            fill_entries_kernel<<<dim3(1u << lvl, (unsigned)((rt + kFillRows - 1) / kFillRows)), 256, fsmem, st>>>(
+                a, 0, nullptr, 0, 0);
+            dm_count_launches(1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         skel_level_kernel<<<1 << lvl, kSkelThreads, smem, st>>>(a);
         dm_count_launches(1);
         e = cudaGetLastError();
@@ -445,7 +586,20 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
 }
 
 cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cudaStream_t st) {
-    if (pack_near) {
+    if (pack_near && H.d > 3 && H.leaf_max <= kSkelMaxCand) {
+        SkelArgs a{};
+        a.Xp = H.Xs;
+        a.sp = H.sp;
+        a.N = H.N;
+        a.d = H.d;
+        a.L = H.L;
+        const size_t fsmem = dm_fill_smem_bytes();
+        cudaError_t e = dm_allow_smem((const void *)fill_entries_kernel, fsmem);
+        if (e != cudaSuccess) return e;
+        dim3 grid(1u << H.L, (unsigned)((H.leaf_max + kFillRows - 1) / kFillRows));
+        fill_entries_kernel<<<grid, 256, fsmem, st>>>(a, 1, Knear, H.leaf_max, H.ldk);
+        dm_count_launches(1);
+    } else if (pack_near) {
         dim3 grid(1u << H.L, (unsigned)((H.leaf_max + 31) / 32));
         pack_near_kernel<<<grid, 128, 0, st>>>(H.Xs, H.sp, H.N, H.d, H.L, H.leaf_max, H.ldk, Knear);
         dm_count_launches(1);

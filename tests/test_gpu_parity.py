@@ -224,9 +224,18 @@ def test_gpu_compression_exact_at_full_rank(dm):
     assert _rel_inf(y, yr, np.abs(x).max()) < 2e-5
 
 
-@pytest.mark.parametrize("n,leaf,rank,tol", [(2048, 128, 64, 1e-5), (3001, 200, 48, 1e-4)])
-def test_gpu_compression_accuracy_and_structure(dm, n, leaf, rank, tol):
-    X = _scurve(n, 4)
+@pytest.mark.parametrize("n,leaf,rank,tol,kind", [(2048, 128, 64, 1e-5, "scurve"), (3001, 200, 48, 1e-4, "scurve"),
+                                                  (2500, 160, 64, 1e-4, "mixture64"), (1800, 128, 64, 1e-4, "mnist")])
+def test_gpu_compression_accuracy_and_structure(dm, n, leaf, rank, tol, kind):
+    """GPU compression: valid structure and an error against the exact operator next to the
+    oracle's own compression; the high-dimensional cases (d = 64, 784) build their sampled
+    blocks and near blocks with the coordinate-tiled entry kernel."""
+    if kind == "scurve":
+        X = _scurve(n, 4)
+    elif kind == "mixture64":
+        X = synth.as_f32(synth.gaussian_mixture(n, d=64, seed=4))
+    else:
+        X = synth.as_f32(synth.mnist_like(n, seed=4))
     eps = O.median_sqdist(X)
     _, _, s = O.degrees(X, eps, 1.0)
     h = dm.dm_create(X, eps=eps)
