@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--n", type=int, default=WORKLOAD["N"], help="override N (testing only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-block", action="store_true", help="skip the block H-matvec and scaling-workload lines")
+    p.add_argument("--sections", default="block_matvec,block_lanczos,scaling_workload,mnist_workload",
+                   help="comma list of the side measurements to run after the headline")
+    p.add_argument("--skip-headline", action="store_true",
+                   help="profiling only: run just the side measurements (no timed headline steps)")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests in the timed serving run (after warm-up); 0 skips it")
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
@@ -470,6 +474,17 @@ def run_ours(args) -> int:
             ms = float(t.item())
         return ms, launches, mv
 
+    if args.skip_headline:
+        out = {}
+        for key in (x for x in args.sections.split(",") if x):
+            fn = {"block_matvec": lambda: block_run(dm, torch, stream, X, W),
+                  "block_lanczos": lambda: block_lanczos_run(dm, stream, X, W),
+                  "scaling_workload": lambda: scaling_workload_run(dm, torch, stream),
+                  "mnist_workload": lambda: mnist_workload_run(dm, stream)}[key]
+            out[key] = fn()
+        if rank == 0:
+            print(json.dumps({"profiling_only": True, **out}))
+        return 0
     for _ in range(args.warmup):
         step(Xd, True)
     clocks = ClockSampler(local)
@@ -511,10 +526,13 @@ def run_ours(args) -> int:
             "ranks": {"min": st["rank_min"], "max": st["rank_max"], "mean": round(st["rank_mean"], 2)},
             "evals_head": [round(float(v), 8) for v in last["ev"][:5]]}
     if world == 1 and not args.no_block:
+        wanted = set(x for x in args.sections.split(",") if x)
         for key, fn in (("block_matvec", lambda: block_run(dm, torch, stream, X, W)),
                         ("block_lanczos", lambda: block_lanczos_run(dm, stream, X, W)),
                         ("scaling_workload", lambda: scaling_workload_run(dm, torch, stream)),
                         ("mnist_workload", lambda: mnist_workload_run(dm, stream))):
+            if key not in wanted:
+                continue
             try:
                 line[key] = fn()
             except Exception as exc:  # a failed side measurement must not hide the headline line

@@ -6,8 +6,8 @@
 //   Z = K~ V_j                                    block H-matvec
 //   H = V^T Z, Z -= V H, twice (CGS2)             all (j+1) b basis columns; FP32 partial
 //                                                 sums reduced in FP64; T(:, block j) = H1 + H2
-//   Z = V_{j+1} B_j by CholQR2                    Gram in FP64, Cholesky in FP64;
-//                                                 T(block j, block j+1) = B_j^T
+//   Z = V_{j+1} B_j by CholQR2                    Gram in FP64, Cholesky in FP64
+//                                                 (B_j^T enters T through step j+1's H)
 // T = V^T K~ V is block tridiagonal up to rounding; it is kept dense (upper triangle) and
 // the Rayleigh-Ritz step reduces it to a tridiagonal matrix by Householder reflections in
 // FP64, so the FP64 Sturm-sequence solver and inverse iteration of the single-vector path
@@ -347,17 +347,19 @@ static cudaError_t project(DmLanczos &Lz, DmBlockLanczos &B, const float *A, int
     return cudaGetLastError();
 }
 
-cudaError_t dm_bl_cholqr(DmLanczos &Lz, DmBlockLanczos &B, int j, bool to_T, cudaStream_t st) {
+cudaError_t dm_bl_cholqr(DmLanczos &Lz, DmBlockLanczos &B, int j, bool next_block, cudaStream_t st) {
     // Z = V_{j+1} B_j: two rounds of (Gram, Cholesky, Z R^-1); the second writes V block j+1
     const int b = B.b;
-    float *Vn = Lz.V + (size_t)(to_T ? (j + 1) : 0) * b * Lz.ldv;
+    float *Vn = Lz.V + (size_t)(next_block ? (j + 1) : 0) * b * Lz.ldv;
     cudaError_t e;
     for (int round = 0; round < 2; ++round) {
         if ((e = project(Lz, B, B.Z, b, B.Z, false, 0, st)) != cudaSuccess) return e;
         const bool last = round == 1;
-        // B_j^T goes to rows j b .., columns (j+1) b .. of T (above the diagonal)
-        bl_chol_kernel<<<1, 32, 0, st>>>(B.H, b, B.Rinv, B.Bacc, round == 0 ? 1 : 0,
-                                         (last && to_T) ? B.T : nullptr, Lz.m_max, j * b, (j + 1) * b, B.flag);
+        // B_j itself is not written into T: the next step's projection V^T K~ V_{j+1} holds
+        // the block T(block j, block j+1) = B_j^T (and the last block column of T_m is this
+        // step's projection), so B_j only serves the residual bound
+        bl_chol_kernel<<<1, 32, 0, st>>>(B.H, b, B.Rinv, B.Bacc, round == 0 ? 1 : 0, nullptr, Lz.m_max, j * b,
+                                         (j + 1) * b, B.flag);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         bl_scale_kernel<<<nblk(Lz.N, 256), 256, 0, st>>>(B.Z, Lz.ldv, b, Lz.N, B.Rinv, last ? Vn : B.Z, Lz.ldv);
