@@ -34,38 +34,49 @@ __device__ __forceinline__ void leaf_range(const DmHmat &H, int a, int64_t *st, 
 
 // ------------------------------------------------------------------ layout changes
 
-// Xb[c][a ldk + j] = x[c ldin + perm[st_a + j]] (perm == nullptr: x is in position order)
+// Xb[c][a ldk + j] = x[c ldin + perm[st_a + j]] (perm == nullptr: x is in position order);
+// a CTA per (leaf a, column c), zero padding past the leaf
 __global__ void blk_permute_in_kernel(const __grid_constant__ DmHmat H, const float *__restrict__ x, int64_t ldin,
                                       const int32_t *__restrict__ perm, int nb, float *__restrict__ Xb,
                                       int64_t ldx) {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (p >= ldx || c >= nb) return;
-    const int a = (int)(p / H.ldk), j = (int)(p - (int64_t)a * H.ldk);
+    const int a = blockIdx.x, c = blockIdx.y;
     int64_t st;
     int m;
     leaf_range(H, a, &st, &m);
-    float v = 0.f;
-    if (j < m) v = x[(size_t)c * ldin + (perm ? perm[st + j] : st + j)];
-    Xb[(size_t)c * ldx + p] = v;
+    const float *xc = x + (size_t)c * ldin;
+    float *out = Xb + (size_t)c * ldx + (size_t)a * H.ldk;
+    for (int j = threadIdx.x; j < H.ldk; j += blockDim.x) {
+        float v = 0.f;
+        if (j < m) v = xc[perm ? perm[st + j] : st + j];
+        out[j] = v;
+    }
 }
 
 // ------------------------------------------------------------------ tree passes
 
+constexpr int kVs = kColTile + 1;  // shared-memory row stride of staged vectors (conflict-free)
+
 // out[o][lane] (= or +=) sum_k A(o, k) V[k][lane] for o < nout, where A(o, k) = A[o ao + k ak]
-// (global memory, read through L1) and V is nk x kColTile in shared memory; warps over o.
+// (global memory) and V is nk x kColTile in shared memory (row stride kVs); a warp per output
+// row: its lanes load 32 consecutive A(o, k) at once and broadcast them by shuffles, so a
+// row costs nk / 32 memory round trips instead of nk.
 __device__ __forceinline__ void blk_gemm_rows(const float *__restrict__ A, int ao, int ak, int nout, int nk,
                                               const float *V, float *out, int ldo, bool add, int ncol) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int o = warp; o < nout; o += nw) {
         const float *a = A + (size_t)o * ao;
         float a0 = 0.f, a1 = 0.f;
-        int k = 0;
-        for (; k + 1 < nk; k += 2) {
-            a0 = fmaf(__ldg(a + (size_t)k * ak), V[k * kColTile + lane], a0);
-            a1 = fmaf(__ldg(a + (size_t)(k + 1) * ak), V[(k + 1) * kColTile + lane], a1);
+        for (int k0 = 0; k0 < nk; k0 += 32) {
+            const int kk = k0 + lane;
+            const float av = kk < nk ? __ldg(a + (size_t)kk * ak) : 0.f;
+            const int kn = nk - k0 < 32 ? nk - k0 : 32;
+            int t = 0;
+            for (; t + 1 < kn; t += 2) {
+                a0 = fmaf(__shfl_sync(DM_FULL, av, t), V[(k0 + t) * kVs + lane], a0);
+                a1 = fmaf(__shfl_sync(DM_FULL, av, t + 1), V[(k0 + t + 1) * kVs + lane], a1);
+            }
+            if (t < kn) a0 = fmaf(__shfl_sync(DM_FULL, av, t), V[(k0 + t) * kVs + lane], a0);
         }
-        if (k < nk) a0 = fmaf(__ldg(a + (size_t)k * ak), V[k * kColTile + lane], a0);
         if (lane < ncol) {
             float *dst = out + (size_t)o * ldo + lane;
             *dst = add ? *dst + (a0 + a1) : (a0 + a1);
@@ -83,9 +94,10 @@ __global__ void __launch_bounds__(kBlkThreads) blk_leaf_n2s_kernel(const __grid_
     int64_t st;
     int m;
     leaf_range(H, a, &st, &m);
+    // coalesced along the leaf's positions j, transposed into rows of kVs floats
     for (int e = threadIdx.x; e < m * kColTile; e += blockDim.x) {
-        const int j = e / kColTile, c = e - j * kColTile;
-        sm[e] = c < ncol ? Xb[(size_t)(c0 + c) * ldx + (size_t)a * H.ldk + j] : 0.f;
+        const int c = e / m, j = e - c * m;
+        sm[j * kVs + c] = c < ncol ? Xb[(size_t)(c0 + c) * ldx + (size_t)a * H.ldk + j] : 0.f;
     }
     __syncthreads();
     const int s = H.ranks[node];
@@ -106,12 +118,12 @@ __global__ void __launch_bounds__(kBlkThreads) blk_up_kernel(const __grid_consta
         const int k = e / kColTile, c = e - k * kColTile;
         float v = 0.f;
         if (c < ncol) v = k < sl ? Wb[l * R + (size_t)k * nb + c0 + c] : Wb[r * R + (size_t)(k - sl) * nb + c0 + c];
-        sm[e] = v;
+        sm[k * kVs + c] = v;
     }
     __syncthreads();
     const float *Bn = H.B + (size_t)n * H.max_rank * H.max_rank;  // s_l x s_r, row-major
     // U_l = B W_r, U_r = B^T W_l (written, not accumulated: the downward pass adds later)
-    blk_gemm_rows(Bn, sr, 1, sl, sr, sm + sl * kColTile, Ub + l * R + c0, nb, false, ncol);
+    blk_gemm_rows(Bn, sr, 1, sl, sr, sm + sl * kVs, Ub + l * R + c0, nb, false, ncol);
     blk_gemm_rows(Bn, 1, sr, sr, sl, sm, Ub + r * R + c0, nb, false, ncol);
     if (n > 0)
         blk_gemm_rows(H.P + (size_t)n * H.max_rank * H.ldp, H.ldp, 1, H.ranks[n], cc, sm, Wb + n * R + c0, nb,
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_down_kernel(const __grid_cons
     const size_t R = (size_t)H.max_rank * nb;
     for (int e = threadIdx.x; e < s * kColTile; e += blockDim.x) {
         const int t = e / kColTile, c = e - t * kColTile;
-        sm[e] = c < ncol ? Ub[n * R + (size_t)t * nb + c0 + c] : 0.f;
+        sm[t * kVs + c] = c < ncol ? Ub[n * R + (size_t)t * nb + c0 + c] : 0.f;
     }
     __syncthreads();
     const float *Pn = H.P + (size_t)n * H.max_rank * H.ldp;  // s x (s_l + s_r), row-major
@@ -264,7 +276,9 @@ __global__ void __launch_bounds__(kBlkThreads) blk_near_kernel(const __grid_cons
 
 // leaf S2N and output: y[c][out(i)] = Yb[c][a ldk + i] + sum_t PT_a[i][t] U_a[t][c]
 // out(i) = perm[st + i] (original order), st + i (position order, posout), or the padded
-// position a ldk + i (may alias Yb); column stride ldo
+// position a ldk + i (may alias Yb); column stride ldo. A thread per row i of the leaf, 32
+// accumulators (the column group); U_a is staged in shared memory and read as broadcasts,
+// so the reads of Yb and the position-order writes are coalesced along the rows.
 __global__ void __launch_bounds__(kBlkThreads) blk_s2n_out_kernel(const __grid_constant__ DmHmat H,
                                                                   const float *Yb, int64_t ldx, int nb,
                                                                   const float *__restrict__ Ub, int far,
@@ -280,25 +294,33 @@ __global__ void __launch_bounds__(kBlkThreads) blk_s2n_out_kernel(const __grid_c
     const size_t R = (size_t)H.max_rank * nb;
     for (int e = threadIdx.x; e < s * kColTile; e += blockDim.x) {
         const int t = e / kColTile, c = e - t * kColTile;
-        sm[e] = c < ncol ? Ub[node * R + (size_t)t * nb + c0 + c] : 0.f;
+        sm[t * kColTile + c] = c < ncol ? Ub[node * R + (size_t)t * nb + c0 + c] : 0.f;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < m; i += nw) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        float acc[kColTile];
+#pragma unroll
+        for (int c = 0; c < kColTile; ++c) acc[c] = 0.f;
         const float *pt = H.PT + ((size_t)a * H.leaf_max + i) * H.ldt;
-        float a0 = 0.f, a1 = 0.f;
-        int t = 0;
-        for (; t + 1 < s; t += 2) {
-            a0 = fmaf(__ldg(pt + t), sm[t * kColTile + lane], a0);
-            a1 = fmaf(__ldg(pt + t + 1), sm[(t + 1) * kColTile + lane], a1);
+        for (int t = 0; t < s; ++t) {
+            const float p = __ldg(pt + t);
+            const float4 *u4 = reinterpret_cast<const float4 *>(sm + t * kColTile);
+#pragma unroll
+            for (int q = 0; q < kColTile / 4; ++q) {
+                const float4 u = u4[q];
+                acc[4 * q] = fmaf(p, u.x, acc[4 * q]);
+                acc[4 * q + 1] = fmaf(p, u.y, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(p, u.z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(p, u.w, acc[4 * q + 3]);
+            }
         }
-        if (t < s) a0 = fmaf(__ldg(pt + t), sm[t * kColTile + lane], a0);
-        if (lane < ncol) {
-            const int c = c0 + lane;
-            const float v = Yb[(size_t)c * ldx + (size_t)a * H.ldk + i] + (a0 + a1);
-            if (perm) y[(size_t)c * ldo + perm[st + i]] = v;
-            else if (posout) y[(size_t)c * ldo + st + i] = v;
-            else y[(size_t)c * ldo + (size_t)a * H.ldk + i] = v;
+        const int64_t dst = perm ? (int64_t)perm[st + i] : (posout ? st + i : (int64_t)a * H.ldk + i);
+#pragma unroll
+        for (int c = 0; c < kColTile; ++c) {
+            if (c < ncol) {
+                const size_t cc = (size_t)(c0 + c);
+                y[cc * ldo + dst] = Yb[cc * ldx + (size_t)a * H.ldk + i] + acc[c];
+            }
         }
     }
 }
@@ -330,8 +352,8 @@ cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const
     const float *Xb = x;
     cudaError_t e;
     if (!x_padded) {
-        dim3 g((unsigned)((ldx + 255) / 256), (unsigned)nb);
-        blk_permute_in_kernel<<<g, 256, 0, st>>>(H, x, ldin, perm_in, nb, W.Xb, ldx);
+        blk_permute_in_kernel<<<dim3((unsigned)nleaves, (unsigned)nb), 128, 0, st>>>(H, x, ldin, perm_in, nb, W.Xb,
+                                                                                   ldx);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         Xb = W.Xb;
@@ -354,19 +376,19 @@ cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const
     const bool far = H.L > 0;
     const unsigned cgroups = (unsigned)((nb + kColTile - 1) / kColTile);
     if (far) {
-        const size_t sm_leaf = sizeof(float) * (size_t)H.leaf_max * kColTile;
+        const size_t sm_leaf = sizeof(float) * (size_t)H.leaf_max * kVs;
         if ((e = dm_allow_smem((const void *)blk_leaf_n2s_kernel, sm_leaf)) != cudaSuccess) return e;
         blk_leaf_n2s_kernel<<<dim3(nleaves, cgroups), kBlkThreads, sm_leaf, st>>>(H, Xb, ldx, nb, W.Wb);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const size_t sm_pair = sizeof(float) * 2 * (size_t)H.max_rank * kColTile;
+        const size_t sm_pair = sizeof(float) * 2 * (size_t)H.max_rank * kVs;
         if ((e = dm_allow_smem((const void *)blk_up_kernel, sm_pair)) != cudaSuccess) return e;
         for (int lv = H.L - 1; lv >= 0; --lv) {
             blk_up_kernel<<<dim3(1u << lv, cgroups), kBlkThreads, sm_pair, st>>>(H, lv, nb, W.Wb, W.Ub);
             dm_count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        const size_t sm_one = sizeof(float) * (size_t)H.max_rank * kColTile;
+        const size_t sm_one = sizeof(float) * (size_t)H.max_rank * kVs;
         if ((e = dm_allow_smem((const void *)blk_down_kernel, sm_one)) != cudaSuccess) return e;
         for (int lv = 1; lv < H.L; ++lv) {
             blk_down_kernel<<<dim3(1u << lv, cgroups), kBlkThreads, sm_one, st>>>(H, lv, nb, W.Ub);
