@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests in the timed serving run (after warm-up); 0 skips it")
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
-    p.add_argument("--serve-slots", type=int, default=4)
+    p.add_argument("--serve-slots", type=int, default=8)
     p.add_argument("--serve-dims", default="3,64", help="point dimensions in the request mix")
     return p.parse_args()
 
