@@ -593,7 +593,8 @@ int eigs_block(dm_ctx *h, int k, double *evals, float *evecs) {
     bool converged = false, ritz_current = false;
     const bool prof = h->cfg.profile != 0;
     std::vector<cudaEvent_t> ev_mv;
-    const int every = h->cfg.check_every / b > 1 ? h->cfg.check_every / b : 1;
+    // each Rayleigh-Ritz check costs an FP64 tridiagonalisation: at most every other block
+    const int every = h->cfg.check_every / b > 2 ? h->cfg.check_every / b : 2;
     int since = 0;
     for (int j = 0; j < jmax; ++j) {
         if (prof) {

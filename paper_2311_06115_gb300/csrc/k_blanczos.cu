@@ -69,16 +69,20 @@ __global__ void __launch_bounds__(kBlThreads) bl_proj_kernel(const float *__rest
     }
 }
 
-// H[r][c] = sum_p part[p][r][c] (FP64); with T: T(row0 + r, col0 + c) += H[r][c]
+// H[r][c] = sum_p part[p][r][c] (FP64); with T: T(row0 + r, col0 + c) += H[r][c].
+// A warp per output: the lanes split the partial sums, then a warp reduction.
 __global__ void bl_reduce_kernel(const float *__restrict__ part, int nparts, int ldpart, int ncols, int b,
                                  double *__restrict__ H, double *T, int ldT, int row0, int col0) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (e >= ncols * b) return;
     const int r = e / b, c = e - r * b;
     double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += (double)part[((size_t)p * ldpart + r) * b + c];
-    H[e] = s;
-    if (T) T[(size_t)(col0 + c) * ldT + row0 + r] += s;
+    for (int p = lane; p < nparts; p += 32) s += (double)part[((size_t)p * ldpart + r) * b + c];
+    s = dm_warp_sum_d(s);
+    if (lane == 0) {
+        H[e] = s;
+        if (T) T[(size_t)(col0 + c) * ldT + row0 + r] += s;
+    }
 }
 
 // Z[c][i] -= sum_r A[r][i] H[r][c]   (thread per row)
@@ -104,63 +108,67 @@ __global__ void __launch_bounds__(kBlThreads) bl_update_kernel(const float *__re
         if (c < b) Z[(size_t)c * ldz + i] -= acc[c];
 }
 
-// Cholesky G = R^T R (FP64, one thread; b <= 16); Rinv = R^-1; Bacc = R (first) or R Bacc.
-// With T (column-major): T(row0 + c, col0 + r) = Bacc[r][c] for r <= c, i.e. B_j^T in the
-// block above the diagonal (B_j is upper triangular).
-// A pivot that is not positive (a rank-deficient block: the Krylov space is exhausted)
-// raises *flag and is replaced by a tiny positive value.
-__global__ void bl_chol_kernel(const double *__restrict__ G, int b, double *__restrict__ Rinv,
-                               double *__restrict__ Bacc, int first, double *T, int ldT, int row0, int col0,
-                               int *flag) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double R[kBlMaxB][kBlMaxB], Ri[kBlMaxB][kBlMaxB];
+// Cholesky G = R^T R (FP64; b <= 16) by one warp in shared memory: lane i owns column i of
+// R (Cholesky) and of R^-1 (triangular inverse), and row i of the product. Rinv = R^-1;
+// Bacc = R (first) or R Bacc. A pivot that is not positive (a rank-deficient block: the
+// Krylov space is exhausted) raises *flag and is replaced by a tiny positive value.
+__global__ void __launch_bounds__(32) bl_chol_kernel(const double *__restrict__ G, int b,
+                                                     double *__restrict__ Rinv, double *__restrict__ Bacc,
+                                                     int first, int *flag) {
+    __shared__ double R[kBlMaxB][kBlMaxB + 1], Ri[kBlMaxB][kBlMaxB + 1], Bo[kBlMaxB][kBlMaxB + 1];
+    const int i = threadIdx.x;
     double tr = 0.0;
-    for (int i = 0; i < b; ++i) tr += G[i * b + i];
+    for (int q = 0; q < b; ++q) tr += G[q * b + q];
     const double tiny = 1e-300 + 1e-28 * tr;
-    for (int i = 0; i < b; ++i)
-        for (int j = 0; j < b; ++j) R[i][j] = 0.0;
-    for (int j = 0; j < b; ++j) {
-        double s = G[j * b + j];
-        for (int k = 0; k < j; ++k) s -= R[k][j] * R[k][j];
-        if (!(s > tiny)) {
-            *flag = 1;
-            s = tiny;
+    if (i < b)
+        for (int q = 0; q < b; ++q) {
+            R[q][i] = 0.0;
+            Ri[q][i] = 0.0;
+            Bo[q][i] = Bacc[q * b + i];
         }
-        R[j][j] = sqrt(s);
-        for (int i = j + 1; i < b; ++i) {
+    __syncwarp();
+    for (int j = 0; j < b; ++j) {
+        // lane j: the pivot; then lanes i > j: R[j][i]
+        if (i == j) {
+            double sd = G[j * b + j];
+            for (int k = 0; k < j; ++k) sd -= R[k][j] * R[k][j];
+            if (!(sd > tiny)) {
+                *flag = 1;
+                sd = tiny;
+            }
+            R[j][j] = sqrt(sd);
+        }
+        __syncwarp();
+        if (i > j && i < b) {
             double t = G[j * b + i];
             for (int k = 0; k < j; ++k) t -= R[k][j] * R[k][i];
             R[j][i] = t / R[j][j];
         }
+        __syncwarp();
     }
-    // inverse of the upper triangular R, column by column
-    for (int i = 0; i < b; ++i)
-        for (int j = 0; j < b; ++j) Ri[i][j] = 0.0;
-    for (int j = 0; j < b; ++j) {
-        Ri[j][j] = 1.0 / R[j][j];
-        for (int i = j - 1; i >= 0; --i) {
+    // column i of R^-1: Ri[i][i] = 1 / R[i][i], then rows q = i-1 .. 0
+    if (i < b) {
+        Ri[i][i] = 1.0 / R[i][i];
+        for (int q = i - 1; q >= 0; --q) {
             double t = 0.0;
-            for (int k = i + 1; k <= j; ++k) t += R[i][k] * Ri[k][j];
-            Ri[i][j] = -t / R[i][i];
+            for (int k = q + 1; k <= i; ++k) t += R[q][k] * Ri[k][i];
+            Ri[q][i] = -t / R[q][q];
         }
     }
-    for (int i = 0; i < b; ++i)
-        for (int j = 0; j < b; ++j) Rinv[i * b + j] = Ri[i][j];
-    double Bn[kBlMaxB][kBlMaxB];
-    for (int i = 0; i < b; ++i)
-        for (int j = 0; j < b; ++j) {
-            if (first) Bn[i][j] = R[i][j];
+    __syncwarp();
+    if (i < b) {
+        for (int q = 0; q < b; ++q) Rinv[q * b + i] = Ri[q][i];
+        // row i of R (first) or R Bacc
+        for (int q = 0; q < b; ++q) {
+            double t;
+            if (first) t = R[i][q];
             else {
-                double t = 0.0;
-                for (int k = 0; k < b; ++k) t += R[i][k] * Bacc[k * b + j];
-                Bn[i][j] = t;
+                t = 0.0;
+                for (int k = i; k < b; ++k) t += R[i][k] * Bo[k][q];
             }
+            Bacc[i * b + q] = t;
         }
-    for (int i = 0; i < b; ++i)
-        for (int j = 0; j < b; ++j) Bacc[i * b + j] = Bn[i][j];
-    if (T)
-        for (int r = 0; r < b; ++r)
-            for (int c = r; c < b; ++c) T[(size_t)(col0 + r) * ldT + row0 + c] = Bn[r][c];
+    }
 }
 
 // out[c][i] = sum_{r <= c} Z[r][i] Rinv[r][c]   (thread per row)
@@ -189,6 +197,7 @@ __global__ void bl_scale_kernel(const float *__restrict__ Z, int64_t ldz, int b,
 // one CTA: W = Q^T T Q with alpha = diag, beta = subdiagonal; the reflector of step k
 // (I - hb_k v v^T, v on rows k+1..m-1) is left in column k of W below the diagonal.
 constexpr int kTrThreads = 512;
+constexpr int kTrSmemMax = 160;  // largest m whose working matrix fits in shared memory
 
 __device__ double cta_sum_d(double v, double *red) {
     v = dm_warp_sum_d(v);
@@ -202,12 +211,15 @@ __device__ double cta_sum_d(double v, double *red) {
 }
 
 __global__ void __launch_bounds__(kTrThreads) bl_tridiag_kernel(const double *__restrict__ T, int ldT, int m,
-                                                                double *W, int ldw, double *__restrict__ alpha,
+                                                                double *Wg, int ldwg, double *__restrict__ alpha,
                                                                 double *__restrict__ beta,
-                                                                double *__restrict__ hb) {
-    extern __shared__ double sv[];  // v (m), p (m)
+                                                                double *__restrict__ hb, int in_smem) {
+    extern __shared__ double sv[];  // v (m), p (m), then the m x m working matrix when in_smem
     __shared__ double red[32];
     double *v = sv, *p = sv + m;
+    // the working matrix lives in shared memory when it fits (m <= kTrSmemMax), else in W
+    double *W = in_smem ? sv + 2 * m : Wg;
+    const int ldw = in_smem ? m : ldwg;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int r = e % m, c = e / m;
         W[(size_t)c * ldw + r] = r <= c ? T[(size_t)c * ldT + r] : T[(size_t)r * ldT + c];
@@ -268,6 +280,14 @@ __global__ void __launch_bounds__(kTrThreads) bl_tridiag_kernel(const double *__
         }
         alpha[m - 1] = W[(size_t)(m - 1) * ldw + (m - 1)];
         beta[m - 1] = 0.0;
+    }
+    if (in_smem) {
+        // the reflectors (below the diagonal) for the back-transformation
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int r = e % m, c = e / m;
+            if (r > c) Wg[(size_t)c * ldwg + r] = W[(size_t)c * ldw + r];
+        }
     }
 }
 
@@ -341,8 +361,8 @@ static cudaError_t project(DmLanczos &Lz, DmBlockLanczos &B, const float *A, int
                                                      B.ldpart);
     dm_count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    bl_reduce_kernel<<<nblk((int64_t)ncols * B.b, 256), 256, 0, st>>>(B.part, B.nparts, B.ldpart, ncols, B.b, B.H,
-                                                                       to_T ? B.T : nullptr, Lz.m_max, 0, col0);
+    bl_reduce_kernel<<<nblk((int64_t)ncols * B.b, 8), 256, 0, st>>>(B.part, B.nparts, B.ldpart, ncols, B.b, B.H,
+                                                                     to_T ? B.T : nullptr, Lz.m_max, 0, col0);
     dm_count_launches(1);
     return cudaGetLastError();
 }
@@ -358,8 +378,7 @@ cudaError_t dm_bl_cholqr(DmLanczos &Lz, DmBlockLanczos &B, int j, bool next_bloc
         // B_j itself is not written into T: the next step's projection V^T K~ V_{j+1} holds
         // the block T(block j, block j+1) = B_j^T (and the last block column of T_m is this
         // step's projection), so B_j only serves the residual bound
-        bl_chol_kernel<<<1, 32, 0, st>>>(B.H, b, B.Rinv, B.Bacc, round == 0 ? 1 : 0, nullptr, Lz.m_max, j * b,
-                                         (j + 1) * b, B.flag);
+        bl_chol_kernel<<<1, 32, 0, st>>>(B.H, b, B.Rinv, B.Bacc, round == 0 ? 1 : 0, B.flag);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         bl_scale_kernel<<<nblk(Lz.N, 256), 256, 0, st>>>(B.Z, Lz.ldv, b, Lz.N, B.Rinv, last ? Vn : B.Z, Lz.ldv);
@@ -386,10 +405,11 @@ cudaError_t dm_bl_orth(DmLanczos &Lz, DmBlockLanczos &B, int j, cudaStream_t st)
 }
 
 cudaError_t dm_bl_ritz(DmLanczos &Lz, DmBlockLanczos &B, int m, int k, cudaStream_t st) {
-    const size_t sm = sizeof(double) * 2 * (size_t)m;
+    const int in_smem = m <= kTrSmemMax ? 1 : 0;
+    const size_t sm = sizeof(double) * (2 * (size_t)m + (in_smem ? (size_t)m * m : 0));
     cudaError_t e = dm_allow_smem((const void *)bl_tridiag_kernel, sm);
     if (e != cudaSuccess) return e;
-    bl_tridiag_kernel<<<1, kTrThreads, sm, st>>>(B.T, Lz.m_max, m, B.W, Lz.m_max, Lz.alpha, Lz.beta, B.hb);
+    bl_tridiag_kernel<<<1, kTrThreads, sm, st>>>(B.T, Lz.m_max, m, B.W, Lz.m_max, Lz.alpha, Lz.beta, B.hb, in_smem);
     dm_count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = dm_lanczos_ritz(Lz, m, k, 0.0, st)) != cudaSuccess) return e;

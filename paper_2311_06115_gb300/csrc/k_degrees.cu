@@ -187,30 +187,6 @@ __global__ void __launch_bounds__(kDegThreads) degree_pass_kernel(const float *_
     if (valid) atomicAdd(out + i, acc);
 }
 
-// exp2 of a packed pair on the FMA pipe, to share the work of the MUFU unit (which bounds
-// the degree passes: 16 ex2 per clock per SM). Cody-Waite style reduction x = n + f with
-// n = round(x) (adding and subtracting 1.5 * 2^23 rounds to the nearest integer), 2^f on
-// [-1/2, 1/2] by a degree-6 polynomial fitted here for minimum maximum relative error
-// (weighted least squares on Chebyshev nodes; 7.9e-8 max relative error, about 1.3 ulp, when
-// evaluated by FP32 Horner steps -- the accuracy class of ex2.approx), and 2^n applied by
-// adding n to the exponent field. Valid for |x| < 125 (normal results).
-__device__ __forceinline__ float2 dm_ex2_fma2(float2 x) {
-    const float2 big = make_float2(12582912.f, 12582912.f);  // 1.5 * 2^23
-    const float2 t = __fadd2_rn(x, big);                      // low mantissa bits hold round(x)
-    const float2 r = __fadd2_rn(t, make_float2(-12582912.f, -12582912.f));
-    const float2 f = __ffma2_rn(r, make_float2(-1.f, -1.f), x); // x - round(x), exact
-    float2 p = make_float2(1.5345810970757157e-4f, 1.5345810970757157e-4f);
-    p = __ffma2_rn(p, f, make_float2(1.3399930903688073e-3f, 1.3399930903688073e-3f));
-    p = __ffma2_rn(p, f, make_float2(9.618489071726799e-3f, 9.618489071726799e-3f));
-    p = __ffma2_rn(p, f, make_float2(5.550328642129898e-2f, 5.550328642129898e-2f));
-    p = __ffma2_rn(p, f, make_float2(2.4022646248340607e-1f, 2.4022646248340607e-1f));
-    p = __ffma2_rn(p, f, make_float2(6.931471824645996e-1f, 6.931471824645996e-1f));
-    p = __ffma2_rn(p, f, make_float2(1.f, 1.f));
-    // t's bits are 0x4B400000 + n; shifted left by 23 the constant part vanishes mod 2^32
-    return make_float2(__int_as_float(__float_as_int(p.x) + (__float_as_int(t.x) << 23)),
-                       __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
-}
-
 // d = 3 specialisation, two rows per thread in packed FP32x2 arithmetic.
 // With centred, pre-scaled coordinates u and n = |u|^2 the entry is
 //   2^-|u_i - u_j|^2 = 2^-n_i * 2^(2 u_i.u_j - n_j),
@@ -289,10 +265,8 @@ __global__ void __launch_bounds__(kD3Threads) degree_pass_d3_kernel(const float 
                 g1 = __ffma2_rn(X.x1[1], cy, g1);
                 g0 = __ffma2_rn(X.x0[0], cx, g0);
                 g1 = __ffma2_rn(X.x0[1], cx, g1);
-                // half of the entries on the MUFU unit, half on the FMA pipe (|g| <= 24 here:
-                // 2 |u_i| |u_j| + n_j with every n <= kDotFormMaxNorm)
                 const float2 e0 = make_float2(dm_ex2(g0.x), dm_ex2(g0.y));
-                const float2 e1 = dm_ex2_fma2(g1);
+                const float2 e1 = make_float2(dm_ex2(g1.x), dm_ex2(g1.y));
                 part0 = __ffma2_rn(e0, wj, part0);
                 part1 = __ffma2_rn(e1, wj, part1);
             }

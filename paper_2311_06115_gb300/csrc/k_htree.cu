@@ -43,6 +43,12 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_n2s_kernel(DmHmat H, const 
     float *sx = reinterpret_cast<float *>(smem4);
     const int nleaves = 1 << H.L;
     const int node = nleaves - 1 + blockIdx.x;
+    // blockIdx.y splits the leaf's basis rows over several CTAs (2 rows per warp each), so
+    // no warp walks more than one pair of rows: this launch is on the critical path of the
+    // matvec (the tree pass waits for it)
+    const int s = H.ranks[node];
+    const int row0 = blockIdx.y * 2 * (blockDim.x >> 5);
+    if (row0 >= s) return;
     int64_t st, sz;
     dm_node_range(H.N, node, &st, &sz);
     const int m = (int)sz, m4 = (m + 3) & ~3;
@@ -52,7 +58,6 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_n2s_kernel(DmHmat H, const 
         sx[j] = v;
     }
     __syncthreads();
-    const int s = H.ranks[node];
     const float *P = H.P + (size_t)node * H.max_rank * H.ldp;
     float *out = H.what + (size_t)node * H.max_rank;
     // warp per pair of rows; each lane issues all 16-byte loads of both rows before the sums
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_n2s_kernel(DmHmat H, const 
     const int c4 = m4 >> 2;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 *v4 = reinterpret_cast<const float4 *>(sx);
-    for (int t = 2 * warp; t < s; t += 2 * nw) {
+    for (int t = row0 + 2 * warp; t < s; t += 2 * nw * (int)gridDim.y) {
         const bool two = t + 1 < s;
         const float4 *ra = reinterpret_cast<const float4 *>(P + (size_t)t * H.ldp);
         const float4 *rb = reinterpret_cast<const float4 *>(P + (size_t)(two ? t + 1 : t) * H.ldp);
@@ -515,7 +520,9 @@ cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y,
     cudaError_t e;
     if (far) {
         const size_t smA = sizeof(float) * (size_t)((H.leaf_max + 3) & ~3);
-        leaf_n2s_kernel<<<nleaves, kLeafThreads, smA, st>>>(H, x, pm);
+        const int rows_per_cta = 2 * (kLeafThreads / 32);
+        const unsigned gy = (unsigned)((H.rank_hi + rows_per_cta - 1) / rows_per_cta);
+        leaf_n2s_kernel<<<dim3((unsigned)nleaves, gy > 0 ? gy : 1u), kLeafThreads, smA, st>>>(H, x, pm);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = dm_allow_smem((const void *)tree_kernel, (size_t)H.tree_smem)) != cudaSuccess) return e;
