@@ -135,6 +135,16 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
  * the last dm_eigs). Errors: DM_ESTATE if dm_eigs has not run; DM_EINVAL. */
 int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi);
 
+/* Leaf-size autotuner (no counterpart in the paper: GOFMM takes max_leaf_node_size from the
+ * user). For each of the ncand candidate leaf sizes, compresses the handle's operator with
+ * (tol, leaf, max_rank), times the compression and one nrhs = 1 H-matvec (median of 5, CUDA
+ * events on the handle's stream) and scores cost = compression + (2k + 20) H-matvecs, the
+ * usual Lanczos step count for k pairs. *best_leaf gets the cheapest candidate and the
+ * handle is left compressed with it; cost_ms (may be NULL) gets every candidate's score.
+ * Errors: DM_EINVAL (no candidates, k < 1, a candidate dm_compress rejects); DM_ECUDA. */
+int dm_tune_leaf(dm_handle h, double tol, int32_t max_rank, int32_t k, const int32_t *candidates, int32_t ncand,
+                 int32_t *best_leaf, float *cost_ms);
+
 /* Release every device buffer of the handle. */
 int dm_destroy(dm_handle h);
 
@@ -189,6 +199,7 @@ typedef struct dm_request {
     int32_t k;             /* eigenpairs wanted (as dm_eigs) */
     int32_t want_vectors;  /* 1: return the N x k eigenvectors too */
     uint64_t seed;
+    int32_t block_size;    /* as dm_config.block_size: 0/1 single-vector, 2..16 block Lanczos */
 } dm_request;
 
 typedef struct dm_result {

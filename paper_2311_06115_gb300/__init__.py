@@ -26,7 +26,7 @@ __all__ = [
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
     "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc", "dm_request",
     "dm_result", "dm_serve_config", "dm_request_bytes", "dm_serve_start", "dm_serve_stop", "dm_submit", "dm_poll",
-    "dm_release",
+    "dm_release", "dm_tune_leaf",
 ]
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
@@ -62,7 +62,7 @@ class dm_stats(C.Structure):
 class dm_request(C.Structure):
     _fields_ = [("points", C.c_void_p), ("N", C.c_int64), ("d", C.c_int32), ("eps", C.c_double),
                 ("alpha", C.c_double), ("tol", C.c_double), ("leaf_size", C.c_int32), ("max_rank", C.c_int32),
-                ("k", C.c_int32), ("want_vectors", C.c_int32), ("seed", C.c_uint64)]
+                ("k", C.c_int32), ("want_vectors", C.c_int32), ("seed", C.c_uint64), ("block_size", C.c_int32)]
 
 
 class dm_result(C.Structure):
@@ -125,6 +125,7 @@ def load(build_if_missing: bool = True):
         "dm_submit": (i32, [C.POINTER(dm_request), C.POINTER(C.c_uint64)]),
         "dm_poll": (i32, [C.c_uint64, C.POINTER(dm_result), C.POINTER(i32)]),
         "dm_release": (i32, [C.c_uint64]),
+        "dm_tune_leaf": (i32, [vp, f64, i32, i32, vp, i32, C.POINTER(i32), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -318,6 +319,16 @@ def dm_coords(h: Handle, k: int, t: int = 1) -> np.ndarray:
     return psi.T
 
 
+def dm_tune_leaf(h: Handle, tol: float, max_rank: int, k: int, candidates=(64, 128, 256, 512)):
+    """Leaf-size autotuner: (best leaf, {leaf: cost in ms}); the handle stays compressed with the best."""
+    cand = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32))
+    cost = np.zeros(len(cand), dtype=np.float32)
+    best = C.c_int32()
+    _check(load().dm_tune_leaf(h, float(tol), int(max_rank), int(k), cand.ctypes.data, len(cand), C.byref(best),
+                               cost.ctypes.data))
+    return int(best.value), {int(c): float(v) for c, v in zip(cand, cost)}
+
+
 def dm_destroy(h: Handle) -> None:
     if h.ptr:
         _check(load().dm_destroy(h))
@@ -392,11 +403,12 @@ def dm_load_hmatrix(h: Handle, L: int, max_rank: int, perm, ranks, skel, P) -> N
 
 # ------------------------------------------------------------------ serving
 
-def _request(points, eps=-1.0, alpha=1.0, tol=1e-5, leaf_size=512, max_rank=128, k=10, want_vectors=True, seed=0):
+def _request(points, eps=-1.0, alpha=1.0, tol=1e-5, leaf_size=512, max_rank=128, k=10, want_vectors=True, seed=0,
+             block_size=0):
     pts = np.ascontiguousarray(points, dtype=np.float32)
     r = dm_request(points=pts.ctypes.data, N=pts.shape[0], d=pts.shape[1], eps=float(eps), alpha=float(alpha),
                    tol=float(tol), leaf_size=int(leaf_size), max_rank=int(max_rank), k=int(k),
-                   want_vectors=1 if want_vectors else 0, seed=int(seed))
+                   want_vectors=1 if want_vectors else 0, seed=int(seed), block_size=int(block_size))
     return r, pts
 
 

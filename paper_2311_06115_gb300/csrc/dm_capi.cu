@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include <map>
@@ -1051,6 +1052,52 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
     h->stats.converged = converged ? 1 : 0;
     h->stats.ms_eigs = t.stop();
     return converged ? DM_OK : fail(DM_ENOCONV, "Lanczos did not converge in %d steps", m);
+}
+
+int dm_tune_leaf(dm_handle h, double tol, int32_t max_rank, int32_t k, const int32_t *candidates, int32_t ncand,
+                 int32_t *best_leaf, float *cost_ms) {
+    if (!h || !candidates || !best_leaf) return fail(DM_EINVAL, "NULL argument");
+    if (ncand < 1 || k < 1) return fail(DM_EINVAL, "need at least one candidate and k >= 1");
+    DM_CHECK(set_device(h));
+    float *xv = nullptr, *yv = nullptr;
+    std::vector<float> costs((size_t)ncand);
+    int best = -1;
+    for (int c = 0; c < ncand; ++c) {
+        DM_CHECK(dm_compress(h, tol, candidates[c], max_rank));
+        const float ms_c = h->stats.ms_tree + h->stats.ms_skeleton + h->stats.ms_pack;
+        if (!xv) {
+            // vectors live with the structure group (freed by the next compression)
+            DM_CHECK(ensure_io(h, h->N));
+            xv = h->io_x;
+            yv = h->io_y;
+            DM_CUDA(cudaMemsetAsync(xv, 0, sizeof(float) * (size_t)h->N, h->stream));
+        }
+        const DmHmat H = h->hmat();
+        std::vector<float> ts;
+        cudaEvent_t e0, e1;
+        DM_CUDA(cudaEventCreate(&e0));
+        DM_CUDA(cudaEventCreate(&e1));
+        for (int r = 0; r < 6; ++r) {
+            DM_CUDA(cudaEventRecord(e0, h->stream));
+            DM_CUDA(dm_hmatvec(H, h->near_mode, xv, yv, true, h->stream));
+            DM_CUDA(cudaEventRecord(e1, h->stream));
+            DM_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            DM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) ts.push_back(ms);  // the first call warms up
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::sort(ts.begin(), ts.end());
+        const float ms_mv = ts[ts.size() / 2];
+        costs[(size_t)c] = ms_c + (float)(2 * k + 20) * ms_mv;
+        if (best < 0 || costs[(size_t)c] < costs[(size_t)best]) best = c;
+    }
+    if (best != ncand - 1) DM_CHECK(dm_compress(h, tol, candidates[best], max_rank));
+    *best_leaf = candidates[best];
+    if (cost_ms)
+        for (int c = 0; c < ncand; ++c) cost_ms[c] = costs[(size_t)c];
+    return DM_OK;
 }
 
 int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi) {

@@ -58,7 +58,7 @@ Server g_srv;
 bool valid_request(const dm_request *r) {
     return r && r->points && r->N >= 2 && r->d >= 1 && r->alpha >= 0.0 && r->tol >= 0.0 && r->leaf_size >= 1 &&
            r->max_rank >= 1 && r->max_rank <= 256 && r->k >= 1 && r->k < r->N && r->k <= dm_lanczos_kmax() &&
-           r->N <= (int64_t)0x7fffffff;
+           r->N <= (int64_t)0x7fffffff && r->block_size >= 0 && r->block_size <= 16;
 }
 
 // pick the first queued job that fits (caller holds the lock); nullptr if none
@@ -95,6 +95,7 @@ void run_job(Job *j, cudaStream_t stream) {
     cfg.free = slot_free;
     cfg.alloc_user = stream;
     cfg.shared_device = 1;  // other slots run concurrently: no cooperative launches
+    cfg.block_size = j->req.block_size;
     dm_handle h = nullptr;
     const int k = j->req.k;
     int st = dm_create(j->points.data(), j->req.N, j->req.d, j->req.eps, j->req.alpha, &cfg, &h);
@@ -182,6 +183,13 @@ uint64_t dm_request_bytes(const dm_request *r) {
     // Lanczos basis, Ritz vectors and small arrays
     b += r256(4 * (mmax + 1) * ldv) + r256(4 * ldv) + 2 * r256(4 * kmax * N);
     b += r256(8 * kmax * 6 * mmax) + r256(8 * kmax * mmax) + r256(4 * kmax * mmax) + 16 * 256;
+    if (r->block_size >= 2) {
+        // block Lanczos: work block, projection partials (2 per SM), T and its reduction, and
+        // the block H-matvec's padded vectors and skeleton weights
+        const uint64_t bs = (uint64_t)r->block_size;
+        b += r256(4 * bs * ldv) + r256(4 * 2 * 152 * (mmax + 1) * bs) + 2 * r256(8 * mmax * mmax);
+        b += 2 * r256(4 * bs * nleaves * ldk) + 2 * r256(4 * nnodes * R * bs) + 8 * 256;
+    }
     return b;
 }
 

@@ -22,6 +22,7 @@
 namespace {
 
 constexpr int kBlkThreads = 256;
+constexpr int kTreeLvThreads = 512;  // leaf N2S and the per-level tree kernels (latency bound: more warps)
 constexpr int kColTile = 32;  // right-hand sides per block of the tree kernels (a lane each)
 
 // start and size of leaf `a`
@@ -57,35 +58,42 @@ __global__ void blk_permute_in_kernel(const __grid_constant__ DmHmat H, const fl
 constexpr int kVs = kColTile + 1;  // shared-memory row stride of staged vectors (conflict-free)
 
 // out[o][lane] (= or +=) sum_k A(o, k) V[k][lane] for o < nout, where A(o, k) = A[o ao + k ak]
-// (global memory) and V is nk x kColTile in shared memory (row stride kVs); a warp per output
-// row: its lanes load 32 consecutive A(o, k) at once and broadcast them by shuffles, so a
-// row costs nk / 32 memory round trips instead of nk.
+// (global memory) and V is nk x kColTile in shared memory (row stride kVs). A warp takes four
+// output rows at a time: its lanes load 32 consecutive A(o, k) of each of the four rows at
+// once and broadcast them by shuffles, so the four accumulation chains run side by side and
+// a row costs nk / 32 memory round trips shared with three others.
 __device__ __forceinline__ void blk_gemm_rows(const float *__restrict__ A, int ao, int ak, int nout, int nk,
                                               const float *V, float *out, int ldo, bool add, int ncol) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = warp; o < nout; o += nw) {
-        const float *a = A + (size_t)o * ao;
-        float a0 = 0.f, a1 = 0.f;
+    for (int o0 = 4 * warp; o0 < nout; o0 += 4 * nw) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int k0 = 0; k0 < nk; k0 += 32) {
             const int kk = k0 + lane;
-            const float av = kk < nk ? __ldg(a + (size_t)kk * ak) : 0.f;
+            float av[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                av[q] = (o0 + q < nout && kk < nk) ? __ldg(A + (size_t)(o0 + q) * ao + (size_t)kk * ak) : 0.f;
             const int kn = nk - k0 < 32 ? nk - k0 : 32;
-            int t = 0;
-            for (; t + 1 < kn; t += 2) {
-                a0 = fmaf(__shfl_sync(DM_FULL, av, t), V[(k0 + t) * kVs + lane], a0);
-                a1 = fmaf(__shfl_sync(DM_FULL, av, t + 1), V[(k0 + t + 1) * kVs + lane], a1);
+            for (int t = 0; t < kn; ++t) {
+                const float v = V[(k0 + t) * kVs + lane];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = fmaf(__shfl_sync(DM_FULL, av[q], t), v, acc[q]);
             }
-            if (t < kn) a0 = fmaf(__shfl_sync(DM_FULL, av, t), V[(k0 + t) * kVs + lane], a0);
         }
         if (lane < ncol) {
-            float *dst = out + (size_t)o * ldo + lane;
-            *dst = add ? *dst + (a0 + a1) : (a0 + a1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (o0 + q < nout) {
+                    float *dst = out + (size_t)(o0 + q) * ldo + lane;
+                    *dst = add ? *dst + acc[q] : acc[q];
+                }
+            }
         }
     }
 }
 
 // leaf N2S: W_a[t][c] = sum_j P_a[t][j] Xb[c][a ldk + j]; grid (nleaves, column groups)
-__global__ void __launch_bounds__(kBlkThreads) blk_leaf_n2s_kernel(const __grid_constant__ DmHmat H,
+__global__ void __launch_bounds__(kTreeLvThreads) blk_leaf_n2s_kernel(const __grid_constant__ DmHmat H,
                                                                    const float *__restrict__ Xb, int64_t ldx,
                                                                    int nb, float *__restrict__ Wb) {
     extern __shared__ float sm[];
@@ -107,7 +115,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_leaf_n2s_kernel(const __grid_
 
 // one level of the upward pass (nodes of level lv): S2S of the children pair, then the
 // node's own N2S (not at the root)
-__global__ void __launch_bounds__(kBlkThreads) blk_up_kernel(const __grid_constant__ DmHmat H, int lv, int nb,
+__global__ void __launch_bounds__(kTreeLvThreads) blk_up_kernel(const __grid_constant__ DmHmat H, int lv, int nb,
                                                              float *__restrict__ Wb, float *__restrict__ Ub) {
     extern __shared__ float sm[];
     const int n = (1 << lv) - 1 + blockIdx.x, c0 = blockIdx.y * kColTile, ncol = min(kColTile, nb - c0);
@@ -131,7 +139,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_up_kernel(const __grid_consta
 }
 
 // one level of the downward pass (nodes of level lv >= 1): [U_l; U_r] += P_n^T U_n
-__global__ void __launch_bounds__(kBlkThreads) blk_down_kernel(const __grid_constant__ DmHmat H, int lv, int nb,
+__global__ void __launch_bounds__(kTreeLvThreads) blk_down_kernel(const __grid_constant__ DmHmat H, int lv, int nb,
                                                                float *__restrict__ Ub) {
     extern __shared__ float sm[];
     const int n = (1 << lv) - 1 + blockIdx.x, c0 = blockIdx.y * kColTile, ncol = min(kColTile, nb - c0);
@@ -378,20 +386,20 @@ cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const
     if (far) {
         const size_t sm_leaf = sizeof(float) * (size_t)H.leaf_max * kVs;
         if ((e = dm_allow_smem((const void *)blk_leaf_n2s_kernel, sm_leaf)) != cudaSuccess) return e;
-        blk_leaf_n2s_kernel<<<dim3(nleaves, cgroups), kBlkThreads, sm_leaf, st>>>(H, Xb, ldx, nb, W.Wb);
+        blk_leaf_n2s_kernel<<<dim3(nleaves, cgroups), kTreeLvThreads, sm_leaf, st>>>(H, Xb, ldx, nb, W.Wb);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const size_t sm_pair = sizeof(float) * 2 * (size_t)H.max_rank * kVs;
         if ((e = dm_allow_smem((const void *)blk_up_kernel, sm_pair)) != cudaSuccess) return e;
         for (int lv = H.L - 1; lv >= 0; --lv) {
-            blk_up_kernel<<<dim3(1u << lv, cgroups), kBlkThreads, sm_pair, st>>>(H, lv, nb, W.Wb, W.Ub);
+            blk_up_kernel<<<dim3(1u << lv, cgroups), kTreeLvThreads, sm_pair, st>>>(H, lv, nb, W.Wb, W.Ub);
             dm_count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         const size_t sm_one = sizeof(float) * (size_t)H.max_rank * kVs;
         if ((e = dm_allow_smem((const void *)blk_down_kernel, sm_one)) != cudaSuccess) return e;
         for (int lv = 1; lv < H.L; ++lv) {
-            blk_down_kernel<<<dim3(1u << lv, cgroups), kBlkThreads, sm_one, st>>>(H, lv, nb, W.Ub);
+            blk_down_kernel<<<dim3(1u << lv, cgroups), kTreeLvThreads, sm_one, st>>>(H, lv, nb, W.Ub);
             dm_count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }

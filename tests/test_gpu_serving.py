@@ -107,3 +107,51 @@ def test_phased_lanczos_step_matches_cooperative(dm):
     # both runs stop at residual <= 1e-7 lambda_1; the subspace angle is that over the gap
     # to lambda_9 (FP64 atomics order the reductions differently from run to run)
     assert _angle(out[0][1], out[1][1]) < 2e-3
+
+
+def test_block_lanczos_requests_in_the_mix(dm):
+    """Requests asking for block Lanczos (block_size 8) run alongside single-vector ones; each
+    matches the same block solve run alone (same structure and arithmetic: identical values)."""
+    reqs = [(3000, 10, 8, 8), (2000, 11, 6, 0), (5000, 12, 8, 8), (1800, 13, 5, 4)]
+    dm.dm_serve_start(slots=3)
+    try:
+        tickets = {}
+        for n, seed, k, b in reqs:
+            X = _points(n, seed)
+            t = dm.dm_submit(X, eps=-1.0, tol=1e-5, leaf_size=128, max_rank=64, k=k, want_vectors=True,
+                             seed=0, block_size=b)
+            tickets[t] = (X, k, b)
+        out = _wait(dm, list(tickets))
+    finally:
+        dm.dm_serve_stop()
+    for t, (X, k, b) in tickets.items():
+        res = out[t]
+        assert res["status"] == 0, res["error"]
+        cfg = dm.dm_config_default(block_size=b, shared_device=1)
+        h = dm.dm_create(X, eps=-1.0, cfg=cfg)
+        dm.dm_compress(h, 1e-5, 128, 64)
+        ev, V, conv = dm.dm_eigs(h, k)
+        dm.dm_destroy(h)
+        assert conv
+        np.testing.assert_allclose(res["evals"], ev, rtol=1e-6, atol=1e-9)
+        assert _angle(res["evecs"], V) < 1e-3
+
+
+def test_leaf_autotuner_picks_cheapest_and_keeps_it(dm):
+    """dm_tune_leaf: the chosen leaf is the argmin of the reported costs, the handle stays
+    compressed with it, and its eigenpairs equal a direct compression with that leaf."""
+    X = _points(6000, 20)
+    h = dm.dm_create(X, eps=-1.0)
+    best, costs = dm.dm_tune_leaf(h, 1e-5, 64, 8, candidates=(64, 128, 256))
+    assert best == min(costs, key=costs.get)
+    assert all(v > 0 for v in costs.values())
+    st = dm.dm_get_stats(h)
+    assert st["leaf_max"] <= best and st["leaf_max"] > best // 2
+    ev, _, conv = dm.dm_eigs(h, 8)
+    dm.dm_destroy(h)
+    h2 = dm.dm_create(X, eps=-1.0)
+    dm.dm_compress(h2, 1e-5, best, 64)
+    ev2, _, conv2 = dm.dm_eigs(h2, 8)
+    dm.dm_destroy(h2)
+    assert conv and conv2
+    np.testing.assert_array_equal(ev, ev2)
