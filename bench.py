@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--n", type=int, default=WORKLOAD["N"], help="override N (testing only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-block", action="store_true", help="skip the block H-matvec and scaling-workload lines")
-    p.add_argument("--sections", default="block_matvec,block_lanczos,scaling_workload,mnist_workload",
+    p.add_argument("--sections", default="block_matvec,block_lanczos,scaling_workload,mnist_workload,batched_clouds",
                    help="comma list of the side measurements to run after the headline")
     p.add_argument("--skip-headline", action="store_true",
                    help="profiling only: run just the side measurements (no timed headline steps)")
@@ -297,6 +297,55 @@ def scaling_workload_run(dm, torch, stream) -> dict:
     return res
 
 
+def batched_clouds_run(dm, n_clouds: int = 256, slots: int = 8, seed: int = 3) -> dict:
+    """Many uneven clouds: n_clouds s-curve / swiss-roll clouds (alternating) with N log-uniform
+    in [1000, 32000], top 8 eigenpairs each by block Lanczos with 16 vectors, max rank 64,
+    tol 1e-5; the leaf size is picked per size octave by the autotuner (dm_tune_leaf over
+    {64, 128, 256} on the octave's first cloud); all clouds are submitted at once and run
+    through the serving slots. Reported: clouds/s and eigenpairs/s over the whole batch."""
+    import numpy as np
+
+    import synth
+
+    Ns = synth.log_uniform_sizes(n_clouds, 1000, 32000, seed=seed)
+    clouds = [synth.as_f32(synth.s_curve(int(n), seed=100 + i) if i % 2 == 0 else synth.swiss_roll(int(n), seed=100 + i))
+              for i, n in enumerate(Ns)]
+    octave = np.floor(np.log2(Ns / 1000.0)).astype(int)
+    leaf_of = {}
+    t0 = time.perf_counter()
+    for o in sorted(set(octave.tolist())):
+        i = int(np.where(octave == o)[0][0])
+        h = dm.dm_create(clouds[i], eps=-1.0)
+        best, _ = dm.dm_tune_leaf(h, 1e-5, 64, 8, candidates=(64, 128, 256))
+        dm.dm_destroy(h)
+        leaf_of[o] = best
+    tune_s = time.perf_counter() - t0
+    dm.dm_serve_start(slots=slots, hbm_budget_bytes=150_000_000_000)
+    done = {}
+    try:
+        t0 = time.perf_counter()
+        tickets = [dm.dm_submit(X, eps=-1.0, tol=1e-5, leaf_size=leaf_of[int(o)], max_rank=64, k=8,
+                                want_vectors=True, seed=0, block_size=16) for X, o in zip(clouds, octave)]
+        while len(done) < len(tickets):
+            for t in tickets:
+                if t not in done:
+                    fin, r = dm.dm_poll(t)
+                    if fin:
+                        done[t] = (r["status"], r["done_ms"] - r["submit_ms"])
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+    finally:
+        dm.dm_serve_stop()
+    lat = np.array([v[1] for v in done.values()])
+    ok = sum(1 for v in done.values() if v[0] == 0)
+    return {"workload": f"{n_clouds} clouds (s-curve / swiss roll), N log-uniform in [1000, 32000], top 8, "
+                        "block Lanczos b=16, max rank 64, tol 1e-5, autotuned leaf",
+            "leaf_by_octave": {str(int(1000 * 2 ** o)): leaf_of[o] for o in leaf_of}, "tune_s": tune_s,
+            "wall_s": wall, "clouds_per_s": n_clouds / wall, "eigenpairs_per_s": 8 * ok / wall,
+            "converged": ok, "latency_p50_ms": float(np.percentile(lat, 50)),
+            "latency_p99_ms": float(np.percentile(lat, 99)), "slots": slots}
+
+
 def mnist_workload_run(dm, stream, reps: int = 2) -> dict:
     """The high-dimensional workload: 60,000 MNIST-shaped vectors in R^784 (8-bit quantised,
     ~80% zeros; synthetic stand-in for MNIST), eps = median, leaf 256, rank 128, tol 1e-4,
@@ -480,7 +529,8 @@ def run_ours(args) -> int:
             fn = {"block_matvec": lambda: block_run(dm, torch, stream, X, W),
                   "block_lanczos": lambda: block_lanczos_run(dm, stream, X, W),
                   "scaling_workload": lambda: scaling_workload_run(dm, torch, stream),
-                  "mnist_workload": lambda: mnist_workload_run(dm, stream)}[key]
+                  "mnist_workload": lambda: mnist_workload_run(dm, stream),
+                  "batched_clouds": lambda: batched_clouds_run(dm)}[key]
             out[key] = fn()
         if rank == 0:
             print(json.dumps({"profiling_only": True, **out}))
@@ -530,7 +580,8 @@ def run_ours(args) -> int:
         for key, fn in (("block_matvec", lambda: block_run(dm, torch, stream, X, W)),
                         ("block_lanczos", lambda: block_lanczos_run(dm, stream, X, W)),
                         ("scaling_workload", lambda: scaling_workload_run(dm, torch, stream)),
-                        ("mnist_workload", lambda: mnist_workload_run(dm, stream))):
+                        ("mnist_workload", lambda: mnist_workload_run(dm, stream)),
+                        ("batched_clouds", lambda: batched_clouds_run(dm))):
             if key not in wanted:
                 continue
             try:
