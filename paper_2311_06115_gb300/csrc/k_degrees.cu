@@ -305,6 +305,158 @@ __global__ void __launch_bounds__(kD3Threads) degree_pass_d3_kernel(const float 
     }
 }
 
+// Symmetric form of the d = 3 pass: W is symmetric, so only the tiles (I, J) with J >= I of
+// the row blocks (kD3Rows = 512 points each) are evaluated. A tile adds each entry to its row
+// sum (thread-local, as in degree_pass_d3_kernel) and, when J > I, also to its column sum:
+// w_i e_ij over the block's 512 rows. Column partials are collected per thread for 32
+// columns at a time and folded across the warp by a reduce-scatter (31 shuffles leave lane
+// l with column l's sum), then the four warps meet in shared memory and each tile column
+// gets one FP64 atomic. Half the exponentials of the full pass; the same per-entry
+// arithmetic (dot form with the row factor 2^-n_i applied once per row, or the difference
+// form), FP32 tile partials and FP64 accumulation.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int sft = 16; sft >= 1; sft >>= 1) {
+        const bool upper = (lane & sft) != 0;
+#pragma unroll
+        for (int i = 0; i < sft; ++i) {
+            const float send = upper ? v[i] : v[i + sft];
+            const float keep = upper ? v[i + sft] : v[i];
+            v[i] = keep + __shfl_xor_sync(DM_FULL, send, sft);
+        }
+    }
+    return v[0];
+}
+
+__global__ void __launch_bounds__(kD3Threads) degree_sym_d3_kernel(const float *__restrict__ Xs,
+                                                                   const float *__restrict__ nrm,
+                                                                   const float *__restrict__ nmax, int64_t N,
+                                                                   const float *__restrict__ w,
+                                                                   double *__restrict__ out, int nb) {
+    __shared__ float4 ta[kDegTile];
+    __shared__ float4 tb[kDegTile];
+    __shared__ float2 tw[kDegTile];
+    __shared__ float colsum[kDegTile];
+    // tile (I, J), J >= I, from the flat index: row I of the triangle starts at I nb - I (I - 1) / 2
+    const int64_t t = blockIdx.x;
+    const double B2 = 2.0 * nb + 1.0;
+    int I = (int)floor((B2 - sqrt(fmax(B2 * B2 - 8.0 * (double)t, 0.0))) * 0.5);
+    auto start = [&](int64_t r) { return r * nb - r * (r - 1) / 2; };
+    while (I > 0 && start(I) > t) --I;
+    while (start(I + 1) <= t) ++I;
+    const int J = I + (int)(t - start(I));
+    const bool offdiag = J > I;
+    const bool dot_form = nrm != nullptr && *nmax <= kDotFormMaxNorm;
+    const float sc = dot_form ? 2.f : 1.f;
+    const int lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)I * kD3Rows + threadIdx.x;
+    float xr[4][3], wr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t rq = row0 + (int64_t)q * kD3Threads;
+        const bool ok = rq < N;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) xr[q][k] = ok ? sc * Xs[rq * 3 + k] : 0.f;
+        // column weights: w_i, times the row factor 2^-n_i in the dot form
+        wr[q] = ok ? (w ? w[rq] : 1.f) * (dot_form ? dm_ex2(-nrm[rq]) : 1.f) : 0.f;
+    }
+    Rows4 X;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        X.x0[p] = make_float2(xr[2 * p][0], xr[2 * p + 1][0]);
+        X.x1[p] = make_float2(xr[2 * p][1], xr[2 * p + 1][1]);
+        X.x2[p] = make_float2(xr[2 * p][2], xr[2 * p + 1][2]);
+    }
+    const float2 W01 = make_float2(wr[0], wr[1]), W23 = make_float2(wr[2], wr[3]);
+    const int64_t c0 = (int64_t)J * kD3Rows;
+    const int64_t c1 = (c0 + kD3Rows < N) ? c0 + kD3Rows : N;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t t0 = c0; t0 < c1; t0 += kDegTile) {
+        const int tn = (int)(c1 - t0 < kDegTile ? c1 - t0 : kDegTile);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kDegTile; e += kD3Threads) {
+            colsum[e] = 0.f;
+            if (e >= tn) continue;
+            const int64_t j = t0 + e;
+            const float x = Xs[j * 3], y = Xs[j * 3 + 1], z = Xs[j * 3 + 2];
+            const float wj = w ? w[j] : 1.f;
+            if (dot_form) {
+                const float nj = -nrm[j];
+                ta[e] = make_float4(x, x, y, y);
+                tb[e] = make_float4(z, z, nj, nj);
+            } else {
+                ta[e] = make_float4(-x, -x, -y, -y);
+                tb[e] = make_float4(-z, -z, 0.f, 0.f);
+            }
+            tw[e] = make_float2(wj, wj);
+        }
+        __syncthreads();
+        float2 part0 = make_float2(0.f, 0.f), part1 = make_float2(0.f, 0.f);
+        for (int jc = 0; jc < tn; jc += 32) {
+            float cp[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                const int j = jc + u;
+                cp[u] = 0.f;
+                if (j < tn) {
+                    const float4 a = ta[j], b = tb[j];
+                    const float2 wj = tw[j];
+                    const float2 cx = make_float2(a.x, a.y), cy = make_float2(a.z, a.w), cz = make_float2(b.x, b.y);
+                    float2 e0, e1;
+                    if (dot_form) {
+                        const float2 cn = make_float2(b.z, b.w);
+                        float2 g0 = __ffma2_rn(X.x2[0], cz, cn);
+                        float2 g1 = __ffma2_rn(X.x2[1], cz, cn);
+                        g0 = __ffma2_rn(X.x1[0], cy, g0);
+                        g1 = __ffma2_rn(X.x1[1], cy, g1);
+                        g0 = __ffma2_rn(X.x0[0], cx, g0);
+                        g1 = __ffma2_rn(X.x0[1], cx, g1);
+                        e0 = make_float2(dm_ex2(g0.x), dm_ex2(g0.y));
+                        e1 = make_float2(dm_ex2(g1.x), dm_ex2(g1.y));
+                    } else {
+                        const float2 d0 = __fadd2_rn(X.x0[0], cx), f0 = __fadd2_rn(X.x0[1], cx);
+                        const float2 d1 = __fadd2_rn(X.x1[0], cy), f1 = __fadd2_rn(X.x1[1], cy);
+                        const float2 d2 = __fadd2_rn(X.x2[0], cz), f2 = __fadd2_rn(X.x2[1], cz);
+                        float2 r0 = __fmul2_rn(d0, d0), r1 = __fmul2_rn(f0, f0);
+                        r0 = __ffma2_rn(d1, d1, r0);
+                        r1 = __ffma2_rn(f1, f1, r1);
+                        r0 = __ffma2_rn(d2, d2, r0);
+                        r1 = __ffma2_rn(f2, f2, r1);
+                        e0 = make_float2(dm_ex2(-r0.x), dm_ex2(-r0.y));
+                        e1 = make_float2(dm_ex2(-r1.x), dm_ex2(-r1.y));
+                    }
+                    part0 = __ffma2_rn(e0, wj, part0);
+                    part1 = __ffma2_rn(e1, wj, part1);
+                    if (offdiag) {
+                        const float2 c2 = __ffma2_rn(e0, W01, __fmul2_rn(e1, W23));
+                        cp[u] = c2.x + c2.y;
+                    }
+                }
+            }
+            if (offdiag) {
+                const float v = warp_reduce_scatter32(cp, lane);
+                if (jc + lane < tn) atomicAdd(&colsum[jc + lane], v);
+            }
+        }
+        acc[0] += (double)part0.x;
+        acc[1] += (double)part0.y;
+        acc[2] += (double)part1.x;
+        acc[3] += (double)part1.y;
+        if (offdiag) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < tn; e += kD3Threads) atomicAdd(out + t0 + e, (double)colsum[e]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t rq = row0 + (int64_t)q * kD3Threads;
+        if (rq >= N) continue;
+        double v = acc[q];
+        if (dot_form) v *= (double)dm_ex2(-nrm[rq]);
+        atomicAdd(out + rq, v);
+    }
+}
+
 // column sums of X (FP64) for the centring
 __global__ void colsum_kernel(const float *__restrict__ X, int64_t N, int d, double *__restrict__ sums) {
     double loc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -456,6 +608,14 @@ cudaError_t dm_launch_degree_pass_centered(const float *Xs, const float *nrm, co
                                            const float *wcol, double *out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * N, st);
     if (e != cudaSuccess) return e;
+    if (d == 3 && N >= 4 * kD3Rows) {
+        // symmetric tiles: half the entries
+        const int64_t nb = (N + kD3Rows - 1) / kD3Rows;
+        const int64_t tiles = nb * (nb + 1) / 2;
+        degree_sym_d3_kernel<<<(unsigned)tiles, kD3Threads, 0, st>>>(Xs, nrm, nmax, N, wcol, out, (int)nb);
+        dm_count_launches(1);
+        return cudaGetLastError();
+    }
     if (d == 3) {
         const int64_t rb = (N + kD3Rows - 1) / kD3Rows;
         int64_t want = (12 * 152 + rb - 1) / rb;

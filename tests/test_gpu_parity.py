@@ -47,10 +47,14 @@ def test_bandwidth_median_bit_exact(dm, n):
     assert dm.dm_get_eps(h) == O.median_sqdist(X, seed=0)
 
 
-@pytest.mark.parametrize("n,alpha", [(2048, 1.0), (1537, 1.0), (999, 0.5), (600, 0.0)])
-def test_degrees_match_oracle(dm, n, alpha):
+@pytest.mark.parametrize("n,alpha,eps_scale", [(2048, 1.0, 1.0), (1537, 1.0, 1.0), (999, 0.5, 1.0), (600, 0.0, 1.0),
+                                                (3001, 1.0, 1.0), (5000, 0.5, 0.05)])
+def test_degrees_match_oracle(dm, n, alpha, eps_scale):
+    """Degree vectors; from N = 2048 on the d = 3 passes evaluate only the upper tiles of the
+    symmetric W (row and column sums). eps_scale 0.05 shrinks the kernel so that the scaled
+    squared norms exceed the dot form's limit: the difference form runs."""
     X = _scurve(n, 1)
-    eps = O.median_sqdist(X)
+    eps = O.median_sqdist(X) * eps_scale
     h = dm.dm_create(X, eps=eps, alpha=alpha)
     q, dg, s = dm.dm_get_degrees(h)
     oq, odg, os_ = O.degrees(X, eps, alpha)
