@@ -549,7 +549,7 @@ int ensure_lanczos(dm_ctx *h) {
     DM_CHECK(h->alloc(&L.alpha, (size_t)L.m_max + 1, G_LANCZOS));
     DM_CHECK(h->alloc(&L.beta, (size_t)L.m_max + 1, G_LANCZOS));
     DM_CHECK(h->alloc(&L.h, (size_t)2 * (L.m_max + 1), G_LANCZOS));
-    DM_CHECK(h->alloc(&L.nrm2, 4, G_LANCZOS));
+    DM_CHECK(h->alloc(&L.nrm2, 1, G_LANCZOS));
     DM_CHECK(h->alloc(&L.theta, (size_t)kmax, G_LANCZOS));
     DM_CHECK(h->alloc(&L.resid, (size_t)kmax, G_LANCZOS));
     DM_CHECK(h->alloc(&L.Y, (size_t)kmax * L.m_max, G_LANCZOS));

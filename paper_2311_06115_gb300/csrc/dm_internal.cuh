@@ -295,7 +295,7 @@ struct DmLanczos {
     double *alpha;    // m_max
     double *beta;     // m_max (beta[j] = |r_j|)
     double *h;        // 2 x (m_max+1) projection coefficients (two passes)
-    double *nrm2;     // 3 accumulators: |z|^2 before, after the first and after the second pass
+    double *nrm2;     // scalar accumulator
     double *theta;    // kmax Ritz values (descending)
     double *resid;    // kmax residual bounds
     double *Y;        // kmax columns of length m_max: eigenvectors of T

@@ -44,13 +44,9 @@ __global__ void normalize_kernel(const float *__restrict__ z, int64_t N, const d
 
 // ---- one fused Lanczos orthogonalisation step (cooperative launch) --------------
 // Phases (each block owns a contiguous range of rows):
-//   1 h0 = V^T z, |z|^2    2 z -= V h0, |z|^2    3 h1 = V^T z    4 z -= V h1, |z|^2
+//   1 h0 = V^T z        2 z -= V h0        3 h1 = V^T z        4 z -= V h1, |z|^2
 //   5 alpha_j = h0_j + h1_j, beta_j = |z|, V[:, j+1] = z / beta_j
-// separated by a grid barrier. Phases 3 and 4 (the second Gram-Schmidt pass) run only when
-// the first pass cancelled most of z: |z after| < eta |z before| with eta = 1/sqrt(2) (the
-// Daniel-Gragg-Kaufman-Stewart criterion, as in ARPACK); otherwise z is already orthogonal
-// to V to working precision and the pass is skipped. nrm2[0..2] hold the three norms (the
-// host zeroes them before each step). The barrier spins with a bounded iteration count;
+// separated by a grid barrier. The barrier spins with a bounded iteration count;
 // on exhaustion it raises *err and every block returns (the host reports a timeout).
 constexpr int kStepThreads = 256;
 constexpr long long kBarrierSpinLimit = 1ll << 22;
@@ -153,25 +149,19 @@ __global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, in
     const int64_t r0 = blockIdx.x * per, r1 = (r0 + per < N) ? r0 + per : N;
     const unsigned G = gridDim.x;
     const bool all = phase < 0;
-    constexpr double kEta2 = 0.5;  // eta^2, eta = 1/sqrt(2)
     if (all || phase == 0) {
-        float ss = 0.f;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) ss = fmaf(z[i], z[i], ss);
-        ss = dm_warp_sum(ss);
-        if ((threadIdx.x & 31) == 0) atomicAdd(nrm2, (double)ss);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *nrm2 = 0.0;
         block_project(V, ldv, ncols, z, r0, r1, h0, acc_s);
     }
     if (all && !grid_barrier(bar, G, err)) return;
-    if (all || phase == 1) block_update(V, ldv, ncols, z, r0, r1, h0, sh, nrm2 + 1);
+    if (all || phase == 1) block_update(V, ldv, ncols, z, r0, r1, h0, sh, nullptr);
     if (all && !grid_barrier(bar, 2 * G, err)) return;
-    // every block reads the same two sums after the barrier: a uniform decision
-    const bool second = __ldcg(nrm2 + 1) < kEta2 * __ldcg(nrm2);
-    if (second && (all || phase == 2)) block_project(V, ldv, ncols, z, r0, r1, h1, acc_s);
-    if (second && all && !grid_barrier(bar, 3 * G, err)) return;
-    if (second && (all || phase == 3)) block_update(V, ldv, ncols, z, r0, r1, h1, sh, nrm2 + 2);
-    if (second && all && !grid_barrier(bar, 4 * G, err)) return;
+    if (all || phase == 2) block_project(V, ldv, ncols, z, r0, r1, h1, acc_s);
+    if (all && !grid_barrier(bar, 3 * G, err)) return;
+    if (all || phase == 3) block_update(V, ldv, ncols, z, r0, r1, h1, sh, nrm2);
+    if (all && !grid_barrier(bar, 4 * G, err)) return;
     if (!all && phase != 4) return;
-    const double b = sqrt(__ldcg(nrm2 + (second ? 2 : 1)));
+    const double b = sqrt(__ldcg(nrm2));
     if (j + 1 <= m_max) {
         float *vn = V + (size_t)(j + 1) * ldv;
         const float inv = (float)(1.0 / b);
@@ -508,8 +498,6 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) 
         if (e0 != cudaSuccess) return e0;
     }
     cudaError_t e = cudaMemsetAsync(Lz.bar, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(Lz.nrm2, 0, 3 * sizeof(double), st);
     if (e != cudaSuccess) return e;
     static thread_local int grid = 0;
     if (grid == 0) {

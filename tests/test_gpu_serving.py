@@ -154,4 +154,5 @@ def test_leaf_autotuner_picks_cheapest_and_keeps_it(dm):
     ev2, _, conv2 = dm.dm_eigs(h2, 8)
     dm.dm_destroy(h2)
     assert conv and conv2
-    np.testing.assert_array_equal(ev, ev2)
+    # same structure and arithmetic; FP64 atomics in the degree sums may add in another order
+    np.testing.assert_allclose(ev, ev2, rtol=1e-6, atol=1e-9)
