@@ -5,10 +5,7 @@
 //                         every S2S, internal S2N) with its operands staged in the
 //                         cluster's shared memory, ending with the incoming skeleton
 //                         potential u_a of every leaf.
-//   C near_bulk_kernel    the stored leaf blocks streamed by bulk copies into a shared-memory
-//                         ring (near_cached_kernel: the register-load form, kept for leaf sizes
-//                         the ring does not fit) -- or, on the fly,
-//     near_cached_kernel  row chunks of the stored leaf blocks streamed with 16-byte
+//   C near_cached_kernel  row chunks of the stored leaf blocks streamed with 16-byte
 //     near_otf_kernel     evict-first loads (or entries recomputed from the points), then
 //                         the leaf S2N y~(I_a) += P_a^T u_a, each row written once.
 //
@@ -24,7 +21,6 @@
 #include <cooperative_groups.h>
 
 #include "dm_internal.cuh"
-#include "dm_tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -419,137 +415,6 @@ __global__ void __launch_bounds__(kNearThreads, 6) near_cached_kernel(const __gr
     }
 }
 
-// Cached near field streamed by the bulk-copy engine. Each CTA walks near items (a leaf and
-// kBulkItemRows of its block rows) with a stride of gridDim.x; the rows of an item arrive in
-// stages of kBulkRowsStage whole block rows (cp.async.bulk, one copy per row, completing on
-// the stage's mbarrier) through a kBulkStages-deep ring, so a CTA keeps about
-// kBulkStages x 12 KB in flight without a register per byte. Warp w reduces row w of every
-// stage against x~(I_a) in shared memory and writes the near result to ynear (position
-// order); once the CTA's items are streamed it waits for the tree pass and applies the leaf
-// S2N to its rows. Waits are bounded: a wait that gives up raises *err and the CTA stops.
-constexpr int kBulkThreads = 256;
-constexpr int kBulkRowsStage = kBulkThreads / 32;  // a row per warp
-constexpr int kBulkStages = 4;
-constexpr int kBulkItemRows = 64;
-
-__global__ void __launch_bounds__(kBulkThreads) near_bulk_kernel(const __grid_constant__ DmHmat H,
-                                                                 const float *__restrict__ x, float *__restrict__ y,
-                                                                 int permuted, int far, int n_items) {
-    using namespace dmtc;
-    extern __shared__ float4 smem4[];
-    const int ldk = H.ldk, m4max = (H.leaf_max + 3) & ~3;
-    float *ring = reinterpret_cast<float *>(smem4);                     // kBulkStages x rows x ldk
-    float *sx = ring + (size_t)kBulkStages * kBulkRowsStage * ldk;       // m4max
-    uint64_t *full = reinterpret_cast<uint64_t *>(sx + ((m4max + 3) & ~3));
-    uint64_t *empty = full + kBulkStages;
-    __shared__ int s_abort;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        for (int s2 = 0; s2 < kBulkStages; ++s2) {
-            mbar_init(&full[s2], 1);
-            mbar_init(&empty[s2], kBulkRowsStage);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
-    }
-    __syncthreads();
-    uint32_t gs = 0;  // this CTA's running stage count: slot gs % S, use gs / S
-    // producer step (thread 0): stage g of the item (rows r0 + 8 (g - gbase) ...)
-    auto issue = [&](uint32_t g, const NearItem &q, int kst) -> bool {
-        const int slot = (int)(g % kBulkStages);
-        if (g >= kBulkStages && !mbar_wait(&empty[slot], ((g / kBulkStages) - 1) & 1u)) return false;
-        const int rfirst = kst * kBulkRowsStage, rn = min(kBulkRowsStage, q.nr - rfirst);
-        mbar_expect_tx(&full[slot], (uint32_t)(rn * ldk * 4));
-        const float *src = H.Knear + ((size_t)q.leaf * H.leaf_max + q.r0 + rfirst) * ldk;
-        float *dst = ring + (size_t)slot * kBulkRowsStage * ldk;
-        for (int r = 0; r < rn; ++r) bulk_load(dst + (size_t)r * ldk, src + (size_t)r * ldk, (uint32_t)(ldk * 4), &full[slot]);
-        return true;
-    };
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const NearItem q = near_item(H, item, kBulkItemRows);
-        if (q.nr == 0) continue;
-        const int nst = (q.nr + kBulkRowsStage - 1) / kBulkRowsStage;
-        // x~(I_a) (the previous item's readers are past the barrier at the end of the loop)
-        const int m4 = (q.m + 3) & ~3;
-        for (int j = threadIdx.x; j < m4; j += blockDim.x) {
-            float v = 0.f;
-            if (j < q.m) v = permuted ? x[q.st + j] : x[H.perm[q.st + j]];
-            sx[j] = v;
-        }
-        if (threadIdx.x == 0)
-            for (int k = 0; k < nst && k < kBulkStages; ++k)
-                if (!issue(gs + k, q, k)) { atomicExch(H.err, 1); s_abort = 1; }
-        __syncthreads();
-        if (s_abort) return;
-        const float4 *x4 = reinterpret_cast<const float4 *>(sx);
-        const int q4 = m4 >> 2;
-        for (int k = 0; k < nst; ++k) {
-            const uint32_t g = gs + k;
-            const int slot = (int)(g % kBulkStages);
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (g / kBulkStages) & 1u) ? 1 : 0) != 0;
-            if (!ok) {
-                if (lane == 0) atomicExch(H.err, 1);
-                s_abort = 1;
-                break;
-            }
-            const int r = k * kBulkRowsStage + warp;
-            if (r < q.nr) {
-                const float4 *row = reinterpret_cast<const float4 *>(ring + ((size_t)slot * kBulkRowsStage + warp) * ldk);
-                float a0 = 0.f, a1 = 0.f;
-                int v = lane;
-                for (; v + 32 < q4; v += 64) {
-                    const float4 p0 = row[v], x0 = x4[v], p1 = row[v + 32], x1 = x4[v + 32];
-                    a0 = fmaf(p0.x, x0.x, fmaf(p0.y, x0.y, fmaf(p0.z, x0.z, fmaf(p0.w, x0.w, a0))));
-                    a1 = fmaf(p1.x, x1.x, fmaf(p1.y, x1.y, fmaf(p1.z, x1.z, fmaf(p1.w, x1.w, a1))));
-                }
-                if (v < q4) {
-                    const float4 p0 = row[v], x0 = x4[v];
-                    a0 = fmaf(p0.x, x0.x, fmaf(p0.y, x0.y, fmaf(p0.z, x0.z, fmaf(p0.w, x0.w, a0))));
-                }
-                const float acc = dm_warp_sum(a0 + a1);
-                if (lane == 0) H.ynear[q.st + q.r0 + r] = acc;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[slot]);
-            if (threadIdx.x == 0 && k + kBulkStages < nst)
-                if (!issue(g + kBulkStages, q, k + kBulkStages)) { atomicExch(H.err, 1); s_abort = 1; }
-        }
-        gs += (uint32_t)nst;
-        __syncthreads();
-        if (s_abort) return;
-    }
-    // leaf S2N of this CTA's rows after the tree pass (rows it wrote itself: block-level visibility)
-    if (far) grid_dep_wait();
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const NearItem q = near_item(H, item, kBulkItemRows);
-        if (q.nr == 0) continue;
-        const int node = (1 << H.L) - 1 + q.leaf;
-        const int sr = far ? __ldg(H.ranks + node) : 0;
-        const float *u = H.uhat + (size_t)node * H.max_rank;
-        for (int li = threadIdx.x; li < q.nr; li += blockDim.x) {
-            const int i = q.r0 + li;
-            float a0 = H.ynear[q.st + i], a1 = 0.f;
-            if (far) {
-                const float4 *prow = reinterpret_cast<const float4 *>(H.PT + ((size_t)q.leaf * H.leaf_max + i) * H.ldt);
-                const int t4 = (sr + 3) >> 2;
-                for (int v = 0; v < t4; ++v) {
-                    const float4 p = __ldg(prow + v);
-                    const int j = 4 * v;
-                    const float u0 = __ldcg(u + j);
-                    const float u1 = j + 1 < sr ? __ldcg(u + j + 1) : 0.f;
-                    const float u2 = j + 2 < sr ? __ldcg(u + j + 2) : 0.f;
-                    const float u3 = j + 3 < sr ? __ldcg(u + j + 3) : 0.f;
-                    if (v & 1) a1 = fmaf(p.x, u0, fmaf(p.y, u1, fmaf(p.z, u2, fmaf(p.w, u3, a1))));
-                    else a0 = fmaf(p.x, u0, fmaf(p.y, u1, fmaf(p.z, u2, fmaf(p.w, u3, a0))));
-                }
-            }
-            const float val = a0 + a1;
-            if (permuted) y[q.st + i] = val;
-            else y[H.perm[q.st + i]] = val;
-        }
-    }
-}
-
 // On-the-fly near field (thread per row; entries s_i s_j 2^-|xs_i - xs_j|^2 from the staged
 // points), then the leaf S2N after waiting for the tree pass. One block per item.
 __global__ void __launch_bounds__(kNearThreads) near_otf_kernel(const __grid_constant__ DmHmat H,
@@ -668,29 +533,7 @@ cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y,
     const int rows = dm_near_item_rows(near_mode, H.leaf_max);
     const int n_items = nleaves * ((H.leaf_max + rows - 1) / rows);
     const int m4max = (H.leaf_max + 3) & ~3;
-    if (near_mode == DM_NEAR_CACHED && H.err && H.ynear) {
-        // bulk-copy stream: a persistent grid of resident CTAs walking the items
-        const int per_leaf = (H.leaf_max + kBulkItemRows - 1) / kBulkItemRows;
-        const int nb_items = nleaves * per_leaf;
-        const size_t smB = sizeof(float) * ((size_t)kBulkStages * kBulkRowsStage * H.ldk + (size_t)((m4max + 3) & ~3)) +
-                           sizeof(uint64_t) * 2 * kBulkStages;
-        if ((e = dm_allow_smem((const void *)near_bulk_kernel, smB)) != cudaSuccess) return e;
-        static thread_local int per_sm = 0, sms = 0;
-        static thread_local size_t per_sm_smem = 0;
-        if (per_sm == 0 || per_sm_smem != smB) {
-            per_sm_smem = smB;
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_bulk_kernel, kBulkThreads, smB)) !=
-                cudaSuccess)
-                return e;
-            if (per_sm < 1) per_sm = 1;
-        }
-        const int grid = nb_items < sms * per_sm ? nb_items : sms * per_sm;
-        e = launch_ex(near_bulk_kernel, (unsigned)grid, kBulkThreads, smB, st, 1u, far, H, x, y, pm, far ? 1 : 0,
-                      nb_items);
-    } else if (near_mode == DM_NEAR_CACHED) {
+    if (near_mode == DM_NEAR_CACHED) {
         const size_t smC = sizeof(float) * ((size_t)m4max + (size_t)((rows + 3) & ~3));
         if ((e = dm_allow_smem((const void *)near_cached_kernel, smC)) != cudaSuccess) return e;
         e = launch_ex(near_cached_kernel, (unsigned)n_items, kNearThreads, smC, st, 1u, far, H, x, y, pm, rows,
