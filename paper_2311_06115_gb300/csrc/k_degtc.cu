@@ -170,8 +170,8 @@ __global__ void degtc_stats_kernel(const float *__restrict__ X, int64_t N, int d
     }
 }
 
-// A (and B) rows, zero padded to kpad. Quantised: A = [v] (BF16), v = rint(255 x) -
-// rint(255 mean). Otherwise (FP32 storage): A = [hi | hi | lo], B = [hi | lo | hi] of the
+// A (and B) rows, zero padded to kpad (`sums` holds the column means by now). Quantised:
+// A = [v] (BF16), v = rint(255 x) - rint(255 mean). Otherwise (FP32 storage): A = [hi | hi | lo], B = [hi | lo | hi] of the
 // centred u = x - mean, hi = u rounded to TF32 (10 mantissa bits), lo = u - hi.
 // nrm_i = the diagonal of A B^T in FP32 (the epilogue's a_i = kappa nrm_i).
 __device__ __forceinline__ float tf32_rn(float u) {
@@ -189,7 +189,7 @@ __global__ void degtc_prep_kernel(const float *__restrict__ X, int64_t N, int d,
         __nv_bfloat16 *ar = reinterpret_cast<__nv_bfloat16 *>(Av) + i * dpad;
         for (int k = threadIdx.x; k < dpad; k += blockDim.x) {
             float v = 0.f;
-            if (k < d) v = rintf(X[i * d + k] * 255.f) - (float)rint(255.0 * sums[k] / (double)N);
+            if (k < d) v = rintf(X[i * d + k] * 255.f) - (float)rint(255.0 * sums[k]);
             ar[k] = __float2bfloat16_rn(v);
             nn = fmaf(v, v, nn);
         }
@@ -199,7 +199,7 @@ __global__ void degtc_prep_kernel(const float *__restrict__ X, int64_t N, int d,
         for (int k = threadIdx.x; k < dpad; k += blockDim.x) {
             float hi = 0.f, lo = 0.f;
             if (k < d) {
-                const float u = (float)((double)X[i * d + k] - sums[k] / (double)N);
+                const float u = (float)((double)X[i * d + k] - sums[k]);
                 hi = tf32_rn(u);
                 lo = u - hi;
             }
@@ -221,6 +221,12 @@ __global__ void degtc_prep_kernel(const float *__restrict__ X, int64_t N, int d,
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
         nrm[i] = t;
     }
+}
+
+// column sums -> column means, once (d divisions instead of one per element)
+__global__ void degtc_means_kernel(double *sums, int64_t N, int d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < d) sums[k] = sums[k] / (double)N;
 }
 
 __global__ void degtc_scale_kernel(float *nrm, int64_t N, double kappa) {
@@ -261,6 +267,8 @@ cudaError_t dm_degtc_prepare(const float *X, int64_t N, int d, double eps, void 
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     S->quant = bad == 0;
     S->kpad = S->quant ? dpad : 3 * dpad;
+    degtc_means_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(S->sums, N, d);
+    dm_count_launches(1);
     degtc_prep_kernel<<<(unsigned)N, 128, 0, st>>>(X, N, d, S->sums, S->quant ? 1 : 0, dpad, S->A, S->B, S->an);
     dm_count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
