@@ -870,6 +870,15 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         w.items = items;
         w.cand1 = c1;
         w.cand2 = c2;
+        // the large levels (nodes above dm_tree_big_node() points) split over many CTAs
+        w.max_big = (int)(h->N / dm_tree_big_node()) + 1;
+        unsigned char *sel = nullptr;
+        DM_CHECK(h->alloc(&sel, (size_t)w.max_big * dm_tree_sel_bytes(), G_WORK));
+        DM_CHECK(h->alloc(&w.hist, (size_t)w.max_big * 256, G_WORK));
+        unsigned char *icnt = nullptr;
+        DM_CHECK(h->alloc(&icnt, nitems * 8, G_WORK));
+        w.sel = sel;
+        w.icnt = icnt;
         int32_t *perm = nullptr;
         DM_CUDA(dm_tree_build(h->X, h->N, h->d, h->eps, L, pa, pb, &perm, &w, h->stream));
         h->perm = perm;

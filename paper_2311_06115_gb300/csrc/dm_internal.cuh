@@ -220,9 +220,16 @@ struct DmTreeWork {
     void *cand1;      // as many candidates of dm_tree_cand_bytes() each
     void *cand2;
     int max_items;
+    // multi-CTA split of large nodes (sel == nullptr: one CTA per node at every level)
+    void *sel;        // max_big per-node select states of dm_tree_sel_bytes()
+    unsigned *hist;   // max_big x 256 digit histograms
+    void *icnt;       // max_items int2 per-item counts
+    int max_big;
 };
 size_t dm_tree_items_bound(int64_t N, int L);
 size_t dm_tree_item_bytes();
+size_t dm_tree_sel_bytes();
+int64_t dm_tree_big_node();  // nodes above this many points split over many CTAs
 size_t dm_tree_cand_bytes();
 cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, int32_t *perm_a, int32_t *perm_b,
                           int32_t **perm_out, DmTreeWork *w, cudaStream_t st);

@@ -184,6 +184,137 @@ __global__ void __launch_bounds__(1024) split_kernel(int first_node, int64_t N, 
     }
 }
 
+// ---- the split of large nodes across many CTAs (levels whose nodes exceed kBigNode points):
+// the same rule as split_kernel -- threshold T = the (ceil(n/2) - 1)-th smallest key by an
+// exact radix select (8-bit digits from the top), then a stable partition -- but the
+// histogram of every digit pass and the partition run over the level's 512-point items, with
+// per-node state in global memory; the partition ranks come from per-item counts.
+constexpr int64_t kBigNode = 8192;
+
+struct SplitSel {
+    unsigned long long prefix;  // digits chosen so far
+    long long k;                // rank still to find among the keys matching prefix
+    long long below;            // keys of the node smaller than the prefix's range
+    long long pad;
+};
+
+__global__ void split_sel_init_kernel(SplitSel *S, int first_node, int count, int64_t N, unsigned *hist) {
+    const int n = blockIdx.x;
+    if (n >= count) return;
+    if (threadIdx.x == 0) {
+        int64_t st, sz;
+        dm_node_range(N, first_node + n, &st, &sz);
+        S[n].prefix = 0ull;
+        S[n].k = (sz + 1) / 2 - 1;
+        S[n].below = 0;
+    }
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[n * 256 + b] = 0u;
+}
+
+__global__ void __launch_bounds__(512) split_hist_kernel(const TreeItem *__restrict__ items,
+                                                         const uint64_t *__restrict__ keys,
+                                                         const SplitSel *__restrict__ S, unsigned *hist,
+                                                         int first_node, int shift) {
+    __shared__ unsigned sh[256];
+    const TreeItem it = items[blockIdx.x];
+    const int n = it.node - first_node;
+    const unsigned long long mask = shift >= 56 ? 0ull : (~0ull << (shift + 8));
+    const unsigned long long pre = S[n].prefix & mask;
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) sh[b] = 0u;
+    __syncthreads();
+    for (long long pos = it.lo + threadIdx.x; pos < it.hi; pos += blockDim.x) {
+        const uint64_t key = keys[pos];
+        if ((key & mask) == pre) atomicAdd(&sh[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (sh[b]) atomicAdd(hist + n * 256 + b, sh[b]);
+}
+
+__global__ void split_step_kernel(SplitSel *S, unsigned *hist, int shift) {
+    const int n = blockIdx.x;
+    __shared__ int s_b;
+    __shared__ long long s_acc;
+    if (threadIdx.x == 0) {
+        long long acc = 0, k = S[n].k;
+        int b = 0;
+        for (; b < 255; ++b) {
+            if (acc + (long long)hist[n * 256 + b] > k) break;
+            acc += hist[n * 256 + b];
+        }
+        s_b = b;
+        s_acc = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        S[n].k -= s_acc;
+        S[n].below += s_acc;
+        S[n].prefix |= (unsigned long long)s_b << shift;
+    }
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[n * 256 + b] = 0u;
+}
+
+// per item: keys below the threshold and keys equal to it
+__global__ void __launch_bounds__(512) split_count_kernel(const TreeItem *__restrict__ items,
+                                                          const uint64_t *__restrict__ keys,
+                                                          const SplitSel *__restrict__ S, int first_node,
+                                                          int2 *__restrict__ icnt) {
+    __shared__ int warp_tot[32];
+    const TreeItem it = items[blockIdx.x];
+    const uint64_t T = S[it.node - first_node].prefix;
+    const long long pos = it.lo + threadIdx.x;
+    const bool valid = pos < it.hi;
+    const uint64_t key = valid ? keys[pos] : ~0ull;
+    int nlt, neq;
+    block_exclusive_count(valid && key < T, &nlt, warp_tot);
+    block_exclusive_count(valid && key == T, &neq, warp_tot);
+    if (threadIdx.x == 0) icnt[blockIdx.x] = make_int2(nlt, neq);
+}
+
+// stable partition: left = keys below T, then the first (ceil(n/2) - below) keys equal to T in
+// position order; an element's destination follows from the counts of the items before it
+__global__ void __launch_bounds__(512) split_scatter_kernel(const TreeItem *__restrict__ items,
+                                                            const uint64_t *__restrict__ keys,
+                                                            const SplitSel *__restrict__ S,
+                                                            const int2 *__restrict__ icnt, int first_node,
+                                                            int64_t N, const int32_t *__restrict__ perm_in,
+                                                            int32_t *__restrict__ perm_out) {
+    __shared__ int warp_tot[32];
+    __shared__ long long s_lt, s_eq;
+    const TreeItem it = items[blockIdx.x];
+    const int n = it.node - first_node;
+    int64_t st, sz;
+    dm_node_range(N, it.node, &st, &sz);
+    const int64_t nl = (sz + 1) / 2;
+    const uint64_t T = S[n].prefix;
+    const long long need_eq = nl - S[n].below;
+    if (threadIdx.x == 0) { s_lt = 0; s_eq = 0; }
+    __syncthreads();
+    long long lt_b = 0, eq_b = 0;
+    for (int t = it.first_item + (int)threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) {
+        const int2 c = icnt[t];
+        lt_b += c.x;
+        eq_b += c.y;
+    }
+    atomicAdd(reinterpret_cast<unsigned long long *>(&s_lt), (unsigned long long)lt_b);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&s_eq), (unsigned long long)eq_b);
+    __syncthreads();
+    const long long pos = it.lo + threadIdx.x;
+    const bool valid = pos < it.hi;
+    const uint64_t key = valid ? keys[pos] : ~0ull;
+    const bool lt = valid && key < T, eq = valid && key == T;
+    int tot;
+    const int lt_rank = block_exclusive_count(lt, &tot, warp_tot);
+    const int eq_rank = block_exclusive_count(eq, &tot, warp_tot);
+    if (!valid) return;
+    const long long gl_lt = s_lt + lt_rank, gl_eq = s_eq + eq_rank;
+    const bool left = lt || (eq && gl_eq < need_eq);
+    const long long left_before = gl_lt + (gl_eq < need_eq ? gl_eq : need_eq);
+    const long long i_node = pos - st;
+    const long long dest = left ? st + left_before : st + nl + (i_node - left_before);
+    perm_out[dest] = perm_in[pos];
+}
+
 }  // namespace
 
 cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, int32_t *perm_a, int32_t *perm_b,
@@ -231,8 +362,27 @@ cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, i
         dm_count_launches(1);
         key_kernel<<<n, kTreeThreads, 0, st>>>(li, X, d, in, c2, w->wbuf, eps, w->keys);
         dm_count_launches(1);
-        split_kernel<<<1 << lvl, 1024, 0, st>>>((1 << lvl) - 1, N, in, w->keys, out);
-        dm_count_launches(1);
+        int64_t s0, sz0;
+        dm_node_range(N, (1 << lvl) - 1, &s0, &sz0);
+        if (sz0 > kBigNode && w->sel && (1 << lvl) <= w->max_big) {
+            // large nodes: select and partition over the level's items
+            SplitSel *S = reinterpret_cast<SplitSel *>(w->sel);
+            const int first = (1 << lvl) - 1, count = 1 << lvl;
+            split_sel_init_kernel<<<count, 256, 0, st>>>(S, first, count, N, w->hist);
+            dm_count_launches(1);
+            for (int shift = 56; shift >= 0; shift -= 8) {
+                split_hist_kernel<<<n, 512, 0, st>>>(li, w->keys, S, w->hist, first, shift);
+                split_step_kernel<<<count, 256, 0, st>>>(S, w->hist, shift);
+                dm_count_launches(2);
+            }
+            int2 *icnt = reinterpret_cast<int2 *>(w->icnt);
+            split_count_kernel<<<n, 512, 0, st>>>(li, w->keys, S, first, icnt);
+            split_scatter_kernel<<<n, 512, 0, st>>>(li, w->keys, S, icnt, first, N, in, out);
+            dm_count_launches(2);
+        } else {
+            split_kernel<<<1 << lvl, 1024, 0, st>>>((1 << lvl) - 1, N, in, w->keys, out);
+            dm_count_launches(1);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         int32_t *t = in;
@@ -249,4 +399,6 @@ size_t dm_tree_items_bound(int64_t N, int L) {
     return n;
 }
 size_t dm_tree_item_bytes() { return sizeof(TreeItem); }
+size_t dm_tree_sel_bytes() { return sizeof(SplitSel); }
+int64_t dm_tree_big_node() { return kBigNode; }
 size_t dm_tree_cand_bytes() { return sizeof(Cand); }

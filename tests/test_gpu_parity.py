@@ -107,8 +107,10 @@ def test_exact_matvec_before_compress(dm):
 
 # ------------------------------------------------------------------ tree
 
-@pytest.mark.parametrize("n,leaf", [(2048, 128), (1500, 100), (777, 50), (4097, 256)])
+@pytest.mark.parametrize("n,leaf", [(2048, 128), (1500, 100), (777, 50), (4097, 256), (20000, 512), (17001, 300)])
 def test_tree_bit_exact(dm, n, leaf):
+    """The permutation equals the oracle's bit for bit; from 8192 points a node is split over
+    many CTAs (digit histograms and partition ranks from per-item counts)."""
     X = _scurve(n, 7)
     eps = O.median_sqdist(X)
     h = dm.dm_create(X, eps=eps)
