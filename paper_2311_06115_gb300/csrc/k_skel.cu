@@ -49,6 +49,8 @@ struct SkelArgs {
     float *R;   // per-CTA slot max_rank x cmax, row-major
     float *Q;   // per-CTA slot max_rank x rmax: orthonormal pivot columns, one contiguous vector each
     int prefilled;  // 1: A already holds K(R, C) (written by fill_entries_kernel for d > 3)
+    int smem_base;  // bytes of the fixed shared-memory layout (16-byte multiple)
+    int smemA;      // dynamic shared memory beyond it for the sampled block (0: A stays in global memory)
 };
 
 constexpr int kSkelMaxCand = 512;  // candidates per node (leaf points or two children's skeletons)
@@ -216,7 +218,6 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
     const int node = (1 << a.level) - 1 + (int)blockIdx.x;
     int64_t st, sz;
     dm_node_range(a.N, node, &st, &sz);
-    float *A = a.A + (size_t)blockIdx.x * a.rmax * a.lda;
     float *R = a.R + (size_t)blockIdx.x * a.max_rank * a.cmax;
     float *Q = a.Q + (size_t)blockIdx.x * a.max_rank * a.rmax;
 
@@ -248,6 +249,19 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
         }
     }
     for (int j = threadIdx.x; j < c; j += blockDim.x) selpos[j] = -1;
+    // the sampled block lives in shared memory when it fits (internal levels: few candidates),
+    // so that the passes of every pivot step avoid L2 round trips; else in the CTA's global slot
+    float *Ag = a.A + (size_t)blockIdx.x * a.rmax * a.lda;
+    const int ldas = (c + 3) & ~3;
+    const bool a_sm = a.smemA > 0 && (size_t)r * ldas * sizeof(float) <= (size_t)a.smemA;
+    float *A = a_sm ? reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem4) + a.smem_base) : Ag;
+    const int lda = a_sm ? ldas : a.lda;
+    if (a_sm && a.prefilled) {
+        for (int e = threadIdx.x; e < r * ldas; e += blockDim.x) {
+            const int i = e / ldas, j = e - i * ldas;
+            A[e] = Ag[(size_t)i * a.lda + j];
+        }
+    }
     __syncthreads();
 
     const SkelSplit sp4 = skel_split(c, r);
@@ -278,7 +292,7 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
                 for (int q = 0; q < 4; ++q) {
                     if (cj[q] < 0) { v[q] = 0.f; continue; }
                     if (a.prefilled) {
-                        v[q] = A[(size_t)i * a.lda + j0 + q];
+                        v[q] = A[(size_t)i * lda + j0 + q];
                     } else if (small_d) {
                         const float t0 = cx[q][0] - xr[i * 4], t1 = cx[q][1] - xr[i * 4 + 1], t2 = cx[q][2] - xr[i * 4 + 2];
                         v[q] = xr[i * 4 + 3] * sj[q] * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2)));
@@ -286,7 +300,7 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
                         v[q] = kentry(a.Xp, a.sp, a.d, Rw[i], cj[q]);
                     }
                 }
-                *reinterpret_cast<float4 *>(A + (size_t)i * a.lda + j0) = make_float4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<float4 *>(A + (size_t)i * lda + j0) = make_float4(v[0], v[1], v[2], v[3]);
                 ss.x = fmaf(v[0], v[0], ss.x);
                 ss.y = fmaf(v[1], v[1], ss.y);
                 ss.z = fmaf(v[2], v[2], ss.z);
@@ -339,7 +353,7 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
         const int p = s_p;
         if (!(s_np > a.tol * s_nrm0) || s_np <= 0.f) break;
         // ---- gather the pivot column, re-orthogonalise it once against q_0..q_{k-1}
-        for (int i = threadIdx.x; i < r; i += blockDim.x) qv[i] = A[(size_t)i * a.lda + p];
+        for (int i = threadIdx.x; i < r; i += blockDim.x) qv[i] = A[(size_t)i * lda + p];
         __syncthreads();
         if (k > 0) {
             for (int t = warp; t < k; t += kSkelWarps) {
@@ -385,7 +399,7 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
                 const float *base = A + j0;
 #pragma unroll 4
                 for (int i = i_lo; i < i_hi; ++i) {
-                    const float4 v = *reinterpret_cast<const float4 *>(base + (size_t)i * a.lda);
+                    const float4 v = *reinterpret_cast<const float4 *>(base + (size_t)i * lda);
                     const float qi = qv[i];
                     dp.x = fmaf(qi, v.x, dp.x);
                     dp.y = fmaf(qi, v.y, dp.y);
@@ -414,13 +428,13 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
                 float *base = A + j0;
 #pragma unroll 4
                 for (int i = i_lo; i < i_hi; ++i) {
-                    float4 v = *reinterpret_cast<float4 *>(base + (size_t)i * a.lda);
+                    float4 v = *reinterpret_cast<float4 *>(base + (size_t)i * lda);
                     const float qi = qv[i];
                     v.x = fmaf(-dk.x, qi, v.x);
                     v.y = fmaf(-dk.y, qi, v.y);
                     v.z = fmaf(-dk.z, qi, v.z);
                     v.w = fmaf(-dk.w, qi, v.w);
-                    *reinterpret_cast<float4 *>(base + (size_t)i * a.lda) = v;
+                    *reinterpret_cast<float4 *>(base + (size_t)i * lda) = v;
                     ss.x = fmaf(v.x, v.x, ss.x);
                     ss.y = fmaf(v.y, v.y, ss.y);
                     ss.z = fmaf(v.z, v.z, ss.z);
@@ -566,6 +580,12 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     e = cudaMemsetAsync(ranks, 0, sizeof(int32_t), st);  // the root has no skeleton
     if (e != cudaSuccess) return e;
     a.prefilled = d > 3 ? 1 : 0;
+    a.smem_base = (int)((smem + 15) & ~(size_t)15);
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t smem_int = (size_t)optin > (size_t)a.smem_base ? (size_t)optin : smem;
+    if ((e = dm_allow_smem((const void *)skel_level_kernel, smem_int)) != cudaSuccess) return e;
     const size_t fsmem = dm_fill_smem_bytes();
     if (a.prefilled && (e = dm_allow_smem((const void *)fill_entries_kernel, fsmem)) != cudaSuccess) return e;
     for (int lvl = L; lvl >= 1; --lvl) {
@@ -577,7 +597,11 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
             dm_count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        skel_level_kernel<<<1 << lvl, kSkelThreads, smem, st>>>(a);
+        // internal levels (few candidates per node) take the whole shared memory for the block;
+        // the leaf level keeps its footprint small so that several CTAs share an SM
+        const bool internal = lvl < L && smem_int > (size_t)a.smem_base;
+        a.smemA = internal ? (int)(smem_int - (size_t)a.smem_base) : 0;
+        skel_level_kernel<<<1 << lvl, kSkelThreads, internal ? smem_int : smem, st>>>(a);
         dm_count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
