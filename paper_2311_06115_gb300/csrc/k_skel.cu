@@ -584,7 +584,11 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     int optin = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem_int = (size_t)optin > (size_t)a.smem_base ? (size_t)optin : smem;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, (const void *)skel_level_kernel)) != cudaSuccess) return e;
+    // dynamic bytes allowed = per-block opt-in limit minus the kernel's static shared memory
+    const size_t dyn_max = ((size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0) & ~(size_t)15;
+    const size_t smem_int = dyn_max > (size_t)a.smem_base ? dyn_max : smem;
     if ((e = dm_allow_smem((const void *)skel_level_kernel, smem_int)) != cudaSuccess) return e;
     const size_t fsmem = dm_fill_smem_bytes();
     if (a.prefilled && (e = dm_allow_smem((const void *)fill_entries_kernel, fsmem)) != cudaSuccess) return e;
