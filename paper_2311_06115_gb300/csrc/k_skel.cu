@@ -50,7 +50,8 @@ struct SkelArgs {
     float *Q;   // per-CTA slot max_rank x rmax: orthonormal pivot columns, one contiguous vector each
     int prefilled;  // 1: A already holds K(R, C) (written by fill_entries_kernel for d > 3)
     int smem_base;  // bytes of the fixed shared-memory layout (16-byte multiple)
-    int smemA;      // dynamic shared memory beyond it for the sampled block (0: A stays in global memory)
+    int smem_extra; // dynamic shared memory beyond it: the sampled block when it fits, then rows of Q,
+                    // then (after the pivot steps) the triangular solve for P
 };
 
 constexpr int kSkelMaxCand = 512;  // candidates per node (leaf points or two children's skeletons)
@@ -253,9 +254,15 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
     // so that the passes of every pivot step avoid L2 round trips; else in the CTA's global slot
     float *Ag = a.A + (size_t)blockIdx.x * a.rmax * a.lda;
     const int ldas = (c + 3) & ~3;
-    const bool a_sm = a.smemA > 0 && (size_t)r * ldas * sizeof(float) <= (size_t)a.smemA;
-    float *A = a_sm ? reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem4) + a.smem_base) : Ag;
+    const size_t extra = a.smem_extra > 0 ? (size_t)a.smem_extra / sizeof(float) : 0;  // floats
+    float *xs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem4) + a.smem_base);
+    const bool a_sm = (size_t)r * ldas <= extra;
+    float *A = a_sm ? xs : Ag;
     const int lda = a_sm ? ldas : a.lda;
+    // rows t < qcap of Q follow in shared memory; later rows stay in the CTA's global slot
+    float *Qs = xs + (a_sm ? (size_t)r * ldas : 0);
+    int qcap = r > 0 ? (int)((extra - (a_sm ? (size_t)r * ldas : 0)) / (size_t)r) : 0;
+    if (qcap > a.max_rank) qcap = a.max_rank;
     if (a_sm && a.prefilled) {
         for (int e = threadIdx.x; e < r * ldas; e += blockDim.x) {
             const int i = e / ldas, j = e - i * ldas;
@@ -357,7 +364,7 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
         __syncthreads();
         if (k > 0) {
             for (int t = warp; t < k; t += kSkelWarps) {
-                const float *qt = Q + (size_t)t * a.rmax;
+                const float *qt = t < qcap ? Qs + (size_t)t * r : Q + (size_t)t * a.rmax;
                 float dsum = 0.f;
                 for (int i = lane; i < r; i += 32) dsum = fmaf(qt[i], qv[i], dsum);
                 dsum = dm_warp_sum(dsum);
@@ -366,7 +373,9 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
             __syncthreads();
             for (int i = threadIdx.x; i < r; i += blockDim.x) {
                 float v = qv[i];
-                for (int t = 0; t < k; ++t) v = fmaf(-coef[t], Q[(size_t)t * a.rmax + i], v);
+                const int kq = k < qcap ? k : qcap;
+                for (int t = 0; t < kq; ++t) v = fmaf(-coef[t], Qs[(size_t)t * r + i], v);
+                for (int t = kq; t < k; ++t) v = fmaf(-coef[t], Q[(size_t)t * a.rmax + i], v);
                 qv[i] = v;
             }
             for (int t = threadIdx.x; t < k; t += blockDim.x) R[(size_t)t * a.cmax + p] += coef[t];
@@ -389,7 +398,8 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
         for (int i = threadIdx.x; i < r; i += blockDim.x) {
             const float v = qv[i] * inv;
             qv[i] = v;
-            Q[(size_t)k * a.rmax + i] = v;
+            if (k < qcap) Qs[(size_t)k * r + i] = v;
+            else Q[(size_t)k * a.rmax + i] = v;
         }
         __syncthreads();
         // ---- R(k, :) = q^T A: float4 partial dots per row slice, reduced through shared memory
@@ -458,7 +468,31 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
 
     // ---- P = [I, R11^-1 R12] in candidate order; rows t < rank of the node's slot
     float *Pn = a.P + (size_t)node * a.max_rank * a.ldp;
-    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+    if ((size_t)rank * ldas <= extra) {
+        // in shared memory (A and Q are dead): Rs = R(0:rank, :); each unselected column is
+        // solved in place (the pivot columns it reads stay R11), in the same operation order as
+        // the global-memory form below; then coalesced row stores with the identity columns
+        float *Rs = xs;
+        for (int e = threadIdx.x; e < rank * ldas; e += blockDim.x) {
+            const int t = e / ldas, j = e - t * ldas;
+            Rs[e] = j < c ? R[(size_t)t * a.cmax + j] : 0.f;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+            if (selpos[j] >= 0) continue;
+            for (int t = rank - 1; t >= 0; --t) {
+                float v = Rs[(size_t)t * ldas + j];
+                for (int u = t + 1; u < rank; ++u) v = fmaf(-Rs[(size_t)t * ldas + piv[u]], Rs[(size_t)u * ldas + j], v);
+                Rs[(size_t)t * ldas + j] = v / Rs[(size_t)t * ldas + piv[t]];
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rank * c; e += blockDim.x) {
+            const int t = e / c, j = e - t * c;
+            const int sp_ = selpos[j];
+            Pn[(size_t)t * a.ldp + j] = sp_ >= 0 ? (t == sp_ ? 1.f : 0.f) : Rs[(size_t)t * ldas + j];
+        }
+    } else for (int j = threadIdx.x; j < c; j += blockDim.x) {
         const int sp_ = selpos[j];
         if (sp_ >= 0) {
             for (int t = 0; t < rank; ++t) Pn[(size_t)t * a.ldp + j] = (t == sp_) ? 1.f : 0.f;
@@ -590,6 +624,15 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     const size_t dyn_max = ((size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0) & ~(size_t)15;
     const size_t smem_int = dyn_max > (size_t)a.smem_base ? dyn_max : smem;
     if ((e = dm_allow_smem((const void *)skel_level_kernel, smem_int)) != cudaSuccess) return e;
+    // the leaf level (many CTAs) takes what still lets two CTAs share an SM (its register
+    // footprint allows two), which holds the Q rows of the ranks seen in practice
+    int sm_bytes = 0, reserved = 0;
+    cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const size_t half = (size_t)sm_bytes / 2;
+    size_t smem_leaf = half > (size_t)reserved + fa.sharedSizeBytes ? (half - reserved - fa.sharedSizeBytes) & ~(size_t)15 : 0;
+    if (smem_leaf > smem_int) smem_leaf = smem_int;
+    if (smem_leaf < (size_t)a.smem_base) smem_leaf = smem;
     const size_t fsmem = dm_fill_smem_bytes();
     if (a.prefilled && (e = dm_allow_smem((const void *)fill_entries_kernel, fsmem)) != cudaSuccess) return e;
     for (int lvl = L; lvl >= 1; --lvl) {
@@ -601,11 +644,11 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
             dm_count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        // internal levels (few candidates per node) take the whole shared memory for the block;
-        // the leaf level keeps its footprint small so that several CTAs share an SM
-        const bool internal = lvl < L && smem_int > (size_t)a.smem_base;
-        a.smemA = internal ? (int)(smem_int - (size_t)a.smem_base) : 0;
-        skel_level_kernel<<<1 << lvl, kSkelThreads, internal ? smem_int : smem, st>>>(a);
+        // internal levels (few candidates per node, at most one CTA per SM) take the whole
+        // shared memory, which holds the sampled block and Q
+        const size_t lsm = lvl < L ? smem_int : smem_leaf;
+        a.smem_extra = lsm > (size_t)a.smem_base ? (int)(lsm - (size_t)a.smem_base) : 0;
+        skel_level_kernel<<<1 << lvl, kSkelThreads, lsm, st>>>(a);
         dm_count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
