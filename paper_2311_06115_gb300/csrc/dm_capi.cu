@@ -548,7 +548,7 @@ int ensure_lanczos(dm_ctx *h) {
     DM_CHECK(h->alloc(&L.z, (size_t)L.ldv, G_LANCZOS));
     DM_CHECK(h->alloc(&L.alpha, (size_t)L.m_max + 1, G_LANCZOS));
     DM_CHECK(h->alloc(&L.beta, (size_t)L.m_max + 1, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.h, (size_t)2 * (L.m_max + 1), G_LANCZOS));
+    DM_CHECK(h->alloc(&L.h, (size_t)2 * (2 * (L.m_max + 1) + 2), G_LANCZOS));
     DM_CHECK(h->alloc(&L.nrm2, 1, G_LANCZOS));
     DM_CHECK(h->alloc(&L.theta, (size_t)kmax, G_LANCZOS));
     DM_CHECK(h->alloc(&L.resid, (size_t)kmax, G_LANCZOS));

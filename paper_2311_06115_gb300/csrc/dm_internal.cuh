@@ -301,7 +301,7 @@ struct DmLanczos {
     float *z;         // work vector (ldv, zero padded)
     double *alpha;    // m_max
     double *beta;     // m_max (beta[j] = |r_j|)
-    double *h;        // 2 x (m_max+1) projection coefficients (two passes)
+    double *h;        // 2 parities x (h0, h1: m_max+1 each; |z'|^2; pad) projection accumulators
     double *nrm2;     // scalar accumulator
     double *theta;    // kmax Ritz values (descending)
     double *resid;    // kmax residual bounds

@@ -43,12 +43,27 @@ __global__ void normalize_kernel(const float *__restrict__ z, int64_t N, const d
 
 
 // ---- one fused Lanczos orthogonalisation step (cooperative launch) --------------
-// Phases (each block owns a contiguous range of rows):
-//   1 h0 = V^T z        2 z -= V h0        3 h1 = V^T z        4 z -= V h1, |z|^2
-//   5 alpha_j = h0_j + h1_j, beta_j = |z|, V[:, j+1] = z / beta_j
-// separated by a grid barrier. The barrier spins with a bounded iteration count;
-// on exhaustion it raises *err and every block returns (the host reports a timeout).
+// Classical Gram-Schmidt twice, in three passes over this block's rows of V:
+//   A  h0 = V^T z                                              | grid barrier
+//   B  z' = z - V h0, then h1 = V^T z' and |z'|^2 (same rows)   | grid barrier
+//   C  z'' = z' - V h1, beta_j = |z''| = sqrt(|z'|^2 - |h1|^2),
+//      alpha_j = h0_j + h1_j, V[:, j+1] = z'' / beta_j
+// |z''|^2 = |z'|^2 - 2 h1^T V^T z' + h1^T V^T V h1 = |z'|^2 - |h1|^2 because V^T z' = h1
+// and V has orthonormal columns (to FP32 rounding after the first pass); the second
+// pass's correction h1 is O(FP32 eps |z'|), so the difference loses nothing.
+//
+// Work layout: rows in 16-byte quads (V and z are zero padded to ldv, a multiple of 64);
+// a warp item is 32 consecutive quads x 8 columns, so every lane has eight 16-byte loads
+// in flight. Dot products reduce by a reduce-scatter over the lanes (9 shuffles for 8
+// columns) into shared FP32 partials, then one FP64 atomic per column and block. The
+// update V h sums its per-chunk float4 partials in a fixed order (deterministic z').
+// The projection accumulators are double-buffered by step parity: block 0 clears the
+// other parity's set during step j, so no step needs a memset of its own; the barrier
+// counter grows monotonically within a solve (targets (2j+1) G and (2j+2) G).
+// Barriers spin with a bounded iteration count; on exhaustion they raise *err and every
+// block returns (the host reports a timeout).
 constexpr int kStepThreads = 256;
+constexpr int kStepWarps = kStepThreads / 32;
 constexpr long long kBarrierSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
@@ -81,105 +96,221 @@ __device__ bool grid_barrier(unsigned *ctr, unsigned target, int *err) {
     return s_ok != 0;
 }
 
-// partial V^T z over this block's rows: each thread owns up to two rows and loads all
-// columns for them back to back; per-column warp sums meet in shared memory and one
-// FP64 atomic per column and block goes to h. V goes through L2 (read four times a step).
-__device__ void block_project(const float *V, int64_t ldv, int ncols, const float *z, int64_t r0, int64_t r1,
-                              double *h, float *acc_s) {
-    const int lane = threadIdx.x & 31;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) acc_s[c] = 0.f;
-    __syncthreads();
-    for (int c0 = 0; c0 < ncols; c0 += 8) {
-        float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            const float zi = z[i];
+// sum of v[u] over the 32 lanes, scattered: lanes with (lane & 3) == 0 end up holding
+// the total for u = 4 b4 + 2 b3 + b2 (b_k = bit k of the lane); returns that value
+__device__ __forceinline__ float reduce_scatter8(float (&v)[8], int lane) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + u < ncols) p[u] = fmaf(__ldcg(V + (size_t)(c0 + u) * ldv + i), zi, p[u]);
-        }
+    for (int sft = 16, half = 4; sft >= 4; sft >>= 1, half >>= 1) {
+        const bool upper = (lane & sft) != 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const float w = dm_warp_sum(p[u]);
-            if (lane == 0 && c0 + u < ncols) atomicAdd(acc_s + c0 + u, w);
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(DM_FULL, send, sft);
         }
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) atomicAdd(h + c, (double)acc_s[c]);
+    float r = v[0];
+    r += __shfl_xor_sync(DM_FULL, r, 2);
+    r += __shfl_xor_sync(DM_FULL, r, 1);
+    return r;
+}
+__device__ __forceinline__ int scatter8_index(int lane) {
+    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-// z -= V h over this block's rows (thread per row, eight columns in flight);
-// optional |z|^2 into nrm2 (FP64)
-__device__ void block_update(const float *V, int64_t ldv, int ncols, float *z, int64_t r0, int64_t r1,
-                             const double *h, float *sh, double *nrm2) {
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) sh[c] = (float)__ldcg(h + c);
-    __syncthreads();
-    float ss = 0.f;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int c0 = 0; c0 < ncols; c0 += 8) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (c0 + u < ncols) ? __ldcg(V + (size_t)(c0 + u) * ldv + i) : 0.f;
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + u < ncols) a[u] = fmaf(v[u], sh[c0 + u], a[u]);
-        }
-        const float v = z[i] - (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
-        z[i] = v;
-        ss = fmaf(v, v, ss);
-    }
-    if (nrm2) {
-        ss = dm_warp_sum(ss);
-        if ((threadIdx.x & 31) == 0) atomicAdd(nrm2, (double)ss);
-    }
-    __syncthreads();
+__device__ __forceinline__ float4 ldq(const float *col, int64_t q) {
+    return __ldcg(reinterpret_cast<const float4 *>(col) + q);
 }
 
-__global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, int64_t ldv, int64_t N, int j,
-                                                                    float *z, double *h0, double *h1, double *nrm2,
-                                                                    double *alpha, double *beta, int m_max,
-                                                                    unsigned *bar, int *err, int phase) {
-    // phase < 0: the whole step in one cooperative launch, phases separated by grid
-    // barriers; phase 0..4: that phase alone (ordinary launches, the kernel boundary
+// acc[c] += sum over quads q0..q0+nq-1 of V(q, c) . y(q), c < ncols (shared FP32 partials);
+// y is global (ys == nullptr: read yg from quad q0) or a shared tile
+__device__ void tile_project(const float *V, int64_t ldv, int ncols, const float *yg, const float4 *ys, int64_t q0,
+                             int nq, float *acc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nch = (ncols + 7) >> 3, ng = (nq + 31) >> 5;
+    for (int it = warp; it < nch * ng; it += kStepWarps) {
+        const int g = it / nch, cc = it - g * nch;
+        const int ql = g * 32 + lane;
+        float p[8];
+        if (ql < nq) {
+            const float4 y = ys ? ys[ql] : ldq(yg, q0 + ql);
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = (cc * 8 + u < ncols) ? ldq(V + (size_t)(cc * 8 + u) * ldv, q0 + ql) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) p[u] = fmaf(v[u].x, y.x, fmaf(v[u].y, y.y, fmaf(v[u].z, y.z, v[u].w * y.w)));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) p[u] = 0.f;
+        }
+        const float r = reduce_scatter8(p, lane);
+        const int c = cc * 8 + scatter8_index(lane);
+        if ((lane & 3) == 0 && c < ncols) atomicAdd(acc + c, r);
+    }
+}
+
+// part[cs][ql] = sum over chunks cc = cs, cs + ncs, ... (ncs = min(chunks, warps)) of
+// sum_{c in cc} hs[c] V(q0 + ql, c): warp w takes chunk slot w % ncs of the quad groups
+// w / ncs, w / ncs + gpr, ... (gpr = warps / ncs groups side by side)
+__device__ void tile_combine(const float *V, int64_t ldv, int ncols, const float *hs, int64_t q0, int nq, int qt,
+                             float4 *part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nch = (ncols + 7) >> 3, ng = (nq + 31) >> 5;
+    const int ncs = nch < kStepWarps ? nch : kStepWarps, gpr = kStepWarps / ncs;
+    const int cs = warp % ncs, gs = warp / ncs;
+    if (gs >= gpr) return;
+    for (int g = gs; g < ng; g += gpr) {
+        const int ql = g * 32 + lane;
+        if (ql >= nq) continue;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int cc = cs; cc < nch; cc += ncs) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = (cc * 8 + u < ncols) ? ldq(V + (size_t)(cc * 8 + u) * ldv, q0 + ql)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float hc = hs[cc * 8 + u];  // zero past ncols
+                s.x = fmaf(hc, v[u].x, s.x);
+                s.y = fmaf(hc, v[u].y, s.y);
+                s.z = fmaf(hc, v[u].z, s.z);
+                s.w = fmaf(hc, v[u].w, s.w);
+            }
+        }
+        part[(size_t)cs * qt + ql] = s;
+    }
+}
+
+// z - (part[0][ql] + part[1][ql] + ...), slots in a fixed order
+__device__ __forceinline__ float4 sub_parts(float4 z, const float4 *part, int ncols, int qt, int ql) {
+    const int nch = (ncols + 7) >> 3, ncs = nch < kStepWarps ? nch : kStepWarps;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int cs = 0; cs < ncs; ++cs) {
+        const float4 p = part[(size_t)cs * qt + ql];
+        s.x += p.x;
+        s.y += p.y;
+        s.z += p.z;
+        s.w += p.w;
+    }
+    return make_float4(z.x - s.x, z.y - s.y, z.z - s.z, z.w - s.w);
+}
+
+__global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, int64_t ldv, int j, float *z,
+                                                                    double *hbuf, int hstride, double *alpha,
+                                                                    double *beta, int m_max, int qt, unsigned *bar,
+                                                                    int *err, int phase) {
+    // phase < 0: the whole step in one cooperative launch, passes separated by grid
+    // barriers; phase 0..2: that pass alone (ordinary launches, the kernel boundary
     // is the barrier)
-    extern __shared__ float sh[];  // (m_max + 1) coefficients, then (m_max + 1) partial sums
-    float *acc_s = sh + (m_max + 1);
-    const int ncols = j + 1;
-    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = blockIdx.x * per, r1 = (r0 + per < N) ? r0 + per : N;
+    const int nchmax = (m_max + 1 + 7) >> 3;
+    extern __shared__ float4 sh4[];
+    float4 *part = sh4;                                            // warps x qt
+    float4 *zs = part + (size_t)kStepWarps * qt;                  // qt
+    float *hs = reinterpret_cast<float *>(zs + qt);               // 8 nchmax coefficients
+    float *acc = hs + 8 * nchmax;                                  // 8 nchmax partial sums
+    __shared__ float red[kStepWarps];
+    __shared__ double s_beta;
+    const int ncols = j + 1, nch = (ncols + 7) >> 3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *h0 = hbuf + (size_t)(j & 1) * hstride, *h1 = h0 + (m_max + 1), *nz = h1 + (m_max + 1);
+    double *other = hbuf + (size_t)((j + 1) & 1) * hstride;
+    const int64_t Qn = ldv >> 2;
+    const int64_t per = (Qn + gridDim.x - 1) / gridDim.x;
+    const int64_t qb0 = blockIdx.x * per, qb1 = (qb0 + per < Qn) ? qb0 + per : Qn;
     const unsigned G = gridDim.x;
     const bool all = phase < 0;
-    if (all || phase == 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) *nrm2 = 0.0;
-        block_project(V, ldv, ncols, z, r0, r1, h0, acc_s);
+
+    if (all || phase == 0) {  // ---- A: h0 = V^T z
+        for (int c = threadIdx.x; c < 8 * nch; c += blockDim.x) acc[c] = 0.f;
+        __syncthreads();
+        for (int64_t q0 = qb0; q0 < qb1; q0 += qt)
+            tile_project(V, ldv, ncols, z, nullptr, q0, (int)(qb1 - q0 < qt ? qb1 - q0 : qt), acc);
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncols; c += blockDim.x) atomicAdd(h0 + c, (double)acc[c]);
     }
-    if (all && !grid_barrier(bar, G, err)) return;
-    if (all || phase == 1) block_update(V, ldv, ncols, z, r0, r1, h0, sh, nullptr);
-    if (all && !grid_barrier(bar, 2 * G, err)) return;
-    if (all || phase == 2) block_project(V, ldv, ncols, z, r0, r1, h1, acc_s);
-    if (all && !grid_barrier(bar, 3 * G, err)) return;
-    if (all || phase == 3) block_update(V, ldv, ncols, z, r0, r1, h1, sh, nrm2);
-    if (all && !grid_barrier(bar, 4 * G, err)) return;
-    if (!all && phase != 4) return;
-    const double b = sqrt(__ldcg(nrm2));
-    if (j + 1 <= m_max) {
-        float *vn = V + (size_t)(j + 1) * ldv;
-        const float inv = (float)(1.0 / b);
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) vn[i] = z[i] * inv;
+    if (all && !grid_barrier(bar, (2u * (unsigned)j + 1u) * G, err)) return;
+    if (all || phase == 1) {  // ---- B: z' = z - V h0; h1 = V^T z'; |z'|^2
+        for (int c = threadIdx.x; c < 8 * nch; c += blockDim.x) {
+            hs[c] = c < ncols ? (float)__ldcg(h0 + c) : 0.f;
+            acc[c] = 0.f;
+        }
+        float ss = 0.f;
+        for (int64_t q0 = qb0; q0 < qb1; q0 += qt) {
+            const int nq = (int)(qb1 - q0 < qt ? qb1 - q0 : qt);
+            __syncthreads();
+            tile_combine(V, ldv, ncols, hs, q0, nq, qt, part);
+            __syncthreads();
+            for (int ql = threadIdx.x; ql < nq; ql += blockDim.x) {
+                const float4 zp = sub_parts(ldq(z, q0 + ql), part, ncols, qt, ql);
+                zs[ql] = zp;
+                reinterpret_cast<float4 *>(z)[q0 + ql] = zp;
+                ss = fmaf(zp.x, zp.x, fmaf(zp.y, zp.y, fmaf(zp.z, zp.z, fmaf(zp.w, zp.w, ss))));
+            }
+            __syncthreads();
+            tile_project(V, ldv, ncols, nullptr, zs, q0, nq, acc);
+        }
+        ss = dm_warp_sum(ss);
+        if (lane == 0) red[warp] = ss;
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncols; c += blockDim.x) atomicAdd(h1 + c, (double)acc[c]);
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < kStepWarps; ++w) t += red[w];
+            atomicAdd(nz, (double)t);
+        }
     }
-    // block 0 records the coefficients, then clears the projection accumulators for the
-    // next step (no other block reads them past barrier 4)
+    if (all && !grid_barrier(bar, (2u * (unsigned)j + 2u) * G, err)) return;
+    if (!all && phase != 2) return;
+    // ---- C: z'' = z' - V h1, beta_j, V[:, j+1] = z'' / beta_j
+    for (int c = threadIdx.x; c < 8 * nch; c += blockDim.x) hs[c] = c < ncols ? (float)__ldcg(h1 + c) : 0.f;
+    if (warp == 0) {
+        double t = 0.0;
+        for (int c = lane; c < ncols; c += 32) {
+            const double v = __ldcg(h1 + c);
+            t = fma(v, v, t);
+        }
+        t = dm_warp_sum_d(t);
+        if (lane == 0) s_beta = sqrt(fmax(__ldcg(nz) - t, 0.0));
+    }
+    __syncthreads();
+    const double b = s_beta;
+    const float inv = b > 0.0 ? (float)(1.0 / b) : 0.f;
+    float *vn = (j + 1 <= m_max) ? V + (size_t)(j + 1) * ldv : nullptr;
+    for (int64_t q0 = qb0; q0 < qb1; q0 += qt) {
+        const int nq = (int)(qb1 - q0 < qt ? qb1 - q0 : qt);
+        __syncthreads();
+        tile_combine(V, ldv, ncols, hs, q0, nq, qt, part);
+        __syncthreads();
+        if (vn)
+            for (int ql = threadIdx.x; ql < nq; ql += blockDim.x) {
+                const float4 zpp = sub_parts(ldq(z, q0 + ql), part, ncols, qt, ql);
+                reinterpret_cast<float4 *>(vn)[q0 + ql] = make_float4(zpp.x * inv, zpp.y * inv, zpp.z * inv, zpp.w * inv);
+            }
+    }
+    // block 0 records the coefficients and clears the other parity's accumulators, which
+    // step j + 1 uses (step j - 1, their last user, has finished)
     if (blockIdx.x == 0) {
         if (threadIdx.x == 0) {
             alpha[j] = __ldcg(h0 + j) + __ldcg(h1 + j);
             beta[j] = b;
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < ncols + 1; c += blockDim.x) {
-            h0[c] = 0.0;
-            h1[c] = 0.0;
-        }
+        for (int c = threadIdx.x; c < hstride; c += blockDim.x) other[c] = 0.0;
     }
+}
+
+size_t step_smem_bytes(int m_max, int qt) {
+    const int nchmax = (m_max + 1 + 7) >> 3;
+    return sizeof(float4) * ((size_t)kStepWarps * qt + qt) + sizeof(float) * 16 * (size_t)nchmax;
+}
+
+int step_tile_quads(int m_max) {
+    // 128 quads (512 rows) per tile while the shared arrays stay under ~100 KB, which
+    // keeps two blocks on an SM (the coefficient arrays grow with m_max)
+    int qt = 128;
+    while (qt > 32 && step_smem_bytes(m_max, qt) > 100 * 1024) qt >>= 1;
+    return qt;
 }
 
 
@@ -492,45 +623,51 @@ cudaEvent_t g_coop_last = nullptr;
 // After Lz.z = A v_j: two Gram-Schmidt passes against V[:, 0..j], alpha_j, beta_j and
 // V[:, j+1], as one cooperative launch (grid = co-resident blocks on every SM).
 cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) {
-    double *h0 = Lz.h, *h1 = Lz.h + (Lz.m_max + 1);
+    const int hstride = 2 * (Lz.m_max + 1) + 2;
+    cudaError_t e;
     if (j == 0) {
-        cudaError_t e0 = cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (Lz.m_max + 1), st);
-        if (e0 != cudaSuccess) return e0;
+        if ((e = cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (size_t)hstride, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(Lz.bar, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     }
-    cudaError_t e = cudaMemsetAsync(Lz.bar, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-    static thread_local int grid = 0;
-    if (grid == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_step_kernel, kStepThreads,
-                                                          sizeof(float) * 2 * (Lz.m_max + 1));
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-        grid = sms * (per_sm < 2 ? per_sm : 2);
+    const int qt = step_tile_quads(Lz.m_max);
+    const size_t shm = step_smem_bytes(Lz.m_max, qt);
+    if ((e = dm_allow_smem((const void *)lanczos_step_kernel, shm)) != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int grid = 0;
+    {
+        // co-resident grid for this shared-memory size (at most two blocks per SM)
+        static std::mutex mu;
+        static std::map<std::pair<int, size_t>, int> grids;
+        std::lock_guard<std::mutex> lk(mu);
+        int &g = grids[std::make_pair(dev, shm)];
+        if (g == 0) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_step_kernel, kStepThreads, shm);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+            g = sms * (per_sm < 2 ? per_sm : 2);
+        }
+        grid = g;
     }
-    int jj = j, mm = Lz.m_max;
-    int64_t N = Lz.N, ldv = Lz.ldv;
-    const size_t shm = sizeof(float) * 2 * (Lz.m_max + 1);
+    int jj = j, mm = Lz.m_max, hs = hstride, q = qt;
+    int64_t ldv = Lz.ldv;
     if (phased) {
-        for (int ph = 0; ph < 5; ++ph) {
-            lanczos_step_kernel<<<grid, kStepThreads, shm, st>>>(Lz.V, ldv, N, jj, Lz.z, h0, h1, Lz.nrm2, Lz.alpha,
-                                                                 Lz.beta, mm, Lz.bar, Lz.err, ph);
+        for (int ph = 0; ph < 3; ++ph) {
+            lanczos_step_kernel<<<grid, kStepThreads, shm, st>>>(Lz.V, ldv, jj, Lz.z, Lz.h, hs, Lz.alpha, Lz.beta, mm,
+                                                                 q, Lz.bar, Lz.err, ph);
             dm_count_launches(1);
         }
         return cudaGetLastError();
     }
     int phase_all = -1;
-    void *args[] = {&Lz.V, &ldv, &N, &jj, &Lz.z, &h0, &h1, &Lz.nrm2, &Lz.alpha, &Lz.beta, &mm, &Lz.bar, &Lz.err,
-                    &phase_all};
+    void *args[] = {&Lz.V, &ldv, &jj, &Lz.z, &Lz.h, &hs, &Lz.alpha, &Lz.beta, &mm, &q, &Lz.bar, &Lz.err, &phase_all};
     // Each step kernel fills every SM; two of them from different streams (concurrent
     // solves) could each hold part of the device while waiting at a grid barrier for
     // blocks that cannot become resident. So all step launches of the process form one
     // chain: a launch waits for the previous one, whichever stream it was on.
     std::lock_guard<std::mutex> lk(g_coop_mu);
-    int dev = 0;
-    cudaGetDevice(&dev);
     cudaEvent_t &mine = g_coop_events[std::make_pair(dev, (void *)st)];
     if (!mine) {
         e = cudaEventCreateWithFlags(&mine, cudaEventDisableTiming);
