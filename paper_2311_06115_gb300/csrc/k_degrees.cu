@@ -198,6 +198,10 @@ __global__ void __launch_bounds__(kDegThreads) degree_pass_kernel(const float *_
 constexpr int kD3Threads = 128;
 constexpr int kD3Rows = 4 * kD3Threads;  // four rows per thread: two packed pairs
 constexpr float kDotFormMaxNorm = 8.f;
+#ifndef DM_SYM_ROW_PAIRS
+#define DM_SYM_ROW_PAIRS 4
+#endif
+constexpr int kSymRowPairs = DM_SYM_ROW_PAIRS;  // row pairs per thread of the symmetric pass
 
 struct Rows4 {
     float2 x0[2], x1[2], x2[2];
@@ -328,11 +332,15 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
-__global__ void __launch_bounds__(kD3Threads) degree_sym_d3_kernel(const float *__restrict__ Xs,
-                                                                   const float *__restrict__ nrm,
-                                                                   const float *__restrict__ nmax, int64_t N,
-                                                                   const float *__restrict__ w,
-                                                                   double *__restrict__ out, int nb) {
+template <int RP>
+__global__ void __launch_bounds__(kD3Rows / (2 * RP)) degree_sym_d3_kernel(const float *__restrict__ Xs,
+                                                                           const float *__restrict__ nrm,
+                                                                           const float *__restrict__ nmax, int64_t N,
+                                                                           const float *__restrict__ w,
+                                                                           double *__restrict__ out, int nb) {
+    // RP packed row pairs per thread: 2 RP rows of the tile against each column, so the
+    // column's shared loads and its lane reduce-scatter are shared by 2 RP entries
+    constexpr int T = kD3Rows / (2 * RP);
     __shared__ float4 ta[kDegTile];
     __shared__ float4 tb[kDegTile];
     __shared__ float2 tw[kDegTile];
@@ -349,32 +357,35 @@ __global__ void __launch_bounds__(kD3Threads) degree_sym_d3_kernel(const float *
     const bool dot_form = nrm != nullptr && *nmax <= kDotFormMaxNorm;
     const float sc = dot_form ? 2.f : 1.f;
     const int lane = threadIdx.x & 31;
+    // rows of this thread: I kD3Rows + threadIdx.x + q T, q < 2 RP; pair p holds rows 2p, 2p+1
     const int64_t row0 = (int64_t)I * kD3Rows + threadIdx.x;
-    float xr[4][3], wr[4];
+    float2 X0[RP], X1[RP], X2[RP], W[RP];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t rq = row0 + (int64_t)q * kD3Threads;
-        const bool ok = rq < N;
+    for (int p = 0; p < RP; ++p) {
+        float xr[2][3], wr[2];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) xr[q][k] = ok ? sc * Xs[rq * 3 + k] : 0.f;
-        // column weights: w_i, times the row factor 2^-n_i in the dot form
-        wr[q] = ok ? (w ? w[rq] : 1.f) * (dot_form ? dm_ex2(-nrm[rq]) : 1.f) : 0.f;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t rq = row0 + (int64_t)(2 * p + h) * T;
+            const bool ok = rq < N;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) xr[h][k] = ok ? sc * Xs[rq * 3 + k] : 0.f;
+            // column weights: w_i, times the row factor 2^-n_i in the dot form
+            wr[h] = ok ? (w ? w[rq] : 1.f) * (dot_form ? dm_ex2(-nrm[rq]) : 1.f) : 0.f;
+        }
+        X0[p] = make_float2(xr[0][0], xr[1][0]);
+        X1[p] = make_float2(xr[0][1], xr[1][1]);
+        X2[p] = make_float2(xr[0][2], xr[1][2]);
+        W[p] = make_float2(wr[0], wr[1]);
     }
-    Rows4 X;
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        X.x0[p] = make_float2(xr[2 * p][0], xr[2 * p + 1][0]);
-        X.x1[p] = make_float2(xr[2 * p][1], xr[2 * p + 1][1]);
-        X.x2[p] = make_float2(xr[2 * p][2], xr[2 * p + 1][2]);
-    }
-    const float2 W01 = make_float2(wr[0], wr[1]), W23 = make_float2(wr[2], wr[3]);
     const int64_t c0 = (int64_t)J * kD3Rows;
     const int64_t c1 = (c0 + kD3Rows < N) ? c0 + kD3Rows : N;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[2 * RP];
+#pragma unroll
+    for (int q = 0; q < 2 * RP; ++q) acc[q] = 0.0;
     for (int64_t t0 = c0; t0 < c1; t0 += kDegTile) {
         const int tn = (int)(c1 - t0 < kDegTile ? c1 - t0 : kDegTile);
         __syncthreads();
-        for (int e = threadIdx.x; e < kDegTile; e += kD3Threads) {
+        for (int e = threadIdx.x; e < kDegTile; e += T) {
             colsum[e] = 0.f;
             if (e >= tn) continue;
             const int64_t j = t0 + e;
@@ -391,7 +402,9 @@ __global__ void __launch_bounds__(kD3Threads) degree_sym_d3_kernel(const float *
             tw[e] = make_float2(wj, wj);
         }
         __syncthreads();
-        float2 part0 = make_float2(0.f, 0.f), part1 = make_float2(0.f, 0.f);
+        float2 part[RP];
+#pragma unroll
+        for (int p = 0; p < RP; ++p) part[p] = make_float2(0.f, 0.f);
         for (int jc = 0; jc < tn; jc += 32) {
             float cp[32];
 #pragma unroll
@@ -402,33 +415,33 @@ __global__ void __launch_bounds__(kD3Threads) degree_sym_d3_kernel(const float *
                     const float4 a = ta[j], b = tb[j];
                     const float2 wj = tw[j];
                     const float2 cx = make_float2(a.x, a.y), cy = make_float2(a.z, a.w), cz = make_float2(b.x, b.y);
-                    float2 e0, e1;
+                    float2 e[RP];
                     if (dot_form) {
                         const float2 cn = make_float2(b.z, b.w);
-                        float2 g0 = __ffma2_rn(X.x2[0], cz, cn);
-                        float2 g1 = __ffma2_rn(X.x2[1], cz, cn);
-                        g0 = __ffma2_rn(X.x1[0], cy, g0);
-                        g1 = __ffma2_rn(X.x1[1], cy, g1);
-                        g0 = __ffma2_rn(X.x0[0], cx, g0);
-                        g1 = __ffma2_rn(X.x0[1], cx, g1);
-                        e0 = make_float2(dm_ex2(g0.x), dm_ex2(g0.y));
-                        e1 = make_float2(dm_ex2(g1.x), dm_ex2(g1.y));
+#pragma unroll
+                        for (int p = 0; p < RP; ++p) {
+                            float2 g = __ffma2_rn(X2[p], cz, cn);
+                            g = __ffma2_rn(X1[p], cy, g);
+                            g = __ffma2_rn(X0[p], cx, g);
+                            e[p] = make_float2(dm_ex2(g.x), dm_ex2(g.y));
+                        }
                     } else {
-                        const float2 d0 = __fadd2_rn(X.x0[0], cx), f0 = __fadd2_rn(X.x0[1], cx);
-                        const float2 d1 = __fadd2_rn(X.x1[0], cy), f1 = __fadd2_rn(X.x1[1], cy);
-                        const float2 d2 = __fadd2_rn(X.x2[0], cz), f2 = __fadd2_rn(X.x2[1], cz);
-                        float2 r0 = __fmul2_rn(d0, d0), r1 = __fmul2_rn(f0, f0);
-                        r0 = __ffma2_rn(d1, d1, r0);
-                        r1 = __ffma2_rn(f1, f1, r1);
-                        r0 = __ffma2_rn(d2, d2, r0);
-                        r1 = __ffma2_rn(f2, f2, r1);
-                        e0 = make_float2(dm_ex2(-r0.x), dm_ex2(-r0.y));
-                        e1 = make_float2(dm_ex2(-r1.x), dm_ex2(-r1.y));
+#pragma unroll
+                        for (int p = 0; p < RP; ++p) {
+                            const float2 d0 = __fadd2_rn(X0[p], cx), d1 = __fadd2_rn(X1[p], cy),
+                                         d2 = __fadd2_rn(X2[p], cz);
+                            float2 r = __fmul2_rn(d0, d0);
+                            r = __ffma2_rn(d1, d1, r);
+                            r = __ffma2_rn(d2, d2, r);
+                            e[p] = make_float2(dm_ex2(-r.x), dm_ex2(-r.y));
+                        }
                     }
-                    part0 = __ffma2_rn(e0, wj, part0);
-                    part1 = __ffma2_rn(e1, wj, part1);
+#pragma unroll
+                    for (int p = 0; p < RP; ++p) part[p] = __ffma2_rn(e[p], wj, part[p]);
                     if (offdiag) {
-                        const float2 c2 = __ffma2_rn(e0, W01, __fmul2_rn(e1, W23));
+                        float2 c2 = __fmul2_rn(e[RP - 1], W[RP - 1]);
+#pragma unroll
+                        for (int p = RP - 2; p >= 0; --p) c2 = __ffma2_rn(e[p], W[p], c2);
                         cp[u] = c2.x + c2.y;
                     }
                 }
@@ -438,18 +451,19 @@ __global__ void __launch_bounds__(kD3Threads) degree_sym_d3_kernel(const float *
                 if (jc + lane < tn) atomicAdd(&colsum[jc + lane], v);
             }
         }
-        acc[0] += (double)part0.x;
-        acc[1] += (double)part0.y;
-        acc[2] += (double)part1.x;
-        acc[3] += (double)part1.y;
+#pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            acc[2 * p] += (double)part[p].x;
+            acc[2 * p + 1] += (double)part[p].y;
+        }
         if (offdiag) {
             __syncthreads();
-            for (int e = threadIdx.x; e < tn; e += kD3Threads) atomicAdd(out + t0 + e, (double)colsum[e]);
+            for (int e = threadIdx.x; e < tn; e += T) atomicAdd(out + t0 + e, (double)colsum[e]);
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t rq = row0 + (int64_t)q * kD3Threads;
+    for (int q = 0; q < 2 * RP; ++q) {
+        const int64_t rq = row0 + (int64_t)q * T;
         if (rq >= N) continue;
         double v = acc[q];
         if (dot_form) v *= (double)dm_ex2(-nrm[rq]);
@@ -612,7 +626,8 @@ cudaError_t dm_launch_degree_pass_centered(const float *Xs, const float *nrm, co
         // symmetric tiles: half the entries
         const int64_t nb = (N + kD3Rows - 1) / kD3Rows;
         const int64_t tiles = nb * (nb + 1) / 2;
-        degree_sym_d3_kernel<<<(unsigned)tiles, kD3Threads, 0, st>>>(Xs, nrm, nmax, N, wcol, out, (int)nb);
+        degree_sym_d3_kernel<kSymRowPairs><<<(unsigned)tiles, kD3Rows / (2 * kSymRowPairs), 0, st>>>(
+            Xs, nrm, nmax, N, wcol, out, (int)nb);
         dm_count_launches(1);
         return cudaGetLastError();
     }
