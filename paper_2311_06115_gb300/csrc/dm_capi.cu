@@ -891,14 +891,14 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         DM_CUDA(dm_permute_points(h->Xs, h->sf, h->perm, h->N, h->d, h->Xp, h->sp, h->stream));
         DmSkelWork w{};
         w.rmax = 2 * max_rank + 10;
-        w.lda = (int)round_up(h->cmax, 32);
+        w.ldr = (int)round_up(w.rmax, 4);
         const size_t smem = dm_skel_smem_bytes(h->cmax, w.rmax, max_rank);
         if (smem > 220 * 1024 || h->cmax > dm_skel_max_candidates())
             return fail(DM_EINVAL, "leaf size (%d) / rank (%d) too large for the skeletonization kernel",
                         h->leaf_max, max_rank);
-        DM_CHECK(h->alloc(&w.A, (size_t)nleaves * w.rmax * w.lda, G_WORK));
+        DM_CHECK(h->alloc(&w.A, (size_t)nleaves * h->cmax * w.ldr, G_WORK));
         DM_CHECK(h->alloc(&w.R, (size_t)nleaves * max_rank * h->cmax, G_WORK));
-        DM_CHECK(h->alloc(&w.Q, (size_t)nleaves * max_rank * w.rmax, G_WORK));
+        DM_CHECK(h->alloc(&w.Q, (size_t)nleaves * max_rank * w.ldr, G_WORK));
         DM_CUDA(dm_skeletonize(h->Xp, h->sp, h->N, h->d, L, h->perm, tol, max_rank, h->cmax, h->ldp, h->cfg.seed,
                                h->ranks, h->skel, h->P, &w, h->stream));
         ms_skel = t.stop();

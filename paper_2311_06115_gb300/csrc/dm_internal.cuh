@@ -236,11 +236,11 @@ cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, i
 
 // k_skel.cu
 struct DmSkelWork {
-    float *A;      // per node slot rmax x lda (row-major)
+    float *A;      // per node slot cmax x ldr (column-major sampled block)
     float *R;      // per node slot max_rank x cmax
-    float *Q;      // per node slot max_rank x rmax
+    float *Q;      // per node slot max_rank x ldr
     int rmax;
-    int lda;       // cmax rounded up to 32
+    int ldr;       // rmax rounded up to 4
 };
 int dm_skel_max_candidates();
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank);

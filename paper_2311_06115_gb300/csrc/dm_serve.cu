@@ -167,7 +167,7 @@ uint64_t dm_request_bytes(const dm_request *r) {
     const uint64_t leaf_max = (N + nleaves - 1) / nleaves;
     const uint64_t ldk = (leaf_max + 3) & ~3ull;
     const uint64_t cmax = leaf_max > 2 * R ? leaf_max : 2 * R;
-    const uint64_t ldp = (cmax + 3) & ~3ull, lda = (cmax + 31) & ~31ull, rmax = 2 * R + 10;
+    const uint64_t ldp = (cmax + 3) & ~3ull, rmax = 2 * R + 10, ldr = (rmax + 3) & ~3ull;
     const uint64_t mmax = 300, kmax = (uint64_t)dm_lanczos_kmax(), ldv = (N + 63) & ~63ull;
     uint64_t b = 0;
     // points, degrees and scalings
@@ -177,7 +177,7 @@ uint64_t dm_request_bytes(const dm_request *r) {
     b += 2 * r256(4 * N) + r256(4 * nleaves * leaf_max * ldk) + r256(4 * (nleaves > 1 ? nleaves - 1 : 1) * R * R);
     b += 2 * r256(4 * nnodes * R) + r256(4 * N) + r256(4 * nnodes) + r256(4 * nleaves * leaf_max * ((R + 3) & ~3ull));
     // transient workspaces of the compression (skeletonization is the largest)
-    b += r256(4 * nleaves * rmax * lda) + r256(4 * nleaves * R * cmax) + r256(4 * nleaves * R * rmax);
+    b += r256(4 * nleaves * cmax * ldr) + r256(4 * nleaves * R * cmax) + r256(4 * nleaves * R * ldr);
     // the upper tree's shared-memory images (at most one cluster's shared memory)
     b += r256((uint64_t)8 * kTreeSmemBudget) + r256(16 * nnodes) + 256;
     // Lanczos basis, Ritz vectors and small arrays

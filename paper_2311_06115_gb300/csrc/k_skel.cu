@@ -8,14 +8,17 @@
 // pivot whose residual column norm is <= tol * (first pivot norm) -- the block-relative
 // reading of the tolerance of Eq. 1.1 -- or at max_rank.
 //
-// GPU design: one CTA per node of a level; the sampled block (at most
-// (2 max_rank + 10) x cmax FP32) lives in a per-CTA slot of global memory that
-// stays in L2 while the CTA works on it. Column-pivoted modified Gram-Schmidt
-// with explicit residual updates (each step recomputes every remaining column
-// norm from its updated residual, so no norm downdating loses the small
-// residuals that decide the rank) and one re-orthogonalisation of the pivot
-// column; a warp owns a column at a time. P_a = [I, R11^-1 R12] by back
-// substitution, one thread per candidate column.
+// GPU design: one CTA per node of a level. The sampled block A = K(R_a, C_a) is stored
+// column-major (a candidate column is one contiguous vector of ldr >= r floats) in shared
+// memory when it fits (internal levels: at most two children's skeletons), else in a
+// per-CTA slot of global memory. Column-pivoted modified Gram-Schmidt with explicit
+// residual updates (each step recomputes every remaining column norm from its updated
+// residual, so no norm downdating loses the small residuals that decide the rank) and one
+// re-orthogonalisation of the pivot column. A warp owns whole columns: one read-modify-
+// write pass per step gives q_k^T a_j (warp reduction), the update a_j -= (q_k^T a_j) q_k
+// and the new norm |a_j|, for a few columns at a time so that every lane keeps several
+// 16-byte loads in flight; every warp finds the next pivot itself from the shared norms,
+// so a step needs three block barriers. P_a = [I, R11^-1 R12] by back substitution.
 #include "dm_internal.cuh"
 
 namespace {
@@ -40,14 +43,14 @@ struct SkelArgs {
     int64_t N;
     int d, L, level;
     float tol;
-    int max_rank, cmax, ldp, rmax, lda;
+    int max_rank, cmax, ldp, rmax, ldr;
     uint64_t seed;
     int32_t *ranks;
     int32_t *skel;
     float *P;
-    float *A;   // per-CTA slot rmax x lda, row-major: A[i][j], i a sampled row, j a candidate
+    float *A;   // per-CTA slot cmax x ldr, column-major: A[j][i], j a candidate, i a sampled row
     float *R;   // per-CTA slot max_rank x cmax, row-major
-    float *Q;   // per-CTA slot max_rank x rmax: orthonormal pivot columns, one contiguous vector each
+    float *Q;   // per-CTA slot max_rank x ldr: orthonormal pivot columns, one contiguous vector each
     int prefilled;  // 1: A already holds K(R, C) (written by fill_entries_kernel for d > 3)
     int smem_base;  // bytes of the fixed shared-memory layout (16-byte multiple)
     int smem_extra; // dynamic shared memory beyond it: the sampled block when it fits, then rows of Q,
@@ -55,23 +58,7 @@ struct SkelArgs {
 };
 
 constexpr int kSkelMaxCand = 512;  // candidates per node (leaf points or two children's skeletons)
-
-// Work split of the sampled block: thread t owns the 4 adjacent columns of group
-// t % ncg over the row slice t / ncg (16-byte loads, coalesced along a row).
-struct SkelSplit {
-    int ncg, nsl, rps;
-};
-__device__ __forceinline__ SkelSplit skel_split(int c, int r) {
-    SkelSplit s;
-    s.ncg = c > 0 ? (c + 3) >> 2 : 1;
-    int nsl = kSkelThreads / s.ncg;
-    const int cap = (r + 15) / 16;  // keep at least 16 rows per slice
-    if (nsl > cap) nsl = cap;
-    if (nsl < 1) nsl = 1;
-    s.nsl = nsl;
-    s.rps = (r + nsl - 1) / nsl;
-    return s;
-}
+constexpr int kSkelMaxF4 = 5;      // float4 rows per lane in the column passes: r <= 640
 
 // ---- kernel entries of a block for d > 3, tiled over the coordinates ------------------
 // E[r][c] = s_row s_col 2^-|xs_row - xs_col|^2 for up to 32 rows (one CTA) and up to 512
@@ -173,54 +160,137 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
         }
     }
     // entries, written with zero padding
+    if (mode == 0) {
+        // column-major: the thread's four consecutive rows of column j are one 16-byte store;
+        // rows from r up to the next multiple of four are written as zeros
+        const int tq = t0 + 4 * rg;
+        if (tq < r) {
+            float si[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) si[i] = rowpos[4 * rg + i] >= 0 ? a.sp[rowpos[4 * rg + i]] : 0.f;
+            float *slot = a.A + (size_t)blockIdx.x * a.cmax * a.ldr;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int j = cg + 32 * q;
+                if (j >= c) continue;
+                const float sj = a.sp[colpos[j]];
+                float v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = rowpos[4 * rg + i] >= 0 ? si[i] * sj * dm_ex2(-acc[i][q]) : 0.f;
+                *reinterpret_cast<float4 *>(slot + (size_t)j * a.ldr + tq) = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int t = t0 + 4 * rg + i;
         const int pos = rowpos[4 * rg + i];
-        float *out;
-        int width;
-        if (mode == 0) {
-            if (t >= r) continue;
-            out = a.A + ((size_t)blockIdx.x * a.rmax + t) * a.lda;
-            width = (c + 3) & ~3;
-        } else {
-            if (t >= leaf_max) continue;
-            out = Knear + ((size_t)blockIdx.x * leaf_max + t) * ldk;
-            width = ldk;
-        }
+        if (t >= leaf_max) continue;
+        float *out = Knear + ((size_t)blockIdx.x * leaf_max + t) * ldk;
         const float si = pos >= 0 ? a.sp[pos] : 0.f;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int j = cg + 32 * q;
-            if (j < width) out[j] = (pos >= 0 && j < c) ? si * a.sp[colpos[j]] * dm_ex2(-acc[i][q]) : 0.f;
+            if (j < ldk) out[j] = (pos >= 0 && j < c) ? si * a.sp[colpos[j]] * dm_ex2(-acc[i][q]) : 0.f;
         }
     }
 }
 
-__global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w))); }
+__device__ __forceinline__ float4 scale4(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+__device__ __forceinline__ float warp_allsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DM_FULL, v, o);
+    return v;
+}
+
+// One pass over a batch of CB of the warp's columns (column j = warp + kSkelWarps (b CB + u)):
+// d_j = q^T a_j, a_j -= d_j q, norms[j] = |a_j|, R(k, j) = d_j. Lane holds float4 rows
+// f = lane + 32 m, m < M, of each column (f < nf). q = qv * inv, recomputed from shared
+// memory at each use (the same product every time).
+template <int M, int CB>
+__device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int c, int b, const float4 *qv, float inv,
+                                             const int *selpos, float *norms, float *Rk) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int jb[CB];
+    bool ok[CB];
+#pragma unroll
+    for (int u = 0; u < CB; ++u) {
+        jb[u] = warp + kSkelWarps * (b * CB + u);
+        ok[u] = jb[u] < c && selpos[jb[u]] < 0;
+    }
+    float4 v[CB][M];
+#pragma unroll
+    for (int u = 0; u < CB; ++u)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int f = lane + 32 * m;
+            v[u][m] = (ok[u] && f < nf) ? reinterpret_cast<const float4 *>(At + (size_t)jb[u] * ldr)[f]
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    float dj[CB];
+#pragma unroll
+    for (int u = 0; u < CB; ++u) dj[u] = 0.f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int f = lane + 32 * m;
+        const float4 q = f < nf ? scale4(qv[f], inv) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < CB; ++u) dj[u] += dot4(v[u][m], q);
+    }
+#pragma unroll
+    for (int u = 0; u < CB; ++u) dj[u] = warp_allsum(dj[u]);
+    float ss[CB];
+#pragma unroll
+    for (int u = 0; u < CB; ++u) ss[u] = 0.f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int f = lane + 32 * m;
+        if (f >= nf) continue;
+        const float4 q = scale4(qv[f], inv);
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            if (!ok[u]) continue;
+            float4 w = v[u][m];
+            w.x = fmaf(-dj[u], q.x, w.x);
+            w.y = fmaf(-dj[u], q.y, w.y);
+            w.z = fmaf(-dj[u], q.z, w.z);
+            w.w = fmaf(-dj[u], q.w, w.w);
+            reinterpret_cast<float4 *>(At + (size_t)jb[u] * ldr)[f] = w;
+            ss[u] += dot4(w, w);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < CB; ++u) {
+        ss[u] = warp_allsum(ss[u]);
+        if (lane == 0 && ok[u]) {
+            norms[jb[u]] = sqrtf(ss[u]);
+            Rk[jb[u]] = dj[u];
+        }
+    }
+}
+
+template <int M, int CB>
+__global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a) {
     // float4-accessed arrays first so that every one starts on a 16-byte boundary
     extern __shared__ float4 smem4[];
-    float *red = reinterpret_cast<float *>(smem4);       // kSkelThreads x 4 partials
-    float *dots = red + 4 * kSkelThreads;                // cmax rounded to 4: R(k, :)
-    float *xr = dots + ((a.cmax + 3) & ~3);              // rmax x 4: row coordinates (d <= 3) and s
-    int *C = reinterpret_cast<int *>(xr + 4 * a.rmax);   // cmax candidate positions
+    float4 *qv4 = smem4;                                 // ldr / 4: pivot residual (then v)
+    float *norms = reinterpret_cast<float *>(qv4 + (a.ldr >> 2));  // cmax
+    float *xr = norms + a.cmax;                          // rmax x 4: row coordinates (d <= 3) and s
+    float *coef = xr + 4 * a.rmax;                       // max_rank: re-orthogonalisation coefficients
+    int *C = reinterpret_cast<int *>(coef + a.max_rank); // cmax candidate positions
     int *Rw = C + a.cmax;                                // rmax row positions
     int *selpos = Rw + a.rmax;                           // cmax: -1 or pivot step
     int *piv = selpos + a.cmax;                          // max_rank
-    float *norms = reinterpret_cast<float *>(piv + a.max_rank);  // cmax
-    float *qv = norms + a.cmax;                          // rmax: current pivot column
-    float *coef = qv + a.rmax;                           // max_rank: re-orthogonalisation coefficients
-    __shared__ float red_v[kSkelWarps];
-    __shared__ int red_i[kSkelWarps];
-    __shared__ int s_p;
-    __shared__ float s_np, s_nrm0, s_qn;
+    __shared__ float wred[kSkelWarps];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int node = (1 << a.level) - 1 + (int)blockIdx.x;
     int64_t st, sz;
     dm_node_range(a.N, node, &st, &sz);
     float *R = a.R + (size_t)blockIdx.x * a.max_rank * a.cmax;
-    float *Q = a.Q + (size_t)blockIdx.x * a.max_rank * a.rmax;
+    float *Q = a.Q + (size_t)blockIdx.x * a.max_rank * a.ldr;
 
     // ---- candidates
     int c;
@@ -251,89 +321,75 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
     }
     for (int j = threadIdx.x; j < c; j += blockDim.x) selpos[j] = -1;
     // the sampled block lives in shared memory when it fits (internal levels: few candidates),
-    // so that the passes of every pivot step avoid L2 round trips; else in the CTA's global slot
-    float *Ag = a.A + (size_t)blockIdx.x * a.rmax * a.lda;
-    const int ldas = (c + 3) & ~3;
+    // else in the CTA's global slot; rows of Q follow it in shared memory while they fit
+    const int nf = (r + 3) >> 2;  // float4 rows per column
+    const int ldr = a.ldr;
+    float *Ag = a.A + (size_t)blockIdx.x * a.cmax * ldr;
     const size_t extra = a.smem_extra > 0 ? (size_t)a.smem_extra / sizeof(float) : 0;  // floats
     float *xs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem4) + a.smem_base);
-    const bool a_sm = (size_t)r * ldas <= extra;
-    float *A = a_sm ? xs : Ag;
-    const int lda = a_sm ? ldas : a.lda;
-    // rows t < qcap of Q follow in shared memory; later rows stay in the CTA's global slot
-    float *Qs = xs + (a_sm ? (size_t)r * ldas : 0);
-    int qcap = r > 0 ? (int)((extra - (a_sm ? (size_t)r * ldas : 0)) / (size_t)r) : 0;
+    const bool a_sm = (size_t)c * ldr <= extra;
+    float *At = a_sm ? xs : Ag;
+    float *Qs = xs + (a_sm ? (size_t)c * ldr : 0);
+    int qcap = (int)((extra - (a_sm ? (size_t)c * ldr : 0)) / (size_t)ldr);
     if (qcap > a.max_rank) qcap = a.max_rank;
-    if (a_sm && a.prefilled) {
-        for (int e = threadIdx.x; e < r * ldas; e += blockDim.x) {
-            const int i = e / ldas, j = e - i * ldas;
-            A[e] = Ag[(size_t)i * a.lda + j];
-        }
-    }
+    auto qrow = [&](int t) -> float4 * {
+        return reinterpret_cast<float4 *>(t < qcap ? Qs + (size_t)t * ldr : Q + (size_t)t * ldr);
+    };
     __syncthreads();
 
-    const SkelSplit sp4 = skel_split(c, r);
-    const int g = threadIdx.x % sp4.ncg, slice = threadIdx.x / sp4.ncg;
-    const bool worker = slice < sp4.nsl;
-    const int j0 = 4 * g;
-    const int i_lo = slice * sp4.rps, i_hi = min(r, i_lo + sp4.rps);
-
-    // ---- sampled block A = K(R, C) (zero in padding columns) and partial column norms
-    {
-        float4 ss = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (worker) {
-            int64_t cj[4];
-            float sj[4], cx[4][3];
-            for (int q = 0; q < 4; ++q) {
-                const int j = j0 + q;
-                cj[q] = j < c ? C[j] : -1;
-                sj[q] = 0.f;
-                cx[q][0] = cx[q][1] = cx[q][2] = 0.f;
-                if (cj[q] >= 0 && !a.prefilled) {
-                    sj[q] = a.sp[cj[q]];
-                    if (small_d)
-                        for (int k = 0; k < a.d; ++k) cx[q][k] = a.Xp[cj[q] * a.d + k];
-                }
+    // ---- sampled block A = K(R, C) (rows r..4 nf - 1 zero) and its column norms: warp per column
+    for (int j = warp; j < c; j += kSkelWarps) {
+        float4 *col = reinterpret_cast<float4 *>(At + (size_t)j * ldr);
+        float ss = 0.f;
+        if (a.prefilled) {
+            const float4 *src = reinterpret_cast<const float4 *>(Ag + (size_t)j * ldr);
+            for (int f = lane; f < nf; f += 32) {
+                const float4 v = src[f];
+                if (a_sm) col[f] = v;
+                ss += dot4(v, v);
             }
-            for (int i = i_lo; i < i_hi; ++i) {
+        } else {
+            const int64_t cj = C[j];
+            const float sj = a.sp[cj];
+            float cx[3] = {0.f, 0.f, 0.f};
+            if (small_d)
+                for (int k = 0; k < a.d; ++k) cx[k] = a.Xp[cj * a.d + k];
+            for (int f = lane; f < nf; f += 32) {
                 float v[4];
-                for (int q = 0; q < 4; ++q) {
-                    if (cj[q] < 0) { v[q] = 0.f; continue; }
-                    if (a.prefilled) {
-                        v[q] = A[(size_t)i * lda + j0 + q];
-                    } else if (small_d) {
-                        const float t0 = cx[q][0] - xr[i * 4], t1 = cx[q][1] - xr[i * 4 + 1], t2 = cx[q][2] - xr[i * 4 + 2];
-                        v[q] = xr[i * 4 + 3] * sj[q] * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2)));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = 4 * f + u;
+                    if (i >= r) { v[u] = 0.f; continue; }
+                    if (small_d) {
+                        const float t0 = cx[0] - xr[i * 4], t1 = cx[1] - xr[i * 4 + 1], t2 = cx[2] - xr[i * 4 + 2];
+                        v[u] = xr[i * 4 + 3] * sj * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2)));
                     } else {
-                        v[q] = kentry(a.Xp, a.sp, a.d, Rw[i], cj[q]);
+                        v[u] = kentry(a.Xp, a.sp, a.d, Rw[i], cj);
                     }
                 }
-                *reinterpret_cast<float4 *>(A + (size_t)i * lda + j0) = make_float4(v[0], v[1], v[2], v[3]);
-                ss.x = fmaf(v[0], v[0], ss.x);
-                ss.y = fmaf(v[1], v[1], ss.y);
-                ss.z = fmaf(v[2], v[2], ss.z);
-                ss.w = fmaf(v[3], v[3], ss.w);
+                const float4 w = make_float4(v[0], v[1], v[2], v[3]);
+                col[f] = w;
+                ss += dot4(w, w);
             }
         }
-        reinterpret_cast<float4 *>(red)[threadIdx.x] = ss;
-        __syncthreads();
-        for (int j = threadIdx.x; j < c; j += blockDim.x) {
-            const int gg = j >> 2, qq = j & 3;
-            float t = 0.f;
-            for (int s2 = 0; s2 < sp4.nsl; ++s2) t += red[(s2 * sp4.ncg + gg) * 4 + qq];
-            norms[j] = sqrtf(t);
-        }
-        __syncthreads();
+        ss = warp_allsum(ss);
+        if (lane == 0) norms[j] = sqrtf(ss);
     }
+    __syncthreads();
 
     int kmax = a.max_rank;
     if (kmax > c) kmax = c;
     if (kmax > r) kmax = r;
+    const int nw = (nf + 31) >> 5;  // warps that own the pivot column's float4 rows
+    const int nb = (((c + kSkelWarps - 1) / kSkelWarps) + CB - 1) / CB;  // column batches per warp
     int rank = 0;
+    float nrm0 = 0.f;
     for (int k = 0; k < kmax; ++k) {
         // ---- pivot: largest residual norm among unselected columns, lowest index on ties
+        // (every warp reduces the same shared norms, so all agree without a barrier)
         float bv = -1.f;
         int bi = 0x7fffffff;
-        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        for (int j = lane; j < c; j += 32) {
             if (selpos[j] < 0) {
                 const float v = norms[j];
                 if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
@@ -345,122 +401,72 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
             const int oi = __shfl_xor_sync(DM_FULL, bi, o);
             if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
-        if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+        if (k == 0) nrm0 = bv;
+        if (!(bv > a.tol * nrm0) || bv <= 0.f) break;
+        const int p = bi;
+        // ---- the pivot column, re-orthogonalised once against q_0..q_{k-1}: coefficients
+        // q_t^T a_p, t = warp, warp + warps, ...
+        float4 ap[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int f = lane + 32 * m;
+            ap[m] = f < nf ? reinterpret_cast<const float4 *>(At + (size_t)p * ldr)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int t = warp; t < k; t += kSkelWarps) {
+            const float4 *qt = qrow(t);
+            float d = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const int f = lane + 32 * m;
+                if (f < nf) d += dot4(qt[f], ap[m]);
+            }
+            d = warp_allsum(d);
+            if (lane == 0) coef[t] = d;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            float v = red_v[0];
-            int i = red_i[0];
-            for (int w = 1; w < kSkelWarps; ++w)
-                if (red_v[w] > v || (red_v[w] == v && red_i[w] < i)) { v = red_v[w]; i = red_i[w]; }
-            s_p = i;
-            s_np = v;
-            if (k == 0) s_nrm0 = v;
+            selpos[p] = k;
+            piv[k] = p;
         }
-        __syncthreads();
-        const int p = s_p;
-        if (!(s_np > a.tol * s_nrm0) || s_np <= 0.f) break;
-        // ---- gather the pivot column, re-orthogonalise it once against q_0..q_{k-1}
-        for (int i = threadIdx.x; i < r; i += blockDim.x) qv[i] = A[(size_t)i * lda + p];
-        __syncthreads();
-        if (k > 0) {
-            for (int t = warp; t < k; t += kSkelWarps) {
-                const float *qt = t < qcap ? Qs + (size_t)t * r : Q + (size_t)t * a.rmax;
-                float dsum = 0.f;
-                for (int i = lane; i < r; i += 32) dsum = fmaf(qt[i], qv[i], dsum);
-                dsum = dm_warp_sum(dsum);
-                if (lane == 0) coef[t] = dsum;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < r; i += blockDim.x) {
-                float v = qv[i];
-                const int kq = k < qcap ? k : qcap;
-                for (int t = 0; t < kq; ++t) v = fmaf(-coef[t], Qs[(size_t)t * r + i], v);
-                for (int t = kq; t < k; ++t) v = fmaf(-coef[t], Q[(size_t)t * a.rmax + i], v);
-                qv[i] = v;
-            }
-            for (int t = threadIdx.x; t < k; t += blockDim.x) R[(size_t)t * a.cmax + p] += coef[t];
-            __syncthreads();
-        }
-        // ---- normalise into q_k
-        if (warp == 0) {
+        // fire-and-forget reductions: nothing waits on a global read before the barrier
+        for (int t = threadIdx.x; t < k; t += blockDim.x) atomicAdd(R + (size_t)t * a.cmax + p, coef[t]);
+        // ---- v = a_p - sum_t coef_t q_t on the warps that own its rows, |v|^2 partials
+        if (warp < nw) {
+            const int f = warp * 32 + lane;
+            float4 v = ap[0];
+#pragma unroll
+            for (int m = 1; m < M; ++m)
+                if (warp == m) v = ap[m];
             float ss = 0.f;
-            for (int i = lane; i < r; i += 32) ss = fmaf(qv[i], qv[i], ss);
-            ss = dm_warp_sum(ss);
-            if (lane == 0) {
-                s_qn = sqrtf(ss);
-                R[(size_t)k * a.cmax + p] = s_qn;
-                selpos[p] = k;
-                piv[k] = p;
+            if (f < nf) {
+                for (int t = 0; t < k; ++t) {
+                    const float4 qt = qrow(t)[f];
+                    const float ct = coef[t];
+                    v.x = fmaf(-ct, qt.x, v.x);
+                    v.y = fmaf(-ct, qt.y, v.y);
+                    v.z = fmaf(-ct, qt.z, v.z);
+                    v.w = fmaf(-ct, qt.w, v.w);
+                }
+                qv4[f] = v;
+                ss = dot4(v, v);
             }
+            ss = warp_allsum(ss);
+            if (lane == 0) wred[warp] = ss;
         }
         __syncthreads();
-        const float inv = 1.f / s_qn;
-        for (int i = threadIdx.x; i < r; i += blockDim.x) {
-            const float v = qv[i] * inv;
-            qv[i] = v;
-            if (k < qcap) Qs[(size_t)k * r + i] = v;
-            else Q[(size_t)k * a.rmax + i] = v;
+        // ---- q_k = v / |v| (each thread forms the norm from the warp partials in one order)
+        float ssv = 0.f;
+        for (int w = 0; w < nw; ++w) ssv += wred[w];
+        const float qn = sqrtf(ssv);
+        const float inv = 1.f / qn;
+        if (threadIdx.x == 0) R[(size_t)k * a.cmax + p] = qn;
+        if (warp < nw) {
+            const int f = warp * 32 + lane;
+            if (f < nf) qrow(k)[f] = scale4(qv4[f], inv);
         }
-        __syncthreads();
-        // ---- R(k, :) = q^T A: float4 partial dots per row slice, reduced through shared memory
-        {
-            float4 dp = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (worker) {
-                const float *base = A + j0;
-#pragma unroll 4
-                for (int i = i_lo; i < i_hi; ++i) {
-                    const float4 v = *reinterpret_cast<const float4 *>(base + (size_t)i * lda);
-                    const float qi = qv[i];
-                    dp.x = fmaf(qi, v.x, dp.x);
-                    dp.y = fmaf(qi, v.y, dp.y);
-                    dp.z = fmaf(qi, v.z, dp.z);
-                    dp.w = fmaf(qi, v.w, dp.w);
-                }
-            }
-            reinterpret_cast<float4 *>(red)[threadIdx.x] = dp;
-            __syncthreads();
-            for (int j = threadIdx.x; j < ((c + 3) & ~3); j += blockDim.x) {
-                float t = 0.f;
-                if (j < c && selpos[j] < 0) {
-                    const int gg = j >> 2, qq = j & 3;
-                    for (int s2 = 0; s2 < sp4.nsl; ++s2) t += red[(s2 * sp4.ncg + gg) * 4 + qq];
-                    R[(size_t)k * a.cmax + j] = t;
-                }
-                dots[j] = t;  // zero for selected and padding columns: their residuals stay as they are
-            }
-            __syncthreads();
-        }
-        // ---- a_j -= R(k, j) q for the remaining columns, partial norms of the new residuals
-        {
-            float4 ss = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (worker) {
-                const float4 dk = *reinterpret_cast<const float4 *>(dots + j0);
-                float *base = A + j0;
-#pragma unroll 4
-                for (int i = i_lo; i < i_hi; ++i) {
-                    float4 v = *reinterpret_cast<float4 *>(base + (size_t)i * lda);
-                    const float qi = qv[i];
-                    v.x = fmaf(-dk.x, qi, v.x);
-                    v.y = fmaf(-dk.y, qi, v.y);
-                    v.z = fmaf(-dk.z, qi, v.z);
-                    v.w = fmaf(-dk.w, qi, v.w);
-                    *reinterpret_cast<float4 *>(base + (size_t)i * lda) = v;
-                    ss.x = fmaf(v.x, v.x, ss.x);
-                    ss.y = fmaf(v.y, v.y, ss.y);
-                    ss.z = fmaf(v.z, v.z, ss.z);
-                    ss.w = fmaf(v.w, v.w, ss.w);
-                }
-            }
-            reinterpret_cast<float4 *>(red)[threadIdx.x] = ss;
-            __syncthreads();
-            for (int j = threadIdx.x; j < c; j += blockDim.x) {
-                if (selpos[j] >= 0) continue;
-                const int gg = j >> 2, qq = j & 3;
-                float t = 0.f;
-                for (int s2 = 0; s2 < sp4.nsl; ++s2) t += red[(s2 * sp4.ncg + gg) * 4 + qq];
-                norms[j] = sqrtf(t);
-            }
-        }
+        // ---- every other remaining column: R(k, j) = q_k^T a_j, a_j -= R(k, j) q_k, |a_j|
+        for (int b = 0; b < nb; ++b)
+            column_batch<M, CB>(At, ldr, nf, c, b, qv4, inv, selpos, norms, R + (size_t)k * a.cmax);
         rank = k + 1;
         __syncthreads();
     }
@@ -468,6 +474,7 @@ __global__ void __launch_bounds__(kSkelThreads) skel_level_kernel(SkelArgs a) {
 
     // ---- P = [I, R11^-1 R12] in candidate order; rows t < rank of the node's slot
     float *Pn = a.P + (size_t)node * a.max_rank * a.ldp;
+    const int ldas = (c + 3) & ~3;
     if ((size_t)rank * ldas <= extra) {
         // in shared memory (A and Q are dead): Rs = R(0:rank, :); each unselected column is
         // solved in place (the pivot columns it reads stay R11), in the same operation order as
@@ -578,8 +585,9 @@ size_t dm_fill_smem_bytes() {
 }
 
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
-    return sizeof(float) * 4 * (size_t)kSkelThreads + sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank) +
-           sizeof(float) * (size_t)(cmax + rmax + max_rank + ((cmax + 3) & ~3) + 4 * rmax);
+    const size_t ldr = (size_t)((rmax + 3) & ~3);
+    return sizeof(float) * ldr + sizeof(float) * (size_t)(cmax + 4 * rmax + max_rank) +
+           sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank);
 }
 
 int dm_skel_max_candidates() { return kSkelMaxCand; }
@@ -606,10 +614,15 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     a.A = w->A;
     a.R = w->R;
     a.Q = w->Q;
-    a.lda = w->lda;
-    if (cmax > kSkelMaxCand || (w->lda & 3) != 0) return cudaErrorInvalidValue;
+    a.ldr = w->ldr;
+    if (cmax > kSkelMaxCand || (w->ldr & 3) != 0 || w->ldr < w->rmax || w->rmax > 4 * 32 * kSkelMaxF4)
+        return cudaErrorInvalidValue;
     const size_t smem = dm_skel_smem_bytes(cmax, w->rmax, max_rank);
-    cudaError_t e = dm_allow_smem((const void *)skel_level_kernel, smem);
+    // float4 rows per lane: three (r <= 384, the default ranks) with three-column batches,
+    // else five (r <= 640) with two
+    const bool wide = w->rmax > 32 * 4 * 3;
+    const void *kern = wide ? (const void *)skel_level_kernel<5, 2> : (const void *)skel_level_kernel<3, 3>;
+    cudaError_t e = dm_allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(ranks, 0, sizeof(int32_t), st);  // the root has no skeleton
     if (e != cudaSuccess) return e;
@@ -619,11 +632,11 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, (const void *)skel_level_kernel)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
     // dynamic bytes allowed = per-block opt-in limit minus the kernel's static shared memory
     const size_t dyn_max = ((size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0) & ~(size_t)15;
     const size_t smem_int = dyn_max > (size_t)a.smem_base ? dyn_max : smem;
-    if ((e = dm_allow_smem((const void *)skel_level_kernel, smem_int)) != cudaSuccess) return e;
+    if ((e = dm_allow_smem(kern, smem_int)) != cudaSuccess) return e;
     // the leaf level (many CTAs) takes what still lets two CTAs share an SM (its register
     // footprint allows two), which holds the Q rows of the ranks seen in practice
     int sm_bytes = 0, reserved = 0;
@@ -648,7 +661,8 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
         // shared memory, which holds the sampled block and Q
         const size_t lsm = lvl < L ? smem_int : smem_leaf;
         a.smem_extra = lsm > (size_t)a.smem_base ? (int)(lsm - (size_t)a.smem_base) : 0;
-        skel_level_kernel<<<1 << lvl, kSkelThreads, lsm, st>>>(a);
+        if (wide) skel_level_kernel<5, 2><<<1 << lvl, kSkelThreads, lsm, st>>>(a);
+        else skel_level_kernel<3, 3><<<1 << lvl, kSkelThreads, lsm, st>>>(a);
         dm_count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
