@@ -207,8 +207,8 @@ __device__ __forceinline__ float warp_allsum(float v) {
 
 // One pass over a batch of CB of the warp's columns (column j = warp + kSkelWarps (b CB + u)):
 // d_j = q^T a_j, a_j -= d_j q, norms[j] = |a_j|, R(k, j) = d_j. Lane holds float4 rows
-// f = lane + 32 m, m < M, of each column (f < nf). q = qv * inv, recomputed from shared
-// memory at each use (the same product every time).
+// f = lane + 32 m, m < M, of each column (f < nf), as two packed FP32x2 halves. q = qv * inv,
+// recomputed from shared memory at each use (the same product every time).
 template <int M, int CB>
 __device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int c, int b, const float4 *qv, float inv,
                                              const int *selpos, float *norms, float *Rk) {
@@ -222,52 +222,66 @@ __device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int c, 
     }
     float4 v[CB][M];
 #pragma unroll
-    for (int u = 0; u < CB; ++u)
+    for (int u = 0; u < CB; ++u) {
+        const float4 *col = reinterpret_cast<const float4 *>(At + (size_t)jb[u] * ldr);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int f = lane + 32 * m;
-            v[u][m] = (ok[u] && f < nf) ? reinterpret_cast<const float4 *>(At + (size_t)jb[u] * ldr)[f]
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[u][m] = (ok[u] && f < nf) ? col[f] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-    float dj[CB];
+    }
+    float2 dp[CB];
 #pragma unroll
-    for (int u = 0; u < CB; ++u) dj[u] = 0.f;
+    for (int u = 0; u < CB; ++u) dp[u] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const int f = lane + 32 * m;
         const float4 q = f < nf ? scale4(qv[f], inv) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 qa = make_float2(q.x, q.y), qb = make_float2(q.z, q.w);
 #pragma unroll
-        for (int u = 0; u < CB; ++u) dj[u] += dot4(v[u][m], q);
+        for (int u = 0; u < CB; ++u) {
+            dp[u] = __ffma2_rn(make_float2(v[u][m].x, v[u][m].y), qa, dp[u]);
+            dp[u] = __ffma2_rn(make_float2(v[u][m].z, v[u][m].w), qb, dp[u]);
+        }
     }
+    float dj[CB];
 #pragma unroll
-    for (int u = 0; u < CB; ++u) dj[u] = warp_allsum(dj[u]);
-    float ss[CB];
+    for (int u = 0; u < CB; ++u) dj[u] = warp_allsum(dp[u].x + dp[u].y);
+    float2 sp2[CB];
 #pragma unroll
-    for (int u = 0; u < CB; ++u) ss[u] = 0.f;
+    for (int u = 0; u < CB; ++u) sp2[u] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const int f = lane + 32 * m;
         if (f >= nf) continue;
         const float4 q = scale4(qv[f], inv);
+        const float2 qa = make_float2(q.x, q.y), qb = make_float2(q.z, q.w);
 #pragma unroll
         for (int u = 0; u < CB; ++u) {
             if (!ok[u]) continue;
-            float4 w = v[u][m];
-            w.x = fmaf(-dj[u], q.x, w.x);
-            w.y = fmaf(-dj[u], q.y, w.y);
-            w.z = fmaf(-dj[u], q.z, w.z);
-            w.w = fmaf(-dj[u], q.w, w.w);
-            reinterpret_cast<float4 *>(At + (size_t)jb[u] * ldr)[f] = w;
-            ss[u] += dot4(w, w);
+            const float2 nd = make_float2(-dj[u], -dj[u]);
+            const float2 wa = __ffma2_rn(nd, qa, make_float2(v[u][m].x, v[u][m].y));
+            const float2 wb = __ffma2_rn(nd, qb, make_float2(v[u][m].z, v[u][m].w));
+            reinterpret_cast<float4 *>(At + (size_t)jb[u] * ldr)[f] = make_float4(wa.x, wa.y, wb.x, wb.y);
+            sp2[u] = __ffma2_rn(wa, wa, sp2[u]);
+            sp2[u] = __ffma2_rn(wb, wb, sp2[u]);
         }
     }
+    // lane u finishes column u: one square root for the batch
+    float my_ss = 0.f, my_d = 0.f;
+    int my_j = -1;
 #pragma unroll
     for (int u = 0; u < CB; ++u) {
-        ss[u] = warp_allsum(ss[u]);
-        if (lane == 0 && ok[u]) {
-            norms[jb[u]] = sqrtf(ss[u]);
-            Rk[jb[u]] = dj[u];
+        const float t = warp_allsum(sp2[u].x + sp2[u].y);
+        if (lane == u && ok[u]) {
+            my_ss = t;
+            my_d = dj[u];
+            my_j = jb[u];
         }
+    }
+    if (my_j >= 0) {
+        norms[my_j] = sqrtf(my_ss);
+        Rk[my_j] = my_d;
     }
 }
 
@@ -275,8 +289,9 @@ template <int M, int CB>
 __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a) {
     // float4-accessed arrays first so that every one starts on a 16-byte boundary
     extern __shared__ float4 smem4[];
-    float4 *qv4 = smem4;                                 // ldr / 4: pivot residual (then v)
-    float *norms = reinterpret_cast<float *>(qv4 + (a.ldr >> 2));  // cmax
+    float4 *qv4 = smem4;                                 // ldr / 4 (ldr a multiple of 4): pivot residual (then v)
+    float4 *ccrd = qv4 + (a.ldr >> 2);                   // cmax: candidate coordinates (d <= 3) and s
+    float *norms = reinterpret_cast<float *>(ccrd + a.cmax);  // cmax
     float *xr = norms + a.cmax;                          // rmax x 4: row coordinates (d <= 3) and s
     float *coef = xr + 4 * a.rmax;                       // max_rank: re-orthogonalisation coefficients
     int *C = reinterpret_cast<int *>(coef + a.max_rank); // cmax candidate positions
@@ -319,7 +334,17 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
             xr[t * 4 + 3] = a.sp[pos];
         }
     }
-    for (int j = threadIdx.x; j < c; j += blockDim.x) selpos[j] = -1;
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        selpos[j] = -1;
+        if (small_d && !a.prefilled) {
+            const int64_t cj = C[j];
+            float4 v = make_float4(0.f, 0.f, 0.f, a.sp[cj]);
+            if (a.d > 0) v.x = a.Xp[cj * a.d];
+            if (a.d > 1) v.y = a.Xp[cj * a.d + 1];
+            if (a.d > 2) v.z = a.Xp[cj * a.d + 2];
+            ccrd[j] = v;
+        }
+    }
     // the sampled block lives in shared memory when it fits (internal levels: few candidates),
     // else in the CTA's global slot; rows of Q follow it in shared memory while they fit
     const int nf = (r + 3) >> 2;  // float4 rows per column
@@ -350,10 +375,14 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
             }
         } else {
             const int64_t cj = C[j];
-            const float sj = a.sp[cj];
-            float cx[3] = {0.f, 0.f, 0.f};
-            if (small_d)
-                for (int k = 0; k < a.d; ++k) cx[k] = a.Xp[cj * a.d + k];
+            float sj = 0.f, cx[3] = {0.f, 0.f, 0.f};
+            if (small_d) {
+                const float4 cc = ccrd[j];
+                cx[0] = cc.x;
+                cx[1] = cc.y;
+                cx[2] = cc.z;
+                sj = cc.w;
+            }
             for (int f = lane; f < nf; f += 32) {
                 float v[4];
 #pragma unroll
@@ -413,7 +442,8 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
             ap[m] = f < nf ? reinterpret_cast<const float4 *>(At + (size_t)p * ldr)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         for (int t = warp; t < k; t += kSkelWarps) {
-            const float4 *qt = qrow(t);
+            const float4 *qt = t < qcap ? reinterpret_cast<const float4 *>(Qs + (size_t)t * ldr)
+                                        : reinterpret_cast<const float4 *>(Q + (size_t)t * ldr);
             float d = 0.f;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
@@ -439,14 +469,15 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
                 if (warp == m) v = ap[m];
             float ss = 0.f;
             if (f < nf) {
-                for (int t = 0; t < k; ++t) {
-                    const float4 qt = qrow(t)[f];
-                    const float ct = coef[t];
+                auto sub = [&](const float4 qt, float ct) {
                     v.x = fmaf(-ct, qt.x, v.x);
                     v.y = fmaf(-ct, qt.y, v.y);
                     v.z = fmaf(-ct, qt.z, v.z);
                     v.w = fmaf(-ct, qt.w, v.w);
-                }
+                };
+                const int kq = k < qcap ? k : qcap;
+                for (int t = 0; t < kq; ++t) sub(reinterpret_cast<const float4 *>(Qs + (size_t)t * ldr)[f], coef[t]);
+                for (int t = kq; t < k; ++t) sub(reinterpret_cast<const float4 *>(Q + (size_t)t * ldr)[f], coef[t]);
                 qv4[f] = v;
                 ss = dot4(v, v);
             }
@@ -465,8 +496,13 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
             if (f < nf) qrow(k)[f] = scale4(qv4[f], inv);
         }
         // ---- every other remaining column: R(k, j) = q_k^T a_j, a_j -= R(k, j) q_k, |a_j|
-        for (int b = 0; b < nb; ++b)
-            column_batch<M, CB>(At, ldr, nf, c, b, qv4, inv, selpos, norms, R + (size_t)k * a.cmax);
+        if (a_sm) {
+            for (int b = 0; b < nb; ++b)
+                column_batch<M, CB>(xs, ldr, nf, c, b, qv4, inv, selpos, norms, R + (size_t)k * a.cmax);
+        } else {
+            for (int b = 0; b < nb; ++b)
+                column_batch<M, CB>(Ag, ldr, nf, c, b, qv4, inv, selpos, norms, R + (size_t)k * a.cmax);
+        }
         rank = k + 1;
         __syncthreads();
     }
@@ -586,7 +622,7 @@ size_t dm_fill_smem_bytes() {
 
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
     const size_t ldr = (size_t)((rmax + 3) & ~3);
-    return sizeof(float) * ldr + sizeof(float) * (size_t)(cmax + 4 * rmax + max_rank) +
+    return sizeof(float) * ldr + sizeof(float) * (size_t)(cmax + 4 * rmax + 4 * cmax + max_rank) +
            sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank);
 }
 
