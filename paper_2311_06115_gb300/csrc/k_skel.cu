@@ -291,9 +291,9 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     extern __shared__ float4 smem4[];
     float4 *qv4 = smem4;                                 // ldr / 4 (ldr a multiple of 4): pivot residual (then v)
     float4 *ccrd = qv4 + (a.ldr >> 2);                   // cmax: candidate coordinates (d <= 3) and s
-    float *norms = reinterpret_cast<float *>(ccrd + a.cmax);  // cmax
-    float *xr = norms + a.cmax;                          // rmax x 4: row coordinates (d <= 3) and s
-    float *coef = xr + 4 * a.rmax;                       // max_rank: re-orthogonalisation coefficients
+    float *xr = reinterpret_cast<float *>(ccrd + a.cmax); // 4 x ldr: row x, y, z, s (d <= 3), one array each
+    float *norms = xr + 4 * a.ldr;                       // cmax
+    float *coef = norms + a.cmax;                        // max_rank: re-orthogonalisation coefficients
     int *C = reinterpret_cast<int *>(coef + a.max_rank); // cmax candidate positions
     int *Rw = C + a.cmax;                                // rmax row positions
     int *selpos = Rw + a.rmax;                           // cmax: -1 or pivot step
@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
         const int pos = (int)(u < st ? u : u + sz);
         Rw[t] = pos;
         if (small_d) {
-            for (int k = 0; k < 3; ++k) xr[t * 4 + k] = k < a.d ? a.Xp[(int64_t)pos * a.d + k] : 0.f;
-            xr[t * 4 + 3] = a.sp[pos];
+            for (int k = 0; k < 3; ++k) xr[k * a.ldr + t] = k < a.d ? a.Xp[(int64_t)pos * a.d + k] : 0.f;
+            xr[3 * a.ldr + t] = a.sp[pos];
         }
     }
     for (int j = threadIdx.x; j < c; j += blockDim.x) {
@@ -385,16 +385,22 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
             }
             for (int f = lane; f < nf; f += 32) {
                 float v[4];
+                if (small_d) {
+                    // rows 4f..4f+3 of each coordinate array: 16-byte loads, consecutive across lanes
+                    const float4 rx = reinterpret_cast<const float4 *>(xr)[f];
+                    const float4 ry = reinterpret_cast<const float4 *>(xr + ldr)[f];
+                    const float4 rz = reinterpret_cast<const float4 *>(xr + 2 * ldr)[f];
+                    const float4 rs = reinterpret_cast<const float4 *>(xr + 3 * ldr)[f];
+                    const float px[4] = {rx.x, rx.y, rx.z, rx.w}, py[4] = {ry.x, ry.y, ry.z, ry.w},
+                                pz[4] = {rz.x, rz.y, rz.z, rz.w}, ps[4] = {rs.x, rs.y, rs.z, rs.w};
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = 4 * f + u;
-                    if (i >= r) { v[u] = 0.f; continue; }
-                    if (small_d) {
-                        const float t0 = cx[0] - xr[i * 4], t1 = cx[1] - xr[i * 4 + 1], t2 = cx[2] - xr[i * 4 + 2];
-                        v[u] = xr[i * 4 + 3] * sj * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2)));
-                    } else {
-                        v[u] = kentry(a.Xp, a.sp, a.d, Rw[i], cj);
+                    for (int u = 0; u < 4; ++u) {
+                        const float t0 = cx[0] - px[u], t1 = cx[1] - py[u], t2 = cx[2] - pz[u];
+                        v[u] = (4 * f + u < r) ? ps[u] * sj * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2))) : 0.f;
                     }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = (4 * f + u < r) ? kentry(a.Xp, a.sp, a.d, Rw[4 * f + u], cj) : 0.f;
                 }
                 const float4 w = make_float4(v[0], v[1], v[2], v[3]);
                 col[f] = w;
@@ -622,7 +628,7 @@ size_t dm_fill_smem_bytes() {
 
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
     const size_t ldr = (size_t)((rmax + 3) & ~3);
-    return sizeof(float) * ldr + sizeof(float) * (size_t)(cmax + 4 * rmax + 4 * cmax + max_rank) +
+    return sizeof(float) * ldr + sizeof(float) * (size_t)(4 * cmax + 4 * ldr + cmax + max_rank) +
            sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank);
 }
 
