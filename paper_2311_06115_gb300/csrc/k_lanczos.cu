@@ -342,50 +342,70 @@ __device__ int sturm_count(const double *__restrict__ al, const double *__restri
     return cnt;
 }
 
-// One warp per wanted eigenvalue (descending index i): multisection to full FP64
-// precision, then the residual bound beta_{m-1} |y_m| from |y_m|^2 = |p_{m-1}(theta) / p_m'(theta)|.
-__global__ void __launch_bounds__(32) ritz_kernel(const double *__restrict__ alpha, const double *__restrict__ beta,
-                                                  int m, double *__restrict__ theta, double *__restrict__ resid,
-                                                  double *__restrict__ work) {
+// One block of kRitzThreads per wanted eigenvalue (descending index i): multisection to full
+// FP64 precision with one shift per thread (four warps: all four FP64 units of the SM, seven
+// bits per round), then the residual bound beta_{m-1} |y_m| from
+// |y_m|^2 = |p_{m-1}(theta) / p_m'(theta)|.
+constexpr int kRitzThreads = 128;
+__global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__restrict__ alpha,
+                                                            const double *__restrict__ beta, int m,
+                                                            double *__restrict__ theta, double *__restrict__ resid,
+                                                            double *__restrict__ work) {
     extern __shared__ double sd[];
     double *al = sd, *b2 = sd + m;
-    const int lane = threadIdx.x;
-    for (int i = lane; i < m; i += 32) {
+    __shared__ unsigned s_above[kRitzThreads / 32];
+    __shared__ double s_lo, s_hi;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < m; i += blockDim.x) {
         al[i] = alpha[i];
         b2[i] = (i < m - 1) ? beta[i] * beta[i] : 0.0;
     }
-    __syncwarp();
-    // Gershgorin interval
-    double lo = 1e300, hi = -1e300;
-    for (int i = lane; i < m; i += 32) {
-        const double r = (i > 0 ? sqrt(b2[i - 1]) : 0.0) + (i < m - 1 ? sqrt(b2[i]) : 0.0);
-        lo = fmin(lo, al[i] - r);
-        hi = fmax(hi, al[i] + r);
-    }
+    __syncthreads();
+    // Gershgorin interval (warp 0)
+    if (warp == 0) {
+        double lo = 1e300, hi = -1e300;
+        for (int i = lane; i < m; i += 32) {
+            const double r = (i > 0 ? sqrt(b2[i - 1]) : 0.0) + (i < m - 1 ? sqrt(b2[i]) : 0.0);
+            lo = fmin(lo, al[i] - r);
+            hi = fmax(hi, al[i] + r);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(DM_FULL, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(DM_FULL, hi, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(DM_FULL, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(DM_FULL, hi, o));
+        }
+        if (lane == 0) {
+            const double span = fmax(hi - lo, 1e-300);
+            s_lo = lo - 1e-3 * span;
+            s_hi = hi + 1e-3 * span;
+        }
     }
-    const double span = fmax(hi - lo, 1e-300);
-    lo -= 1e-3 * span;
-    hi += 1e-3 * span;
+    __syncthreads();
+    double lo = s_lo, hi = s_hi;
     const int target = m - 1 - (int)blockIdx.x;  // ascending index of the wanted eigenvalue
+    constexpr double kDen = (double)(kRitzThreads + 1);
     for (int round = 0; round < 16; ++round) {
-        if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
-        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;  // uniform: every thread holds the same lo, hi
+        const double x = lo + (hi - lo) * (double)(tid + 1) / kDen;
         const int c = sturm_count(al, b2, m, x);
-        const unsigned above = __ballot_sync(DM_FULL, c > target);  // lanes whose shift is above the eigenvalue
-        const double xlo = __shfl_sync(DM_FULL, x, above ? max(__ffs(above) - 2, 0) : 31);
-        const double xhi = __shfl_sync(DM_FULL, x, above ? __ffs(above) - 1 : 31);
-        if (above == 0u) lo = xhi;                      // all shifts below: eigenvalue in (x_31, hi]
+        const unsigned above = __ballot_sync(DM_FULL, c > target);  // shifts above the eigenvalue
+        if (lane == 0) s_above[warp] = above;
+        __syncthreads();
+        int g = -1;  // first shift above
+        for (int w = 0; w < kRitzThreads / 32 && g < 0; ++w)
+            if (s_above[w]) g = 32 * w + __ffs(s_above[w]) - 1;
+        __syncthreads();
+        // every thread re-forms the bracketing shifts with the same arithmetic
+        auto shift = [&](int t) { return lo + (hi - lo) * (double)(t + 1) / kDen; };
+        if (g < 0) lo = shift(kRitzThreads - 1);  // all shifts below: eigenvalue in (x_last, hi]
         else {
-            if (__ffs(above) - 1 > 0) lo = xlo;
-            hi = xhi;
+            const double xh = shift(g);
+            if (g > 0) lo = shift(g - 1);
+            hi = xh;
         }
     }
     const double th = 0.5 * (lo + hi);
-    if (lane == 0) {
+    if (tid == 0) {
         // p and p' of det(T_i - x I) with shared rescaling
         double pm = 1.0, p = al[0] - th, dpm = 0.0, dp = -1.0;
         for (int i = 1; i < m; ++i) {
@@ -458,6 +478,9 @@ __global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const dou
         }
     }
     if (fabs(dd[m - 1]) < pivmin) dd[m - 1] = (dd[m - 1] < 0 ? -pivmin : pivmin);
+    // the pivots are used only as divisors from here on: invert them once (FP64 division is
+    // a long sequence on this part) instead of in each of the three solves
+    for (int i = 0; i < m; ++i) dd[i] = 1.0 / dd[i];
     for (int i = 0; i < m; ++i) y[i] = 2.0 * dm_unit(dm_rng(key, (uint64_t)(iv * 1024 + i))) - 1.0;
     for (int it = 0; it < 3; ++it) {
         // solve L: apply row interchanges and multipliers
@@ -470,9 +493,9 @@ __global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const dou
             }
         }
         // solve U (upper, bandwidth 2)
-        y[m - 1] /= dd[m - 1];
-        if (m > 1) y[m - 2] = (y[m - 2] - du[m - 2] * y[m - 1]) / dd[m - 2];
-        for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
+        y[m - 1] *= dd[m - 1];
+        if (m > 1) y[m - 2] = (y[m - 2] - du[m - 2] * y[m - 1]) * dd[m - 2];
+        for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) * dd[i];
         double nn = 0.0;
         for (int i = 0; i < m; ++i) nn += y[i] * y[i];
         const double inv = 1.0 / sqrt(nn);
@@ -691,7 +714,8 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) 
 
 cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st) {
     (void)conv_tol;
-    ritz_kernel<<<k, 32, sizeof(double) * 2 * (size_t)m, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.resid, nullptr);
+    ritz_kernel<<<k, kRitzThreads, sizeof(double) * 2 * (size_t)m, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.resid,
+                                                                         nullptr);
     dm_count_launches(1);
     return cudaGetLastError();
 }
