@@ -75,23 +75,34 @@ __global__ void __launch_bounds__(512) select_hist_kernel(const double *__restri
         if (h[b]) atomicAdd(&st->hist[b], h[b]);
 }
 
-// one block: pick the bin holding rank k, extend the prefix, clear the histogram
+// one block: pick the bin holding rank k, extend the prefix, clear the histogram. Thread t
+// sums its `per` bins; a block scan of those sums finds the first thread t <= T - 2 whose
+// inclusive count exceeds k (else the last one), and that thread walks its own bins.
 __global__ void __launch_bounds__(1024) select_step_kernel(int shift, int bits, SelectState *__restrict__ st) {
-    __shared__ unsigned part[1024];
-    __shared__ int s_bin;
+    __shared__ long long wsum[32];
+    __shared__ int s_t, s_bin;
     __shared__ long long s_before;
     const int per = kSelBins / blockDim.x;  // bins per thread (2 with 1024 threads)
-    unsigned loc = 0;
-    for (int q = 0; q < per; ++q) loc += st->hist[threadIdx.x * per + q];
-    part[threadIdx.x] = loc;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nt = blockDim.x;
+    long long loc = 0;
+    for (int q = 0; q < per; ++q) loc += st->hist[t * per + q];
+    long long x = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(DM_FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    if (t == 0) s_t = nt - 1;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long acc = 0, k = st->k;
-        int t = 0;
-        for (; t < (int)blockDim.x - 1; ++t) {
-            if (acc + part[t] > k) break;
-            acc += part[t];
-        }
+    long long off = 0;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    const long long incl = off + x, excl = incl - loc;
+    const long long k = st->k;
+    if (t < nt - 1 && incl > k) atomicMin(&s_t, t);
+    __syncthreads();
+    if (t == s_t) {
+        long long acc = excl;
         int b = t * per;
         for (; b < kSelBins - 1; ++b) {
             if (acc + st->hist[b] > k) break;
@@ -101,8 +112,8 @@ __global__ void __launch_bounds__(1024) select_step_kernel(int shift, int bits, 
         s_before = acc;
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) st->hist[b] = 0;
-    if (threadIdx.x == 0) {
+    for (int b = t; b < kSelBins; b += nt) st->hist[b] = 0;
+    if (t == 0) {
         const unsigned long long digit_mask = ((1ull << bits) - 1ull) << shift;
         st->prefix |= ((unsigned long long)s_bin << shift) & digit_mask;
         st->mask |= digit_mask;

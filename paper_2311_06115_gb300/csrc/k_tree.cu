@@ -231,27 +231,39 @@ __global__ void __launch_bounds__(512) split_hist_kernel(const TreeItem *__restr
         if (sh[b]) atomicAdd(hist + n * 256 + b, sh[b]);
 }
 
-__global__ void split_step_kernel(SplitSel *S, unsigned *hist, int shift) {
-    const int n = blockIdx.x;
+// One block of 256 threads per node (thread b owns digit bin b): the digit is the first bin
+// b <= 254 whose inclusive count exceeds the rank k still sought, else 255; the keys of the
+// bins before it move from k to `below`. A block scan of the 256 counts replaces a serial
+// walk over the bins (one dependent global load per bin).
+__global__ void __launch_bounds__(256) split_step_kernel(SplitSel *S, unsigned *hist, int shift) {
+    const int n = blockIdx.x, b = threadIdx.x, lane = b & 31, warp = b >> 5;
+    __shared__ long long wsum[8];
     __shared__ int s_b;
     __shared__ long long s_acc;
-    if (threadIdx.x == 0) {
-        long long acc = 0, k = S[n].k;
-        int b = 0;
-        for (; b < 255; ++b) {
-            if (acc + (long long)hist[n * 256 + b] > k) break;
-            acc += hist[n * 256 + b];
-        }
-        s_b = b;
-        s_acc = acc;
+    const long long h = (long long)hist[n * 256 + b];
+    long long x = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(DM_FULL, x, o);
+        if (lane >= o) x += y;
     }
+    if (lane == 31) wsum[warp] = x;
+    if (b == 0) s_b = 255;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    long long off = 0;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    const long long incl = off + x, excl = incl - h;
+    const long long k = S[n].k;
+    if (b < 255 && incl > k) atomicMin(&s_b, b);
+    __syncthreads();
+    if (b == s_b) s_acc = excl;
+    __syncthreads();
+    if (b == 0) {
         S[n].k -= s_acc;
         S[n].below += s_acc;
         S[n].prefix |= (unsigned long long)s_b << shift;
     }
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[n * 256 + b] = 0u;
+    hist[n * 256 + b] = 0u;
 }
 
 // per item: keys below the threshold and keys equal to it
