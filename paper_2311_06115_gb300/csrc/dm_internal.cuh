@@ -358,6 +358,8 @@ template <class KeyFn>
 __device__ uint64_t dm_cta_select(KeyFn key, int64_t n, int64_t k, unsigned *hist, int64_t *below) {
     __shared__ uint64_t s_prefix;
     __shared__ int64_t s_k, s_below;
+    __shared__ int64_t s_wsum[8];
+    __shared__ int s_bin;
     uint64_t prefix = 0, mask = 0;
     if (threadIdx.x == 0) { s_below = 0; }
     for (int shift = 56; shift >= 0; shift -= 8) {
@@ -380,17 +382,34 @@ __device__ uint64_t dm_cta_select(KeyFn key, int64_t n, int64_t k, unsigned *his
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t kk = (shift == 56) ? k : s_k;
-            int64_t acc = 0;
-            int b = 0;
-            for (; b < 256; ++b) {
-                if (acc + (int64_t)hist[b] > kk) break;
-                acc += hist[b];
+        // the digit: first bin whose inclusive count exceeds the rank still sought, by a scan
+        // of the 256 counts over the first eight warps (blockDim.x >= 256)
+        const int64_t kk = (shift == 56) ? k : s_k;
+        int64_t h = 0, x = 0;
+        if (threadIdx.x < 256) {
+            h = (int64_t)hist[threadIdx.x];
+            x = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(DM_FULL, x, o);
+                if (lane >= o) x += y;
             }
-            s_k = kk - acc;
-            s_below += acc;
-            s_prefix = prefix | ((uint64_t)b << shift);
+            if (lane == 31) s_wsum[threadIdx.x >> 5] = x;
+        }
+        if (threadIdx.x == 0) s_bin = 256;
+        __syncthreads();
+        int64_t excl = 0;
+        if (threadIdx.x < 256) {
+            int64_t off = 0;
+            for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) off += s_wsum[w];
+            excl = off + x - h;
+            if (off + x > kk) atomicMin(&s_bin, (int)threadIdx.x);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x == s_bin) {
+            s_k = kk - excl;
+            s_below += excl;
+            s_prefix = prefix | ((uint64_t)threadIdx.x << shift);
         }
         __syncthreads();
         prefix = s_prefix;
