@@ -213,6 +213,10 @@ constexpr float kDotFormMaxNorm = 8.f;
 #define DM_SYM_ROW_PAIRS 4
 #endif
 constexpr int kSymRowPairs = DM_SYM_ROW_PAIRS;  // row pairs per thread of the symmetric pass
+#ifndef DM_SYM_MIN_BLOCKS
+#define DM_SYM_MIN_BLOCKS 10
+#endif
+constexpr int kSymMinBlocks = DM_SYM_MIN_BLOCKS;  // CTAs per SM the register budget is sized for
 
 struct Rows4 {
     float2 x0[2], x1[2], x2[2];
@@ -344,7 +348,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
 }
 
 template <int RP>
-__global__ void __launch_bounds__(kD3Rows / (2 * RP)) degree_sym_d3_kernel(const float *__restrict__ Xs,
+__global__ void __launch_bounds__(kD3Rows / (2 * RP), kSymMinBlocks) degree_sym_d3_kernel(const float *__restrict__ Xs,
                                                                            const float *__restrict__ nrm,
                                                                            const float *__restrict__ nmax, int64_t N,
                                                                            const float *__restrict__ w,
@@ -390,9 +394,11 @@ __global__ void __launch_bounds__(kD3Rows / (2 * RP)) degree_sym_d3_kernel(const
     }
     const int64_t c0 = (int64_t)J * kD3Rows;
     const int64_t c1 = (c0 + kD3Rows < N) ? c0 + kD3Rows : N;
-    double acc[2 * RP];
+    // FP64 row sums in shared memory (touched once per column tile), keeping registers for the
+    // packed inner loop so that more CTAs fit on an SM
+    __shared__ double acc_s[2 * RP][T];
 #pragma unroll
-    for (int q = 0; q < 2 * RP; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 2 * RP; ++q) acc_s[q][threadIdx.x] = 0.0;
     for (int64_t t0 = c0; t0 < c1; t0 += kDegTile) {
         const int tn = (int)(c1 - t0 < kDegTile ? c1 - t0 : kDegTile);
         __syncthreads();
@@ -464,8 +470,8 @@ __global__ void __launch_bounds__(kD3Rows / (2 * RP)) degree_sym_d3_kernel(const
         }
 #pragma unroll
         for (int p = 0; p < RP; ++p) {
-            acc[2 * p] += (double)part[p].x;
-            acc[2 * p + 1] += (double)part[p].y;
+            acc_s[2 * p][threadIdx.x] += (double)part[p].x;
+            acc_s[2 * p + 1][threadIdx.x] += (double)part[p].y;
         }
         if (offdiag) {
             __syncthreads();
@@ -476,7 +482,7 @@ __global__ void __launch_bounds__(kD3Rows / (2 * RP)) degree_sym_d3_kernel(const
     for (int q = 0; q < 2 * RP; ++q) {
         const int64_t rq = row0 + (int64_t)q * T;
         if (rq >= N) continue;
-        double v = acc[q];
+        double v = acc_s[q][threadIdx.x];
         if (dot_form) v *= (double)dm_ex2(-nrm[rq]);
         atomicAdd(out + rq, v);
     }
