@@ -17,7 +17,8 @@
 // re-orthogonalisation of the pivot column. A warp owns whole columns: one read-modify-
 // write pass per step gives q_k^T a_j (warp reduction), the update a_j -= (q_k^T a_j) q_k
 // and the new norm |a_j|, for a few columns at a time so that every lane keeps several
-// 16-byte loads in flight; every warp finds the next pivot itself from the shared norms,
+// 16-byte loads in flight; each warp keeps its best remaining column, and every warp finds
+// the next pivot itself from those per-warp candidates,
 // so a step needs three block barriers. P_a = [I, R11^-1 R12] by back substitution.
 #include "dm_internal.cuh"
 
@@ -206,12 +207,13 @@ __device__ __forceinline__ float warp_allsum(float v) {
 }
 
 // One pass over a batch of CB of the warp's columns (column j = warp + kSkelWarps (b CB + u)):
-// d_j = q^T a_j, a_j -= d_j q, norms[j] = |a_j|, R(k, j) = d_j. Lane holds float4 rows
+// d_j = q^T a_j, a_j -= d_j q, R(k, j) = d_j, and the lane's running best (|a_j|, j) for the
+// next pivot (lowest index on ties). Lane holds float4 rows
 // f = lane + 32 m, m < M, of each column (f < nf), as two packed FP32x2 halves. q = qv * inv,
 // recomputed from shared memory at each use (the same product every time).
 template <int M, int CB>
 __device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int c, int b, const float4 *qv, float inv,
-                                             const int *selpos, float *norms, float *Rk) {
+                                             const int *selpos, float &best_v, int &best_j, float *Rk) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int jb[CB];
     bool ok[CB];
@@ -280,8 +282,25 @@ __device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int c, 
         }
     }
     if (my_j >= 0) {
-        norms[my_j] = sqrtf(my_ss);
+        const float nv = sqrtf(my_ss);
+        if (nv > best_v || (nv == best_v && my_j < best_j)) {
+            best_v = nv;
+            best_j = my_j;
+        }
         Rk[my_j] = my_d;
+    }
+}
+
+// largest (value, lowest index on ties) over the warp; every lane gets the result
+__device__ __forceinline__ void warp_argmax(float &v, int &j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(DM_FULL, v, o);
+        const int oj = __shfl_xor_sync(DM_FULL, j, o);
+        if (ov > v || (ov == v && oj < j)) {
+            v = ov;
+            j = oj;
+        }
     }
 }
 
@@ -292,13 +311,14 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     float4 *qv4 = smem4;                                 // ldr / 4 (ldr a multiple of 4): pivot residual (then v)
     float4 *ccrd = qv4 + (a.ldr >> 2);                   // cmax: candidate coordinates (d <= 3) and s
     float *xr = reinterpret_cast<float *>(ccrd + a.cmax); // 4 x ldr: row x, y, z, s (d <= 3), one array each
-    float *norms = xr + 4 * a.ldr;                       // cmax
-    float *coef = norms + a.cmax;                        // max_rank: re-orthogonalisation coefficients
+    float *coef = xr + 4 * a.ldr;                        // max_rank: re-orthogonalisation coefficients
     int *C = reinterpret_cast<int *>(coef + a.max_rank); // cmax candidate positions
     int *Rw = C + a.cmax;                                // rmax row positions
     int *selpos = Rw + a.rmax;                           // cmax: -1 or pivot step
     int *piv = selpos + a.cmax;                          // max_rank
     __shared__ float wred[kSkelWarps];
+    __shared__ float wbest_v[kSkelWarps];  // each warp's best remaining column norm and its index
+    __shared__ int wbest_j[kSkelWarps];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int node = (1 << a.level) - 1 + (int)blockIdx.x;
@@ -362,7 +382,10 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     };
     __syncthreads();
 
-    // ---- sampled block A = K(R, C) (rows r..4 nf - 1 zero) and its column norms: warp per column
+    // ---- sampled block A = K(R, C) (rows r..4 nf - 1 zero) and its column norms: warp per column;
+    // warp w owns columns w, w + warps, ... here and in every column pass
+    float best_v = -1.f;
+    int best_j = 0x7fffffff;
     for (int j = warp; j < c; j += kSkelWarps) {
         float4 *col = reinterpret_cast<float4 *>(At + (size_t)j * ldr);
         float ss = 0.f;
@@ -408,7 +431,15 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
             }
         }
         ss = warp_allsum(ss);
-        if (lane == 0) norms[j] = sqrtf(ss);
+        const float nv = sqrtf(ss);
+        if (nv > best_v || (nv == best_v && j < best_j)) {
+            best_v = nv;
+            best_j = j;
+        }
+    }
+    if (lane == 0) {
+        wbest_v[warp] = best_v;
+        wbest_j[warp] = best_j;
     }
     __syncthreads();
 
@@ -421,21 +452,10 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     float nrm0 = 0.f;
     for (int k = 0; k < kmax; ++k) {
         // ---- pivot: largest residual norm among unselected columns, lowest index on ties
-        // (every warp reduces the same shared norms, so all agree without a barrier)
-        float bv = -1.f;
-        int bi = 0x7fffffff;
-        for (int j = lane; j < c; j += 32) {
-            if (selpos[j] < 0) {
-                const float v = norms[j];
-                if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(DM_FULL, bv, o);
-            const int oi = __shfl_xor_sync(DM_FULL, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-        }
+        // (every warp reduces the same per-warp candidates, so all agree without a barrier)
+        float bv = lane < kSkelWarps ? wbest_v[lane] : -1.f;
+        int bi = lane < kSkelWarps ? wbest_j[lane] : 0x7fffffff;
+        warp_argmax(bv, bi);
         if (k == 0) nrm0 = bv;
         if (!(bv > a.tol * nrm0) || bv <= 0.f) break;
         const int p = bi;
@@ -502,12 +522,19 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
             if (f < nf) qrow(k)[f] = scale4(qv4[f], inv);
         }
         // ---- every other remaining column: R(k, j) = q_k^T a_j, a_j -= R(k, j) q_k, |a_j|
+        float cv = -1.f;
+        int cj = 0x7fffffff;
         if (a_sm) {
             for (int b = 0; b < nb; ++b)
-                column_batch<M, CB>(xs, ldr, nf, c, b, qv4, inv, selpos, norms, R + (size_t)k * a.cmax);
+                column_batch<M, CB>(xs, ldr, nf, c, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
         } else {
             for (int b = 0; b < nb; ++b)
-                column_batch<M, CB>(Ag, ldr, nf, c, b, qv4, inv, selpos, norms, R + (size_t)k * a.cmax);
+                column_batch<M, CB>(Ag, ldr, nf, c, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
+        }
+        warp_argmax(cv, cj);
+        if (lane == 0) {
+            wbest_v[warp] = cv;
+            wbest_j[warp] = cj;
         }
         rank = k + 1;
         __syncthreads();
@@ -517,22 +544,28 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     // ---- P = [I, R11^-1 R12] in candidate order; rows t < rank of the node's slot
     float *Pn = a.P + (size_t)node * a.max_rank * a.ldp;
     const int ldas = (c + 3) & ~3;
-    if ((size_t)rank * ldas <= extra) {
-        // in shared memory (A and Q are dead): Rs = R(0:rank, :); each unselected column is
-        // solved in place (the pivot columns it reads stay R11), in the same operation order as
-        // the global-memory form below; then coalesced row stores with the identity columns
-        float *Rs = xs;
+    if ((size_t)rank * ldas + (size_t)rank * rank <= extra) {
+        // in shared memory (A and Q are dead): Rs = R(0:rank, :) and a compact copy
+        // R11[t][u] = R(t, piv[u]); each unselected column is solved in place, in the same
+        // operation order as the global-memory form below; then coalesced row stores with the
+        // identity columns
+        float *Rs = xs, *R11 = xs + (size_t)rank * ldas;
         for (int e = threadIdx.x; e < rank * ldas; e += blockDim.x) {
             const int t = e / ldas, j = e - t * ldas;
             Rs[e] = j < c ? R[(size_t)t * a.cmax + j] : 0.f;
+        }
+        for (int e = threadIdx.x; e < rank * rank; e += blockDim.x) {
+            const int t = e / rank, u = e - t * rank;
+            R11[e] = R[(size_t)t * a.cmax + piv[u]];
         }
         __syncthreads();
         for (int j = threadIdx.x; j < c; j += blockDim.x) {
             if (selpos[j] >= 0) continue;
             for (int t = rank - 1; t >= 0; --t) {
+                const float *r11 = R11 + (size_t)t * rank;
                 float v = Rs[(size_t)t * ldas + j];
-                for (int u = t + 1; u < rank; ++u) v = fmaf(-Rs[(size_t)t * ldas + piv[u]], Rs[(size_t)u * ldas + j], v);
-                Rs[(size_t)t * ldas + j] = v / Rs[(size_t)t * ldas + piv[t]];
+                for (int u = t + 1; u < rank; ++u) v = fmaf(-r11[u], Rs[(size_t)u * ldas + j], v);
+                Rs[(size_t)t * ldas + j] = v / r11[t];
             }
         }
         __syncthreads();
@@ -628,7 +661,7 @@ size_t dm_fill_smem_bytes() {
 
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
     const size_t ldr = (size_t)((rmax + 3) & ~3);
-    return sizeof(float) * ldr + sizeof(float) * (size_t)(4 * cmax + 4 * ldr + cmax + max_rank) +
+    return sizeof(float) * ldr + sizeof(float) * (size_t)(4 * cmax + 4 * ldr + max_rank) +
            sizeof(int) * (size_t)(cmax + rmax + cmax + max_rank);
 }
 
