@@ -171,20 +171,25 @@ __global__ void __launch_bounds__(512) tree_image_kernel(const __grid_constant__
         rk[n] = H.ranks[n];
         own[n] = H.town[n];
     }
+    // a warp per owned node (the nodes' copies are independent, so the warps overlap their
+    // global-memory latency instead of walking the nodes one after another)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int mine = 0;  // owned nodes seen so far: the warp takes every nw-th
     for (int n = 0; n < ninternal; ++n) {
         if (tree_owner(n, ls) != c) continue;
+        if ((mine++ % nw) != warp) continue;
         const int4 ln = H.tlay[n];
         const int s = H.ranks[n], sl = H.ranks[2 * n + 1], sr = H.ranks[2 * n + 2], cc = sl + sr;
         const float *Bg = H.B + (size_t)n * H.max_rank * H.max_rank;
         const int rs = sr | 1;
-        for (int e = threadIdx.x; e < sl * rs; e += blockDim.x) {
+        for (int e = lane; e < sl * rs; e += 32) {
             const int a = e / rs, b = e - a * rs;
             out[ln.y + e] = b < sr ? Bg[a * sr + b] : 0.f;
         }
         if (n == 0) continue;
         const float *Pg = H.P + (size_t)n * H.max_rank * H.ldp;
         const int cs = s | 1;
-        for (int e = threadIdx.x; e < cc * cs; e += blockDim.x) {
+        for (int e = lane; e < cc * cs; e += 32) {
             const int j = e / cs, t = e - j * cs;
             out[ln.x + e] = t < s ? Pg[(size_t)t * H.ldp + j] : 0.f;
         }

@@ -509,11 +509,14 @@ __global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const dou
 __global__ void tvec_orth_kernel(int m, int k, const double *theta, double *Y, int ldy,
                                  float *Yf) {
     __shared__ double red[32];
+    __shared__ double th[kKMax];  // Ritz values staged once (the pair loop tests every pair)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) th[i] = theta[i];
+    __syncthreads();
     double tmax = 0.0;
-    for (int i = 0; i < k; ++i) tmax = fmax(tmax, fabs(theta[i]));
+    for (int i = 0; i < k; ++i) tmax = fmax(tmax, fabs(th[i]));
     for (int i = 1; i < k; ++i) {
         for (int j = 0; j < i; ++j) {
-            if (fabs(theta[i] - theta[j]) > 1e-10 * tmax) continue;
+            if (fabs(th[i] - th[j]) > 1e-10 * tmax) continue;
             double part = 0.0;
             for (int t = threadIdx.x; t < m; t += blockDim.x) part += Y[(size_t)i * ldy + t] * Y[(size_t)j * ldy + t];
             part = dm_warp_sum_d(part);
@@ -548,6 +551,7 @@ __global__ void __launch_bounds__(256) ritzvec_kernel(const float *__restrict__ 
                                                       const float *__restrict__ Yf, int64_t N,
                                                       float *__restrict__ Phi, double *__restrict__ colsum) {
     extern __shared__ float sY[];  // m x k
+    __shared__ float csum[kKMax][8];  // per-warp sums of squares
     for (int e = threadIdx.x; e < m * k; e += blockDim.x) sY[e] = Yf[e];
     __syncthreads();
     const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -555,20 +559,35 @@ __global__ void __launch_bounds__(256) ritzvec_kernel(const float *__restrict__ 
 #pragma unroll
     for (int i = 0; i < kKMax; ++i) acc[i] = 0.f;
     if (pos < N) {
-        for (int t = 0; t < m; ++t) {
-            const float v = V[(size_t)t * ldv + pos];
+        // basis entries eight at a time, all loads issued before the products
+        for (int t0 = 0; t0 < m; t0 += 8) {
+            float v[8];
 #pragma unroll
-            for (int i = 0; i < kKMax; ++i)
-                if (i < k) acc[i] = fmaf(v, sY[t * k + i], acc[i]);
+            for (int u = 0; u < 8; ++u) v[u] = t0 + u < m ? __ldcs(V + (size_t)(t0 + u) * ldv + pos) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (t0 + u >= m) break;
+#pragma unroll
+                for (int i = 0; i < kKMax; ++i)
+                    if (i < k) acc[i] = fmaf(v[u], sY[(t0 + u) * k + i], acc[i]);
+            }
         }
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < kKMax; ++i) {
         if (i < k) {
             if (pos < N) Phi[(size_t)i * N + pos] = acc[i];
             const float ss = dm_warp_sum(acc[i] * acc[i]);
-            if ((threadIdx.x & 31) == 0) atomicAdd(colsum + i, (double)ss);
+            if (lane == 0) csum[i][warp] = ss;
         }
+    }
+    __syncthreads();
+    // one FP64 atomic per column and block (the per-warp form queued thousands on each address)
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)csum[threadIdx.x][w];
+        atomicAdd(colsum + threadIdx.x, t);
     }
 }
 
@@ -576,6 +595,7 @@ __global__ void __launch_bounds__(256) ritzvec_kernel(const float *__restrict__ 
 __global__ void __launch_bounds__(256) colmax_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm,
                                                      int64_t N, int k, const double *__restrict__ colsum,
                                                      unsigned long long *__restrict__ best) {
+    __shared__ unsigned long long wk[8];
     const int i = blockIdx.y;
     const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long key = 0ull;
@@ -588,7 +608,13 @@ __global__ void __launch_bounds__(256) colmax_kernel(const float *__restrict__ P
         const unsigned long long other = __shfl_xor_sync(DM_FULL, key, o);
         key = other > key ? other : key;
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(best + i, key);
+    if ((threadIdx.x & 31) == 0) wk[threadIdx.x >> 5] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = wk[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = wk[w] > b ? wk[w] : b;
+        atomicMax(best + i, b);  // one atomic per block and column
+    }
 }
 
 // sign of each column's largest-magnitude entry: the thread holding that original index reports it
@@ -605,11 +631,14 @@ __global__ void sign_pick_kernel(const float *__restrict__ Phi, const int32_t *_
 __global__ void finalize_vec_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm, int64_t N,
                                     const double *__restrict__ colsum, const int *__restrict__ neg,
                                     float *__restrict__ out) {
+    __shared__ double s_sc;
     const int i = blockIdx.y;
+    // the column's scale once per block (FP64 square root and division are long sequences here)
+    if (threadIdx.x == 0) s_sc = (neg[i] ? -1.0 : 1.0) / sqrt(colsum[i]);
+    __syncthreads();
     const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= N) return;
-    const double sc = (neg[i] ? -1.0 : 1.0) / sqrt(colsum[i]);
-    out[(size_t)i * N + perm[pos]] = (float)((double)Phi[(size_t)i * N + pos] * sc);
+    out[(size_t)i * N + perm[pos]] = (float)((double)Phi[(size_t)i * N + pos] * s_sc);
 }
 
 __global__ void coords_kernel(const float *__restrict__ evecs, const double *__restrict__ theta,

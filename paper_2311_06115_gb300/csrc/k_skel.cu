@@ -594,20 +594,46 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     if (threadIdx.x == 0) a.ranks[node] = rank;
 }
 
-// ---- near blocks K(I_a, I_a), row-major with leading dimension ldk, zero padded
+// ---- near blocks K(I_a, I_a), row-major with leading dimension ldk, zero padded (d <= 3: the
+// leaf's points and s are staged in shared memory; a thread per column, rows of the CTA's slice)
 __global__ void pack_near_kernel(const float *__restrict__ Xp, const float *__restrict__ sp, int64_t N, int d, int L,
                                  int leaf_max, int ldk, float *__restrict__ Knear) {
+    extern __shared__ float4 pts[];  // leaf_max: x, y, z, s
     const int leaf = blockIdx.x;
     int64_t st, sz;
     dm_node_range(N, (1 << L) - 1 + leaf, &st, &sz);
+    if (d > 3) {  // generic dimension: entries straight from the point arrays
+        float *blk = Knear + (size_t)leaf * leaf_max * ldk;
+        const int rows_per = (leaf_max + gridDim.y - 1) / gridDim.y;
+        const int r0 = blockIdx.y * rows_per, r1 = min(leaf_max, r0 + rows_per);
+        for (int i = r0; i < r1; ++i)
+            for (int j = threadIdx.x; j < ldk; j += blockDim.x)
+                blk[(size_t)i * ldk + j] = (i < sz && j < sz) ? kentry(Xp, sp, d, st + i, st + j) : 0.f;
+        return;
+    }
+    for (int j = threadIdx.x; j < (int)sz; j += blockDim.x) {
+        const int64_t g = st + j;
+        float4 v = make_float4(0.f, 0.f, 0.f, sp[g]);
+        if (d > 0) v.x = Xp[g * d];
+        if (d > 1) v.y = Xp[g * d + 1];
+        if (d > 2) v.z = Xp[g * d + 2];
+        pts[j] = v;
+    }
+    __syncthreads();
     float *blk = Knear + (size_t)leaf * leaf_max * ldk;
     const int rows_per = (leaf_max + gridDim.y - 1) / gridDim.y;
     const int r0 = blockIdx.y * rows_per;
     const int r1 = min(leaf_max, r0 + rows_per);
-    for (int i = r0; i < r1; ++i) {
-        for (int j = threadIdx.x; j < ldk; j += blockDim.x) {
+    for (int j = threadIdx.x; j < ldk; j += blockDim.x) {
+        const bool cj = j < sz;
+        const float4 pj = cj ? pts[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = r0; i < r1; ++i) {
             float v = 0.f;
-            if (i < sz && j < sz) v = kentry(Xp, sp, d, st + i, st + j);
+            if (i < sz && cj) {
+                const float4 pi = pts[i];  // broadcast
+                const float t0 = pi.x - pj.x, t1 = pi.y - pj.y, t2 = pi.z - pj.z;
+                v = pi.w * pj.w * dm_ex2(-fmaf(t2, t2, fmaf(t1, t1, t0 * t0)));
+            }
             blk[(size_t)i * ldk + j] = v;
         }
     }
@@ -761,7 +787,8 @@ cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cud
         dm_count_launches(1);
     } else if (pack_near) {
         dim3 grid(1u << H.L, (unsigned)((H.leaf_max + 31) / 32));
-        pack_near_kernel<<<grid, 128, 0, st>>>(H.Xs, H.sp, H.N, H.d, H.L, H.leaf_max, H.ldk, Knear);
+        pack_near_kernel<<<grid, 128, sizeof(float4) * (size_t)H.leaf_max, st>>>(H.Xs, H.sp, H.N, H.d, H.L,
+                                                                                  H.leaf_max, H.ldk, Knear);
         dm_count_launches(1);
     }
     if (H.L > 0) {
