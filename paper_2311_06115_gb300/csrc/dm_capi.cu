@@ -141,6 +141,13 @@ struct dm_ctx {
     DmBlockWork blk{};
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the tree build runs on its own high-priority stream, concurrently with the degree
+    // passes still in flight on `stream` (it needs the points and eps, not the degrees)
+    cudaStream_t tstream = nullptr;
+    cudaEvent_t ev_pre = nullptr;   // recorded on `stream` before the degree passes
+    cudaEvent_t ev_tree = nullptr;  // end of the tree build on `tstream`
+    cudaEvent_t cr_a = nullptr, cr_b = nullptr;  // create phase, resolved when stats are read
+    bool cr_pending = false;
     // io staging
     float *io_x = nullptr, *io_y = nullptr;
     int64_t io_elems = 0;
@@ -152,6 +159,11 @@ struct dm_ctx {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side) cudaStreamDestroy(side);
+        if (ev_pre) cudaEventDestroy(ev_pre);
+        if (ev_tree) cudaEventDestroy(ev_tree);
+        if (cr_a) cudaEventDestroy(cr_a);
+        if (cr_b) cudaEventDestroy(cr_b);
+        if (tstream) cudaStreamDestroy(tstream);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
     void release(const Alloc &a) {
@@ -245,6 +257,16 @@ struct PhaseTimer {
         if (b) cudaEventDestroy(b);
     }
 };
+
+// the create phase is timed by two events resolved on first read, so dm_create returns with
+// the degree passes still running (dm_compress overlaps its tree build with them)
+void resolve_create_time(dm_ctx *h) {
+    if (!h->cr_pending) return;
+    float ms = 0.f;
+    if (cudaEventSynchronize(h->cr_b) == cudaSuccess && cudaEventElapsedTime(&ms, h->cr_a, h->cr_b) == cudaSuccess)
+        h->stats.ms_create = ms;
+    h->cr_pending = false;
+}
 
 int set_device(dm_ctx *h) {
     int cur = -1;
@@ -750,7 +772,10 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
     h->stats.d = d;
     h->stats.alpha = alpha;
     rc = [&]() -> int {
-        PhaseTimer t(h->stream);
+        DM_CUDA(cudaEventCreate(&h->cr_a));
+        DM_CUDA(cudaEventCreate(&h->cr_b));
+        DM_CUDA(cudaEventCreateWithFlags(&h->ev_pre, cudaEventDisableTiming));
+        DM_CUDA(cudaEventRecord(h->cr_a, h->stream));
         DM_CHECK(h->alloc(&h->X, (size_t)N * d, G_BASE));
         DM_CUDA(cudaMemcpyAsync(h->X, points, sizeof(float) * (size_t)N * d, cudaMemcpyDefault, h->stream));
         if (eps <= 0.0) {
@@ -779,12 +804,15 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
         DM_CHECK(h->alloc(&h->sf, (size_t)N, G_BASE));
         DM_CHECK(h->alloc(&h->qaf, (size_t)N, G_BASE));
         DM_CHECK(h->alloc(&h->tmpw, (size_t)N, G_BASE));
+        // the degree passes' temporaries live as long as the handle: dm_create returns while
+        // those passes may still run
         float *nrm = nullptr, *nmax = nullptr;
         double *cwork = nullptr;
-        DM_CHECK(h->alloc(&nrm, (size_t)N, G_WORK));
-        DM_CHECK(h->alloc(&nmax, 1, G_WORK));
-        DM_CHECK(h->alloc(&cwork, 8, G_WORK));
+        DM_CHECK(h->alloc(&nrm, (size_t)N, G_BASE));
+        DM_CHECK(h->alloc(&nmax, 1, G_BASE));
+        DM_CHECK(h->alloc(&cwork, 8, G_BASE));
         DM_CUDA(dm_launch_center_scale(h->X, N, d, eps, h->Xs, nrm, nmax, cwork, h->stream));
+        DM_CUDA(cudaEventRecord(h->ev_pre, h->stream));
         if (d >= kDegTcMinD && dm_degtc_available()) {
             // high dimension: the Gram matrix on the tensor cores, exp and row sums fused
             unsigned char *work = nullptr;
@@ -803,6 +831,7 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
             DM_CUDA(cudaStreamSynchronize(h->stream));
             if (herr) return fail(DM_ETIMEOUT, "a bounded wait of the tensor-core degree pass gave up");
             h->stats.degree_path = S.quant ? 2 : 1;
+            h->free_group(G_WORK);  // the stream has been synchronised
         } else {
             DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, nullptr, h->q, h->stream));
             DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
@@ -810,8 +839,8 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
             DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
             h->stats.degree_path = 0;
         }
-        h->stats.ms_create = t.stop();
-        h->free_group(G_WORK);
+        DM_CUDA(cudaEventRecord(h->cr_b, h->stream));
+        h->cr_pending = true;
         DM_CUDA(cudaGetLastError());
         return DM_OK;
     }();
@@ -827,6 +856,7 @@ int dm_destroy(dm_handle h) {
     if (!h) return fail(DM_EINVAL, "handle is NULL");
     set_device(h);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->tstream) cudaStreamSynchronize(h->tstream);
     delete h;
     return DM_OK;
 }
@@ -847,17 +877,26 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
     h->tol = tol;
     resolve_near_mode(h);
     const int nleaves = 1 << L;
-    // ---- tree
+    // ---- tree, on its own high-priority stream: it waits only for the points and eps (the
+    // event before the degree passes), so it runs while those passes may still be in flight
     float ms_tree = 0, ms_skel = 0, ms_pack = 0;
+    if (!h->tstream) {
+        int lo = 0, hi = 0;
+        DM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        DM_CUDA(cudaStreamCreateWithPriority(&h->tstream, cudaStreamNonBlocking, hi));
+        DM_CUDA(cudaEventCreateWithFlags(&h->ev_tree, cudaEventDisableTiming));
+    }
     {
-        PhaseTimer t(h->stream);
+        const cudaStream_t ts = h->tstream;
+        if (h->ev_pre) DM_CUDA(cudaStreamWaitEvent(ts, h->ev_pre, 0));
+        PhaseTimer t(ts);
         int32_t *pa = nullptr, *pb = nullptr;
         DM_CHECK(h->alloc(&pa, (size_t)h->N, G_STRUCT));
         DM_CHECK(h->alloc(&pb, (size_t)h->N, G_STRUCT));
         // identity permutation: every node starts in increasing original index
         std::vector<int32_t> ident((size_t)h->N);
         for (int64_t i = 0; i < h->N; ++i) ident[(size_t)i] = (int32_t)i;
-        DM_CUDA(cudaMemcpyAsync(pa, ident.data(), sizeof(int32_t) * (size_t)h->N, cudaMemcpyHostToDevice, h->stream));
+        DM_CUDA(cudaMemcpyAsync(pa, ident.data(), sizeof(int32_t) * (size_t)h->N, cudaMemcpyHostToDevice, ts));
         DmTreeWork w{};
         const size_t nitems = dm_tree_items_bound(h->N, L) + 1;
         w.max_items = (int)nitems;
@@ -880,10 +919,12 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         w.sel = sel;
         w.icnt = icnt;
         int32_t *perm = nullptr;
-        DM_CUDA(dm_tree_build(h->X, h->N, h->d, h->eps, L, pa, pb, &perm, &w, h->stream));
+        DM_CUDA(dm_tree_build(h->X, h->N, h->d, h->eps, L, pa, pb, &perm, &w, ts));
         h->perm = perm;
-        ms_tree = t.stop();
+        ms_tree = t.stop();  // the host waits for the tree only; the degree passes may still run
         h->free_group(G_WORK);
+        DM_CUDA(cudaEventRecord(h->ev_tree, ts));
+        DM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_tree, 0));
     }
     // ---- skeletons
     {
@@ -1131,6 +1172,7 @@ int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi) {
 
 int dm_get_stats(dm_handle h, dm_stats *st) {
     if (!h || !st) return fail(DM_EINVAL, "NULL argument");
+    resolve_create_time(h);
     *st = h->stats;
     return DM_OK;
 }
