@@ -146,6 +146,7 @@ struct dm_ctx {
     cudaStream_t tstream = nullptr;
     cudaEvent_t ev_pre = nullptr;   // recorded on `stream` before the degree passes
     cudaEvent_t ev_tree = nullptr;  // end of the tree build on `tstream`
+    cudaEvent_t ev_sel = nullptr;   // end of the second median select on `tstream`
     cudaEvent_t cr_a = nullptr, cr_b = nullptr;  // create phase, resolved when stats are read
     bool cr_pending = false;
     // io staging
@@ -161,6 +162,7 @@ struct dm_ctx {
         if (side) cudaStreamDestroy(side);
         if (ev_pre) cudaEventDestroy(ev_pre);
         if (ev_tree) cudaEventDestroy(ev_tree);
+        if (ev_sel) cudaEventDestroy(ev_sel);
         if (cr_a) cudaEventDestroy(cr_a);
         if (cr_b) cudaEventDestroy(cr_b);
         if (tstream) cudaStreamDestroy(tstream);
@@ -257,6 +259,17 @@ struct PhaseTimer {
         if (b) cudaEventDestroy(b);
     }
 };
+
+// the handle's high-priority side stream (tree build, second median select) and its events
+int ensure_tree_stream(dm_ctx *h) {
+    if (h->tstream) return DM_OK;
+    int lo = 0, hi = 0;
+    DM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    DM_CUDA(cudaStreamCreateWithPriority(&h->tstream, cudaStreamNonBlocking, hi));
+    DM_CUDA(cudaEventCreateWithFlags(&h->ev_tree, cudaEventDisableTiming));
+    DM_CUDA(cudaEventCreateWithFlags(&h->ev_sel, cudaEventDisableTiming));
+    return DM_OK;
+}
 
 // the create phase is timed by two events resolved on first read, so dm_create returns with
 // the degree passes still running (dm_compress overlaps its tree build with them)
@@ -775,6 +788,7 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
         DM_CUDA(cudaEventCreate(&h->cr_a));
         DM_CUDA(cudaEventCreate(&h->cr_b));
         DM_CUDA(cudaEventCreateWithFlags(&h->ev_pre, cudaEventDisableTiming));
+        DM_CHECK(ensure_tree_stream(h));
         DM_CUDA(cudaEventRecord(h->cr_a, h->stream));
         DM_CHECK(h->alloc(&h->X, (size_t)N * d, G_BASE));
         DM_CUDA(cudaMemcpyAsync(h->X, points, sizeof(float) * (size_t)N * d, cudaMemcpyDefault, h->stream));
@@ -787,7 +801,7 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
             DM_CHECK(h->alloc(&res, 1, G_WORK));
             DM_CHECK(h->alloc(&sel, 2 * dm_select_state_bytes(), G_WORK));
             DM_CUDA(dm_launch_pair_sqdist(h->X, N, d, h->cfg.seed, pairs, m, h->stream));
-            DM_CUDA(dm_launch_select_median(pairs, m, sel, res, h->stream));
+            DM_CUDA(dm_launch_select_median(pairs, m, sel, res, h->stream, h->tstream, h->ev_tree, h->ev_sel));
             DM_CUDA(cudaMemcpyAsync(&eps, res, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             DM_CUDA(cudaStreamSynchronize(h->stream));
             h->free_group(G_WORK);
@@ -880,12 +894,7 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
     // ---- tree, on its own high-priority stream: it waits only for the points and eps (the
     // event before the degree passes), so it runs while those passes may still be in flight
     float ms_tree = 0, ms_skel = 0, ms_pack = 0;
-    if (!h->tstream) {
-        int lo = 0, hi = 0;
-        DM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        DM_CUDA(cudaStreamCreateWithPriority(&h->tstream, cudaStreamNonBlocking, hi));
-        DM_CUDA(cudaEventCreateWithFlags(&h->ev_tree, cudaEventDisableTiming));
-    }
+    DM_CHECK(ensure_tree_stream(h));
     {
         const cudaStream_t ts = h->tstream;
         if (h->ev_pre) DM_CUDA(cudaStreamWaitEvent(ts, h->ev_pre, 0));

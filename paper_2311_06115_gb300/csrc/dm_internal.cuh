@@ -179,7 +179,9 @@ struct DmHmat {
 cudaError_t dm_launch_pair_sqdist(const float *X, int64_t N, int d, uint64_t seed, double *out, int64_t m,
                                   cudaStream_t st);
 size_t dm_select_state_bytes();
-cudaError_t dm_launch_select_median(double *vals, int64_t m, void *state, double *result, cudaStream_t st);
+// st2, fork, join (optional, all three or none): a second stream for the second order statistic
+cudaError_t dm_launch_select_median(double *vals, int64_t m, void *state, double *result, cudaStream_t st,
+                                    cudaStream_t st2 = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 cudaError_t dm_launch_scale_points(const float *X, int64_t N, int d, double eps, float *Xs, cudaStream_t st);
 cudaError_t dm_launch_degree_pass(const float *Xs, int64_t N, int d, const float *wcol, double *out,
                                   cudaStream_t st);

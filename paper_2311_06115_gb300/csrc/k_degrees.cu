@@ -576,22 +576,36 @@ size_t dm_select_state_bytes() { return sizeof(SelectState); }
 
 // exact median of vals[0..m): two radix selects (ranks m/2-1 and m/2) into two
 // SelectState records at `state` (2 * dm_select_state_bytes() of device memory)
-cudaError_t dm_launch_select_median(double *vals, int64_t m, void *state, double *result, cudaStream_t st) {
+cudaError_t dm_launch_select_median(double *vals, int64_t m, void *state, double *result, cudaStream_t st,
+                                    cudaStream_t st2, cudaEvent_t fork, cudaEvent_t join) {
     SelectState *S = reinterpret_cast<SelectState *>(state);
     const int even = (m % 2 == 0) ? 1 : 0;
     const long long ranks[2] = {even ? m / 2 - 1 : m / 2, m / 2};
     const int blocks = (int)((m + 511) / 512 < 2 * 152 ? (m + 511) / 512 : 2 * 152);
+    // the two selects are independent chains of small launches: the second runs on st2
+    // (when given) at the same time as the first
+    const bool two = st2 != nullptr && fork != nullptr && join != nullptr;
+    cudaError_t e;
+    if (two) {
+        if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st2, fork, 0)) != cudaSuccess) return e;
+    }
     for (int r = 0; r < 2; ++r) {
-        select_init_kernel<<<1, 256, 0, st>>>(S + r, ranks[r]);
+        const cudaStream_t sr = (two && r == 1) ? st2 : st;
+        select_init_kernel<<<1, 256, 0, sr>>>(S + r, ranks[r]);
         dm_count_launches(1);
         for (int top = 64; top > 0; top -= kSelBits) {
             const int bits = top >= kSelBits ? kSelBits : top;
             const int shift = top - bits;
-            select_hist_kernel<<<blocks, 512, 0, st>>>(vals, m, shift, S + r);
+            select_hist_kernel<<<blocks, 512, 0, sr>>>(vals, m, shift, S + r);
             dm_count_launches(1);
-            select_step_kernel<<<1, 1024, 0, st>>>(shift, bits, S + r);
+            select_step_kernel<<<1, 1024, 0, sr>>>(shift, bits, S + r);
             dm_count_launches(1);
         }
+    }
+    if (two) {
+        if ((e = cudaEventRecord(join, st2)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return e;
     }
     median_finish_kernel<<<1, 1, 0, st>>>(S, S + 1, even, result);
     dm_count_launches(1);

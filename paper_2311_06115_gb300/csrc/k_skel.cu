@@ -654,18 +654,32 @@ __global__ void pack_far_kernel(const float *__restrict__ Xp, const float *__res
 }
 
 // PT[leaf][i][t] = P_leaf[t][i] (t < rank, zero up to ldt), the point-major copy the
-// downward pass reads with contiguous 16-byte loads
-__global__ void transpose_leaf_kernel(DmHmat H, float *__restrict__ PT) {
+// downward pass reads with contiguous 16-byte loads. Slices of 32 points go through a padded
+// shared tile, so both the reads of P's rows and the writes of PT's rows are coalesced.
+constexpr int kTrPts = 32;
+constexpr int kTrMaxT = 256;  // ldt <= max_rank <= 256
+__global__ void __launch_bounds__(256) transpose_leaf_kernel(DmHmat H, float *__restrict__ PT) {
+    __shared__ float tile[kTrMaxT][kTrPts + 1];
     const int leaf = blockIdx.x;
     const int node = (1 << H.L) - 1 + leaf;
     int64_t st, sz;
     dm_node_range(H.N, node, &st, &sz);
     const int s = H.ranks[node];
+    const int ldt = H.ldt;
     const float *Pn = H.P + (size_t)node * H.max_rank * H.ldp;
-    float *out = PT + (size_t)leaf * H.leaf_max * H.ldt;
-    for (int e = threadIdx.x; e < (int)sz * H.ldt; e += blockDim.x) {
-        const int i = e / H.ldt, t = e % H.ldt;
-        out[e] = t < s ? Pn[(size_t)t * H.ldp + i] : 0.f;
+    float *out = PT + (size_t)leaf * H.leaf_max * ldt;
+    for (int i0 = 0; i0 < (int)sz; i0 += kTrPts) {
+        const int np = (int)sz - i0 < kTrPts ? (int)sz - i0 : kTrPts;
+        __syncthreads();
+        for (int e = threadIdx.x; e < ldt * kTrPts; e += blockDim.x) {
+            const int t = e / kTrPts, ii = e - t * kTrPts;
+            tile[t][ii] = (t < s && ii < np) ? Pn[(size_t)t * H.ldp + i0 + ii] : 0.f;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < np * ldt; e += blockDim.x) {
+            const int ii = e / ldt, t = e - ii * ldt;
+            out[(size_t)(i0 + ii) * ldt + t] = tile[t][ii];
+        }
     }
 }
 
@@ -799,6 +813,7 @@ cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cud
 }
 
 cudaError_t dm_transpose_leaf_bases(const DmHmat &H, float *PT, cudaStream_t st) {
+    if (H.ldt > kTrMaxT) return cudaErrorInvalidValue;
     transpose_leaf_kernel<<<1u << H.L, 256, 0, st>>>(H, PT);
     dm_count_launches(1);
     return cudaGetLastError();
