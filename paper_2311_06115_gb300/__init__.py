@@ -237,8 +237,12 @@ def dm_config_default(**overrides) -> dm_config:
 
 
 def dm_create(points, eps: float = -1.0, alpha: float = 1.0, cfg: dm_config | None = None,
-              use_torch_allocator: bool = True) -> Handle:
-    """dm_create: points (N, d) float32, host (numpy/torch) or CUDA tensor."""
+              use_torch_allocator: bool = False) -> Handle:
+    """dm_create: points (N, d) float32, host (numpy/torch) or CUDA tensor.
+
+    By default the library allocates from the device's stream-ordered pool; with
+    use_torch_allocator=True it draws its device memory from torch's caching allocator
+    instead (one pool shared with torch, at the cost of a Python call per allocation)."""
     lib = load()
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float32)

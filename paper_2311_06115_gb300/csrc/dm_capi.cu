@@ -103,6 +103,23 @@ inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
+// The default pool of this process's context on `dev` keeps freed memory instead of
+// returning it at every synchronisation (a setting of the pool, reset with the process)
+inline void keep_pool_memory(int dev) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (int d : done)
+        if (d == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.push_back(dev);
+}
+
 struct dm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -171,10 +188,13 @@ struct dm_ctx {
     void release(const Alloc &a) {
         if (!a.p) return;
         if (cfg.free) cfg.free(a.p, a.bytes, cfg.alloc_user);
-        else cudaFree(a.p);
+        else cudaFreeAsync(a.p, stream);  // after every use enqueued on (or joined into) `stream`
     }
+    // Without a caller allocator: stream-ordered allocations from the device's default pool
+    // (no device-wide synchronisation; the pool keeps freed memory for the next request),
+    // ordered on `on` (the stream that first uses the buffer; default `stream`).
     template <class T>
-    int alloc(T **out, size_t count, int group) {
+    int alloc(T **out, size_t count, int group, cudaStream_t on = nullptr) {
         size_t bytes = sizeof(T) * (count > 0 ? count : 1);
         bytes = (bytes + 255) & ~size_t(255);
         void *p = nullptr;
@@ -182,10 +202,11 @@ struct dm_ctx {
             p = cfg.alloc(bytes, cfg.alloc_user);
             if (!p) return fail(DM_ENOMEM, "device allocation of %zu bytes failed (caller allocator)", bytes);
         } else {
-            cudaError_t e = cudaMalloc(&p, bytes);
+            keep_pool_memory(device);
+            cudaError_t e = cudaMallocAsync(&p, bytes, on ? on : stream);
             if (e != cudaSuccess) {
                 cudaGetLastError();
-                return fail(DM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+                return fail(DM_ENOMEM, "cudaMallocAsync of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
             }
         }
         allocs.push_back({p, bytes, group});
@@ -900,8 +921,8 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         if (h->ev_pre) DM_CUDA(cudaStreamWaitEvent(ts, h->ev_pre, 0));
         PhaseTimer t(ts);
         int32_t *pa = nullptr, *pb = nullptr;
-        DM_CHECK(h->alloc(&pa, (size_t)h->N, G_STRUCT));
-        DM_CHECK(h->alloc(&pb, (size_t)h->N, G_STRUCT));
+        DM_CHECK(h->alloc(&pa, (size_t)h->N, G_STRUCT, ts));
+        DM_CHECK(h->alloc(&pb, (size_t)h->N, G_STRUCT, ts));
         // identity permutation: every node starts in increasing original index
         std::vector<int32_t> ident((size_t)h->N);
         for (int64_t i = 0; i < h->N; ++i) ident[(size_t)i] = (int32_t)i;
@@ -909,22 +930,22 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         DmTreeWork w{};
         const size_t nitems = dm_tree_items_bound(h->N, L) + 1;
         w.max_items = (int)nitems;
-        DM_CHECK(h->alloc(&w.wbuf, (size_t)h->N, G_WORK));
-        DM_CHECK(h->alloc(&w.keys, (size_t)h->N, G_WORK));
+        DM_CHECK(h->alloc(&w.wbuf, (size_t)h->N, G_WORK, ts));
+        DM_CHECK(h->alloc(&w.keys, (size_t)h->N, G_WORK, ts));
         unsigned char *items = nullptr, *c1 = nullptr, *c2 = nullptr;
-        DM_CHECK(h->alloc(&items, nitems * dm_tree_item_bytes(), G_WORK));
-        DM_CHECK(h->alloc(&c1, nitems * dm_tree_cand_bytes(), G_WORK));
-        DM_CHECK(h->alloc(&c2, nitems * dm_tree_cand_bytes(), G_WORK));
+        DM_CHECK(h->alloc(&items, nitems * dm_tree_item_bytes(), G_WORK, ts));
+        DM_CHECK(h->alloc(&c1, nitems * dm_tree_cand_bytes(), G_WORK, ts));
+        DM_CHECK(h->alloc(&c2, nitems * dm_tree_cand_bytes(), G_WORK, ts));
         w.items = items;
         w.cand1 = c1;
         w.cand2 = c2;
         // the large levels (nodes above dm_tree_big_node() points) split over many CTAs
         w.max_big = (int)(h->N / dm_tree_big_node()) + 1;
         unsigned char *sel = nullptr;
-        DM_CHECK(h->alloc(&sel, (size_t)w.max_big * dm_tree_sel_bytes(), G_WORK));
-        DM_CHECK(h->alloc(&w.hist, (size_t)w.max_big * 256, G_WORK));
+        DM_CHECK(h->alloc(&sel, (size_t)w.max_big * dm_tree_sel_bytes(), G_WORK, ts));
+        DM_CHECK(h->alloc(&w.hist, (size_t)w.max_big * 256, G_WORK, ts));
         unsigned char *icnt = nullptr;
-        DM_CHECK(h->alloc(&icnt, nitems * 8, G_WORK));
+        DM_CHECK(h->alloc(&icnt, nitems * 8, G_WORK, ts));
         w.sel = sel;
         w.icnt = icnt;
         int32_t *perm = nullptr;
