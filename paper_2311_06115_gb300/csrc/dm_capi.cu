@@ -166,6 +166,33 @@ struct dm_ctx {
     cudaEvent_t ev_sel = nullptr;   // end of the second median select on `tstream`
     cudaEvent_t cr_a = nullptr, cr_b = nullptr;  // create phase, resolved when stats are read
     bool cr_pending = false;
+    // phases timed by event pairs on a stream, resolved when stats are read (no host wait)
+    struct Lap {
+        cudaEvent_t a, b;
+        float *dst;
+    };
+    std::vector<Lap> laps;
+    cudaEvent_t lap_begin(cudaStream_t s) {
+        cudaEvent_t a = nullptr;
+        if (cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+        return a;
+    }
+    void lap_end(cudaStream_t s, cudaEvent_t a, float *dst) {
+        cudaEvent_t b = nullptr;
+        if (!a || cudaEventCreate(&b) != cudaSuccess) return;
+        cudaEventRecord(b, s);
+        laps.push_back({a, b, dst});
+    }
+    void resolve_laps() {
+        for (auto &l : laps) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(l.b) == cudaSuccess && cudaEventElapsedTime(&ms, l.a, l.b) == cudaSuccess)
+                *l.dst = ms;
+            cudaEventDestroy(l.a);
+            cudaEventDestroy(l.b);
+        }
+        laps.clear();
+    }
     // io staging
     float *io_x = nullptr, *io_y = nullptr;
     int64_t io_elems = 0;
@@ -180,6 +207,10 @@ struct dm_ctx {
         if (ev_pre) cudaEventDestroy(ev_pre);
         if (ev_tree) cudaEventDestroy(ev_tree);
         if (ev_sel) cudaEventDestroy(ev_sel);
+        for (auto &l : laps) {
+            cudaEventDestroy(l.a);
+            cudaEventDestroy(l.b);
+        }
         if (cr_a) cudaEventDestroy(cr_a);
         if (cr_b) cudaEventDestroy(cr_b);
         if (tstream) cudaStreamDestroy(tstream);
@@ -421,10 +452,17 @@ int finish_structure(dm_ctx *h) {
     DM_CUDA(cudaMemsetAsync(h->cnt, 0, sizeof(unsigned) * nnodes, h->stream));
     DM_CUDA(cudaMemsetAsync(h->what, 0, sizeof(float) * (size_t)nnodes * h->max_rank, h->stream));
     DM_CUDA(cudaMemsetAsync(h->uhat, 0, sizeof(float) * (size_t)nnodes * h->max_rank, h->stream));
+    // near and sibling blocks need nothing from the host: enqueue them before the ranks'
+    // round trip, which they then hide
+    {
+        DmHmat H0 = h->hmat();
+        DM_CUDA(dm_pack(H0, h->Knear, h->B, cached, h->stream));
+    }
     // statistics
     std::vector<int32_t> rk(nnodes);
     DM_CUDA(cudaMemcpyAsync(rk.data(), h->ranks, sizeof(int32_t) * nnodes, cudaMemcpyDeviceToHost, h->stream));
     DM_CUDA(cudaStreamSynchronize(h->stream));
+    h->free_group(G_WORK);  // the skeletonization workspace: everything before is complete
     int rank_hi = 1;
     for (int node = 1; node < nnodes; ++node) rank_hi = rk[node] > rank_hi ? rk[node] : rank_hi;
     h->rank_hi = rank_hi;
@@ -447,16 +485,16 @@ int finish_structure(dm_ctx *h) {
             DM_CHECK(h->alloc(&h->timg, (size_t)img_off.back(), G_STRUCT));
             DM_CUDA(cudaMemcpyAsync(h->tlay, lay.data(), sizeof(int4) * lay.size(), cudaMemcpyHostToDevice,
                                     h->stream));
+            // pageable sources: each copy returns once its source is staged, so the host
+            // temporaries may go out of scope without a synchronisation
             DM_CUDA(cudaMemcpyAsync(h->timg_off, img_off.data(), sizeof(int) * img_off.size(),
                                     cudaMemcpyHostToDevice, h->stream));
-            DM_CUDA(cudaStreamSynchronize(h->stream));  // lay, own and img_off are host temporaries
             h->tree_ok = 1;
             h->tree_ls = ls;
             h->tree_smem = smem;
         }
     }
     DmHmat H = h->hmat();
-    DM_CUDA(dm_pack(H, h->Knear, h->B, cached, h->stream));
     DM_CUDA(dm_transpose_leaf_bases(H, h->PT, h->stream));
     DM_CUDA(dm_tree_image(H, h->stream));
     int rmin = 1 << 30, rmax = 0;
@@ -914,7 +952,7 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
     const int nleaves = 1 << L;
     // ---- tree, on its own high-priority stream: it waits only for the points and eps (the
     // event before the degree passes), so it runs while those passes may still be in flight
-    float ms_tree = 0, ms_skel = 0, ms_pack = 0;
+    float ms_tree = 0;
     DM_CHECK(ensure_tree_stream(h));
     {
         const cudaStream_t ts = h->tstream;
@@ -956,9 +994,10 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         DM_CUDA(cudaEventRecord(h->ev_tree, ts));
         DM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_tree, 0));
     }
-    // ---- skeletons
+    // ---- skeletons (no host wait: the workspace is freed after the next synchronisation, in
+    // finish_structure, and the phase is timed by deferred events)
     {
-        PhaseTimer t(h->stream);
+        cudaEvent_t t0 = h->lap_begin(h->stream);
         DM_CUDA(dm_permute_points(h->Xs, h->sf, h->perm, h->N, h->d, h->Xp, h->sp, h->stream));
         DmSkelWork w{};
         w.rmax = 2 * max_rank + 10;
@@ -972,17 +1011,14 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         DM_CHECK(h->alloc(&w.Q, (size_t)nleaves * max_rank * w.ldr, G_WORK));
         DM_CUDA(dm_skeletonize(h->Xp, h->sp, h->N, h->d, L, h->perm, tol, max_rank, h->cmax, h->ldp, h->cfg.seed,
                                h->ranks, h->skel, h->P, &w, h->stream));
-        ms_skel = t.stop();
-        h->free_group(G_WORK);
+        h->lap_end(h->stream, t0, &h->stats.ms_skeleton);
     }
     {
-        PhaseTimer t(h->stream);
+        cudaEvent_t t0 = h->lap_begin(h->stream);
         DM_CHECK(finish_structure(h));
-        ms_pack = t.stop();
+        h->lap_end(h->stream, t0, &h->stats.ms_pack);
     }
     h->stats.ms_tree = ms_tree;
-    h->stats.ms_skeleton = ms_skel;
-    h->stats.ms_pack = ms_pack;
     DM_CUDA(cudaGetLastError());
     return DM_OK;
 }
@@ -1144,6 +1180,7 @@ int dm_tune_leaf(dm_handle h, double tol, int32_t max_rank, int32_t k, const int
     int best = -1;
     for (int c = 0; c < ncand; ++c) {
         DM_CHECK(dm_compress(h, tol, candidates[c], max_rank));
+        h->resolve_laps();
         const float ms_c = h->stats.ms_tree + h->stats.ms_skeleton + h->stats.ms_pack;
         if (!xv) {
             // vectors live with the structure group (freed by the next compression)
@@ -1203,6 +1240,7 @@ int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi) {
 int dm_get_stats(dm_handle h, dm_stats *st) {
     if (!h || !st) return fail(DM_EINVAL, "NULL argument");
     resolve_create_time(h);
+    h->resolve_laps();
     *st = h->stats;
     return DM_OK;
 }
