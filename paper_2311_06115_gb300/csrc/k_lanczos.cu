@@ -62,7 +62,7 @@ __global__ void normalize_kernel(const float *__restrict__ z, int64_t N, const d
 // counter grows monotonically within a solve (targets (2j+1) G and (2j+2) G).
 // Barriers spin with a bounded iteration count; on exhaustion they raise *err and every
 // block returns (the host reports a timeout).
-constexpr int kStepThreads = 256;
+constexpr int kStepThreads = 512;  // one block per SM: fewer arrivals at each grid barrier
 constexpr int kStepWarps = kStepThreads / 32;
 constexpr long long kBarrierSpinLimit = 1ll << 22;
 
@@ -306,9 +306,9 @@ size_t step_smem_bytes(int m_max, int qt) {
 }
 
 int step_tile_quads(int m_max) {
-    // 128 quads (512 rows) per tile while the shared arrays stay under ~100 KB, which
-    // keeps two blocks on an SM (the coefficient arrays grow with m_max)
-    int qt = 128;
+    // 256 quads (1024 rows) per tile while the shared arrays stay under ~100 KB (the
+    // coefficient arrays grow with m_max)
+    int qt = 256;
     while (qt > 32 && step_smem_bytes(m_max, qt) > 100 * 1024) qt >>= 1;
     return qt;
 }
@@ -699,7 +699,7 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) 
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_step_kernel, kStepThreads, shm);
             if (e != cudaSuccess) return e;
             if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-            g = sms * (per_sm < 2 ? per_sm : 2);
+            g = sms;  // one block per SM
         }
         grid = g;
     }
