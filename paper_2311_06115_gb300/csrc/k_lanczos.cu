@@ -342,6 +342,20 @@ __device__ int sturm_count(const double *__restrict__ al, const double *__restri
     return cnt;
 }
 
+// Sturm count in FP32 by the LDL^T recurrence d_i = (alpha_i - x) - beta_{i-1}^2 / d_{i-1}
+// (number of negative d_i = eigenvalues below x); only used to narrow a bracket that FP64
+// counts then confirm
+__device__ int sturm_count_f32(const float *al, const float *b2, int m, float x) {
+    float d = al[0] - x;
+    int cnt = d < 0.f ? 1 : 0;
+    for (int i = 1; i < m; ++i) {
+        if (d == 0.f) d = -1e-30f;
+        d = (al[i] - x) - b2[i - 1] / d;
+        cnt += d < 0.f ? 1 : 0;
+    }
+    return cnt;
+}
+
 // One block of kRitzThreads per wanted eigenvalue (descending index i): multisection to full
 // FP64 precision with one shift per thread (four warps: all four FP64 units of the SM, seven
 // bits per round), then the residual bound beta_{m-1} |y_m| from
@@ -353,12 +367,16 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
                                                             double *__restrict__ work) {
     extern __shared__ double sd[];
     double *al = sd, *b2 = sd + m;
+    float *al32 = reinterpret_cast<float *>(b2 + m), *b232 = al32 + m;
     __shared__ unsigned s_above[kRitzThreads / 32];
     __shared__ double s_lo, s_hi;
+    __shared__ int s_ok[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < m; i += blockDim.x) {
         al[i] = alpha[i];
         b2[i] = (i < m - 1) ? beta[i] * beta[i] : 0.0;
+        al32[i] = (float)al[i];
+        b232[i] = (float)b2[i];
     }
     __syncthreads();
     // Gershgorin interval (warp 0)
@@ -384,6 +402,39 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
     double lo = s_lo, hi = s_hi;
     const int target = m - 1 - (int)blockIdx.x;  // ascending index of the wanted eigenvalue
     constexpr double kDen = (double)(kRitzThreads + 1);
+    // three coarse rounds with FP32 counts (the FP64 pipe is narrow on this part), then two
+    // FP64 counts confirm the bracket; if they do not, the FP64 rounds start from Gershgorin
+    {
+        float flo = (float)lo, fhi = (float)hi;
+        for (int round = 0; round < 3; ++round) {
+            const float x = flo + (fhi - flo) * (float)(tid + 1) / (float)kDen;
+            const int c = sturm_count_f32(al32, b232, m, x);
+            const unsigned above = __ballot_sync(DM_FULL, c > target);
+            if (lane == 0) s_above[warp] = above;
+            __syncthreads();
+            int g = -1;
+            for (int w = 0; w < kRitzThreads / 32 && g < 0; ++w)
+                if (s_above[w]) g = 32 * w + __ffs(s_above[w]) - 1;
+            __syncthreads();
+            auto shift = [&](int t) { return flo + (fhi - flo) * (float)(t + 1) / (float)kDen; };
+            if (g < 0) flo = shift(kRitzThreads - 1);
+            else {
+                const float xh = shift(g);
+                if (g > 0) flo = shift(g - 1);
+                fhi = xh;
+            }
+        }
+        if (tid < 2) {
+            const double x = tid == 0 ? (double)flo : (double)fhi;
+            const int c = sturm_count(al, b2, m, x);
+            s_ok[tid] = tid == 0 ? (c <= target) : (c > target);
+        }
+        __syncthreads();
+        if (s_ok[0] && s_ok[1] && (double)flo < (double)fhi) {
+            lo = (double)flo;
+            hi = (double)fhi;
+        }
+    }
     for (int round = 0; round < 16; ++round) {
         if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;  // uniform: every thread holds the same lo, hi
         const double x = lo + (hi - lo) * (double)(tid + 1) / kDen;
@@ -743,8 +794,8 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) 
 
 cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st) {
     (void)conv_tol;
-    ritz_kernel<<<k, kRitzThreads, sizeof(double) * 2 * (size_t)m, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.resid,
-                                                                         nullptr);
+    ritz_kernel<<<k, kRitzThreads, (sizeof(double) + sizeof(float)) * 2 * (size_t)m, st>>>(Lz.alpha, Lz.beta, m,
+                                                                                            Lz.theta, Lz.resid, nullptr);
     dm_count_launches(1);
     return cudaGetLastError();
 }
