@@ -312,11 +312,13 @@ struct PhaseTimer {
     }
 };
 
-// the handle's high-priority side stream (tree build, second median select) and its events
+// the handle's side stream (tree build, second median select) and its events
 int ensure_tree_stream(dm_ctx *h) {
     if (h->tstream) return DM_OK;
     int lo = 0, hi = 0;
     DM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    // highest priority: the tree's small latency-bound launches take SM slots ahead of the
+    // degree pass's many blocks (only created when the solve has the device to itself)
     DM_CUDA(cudaStreamCreateWithPriority(&h->tstream, cudaStreamNonBlocking, hi));
     DM_CUDA(cudaEventCreateWithFlags(&h->ev_tree, cudaEventDisableTiming));
     DM_CUDA(cudaEventCreateWithFlags(&h->ev_sel, cudaEventDisableTiming));
@@ -847,7 +849,10 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
         DM_CUDA(cudaEventCreate(&h->cr_a));
         DM_CUDA(cudaEventCreate(&h->cr_b));
         DM_CUDA(cudaEventCreateWithFlags(&h->ev_pre, cudaEventDisableTiming));
-        DM_CHECK(ensure_tree_stream(h));
+        // a side stream for the overlapped phases when the solve has the device to itself;
+        // on a shared device (serving slots) the other solves fill it, and one stream per
+        // request avoids creating streams per request
+        if (!h->cfg.shared_device) DM_CHECK(ensure_tree_stream(h));
         DM_CUDA(cudaEventRecord(h->cr_a, h->stream));
         DM_CHECK(h->alloc(&h->X, (size_t)N * d, G_BASE));
         DM_CUDA(cudaMemcpyAsync(h->X, points, sizeof(float) * (size_t)N * d, cudaMemcpyDefault, h->stream));
@@ -861,6 +866,7 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
             DM_CHECK(h->alloc(&sel, 2 * dm_select_state_bytes(), G_WORK));
             DM_CUDA(dm_launch_pair_sqdist(h->X, N, d, h->cfg.seed, pairs, m, h->stream));
             DM_CUDA(dm_launch_select_median(pairs, m, sel, res, h->stream, h->tstream, h->ev_tree, h->ev_sel));
+            // (tstream, ev_tree, ev_sel are null on a shared device: one stream)
             DM_CUDA(cudaMemcpyAsync(&eps, res, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             DM_CUDA(cudaStreamSynchronize(h->stream));
             h->free_group(G_WORK);
@@ -953,10 +959,11 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
     // ---- tree, on its own high-priority stream: it waits only for the points and eps (the
     // event before the degree passes), so it runs while those passes may still be in flight
     float ms_tree = 0;
-    DM_CHECK(ensure_tree_stream(h));
+    if (!h->cfg.shared_device) DM_CHECK(ensure_tree_stream(h));
     {
-        const cudaStream_t ts = h->tstream;
-        if (h->ev_pre) DM_CUDA(cudaStreamWaitEvent(ts, h->ev_pre, 0));
+        const bool side = h->tstream != nullptr;
+        const cudaStream_t ts = side ? h->tstream : h->stream;
+        if (side && h->ev_pre) DM_CUDA(cudaStreamWaitEvent(ts, h->ev_pre, 0));
         PhaseTimer t(ts);
         int32_t *pa = nullptr, *pb = nullptr;
         DM_CHECK(h->alloc(&pa, (size_t)h->N, G_STRUCT, ts));
@@ -984,6 +991,12 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         DM_CHECK(h->alloc(&w.hist, (size_t)w.max_big * 256, G_WORK, ts));
         unsigned char *icnt = nullptr;
         DM_CHECK(h->alloc(&icnt, nitems * 8, G_WORK, ts));
+        if (side && h->cfg.alloc) {
+            // a caller allocator's buffers are valid in `stream`'s order only: the tree then
+            // waits for everything enqueued there (no overlap with the degree passes)
+            DM_CUDA(cudaEventRecord(h->ev_sel, h->stream));
+            DM_CUDA(cudaStreamWaitEvent(ts, h->ev_sel, 0));
+        }
         w.sel = sel;
         w.icnt = icnt;
         int32_t *perm = nullptr;
@@ -991,8 +1004,10 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         h->perm = perm;
         ms_tree = t.stop();  // the host waits for the tree only; the degree passes may still run
         h->free_group(G_WORK);
-        DM_CUDA(cudaEventRecord(h->ev_tree, ts));
-        DM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_tree, 0));
+        if (side) {
+            DM_CUDA(cudaEventRecord(h->ev_tree, ts));
+            DM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_tree, 0));
+        }
     }
     // ---- skeletons (no host wait: the workspace is freed after the next synchronisation, in
     // finish_structure, and the phase is timed by deferred events)

@@ -62,8 +62,11 @@ __global__ void normalize_kernel(const float *__restrict__ z, int64_t N, const d
 // counter grows monotonically within a solve (targets (2j+1) G and (2j+2) G).
 // Barriers spin with a bounded iteration count; on exhaustion they raise *err and every
 // block returns (the host reports a timeout).
-constexpr int kStepThreads = 512;  // one block per SM: fewer arrivals at each grid barrier
-constexpr int kStepWarps = kStepThreads / 32;
+// block sizes: 512 threads, one block per SM, for the cooperative step (fewer arrivals at
+// each grid barrier); 256 threads, two per SM, for the phased step of a shared device (small
+// blocks that fit beside other solves' kernels)
+constexpr int kStepThreadsCoop = 512;
+constexpr int kStepThreadsPhased = 256;
 constexpr long long kBarrierSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
@@ -124,6 +127,7 @@ __device__ __forceinline__ float4 ldq(const float *col, int64_t q) {
 
 // acc[c] += sum over quads q0..q0+nq-1 of V(q, c) . y(q), c < ncols (shared FP32 partials);
 // y is global (ys == nullptr: read yg from quad q0) or a shared tile
+template <int kStepWarps>
 __device__ void tile_project(const float *V, int64_t ldv, int ncols, const float *yg, const float4 *ys, int64_t q0,
                              int nq, float *acc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -153,6 +157,7 @@ __device__ void tile_project(const float *V, int64_t ldv, int ncols, const float
 // part[cs][ql] = sum over chunks cc = cs, cs + ncs, ... (ncs = min(chunks, warps)) of
 // sum_{c in cc} hs[c] V(q0 + ql, c): warp w takes chunk slot w % ncs of the quad groups
 // w / ncs, w / ncs + gpr, ... (gpr = warps / ncs groups side by side)
+template <int kStepWarps>
 __device__ void tile_combine(const float *V, int64_t ldv, int ncols, const float *hs, int64_t q0, int nq, int qt,
                              float4 *part) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -184,6 +189,7 @@ __device__ void tile_combine(const float *V, int64_t ldv, int ncols, const float
 }
 
 // z - (part[0][ql] + part[1][ql] + ...), slots in a fixed order
+template <int kStepWarps>
 __device__ __forceinline__ float4 sub_parts(float4 z, const float4 *part, int ncols, int qt, int ql) {
     const int nch = (ncols + 7) >> 3, ncs = nch < kStepWarps ? nch : kStepWarps;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -197,10 +203,12 @@ __device__ __forceinline__ float4 sub_parts(float4 z, const float4 *part, int nc
     return make_float4(z.x - s.x, z.y - s.y, z.z - s.z, z.w - s.w);
 }
 
-__global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, int64_t ldv, int j, float *z,
+template <int NT>
+__global__ void __launch_bounds__(NT) lanczos_step_kernel(float *V, int64_t ldv, int j, float *z,
                                                                     double *hbuf, int hstride, double *alpha,
                                                                     double *beta, int m_max, int qt, unsigned *bar,
                                                                     int *err, int phase) {
+    constexpr int kStepWarps = NT / 32;
     // phase < 0: the whole step in one cooperative launch, passes separated by grid
     // barriers; phase 0..2: that pass alone (ordinary launches, the kernel boundary
     // is the barrier)
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, in
         for (int c = threadIdx.x; c < 8 * nch; c += blockDim.x) acc[c] = 0.f;
         __syncthreads();
         for (int64_t q0 = qb0; q0 < qb1; q0 += qt)
-            tile_project(V, ldv, ncols, z, nullptr, q0, (int)(qb1 - q0 < qt ? qb1 - q0 : qt), acc);
+            tile_project<kStepWarps>(V, ldv, ncols, z, nullptr, q0, (int)(qb1 - q0 < qt ? qb1 - q0 : qt), acc);
         __syncthreads();
         for (int c = threadIdx.x; c < ncols; c += blockDim.x) atomicAdd(h0 + c, (double)acc[c]);
     }
@@ -240,16 +248,16 @@ __global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, in
         for (int64_t q0 = qb0; q0 < qb1; q0 += qt) {
             const int nq = (int)(qb1 - q0 < qt ? qb1 - q0 : qt);
             __syncthreads();
-            tile_combine(V, ldv, ncols, hs, q0, nq, qt, part);
+            tile_combine<kStepWarps>(V, ldv, ncols, hs, q0, nq, qt, part);
             __syncthreads();
             for (int ql = threadIdx.x; ql < nq; ql += blockDim.x) {
-                const float4 zp = sub_parts(ldq(z, q0 + ql), part, ncols, qt, ql);
+                const float4 zp = sub_parts<kStepWarps>(ldq(z, q0 + ql), part, ncols, qt, ql);
                 zs[ql] = zp;
                 reinterpret_cast<float4 *>(z)[q0 + ql] = zp;
                 ss = fmaf(zp.x, zp.x, fmaf(zp.y, zp.y, fmaf(zp.z, zp.z, fmaf(zp.w, zp.w, ss))));
             }
             __syncthreads();
-            tile_project(V, ldv, ncols, nullptr, zs, q0, nq, acc);
+            tile_project<kStepWarps>(V, ldv, ncols, nullptr, zs, q0, nq, acc);
         }
         ss = dm_warp_sum(ss);
         if (lane == 0) red[warp] = ss;
@@ -281,11 +289,11 @@ __global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, in
     for (int64_t q0 = qb0; q0 < qb1; q0 += qt) {
         const int nq = (int)(qb1 - q0 < qt ? qb1 - q0 : qt);
         __syncthreads();
-        tile_combine(V, ldv, ncols, hs, q0, nq, qt, part);
+        tile_combine<kStepWarps>(V, ldv, ncols, hs, q0, nq, qt, part);
         __syncthreads();
         if (vn)
             for (int ql = threadIdx.x; ql < nq; ql += blockDim.x) {
-                const float4 zpp = sub_parts(ldq(z, q0 + ql), part, ncols, qt, ql);
+                const float4 zpp = sub_parts<kStepWarps>(ldq(z, q0 + ql), part, ncols, qt, ql);
                 reinterpret_cast<float4 *>(vn)[q0 + ql] = make_float4(zpp.x * inv, zpp.y * inv, zpp.z * inv, zpp.w * inv);
             }
     }
@@ -300,16 +308,16 @@ __global__ void __launch_bounds__(kStepThreads) lanczos_step_kernel(float *V, in
     }
 }
 
-size_t step_smem_bytes(int m_max, int qt) {
+size_t step_smem_bytes(int m_max, int qt, int warps) {
     const int nchmax = (m_max + 1 + 7) >> 3;
-    return sizeof(float4) * ((size_t)kStepWarps * qt + qt) + sizeof(float) * 16 * (size_t)nchmax;
+    return sizeof(float4) * ((size_t)warps * qt + qt) + sizeof(float) * 16 * (size_t)nchmax;
 }
 
-int step_tile_quads(int m_max) {
+int step_tile_quads(int m_max, int warps, int qt_max) {
     // 256 quads (1024 rows) per tile while the shared arrays stay under ~100 KB (the
     // coefficient arrays grow with m_max)
-    int qt = 256;
-    while (qt > 32 && step_smem_bytes(m_max, qt) > 100 * 1024) qt >>= 1;
+    int qt = qt_max;
+    while (qt > 32 && step_smem_bytes(m_max, qt, warps) > 100 * 1024) qt >>= 1;
     return qt;
 }
 
@@ -732,25 +740,31 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) 
         if ((e = cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (size_t)hstride, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(Lz.bar, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     }
-    const int qt = step_tile_quads(Lz.m_max);
-    const size_t shm = step_smem_bytes(Lz.m_max, qt);
-    if ((e = dm_allow_smem((const void *)lanczos_step_kernel, shm)) != cudaSuccess) return e;
+    // phased (shared device): 256-thread blocks, two per SM, 512-row tiles; cooperative:
+    // 512-thread blocks, one per SM, 1024-row tiles
+    const int nt = phased ? kStepThreadsPhased : kStepThreadsCoop;
+    const void *kern = phased ? (const void *)lanczos_step_kernel<kStepThreadsPhased>
+                              : (const void *)lanczos_step_kernel<kStepThreadsCoop>;
+    const int qt = step_tile_quads(Lz.m_max, nt / 32, phased ? 128 : 256);
+    const size_t shm = step_smem_bytes(Lz.m_max, qt, nt / 32);
+    if ((e = dm_allow_smem(kern, shm)) != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     int grid = 0;
     {
-        // co-resident grid for this shared-memory size (at most two blocks per SM)
+        // co-resident grid for this block size and shared-memory size
         static std::mutex mu;
         static std::map<std::pair<int, size_t>, int> grids;
         std::lock_guard<std::mutex> lk(mu);
-        int &g = grids[std::make_pair(dev, shm)];
+        int &g = grids[std::make_pair(dev * 2 + (phased ? 1 : 0), shm)];
         if (g == 0) {
             int sms = 0, per_sm = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_step_kernel, kStepThreads, shm);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, shm);
             if (e != cudaSuccess) return e;
             if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-            g = sms;  // one block per SM
+            const int want = phased ? 2 : 1;
+            g = sms * (per_sm < want ? per_sm : want);
         }
         grid = g;
     }
@@ -758,8 +772,8 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) 
     int64_t ldv = Lz.ldv;
     if (phased) {
         for (int ph = 0; ph < 3; ++ph) {
-            lanczos_step_kernel<<<grid, kStepThreads, shm, st>>>(Lz.V, ldv, jj, Lz.z, Lz.h, hs, Lz.alpha, Lz.beta, mm,
-                                                                 q, Lz.bar, Lz.err, ph);
+            lanczos_step_kernel<kStepThreadsPhased><<<grid, kStepThreadsPhased, shm, st>>>(
+                Lz.V, ldv, jj, Lz.z, Lz.h, hs, Lz.alpha, Lz.beta, mm, q, Lz.bar, Lz.err, ph);
             dm_count_launches(1);
         }
         return cudaGetLastError();
@@ -783,8 +797,7 @@ cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st) 
         e = cudaStreamWaitEvent(st, g_coop_last, 0);
         if (e != cudaSuccess) return e;
     }
-    e = cudaLaunchCooperativeKernel((const void *)lanczos_step_kernel, dim3(grid), dim3(kStepThreads), args, shm,
-                                    st);
+    e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kStepThreadsCoop), args, shm, st);
     dm_count_launches(1);
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(mine, st);
