@@ -160,20 +160,22 @@ __device__ __forceinline__ void level_nodes(int g, int ls, int lv, int *first, i
 // copies.
 __global__ void __launch_bounds__(512) tree_image_kernel(const __grid_constant__ DmHmat H, float *img,
                                                          const int *img_off) {
-    const int ls = H.tree_ls, L = H.L, c = blockIdx.x;
+    const int ls = H.tree_ls, L = H.L, c = blockIdx.x;  // image c; blockIdx.y: a share of its nodes
     const int nnodes = (2 << L) - 1, ninternal = (1 << L) - 1;
     float *out = img + img_off[c];
     int4 *lay = reinterpret_cast<int4 *>(out);
     int *rk = reinterpret_cast<int *>(lay + nnodes);
     int2 *own = reinterpret_cast<int2 *>(rk + ((nnodes + 3) & ~3));
-    for (int n = threadIdx.x; n < nnodes; n += blockDim.x) {
-        lay[n] = H.tlay[n];
-        rk[n] = H.ranks[n];
-        own[n] = H.town[n];
-    }
-    // a warp per owned node (the nodes' copies are independent, so the warps overlap their
-    // global-memory latency instead of walking the nodes one after another)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (blockIdx.y == 0)
+        for (int n = threadIdx.x; n < nnodes; n += blockDim.x) {
+            lay[n] = H.tlay[n];
+            rk[n] = H.ranks[n];
+            own[n] = H.town[n];
+        }
+    // a warp per owned node, the warps of all gridDim.y blocks of this image taking the owned
+    // nodes in turn (the copies are independent: their global-memory latencies overlap)
+    const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5) * (int)gridDim.y;
+    const int warp = (int)blockIdx.y * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
     int mine = 0;  // owned nodes seen so far: the warp takes every nw-th
     for (int n = 0; n < ninternal; ++n) {
         if (tree_owner(n, ls) != c) continue;
@@ -503,7 +505,7 @@ cudaError_t launch_ex(void (*kern)(KArgs...), unsigned grid, unsigned block, siz
 
 cudaError_t dm_tree_image(const DmHmat &H, cudaStream_t st) {
     if (!H.tree_ok) return cudaSuccess;
-    tree_image_kernel<<<1 << H.tree_ls, 512, 0, st>>>(H, H.timg, H.timg_off);
+    tree_image_kernel<<<dim3(1u << H.tree_ls, 8u), 512, 0, st>>>(H, H.timg, H.timg_off);
     dm_count_launches(1);
     return cudaGetLastError();
 }

@@ -668,7 +668,8 @@ __global__ void __launch_bounds__(256) transpose_leaf_kernel(DmHmat H, float *__
     const int ldt = H.ldt;
     const float *Pn = H.P + (size_t)node * H.max_rank * H.ldp;
     float *out = PT + (size_t)leaf * H.leaf_max * ldt;
-    for (int i0 = 0; i0 < (int)sz; i0 += kTrPts) {
+    // blockIdx.y picks the CTA's slices (one each when the grid covers the leaf)
+    for (int i0 = (int)blockIdx.y * kTrPts; i0 < (int)sz; i0 += (int)gridDim.y * kTrPts) {
         const int np = (int)sz - i0 < kTrPts ? (int)sz - i0 : kTrPts;
         __syncthreads();
         for (int e = threadIdx.x; e < ldt * kTrPts; e += blockDim.x) {
@@ -814,7 +815,8 @@ cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cud
 
 cudaError_t dm_transpose_leaf_bases(const DmHmat &H, float *PT, cudaStream_t st) {
     if (H.ldt > kTrMaxT) return cudaErrorInvalidValue;
-    transpose_leaf_kernel<<<1u << H.L, 256, 0, st>>>(H, PT);
+    const dim3 grid(1u << H.L, (unsigned)((H.leaf_max + kTrPts - 1) / kTrPts));
+    transpose_leaf_kernel<<<grid, 256, 0, st>>>(H, PT);
     dm_count_launches(1);
     return cudaGetLastError();
 }
