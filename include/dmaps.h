@@ -98,7 +98,9 @@ void dm_config_default(dm_config *cfg);
  * pairs drawn with cfg->seed). alpha is the density exponent of Algorithm 1,
  * step 2 (the paper uses alpha = 1). Computes the degree vectors q, dg and the
  * scaling s exactly (O(N^2) kernel evaluations, FP32 exp, FP64 sums).
- * cfg may be NULL (defaults). Errors: DM_EINVAL if N < 2, d < 1, alpha < 0 or
+ * cfg may be NULL (defaults). points is copied before the call returns; the degree
+ * passes may still be running on the handle's stream then (every later call on the
+ * handle is ordered after them). Errors: DM_EINVAL if N < 2, d < 1, alpha < 0 or
  * a pointer is NULL; DM_ENOMEM; DM_ECUDA. */
 int dm_create(const float *points, int64_t N, int32_t d, double eps, double alpha,
               const dm_config *cfg, dm_handle *out);

@@ -856,6 +856,9 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
         DM_CUDA(cudaEventRecord(h->cr_a, h->stream));
         DM_CHECK(h->alloc(&h->X, (size_t)N * d, G_BASE));
         DM_CUDA(cudaMemcpyAsync(h->X, points, sizeof(float) * (size_t)N * d, cudaMemcpyDefault, h->stream));
+        // the caller may reuse `points` once dm_create returns: wait for this copy (only)
+        DM_CUDA(cudaEventRecord(h->ev_pre, h->stream));
+        DM_CUDA(cudaEventSynchronize(h->ev_pre));
         if (eps <= 0.0) {
             const int64_t npairs = N * (N - 1) / 2;
             const int64_t m = npairs <= ((int64_t)1 << 20) ? npairs : ((int64_t)1 << 20);
