@@ -141,6 +141,8 @@ struct dm_ctx {
     float *what = nullptr, *uhat = nullptr, *ynear = nullptr, *PT = nullptr;
     unsigned *cnt = nullptr;
     int ldt = 4;
+    int64_t *pt_off = nullptr;  // per leaf: offset and row stride of its point-major basis
+    int *pt_ld = nullptr;
     int4 *tlay = nullptr;
     int2 *town = nullptr;
     float *timg = nullptr;
@@ -269,6 +271,8 @@ struct dm_ctx {
         H.P = P;
         H.PT = PT;
         H.ldt = ldt;
+        H.pt_off = pt_off;
+        H.pt_ld = pt_ld;
         H.B = B;
         H.Knear = Knear;
         H.Xs = Xp;
@@ -469,7 +473,25 @@ int finish_structure(dm_ctx *h) {
     for (int node = 1; node < nnodes; ++node) rank_hi = rk[node] > rank_hi ? rk[node] : rank_hi;
     h->rank_hi = rank_hi;
     h->ldt = (int)round_up(rank_hi, 4);
-    DM_CHECK(h->alloc(&h->PT, (size_t)nleaves * h->leaf_max * h->ldt, G_STRUCT));
+    // point-major leaf bases, each leaf's rows at its own rank's stride (rounded up to 4):
+    // the S2N reads then touch only the basis, not the padding to the largest leaf rank
+    {
+        std::vector<int64_t> off(nleaves);
+        std::vector<int> ld(nleaves);
+        int64_t tot = 0;
+        for (int lf = 0; lf < nleaves; ++lf) {
+            const int r = rk[nleaves - 1 + lf];
+            ld[lf] = r > 4 ? (int)round_up(r, 4) : 4;
+            off[lf] = tot;
+            tot += (int64_t)h->leaf_max * ld[lf];
+        }
+        DM_CHECK(h->alloc(&h->PT, (size_t)tot, G_STRUCT));
+        DM_CHECK(h->alloc(&h->pt_off, (size_t)nleaves, G_STRUCT));
+        DM_CHECK(h->alloc(&h->pt_ld, (size_t)nleaves, G_STRUCT));
+        // pageable sources: each copy returns once its source is staged
+        DM_CUDA(cudaMemcpyAsync(h->pt_off, off.data(), sizeof(int64_t) * nleaves, cudaMemcpyHostToDevice, h->stream));
+        DM_CUDA(cudaMemcpyAsync(h->pt_ld, ld.data(), sizeof(int) * nleaves, cudaMemcpyHostToDevice, h->stream));
+    }
     DM_CHECK(h->alloc(&h->herr, 1, G_STRUCT));
     DM_CUDA(cudaMemsetAsync(h->herr, 0, sizeof(int), h->stream));
     {

@@ -147,8 +147,11 @@ struct DmHmat {
     const int32_t *ranks;  // per node
     const int32_t *skel;   // per node, max_rank positions
     const float *P;        // per node slot max_rank x ldp, row-major
-    const float *PT;       // per leaf slot leaf_max x ldt: P_leaf transposed (point-major), zero padded
-    int ldt;               // rank_hi rounded up to 4
+    const float *PT;       // per leaf: P_leaf transposed (point-major), leaf_max rows of pt_ld[leaf] floats
+                           // from PT + pt_off[leaf], zero past the leaf's rank
+    int ldt;               // rank_hi rounded up to 4 (the largest pt_ld)
+    const int64_t *pt_off; // per leaf: offset of its PT rows (floats)
+    const int *pt_ld;      // per leaf: row stride of its PT rows, its rank rounded up to 4 (>= 4)
     const float *B;        // per internal node slot max_rank x max_rank: K(S_l, S_r), row-major s_l x s_r
     const float *Knear;    // per leaf slot leaf_max x ldk (cached mode)
     const float *Xs;       // points in position order, scaled by sqrt(log2(e)/eps), N x d (on-the-fly mode)
@@ -170,6 +173,11 @@ struct DmHmat {
     const int *timg_off;   // 2^tree_ls + 1 offsets (floats, multiples of 4) of the images in timg
     int *err;              // set when a bounded wait of the H-matvec gives up
 };
+
+// row i of leaf `leaf`'s point-major basis (pt_ld[leaf] floats, 16-byte aligned)
+__device__ __forceinline__ const float *dm_pt_row(const DmHmat &H, int leaf, int i) {
+    return H.PT + H.pt_off[leaf] + (size_t)i * H.pt_ld[leaf];
+}
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions in each .cu; all enqueue on `st` and return the

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_s2n_out_kernel(const __grid_c
         float acc[kColTile];
 #pragma unroll
         for (int c = 0; c < kColTile; ++c) acc[c] = 0.f;
-        const float *pt = H.PT + ((size_t)a * H.leaf_max + i) * H.ldt;
+        const float *pt = dm_pt_row(H, a, i);
         for (int t = 0; t < s; ++t) {
             const float p = __ldg(pt + t);
             const float4 *u4 = reinterpret_cast<const float4 *>(sm + t * kColTile);

@@ -409,9 +409,9 @@ __global__ void __launch_bounds__(kDownThreads) down_kernel(DmHmat H, float *__r
         node = child;
         s = sc;
     }
-    // leaf S2N: y_i = y_near_i + PT[i, :] . t, PT rows zero padded to ldt (>= rank, multiple of 4)
-    const float4 *PT = reinterpret_cast<const float4 *>(H.PT + (size_t)leaf * H.leaf_max * H.ldt);
-    const int q4 = H.ldt >> 2;
+    // leaf S2N: y_i = y_near_i + PT[i, :] . t, PT rows zero padded to pt_ld (>= rank, multiple of 4)
+    const float4 *PT = reinterpret_cast<const float4 *>(dm_pt_row(H, leaf, 0));
+    const int q4 = H.pt_ld[leaf] >> 2;
     const float4 *t4 = reinterpret_cast<const float4 *>(ta);
     for (int i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) {
         const float4 *row = PT + (size_t)i * q4;

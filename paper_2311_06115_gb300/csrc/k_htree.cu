@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kNearThreads, 6) near_cached_kernel(const __gr
         const int i = q.r0 + li;
         float a0 = res[li], a1 = 0.f;
         if (far) {
-            const float4 *prow = reinterpret_cast<const float4 *>(H.PT + ((size_t)q.leaf * H.leaf_max + i) * H.ldt);
+            const float4 *prow = reinterpret_cast<const float4 *>(dm_pt_row(H, q.leaf, i));
             const int t4 = (sr + 3) >> 2;  // PT rows are zero beyond the rank
             for (int v = 0; v < t4; ++v) {
                 const float4 p = __ldg(prow + v);
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kNearThreads) near_otf_kernel(const __grid_con
         const int node = (1 << H.L) - 1 + q.leaf;
         const int sr = __ldg(H.ranks + node);
         const float *u = H.uhat + (size_t)node * H.max_rank;
-        const float *prow = H.PT + ((size_t)q.leaf * H.leaf_max + i) * H.ldt;
+        const float *prow = dm_pt_row(H, q.leaf, i);
         for (int j = 0; j < sr; ++j) acc = fmaf(__ldg(prow + j), __ldcg(u + j), acc);
     }
     if (permuted) y[q.st + i] = acc;

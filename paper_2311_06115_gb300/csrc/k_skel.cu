@@ -665,9 +665,9 @@ __global__ void __launch_bounds__(256) transpose_leaf_kernel(DmHmat H, float *__
     int64_t st, sz;
     dm_node_range(H.N, node, &st, &sz);
     const int s = H.ranks[node];
-    const int ldt = H.ldt;
+    const int ldt = H.pt_ld[leaf];  // this leaf's row stride (its rank rounded up to 4)
     const float *Pn = H.P + (size_t)node * H.max_rank * H.ldp;
-    float *out = PT + (size_t)leaf * H.leaf_max * ldt;
+    float *out = PT + H.pt_off[leaf];
     // blockIdx.y picks the CTA's slices (one each when the grid covers the leaf)
     for (int i0 = (int)blockIdx.y * kTrPts; i0 < (int)sz; i0 += (int)gridDim.y * kTrPts) {
         const int np = (int)sz - i0 < kTrPts ? (int)sz - i0 : kTrPts;
