@@ -682,7 +682,11 @@ int ensure_lanczos(dm_ctx *h) {
     DM_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), h->stream));
     DM_CHECK(h->alloc(&h->evecs, (size_t)kmax * h->N, G_LANCZOS));
     // zero the whole basis once: padding rows beyond N must read as zero
-    DM_CUDA(cudaMemsetAsync(L.V, 0, sizeof(float) * (size_t)(L.m_max + 1) * L.ldv, h->stream));
+    // only the padding rows N..ldv-1 of each basis column are read before being written
+    // (the step kernel works on 16-byte row quads up to ldv): zero those, not the whole basis
+    if (L.ldv > h->N)
+        DM_CUDA(cudaMemset2DAsync(L.V + h->N, sizeof(float) * (size_t)L.ldv, 0,
+                                  sizeof(float) * (size_t)(L.ldv - h->N), (size_t)(L.m_max + 1), h->stream));
     DM_CUDA(cudaMemsetAsync(L.z, 0, sizeof(float) * (size_t)L.ldv, h->stream));
     h->lz_ready = true;
     return DM_OK;
