@@ -52,46 +52,71 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_n2s_kernel(DmHmat H, const 
     int64_t st, sz;
     dm_node_range(H.N, node, &st, &sz);
     const int m = (int)sz, m4 = (m + 3) & ~3;
+    const float *P = H.P + (size_t)node * H.max_rank * H.ldp;
+    float *out = H.what + (size_t)node * H.max_rank;
+    // warp per pair of rows; each lane issues all 16-byte loads of both rows before the sums.
+    // The first pair's loads go out before x is staged (they do not depend on it), so the
+    // basis rows and x arrive in one round trip.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c4 = m4 >> 2;  // float4 per row (<= 128 for leaves of up to 512 points)
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto load_pair = [&](int t, float4 (&ka)[4], float4 (&kb)[4], int base) {
+        const bool two = t + 1 < s;
+        const float4 *ra = reinterpret_cast<const float4 *>(P + (size_t)t * H.ldp);
+        const float4 *rb = reinterpret_cast<const float4 *>(P + (size_t)(two ? t + 1 : t) * H.ldp);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = base + lane + 32 * u;
+            ka[u] = q < c4 ? __ldg(ra + q) : zero;
+            kb[u] = (two && q < c4) ? __ldg(rb + q) : zero;
+        }
+    };
+    const int t0 = row0 + 2 * warp;
+    float4 ka0[4], kb0[4];
+    if (t0 < s) load_pair(t0, ka0, kb0, 0);
     for (int j = threadIdx.x; j < m4; j += blockDim.x) {
         float v = 0.f;
         if (j < m) v = permuted ? x[st + j] : x[H.perm[st + j]];
         sx[j] = v;
     }
     __syncthreads();
-    const float *P = H.P + (size_t)node * H.max_rank * H.ldp;
-    float *out = H.what + (size_t)node * H.max_rank;
-    // warp per pair of rows; each lane issues all 16-byte loads of both rows before the sums
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int c4 = m4 >> 2;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 *v4 = reinterpret_cast<const float4 *>(sx);
-    for (int t = row0 + 2 * warp; t < s; t += 2 * nw * (int)gridDim.y) {
-        const bool two = t + 1 < s;
-        const float4 *ra = reinterpret_cast<const float4 *>(P + (size_t)t * H.ldp);
-        const float4 *rb = reinterpret_cast<const float4 *>(P + (size_t)(two ? t + 1 : t) * H.ldp);
-        float acc_a = 0.f, acc_b = 0.f;
-        for (int base = 0; base < c4; base += 128) {
-            float4 ka[4], kb[4];
+    auto finish_pair = [&](int t, const float4 (&ka)[4], const float4 (&kb)[4], int base, float &acc_a,
+                           float &acc_b) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = base + lane + 32 * u;
-                ka[u] = q < c4 ? __ldg(ra + q) : zero;
-                kb[u] = (two && q < c4) ? __ldg(rb + q) : zero;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = base + lane + 32 * u;
-                const float4 xv = q < c4 ? v4[q] : zero;
-                acc_a = fmaf(ka[u].x, xv.x, fmaf(ka[u].y, xv.y, fmaf(ka[u].z, xv.z, fmaf(ka[u].w, xv.w, acc_a))));
-                acc_b = fmaf(kb[u].x, xv.x, fmaf(kb[u].y, xv.y, fmaf(kb[u].z, xv.z, fmaf(kb[u].w, xv.w, acc_b))));
-            }
+        for (int u = 0; u < 4; ++u) {
+            const int q = base + lane + 32 * u;
+            const float4 xv = q < c4 ? v4[q] : zero;
+            acc_a = fmaf(ka[u].x, xv.x, fmaf(ka[u].y, xv.y, fmaf(ka[u].z, xv.z, fmaf(ka[u].w, xv.w, acc_a))));
+            acc_b = fmaf(kb[u].x, xv.x, fmaf(kb[u].y, xv.y, fmaf(kb[u].z, xv.z, fmaf(kb[u].w, xv.w, acc_b))));
         }
+    };
+    auto store_pair = [&](int t, float acc_a, float acc_b) {
         acc_a = dm_warp_sum(acc_a);
         acc_b = dm_warp_sum(acc_b);
         if (lane == 0) {
             out[t] = acc_a;
-            if (two) out[t + 1] = acc_b;
+            if (t + 1 < s) out[t + 1] = acc_b;
         }
+    };
+    if (t0 < s) {  // the first pair: its first 128 float4 per row were loaded before the staging
+        float acc_a = 0.f, acc_b = 0.f;
+        finish_pair(t0, ka0, kb0, 0, acc_a, acc_b);
+        for (int base = 128; base < c4; base += 128) {  // rows longer than 512 floats
+            float4 ka[4], kb[4];
+            load_pair(t0, ka, kb, base);
+            finish_pair(t0, ka, kb, base, acc_a, acc_b);
+        }
+        store_pair(t0, acc_a, acc_b);
+    }
+    for (int t = t0 + 2 * nw * (int)gridDim.y; t < s; t += 2 * nw * (int)gridDim.y) {
+        float acc_a = 0.f, acc_b = 0.f;
+        for (int base = 0; base < c4; base += 128) {
+            float4 ka[4], kb[4];
+            load_pair(t, ka, kb, base);
+            finish_pair(t, ka, kb, base, acc_a, acc_b);
+        }
+        store_pair(t, acc_a, acc_b);
     }
 }
 
