@@ -56,7 +56,7 @@ def parse():
                    help="requests in the timed serving run (after warm-up); 0 skips it")
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
     p.add_argument("--serve-slots", type=int, default=8)
-    p.add_argument("--serve-dims", default="3,64", help="point dimensions in the request mix")
+    p.add_argument("--serve-dims", default="3,64,784", help="point dimensions in the request mix")
     return p.parse_args()
 
 
@@ -119,7 +119,8 @@ class ClockSampler:
 # ------------------------------------------------------------------ serving: Poisson arrivals of mixed requests
 
 SERVE_MIX = ("N log-uniform in [2000, 100000], d from {dims} (s-curve for d=3, 8-component Gaussian mixture "
-             "for d=64), k uniform in [5, 32], tol from {{1e-4, 1e-5}}, leaf 512, rank 128, eigenvectors returned")
+             "for d=64, MNIST-shaped for d=784), k uniform in [5, 32], tol from {{1e-4, 1e-5}}, leaf 512, rank 128, "
+             "eigenvectors returned")
 
 
 def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: int = 100, seed: int = 7,
@@ -136,8 +137,12 @@ def serve_run(dm, n_req: int, rate: float, slots: int, dims: list[int], warm: in
     g = np.random.default_rng(seed)
     base = {}
     for d in dims:
-        base[d] = synth.as_f32(synth.s_curve(200_000, seed=11) if d == 3 else
-                               synth.gaussian_mixture(200_000, d=d, seed=11))
+        if d == 3:
+            base[d] = synth.as_f32(synth.s_curve(200_000, seed=11))
+        elif d == 784:
+            base[d] = synth.as_f32(synth.mnist_like(200_000, seed=11))
+        else:
+            base[d] = synth.as_f32(synth.gaussian_mixture(200_000, d=d, seed=11))
     total = warm + n_req
     Ns = np.exp(g.uniform(np.log(2000), np.log(100_000), size=total)).astype(np.int64)
     ds = g.choice(dims, size=total)
