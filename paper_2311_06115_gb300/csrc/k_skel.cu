@@ -62,30 +62,39 @@ constexpr int kSkelMaxCand = 512;  // candidates per node (leaf points or two ch
 constexpr int kSkelMaxF4 = 5;      // float4 rows per lane in the column passes: r <= 640
 
 // ---- kernel entries of a block for d > 3, tiled over the coordinates ------------------
-// E[r][c] = s_row s_col 2^-|xs_row - xs_col|^2 for up to 32 rows (one CTA) and up to 512
+// E[r][c] = s_row s_col 2^-|xs_row - xs_col|^2 for up to 32 rows (one CTA) and up to 32 QN
 // columns. Both point sets are staged through shared memory 32 coordinates at a time; each
-// thread owns 4 rows x 16 columns (columns g + 32 q) of squared distances in registers.
+// thread owns 4 rows x QN columns (columns g + 32 q) of squared distances in registers,
+// summed over the coordinates in order exactly as kentry does.
 // Work item `mode`: 0 = the sampled block K(R, C) of node (2^level - 1 + blockIdx.x), rows
 // drawn exactly as in skel_level_kernel, into its A slot; 1 = the leaf block K(I_a, I_a) of
-// leaf blockIdx.x into its Knear slot (zero padded).
+// leaf blockIdx.x into its Knear slot (zero padded); 2 = the sibling block
+// B_p = K(S_l, S_r) of internal node p = blockIdx.x (rows the left child's skeleton, columns
+// the right child's), row-major s_l x s_r at B + p max_rank^2.
 constexpr int kFillRows = 32;
 constexpr int kFillK = 32;
 
+template <int QN>
 __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode, float *__restrict__ Knear,
                                                            int leaf_max, int ldk) {
+    constexpr int kCols = 32 * QN;
     extern __shared__ float fsm[];
     float *xr = fsm;                                  // kFillRows x (kFillK + 1)
-    float *xc = xr + kFillRows * (kFillK + 1);         // kSkelMaxCand x (kFillK + 1)
-    int *rowpos = reinterpret_cast<int *>(xc + kSkelMaxCand * (kFillK + 1));  // kFillRows
-    int *colpos = rowpos + kFillRows;                 // kSkelMaxCand
+    float *xc = xr + kFillRows * (kFillK + 1);         // kCols x (kFillK + 1)
+    int *rowpos = reinterpret_cast<int *>(xc + kCols * (kFillK + 1));  // kFillRows
+    int *colpos = rowpos + kFillRows;                 // kCols
     __shared__ int s_c, s_r;
     const int tid = threadIdx.x;
-    const int node = mode == 0 ? (1 << a.level) - 1 + (int)blockIdx.x : (1 << a.L) - 1 + (int)blockIdx.x;
+    const int node = mode == 0 ? (1 << a.level) - 1 + (int)blockIdx.x
+                     : mode == 1 ? (1 << a.L) - 1 + (int)blockIdx.x : (int)blockIdx.x;
     int64_t st, sz;
     dm_node_range(a.N, node, &st, &sz);
     const int t0 = blockIdx.y * kFillRows;
     if (tid == 0) {
-        if (mode == 0) {
+        if (mode == 2) {
+            s_r = a.ranks[2 * node + 1];
+            s_c = a.ranks[2 * node + 2];
+        } else if (mode == 0) {
             const int64_t off = a.N - sz;
             const int rtarget = 2 * a.max_rank + 10;
             s_r = (int)(off <= rtarget ? off : rtarget);
@@ -97,13 +106,15 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
     }
     __syncthreads();
     const int r = s_r, c = s_c;
-    if (t0 >= r && !(mode == 1 && t0 < leaf_max)) return;
+    if (c > kCols || (t0 >= r && !(mode == 1 && t0 < leaf_max))) return;  // the host sizes QN to the columns
     // row and column positions
     if (tid < kFillRows) {
         const int t = t0 + tid;
         int pos = -1;
         if (t < r) {
-            if (mode == 0) {
+            if (mode == 2) {
+                pos = a.skel[(int64_t)(2 * node + 1) * a.max_rank + t];
+            } else if (mode == 0) {
                 const int64_t off = a.N - sz;
                 const int rtarget = 2 * a.max_rank + 10;
                 const uint64_t key = dm_stream_key(a.seed, DM_TAG_ROWS, (uint64_t)node);
@@ -117,7 +128,8 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
     }
     for (int j = tid; j < c; j += blockDim.x) {
         int pos;
-        if (mode == 1 || a.level == a.L) pos = (int)(st + j);
+        if (mode == 2) pos = a.skel[(int64_t)(2 * node + 2) * a.max_rank + j];
+        else if (mode == 1 || a.level == a.L) pos = (int)(st + j);
         else {
             const int l = 2 * node + 1, rr = 2 * node + 2, sl = a.ranks[l];
             pos = j < sl ? a.skel[(int64_t)l * a.max_rank + j] : a.skel[(int64_t)rr * a.max_rank + (j - sl)];
@@ -126,11 +138,11 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
     }
     __syncthreads();
     const int rg = tid & 7, cg = tid >> 3;  // rows 4 rg .. 4 rg + 3; columns cg + 32 q
-    float acc[4][16];
+    float acc[4][QN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[i][q] = 0.f;
+        for (int q = 0; q < QN; ++q) acc[i][q] = 0.f;
     const int d = a.d;
     for (int k0 = 0; k0 < d; k0 += kFillK) {
         __syncthreads();
@@ -150,7 +162,7 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
 #pragma unroll
             for (int i = 0; i < 4; ++i) xv[i] = xr[(4 * rg + i) * (kFillK + 1) + k];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < QN; ++q) {
                 const float cv = xc[(cg + 32 * q) * (kFillK + 1) + k];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -161,6 +173,21 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
         }
     }
     // entries, written with zero padding
+    if (mode == 2) {
+        float *Bn = Knear + (size_t)blockIdx.x * a.max_rank * a.max_rank;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int t = t0 + 4 * rg + i;
+            if (t >= r) continue;
+            const float si = a.sp[rowpos[4 * rg + i]];
+#pragma unroll
+            for (int q = 0; q < QN; ++q) {
+                const int j = cg + 32 * q;
+                if (j < c) Bn[(size_t)t * c + j] = si * a.sp[colpos[j]] * dm_ex2(-acc[i][q]);
+            }
+        }
+        return;
+    }
     if (mode == 0) {
         // column-major: the thread's four consecutive rows of column j are one 16-byte store;
         // rows from r up to the next multiple of four are written as zeros
@@ -171,7 +198,7 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
             for (int i = 0; i < 4; ++i) si[i] = rowpos[4 * rg + i] >= 0 ? a.sp[rowpos[4 * rg + i]] : 0.f;
             float *slot = a.A + (size_t)blockIdx.x * a.cmax * a.ldr;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < QN; ++q) {
                 const int j = cg + 32 * q;
                 if (j >= c) continue;
                 const float sj = a.sp[colpos[j]];
@@ -191,7 +218,7 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
         float *out = Knear + ((size_t)blockIdx.x * leaf_max + t) * ldk;
         const float si = pos >= 0 ? a.sp[pos] : 0.f;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < QN; ++q) {
             const int j = cg + 32 * q;
             if (j < ldk) out[j] = (pos >= 0 && j < c) ? si * a.sp[colpos[j]] * dm_ex2(-acc[i][q]) : 0.f;
         }
@@ -696,9 +723,32 @@ __global__ void permute_points_kernel(const float *__restrict__ Xs, const float 
 
 }  // namespace
 
-size_t dm_fill_smem_bytes() {
-    return sizeof(float) * (size_t)(kFillRows + kSkelMaxCand) * (kFillK + 1) + sizeof(int) * (kFillRows + kSkelMaxCand);
+namespace {
+
+size_t fill_smem_bytes(int qn) {
+    return sizeof(float) * (size_t)(kFillRows + 32 * qn) * (kFillK + 1) + sizeof(int) * (size_t)(kFillRows + 32 * qn);
 }
+
+template <int QN>
+cudaError_t launch_fill_qn(dim3 grid, const SkelArgs &a, int mode, float *out, int leaf_max, int ldk, cudaStream_t st) {
+    const size_t sm = fill_smem_bytes(QN);
+    cudaError_t e = dm_allow_smem((const void *)fill_entries_kernel<QN>, sm);
+    if (e != cudaSuccess) return e;
+    fill_entries_kernel<QN><<<grid, 256, sm, st>>>(a, mode, out, leaf_max, ldk);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+// the entry fill with the fewest column groups per thread that covers `cols` columns
+cudaError_t launch_fill(int cols, dim3 grid, const SkelArgs &a, int mode, float *out, int leaf_max, int ldk,
+                        cudaStream_t st) {
+    if (cols <= 128) return launch_fill_qn<4>(grid, a, mode, out, leaf_max, ldk, st);
+    if (cols <= 256) return launch_fill_qn<8>(grid, a, mode, out, leaf_max, ldk, st);
+    if (cols <= kSkelMaxCand) return launch_fill_qn<16>(grid, a, mode, out, leaf_max, ldk, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
 
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
     const size_t ldr = (size_t)((rmax + 3) & ~3);
@@ -762,16 +812,13 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     size_t smem_leaf = half > (size_t)reserved + fa.sharedSizeBytes ? (half - reserved - fa.sharedSizeBytes) & ~(size_t)15 : 0;
     if (smem_leaf > smem_int) smem_leaf = smem_int;
     if (smem_leaf < (size_t)a.smem_base) smem_leaf = smem;
-    const size_t fsmem = dm_fill_smem_bytes();
-    if (a.prefilled && (e = dm_allow_smem((const void *)fill_entries_kernel, fsmem)) != cudaSuccess) return e;
     for (int lvl = L; lvl >= 1; --lvl) {
         a.level = lvl;
         if (a.prefilled) {
+            // rows: at most 2 max_rank + 10 sampled; columns: the candidates, at most cmax
             const int rt = 2 * max_rank + 10;
-            fill_entries_kernel<<<dim3(1u << lvl, (unsigned)((rt + kFillRows - 1) / kFillRows)), 256, fsmem, st>>>(
-                a, 0, nullptr, 0, 0);
-            dm_count_launches(1);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            const dim3 grid(1u << lvl, (unsigned)((rt + kFillRows - 1) / kFillRows));
+            if ((e = launch_fill(cmax, grid, a, 0, nullptr, 0, 0, st)) != cudaSuccess) return e;
         }
         // internal levels (few candidates per node, at most one CTA per SM) take the whole
         // shared memory, which holds the sampled block and Q
@@ -787,26 +834,32 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
 }
 
 cudaError_t dm_pack(const DmHmat &H, float *Knear, float *B, bool pack_near, cudaStream_t st) {
-    if (pack_near && H.d > 3 && H.leaf_max <= kSkelMaxCand) {
-        SkelArgs a{};
-        a.Xp = H.Xs;
-        a.sp = H.sp;
-        a.N = H.N;
-        a.d = H.d;
-        a.L = H.L;
-        const size_t fsmem = dm_fill_smem_bytes();
-        cudaError_t e = dm_allow_smem((const void *)fill_entries_kernel, fsmem);
-        if (e != cudaSuccess) return e;
-        dim3 grid(1u << H.L, (unsigned)((H.leaf_max + kFillRows - 1) / kFillRows));
-        fill_entries_kernel<<<grid, 256, fsmem, st>>>(a, 1, Knear, H.leaf_max, H.ldk);
-        dm_count_launches(1);
+    // d > 3: the coordinate-tiled entry fill (near blocks when the leaf fits one CTA's columns,
+    // and the sibling blocks); d <= 3: the direct kernels below
+    SkelArgs a{};
+    a.Xp = H.Xs;
+    a.sp = H.sp;
+    a.N = H.N;
+    a.d = H.d;
+    a.L = H.L;
+    a.max_rank = H.max_rank;
+    a.ranks = const_cast<int32_t *>(H.ranks);  // read only
+    a.skel = const_cast<int32_t *>(H.skel);
+    const int near_cols = H.ldk > H.leaf_max ? H.ldk : H.leaf_max;
+    cudaError_t e = cudaSuccess;
+    if (pack_near && H.d > 3 && near_cols <= kSkelMaxCand) {
+        const dim3 grid(1u << H.L, (unsigned)((H.leaf_max + kFillRows - 1) / kFillRows));
+        if ((e = launch_fill(near_cols, grid, a, 1, Knear, H.leaf_max, H.ldk, st)) != cudaSuccess) return e;
     } else if (pack_near) {
         dim3 grid(1u << H.L, (unsigned)((H.leaf_max + 31) / 32));
         pack_near_kernel<<<grid, 128, sizeof(float4) * (size_t)H.leaf_max, st>>>(H.Xs, H.sp, H.N, H.d, H.L,
                                                                                   H.leaf_max, H.ldk, Knear);
         dm_count_launches(1);
     }
-    if (H.L > 0) {
+    if (H.L > 0 && H.d > 3 && H.max_rank <= kSkelMaxCand) {
+        const dim3 grid((1u << H.L) - 1, (unsigned)((H.max_rank + kFillRows - 1) / kFillRows));
+        if ((e = launch_fill(H.max_rank, grid, a, 2, B, 0, 0, st)) != cudaSuccess) return e;
+    } else if (H.L > 0) {
         pack_far_kernel<<<(1 << H.L) - 1, 256, 0, st>>>(H.Xs, H.sp, H.d, H.ranks, H.skel, H.max_rank, B);
         dm_count_launches(1);
     }
