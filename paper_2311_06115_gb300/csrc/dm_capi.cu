@@ -41,6 +41,30 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+// Pinned host staging for the convergence checks' device-to-host reads, one buffer per
+// host thread, allocated once and reused (an eigensolve runs on one thread at a time):
+// copies to pageable memory would each wait for the stream on their own.
+double *check_staging(size_t count) {
+    struct Buf {
+        double *p = nullptr;
+        size_t n = 0;
+        ~Buf() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    thread_local Buf b;
+    if (b.n < count) {
+        if (b.p) cudaFreeHost(b.p);
+        b.p = nullptr;
+        b.n = 0;
+        void *q = nullptr;
+        if (cudaHostAlloc(&q, sizeof(double) * count, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+        b.p = static_cast<double *>(q);
+        b.n = count;
+    }
+    return b.p;
+}
+
 }  // namespace
 
 cudaError_t dm_allow_smem(const void *kern, size_t bytes) {
@@ -167,6 +191,9 @@ struct dm_ctx {
     cudaEvent_t ev_tree = nullptr;  // end of the tree build on `tstream`
     cudaEvent_t ev_sel = nullptr;   // end of the second median select on `tstream`
     cudaEvent_t cr_a = nullptr, cr_b = nullptr;  // create phase, resolved when stats are read
+    cudaEvent_t ev_chk = nullptr;                 // end of a convergence check's reads
+    cudaEvent_t ev_step = nullptr;                // end of the Lanczos step a check reads
+    cudaStream_t cstream = nullptr;               // convergence checks beside the next step
     bool cr_pending = false;
     // phases timed by event pairs on a stream, resolved when stats are read (no host wait)
     struct Lap {
@@ -215,6 +242,9 @@ struct dm_ctx {
         }
         if (cr_a) cudaEventDestroy(cr_a);
         if (cr_b) cudaEventDestroy(cr_b);
+        if (ev_chk) cudaEventDestroy(ev_chk);
+        if (ev_step) cudaEventDestroy(ev_step);
+        if (cstream) cudaStreamDestroy(cstream);
         if (tstream) cudaStreamDestroy(tstream);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
@@ -805,7 +835,7 @@ void dm_config_default(dm_config *cfg) {
     cfg->near_mode = DM_NEAR_AUTO;
     cfg->m_max = 300;
     cfg->conv_tol = 1e-7;
-    cfg->check_every = 4;
+    cfg->check_every = 2;
     cfg->device = -1;
     cfg->stream = nullptr;
 }
@@ -1140,7 +1170,16 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
     bool converged = false, ritz_current = false;
     std::vector<cudaEvent_t> ev_mv;
     const bool prof = h->cfg.profile != 0;
-    for (int j = 0; j < m_cap; ++j) {
+    double *hk = check_staging((size_t)2 * dm_lanczos_kmax() + 1);
+    if (!hk) return fail(DM_ENOMEM, "pinned host staging for the convergence checks");
+    if (!h->ev_chk) DM_CUDA(cudaEventCreateWithFlags(&h->ev_chk, cudaEventDisableTiming));
+    // on a device of its own, a check runs on a second stream while the next step runs on
+    // the first; on a shared device it runs in order on the handle's stream
+    const bool overlap = h->cfg.shared_device == 0;
+    if (overlap && !h->cstream) DM_CUDA(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    if (overlap && !h->ev_step) DM_CUDA(cudaEventCreateWithFlags(&h->ev_step, cudaEventDisableTiming));
+    // one Lanczos step j: the H-matvec of basis vector j, then its orthogonalisation
+    auto launch_step = [&](int j) -> int {
         if (prof) {
             cudaEvent_t e0, e1;
             DM_CUDA(cudaEventCreate(&e0));
@@ -1152,20 +1191,48 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
         DM_CUDA(dm_hmatvec(H, h->near_mode, Lz.V + (size_t)j * Lz.ldv, Lz.z, true, h->stream));
         if (prof) DM_CUDA(cudaEventRecord(ev_mv.back(), h->stream));
         DM_CUDA(dm_lanczos_orth(Lz, j, h->cfg.shared_device != 0, h->stream));
+        return DM_OK;
+    };
+    int launched = 0;  // steps enqueued so far
+    for (int j = 0; j < m_cap; ++j) {
+        if (j >= launched) {
+            DM_CHECK(launch_step(j));
+            launched = j + 1;
+        }
         m = j + 1;
         ritz_current = false;
         const bool last = (m == m_cap);
         // convergence checks from m = ceil(5k/4) + 5 on (the wanted pairs rarely converge
         // earlier; 32 steps for k = 20 on the 100k s-curve), then every check_every steps: each
-        // check is an FP64 tridiagonal eigensolve plus a host round trip
+        // check is an FP64 tridiagonal eigensolve whose results the host reads back. With a
+        // device of its own, the check runs on the second stream after step j while step
+        // j + 1 is already queued on the first, so neither the check nor the host's wait holds
+        // up the Lanczos steps; when the check converges, that step's results (basis vector
+        // m + 1, alpha_m, beta_m) are never read. At this point the last step queued is j.
         const int first0 = (5 * k + 3) / 4 + 5 > k + 4 ? (5 * k + 3) / 4 + 5 : k + 4;
         const int first = first0 < m_cap ? first0 : m_cap;
         if (m >= first && ((m - first) % h->cfg.check_every == 0 || last)) {
-            DM_CUDA(dm_lanczos_ritz(Lz, m, k, h->cfg.conv_tol, h->stream));
-            DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
-            DM_CUDA(cudaMemcpyAsync(rs.data(), Lz.resid, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
-            DM_CUDA(cudaMemcpyAsync(&bj, Lz.beta + j, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-            DM_CUDA(cudaStreamSynchronize(h->stream));
+            cudaStream_t cs = h->stream;
+            if (overlap) {
+                DM_CUDA(cudaEventRecord(h->ev_step, h->stream));
+                DM_CUDA(cudaStreamWaitEvent(h->cstream, h->ev_step, 0));
+                cs = h->cstream;
+            }
+            DM_CUDA(dm_lanczos_ritz(Lz, m, k, h->cfg.conv_tol, cs));
+            DM_CUDA(cudaMemcpyAsync(hk, Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, cs));
+            DM_CUDA(cudaMemcpyAsync(hk + k, Lz.resid, sizeof(double) * k, cudaMemcpyDeviceToHost, cs));
+            DM_CUDA(cudaMemcpyAsync(hk + 2 * k, Lz.beta + j, sizeof(double), cudaMemcpyDeviceToHost, cs));
+            DM_CUDA(cudaEventRecord(h->ev_chk, cs));
+            if (overlap && !last && launched == j + 1) {
+                DM_CHECK(launch_step(j + 1));
+                launched = j + 2;
+            }
+            DM_CUDA(cudaEventSynchronize(h->ev_chk));
+            for (int i = 0; i < k; ++i) {
+                th[i] = hk[i];
+                rs[i] = hk[k + i];
+            }
+            bj = hk[2 * k];
             ritz_current = true;
             const double scale = std::fabs(th[0]) > 0 ? std::fabs(th[0]) : 1.0;
             bool ok = true;
@@ -1177,6 +1244,8 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {
             }
         }
     }
+    // the vectors below read theta from the last check
+    if (overlap) DM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_chk, 0));
     if (!ritz_current) {
         DM_CUDA(dm_lanczos_ritz(Lz, m, k, h->cfg.conv_tol, h->stream));
         DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));

@@ -364,6 +364,33 @@ __device__ int sturm_count_f32(const float *al, const float *b2, int m, float x)
     return cnt;
 }
 
+// p_m(x), p_{m-1}(x) and p_m'(x) of det(T_i - x I) by the three-term recurrence and its
+// derivative, all four running terms rescaled together by powers of two (ratios are exact)
+__device__ void charpoly(const double *__restrict__ al, const double *__restrict__ b2, int m, double x,
+                         double *p_out, double *pm_out, double *dp_out) {
+    double pm = 1.0, p = al[0] - x, dpm = 0.0, dp = -1.0;
+    for (int i = 1; i < m; ++i) {
+        const double t = al[i] - x;
+        const double pn = fma(-b2[i - 1], pm, t * p);
+        const double dpn = fma(-b2[i - 1], dpm, fma(t, dp, -p));
+        pm = p;
+        dpm = dp;
+        p = pn;
+        dp = dpn;
+        const int e = (int)((__double_as_longlong(fabs(dp) > fabs(p) ? dp : p) >> 52) & 0x7ff);
+        if (e > 1023 + 500 || e < 1023 - 500) {
+            const int sh = 1023 - e;
+            p = scalbn(p, sh);
+            pm = scalbn(pm, sh);
+            dp = scalbn(dp, sh);
+            dpm = scalbn(dpm, sh);
+        }
+    }
+    *p_out = p;
+    *pm_out = pm;
+    *dp_out = dp;
+}
+
 // One block of kRitzThreads per wanted eigenvalue (descending index i): multisection to full
 // FP64 precision with one shift per thread (four warps: all four FP64 units of the SM, seven
 // bits per round), then the residual bound beta_{m-1} |y_m| from
@@ -377,8 +404,8 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
     double *al = sd, *b2 = sd + m;
     float *al32 = reinterpret_cast<float *>(b2 + m), *b232 = al32 + m;
     __shared__ unsigned s_above[kRitzThreads / 32];
-    __shared__ double s_lo, s_hi;
-    __shared__ int s_ok[2];
+    __shared__ double s_lo, s_hi, s_x;
+    __shared__ int s_ok[2], s_newton;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < m; i += blockDim.x) {
         al[i] = alpha[i];
@@ -441,6 +468,38 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
         if (s_ok[0] && s_ok[1] && (double)flo < (double)fhi) {
             lo = (double)flo;
             hi = (double)fhi;
+            // Newton on p_m(x) = det(T - x I) from the middle of the confirmed bracket, kept
+            // inside it (quadratic convergence for an eigenvalue alone in the bracket); the
+            // iterate is taken when two FP64 Sturm counts place the wanted eigenvalue within
+            // 1e-13 ||T|| of it, otherwise the multisection below narrows the bracket
+            if (tid == 0) {
+                s_newton = 0;
+                double x = 0.5 * (lo + hi);
+                for (int it = 0; it < 12; ++it) {
+                    double p, pm, dp;
+                    charpoly(al, b2, m, x, &p, &pm, &dp);
+                    if (dp == 0.0) break;
+                    const double xn = x - p / dp;
+                    if (!(xn >= lo && xn <= hi)) break;
+                    const double stp = fabs(xn - x);
+                    x = xn;
+                    if (stp <= 1e-14 * fabs(x)) {
+                        s_x = x;
+                        s_newton = 1;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_newton) {
+                const double x = s_x, tv = 1e-13 * fmax(fabs(s_lo), fabs(s_hi));
+                if (tid < 2) {
+                    const int c = sturm_count(al, b2, m, tid == 0 ? x - tv : x + tv);
+                    s_ok[tid] = tid == 0 ? (c <= target) : (c > target);
+                }
+                __syncthreads();
+                if (s_ok[0] && s_ok[1]) lo = hi = x;  // the multisection loop ends at once
+            }
         }
     }
     for (int round = 0; round < 16; ++round) {
@@ -465,26 +524,8 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
     }
     const double th = 0.5 * (lo + hi);
     if (tid == 0) {
-        // p and p' of det(T_i - x I) with shared rescaling
-        double pm = 1.0, p = al[0] - th, dpm = 0.0, dp = -1.0;
-        for (int i = 1; i < m; ++i) {
-            const double t = al[i] - th;
-            const double pn = fma(-b2[i - 1], pm, t * p);
-            const double dpn = fma(-b2[i - 1], dpm, fma(t, dp, -p));
-            pm = p;
-            dpm = dp;
-            p = pn;
-            dp = dpn;
-            const int e = (int)((__double_as_longlong(fabs(dp) > fabs(p) ? dp : p) >> 52) & 0x7ff);
-            if (e > 1023 + 500 || e < 1023 - 500) {
-                const int sh = 1023 - e;
-                p = scalbn(p, sh);
-                pm = scalbn(pm, sh);
-                dp = scalbn(dp, sh);
-                dpm = scalbn(dpm, sh);
-            }
-        }
-        // after the loop: p = p_m, pm = p_{m-1}, dp = p_m'
+        double p, pm, dp;  // p_m, p_{m-1}, p_m' at th
+        charpoly(al, b2, m, th, &p, &pm, &dp);
         const double y2 = (dp != 0.0) ? fabs(pm / dp) : 1.0;
         theta[blockIdx.x] = th;
         resid[blockIdx.x] = beta[m - 1] * sqrt(fmin(y2, 1.0));
@@ -493,16 +534,21 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
 
 // Eigenvector of T_m for theta (one warp per vector, serial in lane 0): inverse
 // iteration with an LU factorisation with partial pivoting of T - theta I (three
-// solves), normalised; written as column i of Y (ld = ldy).
+// solves), normalised; written as column i of Y (ld = ldy). The factors and the iterate
+// live in shared memory when they fit (44 m bytes; the chain of dependent accesses is
+// the kernel's whole cost), else in the global workspace (6 m doubles per vector).
 // The workspace is read and written through several pointers carved out of one
 // buffer, so no parameter here is declared __restrict__: with it the optimised
 // build reorders those accesses and returns wrong vectors.
+constexpr int kTvecSmemMaxM = 1024;  // 44 KB of shared memory
+template <bool kShared>
 __global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const double *beta,
                                                   int m, const double *theta, double *Y,
                                                   int ldy, double *work, uint64_t key) {
+    extern __shared__ double tsm[];
     if (threadIdx.x != 0) return;
     const int iv = blockIdx.x;
-    double *dl = work + (size_t)iv * 6 * m;  // sub (L multipliers)
+    double *dl = kShared ? tsm : work + (size_t)iv * 6 * m;  // sub (L multipliers)
     double *dd = dl + m, *du = dd + m, *du2 = du + m, *y = du2 + m;
     int *ip = reinterpret_cast<int *>(y + m);
     const double th = theta[iv];
@@ -568,14 +614,22 @@ __global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const dou
 __global__ void tvec_orth_kernel(int m, int k, const double *theta, double *Y, int ldy,
                                  float *Yf) {
     __shared__ double red[32];
-    __shared__ double th[kKMax];  // Ritz values staged once (the pair loop tests every pair)
+    __shared__ double th[kKMax];  // Ritz values staged once
+    __shared__ unsigned char clus[kKMax * kKMax];  // clus[i][j]: pair (i, j) is in one cluster
     for (int i = threadIdx.x; i < k; i += blockDim.x) th[i] = theta[i];
     __syncthreads();
     double tmax = 0.0;
     for (int i = 0; i < k; ++i) tmax = fmax(tmax, fabs(th[i]));
+    // every pair tested once, in parallel (a serial scan of the pairs waits out the FP64
+    // latency of each test in turn)
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e - i * k;
+        clus[i * kKMax + j] = (j < i && !(fabs(th[i] - th[j]) > 1e-10 * tmax)) ? 1 : 0;
+    }
+    __syncthreads();
     for (int i = 1; i < k; ++i) {
         for (int j = 0; j < i; ++j) {
-            if (fabs(th[i] - th[j]) > 1e-10 * tmax) continue;
+            if (!clus[i * kKMax + j]) continue;
             double part = 0.0;
             for (int t = threadIdx.x; t < m; t += blockDim.x) part += Y[(size_t)i * ldy + t] * Y[(size_t)j * ldy + t];
             part = dm_warp_sum_d(part);
@@ -814,8 +868,12 @@ cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaSt
 }
 
 cudaError_t dm_lanczos_tvecs(DmLanczos &Lz, int m, int k, cudaStream_t st) {
-    tvec_kernel<<<k, 32, 0, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.Y, Lz.m_max, Lz.twork,
-                                  dm_stream_key(0x5eedULL, DM_TAG_V0, 1));
+    const uint64_t key = dm_stream_key(0x5eedULL, DM_TAG_V0, 1);
+    if (m <= kTvecSmemMaxM)
+        tvec_kernel<true><<<k, 32, (sizeof(double) * 5 + sizeof(int)) * (size_t)m, st>>>(
+            Lz.alpha, Lz.beta, m, Lz.theta, Lz.Y, Lz.m_max, Lz.twork, key);
+    else
+        tvec_kernel<false><<<k, 32, 0, st>>>(Lz.alpha, Lz.beta, m, Lz.theta, Lz.Y, Lz.m_max, Lz.twork, key);
     dm_count_launches(1);
     tvec_orth_kernel<<<1, 256, 0, st>>>(m, k, Lz.theta, Lz.Y, Lz.m_max, Lz.Yf);
     dm_count_launches(1);
