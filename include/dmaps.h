@@ -67,7 +67,7 @@ typedef struct dm_config {
     int32_t near_mode;    /* DM_NEAR_* */
     int32_t m_max;        /* Lanczos basis cap (default 300) */
     double conv_tol;      /* Ritz residual bound beta_j |y_j| <= conv_tol * theta_1 (default 1e-7) */
-    int32_t check_every;  /* Lanczos steps between convergence checks, from step ceil(5k/4)+5 on (default 2) */
+    int32_t check_every;  /* Lanczos steps between convergence checks, from step ceil(5k/4)+5 on (default 1) */
     int32_t device;       /* CUDA device ordinal (default: the current device) */
     void *stream;         /* cudaStream_t to run on; NULL = a stream the handle creates */
     dm_alloc_fn alloc;    /* NULL = cudaMalloc */

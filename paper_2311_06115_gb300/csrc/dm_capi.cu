@@ -835,7 +835,7 @@ void dm_config_default(dm_config *cfg) {
     cfg->near_mode = DM_NEAR_AUTO;
     cfg->m_max = 300;
     cfg->conv_tol = 1e-7;
-    cfg->check_every = 2;
+    cfg->check_every = 1;
     cfg->device = -1;
     cfg->stream = nullptr;
 }

@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
     double *al = sd, *b2 = sd + m;
     float *al32 = reinterpret_cast<float *>(b2 + m), *b232 = al32 + m;
     __shared__ unsigned s_above[kRitzThreads / 32];
-    __shared__ double s_lo, s_hi, s_x;
+    __shared__ double s_lo, s_hi, s_x, s_y2;
     __shared__ int s_ok[2], s_newton;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < m; i += blockDim.x) {
@@ -437,28 +437,66 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
     double lo = s_lo, hi = s_hi;
     const int target = m - 1 - (int)blockIdx.x;  // ascending index of the wanted eigenvalue
     constexpr double kDen = (double)(kRitzThreads + 1);
-    // three coarse rounds with FP32 counts (the FP64 pipe is narrow on this part), then two
-    // FP64 counts confirm the bracket; if they do not, the FP64 rounds start from Gershgorin
-    {
-        float flo = (float)lo, fhi = (float)hi;
-        for (int round = 0; round < 3; ++round) {
-            const float x = flo + (fhi - flo) * (float)(tid + 1) / (float)kDen;
-            const int c = sturm_count_f32(al32, b232, m, x);
-            const unsigned above = __ballot_sync(DM_FULL, c > target);
-            if (lane == 0) s_above[warp] = above;
-            __syncthreads();
-            int g = -1;
-            for (int w = 0; w < kRitzThreads / 32 && g < 0; ++w)
-                if (s_above[w]) g = 32 * w + __ffs(s_above[w]) - 1;
-            __syncthreads();
-            auto shift = [&](int t) { return flo + (fhi - flo) * (float)(t + 1) / (float)kDen; };
-            if (g < 0) flo = shift(kRitzThreads - 1);
-            else {
-                const float xh = shift(g);
-                if (g > 0) flo = shift(g - 1);
-                fhi = xh;
+    // three coarse rounds with FP32 counts (the FP64 pipe is narrow on this part)
+    float flo = (float)lo, fhi = (float)hi;
+    for (int round = 0; round < 3; ++round) {
+        const float x = flo + (fhi - flo) * (float)(tid + 1) / (float)kDen;
+        const int c = sturm_count_f32(al32, b232, m, x);
+        const unsigned above = __ballot_sync(DM_FULL, c > target);
+        if (lane == 0) s_above[warp] = above;
+        __syncthreads();
+        int g = -1;
+        for (int w = 0; w < kRitzThreads / 32 && g < 0; ++w)
+            if (s_above[w]) g = 32 * w + __ffs(s_above[w]) - 1;
+        __syncthreads();
+        auto shift = [&](int t) { return flo + (fhi - flo) * (float)(t + 1) / (float)kDen; };
+        if (g < 0) flo = shift(kRitzThreads - 1);
+        else {
+            const float xh = shift(g);
+            if (g > 0) flo = shift(g - 1);
+            fhi = xh;
+        }
+    }
+    // Newton on p_m(x) = det(T - x I) from the middle of the FP32 bracket, kept inside it
+    // (quadratic convergence for an eigenvalue alone in the bracket), stopped after a step
+    // below 1e-9 |x| (the error left, about step^2 / gap, is then far below the tolerance
+    // checked next unless the gap is tiny). The iterate is taken when two FP64 Sturm counts
+    // place the wanted eigenvalue within 1e-13 ||T|| of it; the residual bound uses the
+    // last Newton evaluation. Otherwise two FP64 counts check the FP32 bracket and FP64
+    // multisection rounds narrow it (from the Gershgorin interval if the check fails).
+    if (tid == 0) {
+        s_newton = 0;
+        const double blo = (double)flo, bhi = (double)fhi;
+        double x = 0.5 * (blo + bhi);
+        for (int it = 0; it < 12 && blo < bhi; ++it) {
+            double p, pm, dp;
+            charpoly(al, b2, m, x, &p, &pm, &dp);
+            if (dp == 0.0) break;
+            const double xn = x - p / dp;
+            if (!(xn >= blo && xn <= bhi)) break;
+            const double stp = fabs(xn - x);
+            x = xn;
+            if (stp <= 1e-9 * fabs(x)) {
+                s_x = x;
+                s_y2 = fabs(pm / dp);
+                s_newton = 1;
+                break;
             }
         }
+    }
+    __syncthreads();
+    bool done = false;
+    if (s_newton) {
+        const double x = s_x, tv = 1e-13 * fmax(fabs(s_lo), fabs(s_hi));
+        if (tid < 2) {
+            const int c = sturm_count(al, b2, m, tid == 0 ? x - tv : x + tv);
+            s_ok[tid] = tid == 0 ? (c <= target) : (c > target);
+        }
+        __syncthreads();
+        done = s_ok[0] && s_ok[1];  // uniform
+        __syncthreads();            // every thread has read s_ok before it is reused
+    }
+    if (!done) {
         if (tid < 2) {
             const double x = tid == 0 ? (double)flo : (double)fhi;
             const int c = sturm_count(al, b2, m, x);
@@ -468,65 +506,36 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
         if (s_ok[0] && s_ok[1] && (double)flo < (double)fhi) {
             lo = (double)flo;
             hi = (double)fhi;
-            // Newton on p_m(x) = det(T - x I) from the middle of the confirmed bracket, kept
-            // inside it (quadratic convergence for an eigenvalue alone in the bracket); the
-            // iterate is taken when two FP64 Sturm counts place the wanted eigenvalue within
-            // 1e-13 ||T|| of it, otherwise the multisection below narrows the bracket
-            if (tid == 0) {
-                s_newton = 0;
-                double x = 0.5 * (lo + hi);
-                for (int it = 0; it < 12; ++it) {
-                    double p, pm, dp;
-                    charpoly(al, b2, m, x, &p, &pm, &dp);
-                    if (dp == 0.0) break;
-                    const double xn = x - p / dp;
-                    if (!(xn >= lo && xn <= hi)) break;
-                    const double stp = fabs(xn - x);
-                    x = xn;
-                    if (stp <= 1e-14 * fabs(x)) {
-                        s_x = x;
-                        s_newton = 1;
-                        break;
-                    }
-                }
-            }
+        }
+        for (int round = 0; round < 16; ++round) {
+            if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;  // uniform: every thread holds the same lo, hi
+            const double x = lo + (hi - lo) * (double)(tid + 1) / kDen;
+            const int c = sturm_count(al, b2, m, x);
+            const unsigned above = __ballot_sync(DM_FULL, c > target);  // shifts above the eigenvalue
+            if (lane == 0) s_above[warp] = above;
             __syncthreads();
-            if (s_newton) {
-                const double x = s_x, tv = 1e-13 * fmax(fabs(s_lo), fabs(s_hi));
-                if (tid < 2) {
-                    const int c = sturm_count(al, b2, m, tid == 0 ? x - tv : x + tv);
-                    s_ok[tid] = tid == 0 ? (c <= target) : (c > target);
-                }
-                __syncthreads();
-                if (s_ok[0] && s_ok[1]) lo = hi = x;  // the multisection loop ends at once
+            int g = -1;  // first shift above
+            for (int w = 0; w < kRitzThreads / 32 && g < 0; ++w)
+                if (s_above[w]) g = 32 * w + __ffs(s_above[w]) - 1;
+            __syncthreads();
+            // every thread re-forms the bracketing shifts with the same arithmetic
+            auto shift = [&](int t) { return lo + (hi - lo) * (double)(t + 1) / kDen; };
+            if (g < 0) lo = shift(kRitzThreads - 1);  // all shifts below: eigenvalue in (x_last, hi]
+            else {
+                const double xh = shift(g);
+                if (g > 0) lo = shift(g - 1);
+                hi = xh;
             }
         }
     }
-    for (int round = 0; round < 16; ++round) {
-        if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;  // uniform: every thread holds the same lo, hi
-        const double x = lo + (hi - lo) * (double)(tid + 1) / kDen;
-        const int c = sturm_count(al, b2, m, x);
-        const unsigned above = __ballot_sync(DM_FULL, c > target);  // shifts above the eigenvalue
-        if (lane == 0) s_above[warp] = above;
-        __syncthreads();
-        int g = -1;  // first shift above
-        for (int w = 0; w < kRitzThreads / 32 && g < 0; ++w)
-            if (s_above[w]) g = 32 * w + __ffs(s_above[w]) - 1;
-        __syncthreads();
-        // every thread re-forms the bracketing shifts with the same arithmetic
-        auto shift = [&](int t) { return lo + (hi - lo) * (double)(t + 1) / kDen; };
-        if (g < 0) lo = shift(kRitzThreads - 1);  // all shifts below: eigenvalue in (x_last, hi]
-        else {
-            const double xh = shift(g);
-            if (g > 0) lo = shift(g - 1);
-            hi = xh;
-        }
-    }
-    const double th = 0.5 * (lo + hi);
     if (tid == 0) {
-        double p, pm, dp;  // p_m, p_{m-1}, p_m' at th
-        charpoly(al, b2, m, th, &p, &pm, &dp);
-        const double y2 = (dp != 0.0) ? fabs(pm / dp) : 1.0;
+        const double th = done ? s_x : 0.5 * (lo + hi);
+        double y2 = s_y2;
+        if (!done) {
+            double p, pm, dp;  // p_m, p_{m-1}, p_m' at th
+            charpoly(al, b2, m, th, &p, &pm, &dp);
+            y2 = (dp != 0.0) ? fabs(pm / dp) : 1.0;
+        }
         theta[blockIdx.x] = th;
         resid[blockIdx.x] = beta[m - 1] * sqrt(fmin(y2, 1.0));
     }
