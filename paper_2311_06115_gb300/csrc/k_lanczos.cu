@@ -544,8 +544,9 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
 // Eigenvector of T_m for theta (one warp per vector, serial in lane 0): inverse
 // iteration with an LU factorisation with partial pivoting of T - theta I (three
 // solves), normalised; written as column i of Y (ld = ldy). The factors and the iterate
-// live in shared memory when they fit (44 m bytes; the chain of dependent accesses is
-// the kernel's whole cost), else in the global workspace (6 m doubles per vector).
+// live in shared memory when they fit (44 m bytes), else in the global workspace (6 m
+// doubles per vector). Either way the time is the serial chain of dependent FP64
+// operations (about 67 us at m = 32), not the memory accesses.
 // The workspace is read and written through several pointers carved out of one
 // buffer, so no parameter here is declared __restrict__: with it the optimised
 // build reorders those accesses and returns wrong vectors.

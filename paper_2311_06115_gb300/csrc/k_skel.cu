@@ -667,6 +667,7 @@ __global__ void pack_near_kernel(const float *__restrict__ Xp, const float *__re
 }
 
 // ---- far blocks B_p = K(S_l, S_r) for the children of every internal node, row-major s_l x s_r
+// (d <= 3, where an entry is a few flops; larger d goes through the coordinate-tiled fill)
 __global__ void pack_far_kernel(const float *__restrict__ Xp, const float *__restrict__ sp, int d,
                                 const int32_t *__restrict__ ranks, const int32_t *__restrict__ skel, int max_rank,
                                 float *__restrict__ B) {
