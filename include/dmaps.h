@@ -137,6 +137,19 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
  * the last dm_eigs). Errors: DM_ESTATE if dm_eigs has not run; DM_EINVAL. */
 int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi);
 
+/* Intrinsic dimension d(t) (Algorithm 1, last step) from the eigenvalues of a
+ * dm_eigs call. The paper's inequality is garbled and its delta unspecified; the
+ * reading is Coifman and Lafon's, whose Algorithm 1 restates: with the eigenvalues
+ * indexed from the trivial one, lambda_0 = evals[0] (= 1), d(t) is the largest
+ * l >= 1 with |lambda_l|^t > delta |lambda_1|^t, i.e. the number of non-trivial
+ * diffusion coordinates still above the precision factor delta after t steps.
+ * evals: k host doubles, descending as dm_eigs returns them. t >= 1; 0 < delta < 1.
+ * *d receives d(t) (0 when lambda_1 = 0); *at_k (may be NULL) receives 1 when
+ * d(t) = k - 1, i.e. every eigenvalue given passed and the true d(t) may be larger.
+ * Errors: DM_EINVAL for NULL evals or d, k < 2, t < 1, delta outside (0, 1) or a
+ * NaN eigenvalue. Host computation only; no device work. */
+int dm_intrinsic_dim(const double *evals, int32_t k, int32_t t, double delta, int32_t *d, int32_t *at_k);
+
 /* Leaf-size autotuner (no counterpart in the paper: GOFMM takes max_leaf_node_size from the
  * user). For each of the ncand candidate leaf sizes, compresses the handle's operator with
  * (tol, leaf, max_rank), times the compression and one nrhs = 1 H-matvec (median of 5, CUDA

@@ -16,6 +16,7 @@ in Section 4.1), whose parameters the paper does not give ("parity unpinned").
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import sysconfig
@@ -289,6 +290,24 @@ def lanczos_hmat(X, eps: float, s, H: HStructure, k: int, m_max: int = 300, conv
                                  H.max_rank, H.cmax, H.ranks, H.skel, H.P, k, m_max, conv_tol, v0, ev, V,
                                  C.byref(it))
     return ev, np.ascontiguousarray(V.T), int(it.value), int(st)
+
+
+def intrinsic_dim(evals, t: int, delta: float) -> tuple[int, bool]:
+    """Intrinsic dimension d(t) of Algorithm 1 (last step), in Coifman and Lafon's form
+    (the printed inequality is garbled and delta is not given): eigenvalues indexed from
+    the trivial one, lambda_0 = evals[0]; d(t) = the largest l >= 1 with
+    |lambda_l|^t > delta |lambda_1|^t, tested as t log(|lambda_l| / |lambda_1|) > log(delta)
+    (the same comparison without the range limits of the t-th powers). Also returns
+    whether every eigenvalue given passed (the true d(t) may then be larger)."""
+    lam = [float(v) for v in evals]
+    l1 = abs(lam[1])
+    d = 0
+    if l1 > 0.0:
+        for l in range(1, len(lam)):
+            r = abs(lam[l]) / l1
+            if r > 0.0 and t * math.log(r) > math.log(delta):
+                d = l
+    return d, d == len(lam) - 1
 
 
 def threads() -> int:

@@ -22,7 +22,8 @@ from . import build as _build
 __all__ = [
     "DmError", "DM_OK", "DM_EINVAL", "DM_ENOMEM", "DM_ESTATE", "DM_ENOCONV", "DM_ETIMEOUT", "DM_ECUDA", "DM_EBUSY",
     "DM_NEAR_AUTO", "DM_NEAR_CACHED", "DM_NEAR_ONTHEFLY", "DM_PREC_FP32", "DM_PREC_TF32", "dm_config", "dm_stats", "lib_path", "load",
-    "dm_config_default", "dm_create", "dm_compress", "dm_matvec", "dm_eigs", "dm_coords", "dm_destroy",
+    "dm_config_default", "dm_create", "dm_compress", "dm_matvec", "dm_eigs", "dm_coords", "dm_intrinsic_dim",
+    "dm_destroy",
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
     "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc", "dm_request",
     "dm_result", "dm_serve_config", "dm_request_bytes", "dm_serve_start", "dm_serve_stop", "dm_submit", "dm_poll",
@@ -108,6 +109,7 @@ def load(build_if_missing: bool = True):
         "dm_matvec": (i32, [vp, vp, vp, i32]),
         "dm_eigs": (i32, [vp, i32, vp, vp]),
         "dm_coords": (i32, [vp, i32, i32, vp]),
+        "dm_intrinsic_dim": (i32, [vp, i32, i32, f64, C.POINTER(i32), C.POINTER(i32)]),
         "dm_destroy": (i32, [vp]),
         "dm_status_str": (C.c_char_p, [i32]),
         "dm_last_error": (C.c_char_p, []),
@@ -321,6 +323,15 @@ def dm_coords(h: Handle, k: int, t: int = 1) -> np.ndarray:
     psi = np.empty((k, h.N), dtype=np.float32)
     _check(load().dm_coords(h, int(k), int(t), psi.ctypes.data))
     return psi.T
+
+
+def dm_intrinsic_dim(evals, t: int, delta: float) -> tuple[int, bool]:
+    """dm_intrinsic_dim: (d(t), whether every eigenvalue given passed) for the descending
+    eigenvalues of a dm_eigs call, evals[0] the trivial one."""
+    ev = np.ascontiguousarray(np.asarray(evals, dtype=np.float64))
+    d, at_k = C.c_int32(), C.c_int32()
+    _check(load().dm_intrinsic_dim(ev.ctypes.data, int(ev.size), int(t), float(delta), C.byref(d), C.byref(at_k)))
+    return int(d.value), bool(at_k.value)
 
 
 def dm_tune_leaf(h: Handle, tol: float, max_rank: int, k: int, candidates=(64, 128, 256, 512)):

@@ -1352,6 +1352,27 @@ int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi) {
     return DM_OK;
 }
 
+int dm_intrinsic_dim(const double *evals, int32_t k, int32_t t, double delta, int32_t *d, int32_t *at_k) {
+    if (!evals || !d) return fail(DM_EINVAL, "evals or d is NULL");
+    if (k < 2) return fail(DM_EINVAL, "k must be >= 2 (the trivial eigenvalue and at least one more)");
+    if (t < 1) return fail(DM_EINVAL, "t must be >= 1");
+    if (!(delta > 0.0 && delta < 1.0)) return fail(DM_EINVAL, "delta must be in (0, 1)");
+    for (int l = 0; l < k; ++l)
+        if (std::isnan(evals[l])) return fail(DM_EINVAL, "eigenvalue %d is NaN", l);
+    // |lambda_l|^t > delta |lambda_1|^t, compared as t log(|lambda_l| / |lambda_1|) > log(delta)
+    // so that large t neither underflows nor overflows
+    const double l1 = std::fabs(evals[1]), ld = std::log(delta);
+    int best = 0;
+    if (l1 > 0.0)
+        for (int l = 1; l < k; ++l) {
+            const double r = std::fabs(evals[l]) / l1;
+            if (r > 0.0 && (double)t * std::log(r) > ld) best = l;
+        }
+    *d = best;
+    if (at_k) *at_k = (best == k - 1) ? 1 : 0;
+    return DM_OK;
+}
+
 int dm_get_stats(dm_handle h, dm_stats *st) {
     if (!h || !st) return fail(DM_EINVAL, "NULL argument");
     resolve_create_time(h);

@@ -97,3 +97,25 @@ def test_serving_rejects_bad_requests_and_state():
     with pytest.raises(dm.DmError) as e:
         dm.dm_poll(123456789)
     assert e.value.status == dm.DM_EINVAL
+
+
+def test_intrinsic_dim_matches_oracle():
+    """dm_intrinsic_dim (host computation in the library, no device work) against the
+    oracle's d(t) on random descending spectra, bit for bit; argument errors."""
+    import numpy as np
+
+    import oracle as O
+    import paper_2311_06115_gb300 as dm
+
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        k = int(rng.integers(2, 33))
+        lam = np.concatenate([[1.0], np.sort(rng.uniform(-0.2, 1.0, k - 1))[::-1]])
+        t = int(rng.integers(1, 200))
+        delta = float(rng.uniform(1e-6, 0.999))
+        assert dm.dm_intrinsic_dim(lam, t, delta) == O.intrinsic_dim(lam, t, delta)
+    for bad in [([1.0], 1, 0.5), ([1.0, 0.5], 0, 0.5), ([1.0, 0.5], 1, 0.0), ([1.0, 0.5], 1, 1.0),
+                ([1.0, float("nan")], 1, 0.5)]:
+        with pytest.raises(dm.DmError) as e:
+            dm.dm_intrinsic_dim(*bad)
+        assert e.value.status == dm.DM_EINVAL

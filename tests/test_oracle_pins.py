@@ -361,3 +361,50 @@ def test_golden_scurve_2048_regression():
     ev, _, _, st = O.lanczos_S(X, eps, s, 10, conv_tol=1e-10)
     assert st == 0
     np.testing.assert_allclose(ev, g["evals_top10"], rtol=1e-10)
+
+
+# ------------------------------------------------------------------ intrinsic dimension (Algorithm 1, last step)
+
+def test_intrinsic_dim_worked_example():
+    """lambda = 1, 0.8, 0.6, 0.3, 0.1 and delta = 0.2, powers worked out by hand:
+    t = 1: threshold 0.16 passes 0.8, 0.6, 0.3 -> 3; t = 2: 0.128 passes 0.64, 0.36 -> 2;
+    t = 5: 0.065536 passes 0.32768, 0.07776 -> 2; t = 6: 0.0524288 passes 0.262144 only -> 1."""
+    lam = [1.0, 0.8, 0.6, 0.3, 0.1]
+    assert O.intrinsic_dim(lam, 1, 0.2) == (3, False)
+    assert O.intrinsic_dim(lam, 2, 0.2) == (2, False)
+    assert O.intrinsic_dim(lam, 5, 0.2) == (2, False)
+    assert O.intrinsic_dim(lam, 6, 0.2) == (1, False)
+    assert O.intrinsic_dim(lam, 1, 0.01) == (4, True)  # all pass: more pairs needed
+    assert O.intrinsic_dim([1.0, 0.0, 0.0], 1, 0.5) == (0, False)
+
+
+def test_intrinsic_dim_bruteforce_exact_powers():
+    """Against the definition evaluated in exact rational arithmetic (|lambda_l|^t vs
+    delta |lambda_1|^t), on random spectra away from exact ties."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(7)
+    checked = 0
+    for _ in range(400):
+        k = int(rng.integers(2, 12))
+        lam = [Fraction(1)] + sorted((Fraction(int(v), 1000) for v in rng.integers(-999, 1000, k - 1)),
+                                     reverse=True)
+        t = int(rng.integers(1, 9))
+        delta = Fraction(int(rng.integers(1, 100)), 100)
+        thr = delta * abs(lam[1]) ** t
+        if any(abs(abs(x) ** t - thr) <= Fraction(1, 10**9) * max(thr, Fraction(1, 10**30)) for x in lam[1:]):
+            continue
+        want = max([l for l in range(1, k) if abs(lam[l]) ** t > thr], default=0)
+        got, at_k = O.intrinsic_dim([float(x) for x in lam], t, float(delta))
+        assert got == want, (lam, t, delta)
+        assert at_k == (want == k - 1)
+        checked += 1
+    assert checked > 300
+
+
+def test_intrinsic_dim_non_increasing_in_t():
+    rng = np.random.default_rng(8)
+    for _ in range(50):
+        lam = np.concatenate([[1.0], np.sort(rng.random(15))[::-1]])
+        ds = [O.intrinsic_dim(lam, t, 0.1)[0] for t in range(1, 40)]
+        assert all(a >= b for a, b in zip(ds, ds[1:]))
