@@ -95,6 +95,9 @@ void run_job(Job *j, cudaStream_t stream) {
     cfg.free = slot_free;
     cfg.alloc_user = stream;
     cfg.shared_device = 1;  // other slots run concurrently: no cooperative launches
+    // on a shared device a convergence check runs in order on the slot's stream and the
+    // slot's thread waits for it: check every second step, not every step
+    cfg.check_every = 2;
     cfg.block_size = j->req.block_size;
     dm_handle h = nullptr;
     const int k = j->req.k;
