@@ -6,8 +6,8 @@
  * Approximations using Hierarchical Decomposition" (arXiv 2311.06115):
  *
  *   W_ij  = exp(-||x_i - x_j||^2 / eps)                 (Eq. W, eps = sigma^2)
- *   q     = W 1,  W^a_ij = W_ij / (q_i^a q_j^a)          (Algorithm 1, steps 1-2)
- *   P     = Dg^-1 W^a,  dg = W^a 1                       (Algorithm 1, step 3)
+ *   q     = W 1,  W^a_ij = W_ij / (q_i^a q_j^a)          (Algorithm 1: similarity, density normalisation)
+ *   P     = Dg^-1 W^a,  dg = W^a 1                       (Algorithm 1: Markov normalisation)
  *   S     = Dg^-1/2 W^a Dg^-1/2 = diag(s) W diag(s),  s = q^-a dg^-1/2
  *
  * S is the symmetric conjugate of P (same eigenvalues; right eigenvectors of P
@@ -132,12 +132,13 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs);
 int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
 
 /* Diffusion coordinates of the last dm_eigs: psi_i = theta_i^t Dg^-1/2 phi_i
- * (Algorithm 1, steps 4-5: the eigenvalues of P^t are theta^t and its right
+ * (Algorithm 1: t-step random walk and eigendecomposition; the eigenvalues of
+ * P^t are theta^t and its right
  * eigenvectors Dg^-1/2 phi). psi: N x k column-major float32 (k <= the k of
  * the last dm_eigs). Errors: DM_ESTATE if dm_eigs has not run; DM_EINVAL. */
 int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi);
 
-/* Intrinsic dimension d(t) (Algorithm 1, last step) from the eigenvalues of a
+/* Intrinsic dimension d(t) (Algorithm 1, its lower dimension) from the eigenvalues of a
  * dm_eigs call. The paper's inequality is garbled and its delta unspecified; the
  * reading is Coifman and Lafon's, whose Algorithm 1 restates: with the eigenvalues
  * indexed from the trivial one, lambda_0 = evals[0] (= 1), d(t) is the largest

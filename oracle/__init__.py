@@ -128,7 +128,7 @@ def kernel_W(X, eps: float) -> np.ndarray:
 
 
 def degrees(X, eps: float, alpha: float = 1.0):
-    """(q, dg, s): q = W 1, dg = W^alpha 1, s = q^-alpha dg^-1/2 (Algorithm 1, steps 1-3)."""
+    """(q, dg, s): q = W 1, dg = W^alpha 1, s = q^-alpha dg^-1/2 (Algorithm 1: similarity matrix and normalisations)."""
     X = _pts(X)
     n = X.shape[0]
     q, dg, s = (np.empty(n, dtype=np.float64) for _ in range(3))
@@ -293,7 +293,7 @@ def lanczos_hmat(X, eps: float, s, H: HStructure, k: int, m_max: int = 300, conv
 
 
 def intrinsic_dim(evals, t: int, delta: float) -> tuple[int, bool]:
-    """Intrinsic dimension d(t) of Algorithm 1 (last step), in Coifman and Lafon's form
+    """Intrinsic dimension d(t) of Algorithm 1 (its lower dimension), in Coifman and Lafon's form
     (the printed inequality is garbled and delta is not given): eigenvalues indexed from
     the trivial one, lambda_0 = evals[0]; d(t) = the largest l >= 1 with
     |lambda_l|^t > delta |lambda_1|^t, tested as t log(|lambda_l| / |lambda_1|) > log(delta)

@@ -10,14 +10,15 @@
  *
  * What each part follows:
  *   - Gaussian kernel W_ij = exp(-|x_i - x_j|^2 / eps), eps = sigma^2   (Eq. W, Section 2.1)
- *   - q = W 1, W^a_ij = W_ij / (q_i^a q_j^a), dg = W^a 1, P = Dg^-1 W^a  (Algorithm 1, steps 1-3;
- *     the row-sum denominator of step 3 is read as the Coifman-Lafon one)
+ *   - q = W 1, W^a_ij = W_ij / (q_i^a q_j^a), dg = W^a 1, P = Dg^-1 W^a  (Algorithm 1: similarity
+ *     matrix and normalisations; the Markov denominator is read as the Coifman-Lafon row
+ *     sum of W^a, which makes P row-stochastic)
  *   - S = Dg^-1/2 W^a Dg^-1/2 = diag(s) W diag(s), s = q^-a dg^-1/2: the symmetric
  *     conjugate of P with the same eigenvalues (Section 2.1, SPD requirement of Section 1.2)
  *   - H-matrix form K~ = D + UV (Eq. 2.18) with a balanced binary partition tree and
  *     nested interpolative-decomposition bases (the GOFMM form the paper uses; the paper
- *     gives only its parameters, Section 4.2 footnote) -- tree rule and ID stopping rule
- *     are readings listed in the design doc
+ *     gives only its parameters, Section 4.2 footnote) -- the tree rule and the ID stopping
+ *     rule are readings of this implementation (the paper does not describe them)
  *   - relative-error target ||K~ - K|| / ||K|| <= eps_tol                 (Eq. 1.1)
  *   - Krylov basis and projection by Gram-Schmidt                        (Algorithm 2,
  *     Eq. arnoldi; symmetric case: Lanczos, Section 2.3.1), done twice per step
@@ -122,7 +123,7 @@ void or_kernel_W(const float *X, int64_t N, int32_t d, double eps, double *W) {
         for (int64_t j = 0; j < N; ++j) W[i * N + j] = or_w(X, d, eps, i, j);
 }
 
-/* Algorithm 1, steps 1-3: q_i = sum_j W_ij; dg_i = q_i^-a sum_j W_ij q_j^-a
+/* Algorithm 1, similarity matrix and normalisations: q_i = sum_j W_ij; dg_i = q_i^-a sum_j W_ij q_j^-a
  * (the row sum of W^a); s_i = q_i^-a dg_i^-1/2 so that S = diag(s) W diag(s). */
 void or_degrees(const float *X, int64_t N, int32_t d, double eps, double alpha,
                 double *q, double *dg, double *s) {

@@ -23,7 +23,7 @@ uint64_t or_splitmix64_next(uint64_t *state);
 uint64_t or_stream_key(uint64_t seed, uint32_t tag, uint64_t id);
 uint64_t or_rng(uint64_t key, uint64_t ctr);
 
-/* ---- kernel, bandwidth, degrees (Eq. W and Algorithm 1, steps 1-3) ---- */
+/* ---- kernel, bandwidth, degrees (Eq. W and Algorithm 1: similarity matrix and normalisations) ---- */
 double or_sqdist(const float *X, int32_t d, int64_t i, int64_t j);
 double or_median_sqdist(const float *X, int64_t N, int32_t d, uint64_t seed);
 void or_kernel_W(const float *X, int64_t N, int32_t d, double eps, double *W);

@@ -3,7 +3,7 @@
 //
 // Phases (all device work on the handle's stream):
 //   dm_create   : bandwidth (optional), pre-scaled points, degrees q, dg, scaling s
-//                 (Algorithm 1, steps 1-3)
+//                 (Algorithm 1: similarity matrix and normalisations)
 //   dm_compress : partition tree -> skeletons (interpolative decompositions) ->
 //                 packed near and far blocks (Eq. 2.18)
 //   dm_matvec   : y = K~ x (the LinearOperator of Section 3.3)

@@ -1,6 +1,6 @@
 // k_degrees.cu -- kernel scale, degree vectors and the exact on-the-fly matvec.
 //
-// Algorithm 1, steps 1-3 of the paper: W_ij = exp(-|x_i - x_j|^2 / eps) (Eq. W),
+// Algorithm 1 of the paper (similarity matrix and normalisations): W_ij = exp(-|x_i - x_j|^2 / eps) (Eq. W),
 // q = W 1, W^a = Q^-a W Q^-a, dg = W^a 1, and the symmetric scaling
 // s = q^-a dg^-1/2 so that S = diag(s) W diag(s) is the symmetric conjugate of
 // the Markov matrix P = Dg^-1 W^a. The two O(N^2) passes run on the FP32

@@ -1,7 +1,7 @@
 // k_degtc.cu -- degree passes for high-dimensional points on the tensor cores.
 //
 // A degree pass is out_i = sum_j W_ij w_j with W_ij = exp(-|x_i - x_j|^2 / eps) (Eq. W and
-// Algorithm 1, steps 1-3). For large d the work is the Gram matrix G = X X^T: with
+// Algorithm 1: similarity matrix and normalisations). For large d the work is the Gram matrix G = X X^T: with
 // n_i = |x_i|^2, |x_i - x_j|^2 = n_i + n_j - 2 G_ij. Here G is a tcgen05 GEMM with FP32
 // accumulation in TMEM (128 x 256 tiles), and the epilogue turns each accumulator row into
 // 2^(2 k G_ij - a_i - a_j) w_j (a_i = k n_i, k = log2(e) sigma^2 / eps) summed over the

@@ -98,7 +98,7 @@ def test_markov_rows_sum_to_one(alpha):
     W = O.kernel_W(X, eps)
     q, dg, s = O.degrees(X, eps, alpha)
     Wa = W / np.outer(q ** alpha, q ** alpha)
-    P = Wa / dg[:, None]  # Algorithm 1 step 3 with the row-sum denominator
+    P = Wa / dg[:, None]  # Algorithm 1's Markov normalisation with the row-sum denominator
     np.testing.assert_allclose(P.sum(axis=1), 1.0, rtol=0, atol=1e-13)
     # S = diag(s) W diag(s) is the symmetric conjugate Dg^1/2 P Dg^-1/2
     S = s[:, None] * W * s[None, :]
@@ -363,7 +363,7 @@ def test_golden_scurve_2048_regression():
     np.testing.assert_allclose(ev, g["evals_top10"], rtol=1e-10)
 
 
-# ------------------------------------------------------------------ intrinsic dimension (Algorithm 1, last step)
+# ------------------------------------------------------------------ intrinsic dimension d(t) (Algorithm 1)
 
 def test_intrinsic_dim_worked_example():
     """lambda = 1, 0.8, 0.6, 0.3, 0.1 and delta = 0.2, powers worked out by hand:
