@@ -408,3 +408,23 @@ def test_intrinsic_dim_non_increasing_in_t():
         lam = np.concatenate([[1.0], np.sort(rng.random(15))[::-1]])
         ds = [O.intrinsic_dim(lam, t, 0.1)[0] for t in range(1, 40)]
         assert all(a >= b for a, b in zip(ds, ds[1:]))
+
+
+def test_residual_bound_identity_of_the_ritz_check():
+    """The convergence check's residual bound uses |y_m|^2 = |p_{m-1}(theta) / p_m'(theta)|
+    (y the unit eigenvector of T_m for theta, p_i the characteristic polynomials of the
+    leading i x i submatrices): checked against numpy's eigh on random tridiagonals."""
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        m = int(rng.integers(5, 40))
+        a, b = rng.uniform(-1, 1, m), rng.uniform(0.05, 1, m - 1)
+        T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+        w, Y = np.linalg.eigh(T)
+        for i in range(m):
+            th = w[i]
+            pm, p, dpm, dp = 1.0, a[0] - th, 0.0, -1.0
+            for r in range(1, m):
+                t = a[r] - th
+                pm, p, dpm, dp = p, t * p - b[r - 1] ** 2 * pm, dp, t * dp - p - b[r - 1] ** 2 * dpm
+            # p_{m-1} = pm, p_m' = dp
+            assert abs(abs(pm / dp) - Y[m - 1, i] ** 2) < 1e-8 * max(1.0, Y[m - 1, i] ** 2)
