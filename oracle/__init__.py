@@ -292,6 +292,15 @@ def lanczos_hmat(X, eps: float, s, H: HStructure, k: int, m_max: int = 300, conv
     return ev, np.ascontiguousarray(V.T), int(it.value), int(st)
 
 
+def diffusion_coords(evals, phi, dg, t: int = 1) -> np.ndarray:
+    """Diffusion coordinates after t steps of the walk (Algorithm 1, P^t and its
+    eigendecomposition): P = Dg^-1 W^alpha = Dg^-1/2 S Dg^1/2, so P's right eigenvectors
+    are Dg^-1/2 phi for eigenvectors phi of S, with P^t's eigenvalues theta^t;
+    psi_i = theta_i^t Dg^-1/2 phi_i. phi: (N, k); returns (N, k) float64."""
+    ev = np.asarray(evals, dtype=np.float64)
+    return (ev ** t)[None, :] * np.asarray(phi, dtype=np.float64) / np.sqrt(np.asarray(dg, dtype=np.float64))[:, None]
+
+
 def intrinsic_dim(evals, t: int, delta: float) -> tuple[int, bool]:
     """Intrinsic dimension d(t) of Algorithm 1 (its lower dimension), in Coifman and Lafon's form
     (the printed inequality is garbled and delta is not given): eigenvalues indexed from

@@ -428,3 +428,22 @@ def test_residual_bound_identity_of_the_ritz_check():
                 pm, p, dpm, dp = p, t * p - b[r - 1] ** 2 * pm, dp, t * dp - p - b[r - 1] ** 2 * dpm
             # p_{m-1} = pm, p_m' = dp
             assert abs(abs(pm / dp) - Y[m - 1, i] ** 2) < 1e-8 * max(1.0, Y[m - 1, i] ** 2)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5])
+def test_diffusion_coords_are_right_eigenvectors_of_P(alpha):
+    """psi_i(t) = theta_i^t Dg^-1/2 phi_i: P psi_i(0) = theta_i psi_i(0) for the dense
+    Markov matrix P = Dg^-1 W^alpha built from the kernel, and P^t psi_i(0) = psi_i(t)."""
+    X = synth.as_f32(synth.s_curve(300, seed=5))
+    eps = O.median_sqdist(X)
+    q, dg, s = O.degrees(X, eps, alpha)
+    W = O.kernel_W(X, eps)
+    Wa = W / np.outer(q ** alpha, q ** alpha)
+    P = Wa / dg[:, None]
+    S = s[:, None] * W * s[None, :]
+    ev, V = O.jacobi(S)
+    k = 6
+    psi0 = O.diffusion_coords(ev[:k], V[:, :k], dg, 0)
+    np.testing.assert_allclose(P @ psi0, psi0 * ev[:k][None, :], rtol=0, atol=1e-10)
+    psi3 = O.diffusion_coords(ev[:k], V[:, :k], dg, 3)
+    np.testing.assert_allclose(np.linalg.matrix_power(P, 3) @ psi0, psi3, rtol=0, atol=1e-10)
