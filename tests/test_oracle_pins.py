@@ -447,3 +447,48 @@ def test_diffusion_coords_are_right_eigenvectors_of_P(alpha):
     np.testing.assert_allclose(P @ psi0, psi0 * ev[:k][None, :], rtol=0, atol=1e-10)
     psi3 = O.diffusion_coords(ev[:k], V[:, :k], dg, 3)
     np.testing.assert_allclose(np.linalg.matrix_power(P, 3) @ psi0, psi3, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4, 1e-6])
+def test_id_pivots_and_rank_match_lapack_pivoted_qr(tol):
+    """The ID's pivot order and its stopping rule (stop at the first pivot whose residual
+    column norm is <= tol x the first pivot's) against LAPACK's column-pivoted QR
+    (scipy.linalg.qr, pivoting=True) of the same sampled block, where every off-node
+    row is sampled (n = 128, leaf 32, max rank 48: at most 106 rows per node)."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    n, leaf, max_rank = 128, 32, 48
+    X, eps, s = _setup(n, 9, leaf)
+    perm, L = O.tree(X, eps, leaf)
+    H = O.skeletonize(X, eps, s, perm, L, tol, max_rank, seed=0)
+    W = O.kernel_W(X, eps)
+    Kp = (s[:, None] * W * s[None, :])[np.ix_(perm, perm)]
+    compared = 0
+    for node in range(1, (1 << (L + 1)) - 1):
+        st, sz = O.node_range(n, node)
+        if int(math.log2(node + 1)) == L:
+            C = np.arange(st, st + sz)
+        else:
+            l, rr = 2 * node + 1, 2 * node + 2
+            C = np.concatenate([H.skel[l * max_rank:l * max_rank + H.ranks[l]],
+                                H.skel[rr * max_rank:rr * max_rank + H.ranks[rr]]])
+        off = np.concatenate([np.arange(0, st), np.arange(st + sz, n)])
+        A = Kp[np.ix_(off, C)]
+        _, R, piv = scipy_linalg.qr(A, pivoting=True, mode="economic")
+        d = np.abs(np.diag(R))
+        kmax = min(max_rank, len(C), len(off))
+        thr = tol * d[0]
+        r_lapack = next((j for j in range(kmax) if d[j] <= thr), kmax)
+        if np.any(np.abs(d[:kmax + 1] - thr) <= 1e-9 * thr):
+            continue  # a residual norm at the threshold within rounding: no sharp answer
+        r = H.ranks[node]
+        assert r == r_lapack, (node, r, r_lapack)
+        J = H.skel[node * max_rank:node * max_rank + r]
+        # pivots agree until two residual norms tie within rounding
+        sharp = r
+        for j in range(r - 1):
+            if abs(d[j] - d[j + 1]) <= 1e-12 * d[0]:
+                sharp = j
+                break
+        np.testing.assert_array_equal(J[:sharp], C[piv[:sharp]])
+        compared += 1
+    assert compared >= 4
