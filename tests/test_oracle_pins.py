@@ -492,3 +492,50 @@ def test_id_pivots_and_rank_match_lapack_pivoted_qr(tol):
         np.testing.assert_array_equal(J[:sharp], C[piv[:sharp]])
         compared += 1
     assert compared >= 4
+
+
+def test_hmatvec_equals_dense_assembly_of_eq_2_18():
+    """At a tolerance where the bases are truncated, the H-matvec equals K~ x for K~
+    assembled densely from Eq. 2.18's parts: D = the leaf diagonal blocks, and for every
+    sibling pair (l, r) the block V_l^T K(J_l, J_r) V_r (and its transpose), where the
+    nested basis is V_leaf = P_leaf and V_node = P_node blockdiag(V_left, V_right)."""
+    n, leaf, max_rank = 600, 40, 24
+    X, eps, s = _setup(n, 13, leaf)
+    H = O.compress(X, eps, s, leaf, 1e-3, max_rank)
+    L, perm = H.L, H.perm
+    W = O.kernel_W(X, eps)
+    Kp = (s[:, None] * W * s[None, :])[np.ix_(perm, perm)]
+    Pn = H.P.reshape(-1, H.max_rank, H.cmax)
+    V = {}
+    for node in range((1 << (L + 1)) - 2, 0, -1):  # children before parents
+        r = H.ranks[node]
+        st, sz = O.node_range(n, node)
+        if int(math.log2(node + 1)) == L:
+            V[node] = Pn[node, :r, :sz]
+        else:
+            l, rr = 2 * node + 1, 2 * node + 2
+            Vl, Vr = V[l], V[rr]
+            blk = np.zeros((Vl.shape[0] + Vr.shape[0], Vl.shape[1] + Vr.shape[1]))
+            blk[:Vl.shape[0], :Vl.shape[1]] = Vl
+            blk[Vl.shape[0]:, Vl.shape[1]:] = Vr
+            V[node] = Pn[node, :r, :Vl.shape[0] + Vr.shape[0]] @ blk
+    Kt = np.zeros((n, n))
+    for leaf_node in range((1 << L) - 1, (1 << (L + 1)) - 1):
+        st, sz = O.node_range(n, leaf_node)
+        Kt[st:st + sz, st:st + sz] = Kp[st:st + sz, st:st + sz]
+    for p in range(0, (1 << L) - 1):
+        l, rr = 2 * p + 1, 2 * p + 2
+        sl, sr = O.node_range(n, l), O.node_range(n, rr)
+        Jl = H.skel[l * H.max_rank:l * H.max_rank + H.ranks[l]]
+        Jr = H.skel[rr * H.max_rank:rr * H.max_rank + H.ranks[rr]]
+        F = V[l].T @ Kp[np.ix_(Jl, Jr)] @ V[rr]
+        Kt[sl[0]:sl[0] + sl[1], sr[0]:sr[0] + sr[1]] = F
+        Kt[sr[0]:sr[0] + sr[1], sl[0]:sl[0] + sl[1]] = F.T
+    Korig = np.empty_like(Kt)
+    Korig[np.ix_(perm, perm)] = Kt
+    x = synth.random_rhs(n, 2, 17)
+    yh = O.hmatvec(X, eps, s, H, x)
+    y = Korig @ x
+    np.testing.assert_allclose(yh, y, rtol=0, atol=1e-12 * np.abs(y).max())
+    # and the truncation really happened: K~ differs from K
+    assert np.abs(Korig - (s[:, None] * W * s[None, :])).max() > 1e-8
