@@ -133,15 +133,15 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
 
 /* Diffusion coordinates of the last dm_eigs: psi_i = theta_i^t Dg^-1/2 phi_i
  * (Algorithm 1: t-step random walk and eigendecomposition; the eigenvalues of
- * P^t are theta^t and its right
- * eigenvectors Dg^-1/2 phi). psi: N x k column-major float32 (k <= the k of
- * the last dm_eigs). Errors: DM_ESTATE if dm_eigs has not run; DM_EINVAL. */
+ * P^t are theta^t and its right eigenvectors Dg^-1/2 phi). psi: N x k
+ * column-major float32 (k <= the k of the last dm_eigs). Errors: DM_ESTATE if
+ * dm_eigs has not run; DM_EINVAL. */
 int dm_coords(dm_handle h, int32_t k, int32_t t, float *psi);
 
 /* Intrinsic dimension d(t) (Algorithm 1, its lower dimension) from the eigenvalues of a
  * dm_eigs call. The paper's inequality is garbled and its delta unspecified; the
- * reading is Coifman and Lafon's, whose Algorithm 1 restates: with the eigenvalues
- * indexed from the trivial one, lambda_0 = evals[0] (= 1), d(t) is the largest
+ * reading is Coifman and Lafon's definition, which the paper's Algorithm 1 restates:
+ * with the eigenvalues indexed from the trivial one, lambda_0 = evals[0] (= 1), d(t) is the largest
  * l >= 1 with |lambda_l|^t > delta |lambda_1|^t, i.e. the number of non-trivial
  * diffusion coordinates still above the precision factor delta after t steps.
  * evals: k host doubles, descending as dm_eigs returns them. t >= 1; 0 < delta < 1.
