@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -36,7 +37,19 @@ WORKLOAD = {"workload": "s-curve N=100000 d=3, eps=median sq. distance, alpha=1,
                         "top-20, nrhs=1", "N": 100_000, "d": 3, "leaf": 512, "rank": 128, "tol": 1e-5, "k": 20}
 METRIC = "top-k diffusion-map eigenpairs/s (N=100k s-curve, k=20)"
 UNIT = "eigenpairs/s"
-CPU_SAMPLE_N = 10_000
+# the oracle's full pipeline at the workload's N takes roughly 10 s on 16 host cores (the
+# O(N^2) degree passes dominate); the reference arm sizes its per-step samples so that all
+# of its steps fit in about two minutes
+ORACLE_FULL_S = 10.0
+REFERENCE_BUDGET_S = 120.0
+
+
+def reference_sample_n(steps: int, warmup: int) -> int:
+    """Points per oracle sample of the reference arm: the full workload when the run fits
+    the budget at full size, else fewer (time grows as n^2 through the degree passes)."""
+    per_step = REFERENCE_BUDGET_S / max(1, steps + warmup)
+    n = int(WORKLOAD["N"] * min(1.0, math.sqrt(per_step / ORACLE_FULL_S)))
+    return max(10_000, n // 1000 * 1000)
 
 
 def parse():
@@ -380,11 +393,9 @@ def mnist_workload_run(dm, stream, reps: int = 2) -> dict:
 
 # ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
 
-def oracle_sample(n: int = CPU_SAMPLE_N) -> dict:
-    """The FP64 oracle's full pipeline on an n-point s-curve of the same workload; phase times
-    scaled to the workload's N (degrees as N^2, the rest as N log N)."""
-    import math
-
+def oracle_sample(n: int = WORKLOAD["N"]) -> dict:
+    """The FP64 oracle's full pipeline on an n-point s-curve of the same workload; when n is
+    below the workload's N, phase times are scaled to it (degrees as N^2, the rest as N log N)."""
     import numpy as np
 
     import oracle as O
@@ -412,10 +423,14 @@ def oracle_sample(n: int = CPU_SAMPLE_N) -> dict:
     nlog = (N * math.log2(N)) / (n * math.log2(n))
     total = t["median"] + t["degrees"] * (N / n) ** 2 + (t["tree"] + t["skeleton"] + t["lanczos"]) * nlog
     sample_s = sum(t.values())
-    return {"value": W["k"] / total, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
-            "sample": (f"full FP64 oracle pipeline on a {n}-point s-curve (same generator and parameters; "
-                       f"{sample_s:.1f} s of CPU time, {it} Lanczos steps), phase times scaled to N={N} "
-                       f"(degrees x (N/n)^2, tree/compression/Lanczos x N log N / n log n)"),
+    if n >= N:
+        desc = (f"full FP64 oracle pipeline on the whole {N}-point workload (same generator and parameters; "
+                f"{sample_s:.1f} s wall on the host cores, {it} Lanczos steps; no extrapolation)")
+    else:
+        desc = (f"full FP64 oracle pipeline on a {n}-point s-curve (same generator and parameters; "
+                f"{sample_s:.1f} s wall on the host cores, {it} Lanczos steps), phase times scaled to N={N} "
+                f"(degrees x (N/n)^2, tree/compression/Lanczos x N log N / n log n)")
+    return {"value": W["k"] / total, "unit": UNIT, "cores": O.threads(), "kind": "oracle", "sample": desc,
             "phases_s": {k: round(v, 4) for k, v in t.items()}, "extrapolated_s": round(total, 2)}
 
 
@@ -426,9 +441,10 @@ def run_reference(args) -> int:
     import oracle
 
     oracle.build()
+    n_sample = reference_sample_n(args.steps, args.warmup)
     runs = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample()
+        r = oracle_sample(n_sample)
         if i >= args.warmup:
             runs.append(r)
     vals = [r["value"] for r in runs]
