@@ -16,6 +16,10 @@ eigenvalues and eigenvectors back to the host inside the timed region).
 
 For N > 1 (torchrun, one rank per GPU) every rank solves its own cloud
 (replicas: the solve has no data-path exchange) and value sums over ranks.
+
+`cpu_baseline` times the FP64 oracle's whole pipeline on the same workload on the
+host cores; `--impl reference` times that pipeline once per step, on fewer points
+(phase times scaled to N) when the steps would not fit in about two minutes.
 """
 from __future__ import annotations
 
