@@ -161,9 +161,14 @@ int dm_intrinsic_dim(const double *evals, int32_t k, int32_t t, double delta, in
 int dm_tune_leaf(dm_handle h, double tol, int32_t max_rank, int32_t k, const int32_t *candidates, int32_t ncand,
                  int32_t *best_leaf, float *cost_ms);
 
-/* Release every device buffer of the handle. */
+/* Release every device buffer, stream and event of the handle, ordered after the work
+ * it has queued (no paper counterpart). The handle must not be used afterwards.
+ * Errors: DM_EINVAL for a NULL handle. */
 int dm_destroy(dm_handle h);
 
+/* Name of a status code ("DM_OK", "DM_EINVAL", ...; "DM_UNKNOWN" otherwise), and the
+ * message of the calling thread's last failure (empty if none). Both strings are
+ * library-owned; the message stays valid until this thread's next failing call. */
 const char *dm_status_str(int status);
 const char *dm_last_error(void);
 
@@ -192,6 +197,8 @@ typedef struct dm_stats {
                                 2 = tensor cores, exact BF16 Gram matrix (8-bit quantised data) */
 } dm_stats;
 
+/* Phase times and structure statistics of the handle's last calls (introspection; no
+ * paper counterpart), copied into the caller's struct. Errors: DM_EINVAL for NULL. */
 int dm_get_stats(dm_handle h, dm_stats *st);
 
 /* Number of CUDA kernels this library has launched in this process (all handles). */
@@ -278,7 +285,8 @@ int dm_degrees_noalloc(const float *points, int64_t N, int32_t d, double eps, do
                        double *q, double *dg, double *s, void *stream);
 
 /* eps in use, and the degree vectors of Algorithm 1 (N doubles each, original
- * order; any pointer may be NULL). */
+ * order, host or device buffers; for dm_get_degrees any of q, dg, s may be NULL).
+ * Errors: DM_EINVAL for a NULL handle (or a NULL eps); DM_ECUDA. */
 int dm_get_eps(dm_handle h, double *eps);
 int dm_get_degrees(dm_handle h, double *q, double *dg, double *s);
 
@@ -288,7 +296,9 @@ int dm_get_degrees(dm_handle h, double *q, double *dg, double *s);
  * P[(node*max_rank + t)*cmax + j] = interpolation matrix entry (row t, candidate
  * j; candidates of a leaf are its positions in order, of an internal node the
  * left then right child skeletons), cmax = max(ceil(N/2^L), 2*max_rank).
- * Query sizes first with dm_get_tree(h, &L, NULL) and dm_get_stats. */
+ * Query sizes first with dm_get_tree(h, &L, NULL) and dm_get_stats. Buffers are
+ * caller-owned (host or device); a NULL output is skipped. Errors: DM_EINVAL for a NULL
+ * handle; DM_ESTATE before dm_compress or dm_load_hmatrix; DM_ECUDA. */
 int dm_get_tree(dm_handle h, int32_t *L, int32_t *perm);
 int dm_get_hmatrix(dm_handle h, int32_t *ranks, int32_t *skel, float *P);
 
