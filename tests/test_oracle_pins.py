@@ -539,3 +539,22 @@ def test_hmatvec_equals_dense_assembly_of_eq_2_18():
     np.testing.assert_allclose(yh, y, rtol=0, atol=1e-12 * np.abs(y).max())
     # and the truncation really happened: K~ differs from K
     assert np.abs(Korig - (s[:, None] * W * s[None, :])).max() > 1e-8
+
+
+@pytest.mark.parametrize("conv_tol", [1e-4, 1e-7])
+def test_lanczos_stop_rule_bounds_the_true_residuals(conv_tol):
+    """With full reorthogonalisation the stop rule's bound beta_m |y_m| is the residual
+    |S phi - theta phi| of each Ritz pair, so at the stop every wanted pair's true
+    residual is within conv_tol theta_1 (up to rounding); a looser tolerance stops no later."""
+    X = _scurve(600, 14)
+    eps = O.median_sqdist(X)
+    q, dg, s = O.degrees(X, eps, 1.0)
+    W = O.kernel_W(X, eps)
+    S = s[:, None] * W * s[None, :]
+    k = 8
+    ev, V, it, st = O.lanczos_S(X, eps, s, k, conv_tol=conv_tol)
+    assert st == 0
+    res = np.linalg.norm(S @ V - V * ev[None, :], axis=0)
+    assert np.all(res <= conv_tol * ev[0] * (1 + 1e-6) + 1e-13), res
+    _, _, it_tight, _ = O.lanczos_S(X, eps, s, k, conv_tol=conv_tol * 1e-3)
+    assert it <= it_tight
