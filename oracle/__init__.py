@@ -8,8 +8,9 @@ Every function takes numpy arrays; points are float32 (N, d) C-contiguous (the
 product's storage type), all results are float64. Which passage of the paper
 each routine follows is stated in oracle.c.
 
-Parity status: every routine here is pinned by a closed form, an invariant,
-brute force or a library special case in tests/test_oracle_pins.py, except the
+Parity status: every routine here (including the diffusion coordinates and the
+intrinsic dimension d(t)) is pinned by a closed form, an invariant, brute force,
+exact arithmetic or a library special case in tests/test_oracle_pins.py, except the
 paper's own printed accuracy figures (eigenvalue errors of about 9e-4 and 1e-4
 in Section 4.1), whose parameters the paper does not give ("parity unpinned").
 """
