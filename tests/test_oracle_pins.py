@@ -558,3 +558,86 @@ def test_lanczos_stop_rule_bounds_the_true_residuals(conv_tol):
     assert np.all(res <= conv_tol * ev[0] * (1 + 1e-6) + 1e-13), res
     _, _, it_tight, _ = O.lanczos_S(X, eps, s, k, conv_tol=conv_tol * 1e-3)
     assert it <= it_tight
+
+
+def test_S_matvec_rows_matches_full_product_and_top_eigenpair():
+    """or_S_matvec_rows (the row-sampled checker of the full-size tests) against the full
+    product on chosen rows, and against S dg^1/2 = dg^1/2 (Algorithm 1: the Markov matrix
+    P = Dg^-1 W^a has P 1 = 1, so its conjugate S fixes dg^1/2). Dropping s_i, s_j or the
+    kernel's exponent scale breaks the invariant even where both routines would agree."""
+    n = 700
+    X = _scurve(n, 15)
+    eps = O.median_sqdist(X)
+    q, dg, s = O.degrees(X, eps, 1.0)
+    rows = np.array([0, 1, 77, 350, 351, 698, 699, 77])
+    x = synth.random_rhs(n, 1, 21)[:, 0]
+    full = O.S_matvec(X, eps, s, x)
+    np.testing.assert_allclose(O.S_matvec_rows(X, eps, s, x, rows), full[rows], rtol=1e-13, atol=0)
+    r = np.sqrt(dg)
+    np.testing.assert_allclose(O.S_matvec_rows(X, eps, s, r, rows), r[rows], rtol=1e-12, atol=0)
+    # alpha = 0.5 gives another s; the invariant holds for every alpha
+    _, dg5, s5 = O.degrees(X, eps, 0.5)
+    r5 = np.sqrt(dg5)
+    np.testing.assert_allclose(O.S_matvec_rows(X, eps, s5, r5, rows), r5[rows], rtol=1e-12, atol=0)
+
+
+def _id_rows_recomputed(n, st, sz, rtarget, seed, node):
+    """The ID's sampled rows, recomputed from the published SplitMix64 stream: draw t is
+    u = floor(hi32(rng(key, t)) * off / 2^32) over the off = n - sz off-node positions,
+    mapped past the node's own range [st, st + sz)."""
+    off = n - sz
+    key = O.stream_key(seed, 1, node)
+    u = np.array(O.splitmix64_sequence(key, rtarget), dtype=np.uint64)
+    u = ((u >> np.uint64(32)) * np.uint64(off)) >> np.uint64(32)
+    u = u.astype(np.int64)
+    return np.where(u < st, u, u + sz)
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_id_sampled_rows_branch_matches_recomputed_draws(seed):
+    """The sampled-row branch of the ID (more off-node points than 2 max_rank + 10): the
+    oracle's ranks, skeletons and interpolation matrices equal LAPACK's column-pivoted QR
+    (scipy.linalg.qr, pivoting=True) of K(R, C) with R recomputed here from the seeded
+    stream, so a wrong draw, a row inside the node or a wrong offset changes the result."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    n, leaf, max_rank, tol = 600, 40, 24, 1e-5
+    X, eps, s = _setup(n, 16, leaf)
+    perm, L = O.tree(X, eps, leaf)
+    H = O.skeletonize(X, eps, s, perm, L, tol, max_rank, seed=seed)
+    W = O.kernel_W(X, eps)
+    Kp = (s[:, None] * W * s[None, :])[np.ix_(perm, perm)]
+    Pn = H.P.reshape(-1, H.max_rank, H.cmax)
+    rtarget = 2 * max_rank + 10
+    compared = 0
+    for node in range(1, (1 << (L + 1)) - 1):
+        st, sz = O.node_range(n, node)
+        assert n - sz > rtarget  # every node takes the sampled branch here
+        R = _id_rows_recomputed(n, st, sz, rtarget, seed, node)
+        assert R.min() >= 0 and R.max() < n and not np.any((R >= st) & (R < st + sz))
+        if int(math.log2(node + 1)) == L:
+            C = np.arange(st, st + sz)
+        else:
+            l, rr = 2 * node + 1, 2 * node + 2
+            C = np.concatenate([H.skel[l * max_rank:l * max_rank + H.ranks[l]],
+                                H.skel[rr * max_rank:rr * max_rank + H.ranks[rr]]])
+        A = Kp[np.ix_(R, C)]
+        _, Rq, piv = scipy_linalg.qr(A, pivoting=True, mode="economic")
+        d = np.abs(np.diag(Rq))
+        kmax = min(max_rank, len(C), rtarget)
+        thr = tol * d[0]
+        r_lapack = next((j for j in range(kmax) if d[j] <= thr), kmax)
+        if np.any(np.abs(d[:kmax + 1] - thr) <= 1e-9 * thr):
+            continue
+        if any(abs(d[j] - d[j + 1]) <= 1e-12 * d[0] for j in range(r_lapack)):
+            continue  # pivot ties within rounding: the order is not sharp
+        r = H.ranks[node]
+        assert r == r_lapack, (node, r, r_lapack)
+        J = H.skel[node * max_rank:node * max_rank + r]
+        np.testing.assert_array_equal(J, C[piv[:r]])
+        # P(:, J) = I and P(:, rest) = R11^-1 R12 (invariant to the sign convention of the QR)
+        want = np.zeros((r, len(C)))
+        want[:, piv[:r]] = np.eye(r)
+        want[:, piv[r:]] = scipy_linalg.solve_triangular(Rq[:r, :r], Rq[:r, r:len(C)])
+        np.testing.assert_allclose(Pn[node, :r, :len(C)], want, rtol=0, atol=1e-7 * max(1.0, np.abs(want).max()))
+        compared += 1
+    assert compared >= 10
