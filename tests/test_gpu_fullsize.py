@@ -100,3 +100,29 @@ def test_fullsize_eigs_meet_accuracy_target_at_tight_tolerance(dm, ref):
     print(f"tol 1e-7: max rel eigenvalue error {rel.max():.3e}, angle {_subspace_angle(V.astype(np.float64), ref['V']):.3e}")
     assert rel.max() < 1e-5, rel
     assert _subspace_angle(V.astype(np.float64), ref["V"]) < 1e-3
+
+
+@pytest.fixture(scope="module")
+def H_bench(ref):
+    """The oracle's own compression at the benchmark's parameters (leaf 512, rank 128, tol 1e-5)."""
+    return O.compress(ref["X"], ref["eps"], ref["s"], 512, 1e-5, 128)
+
+
+@pytest.mark.parametrize("nrhs", [1, 16])
+def test_fullsize_hmatvec_replay_elementwise(dm, ref, H_bench, nrhs):
+    """Element-wise parity of the H-matvec at the benchmark shape (256 leaves of 390/391
+    points, depth 8, 510 nodes, the one-cluster tree pass at nrhs = 1 and the block path at
+    nrhs = 16) on the oracle's structure loaded through dm_load_hmatrix, against the oracle's
+    FP64 evaluation of Eq. 2.18 on that structure: 1e-5 max|x| per element, as at small N."""
+    H = H_bench
+    h = dm.dm_create(ref["X"], eps=ref["eps"])
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    st = dm.dm_get_stats(h)
+    assert st["L"] == 8 and st["leaf_max"] == 391
+    x = np.asfortranarray(synth.random_rhs(N, nrhs, seed=31).astype(np.float32))
+    y = dm.dm_matvec(h, x if nrhs > 1 else np.ascontiguousarray(x[:, 0]))
+    yr = O.hmatvec(ref["X"], ref["eps"], ref["s"], H, x.astype(np.float64))
+    err = np.abs(np.asarray(y, np.float64).reshape(N, nrhs) - yr.reshape(N, nrhs)).max() / np.abs(x).max()
+    print(f"nrhs {nrhs}: max |y - y_oracle| / max|x| = {err:.3e}")
+    assert err < 1e-5, err
+    dm.dm_destroy(h)

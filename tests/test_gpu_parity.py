@@ -273,7 +273,13 @@ def test_gpu_compression_accuracy_and_structure(dm, n, leaf, rank, tol, kind):
     err_gpu = np.linalg.norm(y - yr) / np.linalg.norm(yr)
     Ho = O.compress(X, eps, s, leaf, tol, rank)
     err_or = np.linalg.norm(O.hmatvec(X, eps, s, Ho, x) - yr) / np.linalg.norm(yr)
-    assert err_gpu < 10 * err_or + 1e-6, (err_gpu, err_or)
+    # The GPU draws the same seeded rows and takes the same candidates; its FP32 pivot and
+    # rank decisions can differ from the oracle's FP64 ones only where two residual norms
+    # tie within FP32 rounding (~1e-6 relative), which moves the compression error by far
+    # less than 2% (measured ratio 1.000-1.001 on all four cases); the FP32 evaluation adds
+    # ~1e-7 relative (the additive term).
+    print(f"compression error: gpu {err_gpu:.3e} oracle {err_or:.3e} ratio {err_gpu / max(err_or, 1e-300):.3f}")
+    assert err_gpu <= 1.02 * err_or + 1e-6, (err_gpu, err_or)
 
 
 # ------------------------------------------------------------------ Lanczos
@@ -291,9 +297,25 @@ def test_eigs_replayed_structure_match_oracle_lanczos(dm):
     ev, V, conv = dm.dm_eigs(h, 10)
     assert conv
     np.testing.assert_allclose(ev, evo, rtol=2e-5, atol=2e-7)
+    angles = []
     for i in range(10):
         c = abs(float(np.dot(V[:, i].astype(np.float64), Vo[:, i])))
-        assert math.acos(min(1.0, c)) < 2e-3
+        angles.append(math.acos(min(1.0, c)))
+        assert angles[-1] < 2e-3
+    # diffusion coordinates (Algorithm 1: eigenvalues theta^t of P^t, right eigenvectors
+    # Dg^-1/2 phi) against the oracle's coordinates of the oracle's own eigenpairs and
+    # degrees. Per column: an eigenvector off by angle a moves psi by ~a relative, the
+    # eigenvalue's relative error enters t times, and FP32 storage adds ~1e-6; a wrong
+    # power of theta (>= 30% off for every non-trivial pair here) or a missing Dg^-1/2
+    # fails by orders of magnitude.
+    for t in (1, 3):
+        psi = dm.dm_coords(h, 10, t).astype(np.float64)
+        want = O.diffusion_coords(evo, Vo, dg, t)
+        for i in range(10):
+            sgn = 1.0 if np.dot(psi[:, i], want[:, i]) >= 0 else -1.0
+            err = np.linalg.norm(sgn * psi[:, i] - want[:, i]) / np.linalg.norm(want[:, i])
+            bound = 2.0 * angles[i] + t * abs(ev[i] - evo[i]) / evo[i] + 5e-6
+            assert err <= bound, (t, i, err, bound)
 
 
 @pytest.mark.parametrize("b,k,prec", [(8, 10, 0), (16, 10, 0), (4, 6, 0), (16, 10, 1)])
@@ -363,10 +385,15 @@ def test_eigs_c1_workload_against_dense_oracle(dm):
     _, Vo, _, _ = O.lanczos_S(X, g["eps"], s, 10, conv_tol=1e-10)
     sv = np.linalg.svd(Vo.T @ V.astype(np.float64), compute_uv=False)
     assert math.acos(min(1.0, sv.min())) < 1e-3
-    # diffusion coordinates psi = theta^t Dg^-1/2 phi
-    psi = dm.dm_coords(h, 4, 2)
-    want = (ev[:4] ** 2)[None, :] * V[:, :4].astype(np.float64) / np.sqrt(dg)[:, None]
-    np.testing.assert_allclose(psi, want, rtol=2e-5, atol=1e-9)
+    # diffusion coordinates psi = theta^t Dg^-1/2 phi against the oracle's coordinates of
+    # the exact operator's eigenpairs: the four leading pairs are well separated, so each
+    # column agrees to the approximation error of tol 1e-5 (measured ~1e-5 relative)
+    evx, Vx, _, _ = O.lanczos_S(X, g["eps"], s, 4, conv_tol=1e-10)
+    psi = dm.dm_coords(h, 4, 2).astype(np.float64)
+    want = O.diffusion_coords(evx, Vx, dg, 2)
+    for i in range(4):
+        sgn = 1.0 if np.dot(psi[:, i], want[:, i]) >= 0 else -1.0
+        assert np.linalg.norm(sgn * psi[:, i] - want[:, i]) / np.linalg.norm(want[:, i]) < 1e-3
 
 
 def test_eigs_state_errors(dm):
