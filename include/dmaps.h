@@ -204,6 +204,19 @@ int dm_get_stats(dm_handle h, dm_stats *st);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t dm_kernel_launches(void);
 
+/* Failure-detection self-test of the bounded grid barrier that separates the passes of
+ * the cooperative Lanczos step (no paper counterpart). `blocks` (1..8, always resident at
+ * once) blocks meet at that barrier, whose target counts `missing` more arrivals than
+ * there are blocks. Each block polls at most `spin_limit` (1..2^24) times, about 0.1-1 us
+ * per poll, then raises the device error flag and returns, exactly as the Lanczos step
+ * does. *passed (may be NULL) receives the number of blocks that got through.
+ * Returns DM_OK when every block passed (missing = 0), DM_ETIMEOUT when the wait gave up
+ * (missing > 0: nothing can complete the count), so the timeout path is exercised
+ * without faulting or hanging the device; the device stays usable either way.
+ * Allocates and frees 16 bytes of device memory on the current device; synchronous.
+ * Errors: DM_EINVAL for arguments out of range; DM_ENOMEM; DM_ECUDA. */
+int dm_selftest_wait_timeout(int32_t blocks, int32_t missing, int64_t spin_limit, int32_t *passed);
+
 /* ---- serving: continuous admission of independent solves ----
  * A process-wide server runs `slots` solves at once, each on its own CUDA stream,
  * so their kernels overlap on the device. Requests wait in a queue and are
@@ -265,22 +278,30 @@ int dm_release(dm_ticket t);
  * services with a memory budget fixed up front, and hot paths that must not take
  * cudaMalloc's implicit device-wide synchronisation.
  *
- * Computes the same degree vectors as dm_create (q = W 1, dg = W^a 1,
+ * Computes the degree vectors of dm_create (q = W 1, dg = W^a 1,
  * s = q^-a dg^-1/2, each N doubles in the original point order) for N points
  * (N x d row-major float32) with an explicit eps > 0, enqueued on `stream`
  * (a cudaStream_t; NULL = the legacy default stream) and not synchronised: the
- * outputs are ready when the stream reaches this work. All four pointers must
- * be device memory the caller owns. It calls no cudaMalloc, cudaFree or other
+ * outputs are ready when the stream reaches this work. Its kernel entries are
+ * always the FP32 difference form |x_i - x_j|^2, where dm_create takes a centred
+ * dot-product form at d = 3 and a tensor-core Gram matrix at d >= 16, so the two
+ * agree to rounding, not bit for bit: within 2e-6 relative at d <= 15 and 5e-6
+ * relative at d >= 16 (FP32 entries, FP64 sums). All four pointers must be
+ * device memory the caller owns, on the current device. It calls no cudaMalloc, cudaFree or other
  * allocating routine: its intermediate arrays live in one fixed 16 MiB
  * module-scope device array that every GPU loading this library holds until
  * the process exits, which limits N * (4 d + 16) bytes (rounded up to 256-byte
  * pieces) to 16 MiB — about 670,000 points at d = 3.
  * The first call on a device looks up that array's device address with that
- * device current; make this first call before any stream capture.
+ * device current; make this first call before any stream capture. The address
+ * is kept for the life of the process: after cudaDeviceReset on a device, do not
+ * call this function on that device again.
  * Every call shares the one array, so calls whose work overlaps on the GPU
  * (different streams, threads or devices' streams racing on one device) race;
- * serialise them. Errors: DM_EINVAL on a NULL or host pointer, N < 2, d < 1,
- * eps <= 0, alpha < 0, or a size above the limit; DM_ECUDA if a launch fails. */
+ * serialise them. Errors: DM_EINVAL on a NULL or host pointer, a pointer to
+ * another device's memory, N < 2, d < 1, eps <= 0, alpha < 0, or a size above
+ * the limit; DM_ECUDA if a launch fails. The output pointers must each hold N
+ * doubles: the library cannot check the size of a raw device buffer. */
 int dm_degrees_noalloc(const float *points, int64_t N, int32_t d, double eps, double alpha,
                        double *q, double *dg, double *s, void *stream);
 

@@ -27,7 +27,7 @@ __all__ = [
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
     "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc", "dm_request",
     "dm_result", "dm_serve_config", "dm_request_bytes", "dm_serve_start", "dm_serve_stop", "dm_submit", "dm_poll",
-    "dm_release", "dm_tune_leaf",
+    "dm_release", "dm_tune_leaf", "dm_selftest_wait_timeout",
 ]
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True):
         "dm_poll": (i32, [C.c_uint64, C.POINTER(dm_result), C.POINTER(i32)]),
         "dm_release": (i32, [C.c_uint64]),
         "dm_tune_leaf": (i32, [vp, f64, i32, i32, vp, i32, C.POINTER(i32), vp]),
+        "dm_selftest_wait_timeout": (i32, [i32, i32, i64, C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -354,18 +355,42 @@ def dm_degrees_noalloc(points, eps: float, alpha: float, q, dg, s, stream=None) 
     """dm_degrees_noalloc: CUDA float32 points (N, d) and CUDA float64 outputs q, dg, s (N,).
 
     Enqueues on `stream` (a torch.cuda.Stream or raw handle; default: torch's current stream)
-    and does not synchronise."""
+    and does not synchronise. Raises ValueError unless points is a C-contiguous float32 CUDA
+    tensor of shape (N, d) and q, dg, s are contiguous float64 CUDA tensors of N elements, all
+    on one device (that of `stream` when it is a torch stream): the library writes N doubles
+    through each output pointer and reads the points as row-major."""
     torch = _torch()
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float32
+            and points.dim() == 2 and points.is_contiguous()):
+        raise ValueError("dm_degrees_noalloc: points must be a C-contiguous float32 CUDA tensor of shape (N, d)")
     N, d = int(points.shape[0]), int(points.shape[1])
+    for name, t in (("q", q), ("dg", dg), ("s", s)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() == N):
+            raise ValueError(f"dm_degrees_noalloc: {name} must be a contiguous float64 CUDA tensor of {N} elements")
+        if t.device != points.device:
+            raise ValueError(f"dm_degrees_noalloc: {name} is on {t.device}, points on {points.device}")
+    if stream is None:
+        stream = torch.cuda.current_stream(points.device)
+    if hasattr(stream, "device") and torch.device(stream.device) != points.device:
+        raise ValueError(f"dm_degrees_noalloc: stream is on {stream.device}, the tensors on {points.device}")
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     _check(load().dm_degrees_noalloc(_ptr(points), N, d, float(eps), float(alpha), _ptr(q), _ptr(dg), _ptr(s),
                                      handle))
 
 
 def dm_kernel_launches() -> int:
     return int(load().dm_kernel_launches())
+
+
+def dm_selftest_wait_timeout(blocks: int, missing: int, spin_limit: int) -> tuple[int, int]:
+    """dm_selftest_wait_timeout: (status, blocks that passed); the status is returned, not
+    raised, since DM_ETIMEOUT is the expected answer when arrivals are missing."""
+    passed = C.c_int32(-1)
+    st = int(load().dm_selftest_wait_timeout(int(blocks), int(missing), int(spin_limit), C.byref(passed)))
+    if st not in (DM_OK, DM_ETIMEOUT):
+        raise DmError(st, dm_last_error())
+    return st, int(passed.value)
 
 
 def dm_get_stats(h: Handle) -> dict:

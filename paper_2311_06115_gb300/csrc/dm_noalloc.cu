@@ -20,6 +20,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of the scratch array, looked up once per device with that
 // device current. In host code the array's name is only a host-side stand-in.
+// The cached address belongs to the device's primary context as it was at the
+// first call: after cudaDeviceReset (which reloads this module) it is stale, so
+// a process that resets a device must not call dm_degrees_noalloc on it again.
 std::mutex g_scratch_mu;
 void *g_scratch_addr[256];
 
@@ -40,13 +43,17 @@ int scratch_for_current_device(void **out) {
     return DM_OK;
 }
 
-bool on_device(const void *p) {
+// 1: device (or managed) memory of device `dev`; 0: host memory or unknown; -1: device
+// memory of another GPU (its kernels would make peer or illegal accesses).
+int on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type != cudaMemoryTypeDevice) return 0;
+    return a.device == dev ? 1 : -1;
 }
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -66,8 +73,15 @@ extern "C" int dm_degrees_noalloc(const float *points, int64_t N, int32_t d, dou
         return dm_fail_msg(DM_EINVAL, "dm_degrees_noalloc: needs N >= 2, d >= 1, eps > 0, alpha >= 0");
     if (dm_noalloc_scratch_need(N, d) > kNoAllocScratchBytes)
         return dm_fail_msg(DM_EINVAL, "dm_degrees_noalloc: N * (4 d + 16) bytes exceed the 16 MiB scratch array");
-    if (!on_device(points) || !on_device(q) || !on_device(dg) || !on_device(s))
-        return dm_fail_msg(DM_EINVAL, "dm_degrees_noalloc: points, q, dg and s must be device memory");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return dm_fail_msg(DM_ECUDA, "dm_degrees_noalloc: no current device");
+    int where[4] = {on_device(points, dev), on_device(q, dev), on_device(dg, dev), on_device(s, dev)};
+    for (int w : where) {
+        if (w == 0) return dm_fail_msg(DM_EINVAL, "dm_degrees_noalloc: points, q, dg and s must be device memory");
+        if (w < 0)
+            return dm_fail_msg(DM_EINVAL,
+                               "dm_degrees_noalloc: a buffer is on another device than the current one");
+    }
     void *base = nullptr;
     if (scratch_for_current_device(&base) != DM_OK)
         return dm_fail_msg(DM_ECUDA, "dm_degrees_noalloc: cudaGetSymbolAddress of the scratch array failed");
