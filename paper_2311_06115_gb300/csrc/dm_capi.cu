@@ -858,6 +858,33 @@ const char *dm_last_error(void) { return g_err.c_str(); }
 
 int64_t dm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+int dm_selftest_wait_timeout(int32_t blocks, int32_t missing, int64_t spin_limit, int32_t *passed) {
+    if (blocks < 1 || blocks > 8 || missing < 0 || spin_limit < 1 || spin_limit > ((int64_t)1 << 24))
+        return fail(DM_EINVAL, "dm_selftest_wait_timeout: needs 1 <= blocks <= 8, missing >= 0, "
+                               "1 <= spin_limit <= 2^24");
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DM_ENOMEM, "dm_selftest_wait_timeout: cudaMalloc of 16 bytes failed");
+    }
+    unsigned *ctr = static_cast<unsigned *>(mem);
+    int *err = reinterpret_cast<int *>(ctr + 2);
+    unsigned host[2] = {0, 0};
+    int herr = 0;
+    cudaError_t e = dm_launch_barrier_selftest(ctr, err, blocks, missing, (long long)spin_limit, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(host, ctr, sizeof(host), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DM_ECUDA, "dm_selftest_wait_timeout: %s", cudaGetErrorString(e));
+    }
+    if (passed) *passed = (int32_t)host[1];
+    if (herr) return fail(DM_ETIMEOUT, "dm_selftest_wait_timeout: the grid barrier gave up waiting (as intended "
+                                       "when arrivals are missing)");
+    return DM_OK;
+}
+
 int dm_create(const float *points, int64_t N, int32_t d, double eps, double alpha, const dm_config *cfg,
               dm_handle *out) {
     if (!out) return fail(DM_EINVAL, "out handle is NULL");

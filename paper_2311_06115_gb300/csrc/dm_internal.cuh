@@ -326,6 +326,8 @@ struct DmLanczos {
     int *err;         // set when a bounded device wait gave up
 };
 int dm_lanczos_kmax();
+cudaError_t dm_launch_barrier_selftest(unsigned *ctr, int *err, int blocks, int missing, long long spin_limit,
+                                       cudaStream_t st);
 cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st);
 cudaError_t dm_lanczos_orth(DmLanczos &Lz, int j, bool phased, cudaStream_t st);
 cudaError_t dm_lanczos_ritz(DmLanczos &Lz, int m, int k, double conv_tol, cudaStream_t st);

@@ -76,7 +76,7 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
 }
 
 // returns false when the barrier timed out (in this or another block)
-__device__ bool grid_barrier(unsigned *ctr, unsigned target, int *err) {
+__device__ bool grid_barrier(unsigned *ctr, unsigned target, int *err, long long spin_limit = kBarrierSpinLimit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -85,7 +85,7 @@ __device__ bool grid_barrier(unsigned *ctr, unsigned target, int *err) {
         int ok = 1;
         long long spins = 0;
         while (ld_acquire_gpu(ctr) < target) {
-            if (++spins > kBarrierSpinLimit || *((volatile int *)err) != 0) {
+            if (++spins > spin_limit || *((volatile int *)err) != 0) {
                 ok = 0;
                 atomicExch(err, 1);
                 break;
@@ -922,6 +922,26 @@ cudaError_t dm_lanczos_phi(DmLanczos &Lz, int m, int k, const int32_t *perm, flo
 cudaError_t dm_launch_coords(const float *evecs, const double *theta, const double *dg, int64_t N, int k, int t,
                              float *psi, cudaStream_t st) {
     coords_kernel<<<dim3(nblk(N, 256), (unsigned)k), 256, 0, st>>>(evecs, theta, dg, N, t, psi);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+// Failure-detection self-test of the bounded grid barrier above: `blocks` blocks meet at a
+// barrier whose target counts `missing` more arrivals than there are blocks. With missing
+// = 0 every block passes (blocks <= 8, always co-resident); with missing > 0 nothing ever
+// completes the count, every block gives up after `spin_limit` polls, raises *err and
+// returns, and ctr[1] counts the blocks that passed.
+__global__ void barrier_selftest_kernel(unsigned *ctr, unsigned target, int *err, long long spin_limit) {
+    if (!grid_barrier(ctr, target, err, spin_limit)) return;
+    if (threadIdx.x == 0) atomicAdd(ctr + 1, 1u);
+}
+
+cudaError_t dm_launch_barrier_selftest(unsigned *ctr, int *err, int blocks, int missing, long long spin_limit,
+                                       cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    barrier_selftest_kernel<<<blocks, 128, 0, st>>>(ctr, (unsigned)(blocks + missing), err, spin_limit);
     dm_count_launches(1);
     return cudaGetLastError();
 }
