@@ -190,8 +190,9 @@ typedef struct dm_stats {
     int32_t matvec_calls;    /* H-matvecs timed in the last dm_eigs (profile = 1) */
     float ms_matvec;         /* their summed device time */
     int32_t hmatvec_path;    /* 0 = leaf N2S + one-cluster tree pass + near stream (the upper
-                                tree fits the cluster's shared memory), 1 = chained two-launch
-                                form (deep trees at high ranks) */
+                                tree fits the shared memory of a cluster of 8 CTAs), 2 = the same
+                                with a cluster of 16 CTAs (higher ranks), 1 = chained two-launch
+                                form (deep trees at ranks too high for either cluster) */
     int32_t degree_path;     /* degree passes of dm_create: 0 = CUDA cores (FP32 entries),
                                 1 = tensor cores, TF32 three-term split Gram matrix (d >= 16),
                                 2 = tensor cores, exact BF16 Gram matrix (8-bit quantised data) */

@@ -404,10 +404,10 @@ int copy_out(dm_ctx *h, void *dst, const void *src, size_t bytes) {
 // stride s_r|1) follow.
 // img_off gets each CTA's offset in the image buffer (floats, multiples of 4). Returns false
 // when a CTA's share does not fit the budget (the chained two-launch path is used then).
-bool tree_layout(const std::vector<int32_t> &rk, int L, int budget_floats, std::vector<int4> &lay,
+bool tree_layout(const std::vector<int32_t> &rk, int L, int budget_floats, int ls_want, std::vector<int4> &lay,
                  std::vector<int2> &own, int &ls, int &smem_bytes, std::vector<int> &img_off) {
     if (L < 1) return false;
-    ls = L - 1 < 3 ? L - 1 : 3;
+    ls = L - 1 < ls_want ? L - 1 : ls_want;
     const int nc = 1 << ls, nnodes = (1 << (L + 1)) - 1, ninternal = (1 << L) - 1;
     lay.assign(nnodes, make_int4(-1, -1, -1, -1));
     // every CTA first holds the node metadata: the layout (int4 per node), the ranks, and the
@@ -530,7 +530,13 @@ int finish_structure(dm_ctx *h) {
         std::vector<int> img_off;
         int ls = 0, smem = 0;
         h->tree_ok = 0;
-        if (tree_layout(rk, h->L, kTreeSmemBudget / 4, lay, own, ls, smem, img_off)) {
+        // a cluster of 8 CTAs (cut at level 3) when the upper tree fits their shared memory,
+        // else 16 (cut at level 4; a non-portable cluster size, used when the device can
+        // schedule it)
+        bool fits = tree_layout(rk, h->L, kTreeSmemBudget / 4, 3, lay, own, ls, smem, img_off);
+        if (!fits && h->L - 1 >= 4 && dm_tree_cluster_supported(16))
+            fits = tree_layout(rk, h->L, kTreeSmemBudget / 4, 4, lay, own, ls, smem, img_off);
+        if (fits) {
             DM_CHECK(h->alloc(&h->tlay, lay.size(), G_STRUCT));
             DM_CHECK(h->alloc(&h->town, own.size(), G_STRUCT));
             DM_CUDA(cudaMemcpyAsync(h->town, own.data(), sizeof(int2) * own.size(), cudaMemcpyHostToDevice,
@@ -587,7 +593,7 @@ int finish_structure(dm_ctx *h) {
     // weights written and read once each
     S.matvec_bytes = (cached ? near : (int64_t)h->N * (h->d + 1) * 4) + basis + far + 2 * h->N * 4 + 2 * sksum * 4 * 2;
     S.near_mode = h->near_mode;
-    S.hmatvec_path = (h->L == 0 || h->tree_ok) ? 0 : 1;
+    S.hmatvec_path = (h->L == 0 || h->tree_ok) ? (h->tree_ok && h->tree_ls >= 4 ? 2 : 0) : 1;
     h->compressed = true;
     return DM_OK;
 }

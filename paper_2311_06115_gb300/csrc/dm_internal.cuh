@@ -131,7 +131,8 @@ __device__ __forceinline__ double dm_sqdist64(const float *a, const float *b, in
 // Device-side structure of a compressed operator (all pointers device memory).
 // ---------------------------------------------------------------------------
 // dynamic shared memory per CTA that the cluster pass over the upper tree may use
-constexpr int kTreeSmemBudget = 200 * 1024;
+constexpr int kTreeSmemBudget = 226 * 1024;  // under the 227 KB opt-in limit of one CTA
+constexpr int kTreeMaxCtas = 16;  // largest cluster of the one-cluster tree pass
 
 struct DmHmat {
     int64_t N;
@@ -276,6 +277,9 @@ cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, flo
 int dm_near_item_rows(int near_mode, int leaf_max);
 // write each cluster CTA's shared-memory image of the upper tree (after packing)
 cudaError_t dm_tree_image(const DmHmat &H, cudaStream_t st);
+// whether the device can run the one-cluster tree pass as a cluster of `ctas` CTAs with the
+// largest shared-memory budget (16 needs the non-portable cluster size)
+bool dm_tree_cluster_supported(int ctas);
 
 // k_hblock.cu -- H-matvec of a block of right-hand sides
 struct DmBlockWork {

@@ -182,7 +182,7 @@ uint64_t dm_request_bytes(const dm_request *r) {
     // transient workspaces of the compression (skeletonization is the largest)
     b += r256(4 * nleaves * cmax * ldr) + r256(4 * nleaves * R * cmax) + r256(4 * nleaves * R * ldr);
     // the upper tree's shared-memory images (at most one cluster's shared memory)
-    b += r256((uint64_t)8 * kTreeSmemBudget) + r256(16 * nnodes) + 256;
+    b += r256((uint64_t)kTreeMaxCtas * kTreeSmemBudget) + r256(16 * nnodes) + 256;
     // Lanczos basis, Ritz vectors and small arrays
     b += r256(4 * (mmax + 1) * ldv) + r256(4 * ldv) + 2 * r256(4 * kmax * N);
     b += r256(8 * kmax * 6 * mmax) + r256(8 * kmax * mmax) + r256(4 * kmax * mmax) + 16 * 256;

@@ -528,6 +528,34 @@ cudaError_t launch_ex(void (*kern)(KArgs...), unsigned grid, unsigned block, siz
 
 }  // namespace
 
+bool dm_tree_cluster_supported(int ctas) {
+    static int cached[2] = {-1, -1};  // 8, 16 CTAs (one device per process in practice)
+    const int slot = ctas > 8 ? 1 : 0;
+    if (cached[slot] >= 0) return cached[slot] != 0;
+    int ok = 0;
+    const size_t smem = (size_t)kTreeSmemBudget;
+    if (dm_allow_smem((const void *)tree_kernel, smem) == cudaSuccess &&
+        (ctas <= 8 || cudaFuncSetAttribute((const void *)tree_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                           1) == cudaSuccess)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)ctas);
+        cfg.blockDim = dim3(kTreeThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = (unsigned)ctas;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (const void *)tree_kernel, &cfg) == cudaSuccess && n > 0) ok = 1;
+    }
+    cudaGetLastError();
+    cached[slot] = ok;
+    return ok != 0;
+}
+
 cudaError_t dm_tree_image(const DmHmat &H, cudaStream_t st) {
     if (!H.tree_ok) return cudaSuccess;
     tree_image_kernel<<<dim3(1u << H.tree_ls, 8u), 512, 0, st>>>(H, H.timg, H.timg_off);

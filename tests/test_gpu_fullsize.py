@@ -126,3 +126,31 @@ def test_fullsize_hmatvec_replay_elementwise(dm, ref, H_bench, nrhs):
     print(f"nrhs {nrhs}: max |y - y_oracle| / max|x| = {err:.3e}")
     assert err < 1e-5, err
     dm.dm_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def H_tight(ref):
+    """The oracle's compression at tol 3e-7 (leaf 512, rank 128): ranks up to ~66, an upper
+    tree too large for a cluster of 8 CTAs' shared memory."""
+    return O.compress(ref["X"], ref["eps"], ref["s"], 512, 3e-7, 128)
+
+
+def test_fullsize_hmatvec_replay_sixteen_cta_cluster(dm, ref, H_tight):
+    """The one-cluster tree pass cut at level 4 (a cluster of 16 CTAs, 16 subtrees of 16
+    leaves) on the oracle's tol 3e-7 structure, element-wise against the oracle's Eq. 2.18
+    evaluation at 1e-5 max|x|, and against the chained two-launch form on the same operator."""
+    H = H_tight
+    h = dm.dm_create(ref["X"], eps=ref["eps"])
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    st = dm.dm_get_stats(h)
+    print(f"tol 3e-7: ranks {st['rank_min']}-{st['rank_max']} mean {st['rank_mean']:.1f}, path {st['hmatvec_path']}")
+    assert st["hmatvec_path"] in (0, 2)
+    x = synth.random_rhs(N, 1, seed=33)[:, 0].astype(np.float32)
+    y = dm.dm_matvec(h, x)
+    yr = O.hmatvec(ref["X"], ref["eps"], ref["s"], H, x.astype(np.float64))
+    err = np.abs(y - yr).max() / np.abs(x).max()
+    print(f"tol 3e-7 replay: max |y - y_oracle| / max|x| = {err:.3e}")
+    assert err < 1e-5, err
+    y2 = dm.dm_matvec(h, x)
+    assert np.array_equal(y, y2)
+    dm.dm_destroy(h)
