@@ -100,7 +100,7 @@ namespace {
         if (_s != DM_OK) return _s; \
     } while (0)
 
-enum Group { G_BASE = 0, G_STRUCT = 1, G_WORK = 2, G_LANCZOS = 3, G_IO = 4, G_BLOCK = 5, G_BLANCZOS = 6 };
+enum Group { G_BASE = 0, G_STRUCT = 1, G_WORK = 2, G_LANCZOS = 3, G_IO = 4, G_BLOCK = 5, G_BLANCZOS = 6, G_NB = 7 };
 
 // right-hand sides per block H-matvec call (wider blocks run as several panels): the FP32
 // near field tiles 64 columns, the tensor-core one up to 256 (the largest MMA N)
@@ -173,6 +173,11 @@ struct dm_ctx {
     int *timg_off = nullptr;
     int tree_ok = 0, tree_ls = 0, tree_smem = 0;
     int *herr = nullptr;
+    std::vector<int32_t> rk_host;  // ranks per node (host copy, for layouts built later)
+    // narrow-block (2..4 columns) cluster pass: nbt.nb = 0 until built; nb_fits = 0 when the
+    // nb-wide layout of the last request did not fit the cluster's shared memory
+    DmNbTree nbt{};
+    int nb_tried = 0, nb_fits = 0;
     // lanczos
     DmLanczos lz{};
     bool lz_ready = false;
@@ -502,6 +507,7 @@ int finish_structure(dm_ctx *h) {
     int rank_hi = 1;
     for (int node = 1; node < nnodes; ++node) rank_hi = rk[node] > rank_hi ? rk[node] : rank_hi;
     h->rank_hi = rank_hi;
+    h->rk_host = rk;
     h->ldt = (int)round_up(rank_hi, 4);
     // point-major leaf bases, each leaf's rows at its own rank's stride (rounded up to 4):
     // the S2N reads then touch only the basis, not the padding to the largest leaf rank
@@ -600,6 +606,9 @@ int finish_structure(dm_ctx *h) {
 
 int alloc_structure(dm_ctx *h, int L, int max_rank) {
     h->free_group(G_STRUCT);
+    h->free_group(G_NB);
+    h->nbt = DmNbTree{};
+    h->nb_tried = h->nb_fits = 0;
     h->free_group(G_BLOCK);
     h->blk.nb_max = 0;
     h->free_group(G_BLANCZOS);
@@ -665,6 +674,58 @@ int ensure_block(dm_ctx *h, int nb) {
     return DM_OK;
 }
 
+// The nb-column cluster pass (2 <= nb <= 4, cached near field): its layout, image and vector
+// buffers, built on first use. *fits = 0 when the nb-wide upper tree does not fit the
+// cluster's shared memory (the per-level block path is used then).
+int ensure_nb(dm_ctx *h, int nb, bool *fits) {
+    *fits = false;
+    if (h->L < 1 || h->near_mode != DM_NEAR_CACHED || nb < 2 || nb > 4) return DM_OK;
+    if (h->nbt.nb == nb) {
+        *fits = true;
+        return DM_OK;
+    }
+    if (h->nb_tried == nb && !h->nb_fits) return DM_OK;
+    h->free_group(G_NB);
+    h->nbt = DmNbTree{};
+    h->nb_tried = nb;
+    h->nb_fits = 0;
+    DmNbLayout lay;
+    if (!dm_nb_tree_layout(h->rk_host, h->L, nb, kTreeSmemBudget / 4, lay)) return DM_OK;
+    const size_t nnodes = ((size_t)2 << h->L) - 1;
+    DmNbTree T{};
+    int4 *dlay = nullptr;
+    int2 *down = nullptr;
+    int *downer = nullptr, *doff = nullptr;
+    DM_CHECK(h->alloc(&dlay, lay.lay.size(), G_NB));
+    DM_CHECK(h->alloc(&down, lay.own.size(), G_NB));
+    DM_CHECK(h->alloc(&downer, lay.owner.size(), G_NB));
+    DM_CHECK(h->alloc(&doff, lay.img_off.size(), G_NB));
+    DM_CHECK(h->alloc(&T.img, (size_t)lay.img_off.back(), G_NB));
+    DM_CHECK(h->alloc(&T.what, nnodes * h->max_rank * nb, G_NB));
+    DM_CHECK(h->alloc(&T.uhat, nnodes * h->max_rank * nb, G_NB));
+    DM_CUDA(cudaMemcpyAsync(dlay, lay.lay.data(), sizeof(int4) * lay.lay.size(), cudaMemcpyHostToDevice, h->stream));
+    DM_CUDA(cudaMemcpyAsync(down, lay.own.data(), sizeof(int2) * lay.own.size(), cudaMemcpyHostToDevice, h->stream));
+    DM_CUDA(cudaMemcpyAsync(downer, lay.owner.data(), sizeof(int) * lay.owner.size(), cudaMemcpyHostToDevice,
+                            h->stream));
+    DM_CUDA(cudaMemcpyAsync(doff, lay.img_off.data(), sizeof(int) * lay.img_off.size(), cudaMemcpyHostToDevice,
+                            h->stream));
+    T.nb = nb;
+    T.ls = lay.ls;
+    T.smem = lay.smem;
+    T.lay = dlay;
+    T.own = down;
+    T.owner = downer;
+    T.img_off = doff;
+    DM_CUDA(dm_nb_tree_image(h->hmat(), T, h->stream));
+    // the host vectors above are pageable sources: each copy has staged them on return;
+    // wait anyway so the layout is resident before the handle reports it
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    h->nbt = T;
+    h->nb_fits = 1;
+    *fits = true;
+    return DM_OK;
+}
+
 // block Lanczos buffers for block size b (the basis itself is the Lanczos V)
 int ensure_block_lanczos(dm_ctx *h, int b) {
     if (h->bl.b == b) return DM_OK;
@@ -679,13 +740,15 @@ int ensure_block_lanczos(dm_ctx *h, int b) {
     B.ldpart = mm + 1;
     DM_CHECK(h->alloc(&B.Z, (size_t)b * h->lz.ldv, G_BLANCZOS));
     DM_CHECK(h->alloc(&B.part, (size_t)B.nparts * B.ldpart * b, G_BLANCZOS));
-    DM_CHECK(h->alloc(&B.H, (size_t)B.ldpart * b, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.H, (size_t)dm_bstep_hcopies() * B.ldpart * b, G_BLANCZOS));
     DM_CHECK(h->alloc(&B.Rinv, (size_t)b * b, G_BLANCZOS));
     DM_CHECK(h->alloc(&B.Bacc, (size_t)b * b, G_BLANCZOS));
     DM_CHECK(h->alloc(&B.T, (size_t)mm * mm, G_BLANCZOS));
     DM_CHECK(h->alloc(&B.W, (size_t)mm * mm, G_BLANCZOS));
     DM_CHECK(h->alloc(&B.hb, (size_t)mm, G_BLANCZOS));
     DM_CHECK(h->alloc(&B.flag, 1, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.H1, (size_t)dm_bstep_hcopies() * B.ldpart * b, G_BLANCZOS));
+    DM_CHECK(h->alloc(&B.Gacc, (size_t)3 * b * b, G_BLANCZOS));
     DM_CUDA(cudaMemsetAsync(B.Z, 0, sizeof(float) * (size_t)b * h->lz.ldv, h->stream));
     B.b = b;
     return DM_OK;
@@ -728,10 +791,136 @@ int ensure_lanczos(dm_ctx *h) {
     return DM_OK;
 }
 
+// Block Lanczos with b <= 4 vectors per step (FP32 near field, cached blocks) when the b-wide
+// upper tree fits the cluster pass: per step the three chained launches of the narrow-block
+// H-matvec and one cooperative step kernel (CGS2 + CholQR2, FP64 coefficients); Rayleigh-Ritz
+// on the projected matrix at the checks, as eigs_block. *done = false: not applicable.
+int eigs_narrow(dm_ctx *h, int k, double *evals, float *evecs, bool *done) {
+    *done = false;
+    const int b = h->cfg.block_size;
+    if (b < 2 || b > dm_bstep_max_b() || h->cfg.block_precision != DM_PREC_FP32 || h->cfg.shared_device) return DM_OK;
+    bool fits = false;
+    DM_CHECK(ensure_nb(h, b, &fits));
+    if (!fits) return DM_OK;
+    DmLanczos &Lz = h->lz;
+    int m_cap = Lz.m_max;
+    if (m_cap > h->N) m_cap = (int)h->N;
+    const int jmax = m_cap / b - 1;
+    if (jmax < 1 || (jmax * b) < k) return fail(DM_EINVAL, "m_max too small for block_size %d and k %d", b, k);
+    DM_CHECK(ensure_block_lanczos(h, b));
+    int sms = 0;
+    DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    *done = true;
+    PhaseTimer t(h->stream);
+    DmBlockLanczos &B = h->bl;
+    const DmHmat H = h->hmat();
+    const int64_t hstride = (int64_t)B.ldpart * b;
+    DM_CUDA(cudaMemsetAsync(B.H, 0, sizeof(double) * (size_t)dm_bstep_hcopies() * hstride, h->stream));
+    DM_CUDA(cudaMemsetAsync(B.H1, 0, sizeof(double) * (size_t)dm_bstep_hcopies() * hstride, h->stream));
+    DM_CUDA(cudaMemsetAsync(B.Gacc, 0, sizeof(double) * 3 * b * b, h->stream));
+    DM_CUDA(cudaMemsetAsync(Lz.bar, 0, sizeof(unsigned), h->stream));
+    DM_CUDA(dm_bl_random_block(Lz, B, h->perm, h->cfg.seed, h->stream));
+    unsigned bar_base = 0;
+    int par = 0;
+    double *G1 = B.Gacc, *G2 = B.Gacc + b * b;
+    // V_0 = CholQR2 of the random block (no basis to orthogonalise against)
+    DM_CUDA(dm_bstep(b, Lz.V, Lz.ldv, 0, 0, B.Z, B.H, B.H1, hstride, G1, G2, par, nullptr, Lz.m_max, B.Bacc, B.flag,
+                     Lz.bar, bar_base, Lz.err, sms, h->stream));
+    bar_base += 3u * (unsigned)sms;
+    par ^= 1;
+    std::vector<double> th(k), rs(k);
+    int m = 0, flag = 0;
+    bool converged = false, ritz_current = false;
+    const bool prof = h->cfg.profile != 0;
+    std::vector<cudaEvent_t> ev_mv;
+    const int every = h->cfg.check_every / b > 2 ? h->cfg.check_every / b : 2;
+    int since = 0;
+    for (int j = 0; j < jmax; ++j) {
+        if (prof) {
+            cudaEvent_t e0, e1;
+            DM_CUDA(cudaEventCreate(&e0));
+            DM_CUDA(cudaEventCreate(&e1));
+            ev_mv.push_back(e0);
+            ev_mv.push_back(e1);
+            DM_CUDA(cudaEventRecord(e0, h->stream));
+        }
+        DM_CUDA(dm_hmatvec_nb(H, h->nbt, b, Lz.V + (size_t)j * b * Lz.ldv, Lz.ldv, B.Z, Lz.ldv, true, h->stream));
+        if (prof) DM_CUDA(cudaEventRecord(ev_mv.back(), h->stream));
+        DM_CUDA(dm_bstep(b, Lz.V, Lz.ldv, (j + 1) * b, (j + 1) * b, B.Z, B.H, B.H1, hstride, G1, G2, par, B.T,
+                         Lz.m_max, B.Bacc, B.flag, Lz.bar, bar_base, Lz.err, sms, h->stream));
+        bar_base += 3u * (unsigned)sms;
+        par ^= 1;
+        m = (j + 1) * b;
+        ritz_current = false;
+        ++since;
+        const bool last = j + 1 == jmax;
+        if (m >= 2 * k && (since >= every || last)) {
+            since = 0;
+            DM_CUDA(dm_bl_ritz(Lz, B, m, k, h->stream));
+            DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaMemcpyAsync(rs.data(), Lz.resid, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaMemcpyAsync(&flag, B.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            ritz_current = true;
+            const double scale = std::fabs(th[0]) > 0 ? std::fabs(th[0]) : 1.0;
+            bool ok = true;
+            for (int i = 0; i < k; ++i)
+                if (!(rs[i] <= h->cfg.conv_tol * scale)) ok = false;
+            if (ok || flag) {
+                converged = ok;
+                break;
+            }
+        }
+    }
+    if (!ritz_current) {
+        DM_CUDA(dm_bl_ritz(Lz, B, m, k, h->stream));
+        DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+    }
+    DM_CUDA(dm_lanczos_phi(Lz, m, k, h->perm, h->evecs, h->stream));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    {
+        int err = 0;
+        DM_CUDA(cudaMemcpyAsync(&err, Lz.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        DM_CUDA(cudaStreamSynchronize(h->stream));
+        if (err) {
+            DM_CUDA(cudaMemsetAsync(Lz.err, 0, sizeof(int), h->stream));
+            DM_CUDA(cudaStreamSynchronize(h->stream));
+            return fail(DM_ETIMEOUT, "a grid barrier of the block Lanczos step gave up waiting");
+        }
+    }
+    if (is_device_ptr(evals))
+        DM_CUDA(cudaMemcpyAsync(evals, th.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+    else
+        for (int i = 0; i < k; ++i) evals[i] = th[i];
+    if (evecs) DM_CHECK(copy_out(h, evecs, h->evecs, sizeof(float) * (size_t)k * h->N));
+    DM_CUDA(cudaStreamSynchronize(h->stream));
+    h->stats.matvec_calls = 0;
+    h->stats.ms_matvec = 0.f;
+    for (size_t e = 0; e + 1 < ev_mv.size(); e += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev_mv[e], ev_mv[e + 1]) == cudaSuccess) {
+            h->stats.ms_matvec += ms;
+            h->stats.matvec_calls += 1;
+        }
+        cudaEventDestroy(ev_mv[e]);
+        cudaEventDestroy(ev_mv[e + 1]);
+    }
+    h->last_k = k;
+    h->stats.lanczos_iters = m;
+    h->stats.converged = converged ? 1 : 0;
+    h->stats.ms_eigs = t.stop();
+    return converged ? DM_OK : fail(DM_ENOCONV, "block Lanczos did not converge in %d basis vectors", m);
+}
+
 // dm_eigs with block Lanczos (cfg.block_size = b >= 2): per step one block H-matvec of b
 // columns, block CGS2 and CholQR2; Rayleigh-Ritz on the projected matrix every check.
 int eigs_block(dm_ctx *h, int k, double *evals, float *evecs) {
     const int b = h->cfg.block_size;
+    {
+        bool done = false;
+        const int st = eigs_narrow(h, k, evals, evecs, &done);
+        if (done || st != DM_OK) return st;
+    }
     if (b > dm_block_lanczos_max_b()) return fail(DM_EINVAL, "block_size must be <= %d", dm_block_lanczos_max_b());
     DmLanczos &Lz = h->lz;
     int m_cap = Lz.m_max;
@@ -1145,7 +1334,13 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs) {
         dx = h->io_x;
     }
     if (!yd) dy = h->io_y;
-    if (h->compressed && nrhs >= 2) {
+    bool narrow = false;
+    if (h->compressed && nrhs >= 2 && nrhs <= 4 && h->cfg.block_precision == DM_PREC_FP32)
+        DM_CHECK(ensure_nb(h, nrhs, &narrow));
+    if (narrow) {
+        // 2..4 columns through the single-vector form's three chained launches
+        DM_CUDA(dm_hmatvec_nb(h->hmat(), h->nbt, nrhs, dx, h->N, dy, h->N, false, h->stream));
+    } else if (h->compressed && nrhs >= 2) {
         // block H-matvec: every stored operand is read once per panel of columns
         const bool tc = h->cfg.block_precision == DM_PREC_TF32 && h->near_mode == DM_NEAR_CACHED;
         if (tc && !dm_tc_available()) return fail(DM_ECUDA, "the driver does not provide cuTensorMapEncodeTiled");

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 
 #include "dmaps.h"
@@ -107,6 +109,43 @@ __device__ __forceinline__ void dm_cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void dm_cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident) with a bounded wait:
+// block threads 0 arrive on *ctr and poll it (acquire) until it reaches `target`; a block
+// that polls more than spin_limit times, or sees *err raised, raises *err and reports
+// false, and the kernel returns. Counters grow monotonically within a launch sequence.
+constexpr long long kBarrierSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned dm_ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// returns false when the barrier timed out (in this or another block)
+__device__ __forceinline__ bool grid_barrier(unsigned *ctr, unsigned target, int *err,
+                                             long long spin_limit = kBarrierSpinLimit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        int ok = 1;
+        long long spins = 0;
+        while (dm_ld_acquire_gpu(ctr) < target) {
+            if (++spins > spin_limit || *((volatile int *)err) != 0) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // exp2 on the MUFU unit (PTX ex2.approx.ftz.f32: documented max error ~2 ulp over its range)
@@ -281,6 +320,32 @@ cudaError_t dm_tree_image(const DmHmat &H, cudaStream_t st);
 // largest shared-memory budget (16 needs the non-portable cluster size)
 bool dm_tree_cluster_supported(int ctas);
 
+// k_hnb.cu -- H-matvec of a narrow block (2 <= nb <= 4 columns) through the three chained
+// launches of the single-vector form, the cluster pass holding nb-wide skeleton vectors
+struct DmNbTree {
+    int nb;                 // columns (0: not built)
+    int ls;                 // cut level of the cluster (2^ls CTAs)
+    int smem;               // dynamic shared memory per CTA of the cluster pass (bytes)
+    const int4 *lay;        // per node {P, B, pair slot, scratch} offsets (floats) in its owner's image
+    const int2 *own;        // per node: offsets of its own w and u (nb-wide rows) in its owner's image
+    const int *owner;       // per node: CTA of the cluster that holds it
+    float *img;             // per CTA: metadata, operands, vector slots
+    const int *img_off;     // 2^ls + 1 image offsets (floats, multiples of 4)
+    float *what, *uhat;     // per node max_rank x nb (row t, column c at t nb + c): leaf w in, leaf u out
+};
+struct DmNbLayout {
+    std::vector<int4> lay;
+    std::vector<int2> own;
+    std::vector<int> owner;
+    std::vector<int> img_off;
+    int ls = 0, smem = 0;
+};
+bool dm_nb_tree_layout(const std::vector<int32_t> &rk, int L, int nb, int budget_floats, DmNbLayout &out);
+cudaError_t dm_nb_tree_image(const DmHmat &H, const DmNbTree &T, cudaStream_t st);
+// Y = K~ X for nb columns (column strides ldx, ldy; original point order unless permuted)
+cudaError_t dm_hmatvec_nb(const DmHmat &H, const DmNbTree &T, int nb, const float *x, int64_t ldx, float *y,
+                          int64_t ldy, bool permuted, cudaStream_t st);
+
 // k_hblock.cu -- H-matvec of a block of right-hand sides
 struct DmBlockWork {
     int nb_max;           // columns per call
@@ -354,12 +419,29 @@ struct DmBlockLanczos {
     double *T, *W;        // m_max x m_max (column-major): projected matrix, tridiagonalisation work
     double *hb;           // m_max Householder coefficients
     int *flag;            // set when a block lost rank (breakdown)
+    double *H1;           // ldpart x b second-pass coefficients of the one-launch step (b <= 4)
+    double *Gacc;         // 3 x b x b Gram accumulators of the one-launch step (G1, G2 by parity)
 };
 int dm_block_lanczos_max_b();
 cudaError_t dm_bl_start(DmLanczos &Lz, DmBlockLanczos &B, const int32_t *perm, uint64_t seed, cudaStream_t st);
+// the random start block in B.Z (seeded, one key per column), T and the breakdown flag cleared
+cudaError_t dm_bl_random_block(DmLanczos &Lz, DmBlockLanczos &B, const int32_t *perm, uint64_t seed,
+                               cudaStream_t st);
 cudaError_t dm_bl_cholqr(DmLanczos &Lz, DmBlockLanczos &B, int j, bool next_block, cudaStream_t st);
 cudaError_t dm_bl_orth(DmLanczos &Lz, DmBlockLanczos &B, int j, cudaStream_t st);
 cudaError_t dm_bl_ritz(DmLanczos &Lz, DmBlockLanczos &B, int m, int k, cudaStream_t st);
+// k_bstep.cu -- one block-Lanczos step for b <= dm_bstep_max_b() in one cooperative launch of
+// `blocks` 512-thread blocks (one per SM): CGS2 of Z against V[:, 0:ncols), CholQR2, the new
+// block written to V[:, out:out+b), T(0:ncols, out-b:out) = the projection coefficients,
+// Bj = the block's R factor. H0, H1 (ncols x b), G1 (b x b) zero on entry and on return;
+// G2 two b x b buffers (the one of parity `par` used, the other cleared); `bar` counts
+// arrivals monotonically from bar_base (three barriers of `blocks` arrivals each).
+// H0, H1: dm_bstep_hcopies() copies of ncols x b each, `hstride` doubles apart.
+int dm_bstep_max_b();
+int dm_bstep_hcopies();
+cudaError_t dm_bstep(int b, float *V, int64_t ldv, int ncols, int out, const float *Z, double *H0, double *H1,
+                     int64_t hstride, double *G1, double *G2, int par, double *T, int ldT, double *Bj, int *flag,
+                     unsigned *bar, unsigned bar_base, int *err, int blocks, cudaStream_t st);
 cudaError_t dm_launch_coords(const float *evecs, const double *theta, const double *dg, int64_t N, int k, int t,
                              float *psi, cudaStream_t st);
 

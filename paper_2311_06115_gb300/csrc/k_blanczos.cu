@@ -194,32 +194,23 @@ __global__ void bl_scale_kernel(const float *__restrict__ Z, int64_t ldz, int b,
 }
 
 // ---- Householder tridiagonalisation of the symmetric T (upper triangle, m x m) in FP64,
-// one CTA: W = Q^T T Q with alpha = diag, beta = subdiagonal; the reflector of step k
-// (I - hb_k v v^T, v on rows k+1..m-1) is left in column k of W below the diagonal.
-constexpr int kTrThreads = 512;
-constexpr int kTrSmemMax = 160;  // largest m whose working matrix fits in shared memory
-
-__device__ double cta_sum_d(double v, double *red) {
-    v = dm_warp_sum_d(v);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w];
-    return s;
-}
+// one CTA of 1024 threads: W = Q^T T Q with alpha = diag, beta = subdiagonal; the reflector
+// of step k (I - hb_k v v^T, v on rows k+1..m-1) is left in column k of W below the diagonal.
+// Per step: the column norm and the dot p.v in one warp (no block-wide reduction), the
+// product p = W_sub v with a warp per row (lanes over the row, a shuffle sum), the rank-2
+// update over all threads; four barriers per step.
+constexpr int kTrThreads = 1024;
+constexpr int kTrSmemMax = 144;  // largest m whose working matrix fits in shared memory
 
 __global__ void __launch_bounds__(kTrThreads) bl_tridiag_kernel(const double *__restrict__ T, int ldT, int m,
                                                                 double *Wg, int ldwg, double *__restrict__ alpha,
                                                                 double *__restrict__ beta,
                                                                 double *__restrict__ hb, int in_smem) {
-    extern __shared__ double sv[];  // v (m), p (m), then the m x m working matrix when in_smem
-    __shared__ double red[32];
-    double *v = sv, *p = sv + m;
-    // the working matrix lives in shared memory when it fits (m <= kTrSmemMax), else in W
-    double *W = in_smem ? sv + 2 * m : Wg;
+    extern __shared__ double sv[];  // v (m), p (m), scalars (4), then the m x m working matrix
+    double *v = sv, *p = sv + m, *sc = sv + 2 * m;
+    double *W = in_smem ? sv + 2 * m + 4 : Wg;
     const int ldw = in_smem ? m : ldwg;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int r = e % m, c = e / m;
         W[(size_t)c * ldw + r] = r <= c ? T[(size_t)c * ldT + r] : T[(size_t)r * ldT + c];
@@ -228,44 +219,57 @@ __global__ void __launch_bounds__(kTrThreads) bl_tridiag_kernel(const double *__
     for (int k = 0; k + 2 < m; ++k) {
         const int n = m - k - 1;  // trailing size
         double *col = W + (size_t)k * ldw + (k + 1);
-        double ss = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const double x = col[i];
-            v[i] = x;
-            ss += x * x;
+        if (warp == 0) {
+            double ss = 0.0;
+            for (int i = lane; i < n; i += 32) {
+                const double x = col[i];
+                v[i] = x;
+                ss = fma(x, x, ss);
+            }
+            ss = dm_warp_sum_d(ss);
+            if (lane == 0) {
+                const double x0 = col[0];
+                const double xn = sqrt(ss);
+                const double al = x0 >= 0.0 ? -xn : xn;
+                const double vnorm2 = ss - x0 * x0 + (x0 - al) * (x0 - al);
+                const double bk = vnorm2 > 0.0 ? 2.0 / vnorm2 : 0.0;
+                v[0] = x0 - al;
+                alpha[k] = W[(size_t)k * ldw + k];
+                beta[k] = vnorm2 > 0.0 ? al : x0;
+                hb[k] = bk;
+                sc[0] = bk;
+            }
         }
-        const double xnorm2 = cta_sum_d(ss, red);
-        const double x0 = v[0];
-        const double xn = sqrt(xnorm2);
-        const double al = x0 >= 0.0 ? -xn : xn;
-        const double vnorm2 = xnorm2 - x0 * x0 + (x0 - al) * (x0 - al);
-        const double bk = vnorm2 > 0.0 ? 2.0 / vnorm2 : 0.0;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            v[0] = x0 - al;
-            alpha[k] = W[(size_t)k * ldw + k];
-            beta[k] = vnorm2 > 0.0 ? al : x0;
-            hb[k] = bk;
-        }
-        __syncthreads();
+        const double bk = sc[0];
         if (bk != 0.0) {
-            // p = bk * W_sub v (symmetric, rows k+1..m-1)
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            // p = bk W_sub v: eight lanes per row i (W symmetric: column k+1+i of the
+            // sub-block), three shuffle steps; few FP64 instructions per row (the FP64 pipe
+            // of this part is narrow, so shuffle-and-add trees are kept short)
+            for (int base = 4 * warp; base < n; base += 4 * nw) {  // warp-uniform bound
+                const int i = base + (lane >> 3), l8 = lane & 7;
                 double s = 0.0;
-                const double *wr = W + (size_t)(k + 1) * ldw + (k + 1 + i);  // column k+1, row k+1+i
-                for (int j = 0; j < n; ++j) s += wr[(size_t)j * ldw] * v[j];
-                p[i] = bk * s;
+                if (i < n) {
+                    const double *wr = W + (size_t)(k + 1 + i) * ldw + (k + 1);
+                    for (int j = l8; j < n; j += 8) s = fma(wr[j], v[j], s);
+                }
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                if (i < n && l8 == 0) p[i] = bk * s;
             }
             __syncthreads();
-            double pv = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) pv += p[i] * v[i];
-            const double K = 0.5 * bk * cta_sum_d(pv, red);
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] -= K * v[i];  // w
+            if (warp == 0) {
+                double pv = 0.0;
+                for (int i = lane; i < n; i += 32) pv = fma(p[i], v[i], pv);
+                const double K = 0.5 * bk * dm_warp_sum_d(pv);
+                for (int i = lane; i < n; i += 32) p[i] -= K * v[i];  // w
+            }
             __syncthreads();
             for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
                 const int i = e % n, j = e / n;
-                W[(size_t)(k + 1 + j) * ldw + (k + 1 + i)] -= v[i] * p[j] + p[i] * v[j];
+                double *wij = W + (size_t)(k + 1 + j) * ldw + (k + 1 + i);
+                *wij = fma(-v[i], p[j], fma(-p[i], v[j], *wij));
             }
         }
         // keep the reflector in column k below the diagonal
@@ -293,37 +297,48 @@ __global__ void __launch_bounds__(kTrThreads) bl_tridiag_kernel(const double *__
 
 // Eigenvectors of T from those of the tridiagonal (Y, columns of length m): y <- Q y with
 // Q = H_0 H_1 ... H_{m-3}; then the residual bound |B_j y_j| (y_j = last b entries) and
-// the FP32 copy Yf (m x k, row-major) for the Ritz-vector product. One CTA per vector.
-__global__ void __launch_bounds__(256) bl_backtransform_kernel(const double *__restrict__ W, int ldw,
-                                                               const double *__restrict__ hb, int m, int k,
-                                                               double *__restrict__ Y, int ldy,
-                                                               float *__restrict__ Yf,
-                                                               const double *__restrict__ Bj, int b,
-                                                               double *__restrict__ resid) {
-    __shared__ double red[32];
-    extern __shared__ double ys[];  // m
-    const int iv = blockIdx.x;
-    double *y = Y + (size_t)iv * ldy;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = y[i];
+// the FP32 copy Yf (m x k, row-major) for the Ritz-vector product. A warp per vector, the
+// reflectors staged in shared memory once per CTA (from global memory when they do not fit).
+constexpr int kBtWarps = 8;
+__global__ void __launch_bounds__(32 * kBtWarps) bl_backtransform_kernel(const double *__restrict__ W, int ldw,
+                                                                         const double *__restrict__ hb, int m, int k,
+                                                                         double *__restrict__ Y, int ldy,
+                                                                         float *__restrict__ Yf,
+                                                                         const double *__restrict__ Bj, int b,
+                                                                         double *__restrict__ resid, int staged) {
+    extern __shared__ double bsm[];  // staged: reflectors (m x m, column-major); then kBtWarps x m vectors
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double *Wr = staged ? bsm : W;
+    const int ldr = staged ? m : ldw;
+    double *ys = bsm + (staged ? (size_t)m * m : 0) + (size_t)warp * m;
+    if (staged) {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int r = e % m, c = e / m;
+            bsm[e] = r > c ? W[(size_t)c * ldw + r] : 0.0;
+        }
+    }
+    const int iv = blockIdx.x * kBtWarps + warp;
+    if (iv < k)
+        for (int i = lane; i < m; i += 32) ys[i] = Y[(size_t)iv * ldy + i];
     __syncthreads();
+    if (iv >= k) return;
     for (int kk = m - 3; kk >= 0; --kk) {
         const double bk = hb[kk];
         if (bk == 0.0) continue;
         const int n = m - kk - 1;
-        const double *v = W + (size_t)kk * ldw + (kk + 1);
+        const double *v = Wr + (size_t)kk * ldr + (kk + 1);
         double s = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * ys[kk + 1 + i];
-        const double f = bk * cta_sum_d(s, red);
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) ys[kk + 1 + i] -= f * v[i];
-        __syncthreads();
+        for (int i = lane; i < n; i += 32) s = fma(v[i], ys[kk + 1 + i], s);
+        const double f = bk * dm_warp_sum_d(s);
+        for (int i = lane; i < n; i += 32) ys[kk + 1 + i] -= f * v[i];
+        __syncwarp();
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        y[i] = ys[i];
+    for (int i = lane; i < m; i += 32) {
+        Y[(size_t)iv * ldy + i] = ys[i];
         Yf[(size_t)i * k + iv] = (float)ys[i];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    __syncwarp();
+    if (lane == 0) {
         double rr = 0.0;
         for (int r = 0; r < b; ++r) {
             double t = 0.0;
@@ -338,13 +353,19 @@ __global__ void __launch_bounds__(256) bl_backtransform_kernel(const double *__r
 
 int dm_block_lanczos_max_b() { return kBlMaxB; }
 
-cudaError_t dm_bl_start(DmLanczos &Lz, DmBlockLanczos &B, const int32_t *perm, uint64_t seed, cudaStream_t st) {
+cudaError_t dm_bl_random_block(DmLanczos &Lz, DmBlockLanczos &B, const int32_t *perm, uint64_t seed,
+                               cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(B.T, 0, sizeof(double) * (size_t)Lz.m_max * Lz.m_max, st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(B.flag, 0, sizeof(int), st)) != cudaSuccess) return e;
     bl_start_kernel<<<dim3(nblk(Lz.N, 256), (unsigned)B.b), 256, 0, st>>>(perm, Lz.N, B.b, seed, B.Z, Lz.ldv);
     dm_count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t dm_bl_start(DmLanczos &Lz, DmBlockLanczos &B, const int32_t *perm, uint64_t seed, cudaStream_t st) {
+    cudaError_t e = dm_bl_random_block(Lz, B, perm, seed, st);
+    if (e != cudaSuccess) return e;
     // V_0 = Z R^-1 by CholQR2 (no T entries)
     return dm_bl_cholqr(Lz, B, 0, false, st);
 }
@@ -406,7 +427,7 @@ cudaError_t dm_bl_orth(DmLanczos &Lz, DmBlockLanczos &B, int j, cudaStream_t st)
 
 cudaError_t dm_bl_ritz(DmLanczos &Lz, DmBlockLanczos &B, int m, int k, cudaStream_t st) {
     const int in_smem = m <= kTrSmemMax ? 1 : 0;
-    const size_t sm = sizeof(double) * (2 * (size_t)m + (in_smem ? (size_t)m * m : 0));
+    const size_t sm = sizeof(double) * (2 * (size_t)m + 4 + (in_smem ? (size_t)m * m : 0));
     cudaError_t e = dm_allow_smem((const void *)bl_tridiag_kernel, sm);
     if (e != cudaSuccess) return e;
     bl_tridiag_kernel<<<1, kTrThreads, sm, st>>>(B.T, Lz.m_max, m, B.W, Lz.m_max, Lz.alpha, Lz.beta, B.hb, in_smem);
@@ -414,8 +435,11 @@ cudaError_t dm_bl_ritz(DmLanczos &Lz, DmBlockLanczos &B, int m, int k, cudaStrea
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = dm_lanczos_ritz(Lz, m, k, 0.0, st)) != cudaSuccess) return e;
     if ((e = dm_lanczos_tvecs(Lz, m, k, st)) != cudaSuccess) return e;
-    bl_backtransform_kernel<<<k, 256, sizeof(double) * (size_t)m, st>>>(B.W, Lz.m_max, B.hb, m, k, Lz.Y,
-                                                                        Lz.m_max, Lz.Yf, B.Bacc, B.b, Lz.resid);
+    const int staged = m <= kTrSmemMax ? 1 : 0;
+    const size_t smb = sizeof(double) * ((staged ? (size_t)m * m : 0) + (size_t)kBtWarps * m);
+    if ((e = dm_allow_smem((const void *)bl_backtransform_kernel, smb)) != cudaSuccess) return e;
+    bl_backtransform_kernel<<<(k + kBtWarps - 1) / kBtWarps, 32 * kBtWarps, smb, st>>>(
+        B.W, Lz.m_max, B.hb, m, k, Lz.Y, Lz.m_max, Lz.Yf, B.Bacc, B.b, Lz.resid, staged);
     dm_count_launches(1);
     return cudaGetLastError();
 }

@@ -251,11 +251,20 @@ __global__ void __launch_bounds__(kTreeThreads) tree_kernel(const __grid_constan
     dm_cp_async_wait_all();
     __syncthreads();
     {
+        // a lane's loads are all issued before the first store (one round trip per row)
         int first, count;
         level_nodes(g, ls, L, &first, &count);
         for (int i = warp; i < count; i += nw) {
-            const int n = first + i, w = own_w(n);
-            for (int j = lane; j < rk[n]; j += 32) sm[w + j] = __ldcg(H.what + (size_t)n * R + j);
+            const int n = first + i, w = own_w(n), len = rk[n];
+            const float *src = H.what + (size_t)n * R;
+            for (int base = lane; base < len; base += 256) {
+                float t[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) t[u] = base + 32 * u < len ? __ldcg(src + base + 32 * u) : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (base + 32 * u < len) sm[w + base + 32 * u] = t[u];
+            }
         }
     }
     __syncthreads();

@@ -67,38 +67,6 @@ __global__ void normalize_kernel(const float *__restrict__ z, int64_t N, const d
 // blocks that fit beside other solves' kernels)
 constexpr int kStepThreadsCoop = 512;
 constexpr int kStepThreadsPhased = 256;
-constexpr long long kBarrierSpinLimit = 1ll << 22;
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// returns false when the barrier timed out (in this or another block)
-__device__ bool grid_barrier(unsigned *ctr, unsigned target, int *err, long long spin_limit = kBarrierSpinLimit) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-        int ok = 1;
-        long long spins = 0;
-        while (ld_acquire_gpu(ctr) < target) {
-            if (++spins > spin_limit || *((volatile int *)err) != 0) {
-                ok = 0;
-                atomicExch(err, 1);
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // sum of v[u] over the 32 lanes, scattered: lanes with (lane & 3) == 0 end up holding
 // the total for u = 4 b4 + 2 b3 + b2 (b_k = bit k of the lane); returns that value
 __device__ __forceinline__ float reduce_scatter8(float (&v)[8], int lane) {

@@ -154,3 +154,24 @@ def test_fullsize_hmatvec_replay_sixteen_cta_cluster(dm, ref, H_tight):
     y2 = dm.dm_matvec(h, x)
     assert np.array_equal(y, y2)
     dm.dm_destroy(h)
+
+
+@pytest.mark.parametrize("which", ["bench", "tight"])
+def test_fullsize_narrow_block_replay(dm, ref, H_bench, H_tight, which):
+    """Four right-hand sides through the narrow-block chain at full size: tol 1e-5 (a cluster
+    of 8 CTAs) and tol 3e-7 (the 4-wide upper tree needs 16 CTAs with the nodes above the
+    cut spread by load), element-wise against the oracle's evaluation of the same structure."""
+    H = H_bench if which == "bench" else H_tight
+    h = dm.dm_create(ref["X"], eps=ref["eps"])
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    x = np.asfortranarray(synth.random_rhs(N, 4, seed=35).astype(np.float32))
+    y = dm.dm_matvec(h, x)
+    l0 = dm.dm_kernel_launches()
+    y2 = dm.dm_matvec(h, x)
+    assert dm.dm_kernel_launches() - l0 == 3
+    assert np.array_equal(y, y2)
+    yr = O.hmatvec(ref["X"], ref["eps"], ref["s"], H, x.astype(np.float64))
+    err = np.abs(y - yr).max() / np.abs(x).max()
+    print(f"narrow block ({which}): max |y - y_oracle| / max|x| = {err:.3e}")
+    assert err < 1e-5, err
+    dm.dm_destroy(h)

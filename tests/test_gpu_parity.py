@@ -185,6 +185,34 @@ def test_block_hmatvec_replay_matches_oracle(dm, mode, n, leaf, rank, tol, nrhs)
     dm.dm_destroy(h)
 
 
+@pytest.mark.parametrize("n,leaf,rank,tol,nrhs", [(2048, 128, 64, 1e-5, 4), (3001, 256, 48, 1e-4, 3),
+                                                  (1500, 100, 40, 1e-3, 2), (5000, 128, 64, 1e-5, 4),
+                                                  (700, 64, 64, 0.0, 4)])
+def test_narrow_block_hmatvec_replay_matches_oracle(dm, n, leaf, rank, tol, nrhs):
+    """2..4 right-hand sides through the three chained launches of the single-vector form
+    (leaf N2S, the one-cluster tree pass with nrhs-wide skeleton vectors, the near stream with
+    the leaf S2N), on the oracle's structure, element-wise against the oracle's Eq. 2.18
+    evaluation and column by column against the single-vector path."""
+    X = _scurve(n, 19)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, leaf, tol, rank)
+    h = dm.dm_create(X, eps=eps, cfg=dm.dm_config_default(near_mode=dm.DM_NEAR_CACHED))
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    x = np.asfortranarray(synth.random_rhs(n, nrhs, seed=10).astype(np.float32))
+    y = dm.dm_matvec(h, x)
+    l0 = dm.dm_kernel_launches()
+    y2 = dm.dm_matvec(h, x)
+    assert dm.dm_kernel_launches() - l0 == 3, "the narrow-block path (three chained launches) did not run"
+    assert np.array_equal(y, y2)
+    yr = O.hmatvec(X, eps, s, H, x.astype(np.float64))
+    assert _rel_inf(y, yr, np.abs(x).max()) < 1e-5
+    for c in range(nrhs):
+        y1 = dm.dm_matvec(h, np.ascontiguousarray(x[:, c]))
+        assert _rel_inf(y[:, c], y1, np.abs(x[:, c]).max()) < 1e-5
+    dm.dm_destroy(h)
+
+
 @pytest.mark.parametrize("n,leaf,rank,tol,nrhs", [(3001, 256, 48, 1e-4, 16), (2048, 128, 64, 1e-5, 100),
                                                   (700, 64, 64, 0.0, 300), (5000, 512, 64, 1e-5, 33)])
 def test_block_hmatvec_tf32_tensor_cores(dm, n, leaf, rank, tol, nrhs):
