@@ -278,48 +278,63 @@ def accuracy_errors(ref: dict, ev, V, psi=None, t: int = 1) -> dict:
     return out
 
 
-def accuracy_run(dm, torch, stream, X, W, steps: int = 5, tols=None) -> dict:
-    """Eigenvalue, subspace-angle and diffusion-coordinate errors of the single-vector FP32 path
-    against the FP64 reference at the workload's tolerance (1e-5) and at 3e-7 (the loosest
-    tolerance whose eigenvalues stay within 1e-5 relative of FP64 on this workload), each with
-    its own throughput (create + compress + eigs + destroy, points in HBM, CUDA events)."""
+def accuracy_run(dm, torch, stream, X, W, steps: int = 5, tols=None, blocks=(0, 4)) -> dict:
+    """The accuracy target against FP64, per compression tolerance and eigensolver: the
+    single-vector FP32 Lanczos (block 0) and block Lanczos with 4 vectors per step (FP32
+    H-matvec of 4 right-hand sides, FP64 Gram-Schmidt and Cholesky coefficients, FP64
+    Rayleigh-Ritz), each with its eigenvalue, subspace-angle and diffusion-coordinate errors
+    against the FP64 reference and its throughput (create + compress + eigs + destroy, points
+    in HBM, CUDA events), at the workload's tolerance (1e-5) and at 3e-7 (the loosest
+    tolerance whose eigenvalues stay within 1e-5 relative of FP64 on this workload)."""
     import numpy as np
 
     Xd = torch.from_numpy(X).cuda()
     res = {}
     tols = tols or (W["tol"], 3e-7)
     for tol in tols:
-        cfg = dm.dm_config_default(stream=stream.cuda_stream)
-        ts = []
-        for i in range(steps + 2):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            h = dm.dm_create(Xd, eps=-1.0, alpha=1.0, cfg=cfg)
-            dm.dm_compress(h, tol, W["leaf"], W["rank"])
-            ev, V, conv = dm.dm_eigs(h, W["k"], evecs=True, device_out=True)
-            if i == steps + 1:
+        for b in blocks:
+            cfg = dm.dm_config_default(stream=stream.cuda_stream, block_size=b)
+            ts, te = [], []
+            for i in range(steps + 2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h = dm.dm_create(Xd, eps=-1.0, alpha=1.0, cfg=cfg)
+                dm.dm_compress(h, tol, W["leaf"], W["rank"])
+                ev, V, conv = dm.dm_eigs(h, W["k"], evecs=True, device_out=True)
                 st = dm.dm_get_stats(h)
-                psi = dm.dm_coords(h, W["k"], 1)
-                Vh = V.cpu().numpy()
-            dm.dm_destroy(h)
-            e1.record(stream)
-            e1.synchronize()
-            if i >= 2:
-                ts.append(e0.elapsed_time(e1))
-        ms = statistics.median(ts)
-        res[f"tol_{tol:g}"] = {"ms_per_solve": ms, "eigenpairs_per_s": W["k"] / (ms * 1e-3),
-                               "converged": bool(conv), "lanczos_iters": st["lanczos_iters"],
-                               "ranks": {"min": st["rank_min"], "max": st["rank_max"],
-                                         "mean": round(st["rank_mean"], 2)},
-                               "phases_ms": {key: round(float(st[key]), 3) for key in
-                                             ("ms_create", "ms_tree", "ms_skeleton", "ms_pack", "ms_eigs")},
-                               "hmatvec_path": st["hmatvec_path"],
-                               "_ev": np.asarray(ev), "_V": Vh, "_psi": psi}
+                if i == steps + 1:
+                    psi = dm.dm_coords(h, W["k"], 1)
+                    Vh = V.cpu().numpy()
+                dm.dm_destroy(h)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= 2:
+                    ts.append(e0.elapsed_time(e1))
+                    te.append(st["ms_eigs"])
+            ms = statistics.median(ts)
+            res[f"tol_{tol:g}_block{b}"] = {
+                "solver": "single-vector Lanczos, FP32 H-matvec" if b == 0 else
+                          f"block Lanczos, {b} vectors per step: FP32 H-matvec of {b} right-hand sides, FP64 "
+                          "Gram-Schmidt/Cholesky coefficients and Rayleigh-Ritz",
+                "ms_per_solve": ms, "eigenpairs_per_s": W["k"] / (ms * 1e-3), "ms_eigs": statistics.median(te),
+                "converged": bool(conv), "basis_vectors": st["lanczos_iters"],
+                "ranks": {"min": st["rank_min"], "max": st["rank_max"], "mean": round(st["rank_mean"], 2)},
+                "phases_ms": {key: round(float(st[key]), 3) for key in
+                              ("ms_create", "ms_tree", "ms_skeleton", "ms_pack", "ms_eigs")},
+                "hmatvec_path": st["hmatvec_path"],
+                "_ev": np.asarray(ev), "_V": Vh, "_psi": psi}
     ref = fp64_reference(X, W)
     for key, r in res.items():
         r.update(accuracy_errors(ref, r.pop("_ev"), r.pop("_V"), r.pop("_psi")))
         r["meets_1e-5_rel_and_1e-3_rad"] = bool(r["max_rel_eigenvalue_error"] <= 1e-5
                                                and r["subspace_angle_rad"] <= 1e-3)
+    for tol in tols:
+        base = res.get(f"tol_{tol:g}_block0")
+        for b in blocks:
+            r = res.get(f"tol_{tol:g}_block{b}")
+            if b and base and r:
+                r["eigs_speedup_vs_single_vector"] = base["ms_eigs"] / r["ms_eigs"]
+                r["solve_speedup_vs_single_vector"] = base["ms_per_solve"] / r["ms_per_solve"]
     res["reference"] = ref["what"]
     res["reference_s"] = round(ref["seconds"], 1)
     res["note"] = ("errors against FP64 combine the approximation of S by the H-matrix (set by tol: Eq. 1.1 "
@@ -374,11 +389,15 @@ def block_run(dm, torch, stream, X, W) -> dict:
 def block_lanczos_run(dm, stream, X, W, reps: int = 3) -> dict:
     """dm_eigs (top-k) by block Lanczos against the single-vector FP32 Lanczos on the same
     compressed operator: device time of the eigensolve phase (median over reps) and the
-    largest relative eigenvalue difference between the two."""
+    largest relative eigenvalue difference between the two. Block 4 runs the narrow-block
+    path (three chained launches per H-matvec, one cooperative launch per step); blocks 8
+    and 16 the general block path (per-level tree launches), FP32 or TF32 tensor-core near
+    field."""
     res = {}
     ref = None
-    for b, prec, name in ((0, dm.DM_PREC_FP32, "single_vector_fp32"), (8, dm.DM_PREC_FP32, "block8_fp32"),
-                          (16, dm.DM_PREC_FP32, "block16_fp32"), (16, dm.DM_PREC_TF32, "block16_tf32")):
+    for b, prec, name in ((0, dm.DM_PREC_FP32, "single_vector_fp32"), (4, dm.DM_PREC_FP32, "block4_fp32"),
+                          (8, dm.DM_PREC_FP32, "block8_fp32"), (16, dm.DM_PREC_FP32, "block16_fp32"),
+                          (16, dm.DM_PREC_TF32, "block16_tf32")):
         cfg = dm.dm_config_default(stream=stream.cuda_stream, block_size=b, block_precision=prec,
                                    near_mode=dm.DM_NEAR_CACHED)
         h = dm.dm_create(X, eps=-1.0, alpha=1.0, cfg=cfg)
