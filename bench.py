@@ -728,6 +728,21 @@ def run_ours(args) -> int:
                 "traffic": traffic.get("hmatvec_bytes_per_launch") if traffic else None,
                 "peak_source": peaks["source"] + " (copy bandwidth, MEASURED_PEAKS.json)",
                 "algorithmic_bytes": mv_bytes, "avg_ms": mv_ms}
+    # the degree passes (d = 3, CUDA cores): exponentials per second against the MUFU ex2 rate
+    # measured by the library's own microbenchmark in this run
+    ex2_n, ex2_ms = dm.dm_sfu_peak()
+    sfu_peak = ex2_n / (ex2_ms * 1e-3)
+    deg_ms = float(st.get("ms_degrees", 0.0))
+    deg_ex2 = 2 * W["N"] * (W["N"] + 1) / 2  # two passes over the upper triangle of W (symmetric tiles)
+    roofline_degree = {"kernel": "degree_sym_d3_kernel (both degree passes of dm_create, upper tiles of the "
+                                 "symmetric W)", "bound": "sfu",
+                       "achieved": (deg_ex2 / (deg_ms * 1e-3)) if deg_ms > 0 else None, "peak": sfu_peak,
+                       "unit": "ex2/s", "frac": (deg_ex2 / (deg_ms * 1e-3) / sfu_peak) if deg_ms > 0 else None,
+                       "algorithmic_ex2": deg_ex2, "avg_ms": deg_ms,
+                       "peak_source": "measured: dm_sfu_peak (independent MUFU ex2 chains, 64 warps per SM, "
+                                      "CUDA events) in this run",
+                       "peak_per_sm_clock": (sfu_peak / (torch.cuda.get_device_properties(local).multi_processor_count
+                                                          * clk["sm_mhz"] * 1e6)) if clk.get("sm_mhz") else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP64 sums and tridiagonal)", "data": "synthetic",
@@ -737,7 +752,7 @@ def run_ours(args) -> int:
                        "l2": "per-step working set (leaf blocks + Krylov basis) exceeds L2"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": W["N"] * W["d"] * 4,
                     "d2h_bytes_per_step": k * 8 + W["N"] * k * 4},
-            "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
+            "gpu_launches": int(launches), "roofline": roofline, "roofline_degree": roofline_degree, "clocks": clk,
             "phases_ms": {key: round(float(st[key]), 3) for key in
                           ("ms_create", "ms_tree", "ms_skeleton", "ms_pack", "ms_eigs")},
             "lanczos_iters": st["lanczos_iters"], "converged": bool(last["conv"]),

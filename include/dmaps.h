@@ -196,6 +196,8 @@ typedef struct dm_stats {
     int32_t degree_path;     /* degree passes of dm_create: 0 = CUDA cores (FP32 entries),
                                 1 = tensor cores, TF32 three-term split Gram matrix (d >= 16),
                                 2 = tensor cores, exact BF16 Gram matrix (8-bit quantised data) */
+    float ms_degrees;        /* device time of the two degree passes of dm_create (CUDA-core path;
+                                0 for the tensor-core path), including the q^-a step between them */
 } dm_stats;
 
 /* Phase times and structure statistics of the handle's last calls (introspection; no
@@ -204,6 +206,15 @@ int dm_get_stats(dm_handle h, dm_stats *st);
 
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t dm_kernel_launches(void);
+
+/* Throughput of the GPU's MUFU ex2 instruction, the exponential of every kernel entry in
+ * the degree passes and the on-the-fly near field (no paper counterpart; the denominator
+ * of those kernels' roofline). Runs 8 x SMs blocks of 256 threads, each thread 8 independent
+ * chains of 4096 exponentials, once to warm up and once timed with CUDA events on the legacy
+ * default stream of the current device. *ex2_count: exponentials of the timed launch;
+ * *ms: its duration. Allocates and frees a small device buffer; synchronous.
+ * Errors: DM_EINVAL for NULL outputs; DM_ENOMEM; DM_ECUDA. */
+int dm_sfu_peak(int64_t *ex2_count, float *ms);
 
 /* Failure-detection self-test of the bounded grid barrier that separates the passes of
  * the cooperative Lanczos step (no paper counterpart). `blocks` (1..8, always resident at

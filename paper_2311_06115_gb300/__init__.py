@@ -27,7 +27,7 @@ __all__ = [
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
     "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc", "dm_request",
     "dm_result", "dm_serve_config", "dm_request_bytes", "dm_serve_start", "dm_serve_stop", "dm_submit", "dm_poll",
-    "dm_release", "dm_tune_leaf", "dm_selftest_wait_timeout",
+    "dm_release", "dm_tune_leaf", "dm_selftest_wait_timeout", "dm_sfu_peak",
 ]
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
@@ -54,7 +54,8 @@ class dm_stats(C.Structure):
                 ("near_mode", C.c_int32), ("lanczos_iters", C.c_int32), ("converged", C.c_int32),
                 ("ms_create", C.c_float), ("ms_tree", C.c_float), ("ms_skeleton", C.c_float),
                 ("ms_pack", C.c_float), ("ms_eigs", C.c_float), ("matvec_calls", C.c_int32),
-                ("ms_matvec", C.c_float), ("hmatvec_path", C.c_int32), ("degree_path", C.c_int32)]
+                ("ms_matvec", C.c_float), ("hmatvec_path", C.c_int32), ("degree_path", C.c_int32),
+                ("ms_degrees", C.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True):
         "dm_release": (i32, [C.c_uint64]),
         "dm_tune_leaf": (i32, [vp, f64, i32, i32, vp, i32, C.POINTER(i32), vp]),
         "dm_selftest_wait_timeout": (i32, [i32, i32, i64, C.POINTER(i32)]),
+        "dm_sfu_peak": (i32, [C.POINTER(i64), C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -381,6 +383,13 @@ def dm_degrees_noalloc(points, eps: float, alpha: float, q, dg, s, stream=None) 
 
 def dm_kernel_launches() -> int:
     return int(load().dm_kernel_launches())
+
+
+def dm_sfu_peak() -> tuple[int, float]:
+    """dm_sfu_peak: (exponentials of the timed launch, its duration in ms)."""
+    n, ms = C.c_int64(), C.c_float()
+    _check(load().dm_sfu_peak(C.byref(n), C.byref(ms)))
+    return int(n.value), float(ms.value)
 
 
 def dm_selftest_wait_timeout(blocks: int, missing: int, spin_limit: int) -> tuple[int, int]:

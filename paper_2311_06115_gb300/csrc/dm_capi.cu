@@ -1053,6 +1053,42 @@ const char *dm_last_error(void) { return g_err.c_str(); }
 
 int64_t dm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+int dm_sfu_peak(int64_t *ex2_count, float *ms) {
+    if (!ex2_count || !ms) return fail(DM_EINVAL, "dm_sfu_peak: NULL output");
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DM_ECUDA, "dm_sfu_peak: no device");
+    }
+    const int blocks = 8 * sms, iters = 4096;
+    float *out = nullptr;
+    if (cudaMalloc(&out, sizeof(float) * (size_t)blocks * 256) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DM_ENOMEM, "dm_sfu_peak: cudaMalloc failed");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = dm_launch_ex2_peak(out, blocks, iters, 0);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) e = dm_launch_ex2_peak(out, blocks, iters, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DM_ECUDA, "dm_sfu_peak: %s", cudaGetErrorString(e));
+    }
+    *ex2_count = (int64_t)blocks * 256 * 8 * iters;
+    *ms = t;
+    return DM_OK;
+}
+
 int dm_selftest_wait_timeout(int32_t blocks, int32_t missing, int64_t spin_limit, int32_t *passed) {
     if (blocks < 1 || blocks > 8 || missing < 0 || spin_limit < 1 || spin_limit > ((int64_t)1 << 24))
         return fail(DM_EINVAL, "dm_selftest_wait_timeout: needs 1 <= blocks <= 8, missing >= 0, "
@@ -1193,9 +1229,11 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
             h->stats.degree_path = S.quant ? 2 : 1;
             h->free_group(G_WORK);  // the stream has been synchronised
         } else {
+            cudaEvent_t lap = h->lap_begin(h->stream);
             DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, nullptr, h->q, h->stream));
             DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
             DM_CUDA(dm_launch_degree_pass_centered(h->Xs, nrm, nmax, N, d, h->qaf, h->dg, h->stream));
+            h->lap_end(h->stream, lap, &h->stats.ms_degrees);
             DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
             h->stats.degree_path = 0;
         }

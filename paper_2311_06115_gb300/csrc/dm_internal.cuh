@@ -316,6 +316,9 @@ cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, flo
 int dm_near_item_rows(int near_mode, int leaf_max);
 // write each cluster CTA's shared-memory image of the upper tree (after packing)
 cudaError_t dm_tree_image(const DmHmat &H, cudaStream_t st);
+// MUFU ex2 throughput kernel: blocks x 256 threads x 8 chains x iters exponentials into out
+// (blocks x 256 floats)
+cudaError_t dm_launch_ex2_peak(float *out, int blocks, int iters, cudaStream_t st);
 // whether the device can run the one-cluster tree pass as a cluster of `ctas` CTAs with the
 // largest shared-memory budget (16 needs the non-portable cluster size)
 bool dm_tree_cluster_supported(int ctas);

@@ -723,3 +723,27 @@ cudaError_t dm_launch_dense_matvec_ws(const float *Xs, const float *sf, int64_t 
     dm_count_launches(1);
     return cudaGetLastError();
 }
+
+// Throughput of the MUFU ex2 instruction (the exponential of every kernel entry): each thread
+// runs 8 independent chains x <- ex2(-x / 2) (one FMA-pipe multiply and one MUFU ex2 per
+// link; the values stay in (0.5, 1]), so with 64 warps per SM the MUFU pipe, not latency,
+// sets the rate. The result is written so no chain is eliminated.
+__global__ void __launch_bounds__(256) ex2_peak_kernel(float *out, int iters) {
+    float a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = 0.5f + 0.01f * (float)u + 1e-7f * (float)threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = dm_ex2(-0.5f * a[u]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += a[u];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t dm_launch_ex2_peak(float *out, int blocks, int iters, cudaStream_t st) {
+    ex2_peak_kernel<<<blocks, 256, 0, st>>>(out, iters);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
