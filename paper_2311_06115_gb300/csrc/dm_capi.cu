@@ -829,13 +829,21 @@ int eigs_narrow(dm_ctx *h, int k, double *evals, float *evecs, bool *done) {
     bar_base += 3u * (unsigned)sms;
     par ^= 1;
     std::vector<double> th(k), rs(k);
-    int m = 0, flag = 0;
+    int m = 0, flag = 0, total = 0, restarts = 0;
     bool converged = false, ritz_current = false;
     const bool prof = h->cfg.profile != 0;
     std::vector<cudaEvent_t> ev_mv;
     const int every = h->cfg.check_every / b > 2 ? h->cfg.check_every / b : 2;
     int since = 0;
-    for (int j = 0; j < jmax; ++j) {
+    // thick restart once the basis is full: keep kr Ritz vectors (k plus half as many again, at
+    // least one block more) and the newest block; the step after it needs kr + 2b columns
+    const int cap = m_cap + 1;  // basis columns available (V holds m_max + 1)
+    int kr = k + (k / 2 > b ? k / 2 : b);
+    if (kr > dm_lanczos_kmax()) kr = dm_lanczos_kmax();
+    const bool can_restart = kr >= k && kr + 3 * b <= cap;
+    constexpr int kMaxRestarts = 64;
+    int col = 0;  // first column of the current block V_j
+    while (col + 2 * b <= cap) {
         if (prof) {
             cudaEvent_t e0, e1;
             DM_CUDA(cudaEventCreate(&e0));
@@ -844,31 +852,45 @@ int eigs_narrow(dm_ctx *h, int k, double *evals, float *evecs, bool *done) {
             ev_mv.push_back(e1);
             DM_CUDA(cudaEventRecord(e0, h->stream));
         }
-        DM_CUDA(dm_hmatvec_nb(H, h->nbt, b, Lz.V + (size_t)j * b * Lz.ldv, Lz.ldv, B.Z, Lz.ldv, true, h->stream));
+        DM_CUDA(dm_hmatvec_nb(H, h->nbt, b, Lz.V + (size_t)col * Lz.ldv, Lz.ldv, B.Z, Lz.ldv, true, h->stream));
         if (prof) DM_CUDA(cudaEventRecord(ev_mv.back(), h->stream));
-        DM_CUDA(dm_bstep(b, Lz.V, Lz.ldv, (j + 1) * b, (j + 1) * b, B.Z, B.H, B.H1, hstride, G1, G2, par, B.T,
-                         Lz.m_max, B.Bacc, B.flag, Lz.bar, bar_base, Lz.err, sms, h->stream));
+        DM_CUDA(dm_bstep(b, Lz.V, Lz.ldv, col + b, col + b, B.Z, B.H, B.H1, hstride, G1, G2, par, B.T, Lz.m_max,
+                         B.Bacc, B.flag, Lz.bar, bar_base, Lz.err, sms, h->stream));
         bar_base += 3u * (unsigned)sms;
         par ^= 1;
-        m = (j + 1) * b;
+        col += b;
+        m = col;
+        total += b;
         ritz_current = false;
         ++since;
-        const bool last = j + 1 == jmax;
-        if (m >= 2 * k && (since >= every || last)) {
+        const bool full = col + 2 * b > cap;  // the next step has no room: check (and restart) now
+        if ((m >= 2 * k && since >= every) || (full && m >= k)) {
             since = 0;
-            DM_CUDA(dm_bl_ritz(Lz, B, m, k, h->stream));
+            const int want = full && can_restart && restarts < kMaxRestarts ? kr : k;
+            DM_CUDA(dm_bl_ritz(Lz, B, m, want, h->stream));
             DM_CUDA(cudaMemcpyAsync(th.data(), Lz.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
             DM_CUDA(cudaMemcpyAsync(rs.data(), Lz.resid, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
             DM_CUDA(cudaMemcpyAsync(&flag, B.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
             DM_CUDA(cudaStreamSynchronize(h->stream));
-            ritz_current = true;
+            ritz_current = want == k;
             const double scale = std::fabs(th[0]) > 0 ? std::fabs(th[0]) : 1.0;
             bool ok = true;
             for (int i = 0; i < k; ++i)
                 if (!(rs[i] <= h->cfg.conv_tol * scale)) ok = false;
             if (ok || flag) {
                 converged = ok;
+                if (!ritz_current) {
+                    DM_CUDA(dm_bl_ritz(Lz, B, m, k, h->stream));
+                    ritz_current = true;
+                }
                 break;
+            }
+            if (want == kr) {
+                DM_CUDA(dm_lanczos_restart(Lz, m, kr, m, b, B.T, Lz.m_max, h->stream));
+                col = kr;
+                m = kr;
+                ++restarts;
+                ritz_current = false;
             }
         }
     }
@@ -906,10 +928,12 @@ int eigs_narrow(dm_ctx *h, int k, double *evals, float *evecs, bool *done) {
         cudaEventDestroy(ev_mv[e + 1]);
     }
     h->last_k = k;
-    h->stats.lanczos_iters = m;
+    h->stats.lanczos_iters = total;
     h->stats.converged = converged ? 1 : 0;
     h->stats.ms_eigs = t.stop();
-    return converged ? DM_OK : fail(DM_ENOCONV, "block Lanczos did not converge in %d basis vectors", m);
+    return converged ? DM_OK
+                     : fail(DM_ENOCONV, "block Lanczos did not converge in %d basis vectors (%d restarts)", total,
+                            restarts);
 }
 
 // dm_eigs with block Lanczos (cfg.block_size = b >= 2): per step one block H-matvec of b

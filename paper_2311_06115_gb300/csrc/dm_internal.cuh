@@ -409,6 +409,9 @@ cudaError_t dm_lanczos_vectors(DmLanczos &Lz, int m, int k, const int32_t *perm,
 // then the Ritz vectors V Yf, normalised, signed and scattered to the original order
 cudaError_t dm_lanczos_tvecs(DmLanczos &Lz, int m, int k, cudaStream_t st);
 cudaError_t dm_lanczos_phi(DmLanczos &Lz, int m, int k, const int32_t *perm, float *evecs_orig, cudaStream_t st);
+// thick restart of a dense-T (block) Lanczos: V[:, 0:kr] = normalised V[:, 0:m] Y[:, 0:kr] (Yf of a
+// Rayleigh-Ritz step with kr pairs), V[:, kr:kr+b] = V[:, src:src+b], T = diag(theta[0:kr])
+cudaError_t dm_lanczos_restart(DmLanczos &Lz, int m, int kr, int src, int b, double *T, int ldT, cudaStream_t st);
 
 // k_blanczos.cu -- block Lanczos (block size b <= dm_block_lanczos_max_b()); the basis lives
 // in Lz.V (position order), the Ritz data in Lz.alpha/beta/theta/resid/Y/Yf.

@@ -887,6 +887,47 @@ cudaError_t dm_lanczos_phi(DmLanczos &Lz, int m, int k, const int32_t *perm, flo
     return cudaGetLastError();
 }
 
+// Thick restart (Section 2.3's implicit restart with exact shifts, in its explicit form):
+// the kr Ritz vectors V[:, 0:m] Y[:, 0:kr] (normalised) replace the first kr basis columns,
+// the newest block V[:, src:src+b] moves to columns kr..kr+b-1, and the projected matrix
+// becomes diag(theta_1..theta_kr); the next block step's projection fills the coupling
+// column (B_j y_i, last block) itself.
+__global__ void restart_basis_kernel(float *V, int64_t ldv, int64_t N, const float *__restrict__ Phi,
+                                     const double *__restrict__ colsum, int kr, int src, int b) {
+    const int c = blockIdx.y;
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < kr) {
+        if (pos < N) V[(size_t)c * ldv + pos] = Phi[(size_t)c * N + pos] * (float)(1.0 / sqrt(colsum[c]));
+    } else if (pos < ldv) {
+        V[(size_t)c * ldv + pos] = V[(size_t)(src + c - kr) * ldv + pos];
+    }
+}
+
+__global__ void restart_T_kernel(double *T, int ldT, int n, const double *__restrict__ theta, int kr) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * ldT) return;
+    const int c = (int)(e / ldT), r = (int)(e - (int64_t)c * ldT);
+    T[e] = (r == c && r < kr) ? theta[r] : 0.0;
+}
+
+cudaError_t dm_lanczos_restart(DmLanczos &Lz, int m, int kr, int src, int b, double *T, int ldT, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(Lz.colsum, 0, sizeof(double) * kr, st);
+    if (e != cudaSuccess) return e;
+    const size_t ysh = sizeof(float) * (size_t)m * kr;
+    if ((e = dm_allow_smem((const void *)ritzvec_kernel, ysh)) != cudaSuccess) return e;
+    ritzvec_kernel<<<nblk(Lz.N, 256), 256, ysh, st>>>(Lz.V, Lz.ldv, m, kr, Lz.Yf, Lz.N, Lz.phi, Lz.colsum);
+    dm_count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    restart_basis_kernel<<<dim3(nblk(Lz.ldv, 256), (unsigned)(kr + b)), 256, 0, st>>>(Lz.V, Lz.ldv, Lz.N, Lz.phi,
+                                                                                     Lz.colsum, kr, src, b);
+    dm_count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t tot = (int64_t)Lz.m_max * ldT;
+    restart_T_kernel<<<nblk(tot, 256), 256, 0, st>>>(T, ldT, Lz.m_max, Lz.theta, kr);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t dm_launch_coords(const float *evecs, const double *theta, const double *dg, int64_t N, int k, int t,
                              float *psi, cudaStream_t st) {
     coords_kernel<<<dim3(nblk(N, 256), (unsigned)k), 256, 0, st>>>(evecs, theta, dg, N, t, psi);

@@ -387,6 +387,37 @@ def test_block_lanczos_replayed_structure_match_oracle(dm, b, k, prec):
     dm.dm_destroy(h)
 
 
+@pytest.mark.parametrize("b,k,m_max", [(4, 10, 32), (2, 8, 22), (4, 20, 44), (3, 6, 20)])
+def test_thick_restart_matches_unrestarted_oracle(dm, b, k, m_max):
+    """Thick restart (the explicit form of Section 2.3's implicit restart with exact shifts):
+    with a basis capped below what the unrestarted solve needs, block Lanczos keeps k + p
+    Ritz vectors and the newest block at each restart. Its eigenpairs must be those of the
+    oracle's unrestarted FP64 Lanczos on the same replayed structure, and the basis must
+    really have been restarted (more vectors generated than the cap)."""
+    n = 2048
+    X = _scurve(n, 0)
+    eps = O.median_sqdist(X)
+    _, dg, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, 128, 1e-5, 64)
+    evo1, Vo1, _, sto = O.lanczos_hmat(X, eps, s, H, k + 1, conv_tol=1e-10)
+    assert sto == 0
+    evo, Vo = evo1[:k], Vo1[:, :k]
+    cfg = dm.dm_config_default(block_size=b, m_max=m_max, near_mode=dm.DM_NEAR_CACHED)
+    h = dm.dm_create(X, eps=eps, cfg=cfg)
+    dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+    ev, V, conv = dm.dm_eigs(h, k)
+    assert conv
+    st = dm.dm_get_stats(h)
+    assert st["lanczos_iters"] > m_max, st["lanczos_iters"]
+    np.testing.assert_allclose(ev, evo, rtol=2e-5, atol=2e-7)
+    G = V.astype(np.float64).T @ V.astype(np.float64)
+    assert np.abs(G - np.eye(k)).max() < 2e-5
+    for i in range(k):
+        c = abs(float(np.dot(V[:, i].astype(np.float64), Vo[:, i])))
+        assert math.acos(min(1.0, c)) < 2e-3
+    dm.dm_destroy(h)
+
+
 def test_eigs_c1_workload_against_dense_oracle(dm):
     """2048-point s-curve, leaf 128, rank 64, tol 1e-5, top 10 (the small parity workload)."""
     import json
