@@ -65,8 +65,8 @@ def parse():
     p.add_argument("--n", type=int, default=WORKLOAD["N"], help="override N (testing only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-block", action="store_true", help="skip the block H-matvec and scaling-workload lines")
-    p.add_argument("--sections", default="accuracy,block_matvec,block_lanczos,scaling_workload,mnist_workload,"
-                                         "batched_clouds",
+    p.add_argument("--sections", default="accuracy,precision,block_matvec,block_lanczos,scaling_workload,"
+                                         "mnist_workload,batched_clouds",
                    help="comma list of the side measurements to run after the headline")
     p.add_argument("--skip-headline", action="store_true",
                    help="profiling only: run just the side measurements (no timed headline steps)")
@@ -242,7 +242,7 @@ def fp64_reference(X, W) -> dict:
     q, dg, s = O.degrees(X, eps, 1.0)
     H = O.compress(X, eps, s, W["leaf"], 1e-9, W["rank"])
     ev, V, it, st = O.lanczos_hmat(X, eps, s, H, W["k"], conv_tol=1e-11)
-    _FP64_REF.update(ev=ev, V=V, dg=dg, eps=eps, converged=st == 0, seconds=time.perf_counter() - t0,
+    _FP64_REF.update(ev=ev, V=V, dg=dg, s=s, eps=eps, converged=st == 0, seconds=time.perf_counter() - t0,
                      what="FP64 oracle: exact degrees, H-matrix at tol 1e-9 (leaf %d, rank %d), Lanczos to "
                           "residual 1e-11, on the host cores" % (W["leaf"], W["rank"]))
     return _FP64_REF
@@ -418,6 +418,64 @@ def block_lanczos_run(dm, stream, X, W, reps: int = 3) -> dict:
     return res
 
 
+def precision_run(dm, torch, stream, X, W, reps: int = 10) -> dict:
+    """The precision matrix of the near field on the bench workload: FP32 (CUDA cores), TF32 and
+    split TF32 (three products of TF32 high and low parts; tcgen05, FP32 accumulation). For each:
+    the block H-matvec at nrhs 16 and 64 (device time, and the error against the FP64 oracle's
+    evaluation of the same compressed structure, max |y - y_fp64| / max |x|), and block Lanczos
+    with 16 vectors (eigensolve time, eigenvalue and subspace-angle errors against the FP64
+    reference solve)."""
+    import numpy as np
+
+    import oracle as O
+
+    O.build()
+    ref = fp64_reference(X, W)
+    eps = ref["eps"]
+    s_host = _FP64_REF.get("s")
+    if s_host is None:
+        _, _, s_host = O.degrees(X, eps, 1.0)
+        _FP64_REF["s"] = s_host
+    Hs = O.compress(X, eps, s_host, W["leaf"], W["tol"], W["rank"])
+    N = X.shape[0]
+    g = np.random.default_rng(7)
+    xs = {nb: np.asfortranarray((g.random((N, nb)) * 2 - 1).astype(np.float32)) for nb in (16, 64)}
+    yref = {nb: O.hmatvec(X, eps, s_host, Hs, xs[nb][:, :16].astype(np.float64)) for nb in (16,)}
+    out = {"structure": "the oracle's FP64 compression (tol %g, leaf %d, rank %d), loaded with dm_load_hmatrix"
+                        % (W["tol"], W["leaf"], W["rank"])}
+    for prec, name in ((dm.DM_PREC_FP32, "fp32"), (dm.DM_PREC_TF32, "tf32"), (dm.DM_PREC_TF32X3, "tf32x3")):
+        r = {}
+        cfg = dm.dm_config_default(stream=stream.cuda_stream, block_precision=prec, near_mode=dm.DM_NEAR_CACHED)
+        h = dm.dm_create(X, eps=eps, alpha=1.0, cfg=cfg)
+        dm.dm_load_hmatrix(h, Hs.L, Hs.max_rank, Hs.perm, Hs.ranks, Hs.skel, Hs.P.astype(np.float32))
+        for nb in (16, 64):
+            xd = torch.from_numpy(xs[nb]).cuda()
+            xd = xd.t().contiguous().t() if nb > 1 else xd
+            r[f"nrhs{nb}_ms"] = _time_matvec(dm, torch, stream, h, xd, reps)
+            if nb in yref:
+                y = dm.dm_matvec(h, xs[nb])
+                r["hmatvec_error_vs_fp64"] = float(np.abs(y - yref[nb]).max() / np.abs(xs[nb]).max())
+        dm.dm_destroy(h)
+        cfg = dm.dm_config_default(stream=stream.cuda_stream, block_precision=prec, near_mode=dm.DM_NEAR_CACHED,
+                                   block_size=16)
+        h = dm.dm_create(X, eps=-1.0, alpha=1.0, cfg=cfg)
+        dm.dm_compress(h, W["tol"], W["leaf"], W["rank"])
+        ts = []
+        for _ in range(3):
+            ev, V, conv = dm.dm_eigs(h, W["k"], evecs=True, device_out=True)
+            ts.append(dm.dm_get_stats(h)["ms_eigs"])
+        r["block16_ms_eigs"] = statistics.median(ts)
+        r["block16_converged"] = bool(conv)
+        e = accuracy_errors(ref, ev, V.cpu().numpy())
+        r["block16_max_rel_eigenvalue_error_vs_fp64"] = e["max_rel_eigenvalue_error"]
+        r["block16_subspace_angle_rad_vs_fp64"] = e["subspace_angle_rad"]
+        dm.dm_destroy(h)
+        out[name] = r
+    out["note"] = ("at nrhs <= 64 the near product moves 2 nrhs flops per 4 stored bytes, so HBM, not the tensor "
+                   "pipe, bounds it; the tensor cores shorten the compute, the split form keeps FP32-level error")
+    return out
+
+
 def scaling_workload_run(dm, torch, stream) -> dict:
     """The paper's evaluation workload of Section 4.2 (a 100k x 100k Gaussian kernel of 6-D
     random points times a 100k x 512 block), here on the diffusion-normalised operator with
@@ -432,7 +490,7 @@ def scaling_workload_run(dm, torch, stream) -> dict:
                             "(text) / 4.5 s (figure)"}
     g = torch.Generator(device="cuda").manual_seed(4)
     xb = (torch.rand(512, X.shape[0], device="cuda", generator=g) * 2 - 1).t()
-    for prec, name in ((dm.DM_PREC_TF32, "tf32"), (dm.DM_PREC_FP32, "fp32")):
+    for prec, name in ((dm.DM_PREC_TF32, "tf32"), (dm.DM_PREC_TF32X3, "tf32x3"), (dm.DM_PREC_FP32, "fp32")):
         cfg = dm.dm_config_default(stream=stream.cuda_stream, block_precision=prec, near_mode=dm.DM_NEAR_CACHED)
         t0 = time.perf_counter()
         h = dm.dm_create(X, eps=-1.0, alpha=1.0, cfg=cfg)
@@ -694,6 +752,7 @@ def run_ours(args) -> int:
         out = {}
         for key in (x for x in args.sections.split(",") if x):
             fn = {"accuracy": lambda: accuracy_run(dm, torch, stream, X, W),
+                  "precision": lambda: precision_run(dm, torch, stream, X, W),
                   "block_matvec": lambda: block_run(dm, torch, stream, X, W),
                   "block_lanczos": lambda: block_lanczos_run(dm, stream, X, W),
                   "scaling_workload": lambda: scaling_workload_run(dm, torch, stream),
@@ -760,7 +819,8 @@ def run_ours(args) -> int:
             "evals_head": [round(float(v), 8) for v in last["ev"][:5]]}
     if world == 1 and not args.no_block:
         wanted = set(x for x in args.sections.split(",") if x)
-        for key, fn in (("block_matvec", lambda: block_run(dm, torch, stream, X, W)),
+        for key, fn in (("precision", lambda: precision_run(dm, torch, stream, X, W)),
+                        ("block_matvec", lambda: block_run(dm, torch, stream, X, W)),
                         ("block_lanczos", lambda: block_lanczos_run(dm, stream, X, W)),
                         ("scaling_workload", lambda: scaling_workload_run(dm, torch, stream)),
                         ("mnist_workload", lambda: mnist_workload_run(dm, stream)),

@@ -79,15 +79,20 @@ typedef struct dm_config {
                               instead of one cooperative launch whose blocks wait on one another,
                               so it never depends on SMs that other kernels hold. 0 (default) =
                               one cooperative launch per step. */
-    int32_t block_precision; /* near field of the block H-matvec (dm_matvec with nrhs >= 2, cached
-                                mode): DM_PREC_FP32 (default, FP32 FMA on the CUDA cores) or
-                                DM_PREC_TF32 (tcgen05 tensor cores, TF32 inputs, FP32 accumulation) */
+    int32_t block_precision; /* near field of the block H-matvec (dm_matvec with nrhs >= 5, or 2..4
+                                when the narrow-block form does not apply; cached mode):
+                                DM_PREC_FP32 (default, FP32 FMA on the CUDA cores), DM_PREC_TF32
+                                (tcgen05 tensor cores, TF32 inputs, FP32 accumulation: about 2^-10
+                                relative per term) or DM_PREC_TF32X3 (tcgen05 with each operand
+                                split into a TF32 high part and a TF32 remainder, three products
+                                hi*hi + hi*lo + lo*hi: about 2^-20 relative per term) */
     int32_t block_size;   /* dm_eigs: 0 or 1 = single-vector Lanczos (default); 2..16 = block Lanczos
                              with this many vectors per step (one block H-matvec per step) */
 } dm_config;
 
 #define DM_PREC_FP32 0
 #define DM_PREC_TF32 1
+#define DM_PREC_TF32X3 2
 
 /* Fill *cfg with the defaults listed above. */
 void dm_config_default(dm_config *cfg);

@@ -21,7 +21,7 @@ from . import build as _build
 
 __all__ = [
     "DmError", "DM_OK", "DM_EINVAL", "DM_ENOMEM", "DM_ESTATE", "DM_ENOCONV", "DM_ETIMEOUT", "DM_ECUDA", "DM_EBUSY",
-    "DM_NEAR_AUTO", "DM_NEAR_CACHED", "DM_NEAR_ONTHEFLY", "DM_PREC_FP32", "DM_PREC_TF32", "dm_config", "dm_stats", "lib_path", "load",
+    "DM_NEAR_AUTO", "DM_NEAR_CACHED", "DM_NEAR_ONTHEFLY", "DM_PREC_FP32", "DM_PREC_TF32", "DM_PREC_TF32X3", "dm_config", "dm_stats", "lib_path", "load",
     "dm_config_default", "dm_create", "dm_compress", "dm_matvec", "dm_eigs", "dm_coords", "dm_intrinsic_dim",
     "dm_destroy",
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
@@ -32,7 +32,7 @@ __all__ = [
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 DM_NEAR_AUTO, DM_NEAR_CACHED, DM_NEAR_ONTHEFLY = 0, 1, 2
-DM_PREC_FP32, DM_PREC_TF32 = 0, 1
+DM_PREC_FP32, DM_PREC_TF32, DM_PREC_TF32X3 = 0, 1, 2
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)

@@ -954,8 +954,9 @@ int eigs_block(dm_ctx *h, int k, double *evals, float *evecs) {
     if (jmax < 1 || (jmax * b) < k) return fail(DM_EINVAL, "m_max too small for block_size %d and k %d", b, k);
     DM_CHECK(ensure_block_lanczos(h, b));
     DM_CHECK(ensure_block(h, b));
-    const bool tc = h->cfg.block_precision == DM_PREC_TF32 && h->near_mode == DM_NEAR_CACHED;
+    const bool tc = h->cfg.block_precision != DM_PREC_FP32 && h->near_mode == DM_NEAR_CACHED;
     if (tc && !dm_tc_available()) return fail(DM_ECUDA, "the driver does not provide cuTensorMapEncodeTiled");
+    const int near_prec = tc ? h->cfg.block_precision : DM_PREC_FP32;
     PhaseTimer t(h->stream);
     DmBlockLanczos &B = h->bl;
     const DmHmat H = h->hmat();
@@ -977,8 +978,8 @@ int eigs_block(dm_ctx *h, int k, double *evals, float *evecs) {
             ev_mv.push_back(e1);
             DM_CUDA(cudaEventRecord(e0, h->stream));
         }
-        DM_CUDA(dm_hmatvec_block(H, h->near_mode, tc, h->blk, b, Lz.V + (size_t)j * b * Lz.ldv, Lz.ldv, nullptr,
-                                 false, B.Z, Lz.ldv, DM_BLK_POSITION, h->stream));
+        DM_CUDA(dm_hmatvec_block(H, h->near_mode, near_prec, h->blk, b, Lz.V + (size_t)j * b * Lz.ldv, Lz.ldv,
+                                 nullptr, false, B.Z, Lz.ldv, DM_BLK_POSITION, h->stream));
         if (prof) DM_CUDA(cudaEventRecord(ev_mv.back(), h->stream));
         DM_CUDA(dm_bl_orth(Lz, B, j, h->stream));
         m = (j + 1) * b;
@@ -1150,6 +1151,8 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
     if (d < 1) return fail(DM_EINVAL, "d must be >= 1 (got %d)", d);
     if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(DM_EINVAL, "alpha must be finite and >= 0");
     if (!std::isfinite(eps)) return fail(DM_EINVAL, "eps must be finite");
+    if (cfg && (cfg->block_precision < DM_PREC_FP32 || cfg->block_precision > DM_PREC_TF32X3))
+        return fail(DM_EINVAL, "block_precision must be DM_PREC_FP32, DM_PREC_TF32 or DM_PREC_TF32X3");
     dm_ctx *h = new dm_ctx();
     dm_config_default(&h->cfg);
     if (cfg) h->cfg = *cfg;
@@ -1404,15 +1407,16 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs) {
         DM_CUDA(dm_hmatvec_nb(h->hmat(), h->nbt, nrhs, dx, h->N, dy, h->N, false, h->stream));
     } else if (h->compressed && nrhs >= 2) {
         // block H-matvec: every stored operand is read once per panel of columns
-        const bool tc = h->cfg.block_precision == DM_PREC_TF32 && h->near_mode == DM_NEAR_CACHED;
+        const bool tc = h->cfg.block_precision != DM_PREC_FP32 && h->near_mode == DM_NEAR_CACHED;
         if (tc && !dm_tc_available()) return fail(DM_ECUDA, "the driver does not provide cuTensorMapEncodeTiled");
+        const int near_prec = tc ? h->cfg.block_precision : DM_PREC_FP32;
         const int panel = tc ? kBlockPanelTc : kBlockPanelFp32;
         const int nbp = nrhs < panel ? nrhs : panel;
         DM_CHECK(ensure_block(h, nbp));
         const DmHmat H = h->hmat();
         for (int c0 = 0; c0 < nrhs; c0 += panel) {
             const int nb = nrhs - c0 < panel ? nrhs - c0 : panel;
-            DM_CUDA(dm_hmatvec_block(H, h->near_mode, tc, h->blk, nb, dx + (size_t)c0 * h->N, h->N, h->perm,
+            DM_CUDA(dm_hmatvec_block(H, h->near_mode, near_prec, h->blk, nb, dx + (size_t)c0 * h->N, h->N, h->perm,
                                      false, dy + (size_t)c0 * h->N, h->N, DM_BLK_ORIGINAL, h->stream));
         }
         if (tc) {

@@ -363,16 +363,17 @@ int64_t dm_block_ldx(const DmHmat &H);
 // position order when perm_in = nullptr, or already in the padded leaf layout (x_padded,
 // column stride W.ldx). Y (column stride ldo): DM_BLK_ORIGINAL, DM_BLK_POSITION or
 // DM_BLK_PADDED (the padded leaf layout).
-// near_tc: the cached near field on the tensor cores (TF32), else FP32 on the CUDA cores.
+// near_prec (cached near field): DM_PREC_FP32 on the CUDA cores, DM_PREC_TF32 on the tensor
+// cores, DM_PREC_TF32X3 on the tensor cores with three-term split operands.
 enum { DM_BLK_PADDED = 0, DM_BLK_ORIGINAL = 1, DM_BLK_POSITION = 2 };
-cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const DmBlockWork &W, int nb,
+cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, int near_prec, const DmBlockWork &W, int nb,
                              const float *x, int64_t ldin, const int32_t *perm_in, bool x_padded, float *y,
                              int64_t ldo, int y_layout, cudaStream_t st);
 // k_tc.cu: Yb = K_a Xb per leaf on tcgen05 (TF32 in, FP32 accumulate); *err set when a
 // bounded wait gave up. dm_tc_available: the driver provides cuTensorMapEncodeTiled.
 bool dm_tc_available();
 cudaError_t dm_launch_near_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, float *Yb, int *err,
-                              cudaStream_t st);
+                              bool split, cudaStream_t st);
 
 // k_lanczos.cu
 struct DmLanczos {

@@ -351,7 +351,7 @@ cudaError_t launch_near(const DmHmat &H, int onthefly, const float *Xb, int64_t 
 
 int64_t dm_block_ldx(const DmHmat &H) { return (int64_t)(1 << H.L) * H.ldk; }
 
-cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const DmBlockWork &W, int nb,
+cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, int near_prec, const DmBlockWork &W, int nb,
                              const float *x, int64_t ldin, const int32_t *perm_in, bool x_padded, float *y,
                              int64_t ldo, int y_layout, cudaStream_t st) {
     if (nb < 1 || nb > W.nb_max) return cudaErrorInvalidValue;
@@ -373,7 +373,8 @@ cudaError_t dm_hmatvec_block(const DmHmat &H, int near_mode, bool near_tc, const
         if ((e = cudaStreamWaitEvent(sn, W.fork, 0)) != cudaSuccess) return e;
     }
     const int onthefly = near_mode == DM_NEAR_CACHED ? 0 : 1;
-    if (near_tc && !onthefly) e = dm_launch_near_tc(H, Xb, ldx, nb, W.Yb, H.err, sn);
+    if (near_prec != DM_PREC_FP32 && !onthefly)
+        e = dm_launch_near_tc(H, Xb, ldx, nb, W.Yb, H.err, near_prec == DM_PREC_TF32X3, sn);
     else if (nb <= 16) e = launch_near<16>(H, onthefly, Xb, ldx, nb, W.Yb, sn);
     else if (nb <= 32) e = launch_near<32>(H, onthefly, Xb, ldx, nb, W.Yb, sn);
     else e = launch_near<64>(H, onthefly, Xb, ldx, nb, W.Yb, sn);

@@ -16,6 +16,12 @@
 // leaf's own rows cross HBM; accumulator rows past the leaf are never stored. Columns past
 // the block (ldk) and right-hand sides past nb are zero-filled by TMA.
 //
+// Split mode (three-term TF32, accuracy close to FP32): warps 2-3 split every staged tile
+// into a TF32-exact high part (the low 13 mantissa bits cleared, written in place) and the
+// low remainder (x - hi, exact in FP32, into a second buffer), then release the stage to the
+// MMA issuer through a third mbarrier; the issuer accumulates hi*hi + hi*lo + lo*hi (the
+// lo*lo term, ~2^-20 relative, is dropped). The split tiles halve the stages that fit.
+//
 // Every mbarrier wait is bounded (about a second of clock cycles); a wait that gives up
 // raises *err, skips the stores and still frees the tensor memory, and the host reports
 // DM_ETIMEOUT.
@@ -27,9 +33,19 @@ namespace {
 using namespace dmtc;
 
 constexpr int kTcThreads = 128;
-constexpr int kTcStages = 4;
 constexpr uint32_t kTcABytes = 128 * 128;  // 128 rows x 32 FP32
-template <int NT>
+constexpr int kSplitThreads = 64;          // warps 2-3 split the tiles in split mode
+
+template <int NT, bool SPLIT>
+__host__ __device__ constexpr int tc_stages() {
+    return !SPLIT ? 4 : (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4));
+}
+template <int NT, bool SPLIT>
+__host__ __device__ constexpr uint32_t tc_stage_bytes() {
+    return (kTcABytes + NT * 128) * (SPLIT ? 2u : 1u);
+}
+
+template <int NT, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmA8,
                                                              const __grid_constant__ CUtensorMap tmB,
@@ -37,8 +53,10 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
                                                              float *__restrict__ Yb, int64_t ldx, int mtiles,
                                                              int *err) {
     static_assert(NT >= 16 && NT <= 256 && (NT & (NT - 1)) == 0, "NT: power of two in [16, 256]");
+    constexpr int kTcStages = tc_stages<NT, SPLIT>();
     constexpr uint32_t kBBytes = NT * 128;
-    constexpr uint32_t kStageBytes = kTcABytes + kBBytes;
+    constexpr uint32_t kHiBytes = kTcABytes + kBBytes;  // A then B (high parts); low parts follow
+    constexpr uint32_t kStageBytes = tc_stage_bytes<NT, SPLIT>();
     constexpr uint32_t kTmemCols = NT < 32 ? 32 : NT;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
@@ -46,7 +64,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
     uint8_t *tiles = smem_raw + (base - raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(tiles + kTcStages * kStageBytes);
     uint64_t *empty = full + kTcStages;
-    uint64_t *done = empty + kTcStages;
+    uint64_t *conv = empty + kTcStages;  // split mode: the stage's tiles are split
+    uint64_t *done = conv + kTcStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -63,6 +82,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
         for (int s = 0; s < kTcStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+            mbar_init(&conv[s], kSplitThreads);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -98,7 +118,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
         bool ok = true;
         for (int k = 0; k < ksteps; ++k) {
             const int s = k % kTcStages;
-            if (!mbar_wait(&full[s], (unsigned)(k / kTcStages) & 1u)) {
+            if (!mbar_wait(SPLIT ? &conv[s] : &full[s], (unsigned)(k / kTcStages) & 1u)) {
                 atomicExch(err, 1);
                 ok = false;
                 break;
@@ -106,12 +126,47 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
             tc_fence_after();
             const uint32_t sa = base + (uint32_t)s * kStageBytes, sb = sa + kTcABytes;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
+            for (int kk = 0; kk < 4; ++kk) {
                 tc_mma_tf32(tmem, desc_sw128(sa + 32u * kk), desc_sw128(sb + 32u * kk), idesc,
                             (k > 0 || kk > 0) ? 1u : 0u);
+                if (SPLIT) {
+                    const uint32_t la = sa + kHiBytes, lb = la + kTcABytes;
+                    tc_mma_tf32(tmem, desc_sw128(sa + 32u * kk), desc_sw128(lb + 32u * kk), idesc, 1u);
+                    tc_mma_tf32(tmem, desc_sw128(la + 32u * kk), desc_sw128(sb + 32u * kk), idesc, 1u);
+                }
+            }
             tc_commit(&empty[s]);  // the stage is free once these MMAs have read it
         }
         if (ok) tc_commit(done);
+    } else if (SPLIT && warp >= 2) {
+        // tile splitters: x = hi + lo with hi TF32-exact (written in place), lo = x - hi
+        const int t = threadIdx.x - 64;
+        for (int k = 0; k < ksteps; ++k) {
+            const int s = k % kTcStages;
+            if (!mbar_wait(&full[s], (unsigned)(k / kTcStages) & 1u)) {
+                atomicExch(err, 1);
+                break;
+            }
+            float4 *hi = reinterpret_cast<float4 *>(tiles + (size_t)s * kStageBytes);
+            float4 *lo = reinterpret_cast<float4 *>(tiles + (size_t)s * kStageBytes + kHiBytes);
+            for (int e = t; e < (int)(kHiBytes / 16); e += kSplitThreads) {
+                const float4 x = hi[e];
+                float4 h, l;
+                h.x = __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
+                h.y = __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
+                h.z = __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
+                h.w = __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
+                l.x = x.x - h.x;
+                l.y = x.y - h.y;
+                l.z = x.z - h.z;
+                l.w = x.w - h.w;
+                hi[e] = h;
+                lo[e] = l;
+            }
+            // make the generic-proxy writes visible to the tensor core (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&conv[s]);
+        }
     }
     __syncwarp();
     // epilogue: thread = accumulator row (TMEM lane) 32 warp + lane
@@ -143,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_near_kernel(const __grid_consta
     }
 }
 
-template <int NT>
+template <int NT, bool SPLIT>
 cudaError_t launch_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, float *Yb, int *err, cudaStream_t st) {
     CUtensorMap tmA, tmA8, tmB;
     const uint64_t arows = (uint64_t)(1 << H.L) * H.leaf_max;
@@ -153,13 +208,24 @@ cudaError_t launch_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, flo
         !tc_make_map(&tmB, f32, 4, Xb, (uint64_t)ldx, (uint64_t)nb, (uint64_t)ldx, 32, NT))
         return cudaErrorInvalidValue;
     const int mtiles = (H.leaf_max + 127) / 128;
-    const size_t smem = 1024 + (size_t)kTcStages * (kTcABytes + NT * 128) + (2 * kTcStages + 1) * 8 + 16;
-    cudaError_t e = dm_allow_smem((const void *)tc_near_kernel<NT>, smem);
+    constexpr int stages = tc_stages<NT, SPLIT>();
+    const size_t smem = 1024 + (size_t)stages * tc_stage_bytes<NT, SPLIT>() + (3 * stages + 1) * 8 + 16;
+    cudaError_t e = dm_allow_smem((const void *)tc_near_kernel<NT, SPLIT>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((1 << H.L) * mtiles), (unsigned)((nb + NT - 1) / NT));
-    tc_near_kernel<NT><<<grid, kTcThreads, smem, st>>>(tmA, tmA8, tmB, H, nb, Yb, ldx, mtiles, err);
+    tc_near_kernel<NT, SPLIT><<<grid, kTcThreads, smem, st>>>(tmA, tmA8, tmB, H, nb, Yb, ldx, mtiles, err);
     dm_count_launches(1);
     return cudaGetLastError();
+}
+
+template <bool SPLIT>
+cudaError_t launch_tc_nb(const DmHmat &H, const float *Xb, int64_t ldx, int nb, float *Yb, int *err,
+                         cudaStream_t st) {
+    if (nb <= 16) return launch_tc<16, SPLIT>(H, Xb, ldx, nb, Yb, err, st);
+    if (nb <= 32) return launch_tc<32, SPLIT>(H, Xb, ldx, nb, Yb, err, st);
+    if (nb <= 64) return launch_tc<64, SPLIT>(H, Xb, ldx, nb, Yb, err, st);
+    if (nb <= 128) return launch_tc<128, SPLIT>(H, Xb, ldx, nb, Yb, err, st);
+    return launch_tc<256, SPLIT>(H, Xb, ldx, nb, Yb, err, st);
 }
 
 }  // namespace
@@ -167,11 +233,7 @@ cudaError_t launch_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, flo
 bool dm_tc_available() { return tc_encode_fn() != nullptr; }
 
 cudaError_t dm_launch_near_tc(const DmHmat &H, const float *Xb, int64_t ldx, int nb, float *Yb, int *err,
-                              cudaStream_t st) {
+                              bool split, cudaStream_t st) {
     if (!H.Knear || (ldx & 3) != 0 || (H.ldk & 3) != 0) return cudaErrorInvalidValue;
-    if (nb <= 16) return launch_tc<16>(H, Xb, ldx, nb, Yb, err, st);
-    if (nb <= 32) return launch_tc<32>(H, Xb, ldx, nb, Yb, err, st);
-    if (nb <= 64) return launch_tc<64>(H, Xb, ldx, nb, Yb, err, st);
-    if (nb <= 128) return launch_tc<128>(H, Xb, ldx, nb, Yb, err, st);
-    return launch_tc<256>(H, Xb, ldx, nb, Yb, err, st);
+    return split ? launch_tc_nb<true>(H, Xb, ldx, nb, Yb, err, st) : launch_tc_nb<false>(H, Xb, ldx, nb, Yb, err, st);
 }

@@ -243,6 +243,39 @@ def test_block_hmatvec_tf32_tensor_cores(dm, n, leaf, rank, tol, nrhs):
     dm.dm_destroy(h)
 
 
+@pytest.mark.parametrize("n,leaf,rank,tol,nrhs", [(3001, 256, 48, 1e-4, 16), (2048, 128, 64, 1e-5, 100),
+                                                  (700, 64, 64, 0.0, 300), (5000, 512, 64, 1e-5, 33)])
+def test_block_hmatvec_split_tf32_tensor_cores(dm, n, leaf, rank, tol, nrhs):
+    """Near field on tcgen05 with three-term split operands (x = hi + lo, hi TF32-exact, lo the
+    remainder read as TF32; products hi*hi + hi*lo + lo*hi, FP32 accumulation): each near
+    term carries at most 3 * 2^-20 relative error (the dropped lo*lo term and the TF32
+    rounding of the remainders), so the per-row bound is 4 * 2^-20 (S|x|)_i plus the FP32
+    tolerance of the rest of the path -- a bound the plain TF32 product (2^-9) fails."""
+    X = _scurve(n, 17)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, leaf, tol, rank)
+    x = np.asfortranarray(synth.random_rhs(n, nrhs, seed=9).astype(np.float32))
+    xd = x.astype(np.float64)
+    yr = O.hmatvec(X, eps, s, H, xd)
+    errs = {}
+    for prec in (dm.DM_PREC_TF32, dm.DM_PREC_TF32X3):
+        cfg = dm.dm_config_default(near_mode=dm.DM_NEAR_CACHED, block_precision=prec)
+        h = dm.dm_create(X, eps=eps, cfg=cfg)
+        dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+        y = dm.dm_matvec(h, x)
+        assert np.array_equal(y, dm.dm_matvec(h, x))
+        errs[prec] = np.abs(y - yr).max() / np.abs(x).max()
+        if prec == dm.DM_PREC_TF32X3:
+            for c in range(0, nrhs, max(1, nrhs // 7)):
+                bound = 4.0 * 2.0 ** -20 * O.S_matvec(X, eps, s, np.abs(xd[:, c])) + 1e-5 * np.abs(xd[:, c]).max()
+                assert np.all(np.abs(y[:, c] - yr[:, c]) <= bound), c
+        dm.dm_destroy(h)
+    print(f"near field TF32 {errs[dm.DM_PREC_TF32]:.3e}  split TF32 {errs[dm.DM_PREC_TF32X3]:.3e}")
+    assert errs[dm.DM_PREC_TF32X3] < 1e-5
+    assert errs[dm.DM_PREC_TF32X3] < 0.05 * errs[dm.DM_PREC_TF32]
+
+
 # ------------------------------------------------------------------ GPU compression
 
 def test_gpu_compression_exact_at_full_rank(dm):
@@ -346,7 +379,7 @@ def test_eigs_replayed_structure_match_oracle_lanczos(dm):
             assert err <= bound, (t, i, err, bound)
 
 
-@pytest.mark.parametrize("b,k,prec", [(8, 10, 0), (16, 10, 0), (4, 6, 0), (16, 10, 1)])
+@pytest.mark.parametrize("b,k,prec", [(8, 10, 0), (16, 10, 0), (4, 6, 0), (16, 10, 1), (16, 10, 2)])
 def test_block_lanczos_replayed_structure_match_oracle(dm, b, k, prec):
     """Block Lanczos (b vectors per step, block H-matvec, block CGS2, CholQR2, FP64
     Rayleigh-Ritz through Householder tridiagonalisation) finds the same eigenpairs of the
@@ -369,7 +402,7 @@ def test_block_lanczos_replayed_structure_match_oracle(dm, b, k, prec):
     ev, V, conv = dm.dm_eigs(h, k)
     assert conv
     weyl = 2.0 ** -9
-    if prec == 0:
+    if prec != 1:  # FP32, or the split TF32 near field (2^-20 per term: within the FP32 tolerance)
         np.testing.assert_allclose(ev, evo, rtol=2e-5, atol=2e-7)
     else:
         assert np.abs(ev - evo).max() <= weyl
@@ -377,7 +410,7 @@ def test_block_lanczos_replayed_structure_match_oracle(dm, b, k, prec):
     assert np.abs(G - np.eye(k)).max() < 2e-5
     for i in range(k):
         c = abs(float(np.dot(V[:, i].astype(np.float64), Vo[:, i])))
-        if prec == 0:
+        if prec != 1:
             assert math.acos(min(1.0, c)) < 2e-3
         else:
             gap = min(abs(evo1[i] - evo1[j]) for j in range(k + 1) if j != i)
