@@ -29,6 +29,8 @@ namespace {
 constexpr int kLeafThreads = 256;
 constexpr int kTreeThreads = 1024;
 constexpr int kNearThreads = 256;      // on-the-fly near items (thread per row)
+constexpr int kNearCachedThreads = 256;  // cached near items: 6 CTAs per SM at <= 40 registers
+constexpr int kNearCachedMinBlocks = 6;
 constexpr int kNearRowsTarget = 136;     // rows of a leaf block per cached near item (about one wave)
 
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -268,17 +270,33 @@ __global__ void __launch_bounds__(kTreeThreads) tree_kernel(const __grid_constan
         }
     }
     __syncthreads();
-    // 3. upward pass inside the subtree: S2S of every child pair, N2S of every node; a level's
-    //    nodes share the CTA's warps
+    // 3. upward pass inside the subtree: the N2S chain alone (a level's nodes share the CTA's
+    //    warps); the S2S products feed only the downward pass, so they leave the chain and run
+    //    afterwards, every child pair of the subtree at once
     for (int lv = L - 1; lv >= ls; --lv) {
         int first, count;
         level_nodes(g, ls, lv, &first, &count);
         const int ngw = count >= nw ? 1 : nw / count;
         for (int i = warp / ngw; i < count; i += nw / ngw) {
             const int n = first + i, gw = warp % ngw;
+            if (n == 0) continue;
             const int sl = rk[2 * n + 1], sr = rk[2 * n + 2], pr = lay[n].z;
-            grp_s2s(sm, lay[n].y, sl, sr, pr, sm, gw, ngw, lane);
-            if (n > 0) grp_gemv(sm, lay[n].x, 1, rk[n] | 1, rk[n], sl + sr, pr, sm, own_w(n), false, gw, ngw, lane);
+            grp_gemv(sm, lay[n].x, 1, rk[n] | 1, rk[n], sl + sr, pr, sm, own_w(n), false, gw, ngw, lane);
+        }
+        __syncthreads();
+    }
+    {
+        const int nsub = (1 << (L - ls)) - 1;  // internal nodes of the subtree (levels ls .. L-1)
+        const int tasks = 2 * nsub;             // u_l = B w_r and u_r = B^T w_l of each pair
+        const int ngw = tasks >= nw ? 1 : nw / tasks;
+        for (int tk = warp / ngw; tk < tasks; tk += nw / ngw) {
+            const int gw = warp % ngw, idx = tk >> 1;
+            const int lvo = 31 - __clz(idx + 1);
+            const int n = ((g + 1) << lvo) - 1 + (idx + 1 - (1 << lvo));
+            const int sl = rk[2 * n + 1], sr = rk[2 * n + 2], pr = lay[n].z, bo = lay[n].y;
+            const int rs = sr | 1, c = sl + sr;
+            if ((tk & 1) == 0) grp_gemv(sm, bo, rs, 1, sl, sr, pr + sl, sm, pr + c, false, gw, ngw, lane);
+            else grp_gemv(sm, bo, 1, rs, sr, sl, pr, sm, pr + c + sl, false, gw, ngw, lane);
         }
         __syncthreads();
     }
@@ -380,7 +398,7 @@ __device__ __forceinline__ NearItem near_item(const DmHmat &H, int item, int row
 // memory, a warp per pair of rows with every 16-byte streaming load of both rows issued before
 // the sums (rows of up to 512 floats), then the leaf S2N after waiting for the tree pass.
 // Blocks use little shared memory and few registers, so all items are resident at once.
-__global__ void __launch_bounds__(kNearThreads, 6) near_cached_kernel(const __grid_constant__ DmHmat H,
+__global__ void __launch_bounds__(kNearCachedThreads, kNearCachedMinBlocks) near_cached_kernel(const __grid_constant__ DmHmat H,
                                                                     const float *__restrict__ x,
                                                                     float *__restrict__ y, int permuted, int rows,
                                                                     int far) {
@@ -605,7 +623,7 @@ cudaError_t dm_hmatvec(const DmHmat &H, int near_mode, const float *x, float *y,
     if (near_mode == DM_NEAR_CACHED) {
         const size_t smC = sizeof(float) * ((size_t)m4max + (size_t)((rows + 3) & ~3));
         if ((e = dm_allow_smem((const void *)near_cached_kernel, smC)) != cudaSuccess) return e;
-        e = launch_ex(near_cached_kernel, (unsigned)n_items, kNearThreads, smC, st, 1u, far, H, x, y, pm, rows,
+        e = launch_ex(near_cached_kernel, (unsigned)n_items, kNearCachedThreads, smC, st, 1u, far, H, x, y, pm, rows,
                       far ? 1 : 0);
     } else {
         const size_t smC = sizeof(float) * ((size_t)m4max + (size_t)H.leaf_max * H.d);
