@@ -148,6 +148,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned *ctr, unsigned target, int
     return s_ok != 0;
 }
 
+// 1/sqrt(d) for d > 0 without the FP64 divide and square-root sequences (slow on this part's
+// narrow FP64 pipe): d is scaled by an even power of two into [1, 4), an FP32 estimate is
+// refined by two Newton steps y <- y (3 - d y^2) / 2 in FP64 (relative error 2^-23, then
+// ~2^-45, then below FP64 rounding), and the power of two is restored.
+__device__ __forceinline__ double dm_rsqrt_fp64(double d) {
+    const long long bits = __double_as_longlong(d);
+    const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
+    const int half = ex >= 0 ? ex / 2 : -((1 - ex) / 2);
+    const double down = __longlong_as_double((long long)(1023 - 2 * half) << 52);  // 2^-2half
+    const double ds = d * down;
+    double y = (double)rsqrtf((float)ds);
+    y = y * (1.5 - 0.5 * ds * y * y);
+    y = y * (1.5 - 0.5 * ds * y * y);
+    return y * __longlong_as_double((long long)(1023 - half) << 52);  // 2^-half
+}
+
 // exp2 on the MUFU unit (PTX ex2.approx.ftz.f32: documented max error ~2 ulp over its range)
 __device__ __forceinline__ float dm_ex2(float x) {
     float y;

@@ -44,22 +44,6 @@ struct BStepArgs {
     int64_t per;     // rows per block (multiple of 4)
 };
 
-// 1/sqrt(d) for d > 0 without the FP64 divide and square-root sequences (slow on this part's
-// narrow FP64 pipe): d is scaled by an even power of two into [1, 4), an FP32 estimate is
-// refined by two Newton steps y <- y (3 - d y^2) / 2 in FP64 (relative error 2^-23, then
-// ~2^-45, then below FP64 rounding), and the power of two is restored.
-__device__ __forceinline__ double rsqrt_fp64(double d) {
-    const long long bits = __double_as_longlong(d);
-    const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
-    const int half = ex >= 0 ? ex / 2 : -((1 - ex) / 2);
-    const double down = __longlong_as_double((long long)(1023 - 2 * half) << 52);  // 2^-2half
-    const double ds = d * down;
-    double y = (double)rsqrtf((float)ds);
-    y = y * (1.5 - 0.5 * ds * y * y);
-    y = y * (1.5 - 0.5 * ds * y * y);
-    return y * __longlong_as_double((long long)(1023 - half) << 52);  // 2^-half
-}
-
 // Cholesky G = R^T R of a B x B FP64 matrix (row-major) and R^-1, with reciprocal square
 // roots instead of divisions; a pivot that is not positive (a rank-deficient block) raises
 // *flag and is replaced by a tiny positive value.
@@ -78,7 +62,7 @@ __device__ void chol_small(const double (&G)[B][B], double (&R)[B][B], double (&
             if (flag) *flag = 1;
             d = tiny;
         }
-        inv[j] = rsqrt_fp64(d);
+        inv[j] = dm_rsqrt_fp64(d);
         R[j][j] = d * inv[j];
         for (int i = j + 1; i < B; ++i) {
             double t = G[j][i];
