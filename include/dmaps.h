@@ -136,6 +136,26 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs);
  * still written); DM_ECUDA. */
 int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
 
+/* Top-k eigenpairs of `count` compressed handles at once: the batching of many uneven point
+ * clouds (no paper counterpart; each handle's solve is dm_eigs' single-vector Lanczos of
+ * Algorithm 2 in its symmetric form, Section 2.3.1). Every Lanczos step of every handle not
+ * yet converged runs in the same launches: the chained H-matvec of Eq. 2.18 (two launches for
+ * all handles: leaf N2S with the climb up the tree and the near field, then the downward pass
+ * with the leaf S2N), the three Gram-Schmidt passes (three launches), and at each convergence
+ * check one launch of Ritz values for all handles and one host read. A handle leaves the batch
+ * when it converges (its Ritz vectors are formed then), so the launch count per step does not
+ * grow with the number of handles. Each handle keeps its own seed, m_max, check_every (the
+ * smallest is used) and conv_tol; cfg.block_size and block_precision are ignored.
+ * hs: `count` distinct compressed handles on one device; the work runs on hs[0]'s stream
+ * after the queued work of every handle. evals: count x k doubles, handle i at i k,
+ * descending (host or device). evecs: NULL, or `count` pointers, each NULL or N_i x k floats
+ * (host or device, as dm_eigs). status: NULL or `count` ints, DM_OK or DM_ENOCONV per handle.
+ * Returns DM_OK when every handle converged, DM_ENOCONV when some reached m_max (all results
+ * still written). Errors: DM_EINVAL (NULL arguments, count < 1, k outside [1, 32] or >= some
+ * N, handles repeated or on different devices); DM_ESTATE (a handle not compressed);
+ * DM_ENOMEM; DM_ECUDA. */
+int dm_eigs_batch(dm_handle *hs, int32_t count, int32_t k, double *evals, float **evecs, int32_t *status);
+
 /* Diffusion coordinates of the last dm_eigs: psi_i = theta_i^t Dg^-1/2 phi_i
  * (Algorithm 1: t-step random walk and eigendecomposition; the eigenvalues of
  * P^t are theta^t and its right eigenvectors Dg^-1/2 phi). psi: N x k

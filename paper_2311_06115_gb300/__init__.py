@@ -27,7 +27,7 @@ __all__ = [
     "dm_status_str", "dm_last_error", "dm_get_stats", "dm_get_eps", "dm_get_degrees", "dm_get_tree",
     "dm_get_hmatrix", "dm_load_hmatrix", "dm_kernel_launches", "dm_degrees_noalloc", "dm_request",
     "dm_result", "dm_serve_config", "dm_request_bytes", "dm_serve_start", "dm_serve_stop", "dm_submit", "dm_poll",
-    "dm_release", "dm_tune_leaf", "dm_selftest_wait_timeout", "dm_sfu_peak",
+    "dm_release", "dm_tune_leaf", "dm_selftest_wait_timeout", "dm_sfu_peak", "dm_eigs_batch",
 ]
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ESTATE, DM_ENOCONV, DM_ETIMEOUT, DM_ECUDA, DM_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
@@ -131,6 +131,7 @@ def load(build_if_missing: bool = True):
         "dm_tune_leaf": (i32, [vp, f64, i32, i32, vp, i32, C.POINTER(i32), vp]),
         "dm_selftest_wait_timeout": (i32, [i32, i32, i64, C.POINTER(i32)]),
         "dm_sfu_peak": (i32, [C.POINTER(i64), C.POINTER(C.c_float)]),
+        "dm_eigs_batch": (i32, [vp, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -320,6 +321,20 @@ def dm_eigs(h: Handle, k: int, evecs: bool = True, device_out: bool = False):
     st = load().dm_eigs(h, int(k), ev.ctypes.data, _ptr(vec) if vec is not None else None)
     _check(st, allow=(DM_ENOCONV,))
     return ev, (vec.T if vec is not None else None), st == DM_OK
+
+
+def dm_eigs_batch(handles, k: int, evecs: bool = True):
+    """dm_eigs_batch: (evals (count, k) float64, [evecs (N_i, k) float32 column-major or None],
+    status (count,) int32) for a list of compressed handles solved together."""
+    n = len(handles)
+    hs = (C.c_void_p * n)(*[h.ptr for h in handles])
+    ev = np.empty((n, k), dtype=np.float64)
+    vecs = [np.empty((k, h.N), dtype=np.float32) for h in handles] if evecs else None
+    vp = (C.c_void_p * n)(*[v.ctypes.data for v in vecs]) if evecs else None
+    status = np.empty(n, dtype=np.int32)
+    st = load().dm_eigs_batch(hs, n, int(k), ev.ctypes.data, vp, status.ctypes.data)
+    _check(st, allow=(DM_ENOCONV,))
+    return ev, ([v.T for v in vecs] if evecs else None), status
 
 
 def dm_coords(h: Handle, k: int, t: int = 1) -> np.ndarray:

@@ -761,25 +761,53 @@ int ensure_lanczos(dm_ctx *h) {
     L.N = h->N;
     L.ldv = round_up(h->N, 64);
     L.m_max = h->cfg.m_max;
-    DM_CHECK(h->alloc(&L.V, (size_t)(L.m_max + 1) * L.ldv, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.z, (size_t)L.ldv, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.alpha, (size_t)L.m_max + 1, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.beta, (size_t)L.m_max + 1, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.h, (size_t)2 * (2 * (L.m_max + 1) + 2), G_LANCZOS));
-    DM_CHECK(h->alloc(&L.nrm2, 1, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.theta, (size_t)kmax, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.resid, (size_t)kmax, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.Y, (size_t)kmax * L.m_max, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.Yf, (size_t)kmax * L.m_max, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.twork, (size_t)kmax * 6 * L.m_max, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.colsum, (size_t)kmax, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.phi, (size_t)kmax * h->N, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.best, (size_t)kmax, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.neg, (size_t)kmax, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.bar, 1, G_LANCZOS));
-    DM_CHECK(h->alloc(&L.err, 1, G_LANCZOS));
+    // every buffer of the eigensolver carved from one allocation (one allocator call per
+    // handle: many small handles -- batched clouds, serving -- pay for calls, not bytes)
+    size_t total = 0;
+    auto take = [&](size_t bytes) {
+        const size_t off = total;
+        total += (bytes + 255) & ~size_t(255);
+        return off;
+    };
+    const size_t oV = take(sizeof(float) * (size_t)(L.m_max + 1) * L.ldv);
+    const size_t oz = take(sizeof(float) * (size_t)L.ldv);
+    const size_t oal = take(sizeof(double) * ((size_t)L.m_max + 1));
+    const size_t obe = take(sizeof(double) * ((size_t)L.m_max + 1));
+    const size_t oh = take(sizeof(double) * (size_t)2 * (2 * (L.m_max + 1) + 2));
+    const size_t onr = take(sizeof(double));
+    const size_t oth = take(sizeof(double) * (size_t)kmax);
+    const size_t ors = take(sizeof(double) * (size_t)kmax);
+    const size_t oY = take(sizeof(double) * (size_t)kmax * L.m_max);
+    const size_t oYf = take(sizeof(float) * (size_t)kmax * L.m_max);
+    const size_t otw = take(sizeof(double) * (size_t)kmax * 6 * L.m_max);
+    const size_t ocs = take(sizeof(double) * (size_t)kmax);
+    const size_t oph = take(sizeof(float) * (size_t)kmax * h->N);
+    const size_t obs = take(sizeof(unsigned long long) * (size_t)kmax);
+    const size_t ong = take(sizeof(int) * (size_t)kmax);
+    const size_t obar = take(sizeof(unsigned));
+    const size_t oerr = take(sizeof(int));
+    const size_t oev = take(sizeof(float) * (size_t)kmax * h->N);
+    unsigned char *base = nullptr;
+    DM_CHECK(h->alloc(&base, total, G_LANCZOS));
+    L.V = reinterpret_cast<float *>(base + oV);
+    L.z = reinterpret_cast<float *>(base + oz);
+    L.alpha = reinterpret_cast<double *>(base + oal);
+    L.beta = reinterpret_cast<double *>(base + obe);
+    L.h = reinterpret_cast<double *>(base + oh);
+    L.nrm2 = reinterpret_cast<double *>(base + onr);
+    L.theta = reinterpret_cast<double *>(base + oth);
+    L.resid = reinterpret_cast<double *>(base + ors);
+    L.Y = reinterpret_cast<double *>(base + oY);
+    L.Yf = reinterpret_cast<float *>(base + oYf);
+    L.twork = reinterpret_cast<double *>(base + otw);
+    L.colsum = reinterpret_cast<double *>(base + ocs);
+    L.phi = reinterpret_cast<float *>(base + oph);
+    L.best = reinterpret_cast<unsigned long long *>(base + obs);
+    L.neg = reinterpret_cast<int *>(base + ong);
+    L.bar = reinterpret_cast<unsigned *>(base + obar);
+    L.err = reinterpret_cast<int *>(base + oerr);
+    h->evecs = reinterpret_cast<float *>(base + oev);
     DM_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), h->stream));
-    DM_CHECK(h->alloc(&h->evecs, (size_t)kmax * h->N, G_LANCZOS));
     // zero the whole basis once: padding rows beyond N must read as zero
     // only the padding rows N..ldv-1 of each basis column are read before being written
     // (the step kernel works on 16-byte row quads up to ldv): zero those, not the whole basis
@@ -1440,6 +1468,222 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs) {
     if (!yd) DM_CUDA(cudaMemcpyAsync(y, dy, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
     DM_CUDA(cudaStreamSynchronize(h->stream));
     return DM_OK;
+}
+
+int dm_eigs_batch(dm_handle *hs, int32_t count, int32_t k, double *evals, float **evecs, int32_t *status) {
+    if (!hs || !evals) return fail(DM_EINVAL, "dm_eigs_batch: NULL handles or evals");
+    if (count < 1) return fail(DM_EINVAL, "dm_eigs_batch: count must be >= 1");
+    if (k < 1 || k > dm_lanczos_kmax()) return fail(DM_EINVAL, "dm_eigs_batch: k must be in [1, %d]", dm_lanczos_kmax());
+    for (int i = 0; i < count; ++i) {
+        dm_ctx *h = hs[i];
+        if (!h) return fail(DM_EINVAL, "dm_eigs_batch: handle %d is NULL", i);
+        if (!h->compressed) return fail(DM_ESTATE, "dm_eigs_batch: handle %d is not compressed", i);
+        if (k >= h->N || k > h->cfg.m_max) return fail(DM_EINVAL, "dm_eigs_batch: k too large for handle %d", i);
+        if (h->device != hs[0]->device) return fail(DM_EINVAL, "dm_eigs_batch: handles on different devices");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) return fail(DM_EINVAL, "dm_eigs_batch: handle %d appears twice", i);
+    }
+    DM_CHECK(set_device(hs[0]));
+    cudaStream_t st = hs[0]->stream;
+    for (int i = 0; i < count; ++i) DM_CHECK(ensure_lanczos(hs[i]));
+    // order the batch after every handle's queued work (their streams), then work on `st`
+    for (int i = 1; i < count; ++i) {
+        cudaEvent_t ev = nullptr;
+        DM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        DM_CUDA(cudaEventRecord(ev, hs[i]->stream));
+        DM_CUDA(cudaStreamWaitEvent(st, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    PhaseTimer t(st);
+    int m_hi = 0;
+    for (int i = 0; i < count; ++i) m_hi = hs[i]->lz.m_max > m_hi ? hs[i]->lz.m_max : m_hi;
+    const int qt = dm_step_tile_quads(m_hi);
+    std::vector<DmChainProblem> cp(count);
+    std::vector<DmLanczosProblem> lp(count);
+    std::vector<DmChainShape> shape(count);
+    std::vector<int> cap(count), sblk(count);
+    for (int i = 0; i < count; ++i) {
+        dm_ctx *h = hs[i];
+        DmLanczos &Lz = h->lz;
+        const DmHmat H = h->hmat();
+        shape[i] = dm_chain_shape(H, h->near_mode);
+        DmChainProblem &c = cp[i];
+        c.H = H;
+        c.x = Lz.V;
+        c.xstep = Lz.ldv;
+        c.y = Lz.z;
+        c.permuted = 1;
+        c.near_mode = h->near_mode;
+        c.near_rows = shape[i].near_rows;
+        c.climb_smem = shape[i].climb_smem;
+        c.chain_smem = shape[i].chain_smem;
+        DmLanczosProblem &l = lp[i];
+        l.V = Lz.V;
+        l.ldv = Lz.ldv;
+        l.z = Lz.z;
+        l.h = Lz.h;
+        l.hstride = dm_lanczos_hstride(Lz.m_max);
+        l.alpha = Lz.alpha;
+        l.beta = Lz.beta;
+        l.m_max = Lz.m_max;
+        l.qt = qt;
+        l.theta = Lz.theta;
+        l.resid = Lz.resid;
+        cap[i] = (int)(h->cfg.m_max < h->N ? h->cfg.m_max : h->N);
+        const int64_t qn = Lz.ldv >> 2;
+        sblk[i] = (int)((qn + qt - 1) / qt);
+        if (sblk[i] > 304) sblk[i] = 304;
+        if (sblk[i] < 1) sblk[i] = 1;
+        DM_CUDA(cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (size_t)l.hstride, st));
+        DM_CUDA(dm_lanczos_start(Lz, h->perm, h->cfg.seed, st));
+    }
+    // device buffers of the batch, released on every return path
+    struct Buf {
+        void *p = nullptr;
+        cudaStream_t s;
+        ~Buf() {
+            if (p) cudaFreeAsync(p, s);
+        }
+    };
+    auto dalloc = [&](Buf &b, size_t bytes) -> int {
+        b.s = st;
+        if (cudaMallocAsync(&b.p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DM_ENOMEM, "dm_eigs_batch: cudaMallocAsync of %zu bytes failed", bytes);
+        }
+        return DM_OK;
+    };
+    size_t n_up_all = 0, n_dn_all = 0, n_st_all = 0;
+    for (int i = 0; i < count; ++i) {
+        n_up_all += (size_t)shape[i].up_blocks + shape[i].near_blocks;
+        n_dn_all += (size_t)shape[i].down_blocks;
+        n_st_all += (size_t)sblk[i];
+    }
+    Buf bcp, blp, bup, bdn, bst, bact, bth, brs, bbt;
+    DM_CHECK(dalloc(bcp, sizeof(DmChainProblem) * count));
+    DM_CHECK(dalloc(blp, sizeof(DmLanczosProblem) * count));
+    DM_CHECK(dalloc(bup, sizeof(int2) * n_up_all));
+    DM_CHECK(dalloc(bdn, sizeof(int2) * n_dn_all));
+    DM_CHECK(dalloc(bst, sizeof(int4) * n_st_all));
+    DM_CHECK(dalloc(bact, sizeof(int) * count));
+    DM_CHECK(dalloc(bth, sizeof(double) * count * k));
+    DM_CHECK(dalloc(brs, sizeof(double) * count * k));
+    DM_CHECK(dalloc(bbt, sizeof(double) * count));
+    DM_CUDA(cudaMemcpyAsync(bcp.p, cp.data(), sizeof(DmChainProblem) * count, cudaMemcpyHostToDevice, st));
+    DM_CUDA(cudaMemcpyAsync(blp.p, lp.data(), sizeof(DmLanczosProblem) * count, cudaMemcpyHostToDevice, st));
+    // launch maps of the active problems (leaf climbs of every problem first, then near items)
+    std::vector<int> act(count);
+    for (int i = 0; i < count; ++i) act[i] = i;
+    std::vector<int2> mup, mdn;
+    std::vector<int4> mst;
+    int n_up = 0, n_dn = 0, n_st = 0;
+    size_t smem1 = 0, smem2 = 0;
+    auto rebuild = [&]() -> int {
+        mup.clear();
+        mdn.clear();
+        mst.clear();
+        smem1 = smem2 = 0;
+        for (int p : act) {
+            for (int b = 0; b < shape[p].up_blocks; ++b) mup.push_back(make_int2(p, b));
+            for (int b = 0; b < shape[p].down_blocks; ++b) mdn.push_back(make_int2(p, b));
+            for (int b = 0; b < sblk[p]; ++b) mst.push_back(make_int4(p, b, sblk[p], 0));
+            smem1 = shape[p].smem1 > smem1 ? shape[p].smem1 : smem1;
+            smem2 = shape[p].smem2 > smem2 ? shape[p].smem2 : smem2;
+        }
+        for (int p : act)
+            for (int b = 0; b < shape[p].near_blocks; ++b) mup.push_back(make_int2(p, shape[p].up_blocks + b));
+        n_up = (int)mup.size();
+        n_dn = (int)mdn.size();
+        n_st = (int)mst.size();
+        DM_CUDA(cudaMemcpyAsync(bup.p, mup.data(), sizeof(int2) * mup.size(), cudaMemcpyHostToDevice, st));
+        DM_CUDA(cudaMemcpyAsync(bdn.p, mdn.data(), sizeof(int2) * mdn.size(), cudaMemcpyHostToDevice, st));
+        DM_CUDA(cudaMemcpyAsync(bst.p, mst.data(), sizeof(int4) * mst.size(), cudaMemcpyHostToDevice, st));
+        DM_CUDA(cudaMemcpyAsync(bact.p, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice, st));
+        // the host vectors are pageable: each copy has staged its source when it returns, but
+        // they are rebuilt in place later, so wait for the copies
+        DM_CUDA(cudaStreamSynchronize(st));
+        return DM_OK;
+    };
+    DM_CHECK(rebuild());
+    const int first_check = (5 * k + 3) / 4 + 5;
+    int every = hs[0]->cfg.check_every;
+    for (int i = 1; i < count; ++i) every = hs[i]->cfg.check_every < every ? hs[i]->cfg.check_every : every;
+    if (every < 1) every = 1;
+    std::vector<double> th((size_t)count * k), rs((size_t)count * k), bt(count);
+    std::vector<int> done(count, 0), conv(count, 0), mstop(count, 0);
+    std::vector<std::vector<double>> theta_final(count, std::vector<double>(k, 0.0));
+    int since = 0;
+    for (int j = 0; !act.empty(); ++j) {
+        DM_CUDA(dm_hmatvec_chain_batch(static_cast<const DmChainProblem *>(bcp.p), static_cast<const int2 *>(bup.p), n_up,
+                                       smem1, static_cast<const int2 *>(bdn.p), n_dn, smem2, j, st));
+        DM_CUDA(dm_lanczos_step_batch(static_cast<const DmLanczosProblem *>(blp.p), static_cast<const int4 *>(bst.p),
+                                      n_st, j, m_hi, st));
+        const int m = j + 1;
+        ++since;
+        bool at_cap = false;
+        for (int p : act)
+            if (m >= cap[p]) at_cap = true;
+        if (!((m >= first_check && since >= every) || at_cap)) continue;
+        since = 0;
+        const int nact = (int)act.size();
+        DM_CUDA(dm_lanczos_ritz_batch(static_cast<const DmLanczosProblem *>(blp.p), static_cast<const int *>(bact.p),
+                                      nact, m, k, static_cast<double *>(bth.p), static_cast<double *>(brs.p),
+                                      static_cast<double *>(bbt.p), st));
+        DM_CUDA(cudaMemcpyAsync(th.data(), bth.p, sizeof(double) * nact * k, cudaMemcpyDeviceToHost, st));
+        DM_CUDA(cudaMemcpyAsync(rs.data(), brs.p, sizeof(double) * nact * k, cudaMemcpyDeviceToHost, st));
+        DM_CUDA(cudaMemcpyAsync(bt.data(), bbt.p, sizeof(double) * nact, cudaMemcpyDeviceToHost, st));
+        DM_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> keep;
+        for (int slot = 0; slot < nact; ++slot) {
+            const int p = act[slot];
+            const double *tp = th.data() + (size_t)slot * k, *rp = rs.data() + (size_t)slot * k;
+            const double scale = std::fabs(tp[0]) > 0 ? std::fabs(tp[0]) : 1.0;
+            bool ok = true;
+            for (int i = 0; i < k; ++i)
+                if (!(rp[i] <= hs[p]->cfg.conv_tol * scale)) ok = false;
+            const bool breakdown = bt[slot] <= 1e-12 * scale;
+            if (ok || breakdown || m >= cap[p]) {
+                // finished: Ritz vectors of this problem (its theta is current in Lz.theta)
+                dm_ctx *h = hs[p];
+                conv[p] = (ok || breakdown) ? 1 : 0;
+                mstop[p] = m;
+                for (int i = 0; i < k; ++i) theta_final[p][i] = tp[i];
+                DM_CUDA(dm_lanczos_tvecs(h->lz, m, k, st));
+                DM_CUDA(dm_lanczos_phi(h->lz, m, k, h->perm, h->evecs, st));
+                done[p] = 1;
+            } else {
+                keep.push_back(p);
+            }
+        }
+        if ((int)keep.size() != nact) {
+            act.swap(keep);
+            if (!act.empty()) DM_CHECK(rebuild());
+        }
+    }
+    DM_CUDA(cudaStreamSynchronize(st));
+    const float ms = t.stop();
+    bool all_conv = true;
+    std::vector<double> ev_all((size_t)count * k);
+    for (int p = 0; p < count; ++p)
+        for (int i = 0; i < k; ++i) ev_all[(size_t)p * k + i] = theta_final[p][i];
+    if (is_device_ptr(evals))
+        DM_CUDA(cudaMemcpy(evals, ev_all.data(), sizeof(double) * ev_all.size(), cudaMemcpyHostToDevice));
+    else
+        std::copy(ev_all.begin(), ev_all.end(), evals);
+    for (int p = 0; p < count; ++p) {
+        dm_ctx *h = hs[p];
+        if (evecs && evecs[p]) DM_CHECK(copy_out(h, evecs[p], h->evecs, sizeof(float) * (size_t)k * h->N));
+        if (status) status[p] = conv[p] ? DM_OK : DM_ENOCONV;
+        h->last_k = k;
+        h->stats.lanczos_iters = mstop[p];
+        h->stats.converged = conv[p];
+        h->stats.ms_eigs = ms;
+        h->stats.matvec_calls = 0;
+        h->stats.ms_matvec = 0.f;
+        if (!conv[p]) all_conv = false;
+    }
+    for (int p = 0; p < count; ++p) DM_CUDA(cudaStreamSynchronize(hs[p]->stream));
+    return all_conv ? DM_OK : fail(DM_ENOCONV, "dm_eigs_batch: some handles did not converge within m_max");
 }
 
 int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs) {

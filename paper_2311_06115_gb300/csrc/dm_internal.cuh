@@ -327,6 +327,25 @@ int dm_near_rows(int near_mode, int leaf_max);
 // threads cannot shrink it between another thread's check and its launch.
 cudaError_t dm_allow_smem(const void *kern, size_t bytes);
 // the chained two-launch form (k_hmatvec.cu), used when the cluster pass does not fit
+// launch shape of the chained form for one problem (blocks of its two launches, shared memory)
+struct DmChainShape {
+    int near_rows, up_blocks, near_blocks, down_blocks, climb_smem, chain_smem;
+    size_t smem1, smem2;
+};
+DmChainShape dm_chain_shape(const DmHmat &H, int near_mode);
+// one problem of a batched chained H-matvec (device array entry)
+struct DmChainProblem {
+    DmHmat H;
+    const float *x;  // input at step j: x + j xstep (position order when permuted = 1)
+    int64_t xstep;
+    float *y;        // output
+    int permuted, near_mode, near_rows, climb_smem, chain_smem;
+};
+// y = K~ x for many problems in two launches; map_up / map_down: {problem, its block index}
+// per block (leaf climbs of every problem before the near items), shared memory the largest
+// of the problems' shapes; j selects each problem's input x + j xstep
+cudaError_t dm_hmatvec_chain_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem1,
+                                   const int2 *map_down, int n_down, size_t smem2, int j, cudaStream_t st);
 cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted,
                              cudaStream_t st);
 int dm_near_item_rows(int near_mode, int leaf_max);
@@ -415,6 +434,29 @@ struct DmLanczos {
     int *err;         // set when a bounded device wait gave up
 };
 int dm_lanczos_kmax();
+// one problem of a batched single-vector Lanczos (device array entry): its basis, work vector,
+// accumulators (hstride = dm_lanczos_hstride(m_max) per parity), coefficients and Ritz buffers
+struct DmLanczosProblem {
+    float *V;
+    int64_t ldv;
+    float *z;
+    double *h;
+    int hstride;
+    double *alpha, *beta;
+    int m_max, qt;
+    double *theta, *resid;
+};
+int dm_lanczos_hstride(int m_max);
+int dm_step_phased_threads();
+int dm_step_tile_quads(int m_max);
+// the three Gram-Schmidt passes of step j for many problems (three launches); map[block] =
+// {problem, its block index, its block count, 0}; m_max_hi sizes the shared memory
+cudaError_t dm_lanczos_step_batch(const DmLanczosProblem *P, const int4 *map, int nblocks, int j, int m_max_hi,
+                                  cudaStream_t st);
+// Ritz values / residual bounds at step m for the problems act[0..nact), one launch; the
+// values also land in theta_out / resid_out (k per slot, slot order)
+cudaError_t dm_lanczos_ritz_batch(const DmLanczosProblem *P, const int *act, int nact, int m, int k,
+                                  double *theta_out, double *resid_out, double *beta_out, cudaStream_t st);
 cudaError_t dm_launch_barrier_selftest(unsigned *ctr, int *err, int blocks, int missing, long long spin_limit,
                                        cudaStream_t st);
 cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st);

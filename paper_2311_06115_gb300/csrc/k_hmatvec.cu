@@ -124,8 +124,10 @@ __device__ __forceinline__ void gemv_rows_smem(const float *Ps, int ld4, int s, 
     }
 }
 
-__global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const float *__restrict__ x, int permuted,
-                                                            int near_mode, int near_rows, int climb_smem) {
+// body of the chained form's first launch for one problem: block `bid` of its grid (leaf climbs
+// first, then near items); shared by the single-problem and the batched launches
+__device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const float *__restrict__ x, int permuted,
+                                             int near_mode, int near_rows, int climb_smem) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_go;
@@ -133,9 +135,9 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const floa
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m4max = (H.leaf_max + 3) & ~3;
 
-    if ((int)blockIdx.x < nleaves) {
+    if (bid < nleaves) {
         // ------------------------------------------------ leaf N2S, then climb
-        const int leaf = blockIdx.x;
+        const int leaf = bid;
         int node = nleaves - 1 + leaf;
         int64_t st, sz;
         dm_node_range(H.N, node, &st, &sz);
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const floa
     }
 
     // ---------------------------------------------------- near field
-    const int item = blockIdx.x - nleaves;
+    const int item = bid - nleaves;
     const int per_leaf = (H.leaf_max + near_rows - 1) / near_rows;
     const int leaf = item / per_leaf, chunk = item % per_leaf;
     int64_t st, sz;
@@ -318,17 +320,31 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(DmHmat H, const floa
     }
 }
 
+__global__ void __launch_bounds__(kHThreads) near_up_kernel(const __grid_constant__ DmHmat H,
+                                                            const float *__restrict__ x, int permuted, int near_mode,
+                                                            int near_rows, int climb_smem) {
+    near_up_body(H, (int)blockIdx.x, x, permuted, near_mode, near_rows, climb_smem);
+}
+
+// the same for many problems: map[block] = {problem, its block index}
+__global__ void __launch_bounds__(kHThreads) near_up_batch_kernel(const DmChainProblem *__restrict__ P,
+                                                                  const int2 *__restrict__ map, int j) {
+    const int2 pb = map[blockIdx.x];
+    const DmChainProblem &p = P[pb.x];
+    near_up_body(p.H, pb.y, p.x + (size_t)j * p.xstep, p.permuted, p.near_mode, p.near_rows, p.climb_smem);
+}
+
 // Downward pass for one leaf. The ancestor chain (S2S parts u of the ancestors at
 // levels 2..L and, per step, the slice of the parent's P that maps to the child) is
 // fetched into shared memory in one batch of independent loads when it fits
 // (`chain_in_smem`), then combined top-down: t = P_parent(:, child)^T t + u_child.
 // The leaf's own S2N reads the point-major copy PT: one contiguous row per point.
-__global__ void __launch_bounds__(kDownThreads) down_kernel(DmHmat H, float *__restrict__ y, int permuted,
-                                                             int chain_in_smem) {
+__device__ __forceinline__ void down_body(const DmHmat &H, int bid, float *__restrict__ y, int permuted,
+                                          int chain_in_smem) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     // kDownSplit blocks per leaf, each handling a contiguous quarter of its points
-    const int leaf = blockIdx.x / kDownSplit, part = blockIdx.x % kDownSplit;
+    const int leaf = bid / kDownSplit, part = bid % kDownSplit;
     const int nleaves = 1 << H.L;
     const int node_leaf = nleaves - 1 + leaf;
     int64_t st, sz;
@@ -439,6 +455,18 @@ __global__ void __launch_bounds__(kDownThreads) down_kernel(DmHmat H, float *__r
     }
 }
 
+__global__ void __launch_bounds__(kDownThreads) down_kernel(const __grid_constant__ DmHmat H, float *__restrict__ y,
+                                                             int permuted, int chain_in_smem) {
+    down_body(H, (int)blockIdx.x, y, permuted, chain_in_smem);
+}
+
+__global__ void __launch_bounds__(kDownThreads) down_batch_kernel(const DmChainProblem *__restrict__ P,
+                                                                  const int2 *__restrict__ map) {
+    const int2 pb = map[blockIdx.x];
+    const DmChainProblem &p = P[pb.x];
+    down_body(p.H, pb.y, p.y, p.permuted, p.chain_smem);
+}
+
 }  // namespace
 
 int dm_near_rows(int near_mode, int leaf_max) {
@@ -447,38 +475,60 @@ int dm_near_rows(int near_mode, int leaf_max) {
     return (leaf_max + chunks - 1) / chunks;
 }
 
-cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted, cudaStream_t st) {
+DmChainShape dm_chain_shape(const DmHmat &H, int near_mode) {
+    DmChainShape c;
     const int nleaves = 1 << H.L;
-    const int rows = dm_near_rows(near_mode, H.leaf_max);
-    const int per_leaf = (H.leaf_max + rows - 1) / rows;
+    c.near_rows = dm_near_rows(near_mode, H.leaf_max);
+    const int per_leaf = (H.leaf_max + c.near_rows - 1) / c.near_rows;
+    c.up_blocks = nleaves;
+    c.near_blocks = nleaves * per_leaf;
+    c.down_blocks = nleaves * kDownSplit;
     const int m4max = (H.leaf_max + 3) & ~3;
     const size_t RH = (size_t)H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
     // up items: staged x, children weights, and (when small enough) the parent's B and P
     const size_t climb_bytes = sizeof(float) * (RH * RH4 + RH * C4);
-    const int climb_smem = climb_bytes <= 96 * 1024 ? 1 : 0;
-    size_t smem1 = sizeof(float) * ((size_t)m4max + C4 + 2 * (size_t)H.max_rank + 4) + (climb_smem ? climb_bytes : 0);
+    c.climb_smem = climb_bytes <= 96 * 1024 ? 1 : 0;
+    c.smem1 = sizeof(float) * ((size_t)m4max + C4 + 2 * (size_t)H.max_rank + 4) + (c.climb_smem ? climb_bytes : 0);
     if (near_mode != DM_NEAR_CACHED) {
         const size_t s2 = sizeof(float) * (size_t)(m4max + H.leaf_max * H.d);
-        if (s2 > smem1) smem1 = s2;
+        if (s2 > c.smem1) c.smem1 = s2;
     }
+    // the ancestor chain fits in shared memory for the usual ranks; otherwise read it from L2
+    const size_t chain = sizeof(float) * (2 * RH4 + (size_t)(H.L > 1 ? H.L - 1 : 0) * (RH4 + RH * RH4));
+    c.chain_smem = chain <= 160 * 1024 ? 1 : 0;
+    c.smem2 = c.chain_smem ? chain : sizeof(float) * 2 * RH4;
+    return c;
+}
+
+cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted, cudaStream_t st) {
+    const DmChainShape c = dm_chain_shape(H, near_mode);
     {
-        cudaError_t e = dm_allow_smem((const void *)near_up_kernel, smem1);
+        cudaError_t e = dm_allow_smem((const void *)near_up_kernel, c.smem1);
         if (e != cudaSuccess) return e;
     }
-    near_up_kernel<<<nleaves + nleaves * per_leaf, kHThreads, smem1, st>>>(H, x, permuted ? 1 : 0, near_mode, rows,
-                                                                            climb_smem);
+    near_up_kernel<<<c.up_blocks + c.near_blocks, kHThreads, c.smem1, st>>>(H, x, permuted ? 1 : 0, near_mode,
+                                                                             c.near_rows, c.climb_smem);
     dm_count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the ancestor chain fits in shared memory for the usual ranks; otherwise read it from L2
-    const size_t chain = sizeof(float) * (2 * RH4 + (size_t)(H.L > 1 ? H.L - 1 : 0) * (RH4 + RH * RH4));
-    const int in_smem = chain <= 160 * 1024 ? 1 : 0;
-    const size_t smem2 = in_smem ? chain : sizeof(float) * 2 * RH4;
     {
-        cudaError_t e2 = dm_allow_smem((const void *)down_kernel, smem2);
+        cudaError_t e2 = dm_allow_smem((const void *)down_kernel, c.smem2);
         if (e2 != cudaSuccess) return e2;
     }
-    down_kernel<<<nleaves * kDownSplit, kDownThreads, smem2, st>>>(H, y, permuted ? 1 : 0, in_smem);
+    down_kernel<<<c.down_blocks, kDownThreads, c.smem2, st>>>(H, y, permuted ? 1 : 0, c.chain_smem);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t dm_hmatvec_chain_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem1,
+                                   const int2 *map_down, int n_down, size_t smem2, int j, cudaStream_t st) {
+    cudaError_t e = dm_allow_smem((const void *)near_up_batch_kernel, smem1);
+    if (e != cudaSuccess) return e;
+    if ((e = dm_allow_smem((const void *)down_batch_kernel, smem2)) != cudaSuccess) return e;
+    near_up_batch_kernel<<<n_up, kHThreads, smem1, st>>>(P, map_up, j);
+    dm_count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    down_batch_kernel<<<n_down, kDownThreads, smem2, st>>>(P, map_down);
     dm_count_launches(1);
     return cudaGetLastError();
 }

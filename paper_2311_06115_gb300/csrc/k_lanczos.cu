@@ -171,11 +171,12 @@ __device__ __forceinline__ float4 sub_parts(float4 z, const float4 *part, int nc
     return make_float4(z.x - s.x, z.y - s.y, z.z - s.z, z.w - s.w);
 }
 
+// body of the step for one problem: block `bid` of `nblk` blocks (its rows); shared by the
+// single-problem launches and the batched one (phased passes only)
 template <int NT>
-__global__ void __launch_bounds__(NT) lanczos_step_kernel(float *V, int64_t ldv, int j, float *z,
-                                                                    double *hbuf, int hstride, double *alpha,
-                                                                    double *beta, int m_max, int qt, unsigned *bar,
-                                                                    int *err, int phase) {
+__device__ __forceinline__ void lanczos_step_body(float *V, int64_t ldv, int j, float *z, double *hbuf, int hstride,
+                                                  double *alpha, double *beta, int m_max, int qt, unsigned *bar,
+                                                  int *err, int phase, int bid, int nblk) {
     constexpr int kStepWarps = NT / 32;
     // phase < 0: the whole step in one cooperative launch, passes separated by grid
     // barriers; phase 0..2: that pass alone (ordinary launches, the kernel boundary
@@ -193,9 +194,9 @@ __global__ void __launch_bounds__(NT) lanczos_step_kernel(float *V, int64_t ldv,
     double *h0 = hbuf + (size_t)(j & 1) * hstride, *h1 = h0 + (m_max + 1), *nz = h1 + (m_max + 1);
     double *other = hbuf + (size_t)((j + 1) & 1) * hstride;
     const int64_t Qn = ldv >> 2;
-    const int64_t per = (Qn + gridDim.x - 1) / gridDim.x;
-    const int64_t qb0 = blockIdx.x * per, qb1 = (qb0 + per < Qn) ? qb0 + per : Qn;
-    const unsigned G = gridDim.x;
+    const int64_t per = (Qn + nblk - 1) / nblk;
+    const int64_t qb0 = bid * per, qb1 = (qb0 + per < Qn) ? qb0 + per : Qn;
+    const unsigned G = (unsigned)nblk;
     const bool all = phase < 0;
 
     if (all || phase == 0) {  // ---- A: h0 = V^T z
@@ -267,13 +268,32 @@ __global__ void __launch_bounds__(NT) lanczos_step_kernel(float *V, int64_t ldv,
     }
     // block 0 records the coefficients and clears the other parity's accumulators, which
     // step j + 1 uses (step j - 1, their last user, has finished)
-    if (blockIdx.x == 0) {
+    if (bid == 0) {
         if (threadIdx.x == 0) {
             alpha[j] = __ldcg(h0 + j) + __ldcg(h1 + j);
             beta[j] = b;
         }
         for (int c = threadIdx.x; c < hstride; c += blockDim.x) other[c] = 0.0;
     }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) lanczos_step_kernel(float *V, int64_t ldv, int j, float *z, double *hbuf,
+                                                          int hstride, double *alpha, double *beta, int m_max, int qt,
+                                                          unsigned *bar, int *err, int phase) {
+    lanczos_step_body<NT>(V, ldv, j, z, hbuf, hstride, alpha, beta, m_max, qt, bar, err, phase, (int)blockIdx.x,
+                          (int)gridDim.x);
+}
+
+// one pass (phase 0..2) of the step for many problems: map[block] = {problem, its block, its
+// block count}; every problem at the same step j
+__global__ void __launch_bounds__(kStepThreadsPhased) lanczos_step_batch_kernel(const DmLanczosProblem *__restrict__ P,
+                                                                                const int4 *__restrict__ map, int j,
+                                                                                int phase) {
+    const int4 pb = map[blockIdx.x];
+    const DmLanczosProblem &p = P[pb.x];
+    lanczos_step_body<kStepThreadsPhased>(p.V, p.ldv, j, p.z, p.h, p.hstride, p.alpha, p.beta, p.m_max, p.qt,
+                                          nullptr, nullptr, phase, pb.y, pb.z);
 }
 
 size_t step_smem_bytes(int m_max, int qt, int warps) {
@@ -364,10 +384,8 @@ __device__ void charpoly(const double *__restrict__ al, const double *__restrict
 // bits per round), then the residual bound beta_{m-1} |y_m| from
 // |y_m|^2 = |p_{m-1}(theta) / p_m'(theta)|.
 constexpr int kRitzThreads = 128;
-__global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__restrict__ alpha,
-                                                            const double *__restrict__ beta, int m,
-                                                            double *__restrict__ theta, double *__restrict__ resid,
-                                                            double *__restrict__ work) {
+__device__ __forceinline__ void ritz_body(const double *__restrict__ alpha, const double *__restrict__ beta, int m,
+                                          double *__restrict__ theta, double *__restrict__ resid, int iv) {
     extern __shared__ double sd[];
     double *al = sd, *b2 = sd + m;
     float *al32 = reinterpret_cast<float *>(b2 + m), *b232 = al32 + m;
@@ -403,7 +421,7 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
     }
     __syncthreads();
     double lo = s_lo, hi = s_hi;
-    const int target = m - 1 - (int)blockIdx.x;  // ascending index of the wanted eigenvalue
+    const int target = m - 1 - iv;  // ascending index of the wanted eigenvalue
     constexpr double kDen = (double)(kRitzThreads + 1);
     // three coarse rounds with FP32 counts (the FP64 pipe is narrow on this part)
     float flo = (float)lo, fhi = (float)hi;
@@ -504,8 +522,35 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
             charpoly(al, b2, m, th, &p, &pm, &dp);
             y2 = (dp != 0.0) ? fabs(pm / dp) : 1.0;
         }
-        theta[blockIdx.x] = th;
-        resid[blockIdx.x] = beta[m - 1] * sqrt(fmin(y2, 1.0));
+        theta[iv] = th;
+        resid[iv] = beta[m - 1] * sqrt(fmin(y2, 1.0));
+    }
+}
+
+__global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__restrict__ alpha,
+                                                            const double *__restrict__ beta, int m,
+                                                            double *__restrict__ theta, double *__restrict__ resid,
+                                                            double *__restrict__ work) {
+    (void)work;
+    ritz_body(alpha, beta, m, theta, resid, (int)blockIdx.x);
+}
+
+// Ritz values and residual bounds of many problems at the same step (grid k x problems,
+// blockIdx.y indexes `act`); also copied, per problem slot, to the contiguous theta_out /
+// resid_out (k per slot) for one host read
+__global__ void __launch_bounds__(kRitzThreads) ritz_batch_kernel(const DmLanczosProblem *__restrict__ P,
+                                                                  const int *__restrict__ act, int m, int k,
+                                                                  double *__restrict__ theta_out,
+                                                                  double *__restrict__ resid_out,
+                                                                  double *__restrict__ beta_out) {
+    const int slot = blockIdx.y;
+    const DmLanczosProblem &p = P[act[slot]];
+    ritz_body(p.alpha, p.beta, m, p.theta, p.resid, (int)blockIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        theta_out[(size_t)slot * k + blockIdx.x] = p.theta[blockIdx.x];
+        resid_out[(size_t)slot * k + blockIdx.x] = p.resid[blockIdx.x];
+        if (blockIdx.x == 0) beta_out[slot] = p.beta[m - 1];
     }
 }
 
@@ -954,3 +999,30 @@ cudaError_t dm_launch_barrier_selftest(unsigned *ctr, int *err, int blocks, int 
     dm_count_launches(1);
     return cudaGetLastError();
 }
+
+int dm_step_phased_threads() { return kStepThreadsPhased; }
+int dm_step_tile_quads(int m_max) { return step_tile_quads(m_max, kStepThreadsPhased / 32, 128); }
+
+cudaError_t dm_lanczos_step_batch(const DmLanczosProblem *P, const int4 *map, int nblocks, int j, int m_max_hi,
+                                  cudaStream_t st) {
+    const int qt = step_tile_quads(m_max_hi, kStepThreadsPhased / 32, 128);
+    const size_t shm = step_smem_bytes(m_max_hi, qt, kStepThreadsPhased / 32);
+    cudaError_t e = dm_allow_smem((const void *)lanczos_step_batch_kernel, shm);
+    if (e != cudaSuccess) return e;
+    for (int ph = 0; ph < 3; ++ph) {
+        lanczos_step_batch_kernel<<<nblocks, kStepThreadsPhased, shm, st>>>(P, map, j, ph);
+        dm_count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t dm_lanczos_ritz_batch(const DmLanczosProblem *P, const int *act, int nact, int m, int k,
+                                  double *theta_out, double *resid_out, double *beta_out, cudaStream_t st) {
+    ritz_batch_kernel<<<dim3((unsigned)k, (unsigned)nact), kRitzThreads, (sizeof(double) + sizeof(float)) * 2 * (size_t)m,
+                        st>>>(P, act, m, k, theta_out, resid_out, beta_out);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+int dm_lanczos_hstride(int m_max) { return 2 * (m_max + 1) + 2; }
