@@ -15,6 +15,7 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include <map>
@@ -1470,6 +1471,424 @@ int dm_matvec(dm_handle h, const float *x, float *y, int32_t nrhs) {
     return DM_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Single-vector Lanczos of many compressed handles advanced together: every step of every
+// active problem runs in the same five launches (two H-matvec launches, three Gram-Schmidt
+// passes), each problem at its own step index, so problems join and leave between steps.
+// Convergence checks (Ritz values of T_m) run on each problem's own schedule; the checks due
+// after a step share one launch, and their results are read one step later, while the next
+// step runs, so the host never drains the stream. A problem that converged therefore takes
+// one more step before it leaves (harmless: its Ritz vectors use the first m columns); one
+// at m_max leaves the step list at once and is finished when its check is read. Finished
+// problems are handed out one call later still, once the step after their Ritz-vector
+// launches is queued, so that waiting for their vectors does not idle the GPU either.
+// ---------------------------------------------------------------------------------------
+namespace {
+enum SlotState { kFree = 0, kStepping = 1, kLeaving = 2 };
+}
+
+struct DmBatchSolver {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    // per slot (host); a slot is reused after its problem is finished
+    std::vector<dm_ctx *> h;
+    std::vector<int> k, cap, jh, first, every, since, state, sblk;
+    std::vector<size_t> shm;
+    std::vector<void *> tag;
+    std::vector<DmChainShape> shape;
+    std::vector<DmChainProblem> cp;
+    std::vector<DmLanczosProblem> lp;
+    std::vector<int> act;  // stepping slots, in join order
+    int in_use = 0;
+    bool dirty = true;
+    // launch geometry of the stepping problems
+    int n_up = 0, n_dn = 0, n_st = 0;
+    size_t smem1 = 0, smem2 = 0, smem_step = 0;
+    // descriptors and launch maps in one device blob, uploaded from one of two pinned
+    // staging buffers (each reused only after its last upload has completed)
+    unsigned char *blob = nullptr, *stage[2] = {nullptr, nullptr};
+    size_t c_blob = 0, c_stage[2] = {0, 0};
+    cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+    int cur = 0;
+    const DmChainProblem *dcp = nullptr;
+    const DmLanczosProblem *dlp = nullptr;
+    const int2 *dup = nullptr, *ddn = nullptr;
+    const int4 *dst = nullptr;
+    // per-slot device state: step counter jv and the arrival counter of its last pass
+    int *djv = nullptr;
+    unsigned *darr = nullptr;
+    size_t c_slots = 0;
+    // the check in flight: slots and their m; results land in pinned hres
+    std::vector<int> pend, pend_m;
+    int pend_khi = 1;
+    int *hdue = nullptr, *ddue = nullptr;
+    double *hres = nullptr, *dres = nullptr;
+    cudaEvent_t ev_chk = nullptr;
+    // problems finished at the last call, handed out at the next (ready: ev_done[par])
+    std::vector<DmBatchDone> fin;
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};
+    int par = 0;
+
+    ~DmBatchSolver() {
+        if (st) cudaStreamSynchronize(st);
+        void *ds[] = {blob, djv, darr, ddue, dres};
+        for (void *q : ds)
+            if (q) cudaFree(q);
+        void *hs[] = {stage[0], stage[1], hdue, hres};
+        for (void *q : hs)
+            if (q) cudaFreeHost(q);
+        for (cudaEvent_t e : {ev_stage[0], ev_stage[1], ev_chk, ev_done[0], ev_done[1]})
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+// per-slot arrays for `want` slots: the step counters (kept), the check lists and results
+int batch_slots(DmBatchSolver &B, size_t want) {
+    if (want <= B.c_slots) return DM_OK;
+    size_t n = B.c_slots ? B.c_slots : 64;
+    while (n < want) n *= 2;
+    const size_t per = (size_t)(2 * dm_lanczos_kmax() + 1);  // theta, resid (k each) and beta
+    DM_CUDA(cudaStreamSynchronize(B.st));
+    int *jv = nullptr, *due = nullptr, *hdue = nullptr;
+    unsigned *arr = nullptr;
+    double *res = nullptr, *hres = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&jv), sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&arr), sizeof(unsigned) * n) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&due), sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&res), sizeof(double) * n * per) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&hdue), sizeof(int) * n) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&hres), sizeof(double) * n * per) != cudaSuccess) {
+        cudaGetLastError();
+        void *ds[] = {jv, arr, due, res};
+        for (void *q : ds)
+            if (q) cudaFree(q);
+        if (hdue) cudaFreeHost(hdue);
+        if (hres) cudaFreeHost(hres);
+        return fail(DM_ENOMEM, "batched eigensolver: allocation of %zu slots failed", n);
+    }
+    DM_CUDA(cudaMemsetAsync(arr, 0, sizeof(unsigned) * n, B.st));
+    if (B.djv) {
+        DM_CUDA(cudaMemcpyAsync(jv, B.djv, sizeof(int) * B.c_slots, cudaMemcpyDeviceToDevice, B.st));
+        DM_CUDA(cudaMemcpyAsync(arr, B.darr, sizeof(unsigned) * B.c_slots, cudaMemcpyDeviceToDevice, B.st));
+        DM_CUDA(cudaStreamSynchronize(B.st));
+    }
+    void *ds[] = {B.djv, B.darr, B.ddue, B.dres};
+    for (void *q : ds)
+        if (q) cudaFree(q);
+    if (B.hdue) cudaFreeHost(B.hdue);
+    if (B.hres) cudaFreeHost(B.hres);
+    B.djv = jv;
+    B.darr = arr;
+    B.ddue = due;
+    B.dres = res;
+    B.hdue = hdue;
+    B.hres = hres;
+    B.c_slots = n;
+    return DM_OK;
+}
+
+inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// descriptors of every slot and the launch maps of the stepping problems (leaf climbs of
+// every problem first, then the near items: the climbs are the longer blocks)
+int batch_rebuild(DmBatchSolver &B) {
+    B.n_up = B.n_dn = B.n_st = 0;
+    B.smem1 = B.smem2 = B.smem_step = 0;
+    for (int p : B.act) {
+        B.n_up += B.shape[p].up_blocks + B.shape[p].near_blocks;
+        B.n_dn += B.shape[p].down_blocks;
+        B.n_st += B.sblk[p];
+        B.smem1 = B.shape[p].smem1 > B.smem1 ? B.shape[p].smem1 : B.smem1;
+        B.smem2 = B.shape[p].smem2 > B.smem2 ? B.shape[p].smem2 : B.smem2;
+        B.smem_step = B.shm[p] > B.smem_step ? B.shm[p] : B.smem_step;
+    }
+    const size_t ns = B.cp.size();
+    const size_t o_cp = 0, o_lp = a16(o_cp + sizeof(DmChainProblem) * ns);
+    const size_t o_up = a16(o_lp + sizeof(DmLanczosProblem) * ns);
+    const size_t o_dn = a16(o_up + sizeof(int2) * (size_t)B.n_up);
+    const size_t o_st = a16(o_dn + sizeof(int2) * (size_t)B.n_dn);
+    const size_t bytes = a16(o_st + sizeof(int4) * (size_t)B.n_st);
+    const int c = B.cur;
+    if (B.ev_stage[c]) DM_CUDA(cudaEventSynchronize(B.ev_stage[c]));
+    else DM_CUDA(cudaEventCreateWithFlags(&B.ev_stage[c], cudaEventDisableTiming));
+    if (bytes > B.c_stage[c]) {
+        if (B.stage[c]) cudaFreeHost(B.stage[c]);
+        B.stage[c] = nullptr;
+        B.c_stage[c] = 0;
+        if (cudaMallocHost(reinterpret_cast<void **>(&B.stage[c]), 2 * bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DM_ENOMEM, "batched eigensolver: pinned staging of %zu bytes failed", 2 * bytes);
+        }
+        B.c_stage[c] = 2 * bytes;
+    }
+    if (bytes > B.c_blob) {
+        // kernels still queued may read the old blob
+        DM_CUDA(cudaStreamSynchronize(B.st));
+        if (B.blob) cudaFree(B.blob);
+        B.blob = nullptr;
+        B.c_blob = 0;
+        if (cudaMalloc(reinterpret_cast<void **>(&B.blob), 2 * bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DM_ENOMEM, "batched eigensolver: cudaMalloc of %zu bytes failed", 2 * bytes);
+        }
+        B.c_blob = 2 * bytes;
+    }
+    unsigned char *hs = B.stage[c];
+    std::memcpy(hs + o_cp, B.cp.data(), sizeof(DmChainProblem) * ns);
+    std::memcpy(hs + o_lp, B.lp.data(), sizeof(DmLanczosProblem) * ns);
+    int2 *up = reinterpret_cast<int2 *>(hs + o_up);
+    int2 *dn = reinterpret_cast<int2 *>(hs + o_dn);
+    int4 *sp = reinterpret_cast<int4 *>(hs + o_st);
+    for (int p : B.act) {
+        for (int b = 0; b < B.shape[p].up_blocks; ++b) *up++ = make_int2(p, b);
+        for (int b = 0; b < B.shape[p].down_blocks; ++b) *dn++ = make_int2(p, b);
+        for (int b = 0; b < B.sblk[p]; ++b) *sp++ = make_int4(p, b, B.sblk[p], 0);
+    }
+    for (int p : B.act)
+        for (int b = 0; b < B.shape[p].near_blocks; ++b) *up++ = make_int2(p, B.shape[p].up_blocks + b);
+    // stream-ordered: kernels queued before still read the previous contents
+    DM_CUDA(cudaMemcpyAsync(B.blob, hs, bytes, cudaMemcpyHostToDevice, B.st));
+    DM_CUDA(cudaEventRecord(B.ev_stage[c], B.st));
+    B.cur ^= 1;
+    B.dcp = reinterpret_cast<const DmChainProblem *>(B.blob + o_cp);
+    B.dlp = reinterpret_cast<const DmLanczosProblem *>(B.blob + o_lp);
+    B.dup = reinterpret_cast<const int2 *>(B.blob + o_up);
+    B.ddn = reinterpret_cast<const int2 *>(B.blob + o_dn);
+    B.dst = reinterpret_cast<const int4 *>(B.blob + o_st);
+    B.dirty = false;
+    return DM_OK;
+}
+
+// read the check in flight and finish the problems it decides: their Ritz-vector launches are
+// queued and they wait in B.fin for the next call
+int batch_collect(DmBatchSolver &B) {
+    if (B.pend.empty()) return DM_OK;
+    DM_CUDA(cudaEventSynchronize(B.ev_chk));
+    const int nd = (int)B.pend.size(), khi = B.pend_khi;
+    const double *hth = B.hres, *hrs = hth + (size_t)nd * khi, *hbt = hrs + (size_t)nd * khi;
+    bool left = false;
+    for (int i = 0; i < nd; ++i) {
+        const int p = B.pend[i], m = B.pend_m[i];
+        dm_ctx *h = B.h[p];
+        const int k = B.k[p];
+        const double *tp = hth + (size_t)i * khi, *rp = hrs + (size_t)i * khi;
+        const double scale = std::fabs(tp[0]) > 0 ? std::fabs(tp[0]) : 1.0;
+        bool ok = true;
+        for (int j = 0; j < k; ++j)
+            if (!(rp[j] <= h->cfg.conv_tol * scale)) ok = false;
+        const bool breakdown = hbt[i] <= 1e-12 * scale;
+        if (!(ok || breakdown || B.state[p] == kLeaving)) continue;
+        // finished after m steps: Ritz vectors in original point order from the first m basis
+        // columns (Lz.theta holds this check's values; a later step does not touch them)
+        DM_CUDA(dm_lanczos_tvecs(h->lz, m, k, B.st));
+        DM_CUDA(dm_lanczos_phi(h->lz, m, k, h->perm, h->evecs, B.st));
+        DmBatchDone d;
+        d.h = h;
+        d.tag = B.tag[p];
+        d.status = (ok || breakdown) ? DM_OK : DM_ENOCONV;
+        d.iters = m;
+        d.k = k;
+        d.theta.assign(tp, tp + k);
+        d.evecs = h->evecs;
+        B.fin.push_back(std::move(d));
+        h->last_k = k;
+        h->stats.lanczos_iters = m;
+        h->stats.converged = (ok || breakdown) ? 1 : 0;
+        h->stats.matvec_calls = 0;
+        h->stats.ms_matvec = 0.f;
+        if (B.state[p] == kStepping) B.dirty = true;
+        B.state[p] = kFree;
+        B.h[p] = nullptr;
+        --B.in_use;
+        left = true;
+    }
+    B.pend.clear();
+    B.pend_m.clear();
+    if (left) {
+        std::vector<int> keep;
+        for (int p : B.act)
+            if (B.state[p] == kStepping) keep.push_back(p);
+        B.act.swap(keep);
+        cudaEvent_t &e = B.ev_done[B.par];
+        if (!e) DM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        DM_CUDA(cudaEventRecord(e, B.st));
+        for (DmBatchDone &d : B.fin) d.ready = e;
+    }
+    return DM_OK;
+}
+
+}  // namespace
+
+DmBatchSolver *dm_batch_create(int device, cudaStream_t st) {
+    DmBatchSolver *B = new DmBatchSolver();
+    B->device = device;
+    B->st = st;
+    return B;
+}
+
+void dm_batch_destroy(DmBatchSolver *B) { delete B; }
+
+int dm_batch_active(const DmBatchSolver *B) { return B ? B->in_use + (int)B->fin.size() : 0; }
+
+int dm_batch_prepare(dm_handle h, cudaEvent_t *ready) {
+    if (!h || !ready) return fail(DM_EINVAL, "batched eigensolver: NULL argument");
+    if (!h->compressed) return fail(DM_ESTATE, "batched eigensolver: handle not compressed");
+    DM_CHECK(set_device(h));
+    DM_CHECK(ensure_lanczos(h));
+    *ready = nullptr;
+    DM_CUDA(cudaEventCreateWithFlags(ready, cudaEventDisableTiming));
+    DM_CUDA(cudaEventRecord(*ready, h->stream));
+    return DM_OK;
+}
+
+int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t ready, cudaStream_t adopt) {
+    if (!B || !h) return fail(DM_EINVAL, "batched eigensolver: NULL argument");
+    if (!h->compressed || !h->lz_ready) return fail(DM_ESTATE, "batched eigensolver: handle not prepared");
+    if (k < 1 || k > dm_lanczos_kmax() || k >= h->N || k > h->cfg.m_max)
+        return fail(DM_EINVAL, "batched eigensolver: k out of range");
+    if (h->device != B->device) return fail(DM_EINVAL, "batched eigensolver: handle on another device");
+    int slot = -1;
+    for (size_t i = 0; i < B->state.size(); ++i)
+        if (B->state[i] == kFree) {
+            slot = (int)i;
+            break;
+        }
+    if (slot < 0) {
+        slot = (int)B->state.size();
+        DM_CHECK(batch_slots(*B, (size_t)slot + 1));
+        B->h.push_back(nullptr);
+        B->k.push_back(0);
+        B->cap.push_back(0);
+        B->jh.push_back(0);
+        B->first.push_back(0);
+        B->every.push_back(1);
+        B->since.push_back(0);
+        B->state.push_back(kFree);
+        B->sblk.push_back(1);
+        B->shm.push_back(0);
+        B->tag.push_back(nullptr);
+        B->shape.push_back(DmChainShape{});
+        B->cp.push_back(DmChainProblem{});
+        B->lp.push_back(DmLanczosProblem{});
+    }
+    // everything queued for the handle before it was prepared runs first
+    if (ready) DM_CUDA(cudaStreamWaitEvent(B->st, ready, 0));
+    // the handle's own stream: idle from here on (the solver works on its own stream)
+    if (adopt) h->stream = adopt;
+    DmLanczos &Lz = h->lz;
+    const DmHmat H = h->hmat();
+    const int qt = dm_step_tile_quads(Lz.m_max);
+    B->h[slot] = h;
+    B->k[slot] = k;
+    B->cap[slot] = (int)(h->cfg.m_max < h->N ? h->cfg.m_max : h->N);
+    B->jh[slot] = 0;
+    B->first[slot] = (5 * k + 3) / 4 + 5;
+    B->every[slot] = h->cfg.check_every > 0 ? h->cfg.check_every : 1;
+    B->since[slot] = 0;
+    B->tag[slot] = tag;
+    B->shape[slot] = dm_chain_shape(H, h->near_mode);
+    B->shm[slot] = dm_step_batch_smem(Lz.m_max);
+    DmChainProblem &c = B->cp[slot];
+    c.H = H;
+    c.x = Lz.V;
+    c.xstep = Lz.ldv;
+    c.y = Lz.z;
+    c.permuted = 1;
+    c.near_mode = h->near_mode;
+    c.near_rows = B->shape[slot].near_rows;
+    c.climb_smem = B->shape[slot].climb_smem;
+    c.chain_smem = B->shape[slot].chain_smem;
+    DmLanczosProblem &l = B->lp[slot];
+    l.V = Lz.V;
+    l.ldv = Lz.ldv;
+    l.z = Lz.z;
+    l.h = Lz.h;
+    l.hstride = dm_lanczos_hstride(Lz.m_max);
+    l.alpha = Lz.alpha;
+    l.beta = Lz.beta;
+    l.m_max = Lz.m_max;
+    l.qt = qt;
+    l.theta = Lz.theta;
+    l.resid = Lz.resid;
+    l.k = k;
+    const int64_t qn = Lz.ldv >> 2;
+    const int nb = (int)((qn + qt - 1) / qt);
+    B->sblk[slot] = nb < 1 ? 1 : (nb > 304 ? 304 : nb);
+    DM_CUDA(cudaMemsetAsync(B->djv + slot, 0, sizeof(int), B->st));
+    DM_CUDA(cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (size_t)l.hstride, B->st));
+    DM_CUDA(dm_lanczos_start(Lz, h->perm, h->cfg.seed, B->st));
+    B->state[slot] = kStepping;
+    ++B->in_use;
+    B->act.push_back(slot);
+    B->dirty = true;
+    return DM_OK;
+}
+
+int dm_batch_step(DmBatchSolver *B, std::vector<DmBatchDone> &done) {
+    if (!B) return fail(DM_EINVAL, "batched eigensolver: NULL solver");
+    const cudaStream_t st = B->st;
+    if (!B->act.empty()) {
+        if (B->dirty) DM_CHECK(batch_rebuild(*B));
+        DM_CUDA(dm_hmatvec_chain_batch(B->dcp, B->dup, B->n_up, B->smem1, B->ddn, B->n_dn, B->smem2, B->djv, st));
+        DM_CUDA(dm_lanczos_step_batch(B->dlp, B->dst, B->n_st, B->djv, B->darr, B->smem_step, st));
+    }
+    // the problems finished at the last call: their vectors come before this step
+    for (DmBatchDone &d : B->fin) done.push_back(std::move(d));
+    B->fin.clear();
+    B->par ^= 1;
+    // the previous step's check has been computed while this step was queued: read it
+    DM_CHECK(batch_collect(*B));
+    // checks due after this step
+    std::vector<int> due;
+    int m_hi = 0, k_hi = 1;
+    bool leaving = false;
+    for (int p : B->act) {
+        if (B->state[p] != kStepping) continue;
+        const int m = ++B->jh[p];
+        ++B->since[p];
+        const bool at_cap = m >= B->cap[p];
+        if ((m >= B->first[p] && B->since[p] >= B->every[p]) || at_cap) {
+            due.push_back(p);
+            B->since[p] = 0;
+            m_hi = m > m_hi ? m : m_hi;
+            k_hi = B->k[p] > k_hi ? B->k[p] : k_hi;
+        }
+        if (at_cap) {
+            // no room for another basis vector: off the step list now, finished by its check
+            B->state[p] = kLeaving;
+            leaving = true;
+        }
+    }
+    if (leaving) {
+        std::vector<int> keep;
+        for (int p : B->act)
+            if (B->state[p] == kStepping) keep.push_back(p);
+        B->act.swap(keep);
+        B->dirty = true;
+    }
+    if (due.empty()) return DM_OK;
+    const int nd = (int)due.size();
+    for (int i = 0; i < nd; ++i) B->hdue[i] = due[i];
+    double *th = B->dres, *rs = th + (size_t)nd * k_hi, *bt = rs + (size_t)nd * k_hi;
+    if (!B->ev_chk) DM_CUDA(cudaEventCreateWithFlags(&B->ev_chk, cudaEventDisableTiming));
+    DM_CUDA(cudaMemcpyAsync(B->ddue, B->hdue, sizeof(int) * nd, cudaMemcpyHostToDevice, st));
+    DM_CUDA(dm_lanczos_ritz_batch(B->dlp, B->ddue, nd, B->djv, m_hi, k_hi, th, rs, bt, st));
+    DM_CUDA(cudaMemcpyAsync(B->hres, B->dres, sizeof(double) * (size_t)nd * (2 * k_hi + 1), cudaMemcpyDeviceToHost,
+                            st));
+    DM_CUDA(cudaEventRecord(B->ev_chk, st));
+    B->pend = due;
+    B->pend_m.clear();
+    for (int p : due) B->pend_m.push_back(B->jh[p]);
+    B->pend_khi = k_hi;
+    return DM_OK;
+}
+
+extern "C" {
+
 int dm_eigs_batch(dm_handle *hs, int32_t count, int32_t k, double *evals, float **evecs, int32_t *status) {
     if (!hs || !evals) return fail(DM_EINVAL, "dm_eigs_batch: NULL handles or evals");
     if (count < 1) return fail(DM_EINVAL, "dm_eigs_batch: count must be >= 1");
@@ -1484,202 +1903,37 @@ int dm_eigs_batch(dm_handle *hs, int32_t count, int32_t k, double *evals, float 
             if (hs[j] == h) return fail(DM_EINVAL, "dm_eigs_batch: handle %d appears twice", i);
     }
     DM_CHECK(set_device(hs[0]));
-    cudaStream_t st = hs[0]->stream;
-    for (int i = 0; i < count; ++i) DM_CHECK(ensure_lanczos(hs[i]));
-    // order the batch after every handle's queued work (their streams), then work on `st`
-    for (int i = 1; i < count; ++i) {
-        cudaEvent_t ev = nullptr;
-        DM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        DM_CUDA(cudaEventRecord(ev, hs[i]->stream));
-        DM_CUDA(cudaStreamWaitEvent(st, ev, 0));
-        cudaEventDestroy(ev);
-    }
+    const cudaStream_t st = hs[0]->stream;
+    std::unique_ptr<DmBatchSolver> B(dm_batch_create(hs[0]->device, st));
     PhaseTimer t(st);
-    int m_hi = 0;
-    for (int i = 0; i < count; ++i) m_hi = hs[i]->lz.m_max > m_hi ? hs[i]->lz.m_max : m_hi;
-    const int qt = dm_step_tile_quads(m_hi);
-    std::vector<DmChainProblem> cp(count);
-    std::vector<DmLanczosProblem> lp(count);
-    std::vector<DmChainShape> shape(count);
-    std::vector<int> cap(count), sblk(count);
     for (int i = 0; i < count; ++i) {
-        dm_ctx *h = hs[i];
-        DmLanczos &Lz = h->lz;
-        const DmHmat H = h->hmat();
-        shape[i] = dm_chain_shape(H, h->near_mode);
-        DmChainProblem &c = cp[i];
-        c.H = H;
-        c.x = Lz.V;
-        c.xstep = Lz.ldv;
-        c.y = Lz.z;
-        c.permuted = 1;
-        c.near_mode = h->near_mode;
-        c.near_rows = shape[i].near_rows;
-        c.climb_smem = shape[i].climb_smem;
-        c.chain_smem = shape[i].chain_smem;
-        DmLanczosProblem &l = lp[i];
-        l.V = Lz.V;
-        l.ldv = Lz.ldv;
-        l.z = Lz.z;
-        l.h = Lz.h;
-        l.hstride = dm_lanczos_hstride(Lz.m_max);
-        l.alpha = Lz.alpha;
-        l.beta = Lz.beta;
-        l.m_max = Lz.m_max;
-        l.qt = qt;
-        l.theta = Lz.theta;
-        l.resid = Lz.resid;
-        cap[i] = (int)(h->cfg.m_max < h->N ? h->cfg.m_max : h->N);
-        const int64_t qn = Lz.ldv >> 2;
-        sblk[i] = (int)((qn + qt - 1) / qt);
-        if (sblk[i] > 304) sblk[i] = 304;
-        if (sblk[i] < 1) sblk[i] = 1;
-        DM_CUDA(cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (size_t)l.hstride, st));
-        DM_CUDA(dm_lanczos_start(Lz, h->perm, h->cfg.seed, st));
+        cudaEvent_t ready = nullptr;
+        int e = dm_batch_prepare(hs[i], &ready);
+        if (e == DM_OK) e = dm_batch_add(B.get(), hs[i], k, reinterpret_cast<void *>((intptr_t)i), ready, nullptr);
+        if (ready) cudaEventDestroy(ready);
+        DM_CHECK(e);
     }
-    // device buffers of the batch, released on every return path
-    struct Buf {
-        void *p = nullptr;
-        cudaStream_t s;
-        ~Buf() {
-            if (p) cudaFreeAsync(p, s);
-        }
-    };
-    auto dalloc = [&](Buf &b, size_t bytes) -> int {
-        b.s = st;
-        if (cudaMallocAsync(&b.p, bytes, st) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(DM_ENOMEM, "dm_eigs_batch: cudaMallocAsync of %zu bytes failed", bytes);
-        }
-        return DM_OK;
-    };
-    size_t n_up_all = 0, n_dn_all = 0, n_st_all = 0;
-    for (int i = 0; i < count; ++i) {
-        n_up_all += (size_t)shape[i].up_blocks + shape[i].near_blocks;
-        n_dn_all += (size_t)shape[i].down_blocks;
-        n_st_all += (size_t)sblk[i];
-    }
-    Buf bcp, blp, bup, bdn, bst, bact, bth, brs, bbt;
-    DM_CHECK(dalloc(bcp, sizeof(DmChainProblem) * count));
-    DM_CHECK(dalloc(blp, sizeof(DmLanczosProblem) * count));
-    DM_CHECK(dalloc(bup, sizeof(int2) * n_up_all));
-    DM_CHECK(dalloc(bdn, sizeof(int2) * n_dn_all));
-    DM_CHECK(dalloc(bst, sizeof(int4) * n_st_all));
-    DM_CHECK(dalloc(bact, sizeof(int) * count));
-    DM_CHECK(dalloc(bth, sizeof(double) * count * k));
-    DM_CHECK(dalloc(brs, sizeof(double) * count * k));
-    DM_CHECK(dalloc(bbt, sizeof(double) * count));
-    DM_CUDA(cudaMemcpyAsync(bcp.p, cp.data(), sizeof(DmChainProblem) * count, cudaMemcpyHostToDevice, st));
-    DM_CUDA(cudaMemcpyAsync(blp.p, lp.data(), sizeof(DmLanczosProblem) * count, cudaMemcpyHostToDevice, st));
-    // launch maps of the active problems (leaf climbs of every problem first, then near items)
-    std::vector<int> act(count);
-    for (int i = 0; i < count; ++i) act[i] = i;
-    std::vector<int2> mup, mdn;
-    std::vector<int4> mst;
-    int n_up = 0, n_dn = 0, n_st = 0;
-    size_t smem1 = 0, smem2 = 0;
-    auto rebuild = [&]() -> int {
-        mup.clear();
-        mdn.clear();
-        mst.clear();
-        smem1 = smem2 = 0;
-        for (int p : act) {
-            for (int b = 0; b < shape[p].up_blocks; ++b) mup.push_back(make_int2(p, b));
-            for (int b = 0; b < shape[p].down_blocks; ++b) mdn.push_back(make_int2(p, b));
-            for (int b = 0; b < sblk[p]; ++b) mst.push_back(make_int4(p, b, sblk[p], 0));
-            smem1 = shape[p].smem1 > smem1 ? shape[p].smem1 : smem1;
-            smem2 = shape[p].smem2 > smem2 ? shape[p].smem2 : smem2;
-        }
-        for (int p : act)
-            for (int b = 0; b < shape[p].near_blocks; ++b) mup.push_back(make_int2(p, shape[p].up_blocks + b));
-        n_up = (int)mup.size();
-        n_dn = (int)mdn.size();
-        n_st = (int)mst.size();
-        DM_CUDA(cudaMemcpyAsync(bup.p, mup.data(), sizeof(int2) * mup.size(), cudaMemcpyHostToDevice, st));
-        DM_CUDA(cudaMemcpyAsync(bdn.p, mdn.data(), sizeof(int2) * mdn.size(), cudaMemcpyHostToDevice, st));
-        DM_CUDA(cudaMemcpyAsync(bst.p, mst.data(), sizeof(int4) * mst.size(), cudaMemcpyHostToDevice, st));
-        DM_CUDA(cudaMemcpyAsync(bact.p, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice, st));
-        // the host vectors are pageable: each copy has staged its source when it returns, but
-        // they are rebuilt in place later, so wait for the copies
-        DM_CUDA(cudaStreamSynchronize(st));
-        return DM_OK;
-    };
-    DM_CHECK(rebuild());
-    const int first_check = (5 * k + 3) / 4 + 5;
-    int every = hs[0]->cfg.check_every;
-    for (int i = 1; i < count; ++i) every = hs[i]->cfg.check_every < every ? hs[i]->cfg.check_every : every;
-    if (every < 1) every = 1;
-    std::vector<double> th((size_t)count * k), rs((size_t)count * k), bt(count);
-    std::vector<int> done(count, 0), conv(count, 0), mstop(count, 0);
-    std::vector<std::vector<double>> theta_final(count, std::vector<double>(k, 0.0));
-    int since = 0;
-    for (int j = 0; !act.empty(); ++j) {
-        DM_CUDA(dm_hmatvec_chain_batch(static_cast<const DmChainProblem *>(bcp.p), static_cast<const int2 *>(bup.p), n_up,
-                                       smem1, static_cast<const int2 *>(bdn.p), n_dn, smem2, j, st));
-        DM_CUDA(dm_lanczos_step_batch(static_cast<const DmLanczosProblem *>(blp.p), static_cast<const int4 *>(bst.p),
-                                      n_st, j, m_hi, st));
-        const int m = j + 1;
-        ++since;
-        bool at_cap = false;
-        for (int p : act)
-            if (m >= cap[p]) at_cap = true;
-        if (!((m >= first_check && since >= every) || at_cap)) continue;
-        since = 0;
-        const int nact = (int)act.size();
-        DM_CUDA(dm_lanczos_ritz_batch(static_cast<const DmLanczosProblem *>(blp.p), static_cast<const int *>(bact.p),
-                                      nact, m, k, static_cast<double *>(bth.p), static_cast<double *>(brs.p),
-                                      static_cast<double *>(bbt.p), st));
-        DM_CUDA(cudaMemcpyAsync(th.data(), bth.p, sizeof(double) * nact * k, cudaMemcpyDeviceToHost, st));
-        DM_CUDA(cudaMemcpyAsync(rs.data(), brs.p, sizeof(double) * nact * k, cudaMemcpyDeviceToHost, st));
-        DM_CUDA(cudaMemcpyAsync(bt.data(), bbt.p, sizeof(double) * nact, cudaMemcpyDeviceToHost, st));
-        DM_CUDA(cudaStreamSynchronize(st));
-        std::vector<int> keep;
-        for (int slot = 0; slot < nact; ++slot) {
-            const int p = act[slot];
-            const double *tp = th.data() + (size_t)slot * k, *rp = rs.data() + (size_t)slot * k;
-            const double scale = std::fabs(tp[0]) > 0 ? std::fabs(tp[0]) : 1.0;
-            bool ok = true;
-            for (int i = 0; i < k; ++i)
-                if (!(rp[i] <= hs[p]->cfg.conv_tol * scale)) ok = false;
-            const bool breakdown = bt[slot] <= 1e-12 * scale;
-            if (ok || breakdown || m >= cap[p]) {
-                // finished: Ritz vectors of this problem (its theta is current in Lz.theta)
-                dm_ctx *h = hs[p];
-                conv[p] = (ok || breakdown) ? 1 : 0;
-                mstop[p] = m;
-                for (int i = 0; i < k; ++i) theta_final[p][i] = tp[i];
-                DM_CUDA(dm_lanczos_tvecs(h->lz, m, k, st));
-                DM_CUDA(dm_lanczos_phi(h->lz, m, k, h->perm, h->evecs, st));
-                done[p] = 1;
-            } else {
-                keep.push_back(p);
-            }
-        }
-        if ((int)keep.size() != nact) {
-            act.swap(keep);
-            if (!act.empty()) DM_CHECK(rebuild());
-        }
-    }
+    std::vector<DmBatchDone> done;
+    while (dm_batch_active(B.get()) > 0) DM_CHECK(dm_batch_step(B.get(), done));
     DM_CUDA(cudaStreamSynchronize(st));
     const float ms = t.stop();
-    bool all_conv = true;
-    std::vector<double> ev_all((size_t)count * k);
-    for (int p = 0; p < count; ++p)
-        for (int i = 0; i < k; ++i) ev_all[(size_t)p * k + i] = theta_final[p][i];
+    std::vector<double> ev_all((size_t)count * k, 0.0);
+    std::vector<int> conv(count, 0);
+    for (const DmBatchDone &d : done) {
+        const int p = (int)reinterpret_cast<intptr_t>(d.tag);
+        std::copy(d.theta.begin(), d.theta.end(), ev_all.begin() + (size_t)p * k);
+        conv[p] = d.status == DM_OK;
+    }
     if (is_device_ptr(evals))
         DM_CUDA(cudaMemcpy(evals, ev_all.data(), sizeof(double) * ev_all.size(), cudaMemcpyHostToDevice));
     else
         std::copy(ev_all.begin(), ev_all.end(), evals);
+    bool all_conv = true;
     for (int p = 0; p < count; ++p) {
         dm_ctx *h = hs[p];
         if (evecs && evecs[p]) DM_CHECK(copy_out(h, evecs[p], h->evecs, sizeof(float) * (size_t)k * h->N));
         if (status) status[p] = conv[p] ? DM_OK : DM_ENOCONV;
-        h->last_k = k;
-        h->stats.lanczos_iters = mstop[p];
-        h->stats.converged = conv[p];
         h->stats.ms_eigs = ms;
-        h->stats.matvec_calls = 0;
-        h->stats.ms_matvec = 0.f;
         if (!conv[p]) all_conv = false;
     }
     for (int p = 0; p < count; ++p) DM_CUDA(cudaStreamSynchronize(hs[p]->stream));

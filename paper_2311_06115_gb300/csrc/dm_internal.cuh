@@ -343,9 +343,9 @@ struct DmChainProblem {
 };
 // y = K~ x for many problems in two launches; map_up / map_down: {problem, its block index}
 // per block (leaf climbs of every problem before the near items), shared memory the largest
-// of the problems' shapes; j selects each problem's input x + j xstep
+// of the problems' shapes; jv[p] selects problem p's input x + jv[p] xstep
 cudaError_t dm_hmatvec_chain_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem1,
-                                   const int2 *map_down, int n_down, size_t smem2, int j, cudaStream_t st);
+                                   const int2 *map_down, int n_down, size_t smem2, const int *jv, cudaStream_t st);
 cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted,
                              cudaStream_t st);
 int dm_near_item_rows(int near_mode, int leaf_max);
@@ -445,18 +445,56 @@ struct DmLanczosProblem {
     double *alpha, *beta;
     int m_max, qt;
     double *theta, *resid;
+    int k;  // eigenpairs wanted (Ritz checks)
 };
 int dm_lanczos_hstride(int m_max);
 int dm_step_phased_threads();
 int dm_step_tile_quads(int m_max);
-// the three Gram-Schmidt passes of step j for many problems (three launches); map[block] =
-// {problem, its block index, its block count, 0}; m_max_hi sizes the shared memory
-cudaError_t dm_lanczos_step_batch(const DmLanczosProblem *P, const int4 *map, int nblocks, int j, int m_max_hi,
-                                  cudaStream_t st);
-// Ritz values / residual bounds at step m for the problems act[0..nact), one launch; the
-// values also land in theta_out / resid_out (k per slot, slot order)
-cudaError_t dm_lanczos_ritz_batch(const DmLanczosProblem *P, const int *act, int nact, int m, int k,
-                                  double *theta_out, double *resid_out, double *beta_out, cudaStream_t st);
+// shared memory of one problem's blocks in the batched step (tile of dm_step_tile_quads(m_max))
+size_t dm_step_batch_smem(int m_max);
+// the three Gram-Schmidt passes of the current step of many problems (three launches), each
+// problem at its own step jv[p], which the last pass moves to jv[p] + 1 (arrive[p]: a zeroed
+// counter per problem). map[block] = {problem, its block index, its block count, 0}; shm: the
+// largest dm_step_batch_smem of the problems
+cudaError_t dm_lanczos_step_batch(const DmLanczosProblem *P, const int4 *map, int nblocks, int *jv,
+                                  unsigned *arrive, size_t shm, cudaStream_t st);
+// Ritz values / residual bounds of the problems act[0..nact) after their jv[p] completed steps
+// (k = P[p].k pairs each), one launch; the values also land in theta_out / resid_out
+// (kstride = k_hi per slot, slot order) and beta_{m-1} in beta_out; m_hi >= every jv[p]
+cudaError_t dm_lanczos_ritz_batch(const DmLanczosProblem *P, const int *act, int nact, const int *jv, int m_hi,
+                                  int k_hi, double *theta_out, double *resid_out, double *beta_out, cudaStream_t st);
+
+// Single-vector Lanczos of many compressed handles advanced together (dm_eigs_batch and the
+// request server). Problems join (dm_batch_add) and leave (on convergence, breakdown or m_max)
+// between steps; every step of every active problem runs in the same launches, each problem at
+// its own step, and the convergence checks due at a step share one launch and one host read.
+struct DmBatchSolver;
+struct DmBatchDone {
+    dm_handle h = nullptr;
+    void *tag = nullptr;
+    int status = 0;  // DM_OK (converged or invariant subspace) or DM_ENOCONV (m_max reached)
+    int iters = 0, k = 0;
+    std::vector<double> theta;    // the k largest Ritz values, descending
+    const float *evecs = nullptr;  // device, N x k column-major in original point order
+    // the vectors are complete, and the solver done with the handle, when this event has
+    // completed (valid until the next dm_batch_step call)
+    cudaEvent_t ready = nullptr;
+};
+DmBatchSolver *dm_batch_create(int device, cudaStream_t st);
+void dm_batch_destroy(DmBatchSolver *B);
+int dm_batch_active(const DmBatchSolver *B);
+// on the handle's own stream (call from the thread that runs it): allocate the eigensolver's
+// buffers and record *ready (created here; the caller destroys it after dm_batch_add)
+int dm_batch_prepare(dm_handle h, cudaEvent_t *ready);
+// join: the solver's stream waits for `ready`. The solver works on its own stream only; with
+// a non-null `adopt` the handle's own stream becomes `adopt` (a stream of the caller's that
+// the handle's later work and dm_destroy's wait use: the caller destroys the handle after
+// the DmBatchDone's `ready` event has completed)
+int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t ready, cudaStream_t adopt);
+// one step of every stepping problem and the checks due after it. Problems finished are
+// appended to `done` one call after their check decided (see DmBatchDone.ready); the solver
+// is empty once dm_batch_active returns 0
+int dm_batch_step(DmBatchSolver *B, std::vector<DmBatchDone> &done);
 cudaError_t dm_launch_barrier_selftest(unsigned *ctr, int *err, int blocks, int missing, long long spin_limit,
                                        cudaStream_t st);
 cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st);

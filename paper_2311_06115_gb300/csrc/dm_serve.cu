@@ -1,6 +1,10 @@
-// dm_serve.cu -- request server: independent diffusion-map solves admitted as
-// slots and device memory free up, each slot on its own CUDA stream so that
-// concurrently running solves overlap on the GPU.
+// dm_serve.cu -- request server: independent diffusion-map solves admitted as slots and
+// device memory free up. Each slot builds a request's kernel and compression (dm_create,
+// dm_compress) on its own CUDA stream, so that concurrently running builds overlap on the GPU;
+// single-vector eigensolves then join one batched solver, whose thread advances every resident
+// request's Lanczos iteration in the same launches, each request at its own step, and finishes
+// each one when its own convergence check says so (continuous batching at step level). Block
+// Lanczos requests run their eigensolve on their slot.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -21,6 +25,13 @@ namespace {
 inline uint64_t r256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
 
 enum JobState { kQueued = 0, kRunning = 1, kDone = 2 };
+
+struct Job;
+struct Handoff {
+    Job *j;
+    dm_handle h;
+    cudaEvent_t ready;
+};
 
 struct Job {
     dm_ticket id = 0;
@@ -46,6 +57,15 @@ struct Server {
     std::deque<Job *> queue;
     std::map<dm_ticket, std::unique_ptr<Job>> jobs;
     std::vector<std::thread> workers;
+    // the batched eigensolver: its thread, its stream and the requests handed to it
+    std::thread solver;
+    std::condition_variable cv_solver;
+    std::deque<Handoff> handoff;
+    bool workers_done = false;
+    // slot streams, then the solver's stream and its result stream; destroyed after every
+    // thread has ended (the slots' allocations are freed on their streams, possibly by the
+    // solver's thread)
+    std::vector<cudaStream_t> streams;
     std::chrono::steady_clock::time_point t0;
 
     double now_ms() const {
@@ -85,7 +105,28 @@ void *slot_alloc(size_t bytes, void *user) {
 }
 void slot_free(void *p, size_t, void *user) { cudaFreeAsync(p, reinterpret_cast<cudaStream_t>(user)); }
 
-void run_job(Job *j, cudaStream_t stream) {
+// completed request: release its memory and publish the result (takes the lock)
+void finish_job(Job *j, int status) {
+    {
+        std::lock_guard<std::mutex> lk(g_srv.mu);
+        j->res.status = status;
+        g_srv.used -= j->bytes;
+        j->points.clear();
+        j->points.shrink_to_fit();
+        j->res.done_ms = g_srv.now_ms();
+        j->res.k = j->req.k;
+        j->res.N = j->req.N;
+        j->res.evals = j->evals.empty() ? nullptr : j->evals.data();
+        j->res.evecs = j->evecs.empty() ? nullptr : j->evecs.data();
+        j->res.error = j->error.c_str();
+        j->state = kDone;
+    }
+    g_srv.cv.notify_all();
+}
+
+// build the request's kernel and compression on the slot's stream; single-vector solves are
+// handed to the batched solver (returns false), block solves run here (returns true)
+bool run_job(Job *j, cudaStream_t stream, int *status) {
     dm_config cfg;
     dm_config_default(&cfg);
     cfg.seed = j->req.seed;
@@ -95,15 +136,27 @@ void run_job(Job *j, cudaStream_t stream) {
     cfg.free = slot_free;
     cfg.alloc_user = stream;
     cfg.shared_device = 1;  // other slots run concurrently: no cooperative launches
-    // on a shared device a convergence check runs in order on the slot's stream and the
-    // slot's thread waits for it: check every second step, not every step
+    // a convergence check of a block solve runs in order on the slot's stream and the slot's
+    // thread waits for it: check every second step, not every step
     cfg.check_every = 2;
     cfg.block_size = j->req.block_size;
     dm_handle h = nullptr;
     const int k = j->req.k;
     int st = dm_create(j->points.data(), j->req.N, j->req.d, j->req.eps, j->req.alpha, &cfg, &h);
     if (st == DM_OK) st = dm_compress(h, j->req.tol, j->req.leaf_size, j->req.max_rank);
-    if (st == DM_OK) {
+    if (st == DM_OK && j->req.block_size < 2) {
+        cudaEvent_t ready = nullptr;
+        st = dm_batch_prepare(h, &ready);
+        if (st == DM_OK) {
+            {
+                std::lock_guard<std::mutex> lk(g_srv.mu);
+                g_srv.handoff.push_back(Handoff{j, h, ready});
+            }
+            g_srv.cv_solver.notify_one();
+            return false;
+        }
+        if (ready) cudaEventDestroy(ready);
+    } else if (st == DM_OK) {
         j->evals.assign((size_t)k, 0.0);
         if (j->req.want_vectors) j->evecs.assign((size_t)k * (size_t)j->req.N, 0.f);
         st = dm_eigs(h, k, j->evals.data(), j->req.want_vectors ? j->evecs.data() : nullptr);
@@ -113,13 +166,12 @@ void run_job(Job *j, cudaStream_t stream) {
     }
     if (st != DM_OK && st != DM_ENOCONV) j->error = dm_last_error();
     if (h) dm_destroy(h);
-    j->res.status = st;
+    *status = st;
+    return true;
 }
 
-void worker_main() {
+void worker_main(cudaStream_t stream) {
     cudaSetDevice(g_srv.device);
-    cudaStream_t stream = nullptr;
-    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
     for (;;) {
         Job *j = nullptr;
         {
@@ -138,24 +190,88 @@ void worker_main() {
             j->state = kRunning;
             j->res.start_ms = g_srv.now_ms();
         }
-        run_job(j, stream);
+        int st = DM_OK;
+        const bool finished = run_job(j, stream, &st);
         {
             std::lock_guard<std::mutex> lk(g_srv.mu);
-            g_srv.used -= j->bytes;
             g_srv.busy -= 1;
-            j->points.clear();
-            j->points.shrink_to_fit();
-            j->res.done_ms = g_srv.now_ms();
-            j->res.k = j->req.k;
-            j->res.N = j->req.N;
-            j->res.evals = j->evals.empty() ? nullptr : j->evals.data();
-            j->res.evecs = j->evecs.empty() ? nullptr : j->evecs.data();
-            j->res.error = j->error.c_str();
-            j->state = kDone;
         }
-        g_srv.cv.notify_all();
+        if (finished) finish_job(j, st);
     }
-    if (stream) cudaStreamDestroy(stream);
+}
+
+// the batched eigensolver: takes handed-over requests between steps, advances every resident
+// one by a step, and finishes those whose check decided (results copied to the host, handle
+// destroyed, memory released); ends when the slots have ended and nothing is resident
+void solver_main(cudaStream_t stream, cudaStream_t out) {
+    cudaSetDevice(g_srv.device);
+    std::unique_ptr<DmBatchSolver, void (*)(DmBatchSolver *)> B(dm_batch_create(g_srv.device, stream),
+                                                                dm_batch_destroy);
+    std::vector<std::pair<Job *, dm_handle>> resident;
+    std::vector<DmBatchDone> done;
+    auto drop = [&](Job *j, dm_handle h, int st, const char *why) {
+        j->error = why ? why : dm_last_error();
+        dm_destroy(h);
+        finish_job(j, st);
+    };
+    for (;;) {
+        std::deque<Handoff> in;
+        {
+            std::unique_lock<std::mutex> lk(g_srv.mu);
+            g_srv.cv_solver.wait(lk, [&] {
+                return !g_srv.handoff.empty() || dm_batch_active(B.get()) > 0 || g_srv.workers_done;
+            });
+            in.swap(g_srv.handoff);
+            if (in.empty() && dm_batch_active(B.get()) == 0 && g_srv.workers_done) break;
+        }
+        for (Handoff &x : in) {
+            // the handle's own stream becomes `out`, where its results are read and its wait
+            // before destruction ends at once
+            const int st = dm_batch_add(B.get(), x.h, x.j->req.k, x.j, x.ready, out);
+            cudaEventDestroy(x.ready);
+            if (st == DM_OK) {
+                resident.emplace_back(x.j, x.h);
+            } else {
+                drop(x.j, x.h, st, nullptr);
+            }
+        }
+        if (dm_batch_active(B.get()) == 0) continue;
+        done.clear();
+        const int st = dm_batch_step(B.get(), done);
+        for (DmBatchDone &d : done) {
+            Job *j = static_cast<Job *>(d.tag);
+            j->evals = d.theta;
+            j->res.lanczos_iters = d.iters;
+            int rs = d.status;
+            // on `out`, after the vectors: the step queued after them keeps running meanwhile
+            cudaError_t ce = cudaStreamWaitEvent(out, d.ready, 0);
+            if (ce == cudaSuccess && j->req.want_vectors) {
+                j->evecs.assign((size_t)d.k * (size_t)j->req.N, 0.f);
+                ce = cudaMemcpyAsync(j->evecs.data(), d.evecs, sizeof(float) * j->evecs.size(), cudaMemcpyDeviceToHost,
+                                     out);
+            }
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(out);
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                rs = DM_ECUDA;
+                j->error = "reading the eigenvectors failed";
+            }
+            dm_destroy(d.h);
+            for (size_t i = 0; i < resident.size(); ++i)
+                if (resident[i].first == j) {
+                    resident.erase(resident.begin() + (long)i);
+                    break;
+                }
+            finish_job(j, rs);
+        }
+        if (st != DM_OK) {
+            // the step failed: every resident request fails with it; start over empty
+            const std::string why = dm_last_error();
+            for (auto &r : resident) drop(r.first, r.second, st, why.c_str());
+            resident.clear();
+            B.reset(dm_batch_create(g_srv.device, stream));
+        }
+    }
 }
 
 }  // namespace
@@ -225,8 +341,24 @@ int dm_serve_start(const dm_serve_config *cfg) {
     g_srv.used = 0;
     g_srv.busy = 0;
     g_srv.stopping = false;
+    g_srv.workers_done = false;
     g_srv.t0 = std::chrono::steady_clock::now();
-    for (int i = 0; i < slots; ++i) g_srv.workers.emplace_back(worker_main);
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        return dm_fail_msg(DM_ECUDA, "cannot select the CUDA device");
+    }
+    for (int i = 0; i < slots + 2; ++i) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaStream_t q : g_srv.streams) cudaStreamDestroy(q);
+            g_srv.streams.clear();
+            return dm_fail_msg(DM_ECUDA, "stream creation failed");
+        }
+        g_srv.streams.push_back(s);
+    }
+    for (int i = 0; i < slots; ++i) g_srv.workers.emplace_back(worker_main, g_srv.streams[(size_t)i]);
+    g_srv.solver = std::thread(solver_main, g_srv.streams[(size_t)slots], g_srv.streams[(size_t)slots + 1]);
     g_srv.running = true;
     return DM_OK;
 }
@@ -247,11 +379,22 @@ int dm_serve_stop(void) {
         ws.swap(g_srv.workers);
     }
     g_srv.cv.notify_all();
+    // the slots finish the builds they are on (single-vector ones still go to the solver),
+    // then the solver finishes every resident request
     for (auto &t : ws) t.join();
+    {
+        std::lock_guard<std::mutex> lk(g_srv.mu);
+        g_srv.workers_done = true;
+    }
+    g_srv.cv_solver.notify_all();
+    if (g_srv.solver.joinable()) g_srv.solver.join();
+    for (cudaStream_t s : g_srv.streams) cudaStreamDestroy(s);
+    g_srv.streams.clear();
     std::lock_guard<std::mutex> lk(g_srv.mu);
     g_srv.jobs.clear();
     g_srv.running = false;
     g_srv.stopping = false;
+    g_srv.workers_done = false;
     return DM_OK;
 }
 

@@ -328,10 +328,11 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(const __grid_constan
 
 // the same for many problems: map[block] = {problem, its block index}
 __global__ void __launch_bounds__(kHThreads) near_up_batch_kernel(const DmChainProblem *__restrict__ P,
-                                                                  const int2 *__restrict__ map, int j) {
+                                                                  const int2 *__restrict__ map,
+                                                                  const int *__restrict__ jv) {
     const int2 pb = map[blockIdx.x];
     const DmChainProblem &p = P[pb.x];
-    near_up_body(p.H, pb.y, p.x + (size_t)j * p.xstep, p.permuted, p.near_mode, p.near_rows, p.climb_smem);
+    near_up_body(p.H, pb.y, p.x + (size_t)jv[pb.x] * p.xstep, p.permuted, p.near_mode, p.near_rows, p.climb_smem);
 }
 
 // Downward pass for one leaf. The ancestor chain (S2S parts u of the ancestors at
@@ -521,11 +522,11 @@ cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, flo
 }
 
 cudaError_t dm_hmatvec_chain_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem1,
-                                   const int2 *map_down, int n_down, size_t smem2, int j, cudaStream_t st) {
+                                   const int2 *map_down, int n_down, size_t smem2, const int *jv, cudaStream_t st) {
     cudaError_t e = dm_allow_smem((const void *)near_up_batch_kernel, smem1);
     if (e != cudaSuccess) return e;
     if ((e = dm_allow_smem((const void *)down_batch_kernel, smem2)) != cudaSuccess) return e;
-    near_up_batch_kernel<<<n_up, kHThreads, smem1, st>>>(P, map_up, j);
+    near_up_batch_kernel<<<n_up, kHThreads, smem1, st>>>(P, map_up, jv);
     dm_count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     down_batch_kernel<<<n_down, kDownThreads, smem2, st>>>(P, map_down);

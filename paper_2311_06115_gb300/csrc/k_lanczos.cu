@@ -286,14 +286,28 @@ __global__ void __launch_bounds__(NT) lanczos_step_kernel(float *V, int64_t ldv,
 }
 
 // one pass (phase 0..2) of the step for many problems: map[block] = {problem, its block, its
-// block count}; every problem at the same step j
+// block count}; problem p at its own step jv[p]. In the last pass, the last of a problem's
+// blocks to finish (counted in arrive[p], reset to 0 by it) moves jv[p] to the next step:
+// every block of the problem has read jv[p] by then.
 __global__ void __launch_bounds__(kStepThreadsPhased) lanczos_step_batch_kernel(const DmLanczosProblem *__restrict__ P,
-                                                                                const int4 *__restrict__ map, int j,
+                                                                                const int4 *__restrict__ map,
+                                                                                int *jv, unsigned *arrive,
                                                                                 int phase) {
     const int4 pb = map[blockIdx.x];
     const DmLanczosProblem &p = P[pb.x];
+    __shared__ int sj;
+    if (threadIdx.x == 0) sj = jv[pb.x];
+    __syncthreads();
+    const int j = sj;
     lanczos_step_body<kStepThreadsPhased>(p.V, p.ldv, j, p.z, p.h, p.hstride, p.alpha, p.beta, p.m_max, p.qt,
                                           nullptr, nullptr, phase, pb.y, pb.z);
+    if (phase == 2 && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(arrive + pb.x, 1u) == (unsigned)pb.z - 1u) {
+            arrive[pb.x] = 0u;
+            jv[pb.x] = j + 1;
+        }
+    }
 }
 
 size_t step_smem_bytes(int m_max, int qt, int warps) {
@@ -539,17 +553,21 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_kernel(const double *__rest
 // blockIdx.y indexes `act`); also copied, per problem slot, to the contiguous theta_out /
 // resid_out (k per slot) for one host read
 __global__ void __launch_bounds__(kRitzThreads) ritz_batch_kernel(const DmLanczosProblem *__restrict__ P,
-                                                                  const int *__restrict__ act, int m, int k,
+                                                                  const int *__restrict__ act,
+                                                                  const int *__restrict__ jv, int kstride,
                                                                   double *__restrict__ theta_out,
                                                                   double *__restrict__ resid_out,
                                                                   double *__restrict__ beta_out) {
     const int slot = blockIdx.y;
-    const DmLanczosProblem &p = P[act[slot]];
+    const int pi = act[slot];
+    const DmLanczosProblem &p = P[pi];
+    const int m = jv[pi];  // steps completed
+    if ((int)blockIdx.x >= p.k || m < 1) return;  // uniform per block
     ritz_body(p.alpha, p.beta, m, p.theta, p.resid, (int)blockIdx.x);
     __syncthreads();
     if (threadIdx.x == 0) {
-        theta_out[(size_t)slot * k + blockIdx.x] = p.theta[blockIdx.x];
-        resid_out[(size_t)slot * k + blockIdx.x] = p.resid[blockIdx.x];
+        theta_out[(size_t)slot * kstride + blockIdx.x] = p.theta[blockIdx.x];
+        resid_out[(size_t)slot * kstride + blockIdx.x] = p.resid[blockIdx.x];
         if (blockIdx.x == 0) beta_out[slot] = p.beta[m - 1];
     }
 }
@@ -1003,24 +1021,29 @@ cudaError_t dm_launch_barrier_selftest(unsigned *ctr, int *err, int blocks, int 
 int dm_step_phased_threads() { return kStepThreadsPhased; }
 int dm_step_tile_quads(int m_max) { return step_tile_quads(m_max, kStepThreadsPhased / 32, 128); }
 
-cudaError_t dm_lanczos_step_batch(const DmLanczosProblem *P, const int4 *map, int nblocks, int j, int m_max_hi,
-                                  cudaStream_t st) {
-    const int qt = step_tile_quads(m_max_hi, kStepThreadsPhased / 32, 128);
-    const size_t shm = step_smem_bytes(m_max_hi, qt, kStepThreadsPhased / 32);
+size_t dm_step_batch_smem(int m_max) {
+    return step_smem_bytes(m_max, dm_step_tile_quads(m_max), kStepThreadsPhased / 32);
+}
+
+cudaError_t dm_lanczos_step_batch(const DmLanczosProblem *P, const int4 *map, int nblocks, int *jv,
+                                  unsigned *arrive, size_t shm, cudaStream_t st) {
     cudaError_t e = dm_allow_smem((const void *)lanczos_step_batch_kernel, shm);
     if (e != cudaSuccess) return e;
     for (int ph = 0; ph < 3; ++ph) {
-        lanczos_step_batch_kernel<<<nblocks, kStepThreadsPhased, shm, st>>>(P, map, j, ph);
+        lanczos_step_batch_kernel<<<nblocks, kStepThreadsPhased, shm, st>>>(P, map, jv, arrive, ph);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-cudaError_t dm_lanczos_ritz_batch(const DmLanczosProblem *P, const int *act, int nact, int m, int k,
-                                  double *theta_out, double *resid_out, double *beta_out, cudaStream_t st) {
-    ritz_batch_kernel<<<dim3((unsigned)k, (unsigned)nact), kRitzThreads, (sizeof(double) + sizeof(float)) * 2 * (size_t)m,
-                        st>>>(P, act, m, k, theta_out, resid_out, beta_out);
+cudaError_t dm_lanczos_ritz_batch(const DmLanczosProblem *P, const int *act, int nact, const int *jv, int m_hi,
+                                  int k_hi, double *theta_out, double *resid_out, double *beta_out, cudaStream_t st) {
+    const size_t shm = (sizeof(double) + sizeof(float)) * 2 * (size_t)m_hi;
+    cudaError_t e = dm_allow_smem((const void *)ritz_batch_kernel, shm);
+    if (e != cudaSuccess) return e;
+    ritz_batch_kernel<<<dim3((unsigned)k_hi, (unsigned)nact), kRitzThreads, shm, st>>>(P, act, jv, k_hi, theta_out,
+                                                                                       resid_out, beta_out);
     dm_count_launches(1);
     return cudaGetLastError();
 }
