@@ -1497,15 +1497,16 @@ struct DmBatchSolver {
     std::vector<int> k, cap, jh, first, every, since, state, sblk;
     std::vector<size_t> shm;
     std::vector<void *> tag;
-    std::vector<DmChainShape> shape;
+    std::vector<DmBatchShape> shape;
     std::vector<DmChainProblem> cp;
     std::vector<DmLanczosProblem> lp;
-    std::vector<int> act;  // stepping slots, in join order
+    std::vector<int> act;       // stepping slots, in join order
+    std::vector<int> starting;  // slots whose start vector is drawn before the next step
     int in_use = 0;
     bool dirty = true;
     // launch geometry of the stepping problems
-    int n_up = 0, n_dn = 0, n_st = 0;
-    size_t smem1 = 0, smem2 = 0, smem_step = 0;
+    int n_up = 0, n_nr = 0, n_st = 0, n_start = 0, n_smap = 0;
+    size_t smem_up = 0, smem_nr = 0, smem_step = 0;
     // descriptors and launch maps in one device blob, uploaded from one of two pinned
     // staging buffers (each reused only after its last upload has completed)
     unsigned char *blob = nullptr, *stage[2] = {nullptr, nullptr};
@@ -1514,8 +1515,10 @@ struct DmBatchSolver {
     int cur = 0;
     const DmChainProblem *dcp = nullptr;
     const DmLanczosProblem *dlp = nullptr;
-    const int2 *dup = nullptr, *ddn = nullptr;
+    const int2 *dup = nullptr, *dnr = nullptr;
     const int4 *dst = nullptr;
+    const DmStart *dss = nullptr;
+    const int2 *dsm = nullptr;
     // per-slot device state: step counter jv and the arrival counter of its last pass
     int *djv = nullptr;
     unsigned *darr = nullptr;
@@ -1526,6 +1529,11 @@ struct DmBatchSolver {
     int *hdue = nullptr, *ddue = nullptr;
     double *hres = nullptr, *dres = nullptr;
     cudaEvent_t ev_chk = nullptr;
+    // Ritz-vector launches of the problems a check finished: descriptors and block map in
+    // one device buffer, staged in pinned memory (reused once its last upload completed)
+    unsigned char *fstage = nullptr, *fblob = nullptr;
+    size_t c_fstage = 0, c_fblob = 0;
+    cudaEvent_t ev_fstage = nullptr;
     // problems finished at the last call, handed out at the next (ready: ev_done[par])
     std::vector<DmBatchDone> fin;
     cudaEvent_t ev_done[2] = {nullptr, nullptr};
@@ -1533,13 +1541,13 @@ struct DmBatchSolver {
 
     ~DmBatchSolver() {
         if (st) cudaStreamSynchronize(st);
-        void *ds[] = {blob, djv, darr, ddue, dres};
+        void *ds[] = {blob, djv, darr, ddue, dres, fblob};
         for (void *q : ds)
             if (q) cudaFree(q);
-        void *hs[] = {stage[0], stage[1], hdue, hres};
+        void *hs[] = {stage[0], stage[1], hdue, hres, fstage};
         for (void *q : hs)
             if (q) cudaFreeHost(q);
-        for (cudaEvent_t e : {ev_stage[0], ev_stage[1], ev_chk, ev_done[0], ev_done[1]})
+        for (cudaEvent_t e : {ev_stage[0], ev_stage[1], ev_chk, ev_done[0], ev_done[1], ev_fstage})
             if (e) cudaEventDestroy(e);
     }
 };
@@ -1593,25 +1601,30 @@ int batch_slots(DmBatchSolver &B, size_t want) {
 
 inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// descriptors of every slot and the launch maps of the stepping problems (leaf climbs of
-// every problem first, then the near items: the climbs are the longer blocks)
+// descriptors of every slot and the launch maps of the stepping problems (the climbs, the
+// near items and the Gram-Schmidt blocks of each), plus the start vectors of those joining
 int batch_rebuild(DmBatchSolver &B) {
-    B.n_up = B.n_dn = B.n_st = 0;
-    B.smem1 = B.smem2 = B.smem_step = 0;
+    B.n_up = B.n_nr = B.n_st = 0;
+    B.smem_up = B.smem_nr = B.smem_step = 0;
     for (int p : B.act) {
-        B.n_up += B.shape[p].up_blocks + B.shape[p].near_blocks;
-        B.n_dn += B.shape[p].down_blocks;
+        B.n_up += B.shape[p].climbs;
+        B.n_nr += B.shape[p].items;
         B.n_st += B.sblk[p];
-        B.smem1 = B.shape[p].smem1 > B.smem1 ? B.shape[p].smem1 : B.smem1;
-        B.smem2 = B.shape[p].smem2 > B.smem2 ? B.shape[p].smem2 : B.smem2;
+        B.smem_up = B.shape[p].smem_up > B.smem_up ? B.shape[p].smem_up : B.smem_up;
+        B.smem_nr = B.shape[p].smem_near > B.smem_nr ? B.shape[p].smem_near : B.smem_nr;
         B.smem_step = B.shm[p] > B.smem_step ? B.shm[p] : B.smem_step;
     }
+    B.n_start = (int)B.starting.size();
+    B.n_smap = 0;
+    for (int p : B.starting) B.n_smap += dm_finish_blocks(B.h[p]->lz.N);
     const size_t ns = B.cp.size();
     const size_t o_cp = 0, o_lp = a16(o_cp + sizeof(DmChainProblem) * ns);
     const size_t o_up = a16(o_lp + sizeof(DmLanczosProblem) * ns);
-    const size_t o_dn = a16(o_up + sizeof(int2) * (size_t)B.n_up);
-    const size_t o_st = a16(o_dn + sizeof(int2) * (size_t)B.n_dn);
-    const size_t bytes = a16(o_st + sizeof(int4) * (size_t)B.n_st);
+    const size_t o_nr = a16(o_up + sizeof(int2) * (size_t)B.n_up);
+    const size_t o_st = a16(o_nr + sizeof(int2) * (size_t)B.n_nr);
+    const size_t o_ss = a16(o_st + sizeof(int4) * (size_t)B.n_st);
+    const size_t o_sm = a16(o_ss + sizeof(DmStart) * (size_t)B.n_start);
+    const size_t bytes = a16(o_sm + sizeof(int2) * (size_t)B.n_smap);
     const int c = B.cur;
     if (B.ev_stage[c]) DM_CUDA(cudaEventSynchronize(B.ev_stage[c]));
     else DM_CUDA(cudaEventCreateWithFlags(&B.ev_stage[c], cudaEventDisableTiming));
@@ -1641,15 +1654,36 @@ int batch_rebuild(DmBatchSolver &B) {
     std::memcpy(hs + o_cp, B.cp.data(), sizeof(DmChainProblem) * ns);
     std::memcpy(hs + o_lp, B.lp.data(), sizeof(DmLanczosProblem) * ns);
     int2 *up = reinterpret_cast<int2 *>(hs + o_up);
-    int2 *dn = reinterpret_cast<int2 *>(hs + o_dn);
+    int2 *nr = reinterpret_cast<int2 *>(hs + o_nr);
     int4 *sp = reinterpret_cast<int4 *>(hs + o_st);
-    for (int p : B.act) {
-        for (int b = 0; b < B.shape[p].up_blocks; ++b) *up++ = make_int2(p, b);
-        for (int b = 0; b < B.shape[p].down_blocks; ++b) *dn++ = make_int2(p, b);
+    // the deepest trees first: their climbs and sweeps are the longest chains
+    std::vector<int> order(B.act);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B.cp[a].H.L > B.cp[b].H.L; });
+    for (int p : order) {
+        for (int b = 0; b < B.shape[p].climbs; ++b) *up++ = make_int2(p, b);
+        for (int b = 0; b < B.shape[p].items; ++b) *nr++ = make_int2(p, b);
         for (int b = 0; b < B.sblk[p]; ++b) *sp++ = make_int4(p, b, B.sblk[p], 0);
     }
-    for (int p : B.act)
-        for (int b = 0; b < B.shape[p].near_blocks; ++b) *up++ = make_int2(p, B.shape[p].up_blocks + b);
+    DmStart *ss = reinterpret_cast<DmStart *>(hs + o_ss);
+    int2 *sm = reinterpret_cast<int2 *>(hs + o_sm);
+    for (int i = 0; i < B.n_start; ++i) {
+        const int p = B.starting[(size_t)i];
+        const dm_ctx *h = B.h[p];
+        const DmLanczos &Lz = h->lz;
+        DmStart d{};
+        d.perm = h->perm;
+        d.N = Lz.N;
+        d.key = dm_start_key(h->cfg.seed);
+        d.z = Lz.z;
+        d.V = Lz.V;
+        d.nrm2 = Lz.nrm2;
+        d.h = Lz.h;
+        d.hlen = 2 * B.lp[p].hstride;
+        d.jv = B.djv + p;
+        ss[i] = d;
+        const int nb = dm_finish_blocks(Lz.N);
+        for (int b = 0; b < nb; ++b) *sm++ = make_int2(i, b);
+    }
     // stream-ordered: kernels queued before still read the previous contents
     DM_CUDA(cudaMemcpyAsync(B.blob, hs, bytes, cudaMemcpyHostToDevice, B.st));
     DM_CUDA(cudaEventRecord(B.ev_stage[c], B.st));
@@ -1657,9 +1691,57 @@ int batch_rebuild(DmBatchSolver &B) {
     B.dcp = reinterpret_cast<const DmChainProblem *>(B.blob + o_cp);
     B.dlp = reinterpret_cast<const DmLanczosProblem *>(B.blob + o_lp);
     B.dup = reinterpret_cast<const int2 *>(B.blob + o_up);
-    B.ddn = reinterpret_cast<const int2 *>(B.blob + o_dn);
+    B.dnr = reinterpret_cast<const int2 *>(B.blob + o_nr);
     B.dst = reinterpret_cast<const int4 *>(B.blob + o_st);
+    B.dss = reinterpret_cast<const DmStart *>(B.blob + o_ss);
+    B.dsm = reinterpret_cast<const int2 *>(B.blob + o_sm);
     B.dirty = false;
+    return DM_OK;
+}
+
+// Ritz vectors of the finished problems F (one set of launches for all of them)
+int batch_finish(DmBatchSolver &B, const std::vector<DmFinish> &F) {
+    if (F.empty()) return DM_OK;
+    int m_hi = 1, k_hi = 1;
+    std::vector<int2> map;
+    for (size_t f = 0; f < F.size(); ++f) {
+        m_hi = F[f].m > m_hi ? F[f].m : m_hi;
+        k_hi = F[f].k > k_hi ? F[f].k : k_hi;
+        const int nb = dm_finish_blocks(F[f].N);
+        for (int b = 0; b < nb; ++b) map.push_back(make_int2((int)f, b));
+    }
+    const size_t o_map = a16(sizeof(DmFinish) * F.size());
+    const size_t bytes = o_map + sizeof(int2) * map.size();
+    if (B.ev_fstage) DM_CUDA(cudaEventSynchronize(B.ev_fstage));
+    else DM_CUDA(cudaEventCreateWithFlags(&B.ev_fstage, cudaEventDisableTiming));
+    if (bytes > B.c_fstage) {
+        if (B.fstage) cudaFreeHost(B.fstage);
+        B.fstage = nullptr;
+        B.c_fstage = 0;
+        if (cudaMallocHost(reinterpret_cast<void **>(&B.fstage), 2 * bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DM_ENOMEM, "batched eigensolver: pinned staging of %zu bytes failed", 2 * bytes);
+        }
+        B.c_fstage = 2 * bytes;
+    }
+    if (bytes > B.c_fblob) {
+        DM_CUDA(cudaStreamSynchronize(B.st));  // earlier launches may still read the old buffer
+        if (B.fblob) cudaFree(B.fblob);
+        B.fblob = nullptr;
+        B.c_fblob = 0;
+        if (cudaMalloc(reinterpret_cast<void **>(&B.fblob), 2 * bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DM_ENOMEM, "batched eigensolver: cudaMalloc of %zu bytes failed", 2 * bytes);
+        }
+        B.c_fblob = 2 * bytes;
+    }
+    std::memcpy(B.fstage, F.data(), sizeof(DmFinish) * F.size());
+    std::memcpy(B.fstage + o_map, map.data(), sizeof(int2) * map.size());
+    DM_CUDA(cudaMemcpyAsync(B.fblob, B.fstage, bytes, cudaMemcpyHostToDevice, B.st));
+    DM_CUDA(cudaEventRecord(B.ev_fstage, B.st));
+    DM_CUDA(dm_lanczos_finish_batch(reinterpret_cast<const DmFinish *>(B.fblob), (int)F.size(),
+                                    reinterpret_cast<const int2 *>(B.fblob + o_map), (int)map.size(), m_hi, k_hi,
+                                    B.st));
     return DM_OK;
 }
 
@@ -1671,6 +1753,7 @@ int batch_collect(DmBatchSolver &B) {
     const int nd = (int)B.pend.size(), khi = B.pend_khi;
     const double *hth = B.hres, *hrs = hth + (size_t)nd * khi, *hbt = hrs + (size_t)nd * khi;
     bool left = false;
+    std::vector<DmFinish> F;
     for (int i = 0; i < nd; ++i) {
         const int p = B.pend[i], m = B.pend_m[i];
         dm_ctx *h = B.h[p];
@@ -1684,8 +1767,27 @@ int batch_collect(DmBatchSolver &B) {
         if (!(ok || breakdown || B.state[p] == kLeaving)) continue;
         // finished after m steps: Ritz vectors in original point order from the first m basis
         // columns (Lz.theta holds this check's values; a later step does not touch them)
-        DM_CUDA(dm_lanczos_tvecs(h->lz, m, k, B.st));
-        DM_CUDA(dm_lanczos_phi(h->lz, m, k, h->perm, h->evecs, B.st));
+        const DmLanczos &Lz = h->lz;
+        DmFinish f{};
+        f.alpha = Lz.alpha;
+        f.beta = Lz.beta;
+        f.theta = Lz.theta;
+        f.Y = Lz.Y;
+        f.twork = Lz.twork;
+        f.colsum = Lz.colsum;
+        f.Yf = Lz.Yf;
+        f.phi = Lz.phi;
+        f.evecs = h->evecs;
+        f.V = Lz.V;
+        f.ldv = Lz.ldv;
+        f.N = Lz.N;
+        f.perm = h->perm;
+        f.best = Lz.best;
+        f.neg = Lz.neg;
+        f.ldy = Lz.m_max;
+        f.m = m;
+        f.k = k;
+        F.push_back(f);
         DmBatchDone d;
         d.h = h;
         d.tag = B.tag[p];
@@ -1708,6 +1810,7 @@ int batch_collect(DmBatchSolver &B) {
     }
     B.pend.clear();
     B.pend_m.clear();
+    DM_CHECK(batch_finish(B, F));
     if (left) {
         std::vector<int> keep;
         for (int p : B.act)
@@ -1733,6 +1836,11 @@ DmBatchSolver *dm_batch_create(int device, cudaStream_t st) {
 void dm_batch_destroy(DmBatchSolver *B) { delete B; }
 
 int dm_batch_active(const DmBatchSolver *B) { return B ? B->in_use + (int)B->fin.size() : 0; }
+
+int dm_batch_reserve(DmBatchSolver *B, int n) {
+    if (!B || n < 0) return fail(DM_EINVAL, "batched eigensolver: bad reserve");
+    return batch_slots(*B, (size_t)n);
+}
 
 int dm_batch_prepare(dm_handle h, cudaEvent_t *ready) {
     if (!h || !ready) return fail(DM_EINVAL, "batched eigensolver: NULL argument");
@@ -1771,7 +1879,7 @@ int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t re
         B->sblk.push_back(1);
         B->shm.push_back(0);
         B->tag.push_back(nullptr);
-        B->shape.push_back(DmChainShape{});
+        B->shape.push_back(DmBatchShape{});
         B->cp.push_back(DmChainProblem{});
         B->lp.push_back(DmLanczosProblem{});
     }
@@ -1790,7 +1898,7 @@ int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t re
     B->every[slot] = h->cfg.check_every > 0 ? h->cfg.check_every : 1;
     B->since[slot] = 0;
     B->tag[slot] = tag;
-    B->shape[slot] = dm_chain_shape(H, h->near_mode);
+    B->shape[slot] = dm_batch_shape(H, h->near_mode);
     B->shm[slot] = dm_step_batch_smem(Lz.m_max);
     DmChainProblem &c = B->cp[slot];
     c.H = H;
@@ -1799,9 +1907,9 @@ int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t re
     c.y = Lz.z;
     c.permuted = 1;
     c.near_mode = h->near_mode;
-    c.near_rows = B->shape[slot].near_rows;
+    c.near_rows = B->shape[slot].item_rows;
     c.climb_smem = B->shape[slot].climb_smem;
-    c.chain_smem = B->shape[slot].chain_smem;
+    c.chain_smem = 0;
     DmLanczosProblem &l = B->lp[slot];
     l.V = Lz.V;
     l.ldv = Lz.ldv;
@@ -1818,9 +1926,7 @@ int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t re
     const int64_t qn = Lz.ldv >> 2;
     const int nb = (int)((qn + qt - 1) / qt);
     B->sblk[slot] = nb < 1 ? 1 : (nb > 304 ? 304 : nb);
-    DM_CUDA(cudaMemsetAsync(B->djv + slot, 0, sizeof(int), B->st));
-    DM_CUDA(cudaMemsetAsync(Lz.h, 0, sizeof(double) * 2 * (size_t)l.hstride, B->st));
-    DM_CUDA(dm_lanczos_start(Lz, h->perm, h->cfg.seed, B->st));
+    B->starting.push_back(slot);  // its start vector (and step counter) set with the others joining now
     B->state[slot] = kStepping;
     ++B->in_use;
     B->act.push_back(slot);
@@ -1833,7 +1939,12 @@ int dm_batch_step(DmBatchSolver *B, std::vector<DmBatchDone> &done) {
     const cudaStream_t st = B->st;
     if (!B->act.empty()) {
         if (B->dirty) DM_CHECK(batch_rebuild(*B));
-        DM_CUDA(dm_hmatvec_chain_batch(B->dcp, B->dup, B->n_up, B->smem1, B->ddn, B->n_dn, B->smem2, B->djv, st));
+        if (B->n_start > 0) {
+            DM_CUDA(dm_lanczos_start_batch(B->dss, B->n_start, B->dsm, B->n_smap, st));
+            B->starting.clear();
+            B->n_start = 0;
+        }
+        DM_CUDA(dm_hmatvec_batch(B->dcp, B->dup, B->n_up, B->smem_up, B->dnr, B->n_nr, B->smem_nr, B->djv, st));
         DM_CUDA(dm_lanczos_step_batch(B->dlp, B->dst, B->n_st, B->djv, B->darr, B->smem_step, st));
     }
     // the problems finished at the last call: their vectors come before this step
@@ -1887,6 +1998,47 @@ int dm_batch_step(DmBatchSolver *B, std::vector<DmBatchDone> &done) {
     return DM_OK;
 }
 
+namespace {
+
+// idle batched solvers kept per device between dm_eigs_batch calls: their device, pinned and
+// slot arrays are allocated once rather than per call
+std::mutex g_batch_mu;
+std::vector<DmBatchSolver *> g_batch_pool;
+
+struct BatchLease {
+    DmBatchSolver *B = nullptr;
+    BatchLease(int device, cudaStream_t st) {
+        {
+            std::lock_guard<std::mutex> lk(g_batch_mu);
+            for (size_t i = 0; i < g_batch_pool.size(); ++i)
+                if (g_batch_pool[i]->device == device) {
+                    B = g_batch_pool[i];
+                    g_batch_pool.erase(g_batch_pool.begin() + (long)i);
+                    break;
+                }
+        }
+        if (B) {
+            B->st = st;  // idle and synchronised when it was returned to the pool
+        } else {
+            B = dm_batch_create(device, st);
+        }
+    }
+    ~BatchLease() {
+        if (!B) return;
+        if (dm_batch_active(B) == 0 && B->act.empty() && B->pend.empty()) {
+            cudaStreamSynchronize(B->st);
+            B->st = nullptr;  // the caller's stream may be destroyed with its handle
+            std::lock_guard<std::mutex> lk(g_batch_mu);
+            g_batch_pool.push_back(B);
+        } else {
+            dm_batch_destroy(B);  // left mid-solve by an error: not reusable
+        }
+    }
+    DmBatchSolver *get() const { return B; }
+};
+
+}  // namespace
+
 extern "C" {
 
 int dm_eigs_batch(dm_handle *hs, int32_t count, int32_t k, double *evals, float **evecs, int32_t *status) {
@@ -1904,7 +2056,10 @@ int dm_eigs_batch(dm_handle *hs, int32_t count, int32_t k, double *evals, float 
     }
     DM_CHECK(set_device(hs[0]));
     const cudaStream_t st = hs[0]->stream;
-    std::unique_ptr<DmBatchSolver> B(dm_batch_create(hs[0]->device, st));
+    // an idle solver of this device from the pool (its buffers grown by earlier calls), else a new one
+    BatchLease B(hs[0]->device, st);
+    if (!B.get()) return fail(DM_ENOMEM, "dm_eigs_batch: no batched solver");
+    DM_CHECK(dm_batch_reserve(B.get(), count));
     PhaseTimer t(st);
     for (int i = 0; i < count; ++i) {
         cudaEvent_t ready = nullptr;

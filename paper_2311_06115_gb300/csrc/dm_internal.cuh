@@ -341,11 +341,18 @@ struct DmChainProblem {
     float *y;        // output
     int permuted, near_mode, near_rows, climb_smem, chain_smem;
 };
-// y = K~ x for many problems in two launches; map_up / map_down: {problem, its block index}
-// per block (leaf climbs of every problem before the near items), shared memory the largest
-// of the problems' shapes; jv[p] selects problem p's input x + jv[p] xstep
-cudaError_t dm_hmatvec_chain_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem1,
-                                   const int2 *map_down, int n_down, size_t smem2, const int *jv, cudaStream_t st);
+// y = K~ x for many problems in two launches: map_up[block] = {problem, leaf} (leaf N2S, the
+// climb, and the top-down sweep of each tree's internal levels), then map_near[block] =
+// {problem, near item} (near rows and the leaf S2N). Per problem: dm_batch_shape's climbs and
+// items; shared memory the largest of the problems'. jv[p] selects problem p's input
+// x + jv[p] xstep. In DmChainProblem, near_rows = item_rows.
+struct DmBatchShape {
+    int climbs, items, item_rows, climb_smem;
+    size_t smem_up, smem_near;
+};
+DmBatchShape dm_batch_shape(const DmHmat &H, int near_mode);
+cudaError_t dm_hmatvec_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem_up,
+                             const int2 *map_near, int n_near, size_t smem_near, const int *jv, cudaStream_t st);
 cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted,
                              cudaStream_t st);
 int dm_near_item_rows(int near_mode, int leaf_max);
@@ -464,6 +471,38 @@ cudaError_t dm_lanczos_step_batch(const DmLanczosProblem *P, const int4 *map, in
 cudaError_t dm_lanczos_ritz_batch(const DmLanczosProblem *P, const int *act, int nact, const int *jv, int m_hi,
                                   int k_hi, double *theta_out, double *resid_out, double *beta_out, cudaStream_t st);
 
+// Ritz vectors of many finished single-vector problems in six launches (tridiagonal
+// eigenvectors, their orthogonalisation, V Y, column maxima, signs, normalised scatter to the
+// original point order). map[block] = {problem, its block of 256 positions}: dm_finish_blocks(N)
+// blocks per problem; m_hi / k_hi bound the problems' m and k.
+struct DmFinish {
+    const double *alpha, *beta, *theta;
+    double *Y, *twork, *colsum;
+    float *Yf, *phi, *evecs;
+    const float *V;
+    int64_t ldv, N;
+    const int32_t *perm;
+    unsigned long long *best;
+    int *neg;
+    int ldy, m, k, pad;
+};
+int dm_finish_blocks(int64_t N);
+// start vectors of many problems (the draws of dm_lanczos_start): h[0..hlen), *nrm2 and *jv zeroed,
+// z = uniform(-1, 1) per original index, V[:, 0] = z / |z|; map as for dm_lanczos_finish_batch
+struct DmStart {
+    const int32_t *perm;
+    int64_t N;
+    uint64_t key;  // dm_start_key(seed)
+    float *z, *V;
+    double *nrm2, *h;
+    int *jv;  // the problem's step counter, set to 0
+    int hlen, pad;
+};
+uint64_t dm_start_key(uint64_t seed);
+cudaError_t dm_lanczos_start_batch(const DmStart *S, int ns, const int2 *map, int nmap, cudaStream_t st);
+cudaError_t dm_lanczos_finish_batch(const DmFinish *F, int nf, const int2 *map, int nmap, int m_hi, int k_hi,
+                                    cudaStream_t st);
+
 // Single-vector Lanczos of many compressed handles advanced together (dm_eigs_batch and the
 // request server). Problems join (dm_batch_add) and leave (on convergence, breakdown or m_max)
 // between steps; every step of every active problem runs in the same launches, each problem at
@@ -482,6 +521,8 @@ struct DmBatchDone {
 };
 DmBatchSolver *dm_batch_create(int device, cudaStream_t st);
 void dm_batch_destroy(DmBatchSolver *B);
+// room for n problems at once (grows the solver's arrays now rather than while joining)
+int dm_batch_reserve(DmBatchSolver *B, int n);
 int dm_batch_active(const DmBatchSolver *B);
 // on the handle's own stream (call from the thread that runs it): allocate the eigensolver's
 // buffers and record *ready (created here; the caller destroys it after dm_batch_add)

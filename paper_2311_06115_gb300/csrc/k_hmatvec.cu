@@ -124,20 +124,50 @@ __device__ __forceinline__ void gemv_rows_smem(const float *Ps, int ld4, int s, 
     }
 }
 
-// body of the chained form's first launch for one problem: block `bid` of its grid (leaf climbs
-// first, then near items); shared by the single-problem and the batched launches
-__device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const float *__restrict__ x, int permuted,
-                                             int near_mode, int near_rows, int climb_smem) {
+// Top-down S2N over the internal levels 2..L-1 of one tree, by the block that completed the
+// root: in level order, u_node += P_parent(:, node's columns)^T u_parent, in place, so that
+// every internal node's u becomes its total incoming far-field vector (level 1: u itself);
+// the leaves' totals are formed by their near items. A warp per node, lanes over its rank.
+__device__ __forceinline__ void sweep_down(const DmHmat &H) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int R = H.max_rank;
+    for (int lvl = 2; lvl < H.L; ++lvl) {
+        const int first = (1 << lvl) - 1, count = 1 << lvl;
+        for (int q = warp; q < count; q += kHWarps) {
+            const int nd = first + q, par = (nd - 1) >> 1;
+            const int sc = H.ranks[nd], sp = H.ranks[par];
+            const int off = (nd == 2 * par + 2) ? H.ranks[2 * par + 1] : 0;
+            const float *Pn = H.P + (size_t)par * R * H.ldp + off;
+            const float *tp = H.uhat + (size_t)par * R;
+            float *un = H.uhat + (size_t)nd * R;
+            for (int j = lane; j < sc; j += 32) {
+                float a0 = __ldcg(un + j), a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                int t = 0;
+                for (; t + 4 <= sp; t += 4) {
+                    a0 = fmaf(__ldg(Pn + (size_t)t * H.ldp + j), __ldcg(tp + t), a0);
+                    a1 = fmaf(__ldg(Pn + (size_t)(t + 1) * H.ldp + j), __ldcg(tp + t + 1), a1);
+                    a2 = fmaf(__ldg(Pn + (size_t)(t + 2) * H.ldp + j), __ldcg(tp + t + 2), a2);
+                    a3 = fmaf(__ldg(Pn + (size_t)(t + 3) * H.ldp + j), __ldcg(tp + t + 3), a3);
+                }
+                for (; t < sp; ++t) a0 = fmaf(__ldg(Pn + (size_t)t * H.ldp + j), __ldcg(tp + t), a0);
+                __stcg(un + j, (a0 + a1) + (a2 + a3));
+            }
+        }
+        __syncthreads();  // this level's totals are the next level's parents
+    }
+}
+
+// Leaf N2S of leaf `leaf`, then the climb by last arrival (see the file header). With `sweep`,
+// the block that completes the root then runs sweep_down.
+__device__ __forceinline__ void climb_body(const DmHmat &H, int leaf, const float *__restrict__ x, int permuted,
+                                           int climb_smem, bool sweep) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_go;
     const int nleaves = 1 << H.L;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m4max = (H.leaf_max + 3) & ~3;
-
-    if (bid < nleaves) {
-        // ------------------------------------------------ leaf N2S, then climb
-        const int leaf = bid;
+    {
         int node = nleaves - 1 + leaf;
         int64_t st, sz;
         dm_node_range(H.N, node, &st, &sz);
@@ -158,9 +188,21 @@ __device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const flo
             const int l = 2 * parent + 1, r = 2 * parent + 2;
             const int sl = H.ranks[l], sr = H.ranks[r], sp = parent > 0 ? H.ranks[parent] : 0;
             const int c = sl + sr, c4 = (c + 3) & ~3;
+            // publish this node's weights, then count the arrival at the parent
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned old = atomicAdd(H.cnt + parent, 1u);
+                s_go = (old == 1u);
+                if (old == 1u) H.cnt[parent] = 0u;  // both children arrived: reset for the next call
+                __threadfence();
+            }
+            __syncthreads();
+            if (!s_go) return;  // the sibling's block climbs on
+            node = parent;
             if (climb_smem) {
-                // fetch the parent's operands now (asynchronous copies): they travel while the
-                // fence and the arrival atomic complete
+                // the parent's operands (asynchronous copies), in flight while the children's
+                // weights are read
                 const float *Bn = H.B + (size_t)parent * H.max_rank * H.max_rank;
                 for (int e = threadIdx.x; e < sl * sr; e += blockDim.x) {
                     const int ia = e / sr, ib = e % sr;
@@ -173,25 +215,13 @@ __device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const flo
                     dm_cp_async16(Ps + t * C4 + 4 * q, Pn + (size_t)t * H.ldp + 4 * q);  // rows zero padded to ldp
                 }
             }
-            // publish this node's weights, then count the arrival at the parent
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const unsigned old = atomicAdd(H.cnt + parent, 1u);
-                s_go = (old == 1u);
-                if (old == 1u) H.cnt[parent] = 0u;  // both children arrived: reset for the next call
-                __threadfence();
-            }
-            if (climb_smem) dm_cp_async_wait_all();  // own copies land before the block exits or reads them
-            __syncthreads();
-            if (!s_go) return;
-            node = parent;
             for (int j = threadIdx.x; j < c4; j += blockDim.x) {
                 float v = 0.f;
                 if (j < sl) v = __ldcg(H.what + (size_t)l * H.max_rank + j);
                 else if (j < c) v = __ldcg(H.what + (size_t)r * H.max_rank + (j - sl));
                 sw[j] = v;
             }
+            if (climb_smem) dm_cp_async_wait_all();
             __syncthreads();
             // S2S: u_l = B w_r (warp per row of B), u_r = B^T w_l (thread per column of B)
             if (climb_smem) {
@@ -220,7 +250,13 @@ __device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const flo
                     H.uhat[(size_t)r * H.max_rank + b2] = acc;
                 }
             }
-            if (node == 0) return;
+            if (node == 0) {
+                if (sweep) {
+                    __syncthreads();
+                    sweep_down(H);
+                }
+                return;
+            }
             // N2S of the internal node
             if (climb_smem) gemv_rows_smem(Ps, C4, sp, c, sw, H.what + (size_t)node * H.max_rank);
             else
@@ -228,6 +264,21 @@ __device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const flo
                           H.what + (size_t)node * H.max_rank, nullptr);
             __syncthreads();  // Bs/Ps are refilled for the next parent
         }
+    }
+}
+
+// body of the chained form's first launch for one problem: block `bid` of its grid (leaf climbs
+// first, then near items)
+__device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const float *__restrict__ x, int permuted,
+                                             int near_mode, int near_rows, int climb_smem) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const int nleaves = 1 << H.L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m4max = (H.leaf_max + 3) & ~3;
+    if (bid < nleaves) {
+        climb_body(H, bid, x, permuted, climb_smem, false);
+        return;
     }
 
     // ---------------------------------------------------- near field
@@ -324,15 +375,6 @@ __global__ void __launch_bounds__(kHThreads) near_up_kernel(const __grid_constan
                                                             const float *__restrict__ x, int permuted, int near_mode,
                                                             int near_rows, int climb_smem) {
     near_up_body(H, (int)blockIdx.x, x, permuted, near_mode, near_rows, climb_smem);
-}
-
-// the same for many problems: map[block] = {problem, its block index}
-__global__ void __launch_bounds__(kHThreads) near_up_batch_kernel(const DmChainProblem *__restrict__ P,
-                                                                  const int2 *__restrict__ map,
-                                                                  const int *__restrict__ jv) {
-    const int2 pb = map[blockIdx.x];
-    const DmChainProblem &p = P[pb.x];
-    near_up_body(p.H, pb.y, p.x + (size_t)jv[pb.x] * p.xstep, p.permuted, p.near_mode, p.near_rows, p.climb_smem);
 }
 
 // Downward pass for one leaf. The ancestor chain (S2S parts u of the ancestors at
@@ -461,11 +503,182 @@ __global__ void __launch_bounds__(kDownThreads) down_kernel(const __grid_constan
     down_body(H, (int)blockIdx.x, y, permuted, chain_in_smem);
 }
 
-__global__ void __launch_bounds__(kDownThreads) down_batch_kernel(const DmChainProblem *__restrict__ P,
-                                                                  const int2 *__restrict__ map) {
+// ---- batched form (many problems, two launches) --------------------------------------------
+//  up_batch_kernel        map[block] = {problem, leaf}: leaf N2S and the climb; the block that
+//                         completes a root sweeps that tree's internal levels (sweep_down).
+//  near_s2n_batch_kernel  map[block] = {problem, item}, item = (leaf, chunk of item_rows rows):
+//                         the near rows (cached blocks streamed, or recomputed) into shared
+//                         memory, then the leaf's total incoming vector
+//                         t = u_leaf + P_parent(:, leaf's columns)^T t_parent and
+//                         y_i = near_i + PT[i, :] t for the item's rows, in the problem's y.
+//                         Many items are resident per SM, so one item's latency-bound tail
+//                         overlaps the others' streaming.
+__global__ void __launch_bounds__(kHThreads) up_batch_kernel(const DmChainProblem *__restrict__ P,
+                                                             const int2 *__restrict__ map,
+                                                             const int *__restrict__ jv) {
     const int2 pb = map[blockIdx.x];
     const DmChainProblem &p = P[pb.x];
-    down_body(p.H, pb.y, p.y, p.permuted, p.chain_smem);
+    climb_body(p.H, pb.y, p.x + (size_t)jv[pb.x] * p.xstep, p.permuted, p.climb_smem, true);
+}
+
+struct BatchItem {
+    int leaf, m, r0, nr;
+    int64_t st;
+};
+__device__ __forceinline__ BatchItem batch_item(const DmHmat &H, int item, int rows) {
+    const int per_leaf = (H.leaf_max + rows - 1) / rows;
+    BatchItem it;
+    it.leaf = item / per_leaf;
+    const int chunk = item - it.leaf * per_leaf;
+    int64_t sz;
+    dm_node_range(H.N, (1 << H.L) - 1 + it.leaf, &it.st, &sz);
+    it.m = (int)sz;
+    it.r0 = chunk * rows;
+    it.nr = it.r0 < it.m ? min(rows, it.m - it.r0) : 0;
+    return it;
+}
+
+constexpr int kNearBatchThreads = 256;
+__global__ void __launch_bounds__(kNearBatchThreads, 6) near_s2n_batch_kernel(const DmChainProblem *__restrict__ P,
+                                                                              const int2 *__restrict__ map,
+                                                                              const int *__restrict__ jv) {
+    extern __shared__ float4 smem4[];
+    const int2 pb = map[blockIdx.x];
+    const DmChainProblem &p = P[pb.x];
+    const DmHmat &H = p.H;
+    const BatchItem q = batch_item(H, pb.y, p.near_rows);
+    if (q.nr == 0) return;
+    const int permuted = p.permuted;
+    const float *__restrict__ x = p.x + (size_t)jv[pb.x] * p.xstep;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNearBatchThreads / 32;
+    const int m4 = (q.m + 3) & ~3;
+    const int m4max = (H.leaf_max + 3) & ~3;
+    const int RH4 = (H.rank_hi + 3) & ~3;
+    float *sx = reinterpret_cast<float *>(smem4);  // m4max: x~(I_a), or s_j x_j when recomputed
+    float *res = sx + m4max;                       // item_rows (multiple of 4): near results
+    float *tl = res + ((p.near_rows + 3) & ~3);    // RH4: the leaf's total incoming vector
+    float *tpar = tl + RH4;                        // RH4: the parent's total
+    float *part = tpar + RH4;                      // 4 x RH4: partial sums of P_parent^T t_parent
+    float *spts = part + 4 * RH4;                  // recomputed near field: m x d coordinates
+    if (p.near_mode == DM_NEAR_CACHED) {
+        for (int j = threadIdx.x; j < m4; j += kNearBatchThreads) {
+            float v = 0.f;
+            if (j < q.m) v = permuted ? x[q.st + j] : x[H.perm[q.st + j]];
+            sx[j] = v;
+        }
+        __syncthreads();
+        const float *blk = H.Knear + ((size_t)q.leaf * H.leaf_max + q.r0) * H.ldk;
+        const int q4 = m4 >> 2;
+        const float4 *x4 = reinterpret_cast<const float4 *>(sx);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        // a warp per pair of rows; every 16-byte streaming load of both rows (up to 512
+        // columns) issued before the sums
+        for (int i = 2 * warp; i < q.nr; i += 2 * nw) {
+            const bool two = i + 1 < q.nr;
+            const float4 *ra = reinterpret_cast<const float4 *>(blk + (size_t)i * H.ldk);
+            const float4 *rb = reinterpret_cast<const float4 *>(blk + (size_t)(two ? i + 1 : i) * H.ldk);
+            float acc_a = 0.f, acc_b = 0.f;
+            for (int base = 0; base < q4; base += 128) {
+                float4 ka[4], kb[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int v = base + lane + 32 * t;
+                    ka[t] = v < q4 ? __ldcs(ra + v) : zero;
+                    kb[t] = (two && v < q4) ? __ldcs(rb + v) : zero;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int v = base + lane + 32 * t;
+                    const float4 xv = v < q4 ? x4[v] : zero;
+                    acc_a = fmaf(ka[t].x, xv.x, fmaf(ka[t].y, xv.y, fmaf(ka[t].z, xv.z, fmaf(ka[t].w, xv.w, acc_a))));
+                    acc_b = fmaf(kb[t].x, xv.x, fmaf(kb[t].y, xv.y, fmaf(kb[t].z, xv.z, fmaf(kb[t].w, xv.w, acc_b))));
+                }
+            }
+            acc_a = dm_warp_sum(acc_a);
+            acc_b = dm_warp_sum(acc_b);
+            if (lane == 0) {
+                res[i] = acc_a;
+                if (two) res[i + 1] = acc_b;
+            }
+        }
+    } else {
+        // recomputed: thread per row, entries s_i s_j 2^-|xs_i - xs_j|^2 from staged points
+        const int d = H.d;
+        for (int j = threadIdx.x; j < q.m; j += kNearBatchThreads) {
+            const float xv = permuted ? x[q.st + j] : x[H.perm[q.st + j]];
+            sx[j] = H.sp[q.st + j] * xv;
+        }
+        for (int e = threadIdx.x; e < q.m * d; e += kNearBatchThreads) spts[e] = H.Xs[q.st * d + e];
+        __syncthreads();
+        for (int li = threadIdx.x; li < q.nr; li += kNearBatchThreads) {
+            const int i = q.r0 + li;
+            float acc = 0.f;
+            for (int j = 0; j < q.m; ++j) {
+                float r2 = 0.f;
+                for (int k = 0; k < d; ++k) {
+                    const float t = spts[i * d + k] - spts[j * d + k];
+                    r2 = fmaf(t, t, r2);
+                }
+                acc = fmaf(dm_ex2(-r2), sx[j], acc);
+            }
+            res[li] = H.sp[q.st + i] * acc;
+        }
+    }
+    // the leaf's total incoming vector
+    const int node = (1 << H.L) - 1 + q.leaf;
+    const int s = H.L > 0 ? H.ranks[node] : 0;
+    const int s4 = (s + 3) & ~3;
+    if (H.L >= 2) {
+        const int par = (node - 1) >> 1, sp = H.ranks[par];
+        const int off = (node == 2 * par + 2) ? H.ranks[2 * par + 1] : 0;
+        const float *Pn = H.P + (size_t)par * H.max_rank * H.ldp + off;
+        for (int t = threadIdx.x; t < sp; t += kNearBatchThreads) tpar[t] = __ldcg(H.uhat + (size_t)par * H.max_rank + t);
+        __syncthreads();
+        // four groups of 64 threads over quarters of the parent's rank
+        const int g = threadIdx.x >> 6, j0 = threadIdx.x & 63;
+        const int tq = (sp + 3) >> 2, t0 = g * tq, t1 = min(sp, t0 + tq);
+        for (int j = j0; j < s; j += 64) {
+            float a0 = 0.f, a1 = 0.f;
+            int t = t0;
+            for (; t + 2 <= t1; t += 2) {
+                a0 = fmaf(__ldg(Pn + (size_t)t * H.ldp + j), tpar[t], a0);
+                a1 = fmaf(__ldg(Pn + (size_t)(t + 1) * H.ldp + j), tpar[t + 1], a1);
+            }
+            if (t < t1) a0 = fmaf(__ldg(Pn + (size_t)t * H.ldp + j), tpar[t], a0);
+            part[g * RH4 + j] = a0 + a1;
+        }
+        __syncthreads();
+        const float *u = H.uhat + (size_t)node * H.max_rank;
+        for (int j = threadIdx.x; j < s4; j += kNearBatchThreads)
+            tl[j] = j < s ? __ldcg(u + j) + ((part[j] + part[RH4 + j]) + (part[2 * RH4 + j] + part[3 * RH4 + j])) : 0.f;
+    } else if (H.L == 1) {
+        const float *u = H.uhat + (size_t)node * H.max_rank;
+        for (int j = threadIdx.x; j < s4; j += kNearBatchThreads) tl[j] = j < s ? __ldcg(u + j) : 0.f;
+    }
+    __syncthreads();
+    // leaf S2N: PT rows are zero padded beyond the rank
+    const float4 *t4 = reinterpret_cast<const float4 *>(tl);
+    const int q4 = s4 >> 2;
+    for (int li = threadIdx.x; li < q.nr; li += kNearBatchThreads) {
+        const int i = q.r0 + li;
+        float a0 = res[li], a1 = 0.f;
+        if (q4 > 0) {
+            const float4 *prow = reinterpret_cast<const float4 *>(dm_pt_row(H, q.leaf, i));
+            for (int v = 0; v < q4; v += 2) {
+                const float4 pa = __ldg(prow + v);
+                const float4 ta = t4[v];
+                a0 = fmaf(pa.x, ta.x, fmaf(pa.y, ta.y, fmaf(pa.z, ta.z, fmaf(pa.w, ta.w, a0))));
+                if (v + 1 < q4) {
+                    const float4 pv = __ldg(prow + v + 1);
+                    const float4 tb = t4[v + 1];
+                    a1 = fmaf(pv.x, tb.x, fmaf(pv.y, tb.y, fmaf(pv.z, tb.z, fmaf(pv.w, tb.w, a1))));
+                }
+            }
+        }
+        const float acc = a0 + a1;
+        if (p.permuted) p.y[q.st + i] = acc;
+        else p.y[H.perm[q.st + i]] = acc;
+    }
 }
 
 }  // namespace
@@ -521,15 +734,34 @@ cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, flo
     return cudaGetLastError();
 }
 
-cudaError_t dm_hmatvec_chain_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem1,
-                                   const int2 *map_down, int n_down, size_t smem2, const int *jv, cudaStream_t st) {
-    cudaError_t e = dm_allow_smem((const void *)near_up_batch_kernel, smem1);
-    if (e != cudaSuccess) return e;
-    if ((e = dm_allow_smem((const void *)down_batch_kernel, smem2)) != cudaSuccess) return e;
-    near_up_batch_kernel<<<n_up, kHThreads, smem1, st>>>(P, map_up, jv);
-    dm_count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    down_batch_kernel<<<n_down, kDownThreads, smem2, st>>>(P, map_down);
+DmBatchShape dm_batch_shape(const DmHmat &H, int near_mode) {
+    DmBatchShape c;
+    const int nleaves = 1 << H.L;
+    c.item_rows = dm_near_item_rows(near_mode, H.leaf_max);
+    c.items = nleaves * ((H.leaf_max + c.item_rows - 1) / c.item_rows);
+    c.climbs = H.L > 0 ? nleaves : 0;
+    const int m4max = (H.leaf_max + 3) & ~3;
+    const size_t RH = (size_t)H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
+    const size_t climb_bytes = sizeof(float) * (RH * RH4 + RH * C4);
+    c.climb_smem = climb_bytes <= 96 * 1024 ? 1 : 0;
+    c.smem_up = sizeof(float) * ((size_t)m4max + C4) + (c.climb_smem ? climb_bytes : 0);
+    c.smem_near = sizeof(float) * ((size_t)m4max + (size_t)((c.item_rows + 3) & ~3) + 6 * RH4);
+    if (near_mode != DM_NEAR_CACHED) c.smem_near += sizeof(float) * (size_t)H.leaf_max * H.d;
+    return c;
+}
+
+cudaError_t dm_hmatvec_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem_up,
+                             const int2 *map_near, int n_near, size_t smem_near, const int *jv, cudaStream_t st) {
+    cudaError_t e;
+    if (n_up > 0) {
+        if ((e = dm_allow_smem((const void *)up_batch_kernel, smem_up)) != cudaSuccess) return e;
+        up_batch_kernel<<<n_up, kHThreads, smem_up, st>>>(P, map_up, jv);
+        dm_count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (n_near == 0) return cudaSuccess;
+    if ((e = dm_allow_smem((const void *)near_s2n_batch_kernel, smem_near)) != cudaSuccess) return e;
+    near_s2n_batch_kernel<<<n_near, kNearBatchThreads, smem_near, st>>>(P, map_near, jv);
     dm_count_launches(1);
     return cudaGetLastError();
 }

@@ -583,12 +583,9 @@ __global__ void __launch_bounds__(kRitzThreads) ritz_batch_kernel(const DmLanczo
 // build reorders those accesses and returns wrong vectors.
 constexpr int kTvecSmemMaxM = 1024;  // 44 KB of shared memory
 template <bool kShared>
-__global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const double *beta,
-                                                  int m, const double *theta, double *Y,
-                                                  int ldy, double *work, uint64_t key) {
+__device__ __forceinline__ void tvec_body(const double *alpha, const double *beta, int m, const double *theta,
+                                          double *Y, int ldy, double *work, uint64_t key, int iv) {
     extern __shared__ double tsm[];
-    if (threadIdx.x != 0) return;
-    const int iv = blockIdx.x;
     double *dl = kShared ? tsm : work + (size_t)iv * 6 * m;  // sub (L multipliers)
     double *dd = dl + m, *du = dd + m, *du2 = du + m, *y = du2 + m;
     int *ip = reinterpret_cast<int *>(y + m);
@@ -650,10 +647,17 @@ __global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const dou
     for (int i = 0; i < m; ++i) Y[(size_t)iv * ldy + i] = y[i];
 }
 
+template <bool kShared>
+__global__ void __launch_bounds__(32) tvec_kernel(const double *alpha, const double *beta,
+                                                  int m, const double *theta, double *Y,
+                                                  int ldy, double *work, uint64_t key) {
+    if (threadIdx.x != 0) return;
+    tvec_body<kShared>(alpha, beta, m, theta, Y, ldy, work, key, (int)blockIdx.x);
+}
+
 // Gram-Schmidt of Y's columns within clusters of (numerically) equal Ritz values,
 // then an FP32 copy for the Ritz-vector product.
-__global__ void tvec_orth_kernel(int m, int k, const double *theta, double *Y, int ldy,
-                                 float *Yf) {
+__device__ __forceinline__ void tvec_orth_body(int m, int k, const double *theta, double *Y, int ldy, float *Yf) {
     __shared__ double red[32];
     __shared__ double th[kKMax];  // Ritz values staged once
     __shared__ unsigned char clus[kKMax * kKMax];  // clus[i][j]: pair (i, j) is in one cluster
@@ -700,15 +704,19 @@ __global__ void tvec_orth_kernel(int m, int k, const double *theta, double *Y, i
     }
 }
 
+__global__ void tvec_orth_kernel(int m, int k, const double *theta, double *Y, int ldy, float *Yf) {
+    tvec_orth_body(m, k, theta, Y, ldy, Yf);
+}
+
 // Phi~[pos, i] = sum_t V[t][pos] Y[t][i] (position order), plus per-column |.|^2 (FP64)
-__global__ void __launch_bounds__(256) ritzvec_kernel(const float *__restrict__ V, int64_t ldv, int m, int k,
-                                                      const float *__restrict__ Yf, int64_t N,
-                                                      float *__restrict__ Phi, double *__restrict__ colsum) {
+__device__ __forceinline__ void ritzvec_body(const float *__restrict__ V, int64_t ldv, int m, int k,
+                                             const float *__restrict__ Yf, int64_t N, float *__restrict__ Phi,
+                                             double *__restrict__ colsum, int bx) {
     extern __shared__ float sY[];  // m x k
     __shared__ float csum[kKMax][8];  // per-warp sums of squares
     for (int e = threadIdx.x; e < m * k; e += blockDim.x) sY[e] = Yf[e];
     __syncthreads();
-    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pos = bx * (int64_t)blockDim.x + threadIdx.x;
     float acc[kKMax];
 #pragma unroll
     for (int i = 0; i < kKMax; ++i) acc[i] = 0.f;
@@ -745,13 +753,17 @@ __global__ void __launch_bounds__(256) ritzvec_kernel(const float *__restrict__ 
     }
 }
 
+__global__ void __launch_bounds__(256) ritzvec_kernel(const float *__restrict__ V, int64_t ldv, int m, int k,
+                                                      const float *__restrict__ Yf, int64_t N,
+                                                      float *__restrict__ Phi, double *__restrict__ colsum) {
+    ritzvec_body(V, ldv, m, k, Yf, N, Phi, colsum, (int)blockIdx.x);
+}
+
 // normalise each column and find its largest-magnitude entry (ties: lowest original index)
-__global__ void __launch_bounds__(256) colmax_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm,
-                                                     int64_t N, int k, const double *__restrict__ colsum,
-                                                     unsigned long long *__restrict__ best) {
+__device__ __forceinline__ void colmax_body(const float *__restrict__ Phi, const int32_t *__restrict__ perm,
+                                            int64_t N, unsigned long long *__restrict__ best, int bx, int i) {
     __shared__ unsigned long long wk[8];
-    const int i = blockIdx.y;
-    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pos = bx * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long key = 0ull;
     if (pos < N) {
         const float a = fabsf(Phi[(size_t)i * N + pos]);
@@ -771,28 +783,93 @@ __global__ void __launch_bounds__(256) colmax_kernel(const float *__restrict__ P
     }
 }
 
+__global__ void __launch_bounds__(256) colmax_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm,
+                                                     int64_t N, int k, const double *__restrict__ colsum,
+                                                     unsigned long long *__restrict__ best) {
+    colmax_body(Phi, perm, N, best, (int)blockIdx.x, (int)blockIdx.y);
+}
+
 // sign of each column's largest-magnitude entry: the thread holding that original index reports it
-__global__ void sign_pick_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm, int64_t N,
-                                 const unsigned long long *__restrict__ best, int *__restrict__ neg) {
-    const int i = blockIdx.y;
-    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sign_pick_body(const float *__restrict__ Phi, const int32_t *__restrict__ perm,
+                                               int64_t N, const unsigned long long *__restrict__ best,
+                                               int *__restrict__ neg, int bx, int i) {
+    const int64_t pos = bx * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= N) return;
     const int arg = (int)(0xffffffffu - (unsigned)(best[i] & 0xffffffffull));
     if (perm[pos] == arg) neg[i] = Phi[(size_t)i * N + pos] < 0.f ? 1 : 0;
 }
 
+__global__ void sign_pick_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm, int64_t N,
+                                 const unsigned long long *__restrict__ best, int *__restrict__ neg) {
+    sign_pick_body(Phi, perm, N, best, neg, (int)blockIdx.x, (int)blockIdx.y);
+}
+
 // unit norm, largest-magnitude entry positive, scattered to the original order
-__global__ void finalize_vec_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm, int64_t N,
-                                    const double *__restrict__ colsum, const int *__restrict__ neg,
-                                    float *__restrict__ out) {
+__device__ __forceinline__ void finalize_vec_body(const float *__restrict__ Phi, const int32_t *__restrict__ perm,
+                                                  int64_t N, const double *__restrict__ colsum,
+                                                  const int *__restrict__ neg, float *__restrict__ out, int bx,
+                                                  int i) {
     __shared__ double s_sc;
-    const int i = blockIdx.y;
     // the column's scale once per block (FP64 square root and division are long sequences here)
     if (threadIdx.x == 0) s_sc = (neg[i] ? -1.0 : 1.0) / sqrt(colsum[i]);
     __syncthreads();
-    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pos = bx * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= N) return;
     out[(size_t)i * N + perm[pos]] = (float)((double)Phi[(size_t)i * N + pos] * s_sc);
+}
+
+__global__ void finalize_vec_kernel(const float *__restrict__ Phi, const int32_t *__restrict__ perm, int64_t N,
+                                    const double *__restrict__ colsum, const int *__restrict__ neg,
+                                    float *__restrict__ out) {
+    finalize_vec_body(Phi, perm, N, colsum, neg, out, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// ---- the same steps for many finished problems at once: F[f] describes problem f; the
+// vector launches run over map[block] = {f, its block of 256 positions}, blockIdx.y the column
+template <bool kShared>
+__global__ void __launch_bounds__(32) tvec_batch_kernel(const DmFinish *__restrict__ F, uint64_t key) {
+    const DmFinish &f = F[blockIdx.y];
+    if (threadIdx.x != 0 || (int)blockIdx.x >= f.k) return;
+    tvec_body<kShared>(f.alpha, f.beta, f.m, f.theta, f.Y, f.ldy, f.twork, key, (int)blockIdx.x);
+}
+
+__global__ void tvec_orth_batch_kernel(const DmFinish *__restrict__ F) {
+    const DmFinish &f = F[blockIdx.x];
+    tvec_orth_body(f.m, f.k, f.theta, f.Y, f.ldy, f.Yf);
+    // the column sums and arg-max keys start from zero in the launches that follow
+    for (int i = threadIdx.x; i < f.k; i += blockDim.x) {
+        f.colsum[i] = 0.0;
+        f.best[i] = 0ull;
+    }
+}
+
+__global__ void __launch_bounds__(256) ritzvec_batch_kernel(const DmFinish *__restrict__ F,
+                                                            const int2 *__restrict__ map) {
+    const int2 fb = map[blockIdx.x];
+    const DmFinish &f = F[fb.x];
+    ritzvec_body(f.V, f.ldv, f.m, f.k, f.Yf, f.N, f.phi, f.colsum, fb.y);
+}
+
+__global__ void __launch_bounds__(256) colmax_batch_kernel(const DmFinish *__restrict__ F,
+                                                           const int2 *__restrict__ map) {
+    const int2 fb = map[blockIdx.x];
+    const DmFinish &f = F[fb.x];
+    if ((int)blockIdx.y >= f.k) return;
+    colmax_body(f.phi, f.perm, f.N, f.best, fb.y, (int)blockIdx.y);
+}
+
+__global__ void sign_pick_batch_kernel(const DmFinish *__restrict__ F, const int2 *__restrict__ map) {
+    const int2 fb = map[blockIdx.x];
+    const DmFinish &f = F[fb.x];
+    if ((int)blockIdx.y >= f.k) return;
+    sign_pick_body(f.phi, f.perm, f.N, f.best, f.neg, fb.y, (int)blockIdx.y);
+}
+
+__global__ void finalize_vec_batch_kernel(const DmFinish *__restrict__ F, const int2 *__restrict__ map) {
+    const int2 fb = map[blockIdx.x];
+    const DmFinish &f = F[fb.x];
+    if ((int)blockIdx.y >= f.k) return;
+    finalize_vec_body(f.phi, f.perm, f.N, f.colsum, f.neg, f.evecs, fb.y, (int)blockIdx.y);
 }
 
 __global__ void coords_kernel(const float *__restrict__ evecs, const double *__restrict__ theta,
@@ -809,6 +886,46 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 int dm_lanczos_kmax() { return kKMax; }
+
+// ---- start vectors of many problems: zero their accumulators, draw, normalise (three launches)
+__global__ void start_zero_batch_kernel(const DmStart *__restrict__ S) {
+    const DmStart &s = S[blockIdx.x];
+    for (int i = threadIdx.x; i < s.hlen; i += blockDim.x) s.h[i] = 0.0;
+    if (threadIdx.x == 0) {
+        *s.nrm2 = 0.0;
+        *s.jv = 0;
+    }
+}
+
+__global__ void start_vector_batch_kernel(const DmStart *__restrict__ S, const int2 *__restrict__ map) {
+    const int2 sb = map[blockIdx.x];
+    const DmStart &s = S[sb.x];
+    const int64_t pos = sb.y * (int64_t)blockDim.x + threadIdx.x;
+    float v = 0.f;
+    if (pos < s.N) {
+        v = (float)(2.0 * dm_unit(dm_rng(s.key, (uint64_t)s.perm[pos])) - 1.0);
+        s.z[pos] = v;
+    }
+    const float ss = dm_warp_sum(v * v);
+    if ((threadIdx.x & 31) == 0) atomicAdd(s.nrm2, (double)ss);
+}
+
+__global__ void normalize_batch_kernel(const DmStart *__restrict__ S, const int2 *__restrict__ map) {
+    const int2 sb = map[blockIdx.x];
+    const DmStart &s = S[sb.x];
+    const int64_t i = sb.y * (int64_t)blockDim.x + threadIdx.x;
+    if (i < s.N) s.V[i] = (float)((double)s.z[i] / sqrt(*s.nrm2));
+}
+
+uint64_t dm_start_key(uint64_t seed) { return dm_stream_key(seed, DM_TAG_V0, 0); }
+
+cudaError_t dm_lanczos_start_batch(const DmStart *S, int ns, const int2 *map, int nmap, cudaStream_t st) {
+    start_zero_batch_kernel<<<ns, 256, 0, st>>>(S);
+    start_vector_batch_kernel<<<nmap, 256, 0, st>>>(S, map);
+    normalize_batch_kernel<<<nmap, 256, 0, st>>>(S, map);
+    dm_count_launches(3);
+    return cudaGetLastError();
+}
 
 cudaError_t dm_lanczos_start(DmLanczos &Lz, const int32_t *perm, uint64_t seed, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(Lz.nrm2, 0, sizeof(double), st);
@@ -947,6 +1064,34 @@ cudaError_t dm_lanczos_phi(DmLanczos &Lz, int m, int k, const int32_t *perm, flo
     dm_count_launches(1);
     finalize_vec_kernel<<<g2, 256, 0, st>>>(phi_work, perm, Lz.N, Lz.colsum, Lz.neg, evecs_orig);
     dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+int dm_finish_blocks(int64_t N) { return nblk(N, 256); }
+
+cudaError_t dm_lanczos_finish_batch(const DmFinish *F, int nf, const int2 *map, int nmap, int m_hi, int k_hi,
+                                    cudaStream_t st) {
+    const uint64_t key = dm_stream_key(0x5eedULL, DM_TAG_V0, 1);  // the single-problem path's draws
+    cudaError_t e;
+    if (m_hi <= kTvecSmemMaxM) {
+        const size_t sh = (sizeof(double) * 5 + sizeof(int)) * (size_t)m_hi;
+        if ((e = dm_allow_smem((const void *)tvec_batch_kernel<true>, sh)) != cudaSuccess) return e;
+        tvec_batch_kernel<true><<<dim3((unsigned)k_hi, (unsigned)nf), 32, sh, st>>>(F, key);
+    } else {
+        tvec_batch_kernel<false><<<dim3((unsigned)k_hi, (unsigned)nf), 32, 0, st>>>(F, key);
+    }
+    dm_count_launches(1);
+    tvec_orth_batch_kernel<<<nf, 256, 0, st>>>(F);
+    dm_count_launches(1);
+    const size_t ysh = sizeof(float) * (size_t)m_hi * k_hi;
+    if ((e = dm_allow_smem((const void *)ritzvec_batch_kernel, ysh)) != cudaSuccess) return e;
+    ritzvec_batch_kernel<<<nmap, 256, ysh, st>>>(F, map);
+    dm_count_launches(1);
+    const dim3 g2((unsigned)nmap, (unsigned)k_hi);
+    colmax_batch_kernel<<<g2, 256, 0, st>>>(F, map);
+    sign_pick_batch_kernel<<<g2, 256, 0, st>>>(F, map);
+    finalize_vec_batch_kernel<<<g2, 256, 0, st>>>(F, map);
+    dm_count_launches(3);
     return cudaGetLastError();
 }
 
