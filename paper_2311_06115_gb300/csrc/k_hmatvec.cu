@@ -104,6 +104,41 @@ __device__ __forceinline__ void gemv2_rows_global(const float *__restrict__ P, i
     }
 }
 
+// Leaf N2S, out[t] = P[t, 0:m] . v for t < s (rows zero padded to a multiple of 4): four
+// threads per row and 64 rows per pass of the block, each thread with up to eight 16-byte loads
+// in flight before its sums, so that a leaf's basis arrives in one or two memory round trips.
+__device__ __forceinline__ void gemv_leaf(const float *__restrict__ P, int ldp, int s, int m, const float *v,
+                                          float *out_global) {
+    const int g = threadIdx.x & 3, row = threadIdx.x >> 2;
+    const int q4 = (m + 3) >> 2;
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+    for (int t0 = 0; t0 < s; t0 += kHThreads / 4) {
+        const int t = t0 + row;
+        const bool live = t < s;
+        const float4 *pr = reinterpret_cast<const float4 *>(P + (size_t)(live ? t : 0) * ldp);
+        float acc = 0.f;
+        for (int base = g; base < q4; base += 32) {
+            float4 pv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = base + 4 * u;
+                pv[u] = (live && q < q4) ? __ldg(pr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = base + 4 * u;
+                if (q < q4) {
+                    const float4 xv = v4[q];
+                    acc = fmaf(pv[u].x, xv.x, fmaf(pv[u].y, xv.y, fmaf(pv[u].z, xv.z, fmaf(pv[u].w, xv.w, acc))));
+                }
+            }
+        }
+        acc += __shfl_xor_sync(DM_FULL, acc, 1);
+        acc += __shfl_xor_sync(DM_FULL, acc, 2);
+        if (live && g == 0) out_global[t] = acc;
+    }
+}
+
 // out[t] = P[t, 0:c] . v for t < s from a shared-memory copy of P with row stride ld4 (multiple of 4)
 __device__ __forceinline__ void gemv_rows_smem(const float *Ps, int ld4, int s, int c, const float *v, float *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -157,37 +192,25 @@ __device__ __forceinline__ void sweep_down(const DmHmat &H) {
     }
 }
 
-// Leaf N2S of leaf `leaf`, then the climb by last arrival (see the file header). With `sweep`,
-// the block that completes the root then runs sweep_down.
-__device__ __forceinline__ void climb_body(const DmHmat &H, int leaf, const float *__restrict__ x, int permuted,
-                                           int climb_smem, bool sweep) {
-    extern __shared__ float4 smem4[];
-    float *sm = reinterpret_cast<float *>(smem4);
+// The climb by last arrival (see the file header) from `node`, whose weights this block has
+// written: count the arrival at the parent; the second block to arrive owns the parent, runs
+// the pair's S2S and the parent's N2S, and climbs on. With `owned`, the block already owns
+// node's parent (both children written before this launch) and skips the first arrival. With
+// `sweep`, the block that completes the root then runs sweep_down. sw: shared memory for the
+// children's weights, followed by the parent's operands when climb_smem.
+__device__ __forceinline__ void climb_loop(const DmHmat &H, int node, int climb_smem, bool sweep, bool owned,
+                                           float *sw) {
     __shared__ int s_go;
-    const int nleaves = 1 << H.L;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int m4max = (H.leaf_max + 3) & ~3;
-    {
-        int node = nleaves - 1 + leaf;
-        int64_t st, sz;
-        dm_node_range(H.N, node, &st, &sz);
-        const int m = (int)sz, m4 = (m + 3) & ~3;
-        const int RH = H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
-        float *sx = sm;                          // m4max
-        float *sw = sm + m4max;                  // C4: children weights
-        float *Bs = sw + C4;                     // RH x RH4: parent's K(S_l, S_r)
-        float *Ps = Bs + RH * RH4;               // RH x C4: parent's P
-        stage_x(H, x, permuted != 0, st, m, m4, sx);
-        __syncthreads();
-        const int s_leaf = H.ranks[node];
-        gemv2_rows_global(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, s_leaf, m, sx,
-                          H.what + (size_t)node * H.max_rank);
-        if (H.L == 0) return;
-        for (;;) {
-            const int parent = (node - 1) >> 1;
-            const int l = 2 * parent + 1, r = 2 * parent + 2;
-            const int sl = H.ranks[l], sr = H.ranks[r], sp = parent > 0 ? H.ranks[parent] : 0;
-            const int c = sl + sr, c4 = (c + 3) & ~3;
+    const int RH = H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
+    float *Bs = sw + C4;          // RH x RH4: parent's K(S_l, S_r)
+    float *Ps = Bs + RH * RH4;    // RH x C4: parent's P
+    for (;;) {
+        const int parent = (node - 1) >> 1;
+        const int l = 2 * parent + 1, r = 2 * parent + 2;
+        const int sl = H.ranks[l], sr = H.ranks[r], sp = parent > 0 ? H.ranks[parent] : 0;
+        const int c = sl + sr, c4 = (c + 3) & ~3;
+        if (!owned) {
             // publish this node's weights, then count the arrival at the parent
             __threadfence();
             __syncthreads();
@@ -199,72 +222,92 @@ __device__ __forceinline__ void climb_body(const DmHmat &H, int leaf, const floa
             }
             __syncthreads();
             if (!s_go) return;  // the sibling's block climbs on
-            node = parent;
-            if (climb_smem) {
-                // the parent's operands (asynchronous copies), in flight while the children's
-                // weights are read
-                const float *Bn = H.B + (size_t)parent * H.max_rank * H.max_rank;
-                for (int e = threadIdx.x; e < sl * sr; e += blockDim.x) {
-                    const int ia = e / sr, ib = e % sr;
-                    dm_cp_async4(Bs + ia * RH4 + ib, Bn + e);
-                }
-                const float *Pn = H.P + (size_t)parent * H.max_rank * H.ldp;
-                const int q4 = c4 >> 2;
-                for (int e = threadIdx.x; e < sp * q4; e += blockDim.x) {
-                    const int t = e / q4, q = e % q4;
-                    dm_cp_async16(Ps + t * C4 + 4 * q, Pn + (size_t)t * H.ldp + 4 * q);  // rows zero padded to ldp
-                }
-            }
-            for (int j = threadIdx.x; j < c4; j += blockDim.x) {
-                float v = 0.f;
-                if (j < sl) v = __ldcg(H.what + (size_t)l * H.max_rank + j);
-                else if (j < c) v = __ldcg(H.what + (size_t)r * H.max_rank + (j - sl));
-                sw[j] = v;
-            }
-            if (climb_smem) dm_cp_async_wait_all();
-            __syncthreads();
-            // S2S: u_l = B w_r (warp per row of B), u_r = B^T w_l (thread per column of B)
-            if (climb_smem) {
-                for (int a2 = warp; a2 < sl; a2 += kHWarps) {
-                    float acc = 0.f;
-                    for (int b2 = lane; b2 < sr; b2 += 32) acc = fmaf(Bs[a2 * RH4 + b2], sw[sl + b2], acc);
-                    acc = dm_warp_sum(acc);
-                    if (lane == 0) H.uhat[(size_t)l * H.max_rank + a2] = acc;
-                }
-                for (int b2 = threadIdx.x; b2 < sr; b2 += blockDim.x) {
-                    float acc = 0.f;
-                    for (int a2 = 0; a2 < sl; ++a2) acc = fmaf(Bs[a2 * RH4 + b2], sw[a2], acc);
-                    H.uhat[(size_t)r * H.max_rank + b2] = acc;
-                }
-            } else {
-                const float *Bn = H.B + (size_t)node * H.max_rank * H.max_rank;
-                for (int a2 = warp; a2 < sl; a2 += kHWarps) {
-                    float acc = 0.f;
-                    for (int b2 = lane; b2 < sr; b2 += 32) acc = fmaf(__ldg(Bn + (size_t)a2 * sr + b2), sw[sl + b2], acc);
-                    acc = dm_warp_sum(acc);
-                    if (lane == 0) H.uhat[(size_t)l * H.max_rank + a2] = acc;
-                }
-                for (int b2 = threadIdx.x; b2 < sr; b2 += blockDim.x) {
-                    float acc = 0.f;
-                    for (int a2 = 0; a2 < sl; ++a2) acc = fmaf(__ldg(Bn + (size_t)a2 * sr + b2), sw[a2], acc);
-                    H.uhat[(size_t)r * H.max_rank + b2] = acc;
-                }
-            }
-            if (node == 0) {
-                if (sweep) {
-                    __syncthreads();
-                    sweep_down(H);
-                }
-                return;
-            }
-            // N2S of the internal node
-            if (climb_smem) gemv_rows_smem(Ps, C4, sp, c, sw, H.what + (size_t)node * H.max_rank);
-            else
-                gemv_rows(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, sp, c, sw,
-                          H.what + (size_t)node * H.max_rank, nullptr);
-            __syncthreads();  // Bs/Ps are refilled for the next parent
         }
+        owned = false;
+        node = parent;
+        if (climb_smem) {
+            // the parent's operands (asynchronous copies), in flight while the children's
+            // weights are read
+            const float *Bn = H.B + (size_t)parent * H.max_rank * H.max_rank;
+            for (int e = threadIdx.x; e < sl * sr; e += blockDim.x) {
+                const int ia = e / sr, ib = e % sr;
+                dm_cp_async4(Bs + ia * RH4 + ib, Bn + e);
+            }
+            const float *Pn = H.P + (size_t)parent * H.max_rank * H.ldp;
+            const int q4 = c4 >> 2;
+            for (int e = threadIdx.x; e < sp * q4; e += blockDim.x) {
+                const int t = e / q4, q = e % q4;
+                dm_cp_async16(Ps + t * C4 + 4 * q, Pn + (size_t)t * H.ldp + 4 * q);  // rows zero padded to ldp
+            }
+        }
+        for (int j = threadIdx.x; j < c4; j += blockDim.x) {
+            float v = 0.f;
+            if (j < sl) v = __ldcg(H.what + (size_t)l * H.max_rank + j);
+            else if (j < c) v = __ldcg(H.what + (size_t)r * H.max_rank + (j - sl));
+            sw[j] = v;
+        }
+        if (climb_smem) dm_cp_async_wait_all();
+        __syncthreads();
+        // S2S: u_l = B w_r (warp per row of B), u_r = B^T w_l (thread per column of B)
+        if (climb_smem) {
+            for (int a2 = warp; a2 < sl; a2 += kHWarps) {
+                float acc = 0.f;
+                for (int b2 = lane; b2 < sr; b2 += 32) acc = fmaf(Bs[a2 * RH4 + b2], sw[sl + b2], acc);
+                acc = dm_warp_sum(acc);
+                if (lane == 0) H.uhat[(size_t)l * H.max_rank + a2] = acc;
+            }
+            for (int b2 = threadIdx.x; b2 < sr; b2 += blockDim.x) {
+                float acc = 0.f;
+                for (int a2 = 0; a2 < sl; ++a2) acc = fmaf(Bs[a2 * RH4 + b2], sw[a2], acc);
+                H.uhat[(size_t)r * H.max_rank + b2] = acc;
+            }
+        } else {
+            const float *Bn = H.B + (size_t)node * H.max_rank * H.max_rank;
+            for (int a2 = warp; a2 < sl; a2 += kHWarps) {
+                float acc = 0.f;
+                for (int b2 = lane; b2 < sr; b2 += 32) acc = fmaf(__ldg(Bn + (size_t)a2 * sr + b2), sw[sl + b2], acc);
+                acc = dm_warp_sum(acc);
+                if (lane == 0) H.uhat[(size_t)l * H.max_rank + a2] = acc;
+            }
+            for (int b2 = threadIdx.x; b2 < sr; b2 += blockDim.x) {
+                float acc = 0.f;
+                for (int a2 = 0; a2 < sl; ++a2) acc = fmaf(__ldg(Bn + (size_t)a2 * sr + b2), sw[a2], acc);
+                H.uhat[(size_t)r * H.max_rank + b2] = acc;
+            }
+        }
+        if (node == 0) {
+            if (sweep) {
+                __syncthreads();
+                sweep_down(H);
+            }
+            return;
+        }
+        // N2S of the internal node
+        if (climb_smem) gemv_rows_smem(Ps, C4, sp, c, sw, H.what + (size_t)node * H.max_rank);
+        else
+            gemv_rows(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, sp, c, sw, H.what + (size_t)node * H.max_rank,
+                      nullptr);
+        __syncthreads();  // Bs/Ps are refilled for the next parent
     }
+}
+
+// Leaf N2S of leaf `leaf`, then the climb from it
+__device__ __forceinline__ void climb_body(const DmHmat &H, int leaf, const float *__restrict__ x, int permuted,
+                                           int climb_smem, bool sweep) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const int nleaves = 1 << H.L;
+    const int m4max = (H.leaf_max + 3) & ~3;
+    const int node = nleaves - 1 + leaf;
+    int64_t st, sz;
+    dm_node_range(H.N, node, &st, &sz);
+    const int m = (int)sz, m4 = (m + 3) & ~3;
+    float *sx = sm;  // m4max
+    stage_x(H, x, permuted != 0, st, m, m4, sx);
+    __syncthreads();
+    gemv_leaf(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, H.ranks[node], m, sx, H.what + (size_t)node * H.max_rank);
+    if (H.L == 0) return;
+    climb_loop(H, node, climb_smem, sweep, false, sm + m4max);
 }
 
 // body of the chained form's first launch for one problem: block `bid` of its grid (leaf climbs
@@ -504,8 +547,9 @@ __global__ void __launch_bounds__(kDownThreads) down_kernel(const __grid_constan
 }
 
 // ---- batched form (many problems, two launches) --------------------------------------------
-//  up_batch_kernel        map[block] = {problem, leaf}: leaf N2S and the climb; the block that
-//                         completes a root sweeps that tree's internal levels (sweep_down).
+//  up_batch_kernel        map[block] = {problem, leaf}: leaf N2S and the climb by last arrival;
+//                         the block that completes a root sweeps that tree's internal levels
+//                         top-down (sweep_down).
 //  near_s2n_batch_kernel  map[block] = {problem, item}, item = (leaf, chunk of item_rows rows):
 //                         the near rows (cached blocks streamed, or recomputed) into shared
 //                         memory, then the leaf's total incoming vector
