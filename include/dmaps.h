@@ -221,8 +221,8 @@ typedef struct dm_stats {
     int32_t degree_path;     /* degree passes of dm_create: 0 = CUDA cores (FP32 entries),
                                 1 = tensor cores, TF32 three-term split Gram matrix (d >= 16),
                                 2 = tensor cores, exact BF16 Gram matrix (8-bit quantised data) */
-    float ms_degrees;        /* device time of the two degree passes of dm_create (CUDA-core path;
-                                0 for the tensor-core path), including the q^-a step between them */
+    float ms_degrees;        /* device time of the two degree passes of dm_create, including the
+                                q^-a step between them (tensor-core path: and the operand packing) */
 } dm_stats;
 
 /* Phase times and structure statistics of the handle's last calls (introspection; no

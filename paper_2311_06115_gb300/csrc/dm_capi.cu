@@ -1273,10 +1273,12 @@ int dm_create(const float *points, int64_t N, int32_t d, double eps, double alph
             DM_CHECK(h->alloc(&derr, 1, G_WORK));
             DM_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), h->stream));
             DmDegTc S{};
+            cudaEvent_t lap = h->lap_begin(h->stream);
             DM_CUDA(dm_degtc_prepare(h->X, N, d, eps, work, &S, h->stream));
             DM_CUDA(dm_degtc_pass(S, nullptr, h->q, derr, h->stream));
             DM_CUDA(dm_launch_finish_degrees(N, alpha, h->q, h->qa, h->qaf, h->stream));
             DM_CUDA(dm_degtc_pass(S, h->qaf, h->dg, derr, h->stream));
+            h->lap_end(h->stream, lap, &h->stats.ms_degrees);
             DM_CUDA(dm_launch_finish_scaling(N, h->qa, h->dg, h->s, h->sf, h->stream));
             int herr = 0;
             DM_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
