@@ -139,13 +139,17 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
 /* Top-k eigenpairs of `count` compressed handles at once: the batching of many uneven point
  * clouds (no paper counterpart; each handle's solve is dm_eigs' single-vector Lanczos of
  * Algorithm 2 in its symmetric form, Section 2.3.1). Every Lanczos step of every handle not
- * yet converged runs in the same launches: the chained H-matvec of Eq. 2.18 (two launches for
- * all handles: leaf N2S with the climb up the tree and the near field, then the downward pass
- * with the leaf S2N), the three Gram-Schmidt passes (three launches), and at each convergence
- * check one launch of Ritz values for all handles and one host read. A handle leaves the batch
- * when it converges (its Ritz vectors are formed then), so the launch count per step does not
- * grow with the number of handles. Each handle keeps its own seed, m_max, check_every (the
- * smallest is used) and conv_tol; cfg.block_size and block_precision are ignored.
+ * yet converged runs in the same launches, each handle at its own step: the H-matvec of
+ * Eq. 2.18 in two launches for all handles (leaf N2S and the climb up each tree, whose root
+ * block then sweeps the tree's internal levels top-down; then the near field fused with the
+ * leaf S2N), and the three Gram-Schmidt passes. The start vectors of the handles, and the
+ * Ritz vectors of the handles finishing at the same step, are formed in shared launches too.
+ * Each handle is checked on its own schedule (from step ceil(5k/4)+5, every check_every
+ * steps); the checks due after a step share one launch of Ritz values, read by the host one
+ * step later while the next step runs, so a converged handle takes one step more than its
+ * solo solve before it leaves (its Ritz pairs are those of the checked step). The launch
+ * count per step does not grow with the number of handles. Each handle keeps its own seed,
+ * m_max, check_every and conv_tol; cfg.block_size and block_precision are ignored.
  * hs: `count` distinct compressed handles on one device; the work runs on hs[0]'s stream
  * after the queued work of every handle. evals: count x k doubles, handle i at i k,
  * descending (host or device). evecs: NULL, or `count` pointers, each NULL or N_i x k floats
@@ -255,12 +259,18 @@ int dm_sfu_peak(int64_t *ex2_count, float *ms);
 int dm_selftest_wait_timeout(int32_t blocks, int32_t missing, int64_t spin_limit, int32_t *passed);
 
 /* ---- serving: continuous admission of independent solves ----
- * A process-wide server runs `slots` solves at once, each on its own CUDA stream,
- * so their kernels overlap on the device. Requests wait in a queue and are
- * admitted first-fit, in arrival order, whenever a slot is free and the request's
- * device footprint (dm_request_bytes) fits in what is left of the HBM budget (a
- * request larger than the whole budget runs alone). Each result is computed
- * exactly as by dm_create + dm_compress + dm_eigs on a fresh handle.
+ * A process-wide server builds `slots` requests at once (dm_create + dm_compress), each slot
+ * on its own CUDA stream, so their kernels overlap on the device. Requests wait in a queue
+ * and are admitted first-fit, in arrival order, whenever a slot is free and the request's
+ * device footprint (dm_request_bytes) fits in what is left of the HBM budget (a request
+ * larger than the whole budget runs alone). A built single-vector request (block_size 0 or
+ * 1) then joins the batched eigensolver of dm_eigs_batch, run by one thread of the server:
+ * every resident request's Lanczos step runs in the same launches, each at its own step, and
+ * a request leaves (its results copied out, its memory released) when its own check says it
+ * converged; requests join between steps (continuous batching at the step level). Block
+ * requests run their eigensolve on their slot. Each result is that of dm_create +
+ * dm_compress + dm_eigs on a fresh handle with check_every = 2: the same Lanczos steps and
+ * checks, equal up to the FP32 summation order of the batched H-matvec.
  * Submit and poll are thread-safe. No counterpart in the paper. */
 typedef struct dm_request {
     const float *points;   /* N x d row-major float32, host memory; copied by dm_submit */
@@ -288,7 +298,7 @@ typedef struct dm_result {
 
 typedef struct dm_serve_config {
     int32_t device;             /* CUDA device ordinal (-1: current) */
-    int32_t slots;              /* concurrent solves (default 4) */
+    int32_t slots;              /* concurrent builds (and block solves) (default 4) */
     uint64_t hbm_budget_bytes;  /* admission budget (0: 150 GB) */
     int32_t queue_capacity;     /* waiting requests before DM_EBUSY (0: 65536) */
 } dm_serve_config;
@@ -297,8 +307,8 @@ typedef struct dm_serve_config {
 uint64_t dm_request_bytes(const dm_request *r);
 /* Start the server (DM_ESTATE if running; DM_ECUDA without a device). */
 int dm_serve_start(const dm_serve_config *cfg);
-/* Stop accepting work, finish running solves, drop queued ones (their status
- * becomes DM_ESTATE), join the workers and free every result. */
+/* Stop accepting work, finish the running builds and every resident solve, drop queued
+ * requests (their status becomes DM_ESTATE), join the threads and free every result. */
 int dm_serve_stop(void);
 /* Queue a request; *t identifies it. DM_EINVAL for an invalid request, DM_ESTATE
  * if the server is not running, DM_EBUSY if the queue is full. */
