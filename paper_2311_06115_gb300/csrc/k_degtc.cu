@@ -18,10 +18,11 @@
 // n_i is the same product's diagonal, so the diagonal entries are exp(0) = 1 up to the
 // FP32 accumulation order.
 //
-// One CTA per (128-row, 256-column) tile; warp 0 issues TMA loads into a 2-stage ring,
-// warp 1 issues the MMAs, all four warps run the epilogue (thread = row). Two CTAs fit on
-// an SM (shared memory, and 2 x 256 TMEM columns), so one's epilogue overlaps the other's
-// MMAs. Waits are bounded; a timeout raises *err and the tile is skipped.
+// One CTA per (128-row, 256-column) tile, in a grouped tile order (see the kernel); warp 0
+// issues TMA loads into a 2-stage ring, warp 1 issues the MMAs, all four warps run the
+// epilogue (thread = row). Two CTAs fit on an SM (shared memory, and 2 x 256 TMEM columns),
+// so one's epilogue overlaps the other's MMAs. Waits are bounded; a timeout raises *err and
+// the tile is skipped.
 #include <cuda_bf16.h>
 
 #include "dm_internal.cuh"
@@ -38,6 +39,7 @@ constexpr int kDtBN = 256;
 constexpr uint32_t kDtABytes = kDtBM * 128;   // 128 rows x 128 bytes (64 BF16 or 32 FP32)
 constexpr uint32_t kDtBBytes = kDtBN * 128;   // 256 rows x 128 bytes
 constexpr uint32_t kDtStage = kDtABytes + kDtBBytes;
+constexpr int kDtGroup = 16;  // row tiles per group of the tile order
 
 template <bool kTf32>
 __global__ void __launch_bounds__(kDtThreads) degtc_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -57,7 +59,15 @@ __global__ void __launch_bounds__(kDtThreads) degtc_kernel(const __grid_constant
     float *s_w = s_a + kDtBN;                               // kDtBN weights (0 past N)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t j0 = (int64_t)blockIdx.x * kDtBN, i0 = (int64_t)blockIdx.y * kDtBM;
+    // tiles in groups of kDtGroup row tiles: consecutive CTAs walk the column tiles of one
+    // group, so the CTAs resident at a time share a few row tiles and a band of column tiles
+    // in L2 (in launch order along whole rows, every row tile would stream all of X again)
+    const int64_t ntm = (N + kDtBM - 1) / kDtBM, ntn = (N + kDtBN - 1) / kDtBN;
+    const int64_t pid = blockIdx.x, per_group = (int64_t)kDtGroup * ntn;
+    const int64_t first_m = (pid / per_group) * kDtGroup;
+    const int64_t gsize = ntm - first_m < kDtGroup ? ntm - first_m : kDtGroup;
+    const int64_t r = pid - (pid / per_group) * per_group;
+    const int64_t i0 = (first_m + r % gsize) * kDtBM, j0 = (r / gsize) * kDtBN;
     constexpr int kElems = kTf32 ? 32 : 64;  // K elements per 128-byte row
     const int ksteps = kpad / kElems;
 
@@ -294,8 +304,9 @@ cudaError_t degtc_launch(const DmDegTc &S, const float *w, double *out, int *err
     if (e != cudaSuccess) return e;
     const size_t smem = 1024 + (size_t)kDtStages * kDtStage + 256 + 2 * kDtBN * sizeof(float);
     if ((e = dm_allow_smem((const void *)degtc_kernel<kTf32>, smem)) != cudaSuccess) return e;
-    dim3 grid((unsigned)((S.N + kDtBN - 1) / kDtBN), (unsigned)((S.N + kDtBM - 1) / kDtBM));
-    degtc_kernel<kTf32><<<grid, kDtThreads, smem, st>>>(tmA, tmB, S.N, S.kpad, S.kappa, S.an, w, out, err);
+    const int64_t tiles = ((S.N + kDtBN - 1) / kDtBN) * ((S.N + kDtBM - 1) / kDtBM);
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    degtc_kernel<kTf32><<<(unsigned)tiles, kDtThreads, smem, st>>>(tmA, tmB, S.N, S.kpad, S.kappa, S.an, w, out, err);
     dm_count_launches(1);
     return cudaGetLastError();
 }
