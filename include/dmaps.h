@@ -294,6 +294,8 @@ typedef struct dm_result {
     double submit_ms, start_ms, done_ms;  /* wall-clock times since dm_serve_start */
     int32_t lanczos_iters;
     const char *error;     /* message of the failing call ("" on success); library-owned */
+    double built_ms;       /* wall-clock time since dm_serve_start when the request's build
+                              (dm_create + dm_compress) ended and its eigensolve began */
 } dm_result;
 
 typedef struct dm_serve_config {

@@ -70,7 +70,8 @@ class dm_request(C.Structure):
 class dm_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("k", C.c_int32), ("N", C.c_int64), ("evals", C.POINTER(C.c_double)),
                 ("evecs", C.POINTER(C.c_float)), ("submit_ms", C.c_double), ("start_ms", C.c_double),
-                ("done_ms", C.c_double), ("lanczos_iters", C.c_int32), ("error", C.c_char_p)]
+                ("done_ms", C.c_double), ("lanczos_iters", C.c_int32), ("error", C.c_char_p),
+                ("built_ms", C.c_double)]
 
 
 class dm_serve_config(C.Structure):
@@ -508,7 +509,7 @@ def dm_poll(ticket: int):
     if not done.value:
         return False, None
     out = {"status": int(r.status), "k": int(r.k), "N": int(r.N), "submit_ms": r.submit_ms, "start_ms": r.start_ms,
-           "done_ms": r.done_ms, "lanczos_iters": int(r.lanczos_iters), "evals": None, "evecs": None,
+           "built_ms": r.built_ms, "done_ms": r.done_ms, "lanczos_iters": int(r.lanczos_iters), "evals": None, "evecs": None,
            "error": (r.error or b"").decode(errors="replace")}
     if r.evals:
         out["evals"] = np.ctypeslib.as_array(r.evals, shape=(r.k,)).copy()

@@ -1496,7 +1496,7 @@ struct DmBatchSolver {
     cudaStream_t st = nullptr;
     // per slot (host); a slot is reused after its problem is finished
     std::vector<dm_ctx *> h;
-    std::vector<int> k, cap, jh, first, every, since, state, sblk;
+    std::vector<int> k, cap, jh, first, every, state, sblk;
     std::vector<size_t> shm;
     std::vector<void *> tag;
     std::vector<DmBatchShape> shape;
@@ -1505,10 +1505,11 @@ struct DmBatchSolver {
     std::vector<int> act;       // stepping slots, in join order
     std::vector<int> starting;  // slots whose start vector is drawn before the next step
     int in_use = 0;
+    int64_t gstep = 0;  // steps launched by this solver
     bool dirty = true;
     // launch geometry of the stepping problems
-    int n_up = 0, n_nr = 0, n_st = 0, n_start = 0, n_smap = 0;
-    size_t smem_up = 0, smem_nr = 0, smem_step = 0;
+    int n_up = 0, n_sw = 0, n_nr = 0, n_st = 0, n_start = 0, n_smap = 0;
+    size_t smem_up = 0, smem_sw = 0, smem_nr = 0, smem_step = 0;
     // descriptors and launch maps in one device blob, uploaded from one of two pinned
     // staging buffers (each reused only after its last upload has completed)
     unsigned char *blob = nullptr, *stage[2] = {nullptr, nullptr};
@@ -1517,7 +1518,7 @@ struct DmBatchSolver {
     int cur = 0;
     const DmChainProblem *dcp = nullptr;
     const DmLanczosProblem *dlp = nullptr;
-    const int2 *dup = nullptr, *dnr = nullptr;
+    const int2 *dup = nullptr, *dsw = nullptr, *dnr = nullptr;
     const int4 *dst = nullptr;
     const DmStart *dss = nullptr;
     const int2 *dsm = nullptr;
@@ -1606,10 +1607,12 @@ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 // descriptors of every slot and the launch maps of the stepping problems (the climbs, the
 // near items and the Gram-Schmidt blocks of each), plus the start vectors of those joining
 int batch_rebuild(DmBatchSolver &B) {
-    B.n_up = B.n_nr = B.n_st = 0;
-    B.smem_up = B.smem_nr = B.smem_step = 0;
+    B.n_up = B.n_sw = B.n_nr = B.n_st = 0;
+    B.smem_up = B.smem_sw = B.smem_nr = B.smem_step = 0;
     for (int p : B.act) {
         B.n_up += B.shape[p].climbs;
+        B.n_sw += B.shape[p].sweeps;
+        B.smem_sw = B.shape[p].smem_sweep > B.smem_sw ? B.shape[p].smem_sweep : B.smem_sw;
         B.n_nr += B.shape[p].items;
         B.n_st += B.sblk[p];
         B.smem_up = B.shape[p].smem_up > B.smem_up ? B.shape[p].smem_up : B.smem_up;
@@ -1622,7 +1625,8 @@ int batch_rebuild(DmBatchSolver &B) {
     const size_t ns = B.cp.size();
     const size_t o_cp = 0, o_lp = a16(o_cp + sizeof(DmChainProblem) * ns);
     const size_t o_up = a16(o_lp + sizeof(DmLanczosProblem) * ns);
-    const size_t o_nr = a16(o_up + sizeof(int2) * (size_t)B.n_up);
+    const size_t o_sw = a16(o_up + sizeof(int2) * (size_t)B.n_up);
+    const size_t o_nr = a16(o_sw + sizeof(int2) * (size_t)B.n_sw);
     const size_t o_st = a16(o_nr + sizeof(int2) * (size_t)B.n_nr);
     const size_t o_ss = a16(o_st + sizeof(int4) * (size_t)B.n_st);
     const size_t o_sm = a16(o_ss + sizeof(DmStart) * (size_t)B.n_start);
@@ -1656,6 +1660,7 @@ int batch_rebuild(DmBatchSolver &B) {
     std::memcpy(hs + o_cp, B.cp.data(), sizeof(DmChainProblem) * ns);
     std::memcpy(hs + o_lp, B.lp.data(), sizeof(DmLanczosProblem) * ns);
     int2 *up = reinterpret_cast<int2 *>(hs + o_up);
+    int2 *sw = reinterpret_cast<int2 *>(hs + o_sw);
     int2 *nr = reinterpret_cast<int2 *>(hs + o_nr);
     int4 *sp = reinterpret_cast<int4 *>(hs + o_st);
     // the deepest trees first: their climbs and sweeps are the longest chains
@@ -1663,6 +1668,7 @@ int batch_rebuild(DmBatchSolver &B) {
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B.cp[a].H.L > B.cp[b].H.L; });
     for (int p : order) {
         for (int b = 0; b < B.shape[p].climbs; ++b) *up++ = make_int2(p, b);
+        for (int b = 0; b < B.shape[p].sweeps; ++b) *sw++ = make_int2(p, b);
         for (int b = 0; b < B.shape[p].items; ++b) *nr++ = make_int2(p, b);
         for (int b = 0; b < B.sblk[p]; ++b) *sp++ = make_int4(p, b, B.sblk[p], 0);
     }
@@ -1693,6 +1699,7 @@ int batch_rebuild(DmBatchSolver &B) {
     B.dcp = reinterpret_cast<const DmChainProblem *>(B.blob + o_cp);
     B.dlp = reinterpret_cast<const DmLanczosProblem *>(B.blob + o_lp);
     B.dup = reinterpret_cast<const int2 *>(B.blob + o_up);
+    B.dsw = reinterpret_cast<const int2 *>(B.blob + o_sw);
     B.dnr = reinterpret_cast<const int2 *>(B.blob + o_nr);
     B.dst = reinterpret_cast<const int4 *>(B.blob + o_st);
     B.dss = reinterpret_cast<const DmStart *>(B.blob + o_ss);
@@ -1876,7 +1883,6 @@ int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t re
         B->jh.push_back(0);
         B->first.push_back(0);
         B->every.push_back(1);
-        B->since.push_back(0);
         B->state.push_back(kFree);
         B->sblk.push_back(1);
         B->shm.push_back(0);
@@ -1898,7 +1904,6 @@ int dm_batch_add(DmBatchSolver *B, dm_handle h, int k, void *tag, cudaEvent_t re
     B->jh[slot] = 0;
     B->first[slot] = (5 * k + 3) / 4 + 5;
     B->every[slot] = h->cfg.check_every > 0 ? h->cfg.check_every : 1;
-    B->since[slot] = 0;
     B->tag[slot] = tag;
     B->shape[slot] = dm_batch_shape(H, h->near_mode);
     B->shm[slot] = dm_step_batch_smem(Lz.m_max);
@@ -1946,7 +1951,8 @@ int dm_batch_step(DmBatchSolver *B, std::vector<DmBatchDone> &done) {
             B->starting.clear();
             B->n_start = 0;
         }
-        DM_CUDA(dm_hmatvec_batch(B->dcp, B->dup, B->n_up, B->smem_up, B->dnr, B->n_nr, B->smem_nr, B->djv, st));
+        DM_CUDA(dm_hmatvec_batch(B->dcp, B->dup, B->n_up, B->smem_up, B->dsw, B->n_sw, B->smem_sw, B->dnr, B->n_nr,
+                                 B->smem_nr, B->djv, st));
         DM_CUDA(dm_lanczos_step_batch(B->dlp, B->dst, B->n_st, B->djv, B->darr, B->smem_step, st));
     }
     // the problems finished at the last call: their vectors come before this step
@@ -1955,6 +1961,7 @@ int dm_batch_step(DmBatchSolver *B, std::vector<DmBatchDone> &done) {
     B->par ^= 1;
     // the previous step's check has been computed while this step was queued: read it
     DM_CHECK(batch_collect(*B));
+    ++B->gstep;
     // checks due after this step
     std::vector<int> due;
     int m_hi = 0, k_hi = 1;
@@ -1962,11 +1969,11 @@ int dm_batch_step(DmBatchSolver *B, std::vector<DmBatchDone> &done) {
     for (int p : B->act) {
         if (B->state[p] != kStepping) continue;
         const int m = ++B->jh[p];
-        ++B->since[p];
         const bool at_cap = m >= B->cap[p];
-        if ((m >= B->first[p] && B->since[p] >= B->every[p]) || at_cap) {
+        // checks on the solver's own step count modulo check_every, so that problems joining
+        // at different steps are checked in the same launches (fewer Ritz launches per step)
+        if ((m >= B->first[p] && B->gstep % B->every[p] == 0) || at_cap) {
             due.push_back(p);
-            B->since[p] = 0;
             m_hi = m > m_hi ? m : m_hi;
             k_hi = B->k[p] > k_hi ? B->k[p] : k_hi;
         }

@@ -341,18 +341,20 @@ struct DmChainProblem {
     float *y;        // output
     int permuted, near_mode, near_rows, climb_smem, chain_smem;
 };
-// y = K~ x for many problems in two launches: map_up[block] = {problem, leaf} (leaf N2S, the
-// climb, and the top-down sweep of each tree's internal levels), then map_near[block] =
-// {problem, near item} (near rows and the leaf S2N). Per problem: dm_batch_shape's climbs and
-// items; shared memory the largest of the problems'. jv[p] selects problem p's input
-// x + jv[p] xstep. In DmChainProblem, near_rows = item_rows.
+// y = K~ x for many problems in three launches: map_up[block] = {problem, leaf} (leaf N2S and
+// the climb), map_sweep[block] = {problem, subtree} (the top-down sweep of each tree's
+// internal levels), then map_near[block] = {problem, near item} (near rows and the leaf S2N).
+// Per problem: dm_batch_shape's climbs, sweeps and items; shared memory the largest of the
+// problems'. jv[p] selects problem p's input x + jv[p] xstep. In DmChainProblem, near_rows =
+// item_rows.
 struct DmBatchShape {
-    int climbs, items, item_rows, climb_smem;
-    size_t smem_up, smem_near;
+    int climbs, sweeps, items, item_rows, climb_smem;
+    size_t smem_up, smem_sweep, smem_near;
 };
 DmBatchShape dm_batch_shape(const DmHmat &H, int near_mode);
 cudaError_t dm_hmatvec_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem_up,
-                             const int2 *map_near, int n_near, size_t smem_near, const int *jv, cudaStream_t st);
+                             const int2 *map_sweep, int n_sweep, size_t smem_sweep, const int2 *map_near, int n_near,
+                             size_t smem_near, const int *jv, cudaStream_t st);
 cudaError_t dm_hmatvec_chain(const DmHmat &H, int near_mode, const float *x, float *y, bool permuted,
                              cudaStream_t st);
 int dm_near_item_rows(int near_mode, int leaf_max);

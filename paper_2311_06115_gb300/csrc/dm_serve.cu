@@ -144,6 +144,10 @@ bool run_job(Job *j, cudaStream_t stream, int *status) {
     const int k = j->req.k;
     int st = dm_create(j->points.data(), j->req.N, j->req.d, j->req.eps, j->req.alpha, &cfg, &h);
     if (st == DM_OK) st = dm_compress(h, j->req.tol, j->req.leaf_size, j->req.max_rank);
+    {
+        std::lock_guard<std::mutex> lk(g_srv.mu);
+        j->res.built_ms = g_srv.now_ms();
+    }
     if (st == DM_OK && j->req.block_size < 2) {
         cudaEvent_t ready = nullptr;
         st = dm_batch_prepare(h, &ready);

@@ -159,17 +159,56 @@ __device__ __forceinline__ void gemv_rows_smem(const float *Ps, int ld4, int s, 
     }
 }
 
-// Top-down S2N over the internal levels 2..L-1 of one tree, by the block that completed the
-// root: in level order, u_node += P_parent(:, node's columns)^T u_parent, in place, so that
-// every internal node's u becomes its total incoming far-field vector (level 1: u itself);
-// the leaves' totals are formed by their near items. A warp per node, lanes over its rank.
-__device__ __forceinline__ void sweep_down(const DmHmat &H) {
+// Top-down S2N of the internal levels, in the batched form (sweep_batch_kernel): after the
+// climb every node's u holds its S2S part; its total incoming far-field vector is
+// t_node = u_node + P_parent(:, node's columns)^T t_parent (level 1: u itself). A block owns
+// the subtree under one node q of level lq: it forms t_q along q's ancestor chain in shared
+// memory (reading the ancestors' u, writing none of them), stores t_q over u_q, then the
+// levels below q down to L-1 in place, a warp per node. The leaves' totals are formed by
+// their near items.
+__device__ __forceinline__ void sweep_subtree(const DmHmat &H, int q, int lq, float *ta, float *tb, float *part) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int R = H.max_rank;
-    for (int lvl = 2; lvl < H.L; ++lvl) {
-        const int first = (1 << lvl) - 1, count = 1 << lvl;
-        for (int q = warp; q < count; q += kHWarps) {
-            const int nd = first + q, par = (nd - 1) >> 1;
+    const int R = H.max_rank, RH4 = (H.rank_hi + 3) & ~3;
+    {
+        const int a1 = ((q + 1) >> (lq - 1)) - 1;  // q's ancestor at level 1
+        for (int j = threadIdx.x; j < H.ranks[a1]; j += blockDim.x) ta[j] = __ldcg(H.uhat + (size_t)a1 * R + j);
+        __syncthreads();
+    }
+    // the chain, levels 2..lq: two halves of the parent's rank over the two halves of the block
+    const int half = threadIdx.x >> 7, jj = threadIdx.x & 127;
+    for (int lvl = 2; lvl <= lq; ++lvl) {
+        const int v = ((q + 1) >> (lq - lvl)) - 1, par = (v - 1) >> 1;
+        const int sc = H.ranks[v], sp = H.ranks[par];
+        const int off = (v == 2 * par + 2) ? H.ranks[2 * par + 1] : 0;
+        const float *Pn = H.P + (size_t)par * R * H.ldp + off;
+        const int th = (sp + 1) >> 1, t0 = half * th, t1 = min(sp, t0 + th);
+        for (int j = jj; j < sc; j += 128) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int t = t0;
+            for (; t + 4 <= t1; t += 4) {
+                a0 = fmaf(__ldg(Pn + (size_t)t * H.ldp + j), ta[t], a0);
+                a1 = fmaf(__ldg(Pn + (size_t)(t + 1) * H.ldp + j), ta[t + 1], a1);
+                a2 = fmaf(__ldg(Pn + (size_t)(t + 2) * H.ldp + j), ta[t + 2], a2);
+                a3 = fmaf(__ldg(Pn + (size_t)(t + 3) * H.ldp + j), ta[t + 3], a3);
+            }
+            for (; t < t1; ++t) a0 = fmaf(__ldg(Pn + (size_t)t * H.ldp + j), ta[t], a0);
+            part[half * RH4 + j] = (a0 + a1) + (a2 + a3);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < sc; j += blockDim.x)
+            tb[j] = __ldcg(H.uhat + (size_t)v * R + j) + (part[j] + part[RH4 + j]);
+        __syncthreads();
+        float *tmp = ta;
+        ta = tb;
+        tb = tmp;
+    }
+    for (int j = threadIdx.x; j < H.ranks[q]; j += blockDim.x) __stcg(H.uhat + (size_t)q * R + j, ta[j]);
+    __syncthreads();
+    // the subtree's internal levels below q
+    for (int lvl = lq + 1; lvl < H.L; ++lvl) {
+        const int first = ((q + 1) << (lvl - lq)) - 1, count = 1 << (lvl - lq);
+        for (int i = warp; i < count; i += kHWarps) {
+            const int nd = first + i, par = (nd - 1) >> 1;
             const int sc = H.ranks[nd], sp = H.ranks[par];
             const int off = (nd == 2 * par + 2) ? H.ranks[2 * par + 1] : 0;
             const float *Pn = H.P + (size_t)par * R * H.ldp + off;
@@ -195,11 +234,10 @@ __device__ __forceinline__ void sweep_down(const DmHmat &H) {
 // The climb by last arrival (see the file header) from `node`, whose weights this block has
 // written: count the arrival at the parent; the second block to arrive owns the parent, runs
 // the pair's S2S and the parent's N2S, and climbs on. With `owned`, the block already owns
-// node's parent (both children written before this launch) and skips the first arrival. With
-// `sweep`, the block that completes the root then runs sweep_down. sw: shared memory for the
-// children's weights, followed by the parent's operands when climb_smem.
-__device__ __forceinline__ void climb_loop(const DmHmat &H, int node, int climb_smem, bool sweep, bool owned,
-                                           float *sw) {
+// node's parent (both children written before this launch) and skips the first arrival.
+// sw: shared memory for the children's weights, followed by the parent's operands when
+// climb_smem.
+__device__ __forceinline__ void climb_loop(const DmHmat &H, int node, int climb_smem, bool owned, float *sw) {
     __shared__ int s_go;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int RH = H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
@@ -275,13 +313,7 @@ __device__ __forceinline__ void climb_loop(const DmHmat &H, int node, int climb_
                 H.uhat[(size_t)r * H.max_rank + b2] = acc;
             }
         }
-        if (node == 0) {
-            if (sweep) {
-                __syncthreads();
-                sweep_down(H);
-            }
-            return;
-        }
+        if (node == 0) return;
         // N2S of the internal node
         if (climb_smem) gemv_rows_smem(Ps, C4, sp, c, sw, H.what + (size_t)node * H.max_rank);
         else
@@ -293,7 +325,7 @@ __device__ __forceinline__ void climb_loop(const DmHmat &H, int node, int climb_
 
 // Leaf N2S of leaf `leaf`, then the climb from it
 __device__ __forceinline__ void climb_body(const DmHmat &H, int leaf, const float *__restrict__ x, int permuted,
-                                           int climb_smem, bool sweep) {
+                                           int climb_smem) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const int nleaves = 1 << H.L;
@@ -307,7 +339,7 @@ __device__ __forceinline__ void climb_body(const DmHmat &H, int leaf, const floa
     __syncthreads();
     gemv_leaf(H.P + (size_t)node * H.max_rank * H.ldp, H.ldp, H.ranks[node], m, sx, H.what + (size_t)node * H.max_rank);
     if (H.L == 0) return;
-    climb_loop(H, node, climb_smem, sweep, false, sm + m4max);
+    climb_loop(H, node, climb_smem, false, sm + m4max);
 }
 
 // body of the chained form's first launch for one problem: block `bid` of its grid (leaf climbs
@@ -320,7 +352,7 @@ __device__ __forceinline__ void near_up_body(const DmHmat &H, int bid, const flo
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m4max = (H.leaf_max + 3) & ~3;
     if (bid < nleaves) {
-        climb_body(H, bid, x, permuted, climb_smem, false);
+        climb_body(H, bid, x, permuted, climb_smem);
         return;
     }
 
@@ -546,10 +578,10 @@ __global__ void __launch_bounds__(kDownThreads) down_kernel(const __grid_constan
     down_body(H, (int)blockIdx.x, y, permuted, chain_in_smem);
 }
 
-// ---- batched form (many problems, two launches) --------------------------------------------
-//  up_batch_kernel        map[block] = {problem, leaf}: leaf N2S and the climb by last arrival;
-//                         the block that completes a root sweeps that tree's internal levels
-//                         top-down (sweep_down).
+// ---- batched form (many problems, three launches) ------------------------------------------
+//  up_batch_kernel        map[block] = {problem, leaf}: leaf N2S and the climb by last arrival.
+//  sweep_batch_kernel     map[block] = {problem, subtree}: the internal levels' totals top-down
+//                         (sweep_subtree), 2^min(L-1, 4) blocks per tree of depth L >= 3.
 //  near_s2n_batch_kernel  map[block] = {problem, item}, item = (leaf, chunk of item_rows rows):
 //                         the near rows (cached blocks streamed, or recomputed) into shared
 //                         memory, then the leaf's total incoming vector
@@ -562,7 +594,21 @@ __global__ void __launch_bounds__(kHThreads) up_batch_kernel(const DmChainProble
                                                              const int *__restrict__ jv) {
     const int2 pb = map[blockIdx.x];
     const DmChainProblem &p = P[pb.x];
-    climb_body(p.H, pb.y, p.x + (size_t)jv[pb.x] * p.xstep, p.permuted, p.climb_smem, true);
+    climb_body(p.H, pb.y, p.x + (size_t)jv[pb.x] * p.xstep, p.permuted, p.climb_smem);
+}
+
+// the top-down sweep, map[block] = {problem, s}: the block owns the subtree under node
+// 2^lq - 1 + s of level lq = min(L - 1, kSweepCut) (trees of depth L >= 3)
+constexpr int kSweepCut = 4;
+__global__ void __launch_bounds__(kHThreads) sweep_batch_kernel(const DmChainProblem *__restrict__ P,
+                                                                const int2 *__restrict__ map) {
+    extern __shared__ float4 smem4[];
+    const int2 pb = map[blockIdx.x];
+    const DmHmat &H = P[pb.x].H;
+    const int lq = H.L - 1 < kSweepCut ? H.L - 1 : kSweepCut;
+    const int RH4 = (H.rank_hi + 3) & ~3;
+    float *ta = reinterpret_cast<float *>(smem4), *tb = ta + RH4, *part = tb + RH4;
+    sweep_subtree(H, (1 << lq) - 1 + pb.y, lq, ta, tb, part);
 }
 
 struct BatchItem {
@@ -784,6 +830,7 @@ DmBatchShape dm_batch_shape(const DmHmat &H, int near_mode) {
     c.item_rows = dm_near_item_rows(near_mode, H.leaf_max);
     c.items = nleaves * ((H.leaf_max + c.item_rows - 1) / c.item_rows);
     c.climbs = H.L > 0 ? nleaves : 0;
+    c.sweeps = H.L >= 3 ? 1 << (H.L - 1 < kSweepCut ? H.L - 1 : kSweepCut) : 0;
     const int m4max = (H.leaf_max + 3) & ~3;
     const size_t RH = (size_t)H.rank_hi, RH4 = (RH + 3) & ~3, C4 = (2 * RH + 3) & ~3;
     const size_t climb_bytes = sizeof(float) * (RH * RH4 + RH * C4);
@@ -791,15 +838,23 @@ DmBatchShape dm_batch_shape(const DmHmat &H, int near_mode) {
     c.smem_up = sizeof(float) * ((size_t)m4max + C4) + (c.climb_smem ? climb_bytes : 0);
     c.smem_near = sizeof(float) * ((size_t)m4max + (size_t)((c.item_rows + 3) & ~3) + 6 * RH4);
     if (near_mode != DM_NEAR_CACHED) c.smem_near += sizeof(float) * (size_t)H.leaf_max * H.d;
+    c.smem_sweep = sizeof(float) * 4 * RH4;
     return c;
 }
 
 cudaError_t dm_hmatvec_batch(const DmChainProblem *P, const int2 *map_up, int n_up, size_t smem_up,
-                             const int2 *map_near, int n_near, size_t smem_near, const int *jv, cudaStream_t st) {
+                             const int2 *map_sweep, int n_sweep, size_t smem_sweep, const int2 *map_near, int n_near,
+                             size_t smem_near, const int *jv, cudaStream_t st) {
     cudaError_t e;
     if (n_up > 0) {
         if ((e = dm_allow_smem((const void *)up_batch_kernel, smem_up)) != cudaSuccess) return e;
         up_batch_kernel<<<n_up, kHThreads, smem_up, st>>>(P, map_up, jv);
+        dm_count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (n_sweep > 0) {
+        if ((e = dm_allow_smem((const void *)sweep_batch_kernel, smem_sweep)) != cudaSuccess) return e;
+        sweep_batch_kernel<<<n_sweep, kHThreads, smem_sweep, st>>>(P, map_sweep);
         dm_count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -87,11 +87,11 @@ def test_batch_launches_per_step_do_not_grow_with_count(dm, clouds):
         for h in hs:
             dm.dm_destroy(h)
         # shared by all clouds: start vectors (3 launches per joining group) and Ritz vectors (6
-        # per finishing group); per step: 2 (H-matvec) + 3 (Gram-Schmidt) launches, one more at
+        # per finishing group); per step: 3 (H-matvec) + 3 (Gram-Schmidt) launches, one more at
         # each check. Neither grows with the number of clouds.
         per_step = (launches - 9 * len(sub)) / steps
         counts[len(sub)] = per_step
-        assert per_step <= 6.0, (len(sub), launches, steps)
+        assert per_step <= 7.0, (len(sub), launches, steps)
     print("launches per step:", counts)
 
 
