@@ -264,7 +264,9 @@ int dm_selftest_wait_timeout(int32_t blocks, int32_t missing, int64_t spin_limit
  * and are admitted first-fit, in arrival order, whenever a slot is free and the request's
  * device footprint (dm_request_bytes) fits in what is left of the HBM budget (a request
  * larger than the whole budget runs alone). A built single-vector request (block_size 0 or
- * 1) then joins the batched eigensolver of dm_eigs_batch, run by one thread of the server:
+ * 1) then joins a batched eigensolver of dm_eigs_batch, run by a thread of the server (four,
+ * by request size: up to 5,000, 15,000, 40,000 points and beyond, the smaller on
+ * higher-priority streams, so that small requests are not held to large ones' step time):
  * every resident request's Lanczos step runs in the same launches, each at its own step, and
  * a request leaves (its results copied out, its memory released) when its own check says it
  * converged; requests join between steps (continuous batching at the step level). Block

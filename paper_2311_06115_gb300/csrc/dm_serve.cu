@@ -1,10 +1,10 @@
 // dm_serve.cu -- request server: independent diffusion-map solves admitted as slots and
 // device memory free up. Each slot builds a request's kernel and compression (dm_create,
 // dm_compress) on its own CUDA stream, so that concurrently running builds overlap on the GPU;
-// single-vector eigensolves then join one batched solver, whose thread advances every resident
-// request's Lanczos iteration in the same launches, each request at its own step, and finishes
-// each one when its own convergence check says so (continuous batching at step level). Block
-// Lanczos requests run their eigensolve on their slot.
+// single-vector eigensolves then join a batched solver (one per size class), whose thread
+// advances every resident request's Lanczos iteration in the same launches, each request at
+// its own step, and finishes each one when its own convergence check says so (continuous
+// batching at step level). Block Lanczos requests run their eigensolve on their slot.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -23,6 +23,16 @@ int dm_lanczos_kmax();
 namespace {
 
 inline uint64_t r256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+
+// solver lanes by request size: lane l takes requests of at most kLaneN[l] points (the last
+// lane the rest); lower lanes run on higher-priority streams
+constexpr int kLanes = 4;
+constexpr int64_t kLaneN[kLanes - 1] = {5000, 15000, 40000};
+inline int lane_of(int64_t N) {
+    int l = 0;
+    while (l < kLanes - 1 && N > kLaneN[l]) ++l;
+    return l;
+}
 
 enum JobState { kQueued = 0, kRunning = 1, kDone = 2 };
 
@@ -57,13 +67,17 @@ struct Server {
     std::deque<Job *> queue;
     std::map<dm_ticket, std::unique_ptr<Job>> jobs;
     std::vector<std::thread> workers;
-    // the batched eigensolver: its thread, its stream and the requests handed to it
-    std::thread solver;
-    std::condition_variable cv_solver;
-    std::deque<Handoff> handoff;
+    // batched eigensolvers, one per size class (lane_of), so that small requests are not held
+    // to the step time of large ones: each with its thread and the requests handed to it
+    struct Lane {
+        std::thread th;
+        std::condition_variable cv;
+        std::deque<Handoff> handoff;
+    };
+    Lane lanes[kLanes];
     bool workers_done = false;
-    // slot streams, then the solver's stream and its result stream; destroyed after every
-    // thread has ended (the slots' allocations are freed on their streams, possibly by the
+    // slot streams, then each lane's solver stream and result stream; destroyed after every
+    // thread has ended (the slots' allocations are freed on their streams, possibly by a
     // solver's thread)
     std::vector<cudaStream_t> streams;
     std::chrono::steady_clock::time_point t0;
@@ -152,11 +166,12 @@ bool run_job(Job *j, cudaStream_t stream, int *status) {
         cudaEvent_t ready = nullptr;
         st = dm_batch_prepare(h, &ready);
         if (st == DM_OK) {
+            Server::Lane &ln = g_srv.lanes[lane_of(j->req.N)];
             {
                 std::lock_guard<std::mutex> lk(g_srv.mu);
-                g_srv.handoff.push_back(Handoff{j, h, ready});
+                ln.handoff.push_back(Handoff{j, h, ready});
             }
-            g_srv.cv_solver.notify_one();
+            ln.cv.notify_one();
             return false;
         }
         if (ready) cudaEventDestroy(ready);
@@ -207,8 +222,9 @@ void worker_main(cudaStream_t stream) {
 // the batched eigensolver: takes handed-over requests between steps, advances every resident
 // one by a step, and finishes those whose check decided (results copied to the host, handle
 // destroyed, memory released); ends when the slots have ended and nothing is resident
-void solver_main(cudaStream_t stream, cudaStream_t out) {
+void solver_main(int lane, cudaStream_t stream, cudaStream_t out) {
     cudaSetDevice(g_srv.device);
+    Server::Lane &ln = g_srv.lanes[lane];
     std::unique_ptr<DmBatchSolver, void (*)(DmBatchSolver *)> B(dm_batch_create(g_srv.device, stream),
                                                                 dm_batch_destroy);
     std::vector<std::pair<Job *, dm_handle>> resident;
@@ -222,10 +238,10 @@ void solver_main(cudaStream_t stream, cudaStream_t out) {
         std::deque<Handoff> in;
         {
             std::unique_lock<std::mutex> lk(g_srv.mu);
-            g_srv.cv_solver.wait(lk, [&] {
-                return !g_srv.handoff.empty() || dm_batch_active(B.get()) > 0 || g_srv.workers_done;
+            ln.cv.wait(lk, [&] {
+                return !ln.handoff.empty() || dm_batch_active(B.get()) > 0 || g_srv.workers_done;
             });
-            in.swap(g_srv.handoff);
+            in.swap(ln.handoff);
             if (in.empty() && dm_batch_active(B.get()) == 0 && g_srv.workers_done) break;
         }
         for (Handoff &x : in) {
@@ -351,9 +367,18 @@ int dm_serve_start(const dm_serve_config *cfg) {
         cudaGetLastError();
         return dm_fail_msg(DM_ECUDA, "cannot select the CUDA device");
     }
-    for (int i = 0; i < slots + 2; ++i) {
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    cudaGetLastError();
+    for (int i = 0; i < slots + 2 * kLanes; ++i) {
         cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        // solver streams (slots + 2 l) by lane: the smallest requests' lane at the highest priority
+        int prio = prio_lo;
+        if (i >= slots && (i - slots) % 2 == 0) {
+            const int l = (i - slots) / 2;
+            prio = prio_hi + (prio_lo - prio_hi) * l / (kLanes - 1);  // numerically lower = higher
+        }
+        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio) != cudaSuccess) {
             cudaGetLastError();
             for (cudaStream_t q : g_srv.streams) cudaStreamDestroy(q);
             g_srv.streams.clear();
@@ -362,7 +387,9 @@ int dm_serve_start(const dm_serve_config *cfg) {
         g_srv.streams.push_back(s);
     }
     for (int i = 0; i < slots; ++i) g_srv.workers.emplace_back(worker_main, g_srv.streams[(size_t)i]);
-    g_srv.solver = std::thread(solver_main, g_srv.streams[(size_t)slots], g_srv.streams[(size_t)slots + 1]);
+    for (int l = 0; l < kLanes; ++l)
+        g_srv.lanes[l].th = std::thread(solver_main, l, g_srv.streams[(size_t)(slots + 2 * l)],
+                                        g_srv.streams[(size_t)(slots + 2 * l + 1)]);
     g_srv.running = true;
     return DM_OK;
 }
@@ -390,8 +417,10 @@ int dm_serve_stop(void) {
         std::lock_guard<std::mutex> lk(g_srv.mu);
         g_srv.workers_done = true;
     }
-    g_srv.cv_solver.notify_all();
-    if (g_srv.solver.joinable()) g_srv.solver.join();
+    for (auto &l : g_srv.lanes) {
+        l.cv.notify_all();
+        if (l.th.joinable()) l.th.join();
+    }
     for (cudaStream_t s : g_srv.streams) cudaStreamDestroy(s);
     g_srv.streams.clear();
     std::lock_guard<std::mutex> lk(g_srv.mu);
