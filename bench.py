@@ -48,12 +48,13 @@ ORACLE_FULL_S = 10.0
 REFERENCE_BUDGET_S = 330.0
 
 
-def reference_sample_n(steps: int) -> int:
+def reference_sample_n(steps: int, full_s: float = ORACLE_FULL_S) -> int:
     """Points per timed oracle step of the reference arm: the full workload when the timed
-    steps fit the budget at full size (30 steps do), else fewer (time grows as n^2 through
-    the degree passes)."""
+    steps fit the budget at full size (full_s: the predicted seconds of one full-size step;
+    30 steps of about 9 s fit on the GPU machine's 16 host cores), else fewer (time grows as n^2
+    through the degree passes)."""
     per_step = REFERENCE_BUDGET_S / max(1, steps)
-    n = int(WORKLOAD["N"] * min(1.0, math.sqrt(per_step / ORACLE_FULL_S)))
+    n = int(WORKLOAD["N"] * min(1.0, math.sqrt(per_step / max(full_s, 1e-3))))
     return max(10_000, n // 1000 * 1000)
 
 
@@ -670,11 +671,13 @@ def run_reference(args) -> int:
     import oracle
 
     oracle.build()
-    n_sample = reference_sample_n(args.steps)
     # warm-up steps (untimed) run the same pipeline on 10,000 points: the host code has no
-    # state to warm beyond its first pass, and full-size warm-ups would only lengthen the run
-    for _ in range(args.warmup):
-        oracle_sample(10_000)
+    # state to warm beyond its first pass, and full-size warm-ups would only lengthen the run.
+    # The last one's phase times scaled to the workload predict a full-size step on these cores.
+    full_s = ORACLE_FULL_S
+    for _ in range(max(1, args.warmup)):
+        full_s = oracle_sample(10_000)["extrapolated_s"]
+    n_sample = reference_sample_n(args.steps, full_s)
     runs = [oracle_sample(n_sample) for _ in range(args.steps)]
     vals = [r["value"] for r in runs]
     value = statistics.median(vals)
