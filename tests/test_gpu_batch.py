@@ -95,6 +95,38 @@ def test_batch_launches_per_step_do_not_grow_with_count(dm, clouds):
     print("launches per step:", counts)
 
 
+def test_batch_mixed_schedules_and_basis_caps(dm, clouds):
+    """Handles with their own check_every, and some whose basis cap (m_max) is reached before
+    they converge: those leave the step list at the cap and report DM_ENOCONV with the Ritz
+    pairs of the full basis, exactly as their solo solve does; the others converge as alone."""
+    k = 6
+    capped = {1, 4}
+    hs = []
+    for i, c in enumerate(clouds):
+        H = c["H"]
+        cfg = dm.dm_config_default(seed=i, check_every=1 + (i % 3), m_max=12 if i in capped else 300)
+        h = dm.dm_create(c["X"], eps=c["eps"], cfg=cfg)
+        dm.dm_load_hmatrix(h, H.L, H.max_rank, H.perm, H.ranks, H.skel, H.P.astype(np.float32))
+        hs.append(h)
+    ev, vecs, status = dm.dm_eigs_batch(hs, k)
+    for i, h in enumerate(hs):
+        st = dm.dm_get_stats(h)
+        if i in capped:
+            assert status[i] == dm.DM_ENOCONV and st["lanczos_iters"] == 12, (i, status[i], st["lanczos_iters"])
+        else:
+            assert status[i] == dm.DM_OK, i
+        evs, Vs, conv = dm.dm_eigs(h, k)
+        assert conv == (i not in capped)
+        if i in capped:
+            # the same 12-step basis: the same Ritz values up to the summation order
+            np.testing.assert_allclose(ev[i], evs, rtol=1e-5, atol=1e-7)
+        else:
+            np.testing.assert_allclose(ev[i], evs, rtol=2e-5, atol=2e-7)
+        V = vecs[i].astype(np.float64)
+        np.testing.assert_allclose(V.T @ V, np.eye(k), atol=2e-5)
+        dm.dm_destroy(h)
+
+
 def test_batch_argument_errors(dm, clouds):
     hs = _handles(dm, clouds[:2])
     lib = dm.load()
