@@ -140,9 +140,9 @@ int dm_eigs(dm_handle h, int32_t k, double *evals, float *evecs);
  * clouds (no paper counterpart; each handle's solve is dm_eigs' single-vector Lanczos of
  * Algorithm 2 in its symmetric form, Section 2.3.1). Every Lanczos step of every handle not
  * yet converged runs in the same launches, each handle at its own step: the H-matvec of
- * Eq. 2.18 in two launches for all handles (leaf N2S and the climb up each tree, whose root
- * block then sweeps the tree's internal levels top-down; then the near field fused with the
- * leaf S2N), and the three Gram-Schmidt passes. The start vectors of the handles, and the
+ * Eq. 2.18 in three launches for all handles (leaf N2S and the climb up each tree; the
+ * top-down sweep of the trees' internal levels, split over subtrees; the near field fused
+ * with the leaf S2N), and the three Gram-Schmidt passes. The start vectors of the handles, and the
  * Ritz vectors of the handles finishing at the same step, are formed in shared launches too.
  * Each handle is checked on its own schedule (from step ceil(5k/4)+5, every check_every
  * steps); the checks due after a step share one launch of Ritz values, read by the host one
