@@ -1376,8 +1376,15 @@ int dm_compress(dm_handle h, double tol, int32_t leaf_size, int32_t max_rank) {
         }
         w.sel = sel;
         w.icnt = icnt;
+        // at high dimension the distance sums read an FP64 copy of the points (freed with the
+        // workspace)
+        double *X64 = nullptr;
+        if (h->d >= kWideMinD) {
+            DM_CHECK(h->alloc(&X64, (size_t)h->N * h->d, G_WORK, ts));
+            DM_CUDA(dm_launch_widen(h->X, h->N * h->d, X64, ts));
+        }
         int32_t *perm = nullptr;
-        DM_CUDA(dm_tree_build(h->X, h->N, h->d, h->eps, L, pa, pb, &perm, &w, ts));
+        DM_CUDA(dm_tree_build(h->X, X64, h->N, h->d, h->eps, L, pa, pb, &perm, &w, ts));
         h->perm = perm;
         ms_tree = t.stop();  // the host waits for the tree only; the degree passes may still run
         h->free_group(G_WORK);

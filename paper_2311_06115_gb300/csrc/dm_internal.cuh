@@ -171,16 +171,36 @@ __device__ __forceinline__ float dm_ex2(float x) {
     return y;
 }
 
+// binary32 -> binary64 on the integer pipes (IEEE 754 formats: the exponent is rebiased by
+// 1023 - 127 = 896 and the 23 fraction bits move to the top of the 52): exact, so identical to
+// the conversion instruction, which runs on the FP64 pipe that bounds the distance sums below.
+// Zeros keep their sign; subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double dm_widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0xffu || (e == 0u && (u & 0x7fffffu) != 0u)) return (double)f;
+    const unsigned mag = e == 0u ? 0u : ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double((int)((u & 0x80000000u) | mag), (int)(u << 29));
+}
+__device__ __forceinline__ double dm_widen(double f) { return f; }
+
 // Squared distance of two FP32 points in FP64 without contraction, in the order
 // k = 0..d-1 (reproducible bit for bit on any IEEE machine).
-__device__ __forceinline__ double dm_sqdist64(const float *a, const float *b, int d) {
+// T = float, or double for points widened once beforehand (the same operations in the same
+// order either way)
+template <class T>
+__device__ __forceinline__ double dm_sqdist64(const T *a, const T *b, int d) {
     double r2 = 0.0;
     for (int k = 0; k < d; ++k) {
-        double t = __dsub_rn((double)a[k], (double)b[k]);
+        double t = __dsub_rn(dm_widen(a[k]), dm_widen(b[k]));
         r2 = __dadd_rn(r2, __dmul_rn(t, t));
     }
     return r2;
 }
+// dimension from which the tree build reads an FP64 copy of the points (its distance sums
+// stream each node's rows: at high dimension the FP64 copy's reads cost less than widening
+// every coordinate per pass; the sampled median pairs, which read rows at random, widen)
+constexpr int kWideMinD = 16;
 
 // ---------------------------------------------------------------------------
 // Device-side structure of a compressed operator (all pointers device memory).
@@ -242,6 +262,8 @@ __device__ __forceinline__ const float *dm_pt_row(const DmHmat &H, int leaf, int
 // k_degrees.cu
 cudaError_t dm_launch_pair_sqdist(const float *X, int64_t N, int d, uint64_t seed, double *out, int64_t m,
                                   cudaStream_t st);
+// out[0..n) = X[0..n) in FP64
+cudaError_t dm_launch_widen(const float *X, int64_t n, double *out, cudaStream_t st);
 size_t dm_select_state_bytes();
 // st2, fork, join (optional, all three or none): a second stream for the second order statistic
 cudaError_t dm_launch_select_median(double *vals, int64_t m, void *state, double *result, cudaStream_t st,
@@ -297,8 +319,9 @@ size_t dm_tree_item_bytes();
 size_t dm_tree_sel_bytes();
 int64_t dm_tree_big_node();  // nodes above this many points split over many CTAs
 size_t dm_tree_cand_bytes();
-cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, int32_t *perm_a, int32_t *perm_b,
-                          int32_t **perm_out, DmTreeWork *w, cudaStream_t st);
+// X64: NULL, or the FP64 copy of X, read instead of X
+cudaError_t dm_tree_build(const float *X, const double *X64, int64_t N, int d, double eps, int L, int32_t *perm_a,
+                          int32_t *perm_b, int32_t **perm_out, DmTreeWork *w, cudaStream_t st);
 
 // k_skel.cu
 struct DmSkelWork {

@@ -311,6 +311,8 @@ uint64_t dm_request_bytes(const dm_request *r) {
     uint64_t b = 0;
     // points, degrees and scalings
     b += 2 * r256(4 * N * d) + 5 * r256(8 * N) + 3 * r256(4 * N);
+    // the FP64 copy of the points held until the tree is built (high dimension)
+    if (r->d >= kWideMinD) b += r256(8 * N * d);
     // compressed structure
     b += r256(4 * nnodes) + r256(4 * nnodes * R) + r256(4 * nnodes * R * ldp) + r256(4 * N * d) + r256(4 * N);
     b += 2 * r256(4 * N) + r256(4 * nleaves * leaf_max * ldk) + r256(4 * (nleaves > 1 ? nleaves - 1 : 1) * R * R);

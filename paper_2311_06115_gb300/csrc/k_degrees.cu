@@ -561,14 +561,24 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 cudaError_t dm_launch_pair_sqdist(const float *X, int64_t N, int d, uint64_t seed, double *out, int64_t m,
                                   cudaStream_t st) {
     int64_t npairs = N * (N - 1) / 2;
-    if (npairs == m) {
-        all_pairs_kernel<<<blocks_for(N, 128), 128, 0, st>>>(X, N, d, out);
-        dm_count_launches(1);
-    } else {
-        sampled_pairs_kernel<<<blocks_for(m, 256), 256, 0, st>>>(X, N, d, dm_stream_key(seed, DM_TAG_PAIRS, 0),
-                                                                  out, m);
-        dm_count_launches(1);
-    }
+    const uint64_t key = dm_stream_key(seed, DM_TAG_PAIRS, 0);
+    if (npairs == m) all_pairs_kernel<<<blocks_for(N, 128), 128, 0, st>>>(X, N, d, out);
+    else sampled_pairs_kernel<<<blocks_for(m, 256), 256, 0, st>>>(X, N, d, key, out, m);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void widen_kernel(const float *__restrict__ X, int64_t n, double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)X[i];
+}
+}  // namespace
+
+cudaError_t dm_launch_widen(const float *X, int64_t n, double *out, cudaStream_t st) {
+    const int64_t b = (n + 255) / 256;
+    widen_kernel<<<(unsigned)(b < 8 * 152 ? (b > 0 ? b : 1) : 8 * 152), 256, 0, st>>>(X, n, out);
+    dm_count_launches(1);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,8 @@
 //   key_i = W_iq - W_ip; the ceil(n/2) smallest (key, index) go left; both
 //   children keep increasing original index.
 // All decisions are taken in FP64 with the same operation order as the oracle, so
-// both build the same tree. The O(n) FP64 passes of every level are cut into
+// both build the same tree (at high dimension from an FP64 copy of the points made once,
+// which saves the FP64 pipe two conversions per coordinate). The O(n) FP64 passes of every level are cut into
 // 512-point items spread over all SMs (FP64 is a narrow pipe on this GPU); the
 // exact median and the stable partition run one CTA per node on integer keys.
 #include <vector>
@@ -82,15 +83,16 @@ __device__ int item_source(const TreeItem &it, const TreeItem *items, const Cand
 
 // farthest point (largest FP64 squared distance) from the item's source; optionally
 // store W = exp(-r2/eps) per position for the key pass
+template <class T>
 __global__ void __launch_bounds__(kTreeThreads) farthest_kernel(const TreeItem *__restrict__ items,
-                                                               const float *__restrict__ X, int d,
+                                                               const T *__restrict__ X, int d,
                                                                const int32_t *__restrict__ perm,
                                                                const Cand *__restrict__ prev,
                                                                Cand *__restrict__ out, double *__restrict__ wbuf,
                                                                double eps) {
     const TreeItem it = items[blockIdx.x];
     const int src = item_source(it, items, prev, perm);
-    const float *xs = X + (int64_t)src * d;
+    const T *xs = X + (int64_t)src * d;
     Cand best;
     best.val = 0ull;
     best.idx = 0x7fffffff;
@@ -108,15 +110,16 @@ __global__ void __launch_bounds__(kTreeThreads) farthest_kernel(const TreeItem *
 }
 
 // key_i = W_iq - W_ip as order-preserving 64-bit integers
+template <class T>
 __global__ void __launch_bounds__(kTreeThreads) key_kernel(const TreeItem *__restrict__ items,
-                                                          const float *__restrict__ X, int d,
+                                                          const T *__restrict__ X, int d,
                                                           const int32_t *__restrict__ perm,
                                                           const Cand *__restrict__ candq,
                                                           const double *__restrict__ wbuf, double eps,
                                                           uint64_t *__restrict__ keys) {
     const TreeItem it = items[blockIdx.x];
     const int q = item_source(it, items, candq, perm);
-    const float *xq = X + (int64_t)q * d;
+    const T *xq = X + (int64_t)q * d;
     for (long long pos = it.lo + threadIdx.x; pos < it.hi; pos += blockDim.x) {
         const int i = perm[pos];
         const double r2 = dm_sqdist64(xq, X + (int64_t)i * d, d);
@@ -329,8 +332,8 @@ __global__ void __launch_bounds__(512) split_scatter_kernel(const TreeItem *__re
 
 }  // namespace
 
-cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, int32_t *perm_a, int32_t *perm_b,
-                          int32_t **perm_out, DmTreeWork *w, cudaStream_t st) {
+cudaError_t dm_tree_build(const float *X, const double *X64, int64_t N, int d, double eps, int L, int32_t *perm_a,
+                          int32_t *perm_b, int32_t **perm_out, DmTreeWork *w, cudaStream_t st) {
     // item lists of every level, built on the host from the (deterministic) node ranges
     std::vector<TreeItem> items;
     std::vector<int> level_first(L + 1, 0);
@@ -368,11 +371,16 @@ cudaError_t dm_tree_build(const float *X, int64_t N, int d, double eps, int L, i
     for (int lvl = 0; lvl < L; ++lvl) {
         const int f = level_first[lvl], n = level_first[lvl + 1] - level_first[lvl];
         const TreeItem *li = ditems + f;  // first_item fields are relative to this pointer
-        farthest_kernel<<<n, kTreeThreads, 0, st>>>(li, X, d, in, nullptr, c1, nullptr, eps);
-        dm_count_launches(1);
-        farthest_kernel<<<n, kTreeThreads, 0, st>>>(li, X, d, in, c1, c2, w->wbuf, eps);
-        dm_count_launches(1);
-        key_kernel<<<n, kTreeThreads, 0, st>>>(li, X, d, in, c2, w->wbuf, eps, w->keys);
+        if (X64) {
+            farthest_kernel<double><<<n, kTreeThreads, 0, st>>>(li, X64, d, in, nullptr, c1, nullptr, eps);
+            farthest_kernel<double><<<n, kTreeThreads, 0, st>>>(li, X64, d, in, c1, c2, w->wbuf, eps);
+            key_kernel<double><<<n, kTreeThreads, 0, st>>>(li, X64, d, in, c2, w->wbuf, eps, w->keys);
+        } else {
+            farthest_kernel<float><<<n, kTreeThreads, 0, st>>>(li, X, d, in, nullptr, c1, nullptr, eps);
+            farthest_kernel<float><<<n, kTreeThreads, 0, st>>>(li, X, d, in, c1, c2, w->wbuf, eps);
+            key_kernel<float><<<n, kTreeThreads, 0, st>>>(li, X, d, in, c2, w->wbuf, eps, w->keys);
+        }
+        dm_count_launches(2);
         dm_count_launches(1);
         int64_t s0, sz0;
         dm_node_range(N, (1 << lvl) - 1, &s0, &sz0);
