@@ -20,7 +20,13 @@
 // 16-byte loads in flight; each warp keeps its best remaining column, and every warp finds
 // the next pivot itself from those per-warp candidates,
 // so a step needs three block barriers. P_a = [I, R11^-1 R12] by back substitution.
+#include <cooperative_groups.h>
+
+#include <mutex>
+
 #include "dm_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -233,26 +239,29 @@ __device__ __forceinline__ float warp_allsum(float v) {
     return v;
 }
 
-// One pass over a batch of CB of the warp's columns (column j = warp + kSkelWarps (b CB + u)):
-// d_j = q^T a_j, a_j -= d_j q, R(k, j) = d_j, and the lane's running best (|a_j|, j) for the
-// next pivot (lowest index on ties). Lane holds float4 rows
+// One pass over a batch of CB of the warp's columns: stored column l = warp + kSkelWarps (b CB + u)
+// (l < cn) is candidate j = g0 + gs l (all candidates: g0 = 0, gs = 1; one CTA of a cluster:
+// its share g0 + gs l). d_j = q^T a_j, a_j -= d_j q, R(k, j) = d_j, and the lane's running best
+// (|a_j|, j) for the next pivot (lowest index on ties). Lane holds float4 rows
 // f = lane + 32 m, m < M, of each column (f < nf), as two packed FP32x2 halves. q = qv * inv,
 // recomputed from shared memory at each use (the same product every time).
 template <int M, int CB>
-__device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int c, int b, const float4 *qv, float inv,
-                                             const int *selpos, float &best_v, int &best_j, float *Rk) {
+__device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int cn, int g0, int gs, int b,
+                                             const float4 *qv, float inv, const int *selpos, float &best_v,
+                                             int &best_j, float *Rk) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int jb[CB];
+    int jl[CB], jb[CB];
     bool ok[CB];
 #pragma unroll
     for (int u = 0; u < CB; ++u) {
-        jb[u] = warp + kSkelWarps * (b * CB + u);
-        ok[u] = jb[u] < c && selpos[jb[u]] < 0;
+        jl[u] = warp + kSkelWarps * (b * CB + u);
+        jb[u] = g0 + gs * jl[u];
+        ok[u] = jl[u] < cn && selpos[jb[u]] < 0;
     }
     float4 v[CB][M];
 #pragma unroll
     for (int u = 0; u < CB; ++u) {
-        const float4 *col = reinterpret_cast<const float4 *>(At + (size_t)jb[u] * ldr);
+        const float4 *col = reinterpret_cast<const float4 *>(At + (size_t)jl[u] * ldr);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int f = lane + 32 * m;
@@ -291,7 +300,7 @@ __device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int c, 
             const float2 nd = make_float2(-dj[u], -dj[u]);
             const float2 wa = __ffma2_rn(nd, qa, make_float2(v[u][m].x, v[u][m].y));
             const float2 wb = __ffma2_rn(nd, qb, make_float2(v[u][m].z, v[u][m].w));
-            reinterpret_cast<float4 *>(At + (size_t)jb[u] * ldr)[f] = make_float4(wa.x, wa.y, wb.x, wb.y);
+            reinterpret_cast<float4 *>(At + (size_t)jl[u] * ldr)[f] = make_float4(wa.x, wa.y, wb.x, wb.y);
             sp2[u] = __ffma2_rn(wa, wa, sp2[u]);
             sp2[u] = __ffma2_rn(wb, wb, sp2[u]);
         }
@@ -329,6 +338,63 @@ __device__ __forceinline__ void warp_argmax(float &v, int &j) {
             j = oj;
         }
     }
+}
+
+// P = [I, R11^-1 R12] in candidate order (rows t < rank of the node's slot), the node's
+// skeleton and rank, from R (max_rank x cmax, global) and the pivot order; every thread of
+// the CTA calls it. xs: `extra` floats of shared memory no longer in use.
+__device__ void skel_write_p(const SkelArgs &a, int node, int c, int rank, const int *selpos, const int *piv,
+                             const int *C, const float *R, float *xs, size_t extra) {
+    float *Pn = a.P + (size_t)node * a.max_rank * a.ldp;
+    const int ldas = (c + 3) & ~3;
+    if ((size_t)rank * ldas + (size_t)rank * rank <= extra) {
+        // in shared memory (A and Q are dead): Rs = R(0:rank, :) and a compact copy
+        // R11[t][u] = R(t, piv[u]); each unselected column is solved in place, in the same
+        // operation order as the global-memory form below; then coalesced row stores with the
+        // identity columns
+        float *Rs = xs, *R11 = xs + (size_t)rank * ldas;
+        for (int e = threadIdx.x; e < rank * ldas; e += blockDim.x) {
+            const int t = e / ldas, j = e - t * ldas;
+            Rs[e] = j < c ? R[(size_t)t * a.cmax + j] : 0.f;
+        }
+        for (int e = threadIdx.x; e < rank * rank; e += blockDim.x) {
+            const int t = e / rank, u = e - t * rank;
+            R11[e] = R[(size_t)t * a.cmax + piv[u]];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+            if (selpos[j] >= 0) continue;
+            for (int t = rank - 1; t >= 0; --t) {
+                const float *r11 = R11 + (size_t)t * rank;
+                float v = Rs[(size_t)t * ldas + j];
+                for (int u = t + 1; u < rank; ++u) v = fmaf(-r11[u], Rs[(size_t)u * ldas + j], v);
+                Rs[(size_t)t * ldas + j] = v / r11[t];
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rank * c; e += blockDim.x) {
+            const int t = e / c, j = e - t * c;
+            const int sp_ = selpos[j];
+            Pn[(size_t)t * a.ldp + j] = sp_ >= 0 ? (t == sp_ ? 1.f : 0.f) : Rs[(size_t)t * ldas + j];
+        }
+    } else for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        const int sp_ = selpos[j];
+        if (sp_ >= 0) {
+            for (int t = 0; t < rank; ++t) Pn[(size_t)t * a.ldp + j] = (t == sp_) ? 1.f : 0.f;
+        } else {
+            for (int t = rank - 1; t >= 0; --t) {
+                float v = R[(size_t)t * a.cmax + j];
+                for (int u = t + 1; u < rank; ++u) v = fmaf(-R[(size_t)t * a.cmax + piv[u]], Pn[(size_t)u * a.ldp + j], v);
+                Pn[(size_t)t * a.ldp + j] = v / R[(size_t)t * a.cmax + piv[t]];
+            }
+        }
+    }
+    // zero the row padding so vectorised readers may overrun c up to ldp
+    for (int t = 0; t < rank; ++t)
+        for (int j = c + threadIdx.x; j < a.ldp; j += blockDim.x) Pn[(size_t)t * a.ldp + j] = 0.f;
+    for (int t = threadIdx.x; t < a.max_rank; t += blockDim.x)
+        a.skel[(int64_t)node * a.max_rank + t] = t < rank ? C[piv[t]] : -1;
+    if (threadIdx.x == 0) a.ranks[node] = rank;
 }
 
 template <int M, int CB>
@@ -553,10 +619,10 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
         int cj = 0x7fffffff;
         if (a_sm) {
             for (int b = 0; b < nb; ++b)
-                column_batch<M, CB>(xs, ldr, nf, c, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
+                column_batch<M, CB>(xs, ldr, nf, c, 0, 1, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
         } else {
             for (int b = 0; b < nb; ++b)
-                column_batch<M, CB>(Ag, ldr, nf, c, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
+                column_batch<M, CB>(Ag, ldr, nf, c, 0, 1, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
         }
         warp_argmax(cv, cj);
         if (lane == 0) {
@@ -568,57 +634,268 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     }
     __syncthreads();
 
-    // ---- P = [I, R11^-1 R12] in candidate order; rows t < rank of the node's slot
-    float *Pn = a.P + (size_t)node * a.max_rank * a.ldp;
-    const int ldas = (c + 3) & ~3;
-    if ((size_t)rank * ldas + (size_t)rank * rank <= extra) {
-        // in shared memory (A and Q are dead): Rs = R(0:rank, :) and a compact copy
-        // R11[t][u] = R(t, piv[u]); each unselected column is solved in place, in the same
-        // operation order as the global-memory form below; then coalesced row stores with the
-        // identity columns
-        float *Rs = xs, *R11 = xs + (size_t)rank * ldas;
-        for (int e = threadIdx.x; e < rank * ldas; e += blockDim.x) {
-            const int t = e / ldas, j = e - t * ldas;
-            Rs[e] = j < c ? R[(size_t)t * a.cmax + j] : 0.f;
-        }
-        for (int e = threadIdx.x; e < rank * rank; e += blockDim.x) {
-            const int t = e / rank, u = e - t * rank;
-            R11[e] = R[(size_t)t * a.cmax + piv[u]];
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < c; j += blockDim.x) {
-            if (selpos[j] >= 0) continue;
-            for (int t = rank - 1; t >= 0; --t) {
-                const float *r11 = R11 + (size_t)t * rank;
-                float v = Rs[(size_t)t * ldas + j];
-                for (int u = t + 1; u < rank; ++u) v = fmaf(-r11[u], Rs[(size_t)u * ldas + j], v);
-                Rs[(size_t)t * ldas + j] = v / r11[t];
-            }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < rank * c; e += blockDim.x) {
-            const int t = e / c, j = e - t * c;
-            const int sp_ = selpos[j];
-            Pn[(size_t)t * a.ldp + j] = sp_ >= 0 ? (t == sp_ ? 1.f : 0.f) : Rs[(size_t)t * ldas + j];
-        }
-    } else for (int j = threadIdx.x; j < c; j += blockDim.x) {
-        const int sp_ = selpos[j];
-        if (sp_ >= 0) {
-            for (int t = 0; t < rank; ++t) Pn[(size_t)t * a.ldp + j] = (t == sp_) ? 1.f : 0.f;
-        } else {
-            for (int t = rank - 1; t >= 0; --t) {
-                float v = R[(size_t)t * a.cmax + j];
-                for (int u = t + 1; u < rank; ++u) v = fmaf(-R[(size_t)t * a.cmax + piv[u]], Pn[(size_t)u * a.ldp + j], v);
-                Pn[(size_t)t * a.ldp + j] = v / R[(size_t)t * a.cmax + piv[t]];
-            }
+    skel_write_p(a, node, c, rank, selpos, piv, C, R, xs, extra);
+}
+
+// ---- Clustered form, for sampled blocks larger than one CTA's shared memory.
+// A cluster of G CTAs per node (G = the cluster size) splits the candidates: CTA g keeps the
+// columns j = g + G l, l < ceil(c / G), of the sampled block in its own shared memory, so the
+// column passes stay on the SM, and its own copy of the leading rows of Q (rows past qcap in
+// the node's global Q slot, written by CTA 0). A pivot step: every warp's best remaining
+// column is published in its CTA's shared memory; one cluster barrier; every warp reads the
+// G x 16 candidates and takes the same pivot (largest norm, lowest index on ties); the pivot
+// column is copied from its owner's shared memory; each CTA re-orthogonalises it against its
+// own Q copy and forms q_k with the same operations in the same order as the others (the same
+// q_k everywhere, without a second exchange), then updates its own columns. The owner of the
+// pivot records R(:, p); CTA 0 forms P after a final cluster barrier. Every CTA of a cluster
+// takes the same decisions from the same data, so all reach every cluster barrier.
+template <int M, int CB>
+__global__ void __launch_bounds__(kSkelThreads, 1) skel_cluster_kernel(SkelArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int G = (int)cl.num_blocks();
+    const int g = (int)cl.block_rank();
+    extern __shared__ float4 smem4[];
+    float4 *qv4 = smem4;                                 // ldr / 4: the pivot column, then v
+    float4 *ccrd = qv4 + (a.ldr >> 2);                   // cmax: candidate coordinates (d <= 3) and s
+    float *xr = reinterpret_cast<float *>(ccrd + a.cmax); // 4 x ldr: row x, y, z, s (d <= 3)
+    float *coef = xr + 4 * a.ldr;                        // max_rank
+    int *C = reinterpret_cast<int *>(coef + a.max_rank); // cmax
+    int *Rw = C + a.cmax;                                // rmax
+    int *selpos = Rw + a.rmax;                           // cmax
+    int *piv = selpos + a.cmax;                          // max_rank
+    __shared__ float wred[kSkelWarps];
+    __shared__ float wbest_v[2][kSkelWarps];  // per step parity: each warp's best column (read cluster-wide)
+    __shared__ int wbest_j[2][kSkelWarps];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nl = (int)blockIdx.x / G;  // node within the level
+    const int node = (1 << a.level) - 1 + nl;
+    int64_t st, sz;
+    dm_node_range(a.N, node, &st, &sz);
+    float *R = a.R + (size_t)nl * a.max_rank * a.cmax;
+    float *Q = a.Q + (size_t)nl * a.max_rank * a.ldr;
+
+    int c;
+    if (a.level == a.L) {
+        c = (int)sz;
+        for (int j = threadIdx.x; j < c; j += blockDim.x) C[j] = (int)(st + j);
+    } else {
+        const int l = 2 * node + 1, r = 2 * node + 2;
+        const int sl = a.ranks[l], sr = a.ranks[r];
+        c = sl + sr;
+        for (int j = threadIdx.x; j < c; j += blockDim.x)
+            C[j] = j < sl ? a.skel[(int64_t)l * a.max_rank + j] : a.skel[(int64_t)r * a.max_rank + (j - sl)];
+    }
+    const int64_t off = a.N - sz;
+    const int rtarget = 2 * a.max_rank + 10;
+    const int r = (int)(off <= rtarget ? off : rtarget);
+    const uint64_t key = dm_stream_key(a.seed, DM_TAG_ROWS, (uint64_t)node);
+    const bool small_d = a.d <= 3;
+    for (int t = threadIdx.x; t < r; t += blockDim.x) {
+        int64_t u = (off <= rtarget) ? (int64_t)t : (int64_t)dm_below(dm_rng(key, (uint64_t)t), (uint64_t)off);
+        const int pos = (int)(u < st ? u : u + sz);
+        Rw[t] = pos;
+        if (small_d) {
+            for (int k = 0; k < 3; ++k) xr[k * a.ldr + t] = k < a.d ? a.Xp[(int64_t)pos * a.d + k] : 0.f;
+            xr[3 * a.ldr + t] = a.sp[pos];
         }
     }
-    // zero the row padding so vectorised readers may overrun c up to ldp
-    for (int t = 0; t < rank; ++t)
-        for (int j = c + threadIdx.x; j < a.ldp; j += blockDim.x) Pn[(size_t)t * a.ldp + j] = 0.f;
-    for (int t = threadIdx.x; t < a.max_rank; t += blockDim.x)
-        a.skel[(int64_t)node * a.max_rank + t] = t < rank ? C[piv[t]] : -1;
-    if (threadIdx.x == 0) a.ranks[node] = rank;
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        selpos[j] = -1;
+        if (small_d && !a.prefilled) {
+            const int64_t cj = C[j];
+            float4 v = make_float4(0.f, 0.f, 0.f, a.sp[cj]);
+            if (a.d > 0) v.x = a.Xp[cj * a.d];
+            if (a.d > 1) v.y = a.Xp[cj * a.d + 1];
+            if (a.d > 2) v.z = a.Xp[cj * a.d + 2];
+            ccrd[j] = v;
+        }
+    }
+    // this CTA's columns; the share size (and so qcap) is the same in every CTA of the cluster
+    const int cn = c > g ? (c - g + G - 1) / G : 0;
+    const int cshare = (c + G - 1) / G;
+    const int nf = (r + 3) >> 2;
+    const int ldr = a.ldr;
+    const float *Ag = a.A + (size_t)nl * a.cmax * ldr;
+    const size_t extra = a.smem_extra > 0 ? (size_t)a.smem_extra / sizeof(float) : 0;
+    float *xs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem4) + a.smem_base);
+    float *At = xs;  // the host sizes the launch so that the share always fits
+    float *Qs = xs + (size_t)cshare * ldr;
+    int qcap = (int)((extra - (size_t)cshare * ldr) / (size_t)ldr);
+    if (qcap > a.max_rank) qcap = a.max_rank;
+    __syncthreads();
+
+    // ---- this CTA's columns of the sampled block and their norms (warp per column)
+    float best_v = -1.f;
+    int best_j = 0x7fffffff;
+    for (int jl = warp; jl < cn; jl += kSkelWarps) {
+        const int j = g + G * jl;
+        float4 *col = reinterpret_cast<float4 *>(At + (size_t)jl * ldr);
+        float ss = 0.f;
+        if (a.prefilled) {
+            const float4 *src = reinterpret_cast<const float4 *>(Ag + (size_t)j * ldr);
+            for (int f = lane; f < nf; f += 32) {
+                const float4 v = src[f];
+                col[f] = v;
+                ss += dot4(v, v);
+            }
+        } else {
+            const int64_t cj = C[j];
+            float sj = 0.f, cx[3] = {0.f, 0.f, 0.f};
+            if (small_d) {
+                const float4 cc = ccrd[j];
+                cx[0] = cc.x;
+                cx[1] = cc.y;
+                cx[2] = cc.z;
+                sj = cc.w;
+            }
+            for (int f = lane; f < nf; f += 32) {
+                float v[4];
+                if (small_d) {
+                    const float4 rx = reinterpret_cast<const float4 *>(xr)[f];
+                    const float4 ry = reinterpret_cast<const float4 *>(xr + ldr)[f];
+                    const float4 rz = reinterpret_cast<const float4 *>(xr + 2 * ldr)[f];
+                    const float4 rs = reinterpret_cast<const float4 *>(xr + 3 * ldr)[f];
+                    const float px[4] = {rx.x, rx.y, rx.z, rx.w}, py[4] = {ry.x, ry.y, ry.z, ry.w},
+                                pz[4] = {rz.x, rz.y, rz.z, rz.w}, ps[4] = {rs.x, rs.y, rs.z, rs.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float t0 = cx[0] - px[u], t1 = cx[1] - py[u], t2 = cx[2] - pz[u];
+                        v[u] = (4 * f + u < r) ? ps[u] * sj * dm_ex2(-fmaf(t0, t0, fmaf(t1, t1, t2 * t2))) : 0.f;
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = (4 * f + u < r) ? kentry(a.Xp, a.sp, a.d, Rw[4 * f + u], cj) : 0.f;
+                }
+                const float4 w = make_float4(v[0], v[1], v[2], v[3]);
+                col[f] = w;
+                ss += dot4(w, w);
+            }
+        }
+        ss = warp_allsum(ss);
+        const float nv = sqrtf(ss);
+        if (nv > best_v || (nv == best_v && j < best_j)) {
+            best_v = nv;
+            best_j = j;
+        }
+    }
+    if (lane == 0) {
+        wbest_v[0][warp] = best_v;
+        wbest_j[0][warp] = best_j;
+    }
+
+    int kmax = a.max_rank;
+    if (kmax > c) kmax = c;
+    if (kmax > r) kmax = r;
+    const int nw = (nf + 31) >> 5;  // warps that own the pivot column's float4 rows
+    const int nb = (((cn + kSkelWarps - 1) / kSkelWarps) + CB - 1) / CB;  // column batches per warp
+    int rank = 0;
+    float nrm0 = 0.f;
+    for (int k = 0; k < kmax; ++k) {
+        // candidates of step k published in slot k & 1 of every CTA (the barrier also orders
+        // this CTA's previous column pass before the reuse of qv4 below)
+        cl.sync();
+        float bv = -1.f;
+        int bi = 0x7fffffff;
+        for (int e = lane; e < G * kSkelWarps; e += 32) {
+            const int rr = e / kSkelWarps, w = e - rr * kSkelWarps;
+            const float v = *cl.map_shared_rank(&wbest_v[k & 1][w], rr);
+            const int j = *cl.map_shared_rank(&wbest_j[k & 1][w], rr);
+            if (v > bv || (v == bv && j < bi)) {
+                bv = v;
+                bi = j;
+            }
+        }
+        warp_argmax(bv, bi);
+        if (k == 0) nrm0 = bv;
+        if (!(bv > a.tol * nrm0) || bv <= 0.f) break;
+        const int p = bi, owner = p % G;
+        // the pivot column from its owner's share (no CTA writes a selected column again)
+        {
+            const float4 *src =
+                reinterpret_cast<const float4 *>(cl.map_shared_rank(At + (size_t)(p / G) * ldr, owner));
+            for (int f = threadIdx.x; f < nf; f += blockDim.x) qv4[f] = src[f];
+        }
+        __syncthreads();
+        float4 ap[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int f = lane + 32 * m;
+            ap[m] = f < nf ? qv4[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int t = warp; t < k; t += kSkelWarps) {
+            const float4 *qt = t < qcap ? reinterpret_cast<const float4 *>(Qs + (size_t)t * ldr)
+                                        : reinterpret_cast<const float4 *>(Q + (size_t)t * ldr);
+            float d = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const int f = lane + 32 * m;
+                if (f < nf) d += dot4(qt[f], ap[m]);
+            }
+            d = warp_allsum(d);
+            if (lane == 0) coef[t] = d;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            selpos[p] = k;
+            piv[k] = p;
+        }
+        if (g == owner)
+            for (int t = threadIdx.x; t < k; t += blockDim.x) atomicAdd(R + (size_t)t * a.cmax + p, coef[t]);
+        if (warp < nw) {
+            const int f = warp * 32 + lane;
+            float4 v = ap[0];
+#pragma unroll
+            for (int m = 1; m < M; ++m)
+                if (warp == m) v = ap[m];
+            float ss = 0.f;
+            if (f < nf) {
+                auto sub = [&](const float4 qt, float ct) {
+                    v.x = fmaf(-ct, qt.x, v.x);
+                    v.y = fmaf(-ct, qt.y, v.y);
+                    v.z = fmaf(-ct, qt.z, v.z);
+                    v.w = fmaf(-ct, qt.w, v.w);
+                };
+                const int kq = k < qcap ? k : qcap;
+                for (int t = 0; t < kq; ++t) sub(reinterpret_cast<const float4 *>(Qs + (size_t)t * ldr)[f], coef[t]);
+                for (int t = kq; t < k; ++t) sub(reinterpret_cast<const float4 *>(Q + (size_t)t * ldr)[f], coef[t]);
+                qv4[f] = v;
+                ss = dot4(v, v);
+            }
+            ss = warp_allsum(ss);
+            if (lane == 0) wred[warp] = ss;
+        }
+        __syncthreads();
+        float ssv = 0.f;
+        for (int w = 0; w < nw; ++w) ssv += wred[w];
+        const float qn = sqrtf(ssv);
+        const float inv = 1.f / qn;
+        if (g == owner && threadIdx.x == 0) R[(size_t)k * a.cmax + p] = qn;
+        if (warp < nw) {
+            const int f = warp * 32 + lane;
+            if (f < nf) {
+                const float4 q = scale4(qv4[f], inv);
+                if (k < qcap) reinterpret_cast<float4 *>(Qs + (size_t)k * ldr)[f] = q;
+                else if (g == 0) reinterpret_cast<float4 *>(Q + (size_t)k * ldr)[f] = q;
+            }
+        }
+        // ---- this CTA's remaining columns
+        float cv = -1.f;
+        int cj = 0x7fffffff;
+        for (int b = 0; b < nb; ++b)
+            column_batch<M, CB>(At, ldr, nf, cn, g, G, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
+        warp_argmax(cv, cj);
+        if (lane == 0) {
+            wbest_v[(k + 1) & 1][warp] = cv;
+            wbest_j[(k + 1) & 1][warp] = cj;
+        }
+        rank = k + 1;
+    }
+    // R complete in global memory, and no CTA reads another's shared memory after this barrier
+    __threadfence();
+    cl.sync();
+    if (g != 0) return;
+    skel_write_p(a, node, c, rank, selpos, piv, C, R, xs, extra);
 }
 
 // ---- near blocks K(I_a, I_a), row-major with leading dimension ldk, zero padded (d <= 3: the
@@ -749,6 +1026,56 @@ cudaError_t launch_fill(int cols, dim3 grid, const SkelArgs &a, int mode, float 
     return cudaErrorInvalidValue;
 }
 
+// The clustered ID runs an internal level whose sampled blocks may not fit one CTA's shared
+// memory when its clusters fit one wave (nodes x G <= SMs): a cluster holds G SMs for the
+// whole level, so it only pays where one CTA per node would leave SMs idle; the leaf level
+// (many nodes, two CTAs per SM streaming their blocks through L2) keeps one CTA per node.
+constexpr int kSkelClusterMaxG = 8;       // portable cluster size
+constexpr int kSkelClusterMinQRows = 64;  // fewest Q rows a CTA keeps in shared memory (else all)
+
+template <int M, int CB>
+cudaError_t launch_skel_cluster(const SkelArgs &a, unsigned nodes, int G, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nodes * (unsigned)G);
+    cfg.blockDim = dim3(kSkelThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)G;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, skel_cluster_kernel<M, CB>, a);
+}
+
+// whether clusters of G CTAs of `kern` with `smem` bytes each can be resident (cached per G
+// and shared-memory size; one device per process in practice)
+bool skel_cluster_ok(const void *kern, int G, size_t smem) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void *, int>, std::pair<size_t, int>>> seen;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &e : seen)
+        if (e.first.first == kern && e.first.second == G && e.second.first == smem) return e.second.second != 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(kSkelThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)G;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const int ok = cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0;
+    cudaGetLastError();
+    seen.push_back({{kern, G}, {smem, ok}});
+    return ok != 0;
+}
+
 }  // namespace
 
 size_t dm_skel_smem_bytes(int cmax, int rmax, int max_rank) {
@@ -813,6 +1140,17 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
     size_t smem_leaf = half > (size_t)reserved + fa.sharedSizeBytes ? (half - reserved - fa.sharedSizeBytes) & ~(size_t)15 : 0;
     if (smem_leaf > smem_int) smem_leaf = smem_int;
     if (smem_leaf < (size_t)a.smem_base) smem_leaf = smem;
+    // the clustered form: its whole opt-in shared memory per CTA
+    const void *ckern = wide ? (const void *)skel_cluster_kernel<5, 2> : (const void *)skel_cluster_kernel<3, 3>;
+    cudaFuncAttributes fc;
+    if ((e = cudaFuncGetAttributes(&fc, ckern)) != cudaSuccess) return e;
+    const size_t smem_cl = ((size_t)optin > fc.sharedSizeBytes ? (size_t)optin - fc.sharedSizeBytes : 0) & ~(size_t)15;
+    const bool cl_usable = smem_cl > (size_t)a.smem_base && dm_allow_smem(ckern, smem_cl) == cudaSuccess;
+    cudaGetLastError();
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t colb = sizeof(float) * (size_t)w->ldr;  // one stored column of the block, one row of Q
+    const int leaf_pts = (int)((N + (1ll << L) - 1) >> L);
     for (int lvl = L; lvl >= 1; --lvl) {
         a.level = lvl;
         if (a.prefilled) {
@@ -824,11 +1162,35 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
         // internal levels (few candidates per node, at most one CTA per SM) take the whole
         // shared memory, which holds the sampled block and Q
         const size_t lsm = lvl < L ? smem_int : smem_leaf;
-        a.smem_extra = lsm > (size_t)a.smem_base ? (int)(lsm - (size_t)a.smem_base) : 0;
-        if (wide) skel_level_kernel<5, 2><<<1 << lvl, kSkelThreads, lsm, st>>>(a);
-        else skel_level_kernel<3, 3><<<1 << lvl, kSkelThreads, lsm, st>>>(a);
+        // candidates per node at this level: at most a leaf's points, or two children's ranks
+        const int cb = lvl == L ? leaf_pts : (cmax < 2 * max_rank ? cmax : 2 * max_rank);
+        int G = 0;
+        if (cl_usable && lvl < L && (size_t)cb * colb > lsm - (size_t)a.smem_base) {
+            // the smallest one-wave cluster whose CTAs hold their share of the block and every
+            // row of Q, else the smallest that holds kSkelClusterMinQRows of them
+            const int kall = max_rank < cb ? max_rank : cb;
+            const int kmin = kall < kSkelClusterMinQRows ? kall : kSkelClusterMinQRows;
+            for (int pass = 0; pass < 2 && !G; ++pass) {
+                const int kq = pass == 0 ? kall : kmin;
+                for (int gg = 2; gg <= kSkelClusterMaxG && !G; gg *= 2) {
+                    const size_t need = (size_t)((cb + gg - 1) / gg) * colb + (size_t)kq * colb;
+                    if ((1ll << lvl) * gg <= nsm && need <= smem_cl - (size_t)a.smem_base &&
+                        skel_cluster_ok(ckern, gg, smem_cl))
+                        G = gg;
+                }
+            }
+        }
+        if (G) {
+            a.smem_extra = (int)(smem_cl - (size_t)a.smem_base);
+            e = wide ? launch_skel_cluster<5, 2>(a, 1u << lvl, G, smem_cl, st)
+                     : launch_skel_cluster<3, 3>(a, 1u << lvl, G, smem_cl, st);
+        } else {
+            a.smem_extra = lsm > (size_t)a.smem_base ? (int)(lsm - (size_t)a.smem_base) : 0;
+            if (wide) skel_level_kernel<5, 2><<<1 << lvl, kSkelThreads, lsm, st>>>(a);
+            else skel_level_kernel<3, 3><<<1 << lvl, kSkelThreads, lsm, st>>>(a);
+            e = cudaGetLastError();
+        }
         dm_count_launches(1);
-        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

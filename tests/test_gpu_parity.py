@@ -292,11 +292,14 @@ def test_gpu_compression_exact_at_full_rank(dm):
 
 
 @pytest.mark.parametrize("n,leaf,rank,tol,kind", [(2048, 128, 64, 1e-5, "scurve"), (3001, 200, 48, 1e-4, "scurve"),
-                                                  (2500, 160, 64, 1e-4, "mixture64"), (1800, 128, 64, 1e-4, "mnist")])
+                                                  (2500, 160, 64, 1e-4, "mixture64"), (1800, 128, 64, 1e-4, "mnist"),
+                                                  (6000, 256, 128, 1e-5, "scurve"), (3000, 256, 128, 1e-4, "mnist")])
 def test_gpu_compression_accuracy_and_structure(dm, n, leaf, rank, tol, kind):
     """GPU compression: valid structure and an error against the exact operator next to the
     oracle's own compression; the high-dimensional cases (d = 64, 784) build their sampled
-    blocks and near blocks with the coordinate-tiled entry kernel."""
+    blocks and near blocks with the coordinate-tiled entry kernel. At rank 128 the sampled
+    blocks (266 rows x up to 256 candidates) exceed one CTA's shared memory: those levels run
+    the clustered ID (the block split by columns over a cluster of CTAs)."""
     if kind == "scurve":
         X = _scurve(n, 4)
     elif kind == "mixture64":
