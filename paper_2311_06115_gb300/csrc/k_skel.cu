@@ -68,10 +68,11 @@ constexpr int kSkelMaxCand = 512;  // candidates per node (leaf points or two ch
 constexpr int kSkelMaxF4 = 5;      // float4 rows per lane in the column passes: r <= 640
 
 // ---- kernel entries of a block for d > 3, tiled over the coordinates ------------------
-// E[r][c] = s_row s_col 2^-|xs_row - xs_col|^2 for up to 32 rows (one CTA) and up to 32 QN
-// columns. Both point sets are staged through shared memory 32 coordinates at a time; each
-// thread owns 4 rows x QN columns (columns g + 32 q) of squared distances in registers,
-// summed over the coordinates in order exactly as kentry does.
+// E[r][c] = s_row s_col 2^-|xs_row - xs_col|^2 for up to 32 rows and 32 QN columns per CTA
+// (columns z 32 QN + [0, 32 QN) of the block for blockIdx.z = z, so that a level with few
+// nodes still fills the GPU). Both point sets are staged through shared memory 32
+// coordinates at a time; each thread owns 4 rows x QN columns (columns g + 32 q) of squared
+// distances in registers, summed over the coordinates in order exactly as kentry does.
 // Work item `mode`: 0 = the sampled block K(R, C) of node (2^level - 1 + blockIdx.x), rows
 // drawn exactly as in skel_level_kernel, into its A slot; 1 = the leaf block K(I_a, I_a) of
 // leaf blockIdx.x into its Knear slot (zero padded); 2 = the sibling block
@@ -81,7 +82,7 @@ constexpr int kFillRows = 32;
 constexpr int kFillK = 32;
 
 template <int QN>
-__global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode, float *__restrict__ Knear,
+__global__ void __launch_bounds__(256, QN <= 8 ? 4 : 1) fill_entries_kernel(SkelArgs a, int mode, float *__restrict__ Knear,
                                                            int leaf_max, int ldk) {
     constexpr int kCols = 32 * QN;
     extern __shared__ float fsm[];
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
     int64_t st, sz;
     dm_node_range(a.N, node, &st, &sz);
     const int t0 = blockIdx.y * kFillRows;
+    const int j0 = (int)blockIdx.z * kCols;  // first column of this CTA's tile
     if (tid == 0) {
         if (mode == 2) {
             s_r = a.ranks[2 * node + 1];
@@ -111,8 +113,12 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
         }
     }
     __syncthreads();
-    const int r = s_r, c = s_c;
-    if (c > kCols || (t0 >= r && !(mode == 1 && t0 < leaf_max))) return;  // the host sizes QN to the columns
+    const int r = s_r, c_all = s_c;
+    // the host sizes QN and the column tiles to the columns; the near blocks (mode 1) also
+    // write the zero padding of rows up to leaf_max and columns up to ldk
+    if (c_all > (int)gridDim.z * kCols || (t0 >= r && !(mode == 1 && t0 < leaf_max))) return;
+    if (mode != 1 && j0 >= c_all) return;
+    const int c = c_all - j0 < kCols ? (c_all - j0 > 0 ? c_all - j0 : 0) : kCols;  // this tile's columns
     // row and column positions
     if (tid < kFillRows) {
         const int t = t0 + tid;
@@ -132,7 +138,8 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
         }
         rowpos[tid] = pos;
     }
-    for (int j = tid; j < c; j += blockDim.x) {
+    for (int jt = tid; jt < c; jt += blockDim.x) {
+        const int j = j0 + jt;
         int pos;
         if (mode == 2) pos = a.skel[(int64_t)(2 * node + 2) * a.max_rank + j];
         else if (mode == 1 || a.level == a.L) pos = (int)(st + j);
@@ -140,10 +147,10 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
             const int l = 2 * node + 1, rr = 2 * node + 2, sl = a.ranks[l];
             pos = j < sl ? a.skel[(int64_t)l * a.max_rank + j] : a.skel[(int64_t)rr * a.max_rank + (j - sl)];
         }
-        colpos[j] = pos;
+        colpos[jt] = pos;
     }
     __syncthreads();
-    const int rg = tid & 7, cg = tid >> 3;  // rows 4 rg .. 4 rg + 3; columns cg + 32 q
+    const int rg = tid & 7, cg = tid >> 3;  // rows 4 rg .. 4 rg + 3; tile columns cg + 32 q
     float acc[4][QN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -188,8 +195,8 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
             const float si = a.sp[rowpos[4 * rg + i]];
 #pragma unroll
             for (int q = 0; q < QN; ++q) {
-                const int j = cg + 32 * q;
-                if (j < c) Bn[(size_t)t * c + j] = si * a.sp[colpos[j]] * dm_ex2(-acc[i][q]);
+                const int jt = cg + 32 * q;
+                if (jt < c) Bn[(size_t)t * c_all + j0 + jt] = si * a.sp[colpos[jt]] * dm_ex2(-acc[i][q]);
             }
         }
         return;
@@ -205,13 +212,13 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
             float *slot = a.A + (size_t)blockIdx.x * a.cmax * a.ldr;
 #pragma unroll
             for (int q = 0; q < QN; ++q) {
-                const int j = cg + 32 * q;
-                if (j >= c) continue;
-                const float sj = a.sp[colpos[j]];
+                const int jt = cg + 32 * q;
+                if (jt >= c) continue;
+                const float sj = a.sp[colpos[jt]];
                 float v[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) v[i] = rowpos[4 * rg + i] >= 0 ? si[i] * sj * dm_ex2(-acc[i][q]) : 0.f;
-                *reinterpret_cast<float4 *>(slot + (size_t)j * a.ldr + tq) = make_float4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<float4 *>(slot + (size_t)(j0 + jt) * a.ldr + tq) = make_float4(v[0], v[1], v[2], v[3]);
             }
         }
         return;
@@ -225,8 +232,8 @@ __global__ void __launch_bounds__(256) fill_entries_kernel(SkelArgs a, int mode,
         const float si = pos >= 0 ? a.sp[pos] : 0.f;
 #pragma unroll
         for (int q = 0; q < QN; ++q) {
-            const int j = cg + 32 * q;
-            if (j < ldk) out[j] = (pos >= 0 && j < c) ? si * a.sp[colpos[j]] * dm_ex2(-acc[i][q]) : 0.f;
+            const int jt = cg + 32 * q, j = j0 + jt;
+            if (j < ldk) out[j] = (pos >= 0 && jt < c) ? si * a.sp[colpos[jt]] * dm_ex2(-acc[i][q]) : 0.f;
         }
     }
 }
@@ -1017,13 +1024,25 @@ cudaError_t launch_fill_qn(dim3 grid, const SkelArgs &a, int mode, float *out, i
     return cudaGetLastError();
 }
 
-// the entry fill with the fewest column groups per thread that covers `cols` columns
+// grids (nodes x row tiles) below this many CTAs (two per SM) split their columns
+constexpr unsigned kFillMinCtas = 2 * 152;
+
+// The entry fill for blocks of up to `cols` columns: the fewest column groups per thread that
+// cover them in one tile; a small grid (the upper tree levels, where one CTA per row tile
+// would run its whole block alone on an SM) splits the columns into tiles of 64 (QN = 2,
+// blockIdx.z).
 cudaError_t launch_fill(int cols, dim3 grid, const SkelArgs &a, int mode, float *out, int leaf_max, int ldk,
                         cudaStream_t st) {
-    if (cols <= 128) return launch_fill_qn<4>(grid, a, mode, out, leaf_max, ldk, st);
-    if (cols <= 256) return launch_fill_qn<8>(grid, a, mode, out, leaf_max, ldk, st);
-    if (cols <= kSkelMaxCand) return launch_fill_qn<16>(grid, a, mode, out, leaf_max, ldk, st);
-    return cudaErrorInvalidValue;
+    if (cols > kSkelMaxCand || cols < 1) return cudaErrorInvalidValue;
+    int qn = cols <= 128 ? 4 : cols <= 256 ? 8 : 16;
+    if (grid.x * grid.y < kFillMinCtas) qn = 2;
+    grid.z = (unsigned)((cols + 32 * qn - 1) / (32 * qn));
+    switch (qn) {
+        case 2: return launch_fill_qn<2>(grid, a, mode, out, leaf_max, ldk, st);
+        case 4: return launch_fill_qn<4>(grid, a, mode, out, leaf_max, ldk, st);
+        case 8: return launch_fill_qn<8>(grid, a, mode, out, leaf_max, ldk, st);
+        default: return launch_fill_qn<16>(grid, a, mode, out, leaf_max, ldk, st);
+    }
 }
 
 // The clustered ID runs an internal level whose sampled blocks may not fit one CTA's shared
