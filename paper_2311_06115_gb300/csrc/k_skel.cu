@@ -1069,14 +1069,14 @@ cudaError_t launch_skel_cluster(const SkelArgs &a, unsigned nodes, int G, size_t
     return cudaLaunchKernelEx(&cfg, skel_cluster_kernel<M, CB>, a);
 }
 
-// whether clusters of G CTAs of `kern` with `smem` bytes each can be resident (cached per G
-// and shared-memory size; one device per process in practice)
-bool skel_cluster_ok(const void *kern, int G, size_t smem) {
+// how many clusters of G CTAs of `kern` with `smem` bytes each can be resident at once (0: none;
+// cached per kernel, G and shared-memory size; one device per process in practice)
+int skel_cluster_capacity(const void *kern, int G, size_t smem) {
     static std::mutex mu;
     static std::vector<std::pair<std::pair<const void *, int>, std::pair<size_t, int>>> seen;
     std::lock_guard<std::mutex> lk(mu);
     for (auto &e : seen)
-        if (e.first.first == kern && e.first.second == G && e.second.first == smem) return e.second.second != 0;
+        if (e.first.first == kern && e.first.second == G && e.second.first == smem) return e.second.second;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)G);
     cfg.blockDim = dim3(kSkelThreads);
@@ -1089,10 +1089,10 @@ bool skel_cluster_ok(const void *kern, int G, size_t smem) {
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     int n = 0;
-    const int ok = cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) n = 0;
     cudaGetLastError();
-    seen.push_back({{kern, G}, {smem, ok}});
-    return ok != 0;
+    seen.push_back({{kern, G}, {smem, n}});
+    return n;
 }
 
 }  // namespace
@@ -1185,8 +1185,9 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
         const int cb = lvl == L ? leaf_pts : (cmax < 2 * max_rank ? cmax : 2 * max_rank);
         int G = 0;
         if (cl_usable && lvl < L && (size_t)cb * colb > lsm - (size_t)a.smem_base) {
-            // the smallest one-wave cluster whose CTAs hold their share of the block and every
-            // row of Q, else the smallest that holds kSkelClusterMinQRows of them
+            // the smallest one-wave cluster (every cluster co-resident) whose CTAs hold their
+            // share of the block and every row of Q, else the smallest that holds
+            // kSkelClusterMinQRows of them
             const int kall = max_rank < cb ? max_rank : cb;
             const int kmin = kall < kSkelClusterMinQRows ? kall : kSkelClusterMinQRows;
             for (int pass = 0; pass < 2 && !G; ++pass) {
@@ -1194,7 +1195,7 @@ cudaError_t dm_skeletonize(const float *Xp, const float *sp, int64_t N, int d, i
                 for (int gg = 2; gg <= kSkelClusterMaxG && !G; gg *= 2) {
                     const size_t need = (size_t)((cb + gg - 1) / gg) * colb + (size_t)kq * colb;
                     if ((1ll << lvl) * gg <= nsm && need <= smem_cl - (size_t)a.smem_base &&
-                        skel_cluster_ok(ckern, gg, smem_cl))
+                        skel_cluster_capacity(ckern, gg, smem_cl) >= (1 << lvl))
                         G = gg;
                 }
             }
