@@ -253,9 +253,11 @@ __device__ __forceinline__ float warp_allsum(float v) {
 // f = lane + 32 m, m < M, of each column (f < nf), as two packed FP32x2 halves. q = qv * inv,
 // recomputed from shared memory at each use (the same product every time).
 template <int M, int CB>
-__device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int cn, int g0, int gs, int b,
-                                             const float4 *qv, float inv, const int *selpos, float &best_v,
+__device__ __forceinline__ void column_batch(float *At, int ncs, float *Ag, int ldr, int nf, int cn, int g0, int gs,
+                                             int b, const float4 *qv, float inv, const int *selpos, float &best_v,
                                              int &best_j, float *Rk) {
+    // stored column l lives at At + l ldr for l < ncs (shared memory), else at Ag + l ldr
+    auto colp = [&](int l) { return (l < ncs ? At : Ag) + (size_t)l * ldr; };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int jl[CB], jb[CB];
     bool ok[CB];
@@ -268,7 +270,7 @@ __device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int cn,
     float4 v[CB][M];
 #pragma unroll
     for (int u = 0; u < CB; ++u) {
-        const float4 *col = reinterpret_cast<const float4 *>(At + (size_t)jl[u] * ldr);
+        const float4 *col = reinterpret_cast<const float4 *>(colp(jl[u]));
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int f = lane + 32 * m;
@@ -307,7 +309,7 @@ __device__ __forceinline__ void column_batch(float *At, int ldr, int nf, int cn,
             const float2 nd = make_float2(-dj[u], -dj[u]);
             const float2 wa = __ffma2_rn(nd, qa, make_float2(v[u][m].x, v[u][m].y));
             const float2 wb = __ffma2_rn(nd, qb, make_float2(v[u][m].z, v[u][m].w));
-            reinterpret_cast<float4 *>(At + (size_t)jl[u] * ldr)[f] = make_float4(wa.x, wa.y, wb.x, wb.y);
+            reinterpret_cast<float4 *>(colp(jl[u]))[f] = make_float4(wa.x, wa.y, wb.x, wb.y);
             sp2[u] = __ffma2_rn(wa, wa, sp2[u]);
             sp2[u] = __ffma2_rn(wb, wb, sp2[u]);
         }
@@ -466,17 +468,23 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
         }
     }
     // the sampled block lives in shared memory when it fits (internal levels: few candidates),
-    // else in the CTA's global slot; rows of Q follow it in shared memory while they fit
+    // and rows of Q follow it there while they fit; a larger block keeps its leading columns
+    // in shared memory (after min(kmax, 32) rows of Q) and the rest in the CTA's global slot
     const int nf = (r + 3) >> 2;  // float4 rows per column
     const int ldr = a.ldr;
     float *Ag = a.A + (size_t)blockIdx.x * a.cmax * ldr;
     const size_t extra = a.smem_extra > 0 ? (size_t)a.smem_extra / sizeof(float) : 0;  // floats
     float *xs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem4) + a.smem_base);
-    const bool a_sm = (size_t)c * ldr <= extra;
-    float *At = a_sm ? xs : Ag;
-    float *Qs = xs + (a_sm ? (size_t)c * ldr : 0);
-    int qcap = (int)((extra - (a_sm ? (size_t)c * ldr : 0)) / (size_t)ldr);
+    int kmax = a.max_rank;
+    if (kmax > c) kmax = c;
+    if (kmax > r) kmax = r;
+    const int slots = (int)(extra / (size_t)ldr);  // columns or Q rows that fit in shared memory
+    const int qkeep = kmax < 32 ? kmax : 32;
+    const int ncs = c <= slots ? c : (slots > qkeep ? slots - qkeep : 0);
+    float *Qs = xs + (size_t)ncs * ldr;
+    int qcap = slots - ncs;
     if (qcap > a.max_rank) qcap = a.max_rank;
+    auto colp = [&](int j) { return (j < ncs ? xs : Ag) + (size_t)j * ldr; };
     auto qrow = [&](int t) -> float4 * {
         return reinterpret_cast<float4 *>(t < qcap ? Qs + (size_t)t * ldr : Q + (size_t)t * ldr);
     };
@@ -487,13 +495,13 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     float best_v = -1.f;
     int best_j = 0x7fffffff;
     for (int j = warp; j < c; j += kSkelWarps) {
-        float4 *col = reinterpret_cast<float4 *>(At + (size_t)j * ldr);
+        float4 *col = reinterpret_cast<float4 *>(colp(j));
         float ss = 0.f;
         if (a.prefilled) {
             const float4 *src = reinterpret_cast<const float4 *>(Ag + (size_t)j * ldr);
             for (int f = lane; f < nf; f += 32) {
                 const float4 v = src[f];
-                if (a_sm) col[f] = v;
+                if (j < ncs) col[f] = v;
                 ss += dot4(v, v);
             }
         } else {
@@ -543,9 +551,6 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
     }
     __syncthreads();
 
-    int kmax = a.max_rank;
-    if (kmax > c) kmax = c;
-    if (kmax > r) kmax = r;
     const int nw = (nf + 31) >> 5;  // warps that own the pivot column's float4 rows
     const int nb = (((c + kSkelWarps - 1) / kSkelWarps) + CB - 1) / CB;  // column batches per warp
     int rank = 0;
@@ -565,7 +570,7 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int f = lane + 32 * m;
-            ap[m] = f < nf ? reinterpret_cast<const float4 *>(At + (size_t)p * ldr)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+            ap[m] = f < nf ? reinterpret_cast<const float4 *>(colp(p))[f] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         for (int t = warp; t < k; t += kSkelWarps) {
             const float4 *qt = t < qcap ? reinterpret_cast<const float4 *>(Qs + (size_t)t * ldr)
@@ -624,13 +629,8 @@ __global__ void __launch_bounds__(kSkelThreads, 2) skel_level_kernel(SkelArgs a)
         // ---- every other remaining column: R(k, j) = q_k^T a_j, a_j -= R(k, j) q_k, |a_j|
         float cv = -1.f;
         int cj = 0x7fffffff;
-        if (a_sm) {
-            for (int b = 0; b < nb; ++b)
-                column_batch<M, CB>(xs, ldr, nf, c, 0, 1, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
-        } else {
-            for (int b = 0; b < nb; ++b)
-                column_batch<M, CB>(Ag, ldr, nf, c, 0, 1, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
-        }
+        for (int b = 0; b < nb; ++b)
+            column_batch<M, CB>(xs, ncs, Ag, ldr, nf, c, 0, 1, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
         warp_argmax(cv, cj);
         if (lane == 0) {
             wbest_v[warp] = cv;
@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(kSkelThreads, 1) skel_cluster_kernel(SkelArgs 
         float cv = -1.f;
         int cj = 0x7fffffff;
         for (int b = 0; b < nb; ++b)
-            column_batch<M, CB>(At, ldr, nf, cn, g, G, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
+            column_batch<M, CB>(At, cn, At, ldr, nf, cn, g, G, b, qv4, inv, selpos, cv, cj, R + (size_t)k * a.cmax);
         warp_argmax(cv, cj);
         if (lane == 0) {
             wbest_v[(k + 1) & 1][warp] = cv;
