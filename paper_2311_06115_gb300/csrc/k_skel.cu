@@ -10,8 +10,11 @@
 //
 // GPU design: one CTA per node of a level. The sampled block A = K(R_a, C_a) is stored
 // column-major (a candidate column is one contiguous vector of ldr >= r floats) in shared
-// memory when it fits (internal levels: at most two children's skeletons), else in a
-// per-CTA slot of global memory. Column-pivoted modified Gram-Schmidt with explicit
+// memory when it fits (internal levels: at most two children's skeletons), else its leading
+// columns there and the rest in a per-CTA slot of global memory; an internal level whose
+// blocks do not fit one CTA runs as a cluster of CTAs per node when the clusters fit one
+// wave (skel_cluster_kernel: the columns spread over the CTAs' shared memories, the same
+// operations in the same order per column). Column-pivoted modified Gram-Schmidt with explicit
 // residual updates (each step recomputes every remaining column norm from its updated
 // residual, so no norm downdating loses the small residuals that decide the rank) and one
 // re-orthogonalisation of the pivot column. A warp owns whole columns: one read-modify-
