@@ -293,6 +293,26 @@ def lanczos_hmat(X, eps: float, s, H: HStructure, k: int, m_max: int = 300, conv
     return ev, np.ascontiguousarray(V.T), int(it.value), int(st)
 
 
+def hmatvec_error_2norm(X, eps: float, s, H: HStructure, iters: int = 60, seed: int = 0) -> float:
+    """Estimate of ||S~ - S||_2 for the H-matrix H (Eq. 1.1's error in the operator 2-norm; also
+    the relative error, since ||S||_2 = lambda_1 = 1): power iteration on (S~ - S)^2 with the
+    exact S on the fly. The estimate |E v| / |v| of a unit iterate v is a lower bound that
+    rises towards the largest singular value of E = S~ - S."""
+    n = _pts(X).shape[0]
+    v = start_vector(n, seed)
+    v /= np.linalg.norm(v)
+    est = 0.0
+    for _ in range(iters):
+        ev = hmatvec(X, eps, s, H, v) - S_matvec(X, eps, s, v)
+        est = float(np.linalg.norm(ev))
+        w = hmatvec(X, eps, s, H, ev) - S_matvec(X, eps, s, ev)
+        nw = float(np.linalg.norm(w))
+        if nw == 0.0:
+            break
+        v = w / nw
+    return est
+
+
 def diffusion_coords(evals, phi, dg, t: int = 1) -> np.ndarray:
     """Diffusion coordinates after t steps of the walk (Algorithm 1, P^t and its
     eigendecomposition): P = Dg^-1 W^alpha = Dg^-1/2 S Dg^1/2, so P's right eigenvectors

@@ -346,6 +346,36 @@ def test_gpu_compression_accuracy_and_structure(dm, n, leaf, rank, tol, kind):
     assert err_gpu <= 1.02 * err_or + 1e-6, (err_gpu, err_or)
 
 
+@pytest.mark.parametrize("n,leaf,rank,tol", [(2048, 128, 64, 1e-5), (3000, 128, 128, 1e-5)])
+def test_gpu_compression_error_in_the_operator_2norm(dm, n, leaf, rank, tol):
+    """||S~_gpu - S||_2 (Eq. 1.1 in the operator 2-norm, relative since ||S||_2 = 1) by power
+    iteration on (S~_gpu - S)^2, next to the oracle's own compression's
+    oracle.hmatvec_error_2norm. Both products see the same FP32-representable vector each
+    iteration, so the GPU side adds only its FP32 arithmetic (~1e-7); pivot choices that
+    differ where residual norms tie within FP32 rounding move the error by far less than 5%.
+    The rank-128 case runs its internal levels on the clustered ID."""
+    X = _scurve(n, 7)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    h = dm.dm_create(X, eps=eps)
+    dm.dm_compress(h, tol, leaf, rank)
+    v = O.start_vector(n, 0)
+    v /= np.linalg.norm(v)
+    est_gpu = 0.0
+    for _ in range(60):
+        v32 = v.astype(np.float32)
+        e = dm.dm_matvec(h, v32).astype(np.float64) - O.S_matvec(X, eps, s, v32.astype(np.float64))
+        est_gpu = float(np.linalg.norm(e)) / float(np.linalg.norm(v32.astype(np.float64)))
+        e32 = e.astype(np.float32)
+        w = dm.dm_matvec(h, e32).astype(np.float64) - O.S_matvec(X, eps, s, e32.astype(np.float64))
+        v = w / np.linalg.norm(w)
+    dm.dm_destroy(h)
+    Ho = O.compress(X, eps, s, leaf, tol, rank)
+    est_or = O.hmatvec_error_2norm(X, eps, s, Ho, iters=60)
+    print(f"||S~ - S||_2: gpu {est_gpu:.3e} oracle {est_or:.3e} ratio {est_gpu / est_or:.3f}")
+    assert est_gpu <= 1.05 * est_or + 2e-6, (est_gpu, est_or)
+
+
 # ------------------------------------------------------------------ Lanczos
 
 def test_eigs_replayed_structure_match_oracle_lanczos(dm):

@@ -641,3 +641,29 @@ def test_id_sampled_rows_branch_matches_recomputed_draws(seed):
         np.testing.assert_allclose(Pn[node, :r, :len(C)], want, rtol=0, atol=1e-7 * max(1.0, np.abs(want).max()))
         compared += 1
     assert compared >= 10
+
+
+@pytest.mark.parametrize("n,leaf,rank,tol", [(400, 32, 16, 1e-3), (512, 64, 32, 1e-5)])
+def test_hmatvec_error_2norm_matches_svd_of_the_dense_difference(n, leaf, rank, tol):
+    """The power-iteration estimate of ||S~ - S||_2 (Eq. 1.1 in the operator 2-norm)
+    against the largest singular value of the assembled difference: S~ column by column from
+    the H-matvec of the identity, S from the dense kernel (Eq. W) and the scaling s; the
+    estimate is a lower bound that reaches it within 1e-3."""
+    X = _scurve(n, 3)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, leaf, tol, rank)
+    St = O.hmatvec(X, eps, s, H, np.eye(n))
+    S = s[:, None] * O.kernel_W(X, eps) * s[None, :]
+    exact = np.linalg.norm(St - S, 2)
+    est = O.hmatvec_error_2norm(X, eps, s, H, iters=60)
+    assert est <= exact * (1 + 1e-12) + 1e-15
+    assert est >= exact * (1 - 1e-3)
+
+
+def test_hmatvec_error_2norm_vanishes_at_zero_tolerance_full_rank():
+    X = _scurve(256, 3)
+    eps = O.median_sqdist(X)
+    _, _, s = O.degrees(X, eps, 1.0)
+    H = O.compress(X, eps, s, 32, 0.0, 256)
+    assert O.hmatvec_error_2norm(X, eps, s, H, iters=10) < 1e-12
