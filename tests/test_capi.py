@@ -77,6 +77,22 @@ def test_request_footprint_estimate_is_monotone_and_plausible():
     assert 500e6 < big < 1.5e9
 
 
+def test_request_footprint_counts_the_point_copies():
+    """Points are held as the caller's copy, the centred/scaled copy and the permuted copy
+    (4 N d bytes each); from d = 16 on the tree build also holds an FP64 copy (8 N d bytes)."""
+    import numpy as np
+
+    import paper_2311_06115_gb300 as dm
+
+    n = 60_000
+    kw = dict(leaf_size=256, max_rank=128, k=10)
+    hd = dm.dm_request_bytes(np.zeros((n, 784), np.float32), **kw)
+    assert hd >= 20 * n * 784
+    d15 = dm.dm_request_bytes(np.zeros((n, 15), np.float32), **kw)
+    d16 = dm.dm_request_bytes(np.zeros((n, 16), np.float32), **kw)
+    assert d16 - d15 >= 8 * n * 16 + 12 * n - 3 * 256  # each buffer rounded up to 256 bytes
+
+
 def test_serving_rejects_bad_requests_and_state():
     import numpy as np
     import torch
